@@ -1,0 +1,328 @@
+"""Pins of the oracle's local functions against mathematics: finite
+differences, closed forms, brute force and library eigen-solvers.
+
+Each test names the passage of the paper its function follows."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+
+RNG = np.random.default_rng(1234)
+
+
+def fd_grad(f, x, eps=1e-6):
+    g = np.zeros_like(x)
+    for i in range(len(x)):
+        e = np.zeros_like(x)
+        e[i] = eps
+        g[i] = (f(x + e) - f(x - e)) / (2 * eps)
+    return g
+
+
+def fd_hess(gf, x, eps=1e-6):
+    n = len(x)
+    H = np.zeros((n, n))
+    for i in range(n):
+        e = np.zeros_like(x)
+        e[i] = eps
+        H[:, i] = (gf(x + e) - gf(x - e)) / (2 * eps)
+    return H
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-30)
+
+
+# ---------------------------------------------------------------------------
+# Distances (Eq. 5's d_k; pair geometry of Eq. 6-8)
+# ---------------------------------------------------------------------------
+def brute_pt_d2(x12, n=400):
+    """Squared point-triangle distance by dense barycentric sampling followed
+    by local refinement (no region logic)."""
+    p, a, b, c = x12.reshape(4, 3)
+    best = np.inf
+    us = np.linspace(0, 1, n)
+    U, V = np.meshgrid(us, us)
+    m = U + V <= 1
+    pts = a + U[m, None] * (b - a) + V[m, None] * (c - a)
+    d2 = ((pts - p) ** 2).sum(1)
+    k = np.argmin(d2)
+    u0, v0 = U[m][k], V[m][k]
+    # refine: projected gradient descent on (u, v) in the simplex
+    u, v = u0, v0
+    step = 1.0 / n
+    for _ in range(200):
+        improved = False
+        for du, dv in ((step, 0), (-step, 0), (0, step), (0, -step), (step, -step), (-step, step)):
+            uu, vv = u + du, v + dv
+            if uu < 0 or vv < 0 or uu + vv > 1:
+                continue
+            q = a + uu * (b - a) + vv * (c - a)
+            dd = ((q - p) ** 2).sum()
+            qq = a + u * (b - a) + v * (c - a)
+            if dd < ((qq - p) ** 2).sum():
+                u, v = uu, vv
+                improved = True
+        if not improved:
+            step *= 0.5
+            if step < 1e-14:
+                break
+    q = a + u * (b - a) + v * (c - a)
+    return min(best, ((q - p) ** 2).sum())
+
+
+def brute_ee_d2(x12, n=400):
+    a0, a1, b0, b1 = x12.reshape(4, 3)
+    s = np.linspace(0, 1, n)
+    P = a0 + s[:, None] * (a1 - a0)
+    Q = b0 + s[:, None] * (b1 - b0)
+    D = ((P[:, None, :] - Q[None, :, :]) ** 2).sum(-1)
+    i, j = np.unravel_index(np.argmin(D), D.shape)
+    u, v = s[i], s[j]
+    step = 1.0 / n
+    f = lambda u, v: (((a0 + u * (a1 - a0)) - (b0 + v * (b1 - b0))) ** 2).sum()
+    for _ in range(400):
+        improved = False
+        for du, dv in ((step, 0), (-step, 0), (0, step), (0, -step), (step, step), (-step, -step),
+                       (step, -step), (-step, step)):
+            uu, vv = min(max(u + du, 0), 1), min(max(v + dv, 0), 1)
+            if f(uu, vv) < f(u, v):
+                u, v = uu, vv
+                improved = True
+        if not improved:
+            step *= 0.5
+            if step < 1e-15:
+                break
+    return f(u, v)
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_pt_distance_brute_force(seed):
+    rng = np.random.default_rng(seed)
+    x = rng.standard_normal(12)
+    if seed % 4 == 0:  # point near the triangle's plane
+        x[0:3] = x[3:6] * 0.3 + x[6:9] * 0.3 + x[9:12] * 0.4 + 0.05 * rng.standard_normal(3)
+    d2, kind, w, _, _ = O.stencil_d2(x, 0)
+    ref = brute_pt_d2(x)
+    assert abs(d2 - ref) <= 1e-9 * max(1.0, ref)
+    # weights reproduce the closest-point difference vector: |sum w_i x_i|^2 = d^2
+    diff = (w[:, None] * x.reshape(4, 3)).sum(0)
+    assert abs(diff @ diff - d2) <= 1e-10 * max(1.0, d2)
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_ee_distance_brute_force(seed):
+    rng = np.random.default_rng(100 + seed)
+    x = rng.standard_normal(12)
+    if seed % 5 == 0:  # nearly parallel edges
+        x[9:12] = x[6:9] + (x[3:6] - x[0:3]) * 0.7 + 1e-9 * rng.standard_normal(3)
+    d2, kind, w, _, _ = O.stencil_d2(x, 1)
+    ref = brute_ee_d2(x)
+    assert abs(d2 - ref) <= 1e-9 * max(1.0, ref)
+    diff = (w[:, None] * x.reshape(4, 3)).sum(0)
+    assert abs(diff @ diff - d2) <= 1e-10 * max(1.0, d2)
+
+
+def test_distance_closed_forms():
+    # point 0.3 above the interior of a triangle in the z=0 plane
+    x = np.array([0.2, 0.2, 0.3, 0, 0, 0, 1, 0, 0, 0, 1, 0], dtype=float)
+    d2, kind, _, _, _ = O.stencil_d2(x, 0)
+    assert kind == 2 and abs(d2 - 0.09) < 1e-15
+    # crossed perpendicular edges separated by 0.25 along z
+    x = np.array([-1, 0, 0, 1, 0, 0, 0, -1, 0.25, 0, 1, 0.25], dtype=float)
+    d2, kind, _, _, _ = O.stencil_d2(x, 1)
+    assert kind == 3 and abs(d2 - 0.0625) < 1e-15
+    # parallel edges offset: endpoint-interior distance
+    x = np.array([0, 0, 0, 1, 0, 0, 0.5, 0.2, 0, 1.5, 0.2, 0], dtype=float)
+    d2, kind, _, _, _ = O.stencil_d2(x, 1)
+    assert abs(d2 - 0.04) < 1e-15
+
+
+@pytest.mark.parametrize("seed", range(12))
+@pytest.mark.parametrize("is_ee", [0, 1])
+def test_distance_derivatives_fd(seed, is_ee):
+    rng = np.random.default_rng(seed + 17 * is_ee)
+    x = rng.standard_normal(12)
+    kind0 = O.stencil_d2(x, is_ee)[1]
+    f = lambda y: O.stencil_d2(y, is_ee)[0]
+    g = lambda y: O.stencil_d2(y, is_ee, derivs=True)[3]
+    # stay in the same closest-feature region for the difference quotients
+    for eps in (1e-6,):
+        ok = all(O.stencil_d2(x + eps * e, is_ee)[1] == kind0 for e in np.eye(12)) and all(
+            O.stencil_d2(x - eps * e, is_ee)[1] == kind0 for e in np.eye(12))
+        if not ok:
+            pytest.skip("on a region boundary")
+    _, _, _, g0, H0 = O.stencil_d2(x, is_ee, derivs=True)
+    assert rel(g0, fd_grad(f, x)) < 1e-6
+    assert rel(H0, fd_hess(g, x)) < 1e-5
+
+
+# ---------------------------------------------------------------------------
+# Barrier (Eq. 4, Eq. 5) and its pair derivatives (Eq. 7, Eq. 8)
+# ---------------------------------------------------------------------------
+def test_barrier_vanishes_at_dhat_c2():
+    dh = 1e-3
+    assert O.barrier(dh, dh) == 0.0
+    assert O.barrier(1.5 * dh, dh) == 0.0
+    # first and second derivative vanish at dhat (C2 continuity): one-sided
+    # differences from below are O(eps^2) and O(eps)
+    e = 1e-7 * dh
+    b1 = O.barrier(dh - e, dh)
+    assert b1 < 1e-18 and b1 > 0
+    d = np.linspace(0.05 * dh, 0.99 * dh, 50)
+    b = np.array([O.barrier(t, dh) for t in d])
+    assert np.all(b > 0) and np.all(np.diff(b) < 0)
+    # logarithmic growth toward contact: b(eps dhat) ~ -dhat^2 ln(eps)
+    assert O.barrier(1e-12 * dh, dh) > 0.99 * dh * dh * 12 * np.log(10)
+
+
+@pytest.mark.parametrize("seed", range(10))
+@pytest.mark.parametrize("is_ee", [0, 1])
+def test_pair_barrier_fd(seed, is_ee):
+    rng = np.random.default_rng(500 + seed + 31 * is_ee)
+    dh = 1.0
+    for _ in range(100):
+        x = rng.standard_normal(12) * 0.6
+        d2 = O.stencil_d2(x, is_ee)[0]
+        if 0.05 < d2 < 0.8:
+            break
+    eps_x = 1e-3 if seed % 2 else 10.0  # exercise the mollified branch
+    f = lambda y: O.pair_barrier(y, is_ee, dh, eps_x, project=False)[0]
+    gf = lambda y: O.pair_barrier(y, is_ee, dh, eps_x, project=False)[1]
+    b, g, H = O.pair_barrier(x, is_ee, dh, eps_x, project=False)
+    assert b > 0
+    assert rel(g, fd_grad(f, x)) < 1e-6
+    assert rel(H, fd_hess(gf, x)) < 1e-5
+    _, _, Hp = O.pair_barrier(x, is_ee, dh, eps_x, project=True)
+    ev = np.linalg.eigvalsh(Hp)
+    assert ev.min() >= -1e-10 * np.abs(ev).max()
+
+
+def test_psd_projection_keeps_psd_matrices():
+    A = RNG.standard_normal((12, 12))
+    M = A @ A.T
+    ev_j = O.eigvals(M)
+    assert np.allclose(ev_j, np.linalg.eigvalsh(M), rtol=1e-10, atol=1e-10)
+    S = A + A.T
+    assert np.allclose(O.eigvals(S), np.linalg.eigvalsh(S), rtol=1e-10, atol=1e-10)
+
+
+# ---------------------------------------------------------------------------
+# Friction mollifier (Eq. 10)
+# ---------------------------------------------------------------------------
+def test_f0_f1_definitions():
+    eh = 1e-5
+    ys = np.linspace(1e-9, 3 * eh, 301)
+    # f0' = f1 (finite differences)
+    for y in ys:
+        e = 1e-9 * eh
+        d = (O.f0(y + e, eh) - O.f0(y - e, eh)) / (2 * e)
+        assert abs(d - O.f1(y, eh)) < 1e-6
+    assert abs(O.f0(eh, eh) - eh) < 1e-20
+    # C1 at eps_v h and f1 in [0, 1], increasing
+    assert abs(O.f1(eh * (1 - 1e-12), eh) - 1.0) < 1e-9
+    f1s = np.array([O.f1(y, eh) for y in ys])
+    assert np.all(f1s >= 0) and np.all(f1s <= 1 + 1e-15) and np.all(np.diff(f1s) >= -1e-15)
+    assert O.f1(0.0, eh) == 0.0
+
+
+# ---------------------------------------------------------------------------
+# Neo-Hookean (material section) and affine orthogonality (Eq. 2)
+# ---------------------------------------------------------------------------
+def rot(seed):
+    q, r = np.linalg.qr(np.random.default_rng(seed).standard_normal((3, 3)))
+    q = q @ np.diag(np.sign(np.diag(r)))
+    if np.linalg.det(q) < 0:
+        q[:, 0] *= -1
+    return q
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_neo_hookean_rest_and_fd(seed):
+    mu, lam = 3.5e4, 3.1e5
+    R = rot(seed)
+    psi, g, _ = O.nh(R, mu, lam)
+    assert abs(psi) < 1e-9 * mu and np.abs(g).max() < 1e-9 * mu
+    F = np.eye(3) + 0.2 * np.random.default_rng(seed).standard_normal((3, 3))
+    assert np.linalg.det(F) > 0
+    f = lambda y: O.nh(y, mu, lam)[0]
+    gf = lambda y: O.nh(y, mu, lam)[1]
+    psi, g, H = O.nh(F, mu, lam)
+    assert rel(g, fd_grad(f, F.ravel())) < 1e-6
+    assert rel(H, fd_hess(gf, F.ravel())) < 1e-5
+    _, _, Hp = O.nh(F, mu, lam, project=True)
+    ev = np.linalg.eigvalsh(Hp)
+    assert ev.min() >= -1e-9 * np.abs(ev).max()
+    # inverted element: infinite energy
+    Fi = F.copy()
+    Fi[:, 0] *= -1
+    assert O.nh(Fi, mu, lam)[0] == np.inf
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_ortho_energy(seed):
+    R = rot(seed + 10)
+    v, g, _ = O.ortho(R)
+    assert abs(v) < 1e-24 and np.abs(g).max() < 1e-12
+    A = np.eye(3) + 0.3 * np.random.default_rng(seed).standard_normal((3, 3))
+    v, g, H = O.ortho(A)
+    ref = np.linalg.norm(A @ A.T - np.eye(3)) ** 2  # |A A^T - I|_F^2
+    assert abs(v - ref) < 1e-12 * max(1, ref)
+    f = lambda y: O.ortho(y)[0]
+    gf = lambda y: O.ortho(y)[1]
+    assert rel(g, fd_grad(f, A.ravel())) < 1e-7
+    assert rel(H, fd_hess(gf, A.ravel())) < 1e-6
+
+
+# ---------------------------------------------------------------------------
+# Additive CCD (line-search step bound)
+# ---------------------------------------------------------------------------
+def test_accd_head_on_closed_form():
+    # point at height d0 over a fixed triangle interior, moving straight down
+    for d0, P in ((1e-2, 0.05), (3e-4, 1.0), (0.2, 0.21)):
+        x = np.array([0.2, 0.2, d0, 0, 0, 0, 1, 0, 0, 0, 1, 0], dtype=float)
+        p = np.zeros(12)
+        p[2] = -P
+        t, _ = O.accd(x, p, 0)
+        assert abs(t - 0.9 * d0 / P) < 1e-12 * max(1, d0 / P)
+    # no approach within the step: full step
+    x = np.array([0.2, 0.2, 1.0, 0, 0, 0, 1, 0, 0, 0, 1, 0], dtype=float)
+    p = np.zeros(12)
+    p[2] = -0.1
+    assert O.accd(x, p, 0)[0] == 1.0
+
+
+def true_toi(x, p, is_ee, n=4000):
+    ts = np.linspace(0, 1, n + 1)
+    d = np.array([O.stencil_d2(x + t * p, is_ee)[0] for t in ts])
+    hit = np.nonzero(d <= 1e-24)[0]
+    if len(hit) == 0:
+        # local minima of the sampled distance: refine each by bisection on the
+        # sign of the distance change
+        return 1.0 if d.min() > 0 else 0.0
+    return ts[hit[0]]
+
+
+@pytest.mark.parametrize("seed", range(30))
+@pytest.mark.parametrize("is_ee", [0, 1])
+def test_accd_conservative(seed, is_ee):
+    rng = np.random.default_rng(900 + seed + 50 * is_ee)
+    x = rng.standard_normal(12)
+    # aim the stencil to pass through contact: move point/edge a toward the other feature
+    target = x.reshape(4, 3)[1:].mean(0) if not is_ee else x.reshape(4, 3)[2:].mean(0)
+    src = x.reshape(4, 3)[0] if not is_ee else x.reshape(4, 3)[:2].mean(0)
+    p = np.zeros(12)
+    k = 1 if not is_ee else 2
+    for i in range(k):
+        p[3 * i:3 * i + 3] = 2.0 * (target - src) + 0.1 * rng.standard_normal(3)
+    t, _ = O.accd(x, p, is_ee)
+    assert 0 < t <= 1.0
+    # positions at the returned time are separated
+    assert O.stencil_d2(x + t * p, is_ee)[0] > 0
+    # and no sampled time before t touches
+    ts = np.linspace(0, t, 200)
+    dmin = min(O.stencil_d2(x + s * p, is_ee)[0] for s in ts)
+    assert dmin > 0
+    # distance at t is at least s = 0.1 of the initial one
+    d0 = np.sqrt(O.stencil_d2(x, is_ee)[0])
+    assert np.sqrt(O.stencil_d2(x + t * p, is_ee)[0]) >= 0.1 * d0 * (1 - 1e-9) or t == 1.0

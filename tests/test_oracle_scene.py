@@ -1,0 +1,264 @@
+"""Scene-level pins of the oracle: analytic free fall, closed-form mass
+properties, finite differences of the complete incremental potential,
+monotone Newton energies, intersection-free trajectories (independent
+triangle-triangle tests), momentum conservation and Coulomb sliding."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from oracle.oracle import Oracle
+from paper_2311_05945_b300 import scenes as S
+
+
+def test_free_fall_analytic():
+    # Eq. 1 / Eq. 2 with no contact: the minimiser of the IP is the predictor,
+    # x_n = x_0 + h^2 g n (n+1) / 2 from rest, reached in one Newton step.
+    s = S.scene_free_fall(n_steps=4)
+    o = Oracle(s)
+    x0 = o.tet_positions().copy()
+    q0 = o.affine_q(0).copy()
+    st = o.step(4)
+    h, g, n = s.params.dt, s.params.gravity[1], 4
+    dy = h * h * g * n * (n + 1) / 2
+    x = o.tet_positions()
+    assert np.abs(x[:, 1] - x0[:, 1] - dy).max() < 1e-12
+    assert np.abs(x[:, [0, 2]] - x0[:, [0, 2]]).max() < 1e-12
+    q = o.affine_q(0)
+    assert abs(q[1] - q0[1] - dy) < 1e-12
+    assert np.abs(np.delete(q - q0, 1)).max() < 1e-12
+    assert np.all(st[:, 0, 0] == 1)
+
+
+def test_surface_and_lumped_mass_c1():
+    s = S.scene_c1()
+    o = Oracle(s)
+    c = o.counts()
+    # soft cube surface: 98 verts, 192 tris, 288 edges; plus two boxes (8, 12, 18 each)
+    assert c["n_sv"] == 98 + 16 and c["n_tris"] == 192 + 24 and c["n_edges"] == 288 + 36
+    sv, e, t = o.surface()
+    soft_t = t[:192]
+    P = np.array([s.tets[0].X[sv[i, 2]] for i in range(98)])
+    v = P[soft_t]
+    vol = np.einsum("ij,ij->i", v[:, 0], np.cross(v[:, 1], v[:, 2])).sum() / 6.0
+    assert abs(vol - 1.0) < 1e-12  # closed and outward: encloses the unit cube
+    # every surface edge borders exactly two triangles
+    from collections import Counter
+    cnt = Counter()
+    for tri in soft_t:
+        for a, b in ((0, 1), (1, 2), (2, 0)):
+            cnt[tuple(sorted((tri[a], tri[b])))] += 1
+    assert set(cnt.values()) == {2}
+    m = o.lumped_mass()
+    assert abs(m.sum() - 1000.0) < 1e-9
+
+
+@pytest.mark.parametrize("ext,center", [((0.3, 0.5, 0.7), (0, 0, 0)), ((0.2, 0.1, 0.4), (0.3, -0.2, 0.1))])
+def test_affine_mass_box(ext, center):
+    # M_b = integral rho J^T J (Eq. 2) for a box: m = rho a b c, p-block m I,
+    # a_i-blocks S = integral rho x0 x0^T = m (diag(a^2, b^2, c^2)/12 + c c^T),
+    # p-a_i coupling m c (zero when centred).
+    V, F = S.box_surface(ext, 3)
+    V = V + np.array(center)
+    s = S.Scene("box", S.Params())
+    s.affines.append(S.AffineBody(V, F, S.q_identity((0, 0, 0)), rho=700.0, stiffness=1e8, mu=0.5))
+    o = Oracle(s)
+    M, m, vol = o.affine_mass(0)
+    a, b, c = ext
+    assert abs(vol - a * b * c) < 1e-14
+    assert abs(m - 700.0 * a * b * c) < 1e-11
+    cc = np.array(center, dtype=float)
+    Sref = m * (np.diag([a * a, b * b, c * c]) / 12.0 + np.outer(cc, cc))
+    assert np.allclose(M[:3, :3], m * np.eye(3), atol=1e-12)
+    for i in range(3):
+        blk = M[3 + 3 * i:6 + 3 * i, 3 + 3 * i:6 + 3 * i]
+        assert np.allclose(blk, Sref, atol=1e-12)
+        cpl = M[i, 3 + 3 * i:6 + 3 * i]
+        assert np.allclose(cpl, m * cc, atol=1e-12)
+        for j in range(3):
+            if j != i:
+                assert np.abs(M[3 + 3 * i:6 + 3 * i, 3 + 3 * j:6 + 3 * j]).max() < 1e-15
+
+
+def _advance(o, n):
+    for _ in range(n):
+        o.step(1)
+
+
+def test_full_energy_gradient_fd():
+    # Complete B_t + D (Eq. 4, Eq. 11) with inertia, elasticity, orthogonality,
+    # barrier and lagged friction active: gradient against central differences.
+    s = S.scene_tiny_contact(mu=0.5)
+    o = Oracle(s)
+    _advance(o, 6)
+    o.prepare(0, friction=True)
+    y0 = o.dofs()
+    rng = np.random.default_rng(3)
+    y = y0 + 2e-5 * rng.standard_normal(len(y0)) * (np.abs(y0) > -1)
+    E, g, H, na = o.eval(y, grad=True, hess=True)
+    assert na > 0 and np.isfinite(E)
+    eps = 1e-8
+    fd = np.zeros_like(y)
+    for i in range(len(y)):
+        e = np.zeros_like(y)
+        e[i] = eps
+        fd[i] = (o.eval(y + e)[0] - o.eval(y - e)[0]) / (2 * eps)
+    err = np.abs(fd - g).max() / np.abs(g).max()
+    assert err < 1e-5, err
+    ev = np.linalg.eigvalsh(0.5 * (H + H.T))
+    assert ev.min() > 0  # projected Hessian plus mass terms: SPD
+
+
+def tri_tri_intersect(P, T1, T2):
+    """Independent FP64 test: does any edge of one triangle cross the other."""
+    def orient(a, b, c, d):
+        return np.einsum("...i,...i->...", np.cross(b - a, c - a), d - a)
+
+    def seg_tri(p, q, a, b, c):
+        s1, s2 = orient(a, b, c, p), orient(a, b, c, q)
+        o1, o2, o3 = orient(p, q, a, b), orient(p, q, b, c), orient(p, q, c, a)
+        cross = (s1 * s2 <= 0)
+        same = ((o1 >= 0) & (o2 >= 0) & (o3 >= 0)) | ((o1 <= 0) & (o2 <= 0) & (o3 <= 0))
+        return cross & same
+
+    A = P[T1]
+    B = P[T2]
+    hit = np.zeros(len(T1), dtype=bool)
+    for (i, j) in ((0, 1), (1, 2), (2, 0)):
+        hit |= seg_tri(A[:, i], A[:, j], B[:, 0], B[:, 1], B[:, 2])
+        hit |= seg_tri(B[:, i], B[:, j], A[:, 0], A[:, 1], A[:, 2])
+    return hit
+
+
+def surface_world(o, s):
+    """World positions of the oracle's surface vertices, computed here from
+    the body states (soft: global vertex index; affine: A x0 + p)."""
+    sv, e, t = o.surface()
+    soft = np.concatenate([o.tet_positions(i) for i in range(len(s.tets))]) if s.tets else np.zeros((0, 3))
+    P = np.zeros((len(sv), 3))
+    for i, (b, aff, idx) in enumerate(sv):
+        kind, k = s.body_order()[b]
+        if kind == "tet":
+            P[i] = soft[idx]
+        else:
+            q = o.get_state(b)[:12]
+            A = q[3:].reshape(3, 3)
+            P[i] = A @ s.affines[k].V[idx] + q[:3]
+    return sv, t, P
+
+
+def test_monotone_energy_no_intersection_tiny():
+    s = S.scene_tiny_contact(mu=0.5)
+    o = Oracle(s)
+    for step in range(12):
+        st = o.step(1)
+        log = o.energy_log()
+        assert np.all(np.diff(log) <= 1e-12 * np.abs(log).max()), log
+        assert st[0, 0, 4] > 0  # d_min > 0
+        sv, t, P = surface_world(o, s)
+        body = sv[t[:, 0], 0]
+        i, j = np.triu_indices(len(t), 1)
+        m = body[i] != body[j]
+        shared = np.array([len(set(t[a]) & set(t[b])) > 0 for a, b in zip(i[m], j[m])])
+        ii, jj = i[m][~shared], j[m][~shared]
+        assert not tri_tri_intersect(P, t[ii], t[jj]).any()
+
+
+def test_momentum_conservation_zero_gravity():
+    # no gravity, no fixed or kinematic bodies: total linear momentum
+    # sum m_i v_i + sum (m_b pdot_b + Adot_b integral rho x0) is conserved
+    p = S.Params(dt=0.01, gravity=(0.0, 0.0, 0.0))
+    s = S.Scene("momentum", p)
+    X, T = S.soft_cube(3, 0.2, (0.0, 0.0, 0.0))
+    v0 = np.zeros_like(X)
+    v0[:, 0] = 2.0
+    s.tets.append(S.TetBody(X, T, E=1e5, nu=0.4, rho=1000.0, mu=0.3, v0=v0))
+    V, F = S.box_surface((0.15, 0.15, 0.15), 2)
+    s.affines.append(S.AffineBody(V, F, S.q_identity((0.2 + 0.0755 + 0.01, 0.1, 0.08)), rho=1000.0,
+                                  stiffness=1e8, mu=0.3))
+    o = Oracle(s, tol_scale=1e-3)
+    m = o.lumped_mass()
+    M, mb, _ = o.affine_mass(0)
+
+    def momentum():
+        st = o.get_state(0)
+        n = len(st) // 6
+        v = st[3 * n:].reshape(n, 3)
+        qs = o.get_state(1)
+        qd = qs[12:]
+        c = M[0, 3:6] / mb * mb  # integral rho x0
+        Ad = qd[3:].reshape(3, 3)
+        return (m[:, None] * v).sum(0) + mb * qd[:3] + Ad @ c
+
+    P0 = momentum()
+    touched = False
+    for k in range(12):
+        st = o.step(1)
+        touched |= st[0, 0, 3] > 0
+    assert touched
+    P1 = momentum()
+    assert np.abs(P1 - P0).max() < 1e-6 * np.abs(P0).max()
+
+
+def test_coulomb_sliding_deceleration():
+    # A flat affine block sliding on a fixed floor decelerates at mu g (Eq. 9):
+    # once settled, the lagged normal force balances gravity and the kinetic
+    # friction force is mu N.  The block first settles at rest, then gets 1 m/s.
+    p = S.Params(dt=0.01)
+    s = S.Scene("slide", p)
+    Vf, Ff = S.box_surface((4.0, 0.1, 4.0), 1)
+    s.affines.append(S.AffineBody(Vf, Ff, S.q_identity((0, -0.05, 0)), rho=1000.0, stiffness=1e8,
+                                  mu=0.5, mode=1))
+    V, F = S.box_surface((0.2, 0.04, 0.2), 1)
+    s.affines.append(S.AffineBody(V, F, S.q_identity((0.3, 0.02 + 0.002, 0.1)), rho=1000.0,
+                                  stiffness=1e8, mu=0.5))
+    o = Oracle(s)
+    for _ in range(40):
+        o.step(1)
+    st = o.get_state(1)
+    st[12:] = 0.0
+    st[12] = 1.0
+    o.set_state(1, st)
+    vs = []
+    for k in range(16):
+        o.step(1)
+        vs.append(o.get_state(1)[12])
+    vs = np.array(vs)
+    dec = -(vs[14] - vs[4]) / (10 * p.dt)
+    assert abs(dec - 0.5 * 9.81) < 0.02 * 0.5 * 9.81, (dec, vs)
+
+
+def test_brute_candidates_match_numpy_definition():
+    s = S.random_state_scene(7)
+    o = Oracle(s)
+    sv, e, t = o.surface()
+    _, _, P = surface_world(o, s)
+    P = P + 0.003 * np.random.default_rng(7).standard_normal(P.shape)
+    order = s.body_order()
+    bclass = np.array([0 if k == "tet" else (1 + (s.affines[i].mode == 1) + 2 * (s.affines[i].mode == 2))
+                       for k, i in order], dtype=np.int32)
+    benv = np.zeros(len(order), dtype=np.int32)
+    infl = 0.05
+    pt, ee = O.brute_pairs(P, sv[:, 0], bclass, benv, e, t, infl)
+    # numpy all-pairs definition
+    lo = lambda ids: P[ids].min(1) - infl
+    hi = lambda ids: P[ids].max(1) + infl
+    plo, phi = P - infl, P + infl
+    tlo, thi = lo(t), hi(t)
+    ov = np.all((plo[:, None] <= thi[None]) & (tlo[None] <= phi[:, None]), -1)
+    share = (t[None, :, :] == np.arange(len(P))[:, None, None]).any(-1)
+    svb = sv[:, 0]
+    same_aff = (svb[:, None] == svb[t[:, 0]][None]) & (bclass[svb][:, None] != 0)
+    ref_pt = set(map(tuple, np.argwhere(ov & ~share & ~same_aff)))
+    got_pt = set((a, b) for a, b in zip(pt[:, 0], [tuple(x) for x in pt[:, 1:]]))
+    tri_index = {tuple(x): i for i, x in enumerate(t)}
+    got_pt = set((a, tri_index[b]) for a, b in got_pt)
+    assert got_pt == ref_pt and len(ref_pt) > 0
+    elo, ehi = lo(e), hi(e)
+    ov = np.all((elo[:, None] <= ehi[None]) & (elo[None] <= ehi[:, None]), -1)
+    share = (e[:, None, :, None] == e[None, :, None, :]).any((-1, -2))
+    same_aff = (svb[e[:, 0]][:, None] == svb[e[:, 0]][None]) & (bclass[svb[e[:, 0]]][:, None] != 0)
+    iu = np.triu(np.ones_like(ov), 1)
+    ref_ee = set(map(tuple, np.argwhere(ov & ~share & ~same_aff & iu)))
+    edge_index = {tuple(x): i for i, x in enumerate(e)}
+    got_ee = set((edge_index[(a, b)], edge_index[(c, d)]) for a, b, c, d in ee)
+    assert got_ee == ref_ee and len(ref_ee) > 0
