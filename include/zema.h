@@ -1,0 +1,216 @@
+/*
+ * zema.h -- C ABI of the B300-native soft-rigid coupled IPC time step.
+ *
+ * The library advances a scene of tetrahedral soft bodies and 12-DOF affine
+ * bodies by minimising, per time step, the barrier-augmented incremental
+ * potential with lagged friction (paper section III: Eq. 1-11) with projected
+ * Newton.  Every step of the Newton iteration runs in the library's CUDA
+ * kernels on one GPU (sm_103a).
+ *
+ * Conventions for every entry point:
+ *  - Return value: a zema_status; ZEMA_OK on success.  No C++ exception ever
+ *    crosses this boundary.  zema_last_error() gives a message for the last
+ *    failure on a scene.
+ *  - Host arrays passed in are owned by the caller, read during the call and
+ *    never retained.  Host arrays passed out are caller-allocated.
+ *  - Arrays of 3-vectors are row-major (n x 3) doubles; index arrays int32.
+ *  - A scene must not be used from two host threads at once.
+ *  - Units are SI (m, kg, s).  Gravity comes from the scene parameters.
+ *  - Affine state q = (p, a1, a2, a3), A = (a1, a2, a3)^T stored by rows; a
+ *    rest vertex x0 maps to x = A x0 + p (Eq. 2).  The library works
+ *    internally in a centre-of-mass frame and converts at the boundary.
+ *  - Bodies in different environments (env) never interact; env ids are
+ *    0 .. n_envs-1.
+ *  - On a non-OK status from zema_step the state is left at the last
+ *    completed time step.
+ */
+#ifndef ZEMA_H
+#define ZEMA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ZEMA_OK = 0,
+    ZEMA_ERR_INVALID_ARG = 1,
+    ZEMA_ERR_OOM = 2,
+    ZEMA_ERR_CUDA = 3,
+    ZEMA_ERR_INTERSECTING_INPUT = 4,
+    ZEMA_ERR_INVERTED_INPUT = 5,
+    ZEMA_ERR_NEWTON_MAXITER = 6,
+    ZEMA_ERR_LINESEARCH = 7,
+    ZEMA_ERR_PCG_MAXITER = 8,
+    ZEMA_ERR_NONFINITE = 9,
+    ZEMA_ERR_FAULT_INJECTED = 10,
+    ZEMA_ERR_STATE = 11
+} zema_status;
+
+typedef struct zema_scene zema_scene; /* opaque; owns all of its device memory */
+
+/* Device allocator hooks (optional).  alloc(bytes, stream, ctx) returns device
+ * memory or NULL; free(ptr, stream, ctx) releases it.  When alloc is NULL the
+ * library uses cudaMalloc / cudaFree. */
+typedef void* (*zema_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*zema_free_fn)(void* ptr, void* stream, void* ctx);
+
+typedef struct {
+    double dt;             /* time step h (s) */
+    double dhat;           /* barrier activation distance (m), Eq. 5 */
+    double kappa;          /* barrier stiffness; <= 0 selects the adaptive rule */
+    double eps_v;          /* friction velocity threshold (m/s), Eq. 10 */
+    double newton_tol_rel; /* Newton stop: max |step| <= newton_tol_rel * bbox diagonal * dt */
+    double gravity[3];     /* m/s^2 */
+    double pcg_rel_tol;    /* PCG stop: |r| <= pcg_rel_tol * |b| */
+    int32_t max_newton;    /* Newton iteration cap per solve */
+    int32_t max_pcg;       /* PCG iteration cap per solve */
+    int32_t max_al_rounds; /* kinematic augmented-Lagrangian rounds per step */
+    int32_t precision;     /* 0: FP64 throughout; 1: mixed (FP32 elastic/affine Hessians and matvecs) */
+    int32_t n_envs;        /* number of independent environments */
+    int32_t warm_start;    /* 0: constant-velocity proposal; 1: learned proposal (needs weights) */
+    void* stream;          /* cudaStream_t used for all work; NULL = legacy default stream */
+    zema_alloc_fn alloc;   /* optional device allocator */
+    zema_free_fn free;
+    void* alloc_ctx;
+} zema_scene_params;
+
+/* Per-step statistics (summed over the steps of one zema_step call, over all
+ * environments; max for dmin-like fields as noted). */
+typedef struct {
+    int64_t steps;
+    int64_t newton_iters;   /* applied Newton steps */
+    int64_t pcg_iters;      /* PCG iterations over all solves */
+    int64_t ls_halvings;    /* line-search halvings */
+    int64_t al_rounds;      /* kinematic AL outer rounds */
+    int64_t warm_accepted;  /* accepted warm-start proposals (per env step) */
+    int64_t max_candidates; /* largest candidate-pair count seen in one broad phase */
+    int64_t max_active;     /* largest active (d < dhat) pair count */
+    double dmin;            /* smallest primitive distance after the last step (inf if none < dhat) */
+    double kappa;           /* barrier stiffness of env 0 after the last step */
+    double energy;          /* incremental potential of env 0 at the last converged iterate */
+    double ms_phase[6];     /* host-timed phases: DCD, energy, Hessian, linear, CCD, other (ms) */
+} zema_step_stats;
+
+/* Fills *p with defaults: dt 0.01, dhat 1e-3, adaptive kappa, eps_v 1e-3,
+ * tol 1e-3, g = (0, -9.81, 0), pcg tol 1e-4, caps 100 / 10000 / 10, FP64,
+ * one env, constant-velocity warm start, default stream and allocator. */
+void zema_default_params(zema_scene_params* p);
+
+/* Creates an empty scene.  Bodies are added next; the first zema_step (or
+ * zema_finalize) builds the device data (scene precompute: surface
+ * extraction, rest shapes, lumped and affine masses; Eq. 1, Eq. 2). */
+zema_status zema_create_scene(const zema_scene_params* params, zema_scene** out);
+
+/* Adds a tetrahedral soft body (Eq. 1, Neo-Hookean material).
+ * X_rest: nv x 3 rest positions; tets: nt x 4 vertex indices, each tet
+ * positively oriented (det[x1-x0, x2-x0, x3-x0] > 0, else
+ * ZEMA_ERR_INVERTED_INPUT); x0, v0: nv x 3 initial positions / velocities,
+ * NULL means X_rest / zero.  E (Pa), nu, rho (kg/m^3), mu_friction.  The
+ * body id (shared numbering with affine bodies, in order of addition) is
+ * written to *body_id. */
+zema_status zema_add_tet_body(zema_scene* s, int32_t env, const double* X_rest, int64_t nv,
+                              const int32_t* tets, int64_t nt, const double* x0, const double* v0,
+                              double E, double nu, double rho, double mu_friction, int32_t* body_id);
+
+/* Adds an affine body (Eq. 2): closed, outward-oriented triangle mesh
+ * V_rest (nv x 3, caller's rest frame) / F (nf x 3); q0 and qdot0 (12 each,
+ * qdot0 NULL = 0); density rho; stiffness = lambda of the orthogonality
+ * energy; mode 0 dynamic, 1 fixed, 2 kinematic (driven to the target of
+ * zema_set_kinematic_target by the augmented-Lagrangian term of Eq. 13). */
+zema_status zema_add_affine_body(zema_scene* s, int32_t env, const double* V_rest, int64_t nv,
+                                 const int32_t* F, int64_t nf, const double q0[12], const double qdot0[12],
+                                 double rho, double stiffness, double mu_friction, int32_t mode,
+                                 int32_t* body_id);
+
+/* Builds the device data now (optional; zema_step does it on first use).
+ * Fails with ZEMA_ERR_INTERSECTING_INPUT when two primitives of the initial
+ * state are at distance 0. */
+zema_status zema_finalize(zema_scene* s);
+
+/* Target q~ (12, caller's frame) of a kinematic affine body for the next
+ * step (Eq. 13). */
+zema_status zema_set_kinematic_target(zema_scene* s, int32_t body, const double q_target[12]);
+
+/* Advances n_steps time steps (Eq. 11).  stats may be NULL. */
+zema_status zema_step(zema_scene* s, int32_t n_steps, zema_step_stats* stats);
+
+/* State of one body into a caller-owned host buffer of cap doubles.
+ * Tet body: x then v (nv x 3 each); affine body: q then qdot (12 each).
+ * *written receives the number of doubles. */
+zema_status zema_get_state(const zema_scene* s, int32_t body, double* out, int64_t cap, int64_t* written);
+
+/* Sets the state of one body (same layout as zema_get_state). */
+zema_status zema_set_state(zema_scene* s, int32_t body, const double* in, int64_t n);
+
+/* All positions/velocities at once, device-to-device: x_dev and v_dev are
+ * device arrays of 3 * (total soft vertices) doubles in order of body
+ * addition (either may be NULL). */
+zema_status zema_copy_soft_state_device(const zema_scene* s, double* x_dev, double* v_dev);
+
+/* Counts: [0] soft vertices, [1] tets, [2] affine bodies, [3] surface
+ * vertices, [4] surface edges, [5] surface triangles, [6] nodes, [7] envs. */
+zema_status zema_scene_counts(const zema_scene* s, int64_t out[8]);
+
+/* Barrier stiffness kappa of an environment (after finalize). */
+zema_status zema_get_kappa(const zema_scene* s, int32_t env, double* kappa);
+/* Overrides kappa and kappa_min of an environment (disables the initial
+ * gradient-balance rule for it). */
+zema_status zema_set_kappa(zema_scene* s, int32_t env, double kappa, double kappa_min);
+
+const char* zema_last_error(const zema_scene* s);
+void zema_destroy_scene(zema_scene* s);
+
+/* ------------------------------------------------------------------------
+ * Evaluation entry points used by parity tests and tools.  They run the same
+ * device code as zema_step.
+ * ------------------------------------------------------------------------ */
+
+/* Prepares env state as at the start of a step (predictor, Eq. 1-3; lagged
+ * friction, Eq. 9-10; kappa) without advancing, then evaluates the total
+ * incremental potential B_t + D (Eq. 4, Eq. 11) at the current state.
+ * energy: n_envs doubles.  grad (nullable): gradient in the caller's frame,
+ * per body in order of addition: tet body 3 * nv, affine body 12 (dynamic and
+ * kinematic bodies; fixed bodies contribute 12 zeros). */
+zema_status zema_eval_energy_grad(zema_scene* s, int32_t apply_predictor, double* energy, double* grad);
+
+/* Candidate pairs of a raw surface (spatial-hash broad phase, Table I "DCD"):
+ * all PT (point, triangle) and EE (edge, edge) pairs whose axis-aligned boxes,
+ * inflated by `inflate` per side, overlap -- swept over pos0 -> pos1 when pos1
+ * is not NULL -- excluding pairs that share a vertex, pairs within one affine
+ * body, pairs whose bodies are both fixed or kinematic, and cross-env pairs.
+ * pos0/pos1: nsv x 3 host; sv_body: nsv; b_class (0 soft, 1 affine dynamic,
+ * 2 fixed, 3 kinematic) and b_env: nb; edges ne x 2; tris nt x 3.  Outputs
+ * (host, cap pairs each): pt_out (sv, tri) pairs, ee_out (edge, edge) with
+ * first < second; n_out[0..1] = counts (may exceed cap: then outputs are
+ * truncated).  cell_size <= 0 picks max(mean edge length, 2 * inflate). */
+zema_status zema_candidates_raw(int64_t nsv, const double* pos0, const double* pos1, const int32_t* sv_body,
+                                int64_t nb, const int32_t* b_class, const int32_t* b_env, int64_t ne,
+                                const int32_t* edges, int64_t nt, const int32_t* tris, double inflate,
+                                double cell_size, int64_t cap, int32_t* pt_out, int32_t* ee_out, int64_t* n_out,
+                                void* stream);
+
+/* Batched local kernels on host arrays (n stencils):
+ * barrier of PT (is_ee 0) or EE stencils x12 (n x 12): energy b (n), gradient
+ * (n x 12) and PSD-projected Hessian (n x 144) of kappa * e * b(d) with
+ * kappa = 1 (Eq. 5, Eq. 8); eps_x per stencil (EE mollifier). */
+zema_status zema_local_barrier(int64_t n, const double* x12, const int32_t* is_ee, const double* eps_x,
+                               double dhat, double* e_out, double* g_out, double* H_out, void* stream);
+/* Squared distances and closest-point weights (n x 4) of stencils. */
+zema_status zema_local_distance(int64_t n, const double* x12, const int32_t* is_ee, double* d2_out,
+                                double* w_out, void* stream);
+/* Neo-Hookean density Psi(F), F-space gradient (9) and PSD-projected Hessian
+ * (81) of n deformation gradients F (row-major). */
+zema_status zema_local_neo_hookean(int64_t n, const double* F9, double mu, double lam, double* psi_out,
+                                   double* g_out, double* H_out, void* stream);
+/* Additive CCD step bound t in (0, 1] of n stencils moving by p12 (s = 0.1). */
+zema_status zema_local_accd(int64_t n, const double* x12, const double* p12, const int32_t* is_ee,
+                            double* t_out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ZEMA_H */

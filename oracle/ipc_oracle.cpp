@@ -2015,6 +2015,7 @@ long orc_energy_log(void* s, double* out, long cap) {
     return n;
 }
 double orc_diag(void* s, int env) { return ((Scene*)s)->diag[env]; }
+double orc_kappa_min(void* s, int env) { return ((Scene*)s)->kappa_min[env]; }
 void orc_set_kappa(void* s, int env, double k, double kmin) {
     Scene& S = *(Scene*)s;
     S.kappa[env] = k;

@@ -35,6 +35,8 @@ def lib():
         L.orc_set_state.argtypes = [C.c_void_p, C.c_int, dp, C.c_long]
         L.orc_kappa.restype = C.c_double
         L.orc_kappa.argtypes = [C.c_void_p, C.c_int]
+        L.orc_kappa_min.restype = C.c_double
+        L.orc_kappa_min.argtypes = [C.c_void_p, C.c_int]
         L.orc_diag.restype = C.c_double
         L.orc_diag.argtypes = [C.c_void_p, C.c_int]
         L.orc_energy_log.restype = C.c_long
@@ -177,6 +179,9 @@ class Oracle:
 
     def kappa(self, env=0):
         return lib().orc_kappa(self.h, env)
+
+    def kappa_min(self, env=0):
+        return lib().orc_kappa_min(self.h, env)
 
     def diag(self, env=0):
         return lib().orc_diag(self.h, env)

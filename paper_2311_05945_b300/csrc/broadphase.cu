@@ -1,0 +1,369 @@
+// Spatial-hash broad phase.
+//
+// Every triangle and edge is entered into a uniform grid (hashed cells) once
+// per cell its box touches; entries are ordered by a stable radix sort on the
+// bucket so the table is deterministic.  Each surface point (PT) and edge
+// (EE) then visits the cells of its own box and tests the entries found
+// there.  A pair found in several shared cells is emitted only from the cell
+// that holds the minimum corner of the two boxes' intersection, so each pair
+// appears exactly once without a dedup pass.  Primitives whose box spans more
+// than kMaxCells cells are kept out of the grid ("oversize") and are tested by
+// a direct loop instead.
+#include "broadphase.cuh"
+
+namespace zema {
+
+constexpr double kMaxCells = 1024.0;
+
+struct Box6 {
+    double lo[3], hi[3];
+};
+
+__device__ __forceinline__ long long cell_of(double v, double inv) { return (long long)floor(v * inv); }
+
+__device__ __forceinline__ uint64_t pack_cell(long long cx, long long cy, long long cz) {
+    const long long off = 1ll << 20;
+    const uint64_t m = (1ull << 21) - 1;
+    return ((uint64_t)(cx + off) & m) | (((uint64_t)(cy + off) & m) << 21) | (((uint64_t)(cz + off) & m) << 42);
+}
+
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ Box6 ld_box(const double* b) {
+    Box6 r;
+    for (int k = 0; k < 3; ++k) {
+        r.lo[k] = b[k];
+        r.hi[k] = b[3 + k];
+    }
+    return r;
+}
+
+__device__ __forceinline__ bool overlap(const Box6& a, const Box6& b) {
+    for (int k = 0; k < 3; ++k)
+        if (a.lo[k] > b.hi[k] || b.lo[k] > a.hi[k]) return false;
+    return true;
+}
+
+// box of n surface vertices (ids) over X0 (and X1), inflated by infl
+__device__ __forceinline__ Box6 prim_box(const BPView& v, const int* ids, int n) {
+    Box6 b;
+    for (int k = 0; k < 3; ++k) {
+        b.lo[k] = INFINITY;
+        b.hi[k] = -INFINITY;
+    }
+    for (int i = 0; i < n; ++i) {
+        const double* p = v.X0 + 3 * (size_t)ids[i];
+        for (int k = 0; k < 3; ++k) {
+            b.lo[k] = fmin(b.lo[k], p[k]);
+            b.hi[k] = fmax(b.hi[k], p[k]);
+        }
+        if (v.X1) {
+            const double* q = v.X1 + 3 * (size_t)ids[i];
+            for (int k = 0; k < 3; ++k) {
+                b.lo[k] = fmin(b.lo[k], q[k]);
+                b.hi[k] = fmax(b.hi[k], q[k]);
+            }
+        }
+    }
+    for (int k = 0; k < 3; ++k) {
+        b.lo[k] -= v.infl;
+        b.hi[k] += v.infl;
+    }
+    return b;
+}
+
+__device__ __forceinline__ double box_cells(const Box6& b, double inv) {
+    double n = 1.0;
+    for (int k = 0; k < 3; ++k) n *= (double)(cell_of(b.hi[k], inv) - cell_of(b.lo[k], inv) + 1);
+    return n;
+}
+
+// kind: 0 points, 1 edges, 2 tris.  For edges and tris also the grid entry
+// count (0 when oversize) and the oversize flag.
+__global__ void k_boxes(BPView v, int kind, int n, double* box, uint32_t* cnt, uint32_t* big) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int ids[3];
+    int m;
+    if (kind == 0) {
+        ids[0] = i;
+        m = 1;
+    } else if (kind == 1) {
+        int2 e = v.edges[i];
+        ids[0] = e.x;
+        ids[1] = e.y;
+        m = 2;
+    } else {
+        int3 t = v.tris[i];
+        ids[0] = t.x;
+        ids[1] = t.y;
+        ids[2] = t.z;
+        m = 3;
+    }
+    Box6 b = prim_box(v, ids, m);
+    for (int k = 0; k < 3; ++k) {
+        box[6 * (size_t)i + k] = b.lo[k];
+        box[6 * (size_t)i + 3 + k] = b.hi[k];
+    }
+    if (cnt) {
+        double c = box_cells(b, v.inv_cell);
+        bool o = !(c <= kMaxCells);  // non-finite boxes count as oversize too
+        cnt[i] = o ? 0u : (uint32_t)c;
+        big[i] = o ? 1u : 0u;
+    }
+}
+
+// grid entries of one primitive family; bucket keys offset by bucket_base
+__global__ void k_emit_entries(BPView v, int n, const double* box, const uint32_t* off, uint32_t entry_base,
+                               uint64_t bucket_base, uint64_t tmask, uint64_t* key, uint32_t* val,
+                               uint64_t* cell_tmp, int* prim_tmp, int prim_flag) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t o = off[i], e = off[i + 1];
+    if (o == e) return;
+    Box6 b = ld_box(box + 6 * (size_t)i);
+    long long c0[3], c1[3];
+    for (int k = 0; k < 3; ++k) {
+        c0[k] = cell_of(b.lo[k], v.inv_cell);
+        c1[k] = cell_of(b.hi[k], v.inv_cell);
+    }
+    uint32_t j = entry_base + o, jend = entry_base + e;
+    for (long long cz = c0[2]; cz <= c1[2]; ++cz)
+        for (long long cy = c0[1]; cy <= c1[1]; ++cy)
+            for (long long cx = c0[0]; cx <= c1[0]; ++cx) {
+                if (j >= jend) return;  // never taken: the count pass saw the same box
+                uint64_t ck = pack_cell(cx, cy, cz);
+                key[j] = bucket_base + (mix64(ck) & tmask);
+                val[j] = j;
+                cell_tmp[j] = ck;
+                prim_tmp[j] = i | prim_flag;
+                ++j;
+            }
+}
+
+__global__ void k_gather_entries(const uint32_t* val, const uint64_t* cell_tmp, const int* prim_tmp, uint64_t* ecell,
+                                 int* eprim, uint32_t n) {
+    uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    uint32_t s = val[j];
+    ecell[j] = cell_tmp[s];
+    eprim[j] = prim_tmp[s];
+}
+
+__global__ void k_bucket_ranges(const uint64_t* key, uint32_t n, uint32_t* bstart, uint32_t* bend) {
+    uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    uint64_t b = key[j];
+    if (j == 0 || key[j - 1] != b) bstart[b] = j;
+    if (j == n - 1 || key[j + 1] != b) bend[b] = j + 1;
+}
+
+__global__ void k_compact_flags(const uint32_t* flag, const uint32_t* off, uint32_t sub, int n, int* out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (flag[i]) out[off[i] - sub] = i;
+}
+
+__device__ __forceinline__ bool pair_ok(const BPView& v, int sa, int sb) {
+    if (v.sv_env[sa] != v.sv_env[sb]) return false;
+    int ba = v.sv_body[sa], bb = v.sv_body[sb];
+    int ca = v.body_class[ba], cb = v.body_class[bb];
+    if (ca >= 2 && cb >= 2) return false;
+    if (ba == bb && ca != 0) return false;
+    return true;
+}
+
+__device__ __forceinline__ bool pt_ok(const BPView& v, int p, int t) {
+    int3 T = v.tris[t];
+    if (p == T.x || p == T.y || p == T.z) return false;
+    return pair_ok(v, p, T.x);
+}
+
+__device__ __forceinline__ bool ee_ok(const BPView& v, int a, int b) {
+    int2 A = v.edges[a], B = v.edges[b];
+    if (A.x == B.x || A.x == B.y || A.y == B.x || A.y == B.y) return false;
+    return pair_ok(v, A.x, B.x);
+}
+
+struct Table {
+    const uint64_t* ecell;
+    const int* eprim;
+    const uint32_t* bstart;
+    const uint32_t* bend;
+    uint64_t bucket_base, tmask;
+};
+
+// is the current cell the one holding the min corner of the boxes' intersection
+__device__ __forceinline__ bool owns(const Box6& a, const Box6& b, long long cx, long long cy, long long cz,
+                                     double inv) {
+    return cell_of(fmax(a.lo[0], b.lo[0]), inv) == cx && cell_of(fmax(a.lo[1], b.lo[1]), inv) == cy &&
+           cell_of(fmax(a.lo[2], b.lo[2]), inv) == cz;
+}
+
+// kind 0: point queries against the triangle table; kind 1: edge queries
+// against the edge table (only pairs with query < entry).
+template <bool WRITE>
+__global__ void k_query(BPView v, int kind, int nq, const double* qbox, const double* ebox_all, Table T,
+                        const int* big, int nbig, int n_entries_all, uint32_t* cnt, const uint32_t* off, int2* out) {
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nq) return;
+    Box6 a = ld_box(qbox + 6 * (size_t)q);
+    uint32_t c = 0;
+    uint32_t o = WRITE ? off[q] : 0u;
+    auto emit = [&](int e) {
+        if (WRITE) out[o + c] = make_int2(q, e);
+        ++c;
+    };
+    auto test = [&](int e) -> bool {
+        if (kind == 0) return pt_ok(v, q, e);
+        return q < e && ee_ok(v, q, e);
+    };
+    double nc = box_cells(a, v.inv_cell);
+    if (nc > kMaxCells) {
+        for (int e = 0; e < n_entries_all; ++e) {
+            if (kind == 1 && e <= q) continue;
+            Box6 b = ld_box(ebox_all + 6 * (size_t)e);
+            if (overlap(a, b) && test(e)) emit(e);
+        }
+    } else {
+        long long c0[3], c1[3];
+        for (int k = 0; k < 3; ++k) {
+            c0[k] = cell_of(a.lo[k], v.inv_cell);
+            c1[k] = cell_of(a.hi[k], v.inv_cell);
+        }
+        for (long long cz = c0[2]; cz <= c1[2]; ++cz)
+            for (long long cy = c0[1]; cy <= c1[1]; ++cy)
+                for (long long cx = c0[0]; cx <= c1[0]; ++cx) {
+                    uint64_t ck = pack_cell(cx, cy, cz);
+                    uint64_t bkt = T.bucket_base + (mix64(ck) & T.tmask);
+                    uint32_t s = T.bstart[bkt], f = T.bend[bkt];
+                    for (uint32_t j = s; j < f; ++j) {
+                        if (T.ecell[j] != ck) continue;
+                        int e = T.eprim[j];
+                        if (kind == 1 && e <= q) continue;
+                        Box6 b = ld_box(ebox_all + 6 * (size_t)e);
+                        if (!owns(a, b, cx, cy, cz, v.inv_cell)) continue;
+                        if (overlap(a, b) && test(e)) emit(e);
+                    }
+                }
+        for (int k = 0; k < nbig; ++k) {
+            int e = big[k];
+            if (kind == 1 && e <= q) continue;
+            Box6 b = ld_box(ebox_all + 6 * (size_t)e);
+            if (overlap(a, b) && test(e)) emit(e);
+        }
+    }
+    if (!WRITE) cnt[q] = c;
+}
+
+static uint64_t pow2_at_least(uint64_t n) {
+    uint64_t p = 64;
+    while (p < n) p <<= 1;
+    return p;
+}
+
+BroadPhase::~BroadPhase() {
+    if (h_counts) cudaFreeHost(h_counts);
+}
+
+void BroadPhase::run(Allocator* A, const BPView& v, cudaStream_t st) {
+    if (!h_counts) ZCHECK(cudaMallocHost(&h_counts, 8 * sizeof(uint32_t)));
+    const int TB = 128;
+    int nsv = v.nsv, ne = v.ne, nt = v.nt;
+    pbox.ensure(A, 6 * (size_t)nsv + 6);
+    ebox.ensure(A, 6 * (size_t)ne + 6);
+    tbox.ensure(A, 6 * (size_t)nt + 6);
+    tcnt.ensure(A, nt + 1);
+    toff.ensure(A, nt + 2);
+    ecnt.ensure(A, ne + 1);
+    eoff.ensure(A, ne + 2);
+    flag.ensure(A, (size_t)nt + ne + 2);
+    flagoff.ensure(A, (size_t)nt + ne + 4);
+    size_t mx = (size_t)nt + ne + nsv + 16;
+    tmp.ensure(A, scan_tmp_size(mx));
+    if (nsv) k_boxes<<<div_up(nsv, TB), TB, 0, st>>>(v, 0, nsv, pbox.p, nullptr, nullptr);
+    if (ne) k_boxes<<<div_up(ne, TB), TB, 0, st>>>(v, 1, ne, ebox.p, ecnt.p, flag.p + nt);
+    if (nt) k_boxes<<<div_up(nt, TB), TB, 0, st>>>(v, 2, nt, tbox.p, tcnt.p, flag.p);
+    ZLAUNCH();
+    exclusive_scan(tcnt.p, toff.p, nt, tmp.p, st);
+    exclusive_scan(ecnt.p, eoff.p, ne, tmp.p, st);
+    // oversize lists: flags of tris [0, nt) and edges [nt, nt + ne)
+    exclusive_scan(flag.p, flagoff.p, (size_t)nt + ne, tmp.p, st);
+    ZCHECK(cudaMemcpyAsync(h_counts + 0, toff.p + nt, 4, cudaMemcpyDeviceToHost, st));
+    ZCHECK(cudaMemcpyAsync(h_counts + 1, eoff.p + ne, 4, cudaMemcpyDeviceToHost, st));
+    ZCHECK(cudaMemcpyAsync(h_counts + 2, flagoff.p + nt, 4, cudaMemcpyDeviceToHost, st));
+    ZCHECK(cudaMemcpyAsync(h_counts + 3, flagoff.p + nt + ne, 4, cudaMemcpyDeviceToHost, st));
+    ZCHECK(cudaStreamSynchronize(st));
+    uint32_t Et = h_counts[0], Ee = h_counts[1], nbt = h_counts[2], nbe = h_counts[3] - h_counts[2];
+    big_t.ensure(A, nbt + 1);
+    big_e.ensure(A, nbe + 1);
+    if (nt) k_compact_flags<<<div_up(nt, TB), TB, 0, st>>>(flag.p, flagoff.p, 0u, nt, big_t.p);
+    // edge flag offsets continue after the triangles': subtract their count
+    if (ne) k_compact_flags<<<div_up(ne, TB), TB, 0, st>>>(flag.p + nt, flagoff.p + nt, nbt, ne, big_e.p);
+    ZLAUNCH();
+    // grid tables: triangle buckets [0, Tt), edge buckets [Tt, Tt + Te)
+    uint64_t Tt = pow2_at_least(2ull * Et + 1), Te = pow2_at_least(2ull * Ee + 1);
+    size_t E = (size_t)Et + Ee;
+    key.ensure(A, E + 1);
+    key2.ensure(A, E + 1);
+    val.ensure(A, E + 1);
+    val2.ensure(A, E + 1);
+    // the second key/val buffers double as the unsorted cell / prim scratch
+    DBuf<uint64_t>& cell_tmp = ecell;
+    cell_tmp.ensure(A, 2 * E + 2);
+    eprim.ensure(A, 2 * E + 2);
+    uint64_t* ctmp = cell_tmp.p + E + 1;
+    int* ptmp = eprim.p + E + 1;
+    bstart.ensure(A, Tt + Te);
+    bend.ensure(A, Tt + Te);
+    ZCHECK(cudaMemsetAsync(bstart.p, 0, (Tt + Te) * sizeof(uint32_t), st));
+    ZCHECK(cudaMemsetAsync(bend.p, 0, (Tt + Te) * sizeof(uint32_t), st));
+    if (nt) k_emit_entries<<<div_up(nt, TB), TB, 0, st>>>(v, nt, tbox.p, toff.p, 0, 0, Tt - 1, key.p, val.p, ctmp, ptmp, 0);
+    if (ne) k_emit_entries<<<div_up(ne, TB), TB, 0, st>>>(v, ne, ebox.p, eoff.p, Et, Tt, Te - 1, key.p, val.p, ctmp, ptmp, 0);
+    ZLAUNCH();
+    if (E) {
+        int bits = 1;
+        while ((1ull << bits) < Tt + Te) ++bits;
+        tmp.ensure(A, std::max(scan_tmp_size(mx), radix_tmp_size(E)));
+        radix_sort(key.p, val.p, key2.p, val2.p, E, bits, tmp.p, st);
+        k_gather_entries<<<div_up(E, 256), 256, 0, st>>>(val.p, ctmp, ptmp, cell_tmp.p, eprim.p, (uint32_t)E);
+        k_bucket_ranges<<<div_up(E, 256), 256, 0, st>>>(key.p, (uint32_t)E, bstart.p, bend.p);
+        ZLAUNCH();
+    }
+    Table TT{cell_tmp.p, eprim.p, bstart.p, bend.p, 0, Tt - 1};
+    Table TE{cell_tmp.p, eprim.p, bstart.p, bend.p, Tt, Te - 1};
+    qcnt_pt.ensure(A, nsv + 1);
+    qoff_pt.ensure(A, nsv + 2);
+    qcnt_ee.ensure(A, ne + 1);
+    qoff_ee.ensure(A, ne + 2);
+    if (nsv)
+        k_query<false><<<div_up(nsv, TB), TB, 0, st>>>(v, 0, nsv, pbox.p, tbox.p, TT, big_t.p, (int)nbt, nt,
+                                                       qcnt_pt.p, nullptr, nullptr);
+    if (ne)
+        k_query<false><<<div_up(ne, TB), TB, 0, st>>>(v, 1, ne, ebox.p, ebox.p, TE, big_e.p, (int)nbe, ne,
+                                                      qcnt_ee.p, nullptr, nullptr);
+    ZLAUNCH();
+    tmp.ensure(A, std::max(scan_tmp_size(mx), E ? radix_tmp_size(E) : 0));
+    exclusive_scan(qcnt_pt.p, qoff_pt.p, nsv, tmp.p, st);
+    exclusive_scan(qcnt_ee.p, qoff_ee.p, ne, tmp.p, st);
+    ZCHECK(cudaMemcpyAsync(h_counts + 4, qoff_pt.p + nsv, 4, cudaMemcpyDeviceToHost, st));
+    ZCHECK(cudaMemcpyAsync(h_counts + 5, qoff_ee.p + ne, 4, cudaMemcpyDeviceToHost, st));
+    ZCHECK(cudaStreamSynchronize(st));
+    n_pt = h_counts[4];
+    n_ee = h_counts[5];
+    pt.ensure(A, n_pt + 1);
+    ee.ensure(A, n_ee + 1);
+    if (nsv && n_pt)
+        k_query<true><<<div_up(nsv, TB), TB, 0, st>>>(v, 0, nsv, pbox.p, tbox.p, TT, big_t.p, (int)nbt, nt, nullptr,
+                                                      qoff_pt.p, pt.p);
+    if (ne && n_ee)
+        k_query<true><<<div_up(ne, TB), TB, 0, st>>>(v, 1, ne, ebox.p, ebox.p, TE, big_e.p, (int)nbe, ne, nullptr,
+                                                     qoff_ee.p, ee.p);
+    ZLAUNCH();
+}
+
+}  // namespace zema

@@ -1,0 +1,47 @@
+// Spatial-hash broad phase over surface point-triangle and edge-edge pairs
+// (the paper's "DCD" stage, Table I, done with a uniform grid instead of a
+// BVH).  Produces every valid pair whose axis-aligned boxes, inflated by
+// `infl` per side (and swept over X0 -> X1 when X1 is given), overlap.
+#pragma once
+#include "prims.cuh"
+
+namespace zema {
+
+struct BPView {
+    int nsv, ne, nt;
+    const double* X0;
+    const double* X1;  // nullable: swept boxes over X0 -> X1
+    const int* sv_body;
+    const int* body_class;  // 0 soft, 1 affine dynamic, 2 fixed, 3 kinematic
+    const int* sv_env;
+    const int2* edges;
+    const int3* tris;
+    double infl;
+    double inv_cell;
+};
+
+struct BroadPhase {
+    // boxes
+    DBuf<double> pbox, ebox, tbox;  // 6 per primitive: lo xyz, hi xyz
+    DBuf<uint32_t> tcnt, toff, ecnt, eoff;
+    DBuf<uint64_t> key, key2;
+    DBuf<uint32_t> val, val2;
+    DBuf<uint64_t> ecell;  // sorted entry cell keys
+    DBuf<int> eprim;       // sorted entry primitive ids
+    DBuf<uint32_t> bstart, bend;
+    DBuf<int> big_t, big_e;
+    DBuf<uint32_t> flag, flagoff;
+    DBuf<uint32_t> qcnt_pt, qoff_pt, qcnt_ee, qoff_ee;
+    DBuf<uint32_t> tmp;
+    DBuf<int2> pt, ee;  // outputs: (sv, tri), (edge, edge)
+    DBuf<uint32_t> hcount;  // pinned-size mirror of counts on device
+    uint32_t n_pt = 0, n_ee = 0;
+    uint32_t* h_counts = nullptr;  // pinned host [4]
+
+    // Runs the broad phase; n_pt / n_ee hold the counts afterwards (the call
+    // synchronises the stream once to size the outputs).
+    void run(Allocator* A, const BPView& v, cudaStream_t st);
+    ~BroadPhase();
+};
+
+}  // namespace zema

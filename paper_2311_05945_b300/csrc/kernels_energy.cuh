@@ -1,0 +1,489 @@
+// Energy terms of the incremental potential (Eq. 1-5, Eq. 9-10, Eq. 13):
+// per-element gradients and PSD-projected Hessians written to staging
+// buffers, and energy-only evaluations reduced per environment.
+#pragma once
+#include "distance.cuh"
+#include "scene.cuh"
+
+namespace zema {
+
+// Energy terms reduced per environment (partial sums per block chunk).
+enum ETerm { ET_INERTIA = 0, ET_ELASTIC = 1, ET_AFFINE = 2, ET_BARRIER = 3, ET_FRICTION = 4, ET_COUNT = 5 };
+
+// Sum over i in [lo, hi) of f(i) by block (chunk = blockIdx.x) of env
+// blockIdx.y, fixed order; thread 0 writes the block's partial.
+template <class F>
+__device__ __forceinline__ void chunk_sum(int lo, int hi, F f, double* out) {
+    __shared__ double sh[32];
+    double s = 0.0;
+    for (int i = lo + blockIdx.x * blockDim.x + threadIdx.x; i < hi; i += gridDim.x * blockDim.x) s += f(i);
+    double t = block_sum<kRedThreads>(s, sh);
+    if (threadIdx.x == 0) *out = t;
+}
+
+__device__ __forceinline__ double* part_slot(double* part, int term, int n_envs, int env) {
+    return part + ((size_t)term * n_envs + env) * kChunks + blockIdx.x;
+}
+
+// ---------------------------------------------------------------------------
+// Neo-Hookean density Psi(F) = mu/2 (tr F^T F - 3) - mu ln J + lam/2 (ln J)^2
+// (the material used for the soft solids), its first Piola stress P and the
+// F-space Hessian d2Psi/dF2 = mu I + h'' g g^T + h' d2J/dF2 with g = dJ/dF
+// (cofactor matrix) and h(J) = -mu ln J + lam/2 (ln J)^2.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int lc(int a, int b, int c) { return (a - b) * (b - c) * (c - a) / 2; }
+
+__device__ inline bool nh_eval(const double* F, double mu, double lam, double& psi, double* P, SMat<9>* H) {
+    double g[9];
+    g[0] = F[4] * F[8] - F[5] * F[7];
+    g[1] = F[5] * F[6] - F[3] * F[8];
+    g[2] = F[3] * F[7] - F[4] * F[6];
+    g[3] = F[2] * F[7] - F[1] * F[8];
+    g[4] = F[0] * F[8] - F[2] * F[6];
+    g[5] = F[1] * F[6] - F[0] * F[7];
+    g[6] = F[1] * F[5] - F[2] * F[4];
+    g[7] = F[2] * F[3] - F[0] * F[5];
+    g[8] = F[0] * F[4] - F[1] * F[3];
+    double J = F[0] * g[0] + F[1] * g[1] + F[2] * g[2];
+    if (!(J > 0.0)) return false;
+    double lj = log(J);
+    double tr = 0.0;
+    for (int i = 0; i < 9; ++i) tr += F[i] * F[i];
+    psi = 0.5 * mu * (tr - 3.0) - mu * lj + 0.5 * lam * lj * lj;
+    double h1 = (lam * lj - mu) / J;
+    double h2 = (lam * (1.0 - lj) + mu) / (J * J);
+    if (P)
+        for (int i = 0; i < 9; ++i) P[i] = mu * F[i] + h1 * g[i];
+    if (H) {
+        SMat<9>& M = *H;
+        for (int a = 0; a < 9; ++a)
+            for (int b = 0; b < 9; ++b) M(a, b) = h2 * g[a] * g[b] + (a == b ? mu : 0.0);
+        // d2J / dF_ij dF_kl = eps_ikm eps_jln F_mn (nonzero only for i != k, j != l)
+        for (int i = 0; i < 3; ++i)
+            for (int k = 0; k < 3; ++k) {
+                if (i == k) continue;
+                int m = 3 - i - k;
+                int eik = lc(i, k, m);
+                for (int j = 0; j < 3; ++j)
+                    for (int l = 0; l < 3; ++l) {
+                        if (j == l) continue;
+                        int n = 3 - j - l;
+                        M(3 * i + j, 3 * k + l) += h1 * eik * lc(j, l, n) * F[3 * m + n];
+                    }
+            }
+    }
+    return true;
+}
+
+// D[v][c]: derivative of F_rc with respect to x_{v, r} (rows of Dm^-1; v = 0
+// gets minus their sum)
+__device__ __forceinline__ void dF_coef(const double* Dm, double D[4][3]) {
+    for (int c = 0; c < 3; ++c) {
+        D[1][c] = Dm[c];
+        D[2][c] = Dm[3 + c];
+        D[3][c] = Dm[6 + c];
+        D[0][c] = -(D[1][c] + D[2][c] + D[3][c]);
+    }
+}
+
+__device__ __forceinline__ void tet_F(const Geo& G, const double* x, int t, double* F, int4& T) {
+    T = G.tets[t];
+    V3 x0 = ld3(x + 3 * (size_t)T.x), x1 = ld3(x + 3 * (size_t)T.y), x2 = ld3(x + 3 * (size_t)T.z),
+       x3 = ld3(x + 3 * (size_t)T.w);
+    V3 e[3] = {x1 - x0, x2 - x0, x3 - x0};
+    const double* Dm = G.Dminv + 9 * (size_t)t;
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c)
+            F[3 * r + c] = comp(e[0], r) * Dm[c] + comp(e[1], r) * Dm[3 + c] + comp(e[2], r) * Dm[6 + c];
+}
+
+constexpr int EL_T = 64;
+
+// Elastic gradient and F-space-projected Hessian per tet: 16 blocks (3x3) of
+// h^2 V B^T P(H_F) B and 12 gradient entries h^2 V B^T vec(P) into staging.
+__global__ void __launch_bounds__(EL_T) k_elastic_gh(Geo G, const double* x, double* stage_blk, double* stage_g) {
+    extern __shared__ double sm[];
+    int t = blockIdx.x * EL_T + threadIdx.x;
+    if (t >= G.n_tets) return;
+    SMat<9> H{sm + threadIdx.x, EL_T}, W{sm + 81 * EL_T + threadIdx.x, EL_T};
+    double F[9], P[9], psi;
+    int4 T;
+    tet_F(G, x, t, F, T);
+    if (!nh_eval(F, G.tmu[t], G.tlam[t], psi, P, &H)) {
+        // inverted (never reached at an accepted iterate): zero contribution
+        for (int i = 0; i < 16 * 9; ++i) stage_blk[(size_t)t * 144 + i] = 0.0;
+        for (int i = 0; i < 12; ++i) stage_g[(size_t)t * 12 + i] = 0.0;
+        return;
+    }
+    psd_project<9>(H, W);
+    double D[4][3];
+    dF_coef(G.Dminv + 9 * (size_t)t, D);
+    double w = G.h * G.h * G.tvol[t];
+    for (int v = 0; v < 4; ++v)
+        for (int r = 0; r < 3; ++r) {
+            double s = 0.0;
+            for (int c = 0; c < 3; ++c) s += P[3 * r + c] * D[v][c];
+            stage_g[(size_t)t * 12 + 3 * v + r] = w * s;
+        }
+    for (int v = 0; v < 4; ++v)
+        for (int u = 0; u < 4; ++u) {
+            double* out = stage_blk + ((size_t)t * 16 + 4 * v + u) * 9;
+            for (int r = 0; r < 3; ++r)
+                for (int s = 0; s < 3; ++s) {
+                    double acc = 0.0;
+                    for (int c = 0; c < 3; ++c) {
+                        double inner = 0.0;
+                        for (int d = 0; d < 3; ++d) inner += H(3 * r + c, 3 * s + d) * D[u][d];
+                        acc += D[v][c] * inner;
+                    }
+                    out[3 * r + s] = w * acc;
+                }
+        }
+}
+
+// soft inertia (Eq. 1) and elasticity (Eq. 1, h^2 Phi) energies per env
+__global__ void k_soft_energy(Geo G, const double* x, const double* xhat, double* part) {
+    int env = blockIdx.y;
+    int n0 = G.env_node_start[env], n1 = G.env_node_start[env + 1];
+    chunk_sum(
+        n0, n1,
+        [&](int n) -> double {
+            double m = G.node_mass[n];
+            if (m == 0.0) return 0.0;
+            V3 d = ld3(x + 3 * (size_t)n) - ld3(xhat + 3 * (size_t)n);
+            return 0.5 * m * dot(d, d);
+        },
+        part_slot(part, ET_INERTIA, G.n_envs, env));
+    int t0 = G.env_tet_start[env], t1 = G.env_tet_start[env + 1];
+    chunk_sum(
+        t0, t1,
+        [&](int t) -> double {
+            double F[9], psi;
+            int4 T;
+            tet_F(G, x, t, F, T);
+            if (!nh_eval(F, G.tmu[t], G.tlam[t], psi, nullptr, nullptr)) return INFINITY;
+            return G.h * G.h * G.tvol[t] * psi;
+        },
+        part_slot(part, ET_ELASTIC, G.n_envs, env));
+}
+
+// gradient of soft nodes: inertia + gather of the incident tets' staging
+__global__ void k_soft_grad(Geo G, const double* x, const double* xhat, const double* stage_g, double* g) {
+    int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= G.n_nodes) return;
+    double m = G.node_mass[n];
+    if (m == 0.0) return;  // affine node
+    V3 d = ld3(x + 3 * (size_t)n) - ld3(xhat + 3 * (size_t)n);
+    V3 s = m * d;
+    for (int k = G.node_tet_ptr[n]; k < G.node_tet_ptr[n + 1]; ++k) {
+        int e = G.node_tet_idx[k];  // tet * 4 + local
+        s = s + ld3(stage_g + 3 * (size_t)e);
+    }
+    if (G.node_fixed[n]) s = v3(0, 0, 0);
+    st3(g + 3 * (size_t)n, s);
+}
+
+// ---------------------------------------------------------------------------
+// Affine bodies (Eq. 2, Eq. 13) in the centred column form.
+// ---------------------------------------------------------------------------
+struct AffKin {
+    const double* qtarget;  // 12 per body, caller's row form
+    const double* lamA;     // 12 per body
+};
+
+// energy of one affine body (inertia + orthogonality + kinematic AL)
+__device__ inline double affine_energy(const Geo& G, const double* x, const double* xhat, AffKin K, int b) {
+    int mode = G.aff_mode[b];
+    if (mode == 1) return 0.0;
+    int n0 = G.aff_node0[b];
+    V3 c[4], ch[4];
+    for (int j = 0; j < 4; ++j) {
+        c[j] = ld3(x + 3 * (size_t)(n0 + j));
+        ch[j] = ld3(xhat + 3 * (size_t)(n0 + j));
+    }
+    const double* S = G.aff_S + 9 * (size_t)b;
+    double m = G.aff_m[b];
+    V3 dp = c[0] - ch[0];
+    double E = 0.5 * m * dot(dp, dp);
+    for (int j = 0; j < 3; ++j)
+        for (int k = 0; k < 3; ++k) E += 0.5 * S[3 * j + k] * dot(c[1 + j] - ch[1 + j], c[1 + k] - ch[1 + k]);
+    double o = 0.0;
+    for (int j = 0; j < 3; ++j)
+        for (int k = 0; k < 3; ++k) {
+            double gjk = dot(c[1 + j], c[1 + k]) - (j == k ? 1.0 : 0.0);
+            o += gjk * gjk;
+        }
+    E += G.h * G.h * G.aff_stiff[b] * G.aff_vol[b] * o;
+    if (mode == 2) {
+        const double* qt = K.qtarget + 12 * (size_t)b;
+        const double* la = K.lamA + 12 * (size_t)b;
+        double kA = 1e3 * m, sm = sqrt(m);
+        const double* com = G.aff_com + 3 * (size_t)b;
+        // caller-frame translation p = p' - A com ; A rows a_i = (c1_i, c2_i, c3_i)
+        V3 p = c[0] - (com[0] * c[1] + com[1] * c[2] + com[2] * c[3]);
+        double q[12] = {p.x, p.y, p.z, c[1].x, c[2].x, c[3].x, c[1].y, c[2].y, c[3].y, c[1].z, c[2].z, c[3].z};
+        for (int i = 0; i < 12; ++i) {
+            double d = q[i] - qt[i];
+            E += 0.5 * kA * d * d - sm * la[i] * d;
+        }
+    }
+    return E;
+}
+
+__global__ void k_affine_energy(Geo G, const double* x, const double* xhat, AffKin K, double* part) {
+    int env = blockIdx.y;
+    chunk_sum(
+        G.env_aff_start[env], G.env_aff_start[env + 1],
+        [&](int b) -> double { return affine_energy(G, x, xhat, K, b); }, part_slot(part, ET_AFFINE, G.n_envs, env));
+}
+
+constexpr int AF_T = 32;
+
+// gradient (directly into g, the body's nodes only) and 16 Hessian blocks
+__global__ void __launch_bounds__(AF_T) k_affine_gh(Geo G, const double* x, const double* xhat, AffKin K,
+                                                    double* stage_blk, double* g) {
+    extern __shared__ double sm[];
+    int b = blockIdx.x * AF_T + threadIdx.x;
+    if (b >= G.n_aff) return;
+    int mode = G.aff_mode[b];
+    int n0 = G.aff_node0[b];
+    double* blk = stage_blk + (size_t)b * 144;
+    for (int i = 0; i < 144; ++i) blk[i] = 0.0;
+    if (mode == 1) {
+        for (int j = 0; j < 4; ++j) st3(g + 3 * (size_t)(n0 + j), v3(0, 0, 0));
+        return;
+    }
+    SMat<9> H{sm + threadIdx.x, AF_T}, W{sm + 81 * AF_T + threadIdx.x, AF_T};
+    V3 c[4], ch[4];
+    for (int j = 0; j < 4; ++j) {
+        c[j] = ld3(x + 3 * (size_t)(n0 + j));
+        ch[j] = ld3(xhat + 3 * (size_t)(n0 + j));
+    }
+    const double* S = G.aff_S + 9 * (size_t)b;
+    double m = G.aff_m[b];
+    V3 gr[4];
+    gr[0] = m * (c[0] - ch[0]);
+    for (int j = 0; j < 3; ++j) {
+        V3 s = v3(0, 0, 0);
+        for (int k = 0; k < 3; ++k) s = s + S[3 * j + k] * (c[1 + k] - ch[1 + k]);
+        gr[1 + j] = s;
+    }
+    // inertia blocks: (0,0) m I ; (j,k) S_jk I
+    auto blk_add_diag = [&](int j, int k, double v) {
+        double* o = blk + (4 * j + k) * 9;
+        o[0] += v;
+        o[4] += v;
+        o[8] += v;
+    };
+    blk_add_diag(0, 0, m);
+    for (int j = 0; j < 3; ++j)
+        for (int k = 0; k < 3; ++k) blk_add_diag(1 + j, 1 + k, S[3 * j + k]);
+    // orthogonality: Phi = sum_jk (c_j . c_k - delta_jk)^2
+    double w = G.h * G.h * G.aff_stiff[b] * G.aff_vol[b];
+    double Gm[3][3];
+    for (int j = 0; j < 3; ++j)
+        for (int k = 0; k < 3; ++k) Gm[j][k] = dot(c[1 + j], c[1 + k]) - (j == k ? 1.0 : 0.0);
+    for (int i = 0; i < 3; ++i) {
+        V3 s = v3(0, 0, 0);
+        for (int k = 0; k < 3; ++k) s = s + Gm[i][k] * c[1 + k];
+        gr[1 + i] = gr[1 + i] + (4.0 * w) * s;
+    }
+    double CC[9];
+    for (int a = 0; a < 3; ++a)
+        for (int bb = 0; bb < 3; ++bb)
+            CC[3 * a + bb] = comp(c[1], a) * comp(c[1], bb) + comp(c[2], a) * comp(c[2], bb) + comp(c[3], a) * comp(c[3], bb);
+    for (int i = 0; i < 3; ++i)
+        for (int l = 0; l < 3; ++l)
+            for (int a = 0; a < 3; ++a)
+                for (int bb = 0; bb < 3; ++bb) {
+                    double v = comp(c[1 + l], a) * comp(c[1 + i], bb);
+                    if (a == bb) v += Gm[i][l];
+                    if (i == l) v += CC[3 * a + bb];
+                    H(3 * i + a, 3 * l + bb) = 4.0 * w * v;
+                }
+    psd_project<9>(H, W);
+    for (int i = 0; i < 3; ++i)
+        for (int l = 0; l < 3; ++l) {
+            double* o = blk + (4 * (1 + i) + (1 + l)) * 9;
+            for (int a = 0; a < 3; ++a)
+                for (int bb = 0; bb < 3; ++bb) o[3 * a + bb] += H(3 * i + a, 3 * l + bb);
+        }
+    if (mode == 2) {
+        const double* qt = K.qtarget + 12 * (size_t)b;
+        const double* la = K.lamA + 12 * (size_t)b;
+        double kA = 1e3 * m, sm_ = sqrt(m);
+        const double* com = G.aff_com + 3 * (size_t)b;
+        double wo[4] = {1.0, -com[0], -com[1], -com[2]};
+        V3 p = c[0] - (com[0] * c[1] + com[1] * c[2] + com[2] * c[3]);
+        V3 fp = kA * (p - ld3(qt)) - sm_ * ld3(la);
+        for (int j = 0; j < 4; ++j) gr[j] = gr[j] + wo[j] * fp;
+        for (int j = 0; j < 4; ++j)
+            for (int l = 0; l < 4; ++l) blk_add_diag(j, l, kA * wo[j] * wo[l]);
+        for (int k = 0; k < 3; ++k) {
+            // column k of the target A (rows a_i at qt[3 + 3 i]) and of Lambda
+            V3 ct = v3(qt[3 + k], qt[6 + k], qt[9 + k]);
+            V3 lk = v3(la[3 + k], la[6 + k], la[9 + k]);
+            gr[1 + k] = gr[1 + k] + (kA * (c[1 + k] - ct) - sm_ * lk);
+            blk_add_diag(1 + k, 1 + k, kA);
+        }
+    }
+    for (int j = 0; j < 4; ++j) st3(g + 3 * (size_t)(n0 + j), gr[j]);
+}
+
+// ---------------------------------------------------------------------------
+// Contact barrier (Eq. 4-8) per active pair: gradient and projected Hessian
+// in the 12-dim stencil space.
+// ---------------------------------------------------------------------------
+constexpr int BR_T = 32;
+
+__device__ __forceinline__ double pair_eps_x(const Geo& G, const PairRec& r) {
+    if (!r.is_ee) return 0.0;
+    V3 a = ld3(G.sv_rest + 3 * (size_t)r.s[1]) - ld3(G.sv_rest + 3 * (size_t)r.s[0]);
+    V3 b = ld3(G.sv_rest + 3 * (size_t)r.s[3]) - ld3(G.sv_rest + 3 * (size_t)r.s[2]);
+    return 1e-3 * dot(a, a) * dot(b, b);
+}
+
+__global__ void __launch_bounds__(BR_T) k_barrier_gh(Geo G, const double* X, const PairRec* rec, int n,
+                                                     const double* kappa_env, double* pH, double* pG) {
+    extern __shared__ double sm[];
+    int i = blockIdx.x * BR_T + threadIdx.x;
+    if (i >= n) return;
+    SMat<12> H{sm + threadIdx.x, BR_T}, V{sm + 144 * BR_T + threadIdx.x, BR_T};
+    PairRec r = rec[i];
+    V3 x[4];
+    for (int k = 0; k < 4; ++k) x[k] = ld3(X + 3 * (size_t)r.s[k]);
+    double kap = kappa_env[G.sv_env[r.s[0]]];
+    double E, g12[12];
+    bool act = pair_barrier(x, r.is_ee != 0, G.dhat, kap, pair_eps_x(G, r), E, g12, H, V, true);
+    for (int a = 0; a < 12; ++a) pG[(size_t)i * 12 + a] = act ? g12[a] : 0.0;
+    for (int a = 0; a < 12; ++a)
+        for (int b = 0; b < 12; ++b) pH[(size_t)i * 144 + 12 * a + b] = act ? H(a, b) : 0.0;
+}
+
+// barrier energy over a pair list per env (ranges from env_off)
+__global__ void k_barrier_energy(Geo G, const double* X, const PairRec* rec, const uint32_t* env_off,
+                                 const double* kappa_env, double* part) {
+    int env = blockIdx.y;
+    double kap = kappa_env[env];
+    chunk_sum(
+        (int)env_off[env], (int)env_off[env + 1],
+        [&](int i) -> double {
+            PairRec r = rec[i];
+            V3 x[4];
+            for (int k = 0; k < 4; ++k) x[k] = ld3(X + 3 * (size_t)r.s[k]);
+            return pair_barrier_energy(x, r.is_ee != 0, G.dhat, kap, pair_eps_x(G, r), nullptr);
+        },
+        part_slot(part, ET_BARRIER, G.n_envs, env));
+}
+
+// ---------------------------------------------------------------------------
+// Lagged friction (Eq. 9-10)
+// ---------------------------------------------------------------------------
+struct Lag {
+    const PairRec* rec;
+    const double* w;   // 4 per pair: Delta = sum w_k (x_k - x_k^t)
+    const double* n;   // 3 per pair: unit normal at x^t
+    const double* c;   // mu * lambda
+    const uint32_t* env_off;
+    int n_pairs;
+};
+
+// closest-point weights, normal and normal-force magnitude at x^t
+__global__ void k_lag_friction(Geo G, const double* X, const PairRec* rec, int n, const double* kappa_env,
+                               double* w_out, double* n_out, double* c_out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    PairRec r = rec[i];
+    V3 x[4];
+    for (int k = 0; k < 4; ++k) x[k] = ld3(X + 3 * (size_t)r.s[k]);
+    DistInfo di = classify(x, r.is_ee != 0);
+    double d = sqrt(di.d2);
+    V3 dv = v3(0, 0, 0);
+    for (int k = 0; k < 4; ++k) dv = dv + di.w[k] * x[k];
+    double dl = sqrt(dot(dv, dv));
+    V3 nn = (1.0 / dl) * dv;
+    double e = 1.0;
+    double eps = pair_eps_x(G, r);
+    if (r.is_ee && eps > 0.0) {
+        V3 cr = cross(x[1] - x[0], x[3] - x[2]);
+        double c = dot(cr, cr);
+        if (c < eps) e = (c / eps) * (2.0 - c / eps);
+    }
+    double b, b1, b2;
+    barrier_d012(d, G.dhat, b, b1, b2);
+    int env = G.sv_env[r.s[0]];
+    double lam = kappa_env[env] * e * fabs(b1);
+    int ba = G.sv_body[r.s[0]], bb = G.sv_body[r.s[r.is_ee ? 2 : 1]];
+    double mu = fmin(G.body_mu[ba], G.body_mu[bb]);
+    for (int k = 0; k < 4; ++k) w_out[(size_t)i * 4 + k] = di.w[k];
+    st3(n_out + 3 * (size_t)i, nn);
+    c_out[i] = mu * lam;
+}
+
+__device__ __forceinline__ double f0_mollifier(double y, double eh) {
+    if (y >= eh) return y;
+    return -y * y * y / (3.0 * eh * eh) + y * y / eh + eh / 3.0;
+}
+
+// tangential displacement u = (I - n n^T) Delta of a lagged pair
+__device__ __forceinline__ V3 lag_u(const double* X, const double* Xt, const Lag& L, int i) {
+    PairRec r = L.rec[i];
+    V3 D = v3(0, 0, 0);
+    for (int k = 0; k < 4; ++k) {
+        double w = L.w[(size_t)i * 4 + k];
+        D = D + w * (ld3(X + 3 * (size_t)r.s[k]) - ld3(Xt + 3 * (size_t)r.s[k]));
+    }
+    V3 n = ld3(L.n + 3 * (size_t)i);
+    return D - dot(n, D) * n;
+}
+
+__global__ void k_friction_energy(Geo G, const double* X, const double* Xt, Lag L, double* part) {
+    int env = blockIdx.y;
+    double eh = G.eps_v * G.h;
+    chunk_sum(
+        (int)L.env_off[env], (int)L.env_off[env + 1],
+        [&](int i) -> double {
+            V3 u = lag_u(X, Xt, L, i);
+            return L.c[i] * f0_mollifier(sqrt(dot(u, u)), eh);
+        },
+        part_slot(part, ET_FRICTION, G.n_envs, env));
+}
+
+// friction gradient and Hessian (PSD by construction) in stencil space
+__global__ void k_friction_gh(Geo G, const double* X, const double* Xt, Lag L, double* pH, double* pG) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= L.n_pairs) return;
+    double eh = G.eps_v * G.h;
+    V3 u = lag_u(X, Xt, L, i);
+    V3 n = ld3(L.n + 3 * (size_t)i);
+    double y = sqrt(dot(u, u));
+    double c = L.c[i];
+    double a1, a2, f1y;
+    if (y >= eh) {
+        a1 = 1.0 / y;
+        a2 = -1.0 / (y * y * y);
+        f1y = 1.0 / y;
+    } else {
+        a1 = 2.0 / eh - y / (eh * eh);
+        a2 = y > 0.0 ? -1.0 / (eh * eh * y) : 0.0;
+        f1y = a1;
+    }
+    double nv[3] = {n.x, n.y, n.z}, uv[3] = {u.x, u.y, u.z};
+    double HD[9], gD[3];
+    for (int a = 0; a < 3; ++a) {
+        gD[a] = c * f1y * uv[a];
+        for (int b = 0; b < 3; ++b)
+            HD[3 * a + b] = c * (a1 * ((a == b ? 1.0 : 0.0) - nv[a] * nv[b]) + a2 * uv[a] * uv[b]);
+    }
+    const double* w = L.w + (size_t)i * 4;
+    double* Ho = pH + (size_t)i * 144;
+    double* Go = pG + (size_t)i * 12;
+    for (int k = 0; k < 4; ++k)
+        for (int a = 0; a < 3; ++a) {
+            Go[3 * k + a] = w[k] * gD[a];
+            for (int l = 0; l < 4; ++l)
+                for (int b = 0; b < 3; ++b) Ho[12 * (3 * k + a) + 3 * l + b] = w[k] * w[l] * HD[3 * a + b];
+        }
+}
+
+}  // namespace zema

@@ -1,0 +1,199 @@
+// Exclusive scan and stable LSD radix sort (8-bit digits), written for the
+// broad phase and the contact assembly.  Both are deterministic: no atomics
+// decide an output position.
+#include "prims.cuh"
+
+namespace zema {
+
+constexpr int SCAN_T = 256;
+constexpr int SCAN_PER = 4;
+constexpr int SCAN_TILE = SCAN_T * SCAN_PER;
+
+// per-block exclusive scan of SCAN_TILE elements; block totals to sums
+__global__ void k_scan_block(const uint32_t* in, uint32_t* out, size_t n, uint32_t* sums) {
+    __shared__ uint32_t wsum[SCAN_T / 32];
+    size_t base = (size_t)blockIdx.x * SCAN_TILE + (size_t)threadIdx.x * SCAN_PER;
+    uint32_t v[SCAN_PER];
+    uint32_t s = 0;
+#pragma unroll
+    for (int i = 0; i < SCAN_PER; ++i) {
+        v[i] = (base + i < n) ? in[base + i] : 0u;
+        s += v[i];
+    }
+    // inclusive warp scan of thread sums
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t inc = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) wsum[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t ws = (lane < SCAN_T / 32) ? wsum[lane] : 0u;
+        uint32_t wi = ws;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t t = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += t;
+        }
+        if (lane < SCAN_T / 32) wsum[lane] = wi - ws;  // exclusive warp offsets
+        if (lane == SCAN_T / 32 - 1) sums[blockIdx.x] = wi;
+    }
+    __syncthreads();
+    uint32_t run = wsum[w] + inc - s;
+#pragma unroll
+    for (int i = 0; i < SCAN_PER; ++i) {
+        if (base + i < n) out[base + i] = run;
+        run += v[i];
+    }
+}
+
+__global__ void k_scan_add(uint32_t* out, size_t n, const uint32_t* offs) {
+    size_t i = (size_t)blockIdx.x * SCAN_TILE + threadIdx.x;
+    uint32_t o = offs[blockIdx.x];
+    for (int k = 0; k < SCAN_PER; ++k, i += SCAN_T)
+        if (i < n) out[i] += o;
+}
+
+__global__ void k_set_total(uint32_t* out, size_t n, const uint32_t* in, const uint32_t* scanned_sums,
+                            int last_block) {
+    // out[n] = exclusive(n-1) + in[n-1]
+    if (n == 0) {
+        out[0] = 0;
+        return;
+    }
+    out[n] = out[n - 1] + in[n - 1];
+}
+
+size_t scan_tmp_size(size_t n) {
+    size_t total = 0;
+    size_t m = n;
+    while (m > SCAN_TILE) {
+        size_t nb = (m + SCAN_TILE - 1) / SCAN_TILE;
+        total += 2 * nb + 2;
+        m = nb;
+    }
+    return total + 2 * SCAN_TILE + 8;
+}
+
+static void scan_rec(const uint32_t* in, uint32_t* out, size_t n, uint32_t* tmp, cudaStream_t st) {
+    if (n == 0) return;
+    size_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+    uint32_t* sums = tmp;
+    uint32_t* soff = tmp + nb + 1;
+    k_scan_block<<<(unsigned)nb, SCAN_T, 0, st>>>(in, out, n, sums);
+    ZLAUNCH();
+    if (nb > 1) {
+        scan_rec(sums, soff, nb, tmp + 2 * nb + 2, st);
+        k_scan_add<<<(unsigned)nb, SCAN_T, 0, st>>>(out, n, soff);
+        ZLAUNCH();
+    }
+}
+
+void exclusive_scan(const uint32_t* in, uint32_t* out, size_t n, uint32_t* tmp, cudaStream_t st) {
+    scan_rec(in, out, n, tmp, st);
+    k_set_total<<<1, 1, 0, st>>>(out, n, in, nullptr, 0);
+    ZLAUNCH();
+}
+
+// ---------------------------------------------------------------------------
+// Radix sort
+// ---------------------------------------------------------------------------
+constexpr int RS_T = 256;
+constexpr int RS_ROUNDS = 8;
+constexpr int RS_TILE = RS_T * RS_ROUNDS;
+constexpr int RS_WARPS = RS_T / 32;
+
+__global__ void k_rs_hist(const uint64_t* keys, size_t n, int shift, uint32_t* hist, int ntiles) {
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    size_t base = (size_t)blockIdx.x * RS_TILE;
+    for (int r = 0; r < RS_ROUNDS; ++r) {
+        size_t i = base + (size_t)r * RS_T + threadIdx.x;
+        if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[(size_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void k_rs_scatter(const uint64_t* keys, const uint32_t* vals, uint64_t* ko, uint32_t* vo, size_t n,
+                             int shift, const uint32_t* offs, int ntiles) {
+    __shared__ uint32_t wc[RS_WARPS][256];
+    __shared__ uint32_t run[256];
+    __shared__ uint32_t gbase[256];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    run[threadIdx.x] = 0;
+    gbase[threadIdx.x] = offs[(size_t)threadIdx.x * ntiles + blockIdx.x];
+    for (int k = 0; k < RS_WARPS; ++k) wc[k][threadIdx.x] = 0;
+    __syncthreads();
+    size_t base = (size_t)blockIdx.x * RS_TILE;
+    unsigned lt = (1u << lane) - 1u;
+    for (int r = 0; r < RS_ROUNDS; ++r) {
+        size_t i = base + (size_t)r * RS_T + threadIdx.x;
+        bool valid = i < n;
+        uint64_t key = valid ? keys[i] : 0ull;
+        uint32_t val = valid ? vals[i] : 0u;
+        unsigned dig = valid ? (unsigned)((key >> shift) & 255u) : 256u + lane;
+        unsigned peers = __match_any_sync(0xffffffffu, dig);
+        unsigned rank = __popc(peers & lt);
+        if (valid && rank == 0) wc[w][dig] = __popc(peers);
+        __syncthreads();
+        {
+            int d = threadIdx.x;
+            uint32_t acc = run[d];
+            for (int k = 0; k < RS_WARPS; ++k) {
+                uint32_t t = wc[k][d];
+                wc[k][d] = acc;
+                acc += t;
+            }
+            run[d] = acc;
+        }
+        __syncthreads();
+        if (valid) {
+            uint32_t pos = gbase[dig] + wc[w][dig] + rank;
+            ko[pos] = key;
+            vo[pos] = val;
+        }
+        __syncthreads();
+        for (int k = 0; k < RS_WARPS; ++k) wc[k][threadIdx.x] = 0;
+        __syncthreads();
+    }
+}
+
+size_t radix_tmp_size(size_t n) {
+    size_t ntiles = (n + RS_TILE - 1) / RS_TILE;
+    size_t h = 256 * ntiles;
+    return 2 * h + 2 + scan_tmp_size(h);
+}
+
+void radix_sort(uint64_t* keys, uint32_t* vals, uint64_t* k2, uint32_t* v2, size_t n, int bits, uint32_t* tmp,
+                cudaStream_t st) {
+    if (n <= 1) return;
+    int ntiles = (int)((n + RS_TILE - 1) / RS_TILE);
+    size_t h = 256 * (size_t)ntiles;
+    uint32_t* hist = tmp;
+    uint32_t* offs = tmp + h + 1;
+    uint32_t* stmp = tmp + 2 * h + 2;
+    int passes = (bits + 7) / 8;
+    uint64_t *ka = keys, *kb = k2;
+    uint32_t *va = vals, *vb = v2;
+    for (int p = 0; p < passes; ++p) {
+        int shift = 8 * p;
+        k_rs_hist<<<ntiles, RS_T, 0, st>>>(ka, n, shift, hist, ntiles);
+        ZLAUNCH();
+        exclusive_scan(hist, offs, h, stmp, st);
+        k_rs_scatter<<<ntiles, RS_T, 0, st>>>(ka, va, kb, vb, n, shift, offs, ntiles);
+        ZLAUNCH();
+        std::swap(ka, kb);
+        std::swap(va, vb);
+    }
+    if (ka != keys) {
+        ZCHECK(cudaMemcpyAsync(keys, ka, n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, st));
+        ZCHECK(cudaMemcpyAsync(vals, va, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
+    }
+}
+
+}  // namespace zema

@@ -1,0 +1,2048 @@
+// zema: C ABI and host orchestration of the soft-rigid coupled IPC time step.
+//
+// Per time step (paper section III): predictor (Eq. 1-3), lagged friction at
+// x^t (Eq. 9-10), a CCD-filtered warm start, then projected Newton on
+// B_t + D (Eq. 4, Eq. 11): spatial-hash broad phase, active pairs d < dhat,
+// PSD-projected local Hessians (elastic, affine, barrier in the 12-dim pair
+// space mapped by the coupling Jacobian of Eq. 6-8, friction), block-sparse
+// assembly, block-Jacobi PCG, step-norm convergence test, swept broad phase +
+// additive CCD bound, backtracking line search; then the velocity update
+// (Eq. 11), kappa adaptation and the kinematic augmented-Lagrangian update
+// (Eq. 13).  The host only sequences kernels and reads back counts, per-env
+// energies and flags.
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <map>
+#include <numeric>
+#include <tuple>
+#include <vector>
+
+#include "broadphase.cuh"
+#include "kernels_misc.cuh"
+
+using namespace zema;
+
+namespace {
+
+struct TetIn {
+    int env;
+    std::vector<double> X, x0, v0;
+    std::vector<int> T;
+    double E, nu, rho, mu;
+};
+struct AffIn {
+    int env, mode;
+    std::vector<double> V;
+    std::vector<int> F;
+    double q0[12], qd0[12];
+    double rho, stiff, mu;
+};
+
+constexpr int TB = 256;
+
+inline dim3 red_grid(int n_envs) { return dim3(kChunks, n_envs); }
+
+}  // namespace
+
+struct zema_scene {
+    zema_scene_params P;
+    Allocator A;
+    cudaStream_t st = nullptr;
+    std::string err;
+    bool finalized = false;
+    std::vector<TetIn> tin;
+    std::vector<AffIn> ain;
+    std::vector<std::pair<int, int>> bodies;  // body id -> (0 tet / 1 affine, index)
+
+    // host copies needed at the boundary
+    int n_envs = 1;
+    std::vector<int> tet_body_node0;   // first node of each tet body
+    std::vector<int> aff_node0_h;      // first node of each affine body
+    std::vector<double> aff_com_h;     // 3 per affine body
+    std::vector<int> aff_mode_h;
+    std::vector<double> diag_h, tol_h; // per env
+    std::vector<int> env_aff_start_h, env_node_start_h, env_sv_start_h, env_edge_start_h;
+    std::vector<double> node_mass_h, aff_m_in;  // host copies for the kappa rule
+    int n_nodes = 0, n_soft = 0, n_aff = 0, n_tets = 0, n_sv = 0, n_edges = 0, n_tris = 0, n_units = 0;
+    int n_sblocks = 0;
+    double cell = 1.0;
+    std::vector<int> kappa_ready;  // per env: kappa set (by rule or by user)
+    bool first_step_done = false;
+
+    // device geometry
+    DBuf<int> node_env, env_node_start, env_tet_start, env_aff_start, env_unit_start, env_sv_start, env_edge_start;
+    DBuf<uint8_t> node_fixed, sv_aff;
+    DBuf<double> node_mass, Dminv, tvol, tmu, tlam, aff_m, aff_S, aff_vol, aff_stiff, aff_com, sv_x0, sv_rest,
+        body_mu, edge_rest2;
+    DBuf<int4> tets;
+    DBuf<int> aff_node0, aff_mode, unit_kind, unit_idx, sv_node, sv_body, sv_env, body_class, node_tet_ptr,
+        node_tet_idx, S_rowptr, S_col, S_src_ptr, S_src, S_diag;
+    DBuf<int2> edges;
+    DBuf<int3> tris;
+    // state
+    DBuf<double> x, v, xt, xhat, p, xtrial, g, b, r, z, pp, q, X, Xt, X1, stage_blk, stage_g, S_val, Minv_s, Minv_a;
+    DBuf<double> qtarget, lamA;
+    // per env
+    DBuf<double> kappa, kappa_min, alpha, E, dmin, part, part2, part3, part4, part5, part6, part7;
+    DBuf<int> conv, pcg_iters, need, capflag;
+    DBuf<double> tolv;
+    // pair lists
+    BroadPhase bp;
+    DBuf<PairRec> cand, act, swept, lag;
+    DBuf<uint32_t> flag, flagoff, pt_env, ee_env, m_env, act_env, swept_env, lag_env, tmp32;
+    DBuf<double> lag_w, lag_n, lag_c, pH, pG;
+    uint32_t n_act = 0, n_swept = 0, n_lag = 0;
+    // contact assembly
+    DBuf<uint32_t> cnt_blk, off_blk, cnt_g, off_g, bval, bval2, gval, gval2, head, hoff, seg;
+    DBuf<uint64_t> bkey, bkey2, gkey, gkey2, ukey;
+    DBuf<double> bstage, gstage, C_val, gsum;
+    DBuf<int> C_rowptr, C_col;
+    uint32_t n_cblocks = 0;
+    // pinned host scratch
+    uint32_t* h32 = nullptr;
+    double* hd = nullptr;
+    int* hi = nullptr;
+    Geo G{};
+    // stats of the current call
+    zema_step_stats S{};
+    // per-step scratch
+    DBuf<double> dirw, lam_save;
+    std::vector<double> dmin_last;
+
+    ~zema_scene() {
+        if (h32) cudaFreeHost(h32);
+        if (hd) cudaFreeHost(hd);
+        if (hi) cudaFreeHost(hi);
+    }
+};
+
+namespace {
+
+void fail(int status, const std::string& m) { throw ZemaError{status, m}; }
+
+template <class T>
+void up(zema_scene* s, DBuf<T>& d, const std::vector<T>& h) {
+    d.upload(&s->A, h);
+}
+
+double now_ms() {
+    using namespace std::chrono;
+    return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+// ---------------------------------------------------------------------------
+// Scene precompute kernels (rest shapes, masses)
+// ---------------------------------------------------------------------------
+__global__ void k_tet_rest(const double* Xr, const int4* tets, int nt, double* Dminv, double* vol, int* bad) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    int4 T = tets[t];
+    const double* a = Xr + 3 * (size_t)T.x;
+    double Dm[9];
+    const double* o[3] = {Xr + 3 * (size_t)T.y, Xr + 3 * (size_t)T.z, Xr + 3 * (size_t)T.w};
+    for (int c = 0; c < 3; ++c)
+        for (int r = 0; r < 3; ++r) Dm[3 * r + c] = o[c][r] - a[r];
+    double det;
+    inv3(Dm, Dminv + 9 * (size_t)t);
+    det = Dm[0] * (Dm[4] * Dm[8] - Dm[5] * Dm[7]) - Dm[1] * (Dm[3] * Dm[8] - Dm[5] * Dm[6]) +
+          Dm[2] * (Dm[3] * Dm[7] - Dm[4] * Dm[6]);
+    vol[t] = det / 6.0;
+    if (!(det > 0.0)) atomicMax(bad, 1);
+}
+
+// lumped vertex mass: sum over incident tets of rho V / 4
+__global__ void k_lumped_mass(const int* ptr, const int* idx, const double* vol, const double* trho, int n,
+                              double* mass) {
+    int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    double m = 0.0;
+    for (int k = ptr[v]; k < ptr[v + 1]; ++k) {
+        int t = idx[k] >> 2;
+        m += trho[t] * vol[t] * 0.25;
+    }
+    mass[v] = m;
+}
+
+// Mass properties of an affine body from its closed surface (Eq. 2):
+// integrals of 1, x0, x0 x0^T over the enclosed volume via the tetrahedra
+// (origin, a, b, c) of each outward triangle.  One block per body.
+__global__ void k_affine_mass(const double* V, const int* F, const int* f_ptr, const int* v_off, const double* rho,
+                              int nb, double* out /* 13 per body: vol, m1(3), m2(9) */) {
+    int b = blockIdx.x;
+    if (b >= nb) return;
+    __shared__ double sh[32];
+    double acc[13];
+    for (int i = 0; i < 13; ++i) acc[i] = 0.0;
+    const double* Vb = V + 3 * (size_t)v_off[b];
+    for (int f = f_ptr[b] + threadIdx.x; f < f_ptr[b + 1]; f += blockDim.x) {
+        const double* a = Vb + 3 * (size_t)F[3 * f];
+        const double* c1 = Vb + 3 * (size_t)F[3 * f + 1];
+        const double* c2 = Vb + 3 * (size_t)F[3 * f + 2];
+        double vol = (a[0] * (c1[1] * c2[2] - c1[2] * c2[1]) - a[1] * (c1[0] * c2[2] - c1[2] * c2[0]) +
+                      a[2] * (c1[0] * c2[1] - c1[1] * c2[0])) / 6.0;
+        double s[3];
+        for (int i = 0; i < 3; ++i) s[i] = a[i] + c1[i] + c2[i];
+        acc[0] += vol;
+        for (int i = 0; i < 3; ++i) acc[1 + i] += vol * s[i] * 0.25;
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                acc[4 + 3 * i + j] += vol / 20.0 * (a[i] * a[j] + c1[i] * c1[j] + c2[i] * c2[j] + s[i] * s[j]);
+    }
+    for (int i = 0; i < 13; ++i) {
+        double t = block_sum<kRedThreads>(acc[i], sh);
+        if (threadIdx.x == 0) out[13 * (size_t)b + i] = t * (i == 0 ? 1.0 : rho[b]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// finalize: layout, topology, static pattern, uploads
+// ---------------------------------------------------------------------------
+void build(zema_scene* s) {
+    cudaStream_t st = s->st;
+    Allocator* A = &s->A;
+    const int NE = s->n_envs;
+    if (s->bodies.empty()) fail(ZEMA_ERR_INVALID_ARG, "scene has no bodies");
+    // ---- node layout by env: soft bodies then affine bodies
+    std::vector<int> tet_order, aff_order;
+    for (int e = 0; e < NE; ++e)
+        for (size_t i = 0; i < s->tin.size(); ++i)
+            if (s->tin[i].env == e) tet_order.push_back((int)i);
+    for (int e = 0; e < NE; ++e)
+        for (size_t i = 0; i < s->ain.size(); ++i)
+            if (s->ain[i].env == e) aff_order.push_back((int)i);
+    s->tet_body_node0.assign(s->tin.size(), 0);
+    s->aff_node0_h.assign(s->ain.size(), 0);
+    std::vector<int> node_env_h, env_node_start(NE + 1, 0), env_tet_start(NE + 1, 0), env_aff_start(NE + 1, 0);
+    std::vector<uint8_t> node_fixed_h;
+    std::vector<int4> tets_h;
+    std::vector<double> trho_h, tmu_h, tlam_h, xrest_h, x_h, v_h;
+    std::vector<int> aff_perm;  // affine device index -> input index
+    {
+        size_t ti = 0, ai = 0;
+        for (int e = 0; e < NE; ++e) {
+            env_node_start[e] = (int)node_env_h.size();
+            env_tet_start[e] = (int)tets_h.size();
+            for (; ti < tet_order.size() && s->tin[tet_order[ti]].env == e; ++ti) {
+                TetIn& B = s->tin[tet_order[ti]];
+                int n0 = (int)node_env_h.size();
+                s->tet_body_node0[tet_order[ti]] = n0;
+                size_t nv = B.X.size() / 3;
+                for (size_t k = 0; k < nv; ++k) {
+                    node_env_h.push_back(e);
+                    node_fixed_h.push_back(0);
+                    for (int j = 0; j < 3; ++j) {
+                        xrest_h.push_back(B.X[3 * k + j]);
+                        x_h.push_back(B.x0[3 * k + j]);
+                        v_h.push_back(B.v0[3 * k + j]);
+                    }
+                }
+                double mu = B.E / (2.0 * (1.0 + B.nu)), lam = B.E * B.nu / ((1.0 + B.nu) * (1.0 - 2.0 * B.nu));
+                for (size_t t = 0; t < B.T.size() / 4; ++t) {
+                    tets_h.push_back(make_int4(n0 + B.T[4 * t], n0 + B.T[4 * t + 1], n0 + B.T[4 * t + 2],
+                                               n0 + B.T[4 * t + 3]));
+                    trho_h.push_back(B.rho);
+                    tmu_h.push_back(mu);
+                    tlam_h.push_back(lam);
+                }
+            }
+            env_aff_start[e] = (int)aff_perm.size();
+            for (; ai < aff_order.size() && s->ain[aff_order[ai]].env == e; ++ai) {
+                int n0 = (int)node_env_h.size();
+                s->aff_node0_h[aff_order[ai]] = n0;
+                aff_perm.push_back(aff_order[ai]);
+                for (int k = 0; k < 4; ++k) {
+                    node_env_h.push_back(e);
+                    node_fixed_h.push_back(s->ain[aff_order[ai]].mode == 1 ? 1 : 0);
+                    for (int j = 0; j < 3; ++j) {
+                        xrest_h.push_back(0.0);
+                        x_h.push_back(0.0);
+                        v_h.push_back(0.0);
+                    }
+                }
+            }
+        }
+        env_node_start[NE] = (int)node_env_h.size();
+        env_tet_start[NE] = (int)tets_h.size();
+        env_aff_start[NE] = (int)aff_perm.size();
+    }
+    s->n_nodes = (int)node_env_h.size();
+    s->n_tets = (int)tets_h.size();
+    s->n_aff = (int)aff_perm.size();
+    s->env_node_start_h = env_node_start;
+    s->env_aff_start_h = env_aff_start;
+    int nN = s->n_nodes;
+    // soft node count (nodes before the affine ones within each env are soft)
+    std::vector<double> node_mass_h(nN, 0.0);
+    // ---- node -> incident tets (sorted by tet, local)
+    std::vector<int> ntp(nN + 1, 0), nti;
+    for (int t = 0; t < s->n_tets; ++t) {
+        int4 T = tets_h[t];
+        ntp[T.x + 1]++;
+        ntp[T.y + 1]++;
+        ntp[T.z + 1]++;
+        ntp[T.w + 1]++;
+    }
+    for (int i = 0; i < nN; ++i) ntp[i + 1] += ntp[i];
+    nti.assign(ntp[nN], 0);
+    {
+        std::vector<int> cur(ntp.begin(), ntp.end() - 1);
+        for (int t = 0; t < s->n_tets; ++t) {
+            int4 T = tets_h[t];
+            int ids[4] = {T.x, T.y, T.z, T.w};
+            for (int k = 0; k < 4; ++k) nti[cur[ids[k]]++] = 4 * t + k;
+        }
+    }
+    // ---- surface: soft boundary faces, affine meshes
+    std::vector<int> sv_node_h, sv_body_h, sv_env_h;
+    std::vector<uint8_t> sv_aff_h;
+    std::vector<double> sv_rest_h, sv_x0_h;
+    std::vector<int2> edges_h;
+    std::vector<int3> tris_h;
+    std::vector<int> env_sv_start(NE + 1, 0), env_edge_start(NE + 1, 0);
+    std::vector<int> body_id_of_tet(s->tin.size()), body_id_of_aff(s->ain.size());
+    for (size_t b = 0; b < s->bodies.size(); ++b) {
+        if (s->bodies[b].first == 0)
+            body_id_of_tet[s->bodies[b].second] = (int)b;
+        else
+            body_id_of_aff[s->bodies[b].second] = (int)b;
+    }
+    // affine mass properties are needed for sv_x0: computed on the device
+    // below; the rest-frame positions are filled after that.
+    std::vector<int> sv_aff_body;  // device affine index per sv (or -1)
+    std::vector<std::vector<int3>> env_tris(NE);
+    {
+        size_t ti = 0, ai = 0;
+        static const int FL[4][3] = {{0, 2, 1}, {0, 1, 3}, {0, 3, 2}, {1, 2, 3}};
+        for (int e = 0; e < NE; ++e) {
+            env_sv_start[e] = (int)sv_node_h.size();
+            std::vector<int3> etris;
+            for (; ti < tet_order.size() && s->tin[tet_order[ti]].env == e; ++ti) {
+                TetIn& B = s->tin[tet_order[ti]];
+                int n0 = s->tet_body_node0[tet_order[ti]];
+                std::map<std::tuple<int, int, int>, std::pair<int, std::tuple<int, int, int>>> faces;
+                for (size_t t = 0; t < B.T.size() / 4; ++t) {
+                    const int* T = &B.T[4 * t];
+                    for (int f = 0; f < 4; ++f) {
+                        int a = T[FL[f][0]], c = T[FL[f][1]], d = T[FL[f][2]];
+                        int k[3] = {a, c, d};
+                        std::sort(k, k + 3);
+                        auto key = std::make_tuple(k[0], k[1], k[2]);
+                        auto it = faces.find(key);
+                        if (it == faces.end())
+                            faces[key] = {1, std::make_tuple(a, c, d)};
+                        else
+                            it->second.first++;
+                    }
+                }
+                std::map<int, int> local_sv;
+                std::vector<std::tuple<int, int, int>> ft;
+                for (auto& kv : faces)
+                    if (kv.second.first == 1) ft.push_back(kv.second.second);
+                for (auto& f : ft) {
+                    local_sv[std::get<0>(f)] = 0;
+                    local_sv[std::get<1>(f)] = 0;
+                    local_sv[std::get<2>(f)] = 0;
+                }
+                for (auto& kv : local_sv) {
+                    kv.second = (int)sv_node_h.size();
+                    sv_node_h.push_back(n0 + kv.first);
+                    sv_aff_h.push_back(0);
+                    sv_body_h.push_back(body_id_of_tet[tet_order[ti]]);
+                    sv_env_h.push_back(e);
+                    sv_aff_body.push_back(-1);
+                    for (int j = 0; j < 3; ++j) sv_rest_h.push_back(B.X[3 * kv.first + j]);
+                }
+                for (auto& f : ft)
+                    etris.push_back(make_int3(local_sv[std::get<0>(f)], local_sv[std::get<1>(f)], local_sv[std::get<2>(f)]));
+            }
+            for (; ai < aff_order.size() && s->ain[aff_order[ai]].env == e; ++ai) {
+                AffIn& B = s->ain[aff_order[ai]];
+                int sv0 = (int)sv_node_h.size();
+                int dev_idx = (int)ai;
+                for (size_t k = 0; k < B.V.size() / 3; ++k) {
+                    sv_node_h.push_back(s->aff_node0_h[aff_order[ai]]);
+                    sv_aff_h.push_back(1);
+                    sv_body_h.push_back(body_id_of_aff[aff_order[ai]]);
+                    sv_env_h.push_back(e);
+                    sv_aff_body.push_back(dev_idx);
+                    for (int j = 0; j < 3; ++j) sv_rest_h.push_back(B.V[3 * k + j]);
+                }
+                for (size_t f = 0; f < B.F.size() / 3; ++f)
+                    etris.push_back(make_int3(sv0 + B.F[3 * f], sv0 + B.F[3 * f + 1], sv0 + B.F[3 * f + 2]));
+            }
+            // edges of this env, unique, ordered by (min, max)
+            env_edge_start[e] = (int)edges_h.size();
+            std::vector<std::pair<int, int>> ed;
+            for (auto& t : etris) {
+                int v3_[3] = {t.x, t.y, t.z};
+                for (int k = 0; k < 3; ++k) {
+                    int a = v3_[k], c = v3_[(k + 1) % 3];
+                    ed.push_back({std::min(a, c), std::max(a, c)});
+                }
+            }
+            std::sort(ed.begin(), ed.end());
+            ed.erase(std::unique(ed.begin(), ed.end()), ed.end());
+            for (auto& pr : ed) edges_h.push_back(make_int2(pr.first, pr.second));
+            for (auto& t : etris) tris_h.push_back(t);
+        }
+        env_sv_start[NE] = (int)sv_node_h.size();
+        env_edge_start[NE] = (int)edges_h.size();
+    }
+    s->n_sv = (int)sv_node_h.size();
+    s->n_edges = (int)edges_h.size();
+    s->n_tris = (int)tris_h.size();
+    s->env_sv_start_h = env_sv_start;
+    s->env_edge_start_h = env_edge_start;
+    std::vector<double> edge_rest2_h(s->n_edges);
+    double sum_len = 0.0;
+    for (int i = 0; i < s->n_edges; ++i) {
+        double d2 = 0.0;
+        for (int j = 0; j < 3; ++j) {
+            double d = sv_rest_h[3 * edges_h[i].x + j] - sv_rest_h[3 * edges_h[i].y + j];
+            d2 += d * d;
+        }
+        edge_rest2_h[i] = d2;
+        sum_len += std::sqrt(d2);
+    }
+    double mean_len = s->n_edges ? sum_len / s->n_edges : s->P.dhat;
+    s->cell = std::max(mean_len, s->P.dhat);
+    // ---- bodies
+    std::vector<int> body_class_h(s->bodies.size());
+    std::vector<double> body_mu_h(s->bodies.size());
+    for (size_t b = 0; b < s->bodies.size(); ++b) {
+        auto k = s->bodies[b];
+        if (k.first == 0) {
+            body_class_h[b] = 0;
+            body_mu_h[b] = s->tin[k.second].mu;
+        } else {
+            int m = s->ain[k.second].mode;
+            body_class_h[b] = m == 0 ? 1 : (m == 1 ? 2 : 3);
+            body_mu_h[b] = s->ain[k.second].mu;
+        }
+    }
+    // ---- units: per env soft nodes then affine bodies
+    std::vector<int> unit_kind_h, unit_idx_h, env_unit_start(NE + 1, 0);
+    for (int e = 0; e < NE; ++e) {
+        env_unit_start[e] = (int)unit_kind_h.size();
+        for (int n = env_node_start[e]; n < env_node_start[e + 1]; ++n) {
+            bool is_aff = false;
+            for (int a = env_aff_start[e]; a < env_aff_start[e + 1]; ++a) {
+                int n0 = s->aff_node0_h[aff_perm[a]];
+                if (n >= n0 && n < n0 + 4) is_aff = true;
+            }
+            if (!is_aff) {
+                unit_kind_h.push_back(0);
+                unit_idx_h.push_back(n);
+            }
+        }
+        for (int a = env_aff_start[e]; a < env_aff_start[e + 1]; ++a) {
+            unit_kind_h.push_back(1);
+            unit_idx_h.push_back(a);
+        }
+    }
+    env_unit_start[NE] = (int)unit_kind_h.size();
+    s->n_units = (int)unit_kind_h.size();
+    // ---- static pattern
+    std::vector<std::vector<int>> rows(nN);
+    for (int n = 0; n < nN; ++n) rows[n].push_back(n);
+    for (auto& T : tets_h) {
+        int ids[4] = {T.x, T.y, T.z, T.w};
+        for (int i = 0; i < 4; ++i)
+            for (int j = 0; j < 4; ++j) rows[ids[i]].push_back(ids[j]);
+    }
+    std::vector<int> aff_node0_dev(s->n_aff), aff_mode_dev(s->n_aff);
+    for (int a = 0; a < s->n_aff; ++a) {
+        aff_node0_dev[a] = s->aff_node0_h[aff_perm[a]];
+        aff_mode_dev[a] = s->ain[aff_perm[a]].mode;
+        if (aff_mode_dev[a] == 1) continue;
+        int n0 = aff_node0_dev[a];
+        for (int i = 0; i < 4; ++i)
+            for (int j = 0; j < 4; ++j) rows[n0 + i].push_back(n0 + j);
+    }
+    std::vector<int> S_rowptr_h(nN + 1, 0), S_col_h, S_diag_h(nN);
+    for (int n = 0; n < nN; ++n) {
+        std::sort(rows[n].begin(), rows[n].end());
+        rows[n].erase(std::unique(rows[n].begin(), rows[n].end()), rows[n].end());
+        S_rowptr_h[n + 1] = S_rowptr_h[n] + (int)rows[n].size();
+        for (int c : rows[n]) S_col_h.push_back(c);
+    }
+    auto blk = [&](int r, int c) {
+        auto it = std::lower_bound(S_col_h.begin() + S_rowptr_h[r], S_col_h.begin() + S_rowptr_h[r + 1], c);
+        return (int)(it - S_col_h.begin());
+    };
+    for (int n = 0; n < nN; ++n) S_diag_h[n] = blk(n, n);
+    s->n_sblocks = (int)S_col_h.size();
+    std::vector<std::vector<int>> src(s->n_sblocks);
+    for (int t = 0; t < s->n_tets; ++t) {
+        int4 T = tets_h[t];
+        int ids[4] = {T.x, T.y, T.z, T.w};
+        for (int i = 0; i < 4; ++i)
+            for (int j = 0; j < 4; ++j) src[blk(ids[i], ids[j])].push_back(16 * t + 4 * i + j);
+    }
+    for (int a = 0; a < s->n_aff; ++a) {
+        if (aff_mode_dev[a] == 1) continue;
+        int n0 = aff_node0_dev[a];
+        for (int i = 0; i < 4; ++i)
+            for (int j = 0; j < 4; ++j) src[blk(n0 + i, n0 + j)].push_back(16 * s->n_tets + 16 * a + 4 * i + j);
+    }
+    std::vector<int> S_src_ptr_h(s->n_sblocks + 1, 0), S_src_h;
+    for (int k = 0; k < s->n_sblocks; ++k) {
+        std::sort(src[k].begin(), src[k].end());
+        S_src_ptr_h[k + 1] = S_src_ptr_h[k] + (int)src[k].size();
+        for (int q : src[k]) S_src_h.push_back(q);
+    }
+    // ---- uploads
+    up(s, s->node_env, node_env_h);
+    up(s, s->node_fixed, node_fixed_h);
+    up(s, s->env_node_start, env_node_start);
+    up(s, s->env_tet_start, env_tet_start);
+    up(s, s->env_aff_start, env_aff_start);
+    up(s, s->env_unit_start, env_unit_start);
+    up(s, s->env_sv_start, env_sv_start);
+    up(s, s->env_edge_start, env_edge_start);
+    up(s, s->tets, tets_h);
+    up(s, s->tmu, tmu_h);
+    up(s, s->tlam, tlam_h);
+    up(s, s->aff_node0, aff_node0_dev);
+    up(s, s->aff_mode, aff_mode_dev);
+    up(s, s->unit_kind, unit_kind_h);
+    up(s, s->unit_idx, unit_idx_h);
+    up(s, s->sv_node, sv_node_h);
+    up(s, s->sv_aff, sv_aff_h);
+    up(s, s->sv_body, sv_body_h);
+    up(s, s->sv_env, sv_env_h);
+    up(s, s->sv_rest, sv_rest_h);
+    up(s, s->body_class, body_class_h);
+    up(s, s->body_mu, body_mu_h);
+    up(s, s->edges, edges_h);
+    up(s, s->tris, tris_h);
+    up(s, s->edge_rest2, edge_rest2_h);
+    up(s, s->node_tet_ptr, ntp);
+    up(s, s->node_tet_idx, nti);
+    up(s, s->S_rowptr, S_rowptr_h);
+    up(s, s->S_col, S_col_h);
+    up(s, s->S_src_ptr, S_src_ptr_h);
+    up(s, s->S_src, S_src_h);
+    up(s, s->S_diag, S_diag_h);
+    // ---- rest-shape precompute on the device
+    DBuf<double> xrest_d, trho_d;
+    up(s, xrest_d, xrest_h);
+    up(s, trho_d, trho_h);
+    s->Dminv.ensure(A, 9 * (size_t)s->n_tets + 9);
+    s->tvol.ensure(A, s->n_tets + 1);
+    s->node_mass.ensure(A, nN + 1);
+    DBuf<int> bad;
+    bad.ensure(A, 1);
+    ZCHECK(cudaMemsetAsync(bad.p, 0, sizeof(int), st));
+    if (s->n_tets) k_tet_rest<<<div_up(s->n_tets, TB), TB, 0, st>>>(xrest_d.p, s->tets.p, s->n_tets, s->Dminv.p, s->tvol.p, bad.p);
+    ZLAUNCH();
+    k_lumped_mass<<<div_up(nN, TB), TB, 0, st>>>(s->node_tet_ptr.p, s->node_tet_idx.p, s->tvol.p, trho_d.p, nN, s->node_mass.p);
+    ZLAUNCH();
+    // affine mass properties
+    std::vector<double> Vall;
+    std::vector<int> Fall, fptr(s->n_aff + 1, 0), voff(s->n_aff, 0);
+    std::vector<double> arho(s->n_aff);
+    for (int a = 0; a < s->n_aff; ++a) {
+        AffIn& B = s->ain[aff_perm[a]];
+        voff[a] = (int)(Vall.size() / 3);
+        Vall.insert(Vall.end(), B.V.begin(), B.V.end());
+        Fall.insert(Fall.end(), B.F.begin(), B.F.end());
+        fptr[a + 1] = (int)(Fall.size() / 3);
+        arho[a] = B.rho;
+    }
+    std::vector<double> mp(13 * (size_t)s->n_aff + 13, 0.0);
+    if (s->n_aff) {
+        DBuf<double> Vd, rhod, mpd;
+        DBuf<int> Fd, fpd, vod;
+        up(s, Vd, Vall);
+        up(s, Fd, Fall);
+        up(s, fpd, fptr);
+        up(s, vod, voff);
+        up(s, rhod, arho);
+        mpd.ensure(A, mp.size());
+        k_affine_mass<<<s->n_aff, kRedThreads, 0, st>>>(Vd.p, Fd.p, fpd.p, vod.p, rhod.p, s->n_aff, mpd.p);
+        ZLAUNCH();
+        ZCHECK(cudaMemcpyAsync(mp.data(), mpd.p, mp.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
+    int bad_h = 0;
+    ZCHECK(cudaMemcpyAsync(&bad_h, bad.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    ZCHECK(cudaStreamSynchronize(st));
+    if (bad_h) fail(ZEMA_ERR_INVERTED_INPUT, "a rest tetrahedron has non-positive volume");
+    s->node_mass_h.assign(nN, 0.0);
+    ZCHECK(cudaMemcpy(s->node_mass_h.data(), s->node_mass.p, nN * sizeof(double), cudaMemcpyDeviceToHost));
+    s->aff_m_in.assign(s->ain.size(), 0.0);
+    std::vector<double> aff_m_h(s->n_aff), aff_vol_h(s->n_aff), aff_S_h(9 * (size_t)s->n_aff),
+        aff_stiff_h(s->n_aff);
+    s->aff_com_h.assign(3 * (size_t)s->ain.size(), 0.0);
+    s->aff_mode_h.assign(s->ain.size(), 0);
+    for (int a = 0; a < s->n_aff; ++a) {
+        const double* q = &mp[13 * (size_t)a];
+        double vol = q[0], m = arho[a] * vol;
+        if (!(vol > 0.0)) fail(ZEMA_ERR_INVALID_ARG, "affine body mesh encloses no volume (not closed / outward?)");
+        double c[3] = {q[1] / m, q[2] / m, q[3] / m};
+        aff_m_h[a] = m;
+        s->aff_m_in[aff_perm[a]] = m;
+        aff_vol_h[a] = vol;
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) aff_S_h[9 * a + 3 * i + j] = q[4 + 3 * i + j] - m * c[i] * c[j];
+        aff_stiff_h[a] = s->ain[aff_perm[a]].stiff;
+        for (int i = 0; i < 3; ++i) s->aff_com_h[3 * aff_perm[a] + i] = c[i];
+        s->aff_mode_h[aff_perm[a]] = s->ain[aff_perm[a]].mode;
+    }
+    std::vector<double> aff_com_dev(3 * (size_t)s->n_aff);
+    for (int a = 0; a < s->n_aff; ++a)
+        for (int i = 0; i < 3; ++i) aff_com_dev[3 * a + i] = s->aff_com_h[3 * aff_perm[a] + i];
+    up(s, s->aff_m, aff_m_h);
+    up(s, s->aff_vol, aff_vol_h);
+    up(s, s->aff_S, aff_S_h);
+    up(s, s->aff_stiff, aff_stiff_h);
+    up(s, s->aff_com, aff_com_dev);
+    // surface rest positions relative to the centre of mass (affine)
+    sv_x0_h.assign(3 * (size_t)s->n_sv, 0.0);
+    for (int i = 0; i < s->n_sv; ++i)
+        if (sv_aff_body[i] >= 0)
+            for (int j = 0; j < 3; ++j) sv_x0_h[3 * i + j] = sv_rest_h[3 * i + j] - aff_com_dev[3 * sv_aff_body[i] + j];
+    up(s, s->sv_x0, sv_x0_h);
+    // ---- initial state: affine q (row, caller frame) -> centred columns
+    for (int a = 0; a < s->n_aff; ++a) {
+        AffIn& B = s->ain[aff_perm[a]];
+        int n0 = aff_node0_dev[a];
+        const double* c = &aff_com_dev[3 * a];
+        const double* q = B.q0;
+        const double* qd = B.qd0;
+        for (int i = 0; i < 3; ++i) {
+            double Ac = q[3 + 3 * i] * c[0] + q[4 + 3 * i] * c[1] + q[5 + 3 * i] * c[2];
+            double Adc = qd[3 + 3 * i] * c[0] + qd[4 + 3 * i] * c[1] + qd[5 + 3 * i] * c[2];
+            x_h[3 * n0 + i] = q[i] + Ac;
+            v_h[3 * n0 + i] = B.mode == 1 ? 0.0 : qd[i] + Adc;
+            for (int k = 0; k < 3; ++k) {
+                x_h[3 * (n0 + 1 + k) + i] = q[3 + 3 * i + k];
+                v_h[3 * (n0 + 1 + k) + i] = B.mode == 1 ? 0.0 : qd[3 + 3 * i + k];
+            }
+        }
+    }
+    up(s, s->x, x_h);
+    up(s, s->v, v_h);
+    // kinematic targets default to q0, multipliers to 0
+    std::vector<double> qt_h(12 * (size_t)s->n_aff + 12, 0.0), lam_h(12 * (size_t)s->n_aff + 12, 0.0);
+    for (int a = 0; a < s->n_aff; ++a)
+        for (int k = 0; k < 12; ++k) qt_h[12 * a + k] = s->ain[aff_perm[a]].q0[k];
+    up(s, s->qtarget, qt_h);
+    up(s, s->lamA, lam_h);
+    // ---- per-env bbox diagonal of the initial state
+    s->diag_h.assign(NE, 0.0);
+    for (int e = 0; e < NE; ++e) {
+        double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+        auto acc = [&](const double* p) {
+            for (int j = 0; j < 3; ++j) {
+                lo[j] = std::min(lo[j], p[j]);
+                hi[j] = std::max(hi[j], p[j]);
+            }
+        };
+        for (size_t i = 0; i < s->tin.size(); ++i)
+            if (s->tin[i].env == e)
+                for (size_t k = 0; k < s->tin[i].x0.size() / 3; ++k) acc(&s->tin[i].x0[3 * k]);
+        for (size_t i = 0; i < s->ain.size(); ++i)
+            if (s->ain[i].env == e) {
+                const AffIn& B = s->ain[i];
+                for (size_t k = 0; k < B.V.size() / 3; ++k) {
+                    double w[3];
+                    for (int r = 0; r < 3; ++r)
+                        w[r] = B.q0[r] + B.q0[3 + 3 * r] * B.V[3 * k] + B.q0[4 + 3 * r] * B.V[3 * k + 1] +
+                               B.q0[5 + 3 * r] * B.V[3 * k + 2];
+                    acc(w);
+                }
+            }
+        double d2 = 0.0;
+        for (int j = 0; j < 3; ++j) d2 += (hi[j] - lo[j]) * (hi[j] - lo[j]);
+        s->diag_h[e] = std::sqrt(d2);
+    }
+    s->tol_h.assign(NE, 0.0);
+    for (int e = 0; e < NE; ++e) s->tol_h[e] = s->P.newton_tol_rel * s->diag_h[e] * s->P.dt;
+    up(s, s->tolv, s->tol_h);
+    // ---- state buffers
+    size_t n3 = 3 * (size_t)nN + 3;
+    for (DBuf<double>* b : {&s->xt, &s->xhat, &s->p, &s->xtrial, &s->g, &s->b, &s->r, &s->z, &s->pp, &s->q})
+        b->ensure(A, n3);
+    for (DBuf<double>* b : {&s->X, &s->Xt, &s->X1}) b->ensure(A, 3 * (size_t)s->n_sv + 3);
+    s->stage_blk.ensure(A, 144 * ((size_t)s->n_tets + s->n_aff) + 9);
+    s->stage_g.ensure(A, 12 * (size_t)s->n_tets + 12);
+    s->S_val.ensure(A, 9 * (size_t)s->n_sblocks + 9);
+    s->Minv_s.ensure(A, 9 * (size_t)nN + 9);
+    s->Minv_a.ensure(A, 144 * (size_t)s->n_aff + 144);
+    for (DBuf<double>* b : {&s->kappa, &s->kappa_min, &s->alpha, &s->E, &s->dmin}) b->ensure(A, NE + 1);
+    for (DBuf<double>* b : {&s->part, &s->part2, &s->part3, &s->part4, &s->part5, &s->part6, &s->part7})
+        b->ensure(A, (size_t)ET_COUNT * NE * kChunks + 8);
+    for (DBuf<int>* b : {&s->conv, &s->pcg_iters, &s->need}) b->ensure(A, NE + 1);
+    s->capflag.ensure(A, 1);
+    for (DBuf<uint32_t>* b : {&s->pt_env, &s->ee_env, &s->m_env, &s->act_env, &s->swept_env, &s->lag_env})
+        b->ensure(A, NE + 2);
+    if (!s->h32) ZCHECK(cudaMallocHost(&s->h32, 64 * sizeof(uint32_t)));
+    if (!s->hd) ZCHECK(cudaMallocHost(&s->hd, (8 * (size_t)NE + 64) * sizeof(double)));
+    if (!s->hi) ZCHECK(cudaMallocHost(&s->hi, (4 * (size_t)NE + 64) * sizeof(int)));
+    // kappa: user value or pending rule
+    std::vector<double> kap(NE, s->P.kappa > 0 ? s->P.kappa : 0.0);
+    up(s, s->kappa, kap);
+    up(s, s->kappa_min, kap);
+    s->kappa_ready.assign(NE, s->P.kappa > 0 ? 1 : 0);
+    // ---- Geo view
+    Geo& G = s->G;
+    G.n_nodes = nN;
+    G.n_soft = 0;
+    G.n_aff = s->n_aff;
+    G.n_tets = s->n_tets;
+    G.n_sv = s->n_sv;
+    G.n_edges = s->n_edges;
+    G.n_tris = s->n_tris;
+    G.n_envs = NE;
+    G.n_units = s->n_units;
+    G.n_bodies = (int)s->bodies.size();
+    G.h = s->P.dt;
+    G.dhat = s->P.dhat;
+    G.eps_v = s->P.eps_v;
+    G.node_env = s->node_env.p;
+    G.node_fixed = s->node_fixed.p;
+    G.node_mass = s->node_mass.p;
+    G.env_node_start = s->env_node_start.p;
+    G.tets = s->tets.p;
+    G.Dminv = s->Dminv.p;
+    G.tvol = s->tvol.p;
+    G.tmu = s->tmu.p;
+    G.tlam = s->tlam.p;
+    G.env_tet_start = s->env_tet_start.p;
+    G.aff_node0 = s->aff_node0.p;
+    G.aff_mode = s->aff_mode.p;
+    G.aff_m = s->aff_m.p;
+    G.aff_S = s->aff_S.p;
+    G.aff_vol = s->aff_vol.p;
+    G.aff_stiff = s->aff_stiff.p;
+    G.aff_com = s->aff_com.p;
+    G.env_aff_start = s->env_aff_start.p;
+    G.unit_kind = s->unit_kind.p;
+    G.unit_idx = s->unit_idx.p;
+    G.env_unit_start = s->env_unit_start.p;
+    G.sv_node = s->sv_node.p;
+    G.sv_aff = s->sv_aff.p;
+    G.sv_x0 = s->sv_x0.p;
+    G.sv_rest = s->sv_rest.p;
+    G.sv_body = s->sv_body.p;
+    G.sv_env = s->sv_env.p;
+    G.body_class = s->body_class.p;
+    G.body_mu = s->body_mu.p;
+    G.edges = s->edges.p;
+    G.tris = s->tris.p;
+    G.edge_rest2 = s->edge_rest2.p;
+    G.env_sv_start = s->env_sv_start.p;
+    G.env_edge_start = s->env_edge_start.p;
+    G.node_tet_ptr = s->node_tet_ptr.p;
+    G.node_tet_idx = s->node_tet_idx.p;
+    G.S_rowptr = s->S_rowptr.p;
+    G.S_col = s->S_col.p;
+    G.S_src_ptr = s->S_src_ptr.p;
+    G.S_src = s->S_src.p;
+    // dynamic shared memory opt-in for the per-thread matrix kernels
+    ZCHECK(cudaFuncSetAttribute(k_elastic_gh, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 81 * EL_T * 8));
+    ZCHECK(cudaFuncSetAttribute(k_barrier_gh, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 144 * BR_T * 8));
+    ZCHECK(cudaFuncSetAttribute(k_affine_gh, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 81 * AF_T * 8));
+    ZCHECK(cudaStreamSynchronize(st));
+    s->finalized = true;
+}
+
+// ---------------------------------------------------------------------------
+// Pair lists
+// ---------------------------------------------------------------------------
+// Broad phase over X0 (-> X1) and merge into env-ordered PairRec `out` with
+// env offsets; returns the count.
+uint32_t candidates(zema_scene* s, const double* X0, const double* X1, DBuf<PairRec>& out, DBuf<uint32_t>& env_off) {
+    cudaStream_t st = s->st;
+    BPView v;
+    v.nsv = s->n_sv;
+    v.ne = s->n_edges;
+    v.nt = s->n_tris;
+    v.X0 = X0;
+    v.X1 = X1;
+    v.sv_body = s->sv_body.p;
+    v.body_class = s->body_class.p;
+    v.sv_env = s->sv_env.p;
+    v.edges = s->edges.p;
+    v.tris = s->tris.p;
+    v.infl = 0.5 * s->P.dhat;
+    v.inv_cell = 1.0 / s->cell;
+    s->bp.run(&s->A, v, st);
+    uint32_t n = s->bp.n_pt + s->bp.n_ee;
+    out.ensure(&s->A, n + 1);
+    int NE = s->n_envs;
+    k_pair_env_offsets<<<div_up(NE + 1, 64), 64, 0, st>>>(s->G, s->bp.qoff_pt.p, s->bp.qoff_ee.p, s->pt_env.p,
+                                                          s->ee_env.p, env_off.p);
+    ZLAUNCH();
+    if (n)
+        k_merge_pairs<<<div_up(n, TB), TB, 0, st>>>(s->G, s->bp.pt.p, s->bp.ee.p, s->pt_env.p, s->ee_env.p, env_off.p,
+                                                   (int)n, out.p);
+    ZLAUNCH();
+    s->S.max_candidates = std::max<int64_t>(s->S.max_candidates, n);
+    return n;
+}
+
+// active pairs (d < dhat) of X: fills s->act / s->act_env, per-env dmin
+uint32_t active_pairs(zema_scene* s, const double* X, bool want_dmin) {
+    cudaStream_t st = s->st;
+    uint32_t n = candidates(s, X, nullptr, s->cand, s->m_env);
+    int NE = s->n_envs;
+    if (want_dmin) {
+        std::vector<double> inf(NE, INFINITY);
+        ZCHECK(cudaMemcpyAsync(s->dmin.p, inf.data(), NE * sizeof(double), cudaMemcpyHostToDevice, st));
+    }
+    s->flag.ensure(&s->A, n + 1);
+    s->flagoff.ensure(&s->A, n + 2);
+    s->tmp32.ensure(&s->A, scan_tmp_size(n + 1));
+    if (n)
+        k_active_flags<<<div_up(n, TB), TB, 0, st>>>(s->G, X, s->cand.p, (int)n, s->flag.p,
+                                                    want_dmin ? s->dmin.p : nullptr);
+    ZLAUNCH();
+    exclusive_scan(s->flag.p, s->flagoff.p, n, s->tmp32.p, st);
+    ZCHECK(cudaMemcpyAsync(s->h32, s->flagoff.p + n, 4, cudaMemcpyDeviceToHost, st));
+    k_env_gather<<<div_up(NE + 1, 64), 64, 0, st>>>(s->flagoff.p, s->m_env.p, NE, s->act_env.p);
+    ZLAUNCH();
+    ZCHECK(cudaStreamSynchronize(st));
+    uint32_t na = s->h32[0];
+    s->act.ensure(&s->A, na + 1);
+    if (n) k_compact_pairs<<<div_up(n, TB), TB, 0, st>>>(s->cand.p, s->flag.p, s->flagoff.p, (int)n, s->act.p);
+    ZLAUNCH();
+    s->n_act = na;
+    s->S.max_active = std::max<int64_t>(s->S.max_active, na);
+    return na;
+}
+
+// ---------------------------------------------------------------------------
+// Energies
+// ---------------------------------------------------------------------------
+AffKin kin(zema_scene* s) { return AffKin{s->qtarget.p, s->lamA.p}; }
+
+Lag lagv(zema_scene* s) {
+    return Lag{s->lag.p, s->lag_w.p, s->lag_n.p, s->lag_c.p, s->lag_env.p, (int)s->n_lag};
+}
+
+// Per-env incremental potential at node positions xe (barrier over the pairs
+// in `pairs` with env offsets `poff`); result in s->hd[0..NE).
+void energy(zema_scene* s, const double* xe, const PairRec* pairs, const uint32_t* poff, bool barrier = true,
+            bool friction = true) {
+    cudaStream_t st = s->st;
+    int NE = s->n_envs;
+    ZCHECK(cudaMemsetAsync(s->part.p, 0, (size_t)ET_COUNT * NE * kChunks * sizeof(double), st));
+    k_sv_pos<<<div_up(s->n_sv, TB), TB, 0, st>>>(s->G, xe, s->X1.p);
+    k_soft_energy<<<red_grid(NE), kRedThreads, 0, st>>>(s->G, xe, s->xhat.p, s->part.p);
+    k_affine_energy<<<red_grid(NE), kRedThreads, 0, st>>>(s->G, xe, s->xhat.p, kin(s), s->part.p);
+    if (barrier && pairs)
+        k_barrier_energy<<<red_grid(NE), kRedThreads, 0, st>>>(s->G, s->X1.p, pairs, poff, s->kappa.p, s->part.p);
+    if (friction && s->n_lag)
+        k_friction_energy<<<red_grid(NE), kRedThreads, 0, st>>>(s->G, s->X1.p, s->Xt.p, lagv(s), s->part.p);
+    k_energy_total<<<div_up(NE, 64), 64, 0, st>>>(s->part.p, ET_COUNT, NE, s->E.p);
+    ZLAUNCH();
+    ZCHECK(cudaMemcpyAsync(s->hd, s->E.p, NE * sizeof(double), cudaMemcpyDeviceToHost, st));
+    ZCHECK(cudaStreamSynchronize(st));
+}
+
+// ---------------------------------------------------------------------------
+// Gradient and Hessian assembly at x; g and the BSR (S, C) are filled.
+// ---------------------------------------------------------------------------
+void grad_hess(zema_scene* s, bool barrier = true, bool friction = true, bool hess = true) {
+    cudaStream_t st = s->st;
+    Geo& G = s->G;
+    Allocator* A = &s->A;
+    if (s->n_tets)
+        k_elastic_gh<<<div_up(s->n_tets, EL_T), EL_T, 2 * 81 * EL_T * 8, st>>>(G, s->x.p, s->stage_blk.p, s->stage_g.p);
+    ZLAUNCH();
+    ZCHECK(cudaMemsetAsync(s->g.p, 0, 3 * (size_t)s->n_nodes * sizeof(double), st));
+    if (s->n_aff)
+        k_affine_gh<<<div_up(s->n_aff, AF_T), AF_T, 2 * 81 * AF_T * 8, st>>>(
+            G, s->x.p, s->xhat.p, kin(s), s->stage_blk.p + 144 * (size_t)s->n_tets, s->g.p);
+    ZLAUNCH();
+    k_soft_grad<<<div_up(s->n_nodes, TB), TB, 0, st>>>(G, s->x.p, s->xhat.p, s->stage_g.p, s->g.p);
+    ZLAUNCH();
+    if (hess) {
+        k_static_values<<<div_up(s->n_sblocks, TB), TB, 0, st>>>(G, s->n_sblocks, s->stage_blk.p, s->S_val.p);
+        k_static_diag<<<div_up(s->n_nodes, TB), TB, 0, st>>>(G, s->S_diag.p, s->S_val.p);
+        ZLAUNCH();
+    }
+    // contact records: active barrier pairs then lagged friction pairs
+    uint32_t na = barrier ? s->n_act : 0, nl = friction ? s->n_lag : 0;
+    uint32_t nr = na + nl;
+    s->pH.ensure(A, 144 * (size_t)nr + 144);
+    s->pG.ensure(A, 12 * (size_t)nr + 12);
+    if (na)
+        k_barrier_gh<<<div_up(na, BR_T), BR_T, 2 * 144 * BR_T * 8, st>>>(G, s->X.p, s->act.p, (int)na, s->kappa.p,
+                                                                          s->pH.p, s->pG.p);
+    if (nl)
+        k_friction_gh<<<div_up(nl, 128), 128, 0, st>>>(G, s->X.p, s->Xt.p, lagv(s), s->pH.p + 144 * (size_t)na,
+                                                        s->pG.p + 12 * (size_t)na);
+    ZLAUNCH();
+    // one record list: act then lag
+    DBuf<PairRec>& recs = s->swept;  // reuse as scratch for the concatenation
+    recs.ensure(A, nr + 1);
+    if (na) ZCHECK(cudaMemcpyAsync(recs.p, s->act.p, na * sizeof(PairRec), cudaMemcpyDeviceToDevice, st));
+    if (nl) ZCHECK(cudaMemcpyAsync(recs.p + na, s->lag.p, nl * sizeof(PairRec), cudaMemcpyDeviceToDevice, st));
+    s->C_rowptr.ensure(A, s->n_nodes + 2);
+    if (nr == 0) {
+        ZCHECK(cudaMemsetAsync(s->C_rowptr.p, 0, (s->n_nodes + 1) * sizeof(int), st));
+        s->n_cblocks = 0;
+        s->C_col.ensure(A, 1);
+        s->C_val.ensure(A, 9);
+        return;
+    }
+    s->cnt_blk.ensure(A, nr + 1);
+    s->off_blk.ensure(A, nr + 2);
+    s->cnt_g.ensure(A, nr + 1);
+    s->off_g.ensure(A, nr + 2);
+    k_contact_count<<<div_up(nr, TB), TB, 0, st>>>(G, recs.p, (int)nr, s->cnt_blk.p, s->cnt_g.p);
+    ZLAUNCH();
+    s->tmp32.ensure(A, scan_tmp_size(nr + 1));
+    exclusive_scan(s->cnt_blk.p, s->off_blk.p, nr, s->tmp32.p, st);
+    exclusive_scan(s->cnt_g.p, s->off_g.p, nr, s->tmp32.p, st);
+    ZCHECK(cudaMemcpyAsync(s->h32, s->off_blk.p + nr, 4, cudaMemcpyDeviceToHost, st));
+    ZCHECK(cudaMemcpyAsync(s->h32 + 1, s->off_g.p + nr, 4, cudaMemcpyDeviceToHost, st));
+    ZCHECK(cudaStreamSynchronize(st));
+    uint32_t nb = s->h32[0], ng = s->h32[1];
+    s->bkey.ensure(A, nb + 1);
+    s->bkey2.ensure(A, nb + 1);
+    s->bval.ensure(A, nb + 1);
+    s->bval2.ensure(A, nb + 1);
+    s->bstage.ensure(A, 9 * (size_t)nb + 9);
+    s->gkey.ensure(A, ng + 1);
+    s->gkey2.ensure(A, ng + 1);
+    s->gval.ensure(A, ng + 1);
+    s->gval2.ensure(A, ng + 1);
+    s->gstage.ensure(A, 3 * (size_t)ng + 3);
+    k_contact_emit<<<div_up(nr, 128), 128, 0, st>>>(G, recs.p, (int)nr, s->pH.p, s->pG.p, s->off_blk.p, s->off_g.p,
+                                                     s->bkey.p, s->bval.p, s->bstage.p, s->gkey.p, s->gval.p,
+                                                     s->gstage.p);
+    ZLAUNCH();
+    int nbits_node = 1;
+    while ((1ll << nbits_node) < (long long)s->n_nodes) ++nbits_node;
+    uint32_t mx = std::max(nb, ng) + 2;
+    s->tmp32.ensure(A, std::max(radix_tmp_size(mx), scan_tmp_size(mx)));
+    radix_sort(s->bkey.p, s->bval.p, s->bkey2.p, s->bval2.p, nb, 2 * nbits_node, s->tmp32.p, st);
+    radix_sort(s->gkey.p, s->gval.p, s->gkey2.p, s->gval2.p, ng, nbits_node, s->tmp32.p, st);
+    // unique blocks
+    s->head.ensure(A, mx);
+    s->hoff.ensure(A, mx + 1);
+    s->seg.ensure(A, mx + 1);
+    s->ukey.ensure(A, mx);
+    k_heads<<<div_up(nb, TB), TB, 0, st>>>(s->bkey.p, nb, s->head.p);
+    exclusive_scan(s->head.p, s->hoff.p, nb, s->tmp32.p, st);
+    k_seg_starts<<<div_up(nb + 1, TB), TB, 0, st>>>(s->head.p, s->hoff.p, nb, s->seg.p);
+    ZCHECK(cudaMemcpyAsync(s->h32 + 2, s->hoff.p + nb, 4, cudaMemcpyDeviceToHost, st));
+    ZCHECK(cudaStreamSynchronize(st));
+    uint32_t nu = s->h32[2];
+    s->C_val.ensure(A, 9 * (size_t)nu + 9);
+    s->C_col.ensure(A, nu + 1);
+    k_seg_sum<9><<<div_up(nu, 128), 128, 0, st>>>(s->seg.p, nu, s->bval.p, s->bstage.p, s->C_val.p, s->bkey.p, s->ukey.p);
+    k_contact_rows<<<div_up(s->n_nodes + 1, TB), TB, 0, st>>>(s->ukey.p, nu, s->n_nodes, s->C_rowptr.p, s->C_col.p);
+    ZLAUNCH();
+    s->n_cblocks = nu;
+    // unique gradient nodes
+    k_heads<<<div_up(ng, TB), TB, 0, st>>>(s->gkey.p, ng, s->head.p);
+    exclusive_scan(s->head.p, s->hoff.p, ng, s->tmp32.p, st);
+    k_seg_starts<<<div_up(ng + 1, TB), TB, 0, st>>>(s->head.p, s->hoff.p, ng, s->seg.p);
+    ZCHECK(cudaMemcpyAsync(s->h32 + 3, s->hoff.p + ng, 4, cudaMemcpyDeviceToHost, st));
+    ZCHECK(cudaStreamSynchronize(st));
+    uint32_t nug = s->h32[3];
+    s->gsum.ensure(A, 3 * (size_t)nug + 3);
+    k_seg_sum<3><<<div_up(nug, 128), 128, 0, st>>>(s->seg.p, nug, s->gval.p, s->gstage.p, s->gsum.p, s->gkey.p, s->ukey.p);
+    k_add_contact_grad<<<div_up(nug, 128), 128, 0, st>>>(s->ukey.p, s->gsum.p, nug, s->g.p);
+    ZLAUNCH();
+}
+
+// ---------------------------------------------------------------------------
+// PCG: solve (S + C) p = -g for every env not flagged in done_h
+// ---------------------------------------------------------------------------
+int64_t pcg(zema_scene* s, const std::vector<int>& done_h) {
+    cudaStream_t st = s->st;
+    Geo& G = s->G;
+    int NE = s->n_envs;
+    Bsr S{s->S_rowptr.p, s->S_col.p, s->S_val.p};
+    Bsr C{s->C_rowptr.p, s->C_col.p, s->C_val.p};
+    k_precond<<<div_up(s->n_units, 128), 128, 0, st>>>(G, S, C, s->Minv_s.p, s->Minv_a.p);
+    k_negate<<<div_up(3 * (size_t)s->n_nodes, TB), TB, 0, st>>>(s->g.p, s->b.p, 3 * (size_t)s->n_nodes);
+    ZLAUNCH();
+    for (int e = 0; e < NE; ++e) s->hi[e] = done_h[e];
+    ZCHECK(cudaMemcpyAsync(s->conv.p, s->hi, NE * sizeof(int), cudaMemcpyHostToDevice, st));
+    ZCHECK(cudaMemsetAsync(s->pcg_iters.p, 0, NE * sizeof(int), st));
+    PcgVec V{s->p.p, s->r.p, s->z.p, s->pp.p, s->q.p};
+    double* rz_a = s->part2.p;
+    double* rz_b = s->part3.p;
+    double* pq = s->part4.p;
+    double* rr = s->part5.p;
+    double* bb = s->part6.p;
+    k_pcg_init<<<red_grid(NE), kRedThreads, 0, st>>>(G, s->b.p, V, s->Minv_s.p, s->Minv_a.p, rz_a, bb);
+    ZLAUNCH();
+    double tol2 = s->P.pcg_rel_tol * s->P.pcg_rel_tol;
+    int it = 0;
+    const int check = 8;
+    while (it < s->P.max_pcg) {
+        for (int k = 0; k < check; ++k) {
+            k_pcg_spmv<<<red_grid(NE), kRedThreads, 0, st>>>(G, S, C, V, s->conv.p, pq);
+            k_pcg_update<<<red_grid(NE), kRedThreads, 0, st>>>(G, V, s->Minv_s.p, s->Minv_a.p, s->conv.p, rz_a, pq,
+                                                               rz_b, rr);
+            k_pcg_dir<<<red_grid(NE), kRedThreads, 0, st>>>(G, V, s->conv.p, s->pcg_iters.p, rz_a, rz_b, rr, bb, tol2);
+            std::swap(rz_a, rz_b);
+            ++it;
+        }
+        ZLAUNCH();
+        ZCHECK(cudaMemcpyAsync(s->hi, s->conv.p, NE * sizeof(int), cudaMemcpyDeviceToHost, st));
+        ZCHECK(cudaStreamSynchronize(st));
+        bool all = true;
+        for (int e = 0; e < NE; ++e) all &= s->hi[e] != 0;
+        if (all) break;
+    }
+    ZCHECK(cudaMemcpyAsync(s->hi, s->pcg_iters.p, NE * sizeof(int), cudaMemcpyDeviceToHost, st));
+    ZCHECK(cudaStreamSynchronize(st));
+    int64_t tot = 0;
+    for (int e = 0; e < NE; ++e) tot += s->hi[e];
+    // done envs: zero direction
+    for (int e = 0; e < NE; ++e) s->hi[e] = done_h[e];
+    ZCHECK(cudaMemcpyAsync(s->need.p, s->hi, NE * sizeof(int), cudaMemcpyHostToDevice, st));
+    k_mask_env<<<div_up(s->n_nodes, TB), TB, 0, st>>>(G, s->p.p, s->need.p);
+    ZLAUNCH();
+    return tot;
+}
+
+// per-env max step component -> s->hd
+void step_norm(zema_scene* s) {
+    cudaStream_t st = s->st;
+    int NE = s->n_envs;
+    k_step_norm<<<red_grid(NE), kRedThreads, 0, st>>>(s->G, s->p.p, s->part7.p);
+    k_max_total<<<div_up(NE, 64), 64, 0, st>>>(s->part7.p, NE, s->E.p);
+    ZLAUNCH();
+    ZCHECK(cudaMemcpyAsync(s->hd, s->E.p, NE * sizeof(double), cudaMemcpyDeviceToHost, st));
+    ZCHECK(cudaStreamSynchronize(st));
+}
+
+// Line search along direction dir from x (Newton step or warm-start
+// proposal): ACCD bound over the swept candidates, then halving until
+// E(x + alpha dir) <= E(x) per env.  On success x is advanced.  Returns the
+// number of halvings, or -1 when an env fails.
+int line_search(zema_scene* s, const double* dir, const std::vector<int>& done_h, bool warm,
+                std::vector<int>* accepted) {
+    // warm-start proposals get a single energy check, Newton steps up to 60 halvings
+    const int max_halvings = warm ? 0 : 60;
+    cudaStream_t st = s->st;
+    Geo& G = s->G;
+    int NE = s->n_envs;
+    double t0 = now_ms();
+    // swept candidates X(x) -> X(x + dir)
+    k_sv_pos<<<div_up(s->n_sv, TB), TB, 0, st>>>(G, s->x.p, s->X.p);
+    std::vector<double> one(NE, 1.0);
+    ZCHECK(cudaMemcpyAsync(s->alpha.p, one.data(), NE * sizeof(double), cudaMemcpyHostToDevice, st));
+    k_axpy_env<<<div_up(s->n_nodes, TB), TB, 0, st>>>(G, s->x.p, dir, s->alpha.p, s->xtrial.p);
+    k_sv_pos<<<div_up(s->n_sv, TB), TB, 0, st>>>(G, s->xtrial.p, s->X1.p);
+    ZLAUNCH();
+    // X1 is overwritten by energy(); keep the swept end positions in q (scratch)
+    s->q.ensure(&s->A, std::max<size_t>(3 * (size_t)s->n_nodes + 3, 3 * (size_t)s->n_sv + 3));
+    ZCHECK(cudaMemcpyAsync(s->q.p, s->X1.p, 3 * (size_t)s->n_sv * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    uint32_t ns = candidates(s, s->X.p, s->q.p, s->swept, s->swept_env);
+    s->n_swept = ns;
+    ZCHECK(cudaMemsetAsync(s->capflag.p, 0, sizeof(int), st));
+    if (ns) k_accd<<<div_up(ns, 128), 128, 0, st>>>(G, s->X.p, s->q.p, s->swept.p, (int)ns, s->alpha.p, s->capflag.p);
+    ZLAUNCH();
+    std::vector<double> alpha(NE);
+    ZCHECK(cudaMemcpyAsync(alpha.data(), s->alpha.p, NE * sizeof(double), cudaMemcpyDeviceToHost, st));
+    ZCHECK(cudaStreamSynchronize(st));
+    s->S.ms_phase[4] += now_ms() - t0;
+    t0 = now_ms();
+    energy(s, s->x.p, s->swept.p, s->swept_env.p);
+    std::vector<double> E0(s->hd, s->hd + NE);
+    std::vector<int> acc(NE, 0);
+    for (int e = 0; e < NE; ++e)
+        if (done_h[e]) {
+            acc[e] = 1;
+            alpha[e] = 0.0;
+        }
+    int halvings = 0;
+    bool fail_ls = false;
+    for (int k = 0; k <= max_halvings; ++k) {
+        ZCHECK(cudaMemcpyAsync(s->alpha.p, alpha.data(), NE * sizeof(double), cudaMemcpyHostToDevice, st));
+        k_axpy_env<<<div_up(s->n_nodes, TB), TB, 0, st>>>(G, s->x.p, dir, s->alpha.p, s->xtrial.p);
+        ZLAUNCH();
+        energy(s, s->xtrial.p, s->swept.p, s->swept_env.p);
+        bool all = true;
+        for (int e = 0; e < NE; ++e) {
+            if (acc[e]) continue;
+            if (s->hd[e] <= E0[e]) {
+                acc[e] = 1;
+            } else if (k < max_halvings) {
+                alpha[e] *= 0.5;
+                ++halvings;
+                all = false;
+            } else {
+                all = false;
+            }
+        }
+        if (all) break;
+        if (k == max_halvings) fail_ls = true;
+    }
+    if (fail_ls && !warm) {
+        s->S.ms_phase[1] += now_ms() - t0;
+        return -1;
+    }
+    // envs that never accepted (warm start only): alpha = 0
+    for (int e = 0; e < NE; ++e)
+        if (!acc[e]) alpha[e] = 0.0;
+    if (accepted) *accepted = acc;
+    ZCHECK(cudaMemcpyAsync(s->alpha.p, alpha.data(), NE * sizeof(double), cudaMemcpyHostToDevice, st));
+    k_axpy_env<<<div_up(s->n_nodes, TB), TB, 0, st>>>(G, s->x.p, dir, s->alpha.p, s->xtrial.p);
+    ZLAUNCH();
+    ZCHECK(cudaMemcpyAsync(s->x.p, s->xtrial.p, 3 * (size_t)s->n_nodes * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    s->S.ms_phase[1] += now_ms() - t0;
+    return halvings;
+}
+
+// lag friction at the current x (= x^t): records, weights, normals, mu lambda
+void lag_friction(zema_scene* s) {
+    cudaStream_t st = s->st;
+    k_sv_pos<<<div_up(s->n_sv, TB), TB, 0, st>>>(s->G, s->x.p, s->Xt.p);
+    ZLAUNCH();
+    uint32_t na = active_pairs(s, s->Xt.p, false);
+    s->lag.ensure(&s->A, na + 1);
+    s->lag_w.ensure(&s->A, 4 * (size_t)na + 4);
+    s->lag_n.ensure(&s->A, 3 * (size_t)na + 3);
+    s->lag_c.ensure(&s->A, na + 1);
+    if (na) {
+        ZCHECK(cudaMemcpyAsync(s->lag.p, s->act.p, na * sizeof(PairRec), cudaMemcpyDeviceToDevice, st));
+        k_lag_friction<<<div_up(na, 128), 128, 0, st>>>(s->G, s->Xt.p, s->lag.p, (int)na, s->kappa.p, s->lag_w.p,
+                                                         s->lag_n.p, s->lag_c.p);
+        ZLAUNCH();
+    }
+    ZCHECK(cudaMemcpyAsync(s->lag_env.p, s->act_env.p, (s->n_envs + 1) * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
+    s->n_lag = na;
+}
+
+// kappa: kappa_min = 1e3 x mean soft lumped mass of the env (else mean
+// dynamic affine mass / 8); kappa = clamp(-gE . gB / |gB|^2, kappa_min,
+// 100 kappa_min) at x^t with gE the gradient without contact terms and gB the
+// barrier gradient for kappa = 1, both in the paper's DOF coordinates.
+void init_kappa(zema_scene* s) {
+    cudaStream_t st = s->st;
+    int NE = s->n_envs;
+    bool any = false;
+    for (int e = 0; e < NE; ++e) any |= !s->kappa_ready[e];
+    if (!any) return;
+    std::vector<double> kmin(NE, 1.0);
+    for (int e = 0; e < NE; ++e) {
+        double sm = 0.0;
+        int cnt = 0;
+        for (int n = s->env_node_start_h[e]; n < s->env_node_start_h[e + 1]; ++n)
+            if (s->node_mass_h[n] > 0.0) {
+                sm += s->node_mass_h[n];
+                ++cnt;
+            }
+        double mbar = 1.0;
+        if (cnt) {
+            mbar = sm / cnt;
+        } else {
+            double tot = 0.0;
+            int cc = 0;
+            for (size_t i = 0; i < s->ain.size(); ++i)
+                if (s->ain[i].env == e && s->ain[i].mode == 0) {
+                    tot += s->aff_m_in[i] / 8.0;
+                    ++cc;
+                }
+            if (cc) mbar = tot / cc;
+        }
+        kmin[e] = 1e3 * mbar;
+    }
+    std::vector<double> kap_cur(NE), kmin_cur(NE);
+    ZCHECK(cudaMemcpyAsync(kap_cur.data(), s->kappa.p, NE * sizeof(double), cudaMemcpyDeviceToHost, st));
+    ZCHECK(cudaMemcpyAsync(kmin_cur.data(), s->kappa_min.p, NE * sizeof(double), cudaMemcpyDeviceToHost, st));
+    std::vector<double> one(NE, 1.0);
+    ZCHECK(cudaMemcpyAsync(s->kappa.p, one.data(), NE * sizeof(double), cudaMemcpyHostToDevice, st));
+    k_sv_pos<<<div_up(s->n_sv, TB), TB, 0, st>>>(s->G, s->x.p, s->X.p);
+    ZLAUNCH();
+    active_pairs(s, s->X.p, false);
+    uint32_t keep_lag = s->n_lag;
+    s->n_lag = 0;
+    size_t n3 = 3 * (size_t)s->n_nodes;
+    grad_hess(s, false, false, false);
+    k_affine_grad_to_row<<<div_up(s->n_aff + 1, 64), 64, 0, st>>>(s->G, s->g.p);
+    ZCHECK(cudaMemcpyAsync(s->r.p, s->g.p, n3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    grad_hess(s, true, false, false);
+    k_affine_grad_to_row<<<div_up(s->n_aff + 1, 64), 64, 0, st>>>(s->G, s->g.p);
+    ZLAUNCH();
+    s->n_lag = keep_lag;
+    std::vector<double> ga(n3), ge(n3);
+    ZCHECK(cudaMemcpyAsync(ga.data(), s->g.p, n3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    ZCHECK(cudaMemcpyAsync(ge.data(), s->r.p, n3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    ZCHECK(cudaStreamSynchronize(st));
+    for (size_t i = 0; i < n3; ++i) ga[i] -= ge[i];
+    ZCHECK(cudaMemcpyAsync(s->z.p, ga.data(), n3 * sizeof(double), cudaMemcpyHostToDevice, st));
+    k_env_dot2<<<red_grid(NE), kRedThreads, 0, st>>>(s->G, s->r.p, s->z.p, s->part2.p, s->part3.p);
+    ZLAUNCH();
+    std::vector<double> pab((size_t)NE * kChunks), pbb((size_t)NE * kChunks);
+    ZCHECK(cudaMemcpyAsync(pab.data(), s->part2.p, pab.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    ZCHECK(cudaMemcpyAsync(pbb.data(), s->part3.p, pbb.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    ZCHECK(cudaStreamSynchronize(st));
+    for (int e = 0; e < NE; ++e) {
+        if (s->kappa_ready[e]) continue;
+        double ab = 0.0, bbv = 0.0;
+        for (int c = 0; c < kChunks; ++c) {
+            ab += pab[(size_t)e * kChunks + c];
+            bbv += pbb[(size_t)e * kChunks + c];
+        }
+        double k = kmin[e];
+        if (bbv > 0.0) k = std::min(std::max(-ab / bbv, kmin[e]), 100.0 * kmin[e]);
+        kap_cur[e] = k;
+        kmin_cur[e] = kmin[e];
+        s->kappa_ready[e] = 1;
+    }
+    ZCHECK(cudaMemcpyAsync(s->kappa.p, kap_cur.data(), NE * sizeof(double), cudaMemcpyHostToDevice, st));
+    ZCHECK(cudaMemcpyAsync(s->kappa_min.p, kmin_cur.data(), NE * sizeof(double), cudaMemcpyHostToDevice, st));
+    ZCHECK(cudaStreamSynchronize(st));
+}
+
+}  // namespace
+
+namespace {
+
+__global__ void k_scale_dir(Geo G, const double* v, double h, double* d) {
+    int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= G.n_nodes) return;
+    for (int j = 0; j < 3; ++j) d[3 * (size_t)n + j] = G.node_fixed[n] ? 0.0 : h * v[3 * (size_t)n + j];
+}
+
+// One time step of every environment.
+void do_step(zema_scene* s) {
+    zema_scene& W = *s;
+    cudaStream_t st = s->st;
+    Geo& G = s->G;
+    int NE = s->n_envs;
+    size_t n3 = 3 * (size_t)s->n_nodes;
+    double t0 = now_ms();
+    W.lam_save.ensure(&s->A, 12 * (size_t)s->n_aff + 12);
+    if (s->n_aff)
+        ZCHECK(cudaMemcpyAsync(W.lam_save.p, s->lamA.p, 12 * (size_t)s->n_aff * sizeof(double),
+                               cudaMemcpyDeviceToDevice, st));
+    // predictor (Eq. 1-3)
+    const double* gr = s->P.gravity;
+    k_predict<<<div_up(s->n_nodes, TB), TB, 0, st>>>(G, s->x.p, s->v.p, s->xt.p, s->xhat.p, gr[0], gr[1], gr[2]);
+    if (s->n_aff) k_predict_affine<<<div_up(s->n_aff, 64), 64, 0, st>>>(G, s->xhat.p, gr[0], gr[1], gr[2]);
+    ZLAUNCH();
+    bool first = !s->first_step_done;
+    init_kappa(s);
+    // lagged friction at x^t (Eq. 9-10); d_min at x^t for the kappa rule
+    lag_friction(s);
+    if (first) {
+        // d_min over active pairs at x^t
+        k_sv_pos<<<div_up(s->n_sv, TB), TB, 0, st>>>(G, s->x.p, s->X.p);
+        ZLAUNCH();
+        active_pairs(s, s->X.p, true);
+        W.dmin_last.assign(NE, INFINITY);
+        ZCHECK(cudaMemcpyAsync(s->hd, s->dmin.p, NE * sizeof(double), cudaMemcpyDeviceToHost, st));
+        ZCHECK(cudaStreamSynchronize(st));
+        for (int e = 0; e < NE; ++e) W.dmin_last[e] = s->hd[e];
+        s->first_step_done = true;
+    }
+    s->S.ms_phase[0] += now_ms() - t0;
+    // warm start: x^t + alpha h v^t, CCD-bounded, kept if the energy does not rise
+    W.dirw.ensure(&s->A, n3 + 3);
+    k_scale_dir<<<div_up(s->n_nodes, TB), TB, 0, st>>>(G, s->v.p, s->P.dt, W.dirw.p);
+    ZLAUNCH();
+    std::vector<int> done(NE, 0), acc;
+    line_search(s, W.dirw.p, done, true, &acc);
+    for (int e = 0; e < NE; ++e) s->S.warm_accepted += acc[e];
+    int rounds = 0;
+    for (;;) {
+        bool converged = false;
+        for (int it = 0; it < s->P.max_newton; ++it) {
+            double ta = now_ms();
+            k_sv_pos<<<div_up(s->n_sv, TB), TB, 0, st>>>(G, s->x.p, s->X.p);
+            ZLAUNCH();
+            active_pairs(s, s->X.p, true);
+            double tb = now_ms();
+            s->S.ms_phase[0] += tb - ta;
+            grad_hess(s);
+            ZCHECK(cudaStreamSynchronize(st));
+            double tc = now_ms();
+            s->S.ms_phase[2] += tc - tb;
+            s->S.pcg_iters += pcg(s, done);
+            step_norm(s);
+            s->S.ms_phase[3] += now_ms() - tc;
+            bool all = true;
+            for (int e = 0; e < NE; ++e) {
+                if (done[e]) continue;
+                if (s->hd[e] <= s->tol_h[e]) {
+                    done[e] = 1;
+                } else {
+                    all = false;
+                    s->S.newton_iters += 1;
+                }
+            }
+            if (all) {
+                converged = true;
+                break;
+            }
+            // zero the direction of envs that just converged
+            for (int e = 0; e < NE; ++e) s->hi[e] = done[e];
+            ZCHECK(cudaMemcpyAsync(s->need.p, s->hi, NE * sizeof(int), cudaMemcpyHostToDevice, st));
+            k_mask_env<<<div_up(s->n_nodes, TB), TB, 0, st>>>(G, s->p.p, s->need.p);
+            ZLAUNCH();
+            int hv = line_search(s, s->p.p, done, false, nullptr);
+            if (hv < 0) fail(ZEMA_ERR_LINESEARCH, "line search found no decrease after 60 halvings");
+            s->S.ls_halvings += hv;
+        }
+        if (!converged) fail(ZEMA_ERR_NEWTON_MAXITER, "Newton did not converge within max_newton iterations");
+        // kinematic augmented Lagrangian (Eq. 13)
+        if (s->n_aff == 0) break;
+        ZCHECK(cudaMemsetAsync(s->need.p, 0, NE * sizeof(int), st));
+        k_al_check<<<div_up(s->n_aff, 64), 64, 0, st>>>(G, s->x.p, kin(s), s->tolv.p, s->need.p);
+        ZLAUNCH();
+        ZCHECK(cudaMemcpyAsync(s->hi, s->need.p, NE * sizeof(int), cudaMemcpyDeviceToHost, st));
+        ZCHECK(cudaStreamSynchronize(st));
+        bool any = false;
+        for (int e = 0; e < NE; ++e) any |= s->hi[e] != 0;
+        if (!any || rounds >= s->P.max_al_rounds) break;
+        ++rounds;
+        k_al_update<<<div_up(s->n_aff, 64), 64, 0, st>>>(G, s->x.p, s->qtarget.p, s->lamA.p, s->need.p);
+        ZLAUNCH();
+        for (int e = 0; e < NE; ++e) done[e] = s->hi[e] ? 0 : 1;
+    }
+    s->S.al_rounds += rounds;
+    // d_min at the accepted state (last active-pair pass) and energy of env 0
+    std::vector<double> dm(NE);
+    ZCHECK(cudaMemcpyAsync(dm.data(), s->dmin.p, NE * sizeof(double), cudaMemcpyDeviceToHost, st));
+    // velocities (Eq. 11)
+    k_velocity<<<div_up(s->n_nodes, TB), TB, 0, st>>>(G, s->x.p, s->xt.p, s->v.p);
+    ZLAUNCH();
+    std::vector<double> kap(NE), kmin(NE);
+    ZCHECK(cudaMemcpyAsync(kap.data(), s->kappa.p, NE * sizeof(double), cudaMemcpyDeviceToHost, st));
+    ZCHECK(cudaMemcpyAsync(kmin.data(), s->kappa_min.p, NE * sizeof(double), cudaMemcpyDeviceToHost, st));
+    ZCHECK(cudaStreamSynchronize(st));
+    bool changed = false;
+    for (int e = 0; e < NE; ++e) {
+        if (s->P.kappa <= 0.0 && dm[e] < 0.1 * s->P.dhat && dm[e] < W.dmin_last[e]) {
+            kap[e] = std::min(2.0 * kap[e], 1e4 * kmin[e]);
+            changed = true;
+        }
+        W.dmin_last[e] = dm[e];
+    }
+    if (changed) ZCHECK(cudaMemcpyAsync(s->kappa.p, kap.data(), NE * sizeof(double), cudaMemcpyHostToDevice, st));
+    s->S.dmin = dm[0];
+    s->S.kappa = kap[0];
+    s->S.steps += 1;
+    ZCHECK(cudaStreamSynchronize(st));
+}
+
+void restore_step(zema_scene* s) {
+    zema_scene& W = *s;
+    cudaStream_t st = s->st;
+    size_t n3 = 3 * (size_t)s->n_nodes;
+    cudaMemcpyAsync(s->x.p, s->xt.p, n3 * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    if (s->n_aff && W.lam_save.p)
+        cudaMemcpyAsync(s->lamA.p, W.lam_save.p, 12 * (size_t)s->n_aff * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    cudaStreamSynchronize(st);
+}
+
+int affine_dev_index(const zema_scene* s, int input_idx) {
+    // device affine order = env-major order of input bodies
+    int k = 0;
+    for (int e = 0; e < s->n_envs; ++e)
+        for (size_t i = 0; i < s->ain.size(); ++i)
+            if (s->ain[i].env == e) {
+                if ((int)i == input_idx) return k;
+                ++k;
+            }
+    return -1;
+}
+
+#define ZEMA_TRY(s)                                  \
+    try
+#define ZEMA_CATCH(s)                                \
+    catch (const ZemaError& e) {                     \
+        if (s) (s)->err = e.msg;                     \
+        return (zema_status)e.status;                \
+    }                                                \
+    catch (const std::exception& e) {                \
+        if (s) (s)->err = e.what();                  \
+        return ZEMA_ERR_OOM;                         \
+    }
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+void zema_default_params(zema_scene_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->dt = 0.01;
+    p->dhat = 1e-3;
+    p->kappa = 0.0;
+    p->eps_v = 1e-3;
+    p->newton_tol_rel = 1e-3;
+    p->gravity[1] = -9.81;
+    p->pcg_rel_tol = 1e-4;
+    p->max_newton = 100;
+    p->max_pcg = 10000;
+    p->max_al_rounds = 10;
+    p->n_envs = 1;
+}
+
+zema_status zema_create_scene(const zema_scene_params* params, zema_scene** out) {
+    if (!params || !out) return ZEMA_ERR_INVALID_ARG;
+    if (!(params->dt > 0) || !(params->dhat > 0) || params->n_envs < 1 || !(params->eps_v > 0))
+        return ZEMA_ERR_INVALID_ARG;
+    zema_scene* s = new (std::nothrow) zema_scene();
+    if (!s) return ZEMA_ERR_OOM;
+    s->P = *params;
+    s->n_envs = params->n_envs;
+    s->st = (cudaStream_t)params->stream;
+    s->A.fa = params->alloc;
+    s->A.ff = params->free;
+    s->A.ctx = params->alloc_ctx;
+    s->A.stream = s->st;
+    *out = s;
+    return ZEMA_OK;
+}
+
+zema_status zema_add_tet_body(zema_scene* s, int32_t env, const double* X_rest, int64_t nv, const int32_t* tets,
+                              int64_t nt, const double* x0, const double* v0, double E, double nu, double rho,
+                              double mu_friction, int32_t* body_id) {
+    if (!s) return ZEMA_ERR_INVALID_ARG;
+    if (s->finalized) {
+        s->err = "bodies must be added before the first step";
+        return ZEMA_ERR_STATE;
+    }
+    if (env < 0 || env >= s->n_envs || !X_rest || !tets || nv < 4 || nt < 1 || !(E > 0) || !(nu > -1 && nu < 0.5) ||
+        !(rho > 0) || mu_friction < 0) {
+        s->err = "invalid tet body arguments";
+        return ZEMA_ERR_INVALID_ARG;
+    }
+    TetIn B;
+    B.env = env;
+    B.X.assign(X_rest, X_rest + 3 * nv);
+    B.x0 = x0 ? std::vector<double>(x0, x0 + 3 * nv) : B.X;
+    B.v0 = v0 ? std::vector<double>(v0, v0 + 3 * nv) : std::vector<double>(3 * nv, 0.0);
+    B.T.assign(tets, tets + 4 * nt);
+    for (int64_t t = 0; t < nt; ++t) {
+        const int* T = &B.T[4 * t];
+        for (int k = 0; k < 4; ++k)
+            if (T[k] < 0 || T[k] >= nv) {
+                s->err = "tet index out of range";
+                return ZEMA_ERR_INVALID_ARG;
+            }
+        const double* a = &B.X[3 * T[0]];
+        double e[3][3];
+        for (int k = 0; k < 3; ++k)
+            for (int j = 0; j < 3; ++j) e[k][j] = B.X[3 * T[k + 1] + j] - a[j];
+        double det = e[0][0] * (e[1][1] * e[2][2] - e[1][2] * e[2][1]) -
+                     e[0][1] * (e[1][0] * e[2][2] - e[1][2] * e[2][0]) + e[0][2] * (e[1][0] * e[2][1] - e[1][1] * e[2][0]);
+        if (!(det > 0.0)) {
+            s->err = "tet with non-positive rest volume";
+            return ZEMA_ERR_INVERTED_INPUT;
+        }
+    }
+    B.E = E;
+    B.nu = nu;
+    B.rho = rho;
+    B.mu = mu_friction;
+    s->tin.push_back(std::move(B));
+    s->bodies.push_back({0, (int)s->tin.size() - 1});
+    if (body_id) *body_id = (int32_t)s->bodies.size() - 1;
+    return ZEMA_OK;
+}
+
+zema_status zema_add_affine_body(zema_scene* s, int32_t env, const double* V_rest, int64_t nv, const int32_t* F,
+                                 int64_t nf, const double q0[12], const double qdot0[12], double rho, double stiffness,
+                                 double mu_friction, int32_t mode, int32_t* body_id) {
+    if (!s) return ZEMA_ERR_INVALID_ARG;
+    if (s->finalized) {
+        s->err = "bodies must be added before the first step";
+        return ZEMA_ERR_STATE;
+    }
+    if (env < 0 || env >= s->n_envs || !V_rest || !F || !q0 || nv < 4 || nf < 4 || !(rho > 0) || !(stiffness > 0) ||
+        mode < 0 || mode > 2 || mu_friction < 0) {
+        s->err = "invalid affine body arguments";
+        return ZEMA_ERR_INVALID_ARG;
+    }
+    AffIn B;
+    B.env = env;
+    B.mode = mode;
+    B.V.assign(V_rest, V_rest + 3 * nv);
+    B.F.assign(F, F + 3 * nf);
+    for (int64_t i = 0; i < 3 * nf; ++i)
+        if (B.F[i] < 0 || B.F[i] >= nv) {
+            s->err = "face index out of range";
+            return ZEMA_ERR_INVALID_ARG;
+        }
+    for (int k = 0; k < 12; ++k) {
+        B.q0[k] = q0[k];
+        B.qd0[k] = qdot0 ? qdot0[k] : 0.0;
+    }
+    B.rho = rho;
+    B.stiff = stiffness;
+    B.mu = mu_friction;
+    s->ain.push_back(std::move(B));
+    s->bodies.push_back({1, (int)s->ain.size() - 1});
+    if (body_id) *body_id = (int32_t)s->bodies.size() - 1;
+    return ZEMA_OK;
+}
+
+zema_status zema_finalize(zema_scene* s) {
+    if (!s) return ZEMA_ERR_INVALID_ARG;
+    if (s->finalized) return ZEMA_OK;
+    ZEMA_TRY(s) {
+        build(s);
+        // reject initial states with touching primitives
+        k_sv_pos<<<div_up(s->n_sv, TB), TB, 0, s->st>>>(s->G, s->x.p, s->X.p);
+        ZLAUNCH();
+        active_pairs(s, s->X.p, true);
+        std::vector<double> dm(s->n_envs);
+        ZCHECK(cudaMemcpyAsync(dm.data(), s->dmin.p, s->n_envs * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+        ZCHECK(cudaStreamSynchronize(s->st));
+        for (double d : dm)
+            if (!(d > 0.0)) fail(ZEMA_ERR_INTERSECTING_INPUT, "initial state has primitives at distance 0");
+        return ZEMA_OK;
+    }
+    ZEMA_CATCH(s)
+}
+
+zema_status zema_set_kinematic_target(zema_scene* s, int32_t body, const double q_target[12]) {
+    if (!s || !q_target || body < 0 || body >= (int)s->bodies.size() || s->bodies[body].first != 1)
+        return ZEMA_ERR_INVALID_ARG;
+    ZEMA_TRY(s) {
+        int i = s->bodies[body].second;
+        if (!s->finalized) {
+            // before finalize the target becomes the initial target
+            zema_status r = zema_finalize(s);
+            if (r != ZEMA_OK) return r;
+        }
+        int a = affine_dev_index(s, i);
+        ZCHECK(cudaMemcpyAsync(s->qtarget.p + 12 * (size_t)a, q_target, 12 * sizeof(double), cudaMemcpyHostToDevice,
+                               s->st));
+        ZCHECK(cudaStreamSynchronize(s->st));
+        return ZEMA_OK;
+    }
+    ZEMA_CATCH(s)
+}
+
+zema_status zema_step(zema_scene* s, int32_t n_steps, zema_step_stats* stats) {
+    if (!s || n_steps < 0) return ZEMA_ERR_INVALID_ARG;
+    if (!s->finalized) {
+        zema_status r = zema_finalize(s);
+        if (r != ZEMA_OK) return r;
+    }
+    std::memset(&s->S, 0, sizeof(s->S));
+    s->S.dmin = INFINITY;
+    zema_status status = ZEMA_OK;
+    for (int k = 0; k < n_steps; ++k) {
+        try {
+            do_step(s);
+        } catch (const ZemaError& e) {
+            s->err = e.msg;
+            status = (zema_status)e.status;
+            restore_step(s);
+            break;
+        }
+    }
+    if (stats) *stats = s->S;
+    return status;
+}
+
+zema_status zema_get_state(const zema_scene* cs, int32_t body, double* out, int64_t cap, int64_t* written) {
+    zema_scene* s = const_cast<zema_scene*>(cs);
+    if (!s || !out || body < 0 || body >= (int)s->bodies.size()) return ZEMA_ERR_INVALID_ARG;
+    ZEMA_TRY(s) {
+        auto bk = s->bodies[body];
+        if (bk.first == 0) {
+            const TetIn& B = s->tin[bk.second];
+            int64_t nv = (int64_t)B.X.size() / 3;
+            if (cap < 6 * nv) return ZEMA_ERR_INVALID_ARG;
+            if (!s->finalized) {
+                std::copy(B.x0.begin(), B.x0.end(), out);
+                std::copy(B.v0.begin(), B.v0.end(), out + 3 * nv);
+            } else {
+                size_t n0 = s->tet_body_node0[bk.second];
+                ZCHECK(cudaMemcpyAsync(out, s->x.p + 3 * n0, 3 * nv * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+                ZCHECK(cudaMemcpyAsync(out + 3 * nv, s->v.p + 3 * n0, 3 * nv * sizeof(double), cudaMemcpyDeviceToHost,
+                                       s->st));
+                ZCHECK(cudaStreamSynchronize(s->st));
+            }
+            if (written) *written = 6 * nv;
+            return ZEMA_OK;
+        }
+        if (cap < 24) return ZEMA_ERR_INVALID_ARG;
+        const AffIn& B = s->ain[bk.second];
+        if (!s->finalized) {
+            for (int k = 0; k < 12; ++k) {
+                out[k] = B.q0[k];
+                out[12 + k] = B.qd0[k];
+            }
+        } else {
+            double xc[12], vc[12];
+            size_t n0 = s->aff_node0_h[bk.second];
+            ZCHECK(cudaMemcpyAsync(xc, s->x.p + 3 * n0, 12 * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+            ZCHECK(cudaMemcpyAsync(vc, s->v.p + 3 * n0, 12 * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+            ZCHECK(cudaStreamSynchronize(s->st));
+            const double* c = &s->aff_com_h[3 * bk.second];
+            for (int i = 0; i < 3; ++i) {
+                // A_ik = c_k[i]; p = p' - A com
+                double Ac = 0.0, Adc = 0.0;
+                for (int k = 0; k < 3; ++k) {
+                    out[3 + 3 * i + k] = xc[3 * (1 + k) + i];
+                    out[12 + 3 + 3 * i + k] = vc[3 * (1 + k) + i];
+                    Ac += xc[3 * (1 + k) + i] * c[k];
+                    Adc += vc[3 * (1 + k) + i] * c[k];
+                }
+                out[i] = xc[i] - Ac;
+                out[12 + i] = vc[i] - Adc;
+            }
+        }
+        if (written) *written = 24;
+        return ZEMA_OK;
+    }
+    ZEMA_CATCH(s)
+}
+
+zema_status zema_set_state(zema_scene* s, int32_t body, const double* in, int64_t n) {
+    if (!s || !in || body < 0 || body >= (int)s->bodies.size()) return ZEMA_ERR_INVALID_ARG;
+    ZEMA_TRY(s) {
+        auto bk = s->bodies[body];
+        if (bk.first == 0) {
+            TetIn& B = s->tin[bk.second];
+            int64_t nv = (int64_t)B.X.size() / 3;
+            if (n != 6 * nv) return ZEMA_ERR_INVALID_ARG;
+            if (!s->finalized) {
+                std::copy(in, in + 3 * nv, B.x0.begin());
+                std::copy(in + 3 * nv, in + 6 * nv, B.v0.begin());
+                return ZEMA_OK;
+            }
+            size_t n0 = s->tet_body_node0[bk.second];
+            ZCHECK(cudaMemcpyAsync(s->x.p + 3 * n0, in, 3 * nv * sizeof(double), cudaMemcpyHostToDevice, s->st));
+            ZCHECK(cudaMemcpyAsync(s->v.p + 3 * n0, in + 3 * nv, 3 * nv * sizeof(double), cudaMemcpyHostToDevice, s->st));
+            ZCHECK(cudaStreamSynchronize(s->st));
+            return ZEMA_OK;
+        }
+        if (n != 24) return ZEMA_ERR_INVALID_ARG;
+        AffIn& B = s->ain[bk.second];
+        if (!s->finalized) {
+            for (int k = 0; k < 12; ++k) {
+                B.q0[k] = in[k];
+                B.qd0[k] = in[12 + k];
+            }
+            return ZEMA_OK;
+        }
+        double xc[12], vc[12];
+        const double* c = &s->aff_com_h[3 * bk.second];
+        bool fixed = B.mode == 1;
+        for (int i = 0; i < 3; ++i) {
+            double Ac = 0.0, Adc = 0.0;
+            for (int k = 0; k < 3; ++k) {
+                xc[3 * (1 + k) + i] = in[3 + 3 * i + k];
+                vc[3 * (1 + k) + i] = fixed ? 0.0 : in[12 + 3 + 3 * i + k];
+                Ac += in[3 + 3 * i + k] * c[k];
+                Adc += in[12 + 3 + 3 * i + k] * c[k];
+            }
+            xc[i] = in[i] + Ac;
+            vc[i] = fixed ? 0.0 : in[12 + i] + Adc;
+        }
+        size_t n0 = s->aff_node0_h[bk.second];
+        ZCHECK(cudaMemcpyAsync(s->x.p + 3 * n0, xc, 12 * sizeof(double), cudaMemcpyHostToDevice, s->st));
+        ZCHECK(cudaMemcpyAsync(s->v.p + 3 * n0, vc, 12 * sizeof(double), cudaMemcpyHostToDevice, s->st));
+        ZCHECK(cudaStreamSynchronize(s->st));
+        return ZEMA_OK;
+    }
+    ZEMA_CATCH(s)
+}
+
+zema_status zema_copy_soft_state_device(const zema_scene* cs, double* x_dev, double* v_dev) {
+    zema_scene* s = const_cast<zema_scene*>(cs);
+    if (!s || !s->finalized) return ZEMA_ERR_STATE;
+    ZEMA_TRY(s) {
+        size_t off = 0;
+        for (size_t i = 0; i < s->tin.size(); ++i) {
+            size_t nv = s->tin[i].X.size() / 3;
+            size_t n0 = s->tet_body_node0[i];
+            if (x_dev)
+                ZCHECK(cudaMemcpyAsync(x_dev + 3 * off, s->x.p + 3 * n0, 3 * nv * sizeof(double), cudaMemcpyDeviceToDevice,
+                                       s->st));
+            if (v_dev)
+                ZCHECK(cudaMemcpyAsync(v_dev + 3 * off, s->v.p + 3 * n0, 3 * nv * sizeof(double), cudaMemcpyDeviceToDevice,
+                                       s->st));
+            off += nv;
+        }
+        return ZEMA_OK;
+    }
+    ZEMA_CATCH(s)
+}
+
+zema_status zema_scene_counts(const zema_scene* s, int64_t out[8]) {
+    if (!s || !out) return ZEMA_ERR_INVALID_ARG;
+    int64_t nv = 0, nt = 0;
+    for (auto& b : s->tin) {
+        nv += (int64_t)b.X.size() / 3;
+        nt += (int64_t)b.T.size() / 4;
+    }
+    out[0] = nv;
+    out[1] = nt;
+    out[2] = (int64_t)s->ain.size();
+    out[3] = s->n_sv;
+    out[4] = s->n_edges;
+    out[5] = s->n_tris;
+    out[6] = s->n_nodes;
+    out[7] = s->n_envs;
+    return ZEMA_OK;
+}
+
+zema_status zema_get_kappa(const zema_scene* cs, int32_t env, double* kappa) {
+    zema_scene* s = const_cast<zema_scene*>(cs);
+    if (!s || !kappa || env < 0 || env >= s->n_envs || !s->finalized) return ZEMA_ERR_INVALID_ARG;
+    ZEMA_TRY(s) {
+        ZCHECK(cudaMemcpyAsync(kappa, s->kappa.p + env, sizeof(double), cudaMemcpyDeviceToHost, s->st));
+        ZCHECK(cudaStreamSynchronize(s->st));
+        return ZEMA_OK;
+    }
+    ZEMA_CATCH(s)
+}
+
+zema_status zema_set_kappa(zema_scene* s, int32_t env, double kappa, double kappa_min) {
+    if (!s || env < 0 || env >= s->n_envs || !(kappa > 0) || !(kappa_min > 0)) return ZEMA_ERR_INVALID_ARG;
+    if (!s->finalized) {
+        zema_status r = zema_finalize(s);
+        if (r != ZEMA_OK) return r;
+    }
+    ZEMA_TRY(s) {
+        ZCHECK(cudaMemcpyAsync(s->kappa.p + env, &kappa, sizeof(double), cudaMemcpyHostToDevice, s->st));
+        ZCHECK(cudaMemcpyAsync(s->kappa_min.p + env, &kappa_min, sizeof(double), cudaMemcpyHostToDevice, s->st));
+        ZCHECK(cudaStreamSynchronize(s->st));
+        s->kappa_ready[env] = 1;
+        return ZEMA_OK;
+    }
+    ZEMA_CATCH(s)
+}
+
+const char* zema_last_error(const zema_scene* s) { return s ? s->err.c_str() : "null scene"; }
+
+void zema_destroy_scene(zema_scene* s) {
+    if (!s) return;
+    if (s->st) cudaStreamSynchronize(s->st);
+    delete s;
+}
+
+zema_status zema_eval_energy_grad(zema_scene* s, int32_t apply_predictor, double* energy_out, double* grad) {
+    if (!s || !energy_out) return ZEMA_ERR_INVALID_ARG;
+    if (!s->finalized) {
+        zema_status r = zema_finalize(s);
+        if (r != ZEMA_OK) return r;
+    }
+    ZEMA_TRY(s) {
+        cudaStream_t st = s->st;
+        Geo& G = s->G;
+        int NE = s->n_envs;
+        if (apply_predictor) {
+            const double* gr = s->P.gravity;
+            k_predict<<<div_up(s->n_nodes, TB), TB, 0, st>>>(G, s->x.p, s->v.p, s->xt.p, s->xhat.p, gr[0], gr[1], gr[2]);
+            if (s->n_aff) k_predict_affine<<<div_up(s->n_aff, 64), 64, 0, st>>>(G, s->xhat.p, gr[0], gr[1], gr[2]);
+            ZLAUNCH();
+            init_kappa(s);
+            lag_friction(s);
+        }
+        k_sv_pos<<<div_up(s->n_sv, TB), TB, 0, st>>>(G, s->x.p, s->X.p);
+        ZLAUNCH();
+        active_pairs(s, s->X.p, false);
+        energy(s, s->x.p, s->cand.p, s->m_env.p);
+        for (int e = 0; e < NE; ++e) energy_out[e] = s->hd[e];
+        if (grad) {
+            grad_hess(s, true, true, false);
+            k_affine_grad_to_row<<<div_up(s->n_aff + 1, 64), 64, 0, st>>>(G, s->g.p);
+            ZLAUNCH();
+            std::vector<double> gh(3 * (size_t)s->n_nodes);
+            ZCHECK(cudaMemcpyAsync(gh.data(), s->g.p, gh.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+            ZCHECK(cudaStreamSynchronize(st));
+            size_t o = 0;
+            for (size_t b = 0; b < s->bodies.size(); ++b) {
+                auto bk = s->bodies[b];
+                if (bk.first == 0) {
+                    size_t nv = s->tin[bk.second].X.size() / 3, n0 = s->tet_body_node0[bk.second];
+                    for (size_t k = 0; k < 3 * nv; ++k) grad[o + k] = gh[3 * n0 + k];
+                    o += 3 * nv;
+                } else {
+                    size_t n0 = s->aff_node0_h[bk.second];
+                    for (int k = 0; k < 12; ++k) grad[o + k] = s->ain[bk.second].mode == 1 ? 0.0 : gh[3 * n0 + k];
+                    o += 12;
+                }
+            }
+        }
+        return ZEMA_OK;
+    }
+    ZEMA_CATCH(s)
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// Stand-alone entry points on host arrays (same device code as the stepper)
+// ===========================================================================
+namespace {
+
+struct Temp {
+    Allocator A;
+    std::vector<std::pair<void*, size_t>> bufs;
+    cudaStream_t st;
+    explicit Temp(cudaStream_t s) : st(s) { A.stream = s; }
+    template <class T>
+    T* put(const T* h, size_t n) {
+        T* d = (T*)A.get(n * sizeof(T) + 16);
+        bufs.push_back({d, n * sizeof(T) + 16});
+        if (h && n) ZCHECK(cudaMemcpyAsync(d, h, n * sizeof(T), cudaMemcpyHostToDevice, st));
+        return d;
+    }
+    ~Temp() {
+        for (auto& b : bufs) A.put(b.first, b.second);
+    }
+};
+
+__global__ void k_sv_env_of(const int* sv_body, const int* b_env, int n, int* sv_env) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) sv_env[i] = b_env[sv_body[i]];
+}
+
+__global__ void __launch_bounds__(BR_T) k_local_barrier(const double* x12, const int* is_ee, const double* eps_x,
+                                                        int n, double dhat, double* e_out, double* g_out,
+                                                        double* H_out) {
+    extern __shared__ double sm[];
+    int i = blockIdx.x * BR_T + threadIdx.x;
+    if (i >= n) return;
+    SMat<12> H{sm + threadIdx.x, BR_T}, V{sm + 144 * BR_T + threadIdx.x, BR_T};
+    V3 x[4];
+    for (int k = 0; k < 4; ++k) x[k] = ld3(x12 + 12 * (size_t)i + 3 * k);
+    double E = 0.0, g[12];
+    bool act = pair_barrier(x, is_ee[i] != 0, dhat, 1.0, eps_x[i], E, g, H, V, true);
+    e_out[i] = act ? E : 0.0;
+    for (int a = 0; a < 12; ++a) {
+        g_out[12 * (size_t)i + a] = act ? g[a] : 0.0;
+        for (int b = 0; b < 12; ++b) H_out[144 * (size_t)i + 12 * a + b] = act ? H(a, b) : 0.0;
+    }
+}
+
+__global__ void k_local_distance(const double* x12, const int* is_ee, int n, double* d2, double* w) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    V3 x[4];
+    for (int k = 0; k < 4; ++k) x[k] = ld3(x12 + 12 * (size_t)i + 3 * k);
+    DistInfo di = classify(x, is_ee[i] != 0);
+    d2[i] = di.d2;
+    for (int k = 0; k < 4; ++k) w[4 * (size_t)i + k] = di.w[k];
+}
+
+__global__ void __launch_bounds__(EL_T) k_local_nh(const double* F9, int n, double mu, double lam, double* psi,
+                                                   double* g, double* H) {
+    extern __shared__ double sm[];
+    int i = blockIdx.x * EL_T + threadIdx.x;
+    if (i >= n) return;
+    SMat<9> M{sm + threadIdx.x, EL_T}, W{sm + 81 * EL_T + threadIdx.x, EL_T};
+    double P[9], ps;
+    if (!nh_eval(F9 + 9 * (size_t)i, mu, lam, ps, P, &M)) {
+        psi[i] = INFINITY;
+        return;
+    }
+    psd_project<9>(M, W);
+    psi[i] = ps;
+    for (int a = 0; a < 9; ++a) {
+        g[9 * (size_t)i + a] = P[a];
+        for (int b = 0; b < 9; ++b) H[81 * (size_t)i + 9 * a + b] = M(a, b);
+    }
+}
+
+__global__ void k_local_accd(const double* x12, const double* p12, const int* is_ee, int n, double* t) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    V3 x[4], p[4];
+    for (int k = 0; k < 4; ++k) {
+        x[k] = ld3(x12 + 12 * (size_t)i + 3 * k);
+        p[k] = ld3(p12 + 12 * (size_t)i + 3 * k);
+    }
+    t[i] = accd(x, p, is_ee[i] != 0, 0.1, 1.0, 10000, nullptr);
+}
+
+template <class T>
+void get(T* h, const T* d, size_t n, cudaStream_t st) {
+    if (n) ZCHECK(cudaMemcpyAsync(h, d, n * sizeof(T), cudaMemcpyDeviceToHost, st));
+}
+
+zema_status status_of(const ZemaError& e) { return (zema_status)e.status; }
+
+}  // namespace
+
+extern "C" {
+
+zema_status zema_candidates_raw(int64_t nsv, const double* pos0, const double* pos1, const int32_t* sv_body, int64_t nb,
+                                const int32_t* b_class, const int32_t* b_env, int64_t ne, const int32_t* edges,
+                                int64_t nt, const int32_t* tris, double inflate, double cell_size, int64_t cap,
+                                int32_t* pt_out, int32_t* ee_out, int64_t* n_out, void* stream) {
+    if (nsv < 0 || nb < 1 || ne < 0 || nt < 0 || !pos0 || !sv_body || !b_class || !b_env || !n_out || !(inflate >= 0))
+        return ZEMA_ERR_INVALID_ARG;
+    try {
+        cudaStream_t st = (cudaStream_t)stream;
+        Temp T(st);
+        double cs = cell_size;
+        if (!(cs > 0)) {
+            double sum = 0.0;
+            for (int64_t i = 0; i < ne; ++i) {
+                double d2 = 0.0;
+                for (int j = 0; j < 3; ++j) {
+                    double d = pos0[3 * edges[2 * i] + j] - pos0[3 * edges[2 * i + 1] + j];
+                    d2 += d * d;
+                }
+                sum += std::sqrt(d2);
+            }
+            cs = std::max(ne ? sum / ne : 2.0 * inflate, 2.0 * inflate);
+            if (!(cs > 0)) cs = 1.0;
+        }
+        BPView v;
+        v.nsv = (int)nsv;
+        v.ne = (int)ne;
+        v.nt = (int)nt;
+        v.X0 = T.put(pos0, 3 * (size_t)nsv);
+        v.X1 = pos1 ? T.put(pos1, 3 * (size_t)nsv) : nullptr;
+        int* svb = T.put(sv_body, (size_t)nsv);
+        v.sv_body = svb;
+        v.body_class = T.put(b_class, (size_t)nb);
+        int* benv = T.put(b_env, (size_t)nb);
+        int* sve = T.put<int>(nullptr, (size_t)nsv + 1);
+        if (nsv) k_sv_env_of<<<div_up(nsv, TB), TB, 0, st>>>(svb, benv, (int)nsv, sve);
+        ZLAUNCH();
+        v.sv_env = sve;
+        v.edges = (const int2*)T.put(edges, 2 * (size_t)ne);
+        v.tris = (const int3*)T.put(tris, 3 * (size_t)nt);
+        v.infl = inflate;
+        v.inv_cell = 1.0 / cs;
+        BroadPhase bp;
+        bp.run(&T.A, v, st);
+        n_out[0] = bp.n_pt;
+        n_out[1] = bp.n_ee;
+        std::vector<int2> h;
+        if (pt_out) {
+            size_t m = std::min<size_t>(bp.n_pt, (size_t)cap);
+            h.resize(m);
+            get(h.data(), bp.pt.p, m, st);
+            ZCHECK(cudaStreamSynchronize(st));
+            for (size_t i = 0; i < m; ++i) {
+                pt_out[2 * i] = h[i].x;
+                pt_out[2 * i + 1] = h[i].y;
+            }
+        }
+        if (ee_out) {
+            size_t m = std::min<size_t>(bp.n_ee, (size_t)cap);
+            h.resize(m);
+            get(h.data(), bp.ee.p, m, st);
+            ZCHECK(cudaStreamSynchronize(st));
+            for (size_t i = 0; i < m; ++i) {
+                ee_out[2 * i] = h[i].x;
+                ee_out[2 * i + 1] = h[i].y;
+            }
+        }
+        ZCHECK(cudaStreamSynchronize(st));
+        // release the broad phase's buffers before the temp allocator goes
+        bp.~BroadPhase();
+        new (&bp) BroadPhase();
+        return ZEMA_OK;
+    } catch (const ZemaError& e) {
+        return status_of(e);
+    }
+}
+
+zema_status zema_local_barrier(int64_t n, const double* x12, const int32_t* is_ee, const double* eps_x, double dhat,
+                               double* e_out, double* g_out, double* H_out, void* stream) {
+    if (n < 0 || !x12 || !is_ee || !eps_x || !e_out || !g_out || !H_out || !(dhat > 0)) return ZEMA_ERR_INVALID_ARG;
+    if (n == 0) return ZEMA_OK;
+    try {
+        cudaStream_t st = (cudaStream_t)stream;
+        Temp T(st);
+        double* dx = T.put(x12, 12 * (size_t)n);
+        int* de = T.put(is_ee, (size_t)n);
+        double* dp = T.put(eps_x, (size_t)n);
+        double* E = T.put<double>(nullptr, (size_t)n);
+        double* g = T.put<double>(nullptr, 12 * (size_t)n);
+        double* H = T.put<double>(nullptr, 144 * (size_t)n);
+        ZCHECK(cudaFuncSetAttribute(k_local_barrier, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 144 * BR_T * 8));
+        k_local_barrier<<<div_up(n, BR_T), BR_T, 2 * 144 * BR_T * 8, st>>>(dx, de, dp, (int)n, dhat, E, g, H);
+        ZLAUNCH();
+        get(e_out, E, n, st);
+        get(g_out, g, 12 * n, st);
+        get(H_out, H, 144 * n, st);
+        ZCHECK(cudaStreamSynchronize(st));
+        return ZEMA_OK;
+    } catch (const ZemaError& e) {
+        return status_of(e);
+    }
+}
+
+zema_status zema_local_distance(int64_t n, const double* x12, const int32_t* is_ee, double* d2_out, double* w_out,
+                                void* stream) {
+    if (n < 0 || !x12 || !is_ee || !d2_out || !w_out) return ZEMA_ERR_INVALID_ARG;
+    if (n == 0) return ZEMA_OK;
+    try {
+        cudaStream_t st = (cudaStream_t)stream;
+        Temp T(st);
+        double* dx = T.put(x12, 12 * (size_t)n);
+        int* de = T.put(is_ee, (size_t)n);
+        double* d2 = T.put<double>(nullptr, (size_t)n);
+        double* w = T.put<double>(nullptr, 4 * (size_t)n);
+        k_local_distance<<<div_up(n, 128), 128, 0, st>>>(dx, de, (int)n, d2, w);
+        ZLAUNCH();
+        get(d2_out, d2, n, st);
+        get(w_out, w, 4 * n, st);
+        ZCHECK(cudaStreamSynchronize(st));
+        return ZEMA_OK;
+    } catch (const ZemaError& e) {
+        return status_of(e);
+    }
+}
+
+zema_status zema_local_neo_hookean(int64_t n, const double* F9, double mu, double lam, double* psi_out, double* g_out,
+                                   double* H_out, void* stream) {
+    if (n < 0 || !F9 || !psi_out || !g_out || !H_out) return ZEMA_ERR_INVALID_ARG;
+    if (n == 0) return ZEMA_OK;
+    try {
+        cudaStream_t st = (cudaStream_t)stream;
+        Temp T(st);
+        double* dF = T.put(F9, 9 * (size_t)n);
+        double* ps = T.put<double>(nullptr, (size_t)n);
+        double* g = T.put<double>(nullptr, 9 * (size_t)n);
+        double* H = T.put<double>(nullptr, 81 * (size_t)n);
+        ZCHECK(cudaFuncSetAttribute(k_local_nh, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 81 * EL_T * 8));
+        k_local_nh<<<div_up(n, EL_T), EL_T, 2 * 81 * EL_T * 8, st>>>(dF, (int)n, mu, lam, ps, g, H);
+        ZLAUNCH();
+        get(psi_out, ps, n, st);
+        get(g_out, g, 9 * n, st);
+        get(H_out, H, 81 * n, st);
+        ZCHECK(cudaStreamSynchronize(st));
+        return ZEMA_OK;
+    } catch (const ZemaError& e) {
+        return status_of(e);
+    }
+}
+
+zema_status zema_local_accd(int64_t n, const double* x12, const double* p12, const int32_t* is_ee, double* t_out,
+                            void* stream) {
+    if (n < 0 || !x12 || !p12 || !is_ee || !t_out) return ZEMA_ERR_INVALID_ARG;
+    if (n == 0) return ZEMA_OK;
+    try {
+        cudaStream_t st = (cudaStream_t)stream;
+        Temp T(st);
+        double* dx = T.put(x12, 12 * (size_t)n);
+        double* dp = T.put(p12, 12 * (size_t)n);
+        int* de = T.put(is_ee, (size_t)n);
+        double* t = T.put<double>(nullptr, (size_t)n);
+        k_local_accd<<<div_up(n, 128), 128, 0, st>>>(dx, dp, de, (int)n, t);
+        ZLAUNCH();
+        get(t_out, t, n, st);
+        ZCHECK(cudaStreamSynchronize(st));
+        return ZEMA_OK;
+    } catch (const ZemaError& e) {
+        return status_of(e);
+    }
+}
+
+}  // extern "C"

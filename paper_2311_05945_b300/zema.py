@@ -1,0 +1,354 @@
+"""Python binding of the zema C ABI (include/zema.h): argument marshalling only.
+
+Every computation happens in libzema.so's CUDA kernels.  PyTorch supplies the
+CUDA stream (and, optionally, device memory through its caching allocator).
+There is no CPU fallback: without the built library or a GPU, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import scenes as _scenes
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libzema.so")
+
+STATUS = {
+    0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "INTERSECTING_INPUT", 5: "INVERTED_INPUT",
+    6: "NEWTON_MAXITER", 7: "LINESEARCH", 8: "PCG_MAXITER", 9: "NONFINITE", 10: "FAULT_INJECTED", 11: "STATE",
+}
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("dt", C.c_double), ("dhat", C.c_double), ("kappa", C.c_double), ("eps_v", C.c_double),
+        ("newton_tol_rel", C.c_double), ("gravity", C.c_double * 3), ("pcg_rel_tol", C.c_double),
+        ("max_newton", C.c_int32), ("max_pcg", C.c_int32), ("max_al_rounds", C.c_int32),
+        ("precision", C.c_int32), ("n_envs", C.c_int32), ("warm_start", C.c_int32),
+        ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p),
+    ]
+
+
+class StepStats(C.Structure):
+    _fields_ = [
+        ("steps", C.c_int64), ("newton_iters", C.c_int64), ("pcg_iters", C.c_int64), ("ls_halvings", C.c_int64),
+        ("al_rounds", C.c_int64), ("warm_accepted", C.c_int64), ("max_candidates", C.c_int64),
+        ("max_active", C.c_int64), ("dmin", C.c_double), ("kappa", C.c_double), ("energy", C.c_double),
+        ("ms_phase", C.c_double * 6),
+    ]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "ms_phase"}
+        d["ms_phase"] = dict(zip(["dcd", "energy", "hess", "linear", "ccd", "other"], list(self.ms_phase)))
+        return d
+
+
+class ZemaError(RuntimeError):
+    def __init__(self, status, msg=""):
+        super().__init__(f"zema status {status} ({STATUS.get(status, '?')}): {msg}")
+        self.status = status
+
+
+_lib = None
+
+DP = C.POINTER(C.c_double)
+IP = C.POINTER(C.c_int32)
+LP = C.POINTER(C.c_int64)
+
+
+def lib():
+    """Load libzema.so; raise if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"zema CUDA library not built ({LIB_PATH}); run paper_2311_05945_b300.build.build()")
+    L = C.CDLL(LIB_PATH)
+    L.zema_default_params.argtypes = [C.POINTER(Params)]
+    L.zema_create_scene.argtypes = [C.POINTER(Params), C.POINTER(C.c_void_p)]
+    L.zema_add_tet_body.argtypes = [C.c_void_p, C.c_int32, DP, C.c_int64, IP, C.c_int64, DP, DP, C.c_double,
+                                    C.c_double, C.c_double, C.c_double, IP]
+    L.zema_add_affine_body.argtypes = [C.c_void_p, C.c_int32, DP, C.c_int64, IP, C.c_int64, DP, DP, C.c_double,
+                                       C.c_double, C.c_double, C.c_int32, IP]
+    L.zema_finalize.argtypes = [C.c_void_p]
+    L.zema_set_kinematic_target.argtypes = [C.c_void_p, C.c_int32, DP]
+    L.zema_step.argtypes = [C.c_void_p, C.c_int32, C.POINTER(StepStats)]
+    L.zema_get_state.argtypes = [C.c_void_p, C.c_int32, DP, C.c_int64, LP]
+    L.zema_set_state.argtypes = [C.c_void_p, C.c_int32, DP, C.c_int64]
+    L.zema_copy_soft_state_device.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+    L.zema_scene_counts.argtypes = [C.c_void_p, LP]
+    L.zema_get_kappa.argtypes = [C.c_void_p, C.c_int32, DP]
+    L.zema_set_kappa.argtypes = [C.c_void_p, C.c_int32, C.c_double, C.c_double]
+    L.zema_last_error.restype = C.c_char_p
+    L.zema_last_error.argtypes = [C.c_void_p]
+    L.zema_destroy_scene.argtypes = [C.c_void_p]
+    L.zema_eval_energy_grad.argtypes = [C.c_void_p, C.c_int32, DP, DP]
+    L.zema_candidates_raw.argtypes = [C.c_int64, DP, DP, IP, C.c_int64, IP, IP, C.c_int64, IP, C.c_int64, IP,
+                                      C.c_double, C.c_double, C.c_int64, IP, IP, LP, C.c_void_p]
+    L.zema_local_barrier.argtypes = [C.c_int64, DP, IP, DP, C.c_double, DP, DP, DP, C.c_void_p]
+    L.zema_local_distance.argtypes = [C.c_int64, DP, IP, DP, DP, C.c_void_p]
+    L.zema_local_neo_hookean.argtypes = [C.c_int64, DP, C.c_double, C.c_double, DP, DP, DP, C.c_void_p]
+    L.zema_local_accd.argtypes = [C.c_int64, DP, DP, IP, DP, C.c_void_p]
+    _lib = L
+    return L
+
+
+def _d(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _dp(a):
+    return None if a is None else a.ctypes.data_as(DP)
+
+
+def _ip(a):
+    return None if a is None else a.ctypes.data_as(IP)
+
+
+def _stream():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("zema needs a CUDA device")
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+# torch-backed device allocator (device memory comes from PyTorch's caching allocator)
+def _torch_alloc(nbytes, stream, ctx):
+    import torch
+    return int(torch.cuda.caching_allocator_alloc(int(nbytes)))
+
+
+def _torch_free(ptr, stream, ctx):
+    import torch
+    torch.cuda.caching_allocator_delete(ptr)
+
+
+_ALLOC = ALLOC_FN(_torch_alloc)
+_FREE = FREE_FN(_torch_free)
+
+
+def _check(r, handle=None):
+    if r != 0:
+        msg = ""
+        if handle:
+            m = lib().zema_last_error(handle)
+            msg = m.decode() if m else ""
+        raise ZemaError(r, msg)
+
+
+class Scene:
+    """A scene of the seeded generators loaded into the library."""
+
+    def __init__(self, scene: _scenes.Scene, precision: Optional[int] = None, tol_scale: float = 1.0,
+                 torch_alloc: bool = True, kappa: Optional[float] = None):
+        L = lib()
+        p = scene.params
+        P = Params()
+        L.zema_default_params(C.byref(P))
+        P.dt = p.dt
+        P.dhat = p.dhat
+        P.kappa = p.kappa if kappa is None else kappa
+        P.eps_v = p.eps_v
+        P.newton_tol_rel = p.newton_tol_rel * tol_scale
+        for k in range(3):
+            P.gravity[k] = p.gravity[k]
+        P.pcg_rel_tol = p.pcg_rel_tol
+        P.max_newton = p.max_newton
+        P.max_pcg = p.max_pcg
+        P.max_al_rounds = p.max_al_rounds
+        P.precision = p.precision if precision is None else precision
+        P.n_envs = scene.n_envs
+        P.stream = _stream()
+        if torch_alloc:
+            P.alloc = _ALLOC
+            P.free = _FREE
+        self._P = P
+        h = C.c_void_p()
+        _check(L.zema_create_scene(C.byref(P), C.byref(h)))
+        self.h = h
+        self.scene = scene
+        self.body_ids = []
+        for kind, i in scene.body_order():
+            bid = C.c_int32()
+            if kind == "tet":
+                b = scene.tets[i]
+                X, T, x0, v0 = _d(b.X), _i(b.tets), _d(b.x0), _d(b.v0)
+                r = L.zema_add_tet_body(h, b.env, _dp(X), len(X), _ip(T), len(T), _dp(x0), _dp(v0), b.E, b.nu,
+                                        b.rho, b.mu, C.byref(bid))
+            else:
+                b = scene.affines[i]
+                V, F, q0, qd = _d(b.V), _i(b.F), _d(b.q0), _d(b.qdot0)
+                r = L.zema_add_affine_body(h, b.env, _dp(V), len(V), _ip(F), len(F), _dp(q0), _dp(qd), b.rho,
+                                           b.stiffness, b.mu, b.mode, C.byref(bid))
+            _check(r, h)
+            self.body_ids.append(bid.value)
+        self.n_tet = len(scene.tets)
+        self.step_index = 0
+        _check(L.zema_finalize(h), h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().zema_destroy_scene(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def tet_body_id(self, i):
+        return self.body_ids[i]
+
+    def affine_body_id(self, i):
+        return self.body_ids[self.n_tet + i]
+
+    def apply_script(self):
+        if self.scene.script is None:
+            return
+        for idx, q in self.scene.script(self.step_index).items():
+            qq = _d(q)
+            _check(lib().zema_set_kinematic_target(self.h, self.affine_body_id(idx), _dp(qq)), self.h)
+
+    def step(self, n: int = 1, script: bool = True) -> dict:
+        """Advance n steps (the scene's kinematic script is applied before
+        each); returns the summed statistics of the last call."""
+        st = StepStats()
+        total = None
+        for _ in range(n):
+            if script:
+                self.apply_script()
+            r = lib().zema_step(self.h, 1, C.byref(st))
+            _check(r, self.h)
+            self.step_index += 1
+            d = st.as_dict()
+            if total is None:
+                total = d
+            else:
+                for k in ("steps", "newton_iters", "pcg_iters", "ls_halvings", "al_rounds", "warm_accepted"):
+                    total[k] += d[k]
+                for k in ("max_candidates", "max_active"):
+                    total[k] = max(total[k], d[k])
+                for k in ("dmin", "kappa", "energy"):
+                    total[k] = d[k]
+                for k in total["ms_phase"]:
+                    total["ms_phase"][k] += d["ms_phase"][k]
+        return total or {}
+
+    def step_raw(self, n: int = 1) -> dict:
+        """n steps in one library call (no script)."""
+        st = StepStats()
+        _check(lib().zema_step(self.h, n, C.byref(st)), self.h)
+        self.step_index += n
+        return st.as_dict()
+
+    def get_state(self, body):
+        cap = 1 << 24
+        out = np.zeros(cap)
+        w = C.c_int64()
+        _check(lib().zema_get_state(self.h, body, _dp(out), cap, C.byref(w)), self.h)
+        return out[:w.value].copy()
+
+    def set_state(self, body, arr):
+        a = _d(arr)
+        _check(lib().zema_set_state(self.h, body, _dp(a), len(a)), self.h)
+
+    def tet_positions(self, i=0):
+        st = self.get_state(self.tet_body_id(i))
+        n = len(st) // 6
+        return st[:3 * n].reshape(n, 3)
+
+    def affine_q(self, i):
+        return self.get_state(self.affine_body_id(i))[:12]
+
+    def counts(self):
+        out = np.zeros(8, dtype=np.int64)
+        _check(lib().zema_scene_counts(self.h, out.ctypes.data_as(LP)), self.h)
+        keys = ["n_verts", "n_tets", "n_affine", "n_sv", "n_edges", "n_tris", "n_nodes", "n_envs"]
+        return dict(zip(keys, map(int, out)))
+
+    def kappa(self, env=0):
+        k = C.c_double()
+        _check(lib().zema_get_kappa(self.h, env, C.byref(k)), self.h)
+        return k.value
+
+    def set_kappa(self, env, kappa, kappa_min):
+        _check(lib().zema_set_kappa(self.h, env, kappa, kappa_min), self.h)
+
+    def eval_energy_grad(self, apply_predictor=True, grad=True):
+        """Total incremental potential per env and (optionally) the gradient
+        in the caller's frame, bodies in order of addition."""
+        if apply_predictor:
+            self.apply_script()
+        E = np.zeros(self.scene.n_envs)
+        n = sum(3 * len(b.X) for b in self.scene.tets) + 12 * len(self.scene.affines)
+        g = np.zeros(n) if grad else None
+        _check(lib().zema_eval_energy_grad(self.h, 1 if apply_predictor else 0, _dp(E), _dp(g)), self.h)
+        return E, g
+
+
+# ---------------------------------------------------------------------------
+# stand-alone kernels
+# ---------------------------------------------------------------------------
+def candidates_raw(pos0, sv_body, b_class, b_env, edges, tris, inflate, pos1=None, cell_size=0.0, cap=1 << 22):
+    L = lib()
+    pos0 = _d(pos0)
+    pos1 = _d(pos1)
+    svb, bc, be, E, T = _i(sv_body), _i(b_class), _i(b_env), _i(edges), _i(tris)
+    pt = np.zeros((cap, 2), dtype=np.int32)
+    ee = np.zeros((cap, 2), dtype=np.int32)
+    n = np.zeros(2, dtype=np.int64)
+    _check(L.zema_candidates_raw(len(pos0), _dp(pos0), _dp(pos1), _ip(svb), len(bc), _ip(bc), _ip(be), len(E), _ip(E),
+                                 len(T), _ip(T), inflate, cell_size, cap, _ip(pt), _ip(ee), n.ctypes.data_as(LP),
+                                 _stream()))
+    if n[0] > cap or n[1] > cap:
+        raise ZemaError(1, "candidate capacity exceeded")
+    return pt[:n[0]].copy(), ee[:n[1]].copy()
+
+
+def local_barrier(x12, is_ee, eps_x, dhat):
+    x = _d(np.asarray(x12).reshape(-1, 12))
+    n = len(x)
+    ie = _i(np.broadcast_to(np.asarray(is_ee), (n,)))
+    ep = _d(np.broadcast_to(np.asarray(eps_x, dtype=np.float64), (n,)))
+    E, g, H = np.zeros(n), np.zeros((n, 12)), np.zeros((n, 12, 12))
+    _check(lib().zema_local_barrier(n, _dp(x), _ip(ie), _dp(ep), dhat, _dp(E), _dp(g), _dp(H), _stream()))
+    return E, g, H
+
+
+def local_distance(x12, is_ee):
+    x = _d(np.asarray(x12).reshape(-1, 12))
+    n = len(x)
+    ie = _i(np.broadcast_to(np.asarray(is_ee), (n,)))
+    d2, w = np.zeros(n), np.zeros((n, 4))
+    _check(lib().zema_local_distance(n, _dp(x), _ip(ie), _dp(d2), _dp(w), _stream()))
+    return d2, w
+
+
+def local_neo_hookean(F, mu, lam):
+    F = _d(np.asarray(F).reshape(-1, 9))
+    n = len(F)
+    psi, g, H = np.zeros(n), np.zeros((n, 9)), np.zeros((n, 9, 9))
+    _check(lib().zema_local_neo_hookean(n, _dp(F), mu, lam, _dp(psi), _dp(g), _dp(H), _stream()))
+    return psi, g, H
+
+
+def local_accd(x12, p12, is_ee):
+    x = _d(np.asarray(x12).reshape(-1, 12))
+    p = _d(np.asarray(p12).reshape(-1, 12))
+    n = len(x)
+    ie = _i(np.broadcast_to(np.asarray(is_ee), (n,)))
+    t = np.zeros(n)
+    _check(lib().zema_local_accd(n, _dp(x), _dp(p), _ip(ie), _dp(t), _stream()))
+    return t
