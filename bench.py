@@ -1,0 +1,275 @@
+#!/usr/bin/env python3
+"""Benchmark: IPC time steps per second of the soft-rigid coupled IPC stepper.
+
+Workload: the parallel-jaw grasp scene (seeded synthetic stand-in for the
+paper's grasp objects): a jittered Kuhn-lattice soft ellipsoid (semi-axes
+4/2/3 cm, 9,600 tets, Neo-Hookean E = 5e4 Pa, nu = 0.45) on a fixed floor,
+squeezed and lifted by two kinematic affine box fingers (972 triangles each),
+mu = 0.8, dt = 0.005 s, Newton tolerance 1e-3 x bbox diagonal x dt.  A "step"
+is one full time step of the method (predictor, lagged friction, warm start,
+projected Newton with broad phase, distances, PSD Hessians, assembly, PCG,
+ACCD line search, velocity update).  Timed steps are steps [W, W + K) of the
+grasp script after W warm-up steps.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One JSON line on rank 0.  Under torchrun each rank steps its own replica of
+the workload (environments are independent: weak scaling, no collective in
+the step); the slowest rank's time is used.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "IPC time steps/sec at fixed Newton tol, batched+warm-start vs plain, one B300"
+UNIT = "steps/s"
+WORKLOAD = "parallel-jaw grasp, 1 env: soft ellipsoid 9600 tets + 2 kinematic affine fingers (972 tris each) + fixed floor"
+ROOFLINE_KERNEL = "k_pcg_spmv"
+# DRAM bytes per launch of ROOFLINE_KERNEL from the committed ncu capture
+# (profiles/); None until a capture of the current kernel exists.
+ROOFLINE_TRAFFIC = None
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def build_scene():
+    from paper_2311_05945_b300 import scenes
+    return scenes.scene_c2()
+
+
+def oracle_steps_per_s(n_warm, n_steps):
+    """The CPU oracle, as it stands, on the same workload (single core)."""
+    from oracle.oracle import Oracle
+    sc = build_scene()
+    o = Oracle(sc)
+    if n_warm:
+        o.step(n_warm)
+    t0 = time.perf_counter()
+    o.step(n_steps)
+    dt = time.perf_counter() - t0
+    return n_steps / dt, dt
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    n_warm = min(args.warmup, 1)
+    n_steps = max(1, min(args.steps, 3))
+    v, dt = oracle_steps_per_s(n_warm, n_steps)
+    sample = f"grasp steps [{n_warm}, {n_warm + n_steps}) of the script on the CPU oracle ({dt:.1f} s)"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": n_steps,
+        "warmup": n_warm, "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic (seeded generators)",
+        "config": {"workload": WORKLOAD, "form": "CPU oracle: serial FP64, brute-force pairs, direct/CG solve"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def state_bytes(sc):
+    return sum(8 * 6 * len(b.X) for b in sc.tets) + 8 * 24 * len(sc.affines)
+
+
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+
+    from paper_2311_05945_b300 import zema as Z
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    sc = build_scene()
+    gpu = Z.Scene(sc)
+    st = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        gpu.step(1)
+    torch.cuda.synchronize()
+    # L2 flush buffer: 512 MB, written between timed steps (L2 is 126 MB)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float64, device="cuda")
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stats = []
+    clocks = Clocks(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    if args.profile_region:
+        torch.cuda.profiler.start()
+    Z.profile_kernel(ROOFLINE_KERNEL)
+    l0 = Z.launch_count()
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(st)
+        stats.append(gpu.step(1))
+        ev[k][1].record(st)
+    torch.cuda.synchronize()
+    if args.profile_region:
+        torch.cuda.profiler.stop()
+    launches = Z.launch_count() - l0
+    k_ms, k_launches, k_bytes = Z.profile_read()
+    Z.profile_kernel(None)
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps / (total_ms / 1e3)
+    # end to end through the C ABI with pinned host buffers
+    e2e_steps = max(1, min(args.steps, args.e2e_steps))
+    bodies = list(range(len(sc.body_order())))
+    host = [torch.from_numpy(gpu.get_state(b)).pin_memory() for b in bodies]
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for b in bodies:
+            gpu.set_state_ptr(b, host[b].data_ptr(), host[b].numel())
+        gpu.step(1)
+        for b in bodies:
+            gpu.get_state_ptr(b, host[b].data_ptr(), host[b].numel())
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_val = e2e_steps / e2e_s
+    if dist:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_val = world * e2e_steps / float(t.item())
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    peaks = measured_peaks()
+    peak_gbs = peaks["hbm_gbs"] if peaks else 6400.0
+    roof = None
+    if k_launches:
+        per_launch_bytes = k_bytes / k_launches
+        achieved = per_launch_bytes / (k_ms / k_launches / 1e3) / 1e9
+        roof = {"kernel": ROOFLINE_KERNEL, "bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
+                "frac": achieved / peak_gbs, "traffic": ROOFLINE_TRAFFIC,
+                "peak_source": "measured" if peaks else "fallback",
+                "alg_bytes_per_launch": per_launch_bytes, "avg_launch_us": 1e3 * k_ms / k_launches,
+                "launches": k_launches, "share_of_step_time": k_ms / total_ms if world == 1 else None}
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        v, dt = oracle_steps_per_s(0, args.cpu_steps)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"grasp steps [0, {args.cpu_steps}) of the same script on the CPU oracle ({dt:.1f} s)"}
+    agg = {k: sum(s[k] for s in stats) for k in ("newton_iters", "pcg_iters", "ls_halvings", "al_rounds")}
+    phase = {k: sum(s["ms_phase"][k] for s in stats) for k in stats[0]["ms_phase"]}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic (seeded generators)",
+        "config": {"workload": WORKLOAD, "timed_steps": [args.warmup, args.warmup + args.steps],
+                   "form": "plain FP64 stepper, constant-velocity warm start", "precision": "fp64",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": "flushed between timed steps (512 MB write)",
+                   "newton_iters": agg["newton_iters"], "pcg_iters": agg["pcg_iters"],
+                   "ls_halvings": agg["ls_halvings"], "al_rounds": agg["al_rounds"],
+                   "host_phase_ms": {k: round(v, 2) for k, v in phase.items()}},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": state_bytes(sc),
+                "d2h_bytes_per_step": state_bytes(sc)},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--cpu-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-region", action="store_true",
+                    help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+    else:
+        run_ours(args, rank, world)
+
+
+if __name__ == "__main__":
+    main()

@@ -160,6 +160,21 @@ zema_status zema_get_kappa(const zema_scene* s, int32_t env, double* kappa);
  * gradient-balance rule for it). */
 zema_status zema_set_kappa(zema_scene* s, int32_t env, double kappa, double kappa_min);
 
+/* Number of CUDA kernels the library has launched in this process (all
+ * scenes and entry points); a benchmark reads it before and after a timed
+ * region. */
+long long zema_launch_count(void);
+
+/* Live timing of one kernel for roofline reports: zema_profile_kernel(name)
+ * selects the library kernel (by its function name, e.g. "k_pcg_spmv"; NULL
+ * stops timing) and clears the totals; afterwards every launch of it is
+ * bracketed by CUDA events on the stream it runs on.  zema_profile_read
+ * returns the summed event time (ms), the number of timed launches and the
+ * algorithmic bytes those launches declared (matrix, index and vector traffic
+ * each launch must move at least once).  Synchronises the timed events. */
+int zema_profile_kernel(const char* name);
+int zema_profile_read(double* ms_total, long long* launches, double* alg_bytes);
+
 const char* zema_last_error(const zema_scene* s);
 void zema_destroy_scene(zema_scene* s);
 

@@ -223,12 +223,10 @@ __global__ void k_query(BPView v, int kind, int nq, const double* qbox, const do
         return q < e && ee_ok(v, q, e);
     };
     double nc = box_cells(a, v.inv_cell);
-    if (nc > kMaxCells) {
-        for (int e = 0; e < n_entries_all; ++e) {
-            if (kind == 1 && e <= q) continue;
-            Box6 b = ld_box(ebox_all + 6 * (size_t)e);
-            if (overlap(a, b) && test(e)) emit(e);
-        }
+    if (!(nc <= kMaxCells)) {
+        // oversize query: handled by k_query_big (one block per query)
+        if (!WRITE) cnt[q] = 0;
+        return;
     } else {
         long long c0[3], c1[3];
         for (int k = 0; k < 3; ++k) {
@@ -260,6 +258,52 @@ __global__ void k_query(BPView v, int kind, int nq, const double* qbox, const do
     if (!WRITE) cnt[q] = c;
 }
 
+// Oversize queries (boxes over kMaxCells cells): one block per query; thread
+// t tests the contiguous entry range [t c, (t + 1) c) so that a block scan of
+// the per-thread counts gives each match its position in entry order.
+template <bool WRITE>
+__global__ void k_query_big(BPView v, int kind, const int* qlist, const double* qbox, const double* ebox_all,
+                            int n_entries_all, uint32_t* cnt, const uint32_t* off, int2* out) {
+    __shared__ uint32_t sc[256];
+    int q = qlist[blockIdx.x];
+    Box6 a = ld_box(qbox + 6 * (size_t)q);
+    int chunk = (n_entries_all + blockDim.x - 1) / blockDim.x;
+    int e0 = threadIdx.x * chunk, e1 = min(e0 + chunk, n_entries_all);
+    auto hit = [&](int e) -> bool {
+        if (kind == 1 && e <= q) return false;
+        Box6 b = ld_box(ebox_all + 6 * (size_t)e);
+        if (!overlap(a, b)) return false;
+        return kind == 0 ? pt_ok(v, q, e) : ee_ok(v, q, e);
+    };
+    uint32_t c = 0;
+    for (int e = e0; e < e1; ++e) c += hit(e) ? 1u : 0u;
+    sc[threadIdx.x] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int t = 0; t < (int)blockDim.x; ++t) {
+            uint32_t x = sc[t];
+            sc[t] = run;
+            run += x;
+        }
+        if (!WRITE) cnt[q] = run;
+    }
+    __syncthreads();
+    if (WRITE) {
+        uint32_t o = off[q] + sc[threadIdx.x];
+        for (int e = e0; e < e1; ++e)
+            if (hit(e)) out[o++] = make_int2(q, e);
+    }
+}
+
+// oversize flag of point query boxes
+__global__ void k_point_big(const double* pbox, int n, double inv_cell, uint32_t* flag) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    Box6 a = ld_box(pbox + 6 * (size_t)i);
+    flag[i] = box_cells(a, inv_cell) <= kMaxCells ? 0u : 1u;
+}
+
 static uint64_t pow2_at_least(uint64_t n) {
     uint64_t p = 64;
     while (p < n) p <<= 1;
@@ -271,7 +315,7 @@ BroadPhase::~BroadPhase() {
 }
 
 void BroadPhase::run(Allocator* A, const BPView& v, cudaStream_t st) {
-    if (!h_counts) ZCHECK(cudaMallocHost(&h_counts, 8 * sizeof(uint32_t)));
+    if (!h_counts) ZCHECK(cudaMallocHost(&h_counts, 16 * sizeof(uint32_t)));
     const int TB = 128;
     int nsv = v.nsv, ne = v.ne, nt = v.nt;
     pbox.ensure(A, 6 * (size_t)nsv + 6);
@@ -285,9 +329,9 @@ void BroadPhase::run(Allocator* A, const BPView& v, cudaStream_t st) {
     flagoff.ensure(A, (size_t)nt + ne + 4);
     size_t mx = (size_t)nt + ne + nsv + 16;
     tmp.ensure(A, scan_tmp_size(mx));
-    if (nsv) k_boxes<<<div_up(nsv, TB), TB, 0, st>>>(v, 0, nsv, pbox.p, nullptr, nullptr);
-    if (ne) k_boxes<<<div_up(ne, TB), TB, 0, st>>>(v, 1, ne, ebox.p, ecnt.p, flag.p + nt);
-    if (nt) k_boxes<<<div_up(nt, TB), TB, 0, st>>>(v, 2, nt, tbox.p, tcnt.p, flag.p);
+    if (nsv) ZL(k_boxes, div_up(nsv, TB), TB, 0, st)(v, 0, nsv, pbox.p, nullptr, nullptr);
+    if (ne) ZL(k_boxes, div_up(ne, TB), TB, 0, st)(v, 1, ne, ebox.p, ecnt.p, flag.p + nt);
+    if (nt) ZL(k_boxes, div_up(nt, TB), TB, 0, st)(v, 2, nt, tbox.p, tcnt.p, flag.p);
     ZLAUNCH();
     exclusive_scan(tcnt.p, toff.p, nt, tmp.p, st);
     exclusive_scan(ecnt.p, eoff.p, ne, tmp.p, st);
@@ -301,9 +345,9 @@ void BroadPhase::run(Allocator* A, const BPView& v, cudaStream_t st) {
     uint32_t Et = h_counts[0], Ee = h_counts[1], nbt = h_counts[2], nbe = h_counts[3] - h_counts[2];
     big_t.ensure(A, nbt + 1);
     big_e.ensure(A, nbe + 1);
-    if (nt) k_compact_flags<<<div_up(nt, TB), TB, 0, st>>>(flag.p, flagoff.p, 0u, nt, big_t.p);
+    if (nt) ZL(k_compact_flags, div_up(nt, TB), TB, 0, st)(flag.p, flagoff.p, 0u, nt, big_t.p);
     // edge flag offsets continue after the triangles': subtract their count
-    if (ne) k_compact_flags<<<div_up(ne, TB), TB, 0, st>>>(flag.p + nt, flagoff.p + nt, nbt, ne, big_e.p);
+    if (ne) ZL(k_compact_flags, div_up(ne, TB), TB, 0, st)(flag.p + nt, flagoff.p + nt, nbt, ne, big_e.p);
     ZLAUNCH();
     // grid tables: triangle buckets [0, Tt), edge buckets [Tt, Tt + Te)
     uint64_t Tt = pow2_at_least(2ull * Et + 1), Te = pow2_at_least(2ull * Ee + 1);
@@ -322,16 +366,16 @@ void BroadPhase::run(Allocator* A, const BPView& v, cudaStream_t st) {
     bend.ensure(A, Tt + Te);
     ZCHECK(cudaMemsetAsync(bstart.p, 0, (Tt + Te) * sizeof(uint32_t), st));
     ZCHECK(cudaMemsetAsync(bend.p, 0, (Tt + Te) * sizeof(uint32_t), st));
-    if (nt) k_emit_entries<<<div_up(nt, TB), TB, 0, st>>>(v, nt, tbox.p, toff.p, 0, 0, Tt - 1, key.p, val.p, ctmp, ptmp, 0);
-    if (ne) k_emit_entries<<<div_up(ne, TB), TB, 0, st>>>(v, ne, ebox.p, eoff.p, Et, Tt, Te - 1, key.p, val.p, ctmp, ptmp, 0);
+    if (nt) ZL(k_emit_entries, div_up(nt, TB), TB, 0, st)(v, nt, tbox.p, toff.p, 0, 0, Tt - 1, key.p, val.p, ctmp, ptmp, 0);
+    if (ne) ZL(k_emit_entries, div_up(ne, TB), TB, 0, st)(v, ne, ebox.p, eoff.p, Et, Tt, Te - 1, key.p, val.p, ctmp, ptmp, 0);
     ZLAUNCH();
     if (E) {
         int bits = 1;
         while ((1ull << bits) < Tt + Te) ++bits;
         tmp.ensure(A, std::max(scan_tmp_size(mx), radix_tmp_size(E)));
         radix_sort(key.p, val.p, key2.p, val2.p, E, bits, tmp.p, st);
-        k_gather_entries<<<div_up(E, 256), 256, 0, st>>>(val.p, ctmp, ptmp, cell_tmp.p, eprim.p, (uint32_t)E);
-        k_bucket_ranges<<<div_up(E, 256), 256, 0, st>>>(key.p, (uint32_t)E, bstart.p, bend.p);
+        ZL(k_gather_entries, div_up(E, 256), 256, 0, st)(val.p, ctmp, ptmp, cell_tmp.p, eprim.p, (uint32_t)E);
+        ZL(k_bucket_ranges, div_up(E, 256), 256, 0, st)(key.p, (uint32_t)E, bstart.p, bend.p);
         ZLAUNCH();
     }
     Table TT{cell_tmp.p, eprim.p, bstart.p, bend.p, 0, Tt - 1};
@@ -340,12 +384,27 @@ void BroadPhase::run(Allocator* A, const BPView& v, cudaStream_t st) {
     qoff_pt.ensure(A, nsv + 2);
     qcnt_ee.ensure(A, ne + 1);
     qoff_ee.ensure(A, ne + 2);
+    // oversize point queries (swept boxes of long moves)
+    pflag.ensure(A, nsv + 1);
+    pflagoff.ensure(A, nsv + 2);
+    if (nsv) ZL(k_point_big, div_up(nsv, TB), TB, 0, st)(pbox.p, nsv, v.inv_cell, pflag.p);
+    ZLAUNCH();
+    exclusive_scan(pflag.p, pflagoff.p, nsv, tmp.p, st);
+    ZCHECK(cudaMemcpyAsync(h_counts + 6, pflagoff.p + nsv, 4, cudaMemcpyDeviceToHost, st));
+    ZCHECK(cudaStreamSynchronize(st));
+    uint32_t nbp = h_counts[6];
+    big_p.ensure(A, nbp + 1);
+    if (nsv) ZL(k_compact_flags, div_up(nsv, TB), TB, 0, st)(pflag.p, pflagoff.p, 0u, nsv, big_p.p);
+    ZLAUNCH();
     if (nsv)
-        k_query<false><<<div_up(nsv, TB), TB, 0, st>>>(v, 0, nsv, pbox.p, tbox.p, TT, big_t.p, (int)nbt, nt,
+        ZL(k_query<false>, div_up(nsv, TB), TB, 0, st)(v, 0, nsv, pbox.p, tbox.p, TT, big_t.p, (int)nbt, nt,
                                                        qcnt_pt.p, nullptr, nullptr);
     if (ne)
-        k_query<false><<<div_up(ne, TB), TB, 0, st>>>(v, 1, ne, ebox.p, ebox.p, TE, big_e.p, (int)nbe, ne,
+        ZL(k_query<false>, div_up(ne, TB), TB, 0, st)(v, 1, ne, ebox.p, ebox.p, TE, big_e.p, (int)nbe, ne,
                                                       qcnt_ee.p, nullptr, nullptr);
+    if (nbp) ZL(k_query_big<false>, nbp, 256, 0, st)(v, 0, big_p.p, pbox.p, tbox.p, nt, qcnt_pt.p, nullptr, nullptr);
+    // an oversize edge box is oversize both as an entry and as a query
+    if (nbe) ZL(k_query_big<false>, nbe, 256, 0, st)(v, 1, big_e.p, ebox.p, ebox.p, ne, qcnt_ee.p, nullptr, nullptr);
     ZLAUNCH();
     tmp.ensure(A, std::max(scan_tmp_size(mx), E ? radix_tmp_size(E) : 0));
     exclusive_scan(qcnt_pt.p, qoff_pt.p, nsv, tmp.p, st);
@@ -358,11 +417,13 @@ void BroadPhase::run(Allocator* A, const BPView& v, cudaStream_t st) {
     pt.ensure(A, n_pt + 1);
     ee.ensure(A, n_ee + 1);
     if (nsv && n_pt)
-        k_query<true><<<div_up(nsv, TB), TB, 0, st>>>(v, 0, nsv, pbox.p, tbox.p, TT, big_t.p, (int)nbt, nt, nullptr,
+        ZL(k_query<true>, div_up(nsv, TB), TB, 0, st)(v, 0, nsv, pbox.p, tbox.p, TT, big_t.p, (int)nbt, nt, nullptr,
                                                       qoff_pt.p, pt.p);
     if (ne && n_ee)
-        k_query<true><<<div_up(ne, TB), TB, 0, st>>>(v, 1, ne, ebox.p, ebox.p, TE, big_e.p, (int)nbe, ne, nullptr,
+        ZL(k_query<true>, div_up(ne, TB), TB, 0, st)(v, 1, ne, ebox.p, ebox.p, TE, big_e.p, (int)nbe, ne, nullptr,
                                                      qoff_ee.p, ee.p);
+    if (nbp && n_pt) ZL(k_query_big<true>, nbp, 256, 0, st)(v, 0, big_p.p, pbox.p, tbox.p, nt, nullptr, qoff_pt.p, pt.p);
+    if (nbe && n_ee) ZL(k_query_big<true>, nbe, 256, 0, st)(v, 1, big_e.p, ebox.p, ebox.p, ne, nullptr, qoff_ee.p, ee.p);
     ZLAUNCH();
 }
 

@@ -28,6 +28,21 @@ struct ZemaError {
 
 #define ZLAUNCH() ZCHECK(cudaGetLastError())
 
+// Every kernel launch of the library goes through ZL, which counts it
+// (zema_launch_count reports the total) and, when that kernel is the one
+// selected by zema_profile_kernel, brackets it with CUDA events on the
+// current stream.  A launch site may declare the launch's algorithmic bytes
+// beforehand with alg_bytes_hint().
+long long& launch_counter();
+struct LaunchScope {
+    bool timed;
+    explicit LaunchScope(const char* name);
+    ~LaunchScope();
+};
+void set_current_stream(cudaStream_t st);
+void alg_bytes_hint(double bytes);
+#define ZL(kernel, ...) ::zema::LaunchScope(#kernel), kernel<<<__VA_ARGS__>>>
+
 constexpr int kChunks = 32;   // blocks per environment in segmented reductions
 constexpr int kRedThreads = 256;
 
@@ -97,19 +112,25 @@ __device__ void psd_project(SMat<N> A, SMat<N> V) {
     if (is_pd<N>(A, V)) return;
     for (int i = 0; i < N; ++i)
         for (int j = 0; j < N; ++j) V(i, j) = (i == j) ? 1.0 : 0.0;
-    for (int sweep = 0; sweep < 60; ++sweep) {
+    for (int sweep = 0; sweep < 30; ++sweep) {
         double off = 0.0, diag = 0.0;
         for (int i = 0; i < N; ++i) {
             diag += A(i, i) * A(i, i);
             for (int j = i + 1; j < N; ++j) off += A(i, j) * A(i, j);
         }
-        if (off <= 1e-32 * diag || off == 0.0) break;
+        // off-diagonal mass below (1e-14)^2 of the diagonal: converged to
+        // round-off (cyclic Jacobi converges quadratically; a tighter test
+        // would never be met in FP64)
+        if (off <= 1e-28 * diag) break;
+        bool rotated = false;
         for (int p = 0; p < N - 1; ++p)
             for (int q = p + 1; q < N; ++q) {
                 double apq = A(p, q);
-                if (apq == 0.0) continue;
+                double app = A(p, p), aqq = A(q, q);
+                if (fabs(apq) <= 1e-18 * sqrt(fabs(app * aqq)) || apq == 0.0) continue;
+                rotated = true;
                 // rotation angle that zeroes A(p, q)
-                double tau = (A(q, q) - A(p, p)) / (2.0 * apq);
+                double tau = (aqq - app) / (2.0 * apq);
                 double t = copysign(1.0, tau) / (fabs(tau) + sqrt(1.0 + tau * tau));
                 double c = rsqrt(1.0 + t * t);
                 double s = t * c;
@@ -129,6 +150,7 @@ __device__ void psd_project(SMat<N> A, SMat<N> V) {
                     V(k, q) = s * vkp + c * vkq;
                 }
             }
+        if (!rotated) break;
     }
     // A <- V max(L, 0) V^T ; eigenvalues are on A's diagonal
     double lam[N];

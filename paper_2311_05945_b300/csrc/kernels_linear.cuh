@@ -348,17 +348,42 @@ __global__ void k_pcg_init(Geo G, const double* b, PcgVec V, const double* Minv_
     }
 }
 
-// q = A p over the env's rows and partial p.q
+// q = A p over the env's rows and partial p.q.  One warp per row: lanes
+// stride over the row's blocks and a fixed shuffle tree sums them, so rows
+// with hundreds of contact blocks (affine nodes) do not serialise one thread.
+__device__ __forceinline__ V3 spmv_row_warp(const Bsr& A, int row, const double* p, int lane) {
+    V3 y = v3(0, 0, 0);
+    for (int k = A.rowptr[row] + lane; k < A.rowptr[row + 1]; k += 32) {
+        const double* v = A.val + 9 * (size_t)k;
+        V3 pc = ld3(p + 3 * (size_t)A.col[k]);
+        y.x += v[0] * pc.x + v[1] * pc.y + v[2] * pc.z;
+        y.y += v[3] * pc.x + v[4] * pc.y + v[5] * pc.z;
+        y.z += v[6] * pc.x + v[7] * pc.y + v[8] * pc.z;
+    }
+    return y;
+}
+
 __global__ void k_pcg_spmv(Geo G, Bsr S, Bsr C, PcgVec V, const int* conv, double* part_pq) {
     int env = blockIdx.y;
     __shared__ double sh[32];
     double s = 0.0;
     if (!conv[env]) {
+        int lane = threadIdx.x & 31;
+        int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+        int nwarps = (gridDim.x * blockDim.x) >> 5;
         int n0 = G.env_node_start[env], n1 = G.env_node_start[env + 1];
-        for (int n = n0 + blockIdx.x * blockDim.x + threadIdx.x; n < n1; n += gridDim.x * blockDim.x) {
-            V3 y = spmv_row(S, n, V.p) + spmv_row(C, n, V.p);
-            st3(V.q + 3 * (size_t)n, y);
-            s += dot(y, ld3(V.p + 3 * (size_t)n));
+        for (int n = n0 + warp; n < n1; n += nwarps) {
+            V3 y = spmv_row_warp(S, n, V.p, lane) + spmv_row_warp(C, n, V.p, lane);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                y.x += __shfl_xor_sync(0xffffffffu, y.x, o);
+                y.y += __shfl_xor_sync(0xffffffffu, y.y, o);
+                y.z += __shfl_xor_sync(0xffffffffu, y.z, o);
+            }
+            if (lane == 0) {
+                st3(V.q + 3 * (size_t)n, y);
+                s += dot(y, ld3(V.p + 3 * (size_t)n));
+            }
         }
     }
     double t = block_sum<kRedThreads>(s, sh);

@@ -1,7 +1,97 @@
 // Exclusive scan and stable LSD radix sort (8-bit digits), written for the
 // broad phase and the contact assembly.  Both are deterministic: no atomics
 // decide an output position.
+#include <string>
+#include <vector>
+
 #include "prims.cuh"
+
+namespace zema {
+
+long long& launch_counter() {
+    static long long n = 0;
+    return n;
+}
+
+// --- per-kernel timing (one selected kernel at a time) ---------------------
+namespace {
+struct Prof {
+    std::string name;
+    bool on = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+    size_t used = 0;
+    double bytes = 0.0, pending = 0.0;
+    long long launches = 0;
+};
+Prof& prof() {
+    static Prof p;
+    return p;
+}
+thread_local cudaStream_t g_stream = nullptr;
+}  // namespace
+
+void set_current_stream(cudaStream_t st) { g_stream = st; }
+void alg_bytes_hint(double bytes) { prof().pending = bytes; }
+
+LaunchScope::LaunchScope(const char* name) : timed(false) {
+    ++launch_counter();
+    Prof& P = prof();
+    if (!P.on) return;
+    // match the kernel name, ignoring template arguments
+    const char* a = name;
+    const char* b = P.name.c_str();
+    while (*a && *b && *a == *b) ++a, ++b;
+    if (*b || (*a && *a != '<')) return;
+    if (P.used == P.ev.size()) {
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        P.ev.push_back({e0, e1});
+    }
+    cudaEventRecord(P.ev[P.used].first, g_stream);
+    timed = true;
+}
+
+LaunchScope::~LaunchScope() {
+    if (!timed) return;
+    Prof& P = prof();
+    cudaEventRecord(P.ev[P.used].second, g_stream);
+    ++P.used;
+    ++P.launches;
+    P.bytes += P.pending;
+}
+
+}  // namespace zema
+
+extern "C" {
+// Selects the kernel to time (NULL disables) and clears the totals.
+int zema_profile_kernel(const char* name) {
+    zema::Prof& P = zema::prof();
+    P.on = name != nullptr;
+    P.name = name ? name : "";
+    P.used = 0;
+    P.bytes = 0.0;
+    P.pending = 0.0;
+    P.launches = 0;
+    return 0;
+}
+
+// Totals since zema_profile_kernel: summed event time of the selected
+// kernel's launches, their count and their declared algorithmic bytes.
+int zema_profile_read(double* ms_total, long long* launches, double* alg_bytes) {
+    zema::Prof& P = zema::prof();
+    double ms = 0.0;
+    for (size_t i = 0; i < P.used; ++i) {
+        cudaEventSynchronize(P.ev[i].second);
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, P.ev[i].first, P.ev[i].second) == cudaSuccess) ms += t;
+    }
+    if (ms_total) *ms_total = ms;
+    if (launches) *launches = P.launches;
+    if (alg_bytes) *alg_bytes = P.bytes;
+    return 0;
+}
+}
 
 namespace zema {
 
@@ -83,18 +173,18 @@ static void scan_rec(const uint32_t* in, uint32_t* out, size_t n, uint32_t* tmp,
     size_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
     uint32_t* sums = tmp;
     uint32_t* soff = tmp + nb + 1;
-    k_scan_block<<<(unsigned)nb, SCAN_T, 0, st>>>(in, out, n, sums);
+    ZL(k_scan_block, (unsigned)nb, SCAN_T, 0, st)(in, out, n, sums);
     ZLAUNCH();
     if (nb > 1) {
         scan_rec(sums, soff, nb, tmp + 2 * nb + 2, st);
-        k_scan_add<<<(unsigned)nb, SCAN_T, 0, st>>>(out, n, soff);
+        ZL(k_scan_add, (unsigned)nb, SCAN_T, 0, st)(out, n, soff);
         ZLAUNCH();
     }
 }
 
 void exclusive_scan(const uint32_t* in, uint32_t* out, size_t n, uint32_t* tmp, cudaStream_t st) {
     scan_rec(in, out, n, tmp, st);
-    k_set_total<<<1, 1, 0, st>>>(out, n, in, nullptr, 0);
+    ZL(k_set_total, 1, 1, 0, st)(out, n, in, nullptr, 0);
     ZLAUNCH();
 }
 
@@ -182,10 +272,10 @@ void radix_sort(uint64_t* keys, uint32_t* vals, uint64_t* k2, uint32_t* v2, size
     uint32_t *va = vals, *vb = v2;
     for (int p = 0; p < passes; ++p) {
         int shift = 8 * p;
-        k_rs_hist<<<ntiles, RS_T, 0, st>>>(ka, n, shift, hist, ntiles);
+        ZL(k_rs_hist, ntiles, RS_T, 0, st)(ka, n, shift, hist, ntiles);
         ZLAUNCH();
         exclusive_scan(hist, offs, h, stmp, st);
-        k_rs_scatter<<<ntiles, RS_T, 0, st>>>(ka, va, kb, vb, n, shift, offs, ntiles);
+        ZL(k_rs_scatter, ntiles, RS_T, 0, st)(ka, va, kb, vb, n, shift, offs, ntiles);
         ZLAUNCH();
         std::swap(ka, kb);
         std::swap(va, vb);

@@ -535,9 +535,9 @@ void build(zema_scene* s) {
     DBuf<int> bad;
     bad.ensure(A, 1);
     ZCHECK(cudaMemsetAsync(bad.p, 0, sizeof(int), st));
-    if (s->n_tets) k_tet_rest<<<div_up(s->n_tets, TB), TB, 0, st>>>(xrest_d.p, s->tets.p, s->n_tets, s->Dminv.p, s->tvol.p, bad.p);
+    if (s->n_tets) ZL(k_tet_rest, div_up(s->n_tets, TB), TB, 0, st)(xrest_d.p, s->tets.p, s->n_tets, s->Dminv.p, s->tvol.p, bad.p);
     ZLAUNCH();
-    k_lumped_mass<<<div_up(nN, TB), TB, 0, st>>>(s->node_tet_ptr.p, s->node_tet_idx.p, s->tvol.p, trho_d.p, nN, s->node_mass.p);
+    ZL(k_lumped_mass, div_up(nN, TB), TB, 0, st)(s->node_tet_ptr.p, s->node_tet_idx.p, s->tvol.p, trho_d.p, nN, s->node_mass.p);
     ZLAUNCH();
     // affine mass properties
     std::vector<double> Vall;
@@ -561,7 +561,7 @@ void build(zema_scene* s) {
         up(s, vod, voff);
         up(s, rhod, arho);
         mpd.ensure(A, mp.size());
-        k_affine_mass<<<s->n_aff, kRedThreads, 0, st>>>(Vd.p, Fd.p, fpd.p, vod.p, rhod.p, s->n_aff, mpd.p);
+        ZL(k_affine_mass, s->n_aff, kRedThreads, 0, st)(Vd.p, Fd.p, fpd.p, vod.p, rhod.p, s->n_aff, mpd.p);
         ZLAUNCH();
         ZCHECK(cudaMemcpyAsync(mp.data(), mpd.p, mp.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
     }
@@ -773,11 +773,11 @@ uint32_t candidates(zema_scene* s, const double* X0, const double* X1, DBuf<Pair
     uint32_t n = s->bp.n_pt + s->bp.n_ee;
     out.ensure(&s->A, n + 1);
     int NE = s->n_envs;
-    k_pair_env_offsets<<<div_up(NE + 1, 64), 64, 0, st>>>(s->G, s->bp.qoff_pt.p, s->bp.qoff_ee.p, s->pt_env.p,
+    ZL(k_pair_env_offsets, div_up(NE + 1, 64), 64, 0, st)(s->G, s->bp.qoff_pt.p, s->bp.qoff_ee.p, s->pt_env.p,
                                                           s->ee_env.p, env_off.p);
     ZLAUNCH();
     if (n)
-        k_merge_pairs<<<div_up(n, TB), TB, 0, st>>>(s->G, s->bp.pt.p, s->bp.ee.p, s->pt_env.p, s->ee_env.p, env_off.p,
+        ZL(k_merge_pairs, div_up(n, TB), TB, 0, st)(s->G, s->bp.pt.p, s->bp.ee.p, s->pt_env.p, s->ee_env.p, env_off.p,
                                                    (int)n, out.p);
     ZLAUNCH();
     s->S.max_candidates = std::max<int64_t>(s->S.max_candidates, n);
@@ -797,17 +797,17 @@ uint32_t active_pairs(zema_scene* s, const double* X, bool want_dmin) {
     s->flagoff.ensure(&s->A, n + 2);
     s->tmp32.ensure(&s->A, scan_tmp_size(n + 1));
     if (n)
-        k_active_flags<<<div_up(n, TB), TB, 0, st>>>(s->G, X, s->cand.p, (int)n, s->flag.p,
+        ZL(k_active_flags, div_up(n, TB), TB, 0, st)(s->G, X, s->cand.p, (int)n, s->flag.p,
                                                     want_dmin ? s->dmin.p : nullptr);
     ZLAUNCH();
     exclusive_scan(s->flag.p, s->flagoff.p, n, s->tmp32.p, st);
     ZCHECK(cudaMemcpyAsync(s->h32, s->flagoff.p + n, 4, cudaMemcpyDeviceToHost, st));
-    k_env_gather<<<div_up(NE + 1, 64), 64, 0, st>>>(s->flagoff.p, s->m_env.p, NE, s->act_env.p);
+    ZL(k_env_gather, div_up(NE + 1, 64), 64, 0, st)(s->flagoff.p, s->m_env.p, NE, s->act_env.p);
     ZLAUNCH();
     ZCHECK(cudaStreamSynchronize(st));
     uint32_t na = s->h32[0];
     s->act.ensure(&s->A, na + 1);
-    if (n) k_compact_pairs<<<div_up(n, TB), TB, 0, st>>>(s->cand.p, s->flag.p, s->flagoff.p, (int)n, s->act.p);
+    if (n) ZL(k_compact_pairs, div_up(n, TB), TB, 0, st)(s->cand.p, s->flag.p, s->flagoff.p, (int)n, s->act.p);
     ZLAUNCH();
     s->n_act = na;
     s->S.max_active = std::max<int64_t>(s->S.max_active, na);
@@ -830,14 +830,14 @@ void energy(zema_scene* s, const double* xe, const PairRec* pairs, const uint32_
     cudaStream_t st = s->st;
     int NE = s->n_envs;
     ZCHECK(cudaMemsetAsync(s->part.p, 0, (size_t)ET_COUNT * NE * kChunks * sizeof(double), st));
-    k_sv_pos<<<div_up(s->n_sv, TB), TB, 0, st>>>(s->G, xe, s->X1.p);
-    k_soft_energy<<<red_grid(NE), kRedThreads, 0, st>>>(s->G, xe, s->xhat.p, s->part.p);
-    k_affine_energy<<<red_grid(NE), kRedThreads, 0, st>>>(s->G, xe, s->xhat.p, kin(s), s->part.p);
+    ZL(k_sv_pos, div_up(s->n_sv, TB), TB, 0, st)(s->G, xe, s->X1.p);
+    ZL(k_soft_energy, red_grid(NE), kRedThreads, 0, st)(s->G, xe, s->xhat.p, s->part.p);
+    ZL(k_affine_energy, red_grid(NE), kRedThreads, 0, st)(s->G, xe, s->xhat.p, kin(s), s->part.p);
     if (barrier && pairs)
-        k_barrier_energy<<<red_grid(NE), kRedThreads, 0, st>>>(s->G, s->X1.p, pairs, poff, s->kappa.p, s->part.p);
+        ZL(k_barrier_energy, red_grid(NE), kRedThreads, 0, st)(s->G, s->X1.p, pairs, poff, s->kappa.p, s->part.p);
     if (friction && s->n_lag)
-        k_friction_energy<<<red_grid(NE), kRedThreads, 0, st>>>(s->G, s->X1.p, s->Xt.p, lagv(s), s->part.p);
-    k_energy_total<<<div_up(NE, 64), 64, 0, st>>>(s->part.p, ET_COUNT, NE, s->E.p);
+        ZL(k_friction_energy, red_grid(NE), kRedThreads, 0, st)(s->G, s->X1.p, s->Xt.p, lagv(s), s->part.p);
+    ZL(k_energy_total, div_up(NE, 64), 64, 0, st)(s->part.p, ET_COUNT, NE, s->E.p);
     ZLAUNCH();
     ZCHECK(cudaMemcpyAsync(s->hd, s->E.p, NE * sizeof(double), cudaMemcpyDeviceToHost, st));
     ZCHECK(cudaStreamSynchronize(st));
@@ -850,19 +850,22 @@ void grad_hess(zema_scene* s, bool barrier = true, bool friction = true, bool he
     cudaStream_t st = s->st;
     Geo& G = s->G;
     Allocator* A = &s->A;
+    // per tet: indices 16 B, Dm^-1 72 B, volume and Lame 24 B, positions 96 B
+    // in; 16 blocks 1152 B and gradient 96 B out
+    alg_bytes_hint(1456.0 * s->n_tets);
     if (s->n_tets)
-        k_elastic_gh<<<div_up(s->n_tets, EL_T), EL_T, 2 * 81 * EL_T * 8, st>>>(G, s->x.p, s->stage_blk.p, s->stage_g.p);
+        ZL(k_elastic_gh, div_up(s->n_tets, EL_T), EL_T, 2 * 81 * EL_T * 8, st)(G, s->x.p, s->stage_blk.p, s->stage_g.p);
     ZLAUNCH();
     ZCHECK(cudaMemsetAsync(s->g.p, 0, 3 * (size_t)s->n_nodes * sizeof(double), st));
     if (s->n_aff)
-        k_affine_gh<<<div_up(s->n_aff, AF_T), AF_T, 2 * 81 * AF_T * 8, st>>>(
+        ZL(k_affine_gh, div_up(s->n_aff, AF_T), AF_T, 2 * 81 * AF_T * 8, st)(
             G, s->x.p, s->xhat.p, kin(s), s->stage_blk.p + 144 * (size_t)s->n_tets, s->g.p);
     ZLAUNCH();
-    k_soft_grad<<<div_up(s->n_nodes, TB), TB, 0, st>>>(G, s->x.p, s->xhat.p, s->stage_g.p, s->g.p);
+    ZL(k_soft_grad, div_up(s->n_nodes, TB), TB, 0, st)(G, s->x.p, s->xhat.p, s->stage_g.p, s->g.p);
     ZLAUNCH();
     if (hess) {
-        k_static_values<<<div_up(s->n_sblocks, TB), TB, 0, st>>>(G, s->n_sblocks, s->stage_blk.p, s->S_val.p);
-        k_static_diag<<<div_up(s->n_nodes, TB), TB, 0, st>>>(G, s->S_diag.p, s->S_val.p);
+        ZL(k_static_values, div_up(s->n_sblocks, TB), TB, 0, st)(G, s->n_sblocks, s->stage_blk.p, s->S_val.p);
+        ZL(k_static_diag, div_up(s->n_nodes, TB), TB, 0, st)(G, s->S_diag.p, s->S_val.p);
         ZLAUNCH();
     }
     // contact records: active barrier pairs then lagged friction pairs
@@ -871,10 +874,10 @@ void grad_hess(zema_scene* s, bool barrier = true, bool friction = true, bool he
     s->pH.ensure(A, 144 * (size_t)nr + 144);
     s->pG.ensure(A, 12 * (size_t)nr + 12);
     if (na)
-        k_barrier_gh<<<div_up(na, BR_T), BR_T, 2 * 144 * BR_T * 8, st>>>(G, s->X.p, s->act.p, (int)na, s->kappa.p,
+        ZL(k_barrier_gh, div_up(na, BR_T), BR_T, 2 * 144 * BR_T * 8, st)(G, s->X.p, s->act.p, (int)na, s->kappa.p,
                                                                           s->pH.p, s->pG.p);
     if (nl)
-        k_friction_gh<<<div_up(nl, 128), 128, 0, st>>>(G, s->X.p, s->Xt.p, lagv(s), s->pH.p + 144 * (size_t)na,
+        ZL(k_friction_gh, div_up(nl, 128), 128, 0, st)(G, s->X.p, s->Xt.p, lagv(s), s->pH.p + 144 * (size_t)na,
                                                         s->pG.p + 12 * (size_t)na);
     ZLAUNCH();
     // one record list: act then lag
@@ -894,7 +897,7 @@ void grad_hess(zema_scene* s, bool barrier = true, bool friction = true, bool he
     s->off_blk.ensure(A, nr + 2);
     s->cnt_g.ensure(A, nr + 1);
     s->off_g.ensure(A, nr + 2);
-    k_contact_count<<<div_up(nr, TB), TB, 0, st>>>(G, recs.p, (int)nr, s->cnt_blk.p, s->cnt_g.p);
+    ZL(k_contact_count, div_up(nr, TB), TB, 0, st)(G, recs.p, (int)nr, s->cnt_blk.p, s->cnt_g.p);
     ZLAUNCH();
     s->tmp32.ensure(A, scan_tmp_size(nr + 1));
     exclusive_scan(s->cnt_blk.p, s->off_blk.p, nr, s->tmp32.p, st);
@@ -913,7 +916,7 @@ void grad_hess(zema_scene* s, bool barrier = true, bool friction = true, bool he
     s->gval.ensure(A, ng + 1);
     s->gval2.ensure(A, ng + 1);
     s->gstage.ensure(A, 3 * (size_t)ng + 3);
-    k_contact_emit<<<div_up(nr, 128), 128, 0, st>>>(G, recs.p, (int)nr, s->pH.p, s->pG.p, s->off_blk.p, s->off_g.p,
+    ZL(k_contact_emit, div_up(nr, 128), 128, 0, st)(G, recs.p, (int)nr, s->pH.p, s->pG.p, s->off_blk.p, s->off_g.p,
                                                      s->bkey.p, s->bval.p, s->bstage.p, s->gkey.p, s->gval.p,
                                                      s->gstage.p);
     ZLAUNCH();
@@ -928,28 +931,28 @@ void grad_hess(zema_scene* s, bool barrier = true, bool friction = true, bool he
     s->hoff.ensure(A, mx + 1);
     s->seg.ensure(A, mx + 1);
     s->ukey.ensure(A, mx);
-    k_heads<<<div_up(nb, TB), TB, 0, st>>>(s->bkey.p, nb, s->head.p);
+    ZL(k_heads, div_up(nb, TB), TB, 0, st)(s->bkey.p, nb, s->head.p);
     exclusive_scan(s->head.p, s->hoff.p, nb, s->tmp32.p, st);
-    k_seg_starts<<<div_up(nb + 1, TB), TB, 0, st>>>(s->head.p, s->hoff.p, nb, s->seg.p);
+    ZL(k_seg_starts, div_up(nb + 1, TB), TB, 0, st)(s->head.p, s->hoff.p, nb, s->seg.p);
     ZCHECK(cudaMemcpyAsync(s->h32 + 2, s->hoff.p + nb, 4, cudaMemcpyDeviceToHost, st));
     ZCHECK(cudaStreamSynchronize(st));
     uint32_t nu = s->h32[2];
     s->C_val.ensure(A, 9 * (size_t)nu + 9);
     s->C_col.ensure(A, nu + 1);
-    k_seg_sum<9><<<div_up(nu, 128), 128, 0, st>>>(s->seg.p, nu, s->bval.p, s->bstage.p, s->C_val.p, s->bkey.p, s->ukey.p);
-    k_contact_rows<<<div_up(s->n_nodes + 1, TB), TB, 0, st>>>(s->ukey.p, nu, s->n_nodes, s->C_rowptr.p, s->C_col.p);
+    ZL(k_seg_sum<9>, div_up(nu, 128), 128, 0, st)(s->seg.p, nu, s->bval.p, s->bstage.p, s->C_val.p, s->bkey.p, s->ukey.p);
+    ZL(k_contact_rows, div_up(s->n_nodes + 1, TB), TB, 0, st)(s->ukey.p, nu, s->n_nodes, s->C_rowptr.p, s->C_col.p);
     ZLAUNCH();
     s->n_cblocks = nu;
     // unique gradient nodes
-    k_heads<<<div_up(ng, TB), TB, 0, st>>>(s->gkey.p, ng, s->head.p);
+    ZL(k_heads, div_up(ng, TB), TB, 0, st)(s->gkey.p, ng, s->head.p);
     exclusive_scan(s->head.p, s->hoff.p, ng, s->tmp32.p, st);
-    k_seg_starts<<<div_up(ng + 1, TB), TB, 0, st>>>(s->head.p, s->hoff.p, ng, s->seg.p);
+    ZL(k_seg_starts, div_up(ng + 1, TB), TB, 0, st)(s->head.p, s->hoff.p, ng, s->seg.p);
     ZCHECK(cudaMemcpyAsync(s->h32 + 3, s->hoff.p + ng, 4, cudaMemcpyDeviceToHost, st));
     ZCHECK(cudaStreamSynchronize(st));
     uint32_t nug = s->h32[3];
     s->gsum.ensure(A, 3 * (size_t)nug + 3);
-    k_seg_sum<3><<<div_up(nug, 128), 128, 0, st>>>(s->seg.p, nug, s->gval.p, s->gstage.p, s->gsum.p, s->gkey.p, s->ukey.p);
-    k_add_contact_grad<<<div_up(nug, 128), 128, 0, st>>>(s->ukey.p, s->gsum.p, nug, s->g.p);
+    ZL(k_seg_sum<3>, div_up(nug, 128), 128, 0, st)(s->seg.p, nug, s->gval.p, s->gstage.p, s->gsum.p, s->gkey.p, s->ukey.p);
+    ZL(k_add_contact_grad, div_up(nug, 128), 128, 0, st)(s->ukey.p, s->gsum.p, nug, s->g.p);
     ZLAUNCH();
 }
 
@@ -962,8 +965,8 @@ int64_t pcg(zema_scene* s, const std::vector<int>& done_h) {
     int NE = s->n_envs;
     Bsr S{s->S_rowptr.p, s->S_col.p, s->S_val.p};
     Bsr C{s->C_rowptr.p, s->C_col.p, s->C_val.p};
-    k_precond<<<div_up(s->n_units, 128), 128, 0, st>>>(G, S, C, s->Minv_s.p, s->Minv_a.p);
-    k_negate<<<div_up(3 * (size_t)s->n_nodes, TB), TB, 0, st>>>(s->g.p, s->b.p, 3 * (size_t)s->n_nodes);
+    ZL(k_precond, div_up(s->n_units, 128), 128, 0, st)(G, S, C, s->Minv_s.p, s->Minv_a.p);
+    ZL(k_negate, div_up(3 * (size_t)s->n_nodes, TB), TB, 0, st)(s->g.p, s->b.p, 3 * (size_t)s->n_nodes);
     ZLAUNCH();
     for (int e = 0; e < NE; ++e) s->hi[e] = done_h[e];
     ZCHECK(cudaMemcpyAsync(s->conv.p, s->hi, NE * sizeof(int), cudaMemcpyHostToDevice, st));
@@ -974,17 +977,22 @@ int64_t pcg(zema_scene* s, const std::vector<int>& done_h) {
     double* pq = s->part4.p;
     double* rr = s->part5.p;
     double* bb = s->part6.p;
-    k_pcg_init<<<red_grid(NE), kRedThreads, 0, st>>>(G, s->b.p, V, s->Minv_s.p, s->Minv_a.p, rz_a, bb);
+    ZL(k_pcg_init, red_grid(NE), kRedThreads, 0, st)(G, s->b.p, V, s->Minv_s.p, s->Minv_a.p, rz_a, bb);
     ZLAUNCH();
     double tol2 = s->P.pcg_rel_tol * s->P.pcg_rel_tol;
     int it = 0;
     const int check = 8;
     while (it < s->P.max_pcg) {
+        // algorithmic bytes of one SpMV: every block (72 B values + 4 B column)
+        // and both row-pointer arrays once, p read and q written once
+        double spmv_bytes = 76.0 * ((double)s->n_sblocks + (double)s->n_cblocks) + 8.0 * (s->n_nodes + 1) +
+                            48.0 * s->n_nodes;
         for (int k = 0; k < check; ++k) {
-            k_pcg_spmv<<<red_grid(NE), kRedThreads, 0, st>>>(G, S, C, V, s->conv.p, pq);
-            k_pcg_update<<<red_grid(NE), kRedThreads, 0, st>>>(G, V, s->Minv_s.p, s->Minv_a.p, s->conv.p, rz_a, pq,
+            alg_bytes_hint(spmv_bytes);
+            ZL(k_pcg_spmv, red_grid(NE), kRedThreads, 0, st)(G, S, C, V, s->conv.p, pq);
+            ZL(k_pcg_update, red_grid(NE), kRedThreads, 0, st)(G, V, s->Minv_s.p, s->Minv_a.p, s->conv.p, rz_a, pq,
                                                                rz_b, rr);
-            k_pcg_dir<<<red_grid(NE), kRedThreads, 0, st>>>(G, V, s->conv.p, s->pcg_iters.p, rz_a, rz_b, rr, bb, tol2);
+            ZL(k_pcg_dir, red_grid(NE), kRedThreads, 0, st)(G, V, s->conv.p, s->pcg_iters.p, rz_a, rz_b, rr, bb, tol2);
             std::swap(rz_a, rz_b);
             ++it;
         }
@@ -1002,7 +1010,7 @@ int64_t pcg(zema_scene* s, const std::vector<int>& done_h) {
     // done envs: zero direction
     for (int e = 0; e < NE; ++e) s->hi[e] = done_h[e];
     ZCHECK(cudaMemcpyAsync(s->need.p, s->hi, NE * sizeof(int), cudaMemcpyHostToDevice, st));
-    k_mask_env<<<div_up(s->n_nodes, TB), TB, 0, st>>>(G, s->p.p, s->need.p);
+    ZL(k_mask_env, div_up(s->n_nodes, TB), TB, 0, st)(G, s->p.p, s->need.p);
     ZLAUNCH();
     return tot;
 }
@@ -1011,8 +1019,8 @@ int64_t pcg(zema_scene* s, const std::vector<int>& done_h) {
 void step_norm(zema_scene* s) {
     cudaStream_t st = s->st;
     int NE = s->n_envs;
-    k_step_norm<<<red_grid(NE), kRedThreads, 0, st>>>(s->G, s->p.p, s->part7.p);
-    k_max_total<<<div_up(NE, 64), 64, 0, st>>>(s->part7.p, NE, s->E.p);
+    ZL(k_step_norm, red_grid(NE), kRedThreads, 0, st)(s->G, s->p.p, s->part7.p);
+    ZL(k_max_total, div_up(NE, 64), 64, 0, st)(s->part7.p, NE, s->E.p);
     ZLAUNCH();
     ZCHECK(cudaMemcpyAsync(s->hd, s->E.p, NE * sizeof(double), cudaMemcpyDeviceToHost, st));
     ZCHECK(cudaStreamSynchronize(st));
@@ -1031,11 +1039,11 @@ int line_search(zema_scene* s, const double* dir, const std::vector<int>& done_h
     int NE = s->n_envs;
     double t0 = now_ms();
     // swept candidates X(x) -> X(x + dir)
-    k_sv_pos<<<div_up(s->n_sv, TB), TB, 0, st>>>(G, s->x.p, s->X.p);
+    ZL(k_sv_pos, div_up(s->n_sv, TB), TB, 0, st)(G, s->x.p, s->X.p);
     std::vector<double> one(NE, 1.0);
     ZCHECK(cudaMemcpyAsync(s->alpha.p, one.data(), NE * sizeof(double), cudaMemcpyHostToDevice, st));
-    k_axpy_env<<<div_up(s->n_nodes, TB), TB, 0, st>>>(G, s->x.p, dir, s->alpha.p, s->xtrial.p);
-    k_sv_pos<<<div_up(s->n_sv, TB), TB, 0, st>>>(G, s->xtrial.p, s->X1.p);
+    ZL(k_axpy_env, div_up(s->n_nodes, TB), TB, 0, st)(G, s->x.p, dir, s->alpha.p, s->xtrial.p);
+    ZL(k_sv_pos, div_up(s->n_sv, TB), TB, 0, st)(G, s->xtrial.p, s->X1.p);
     ZLAUNCH();
     // X1 is overwritten by energy(); keep the swept end positions in q (scratch)
     s->q.ensure(&s->A, std::max<size_t>(3 * (size_t)s->n_nodes + 3, 3 * (size_t)s->n_sv + 3));
@@ -1043,7 +1051,7 @@ int line_search(zema_scene* s, const double* dir, const std::vector<int>& done_h
     uint32_t ns = candidates(s, s->X.p, s->q.p, s->swept, s->swept_env);
     s->n_swept = ns;
     ZCHECK(cudaMemsetAsync(s->capflag.p, 0, sizeof(int), st));
-    if (ns) k_accd<<<div_up(ns, 128), 128, 0, st>>>(G, s->X.p, s->q.p, s->swept.p, (int)ns, s->alpha.p, s->capflag.p);
+    if (ns) ZL(k_accd, div_up(ns, 128), 128, 0, st)(G, s->X.p, s->q.p, s->swept.p, (int)ns, s->alpha.p, s->capflag.p);
     ZLAUNCH();
     std::vector<double> alpha(NE);
     ZCHECK(cudaMemcpyAsync(alpha.data(), s->alpha.p, NE * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -1062,7 +1070,7 @@ int line_search(zema_scene* s, const double* dir, const std::vector<int>& done_h
     bool fail_ls = false;
     for (int k = 0; k <= max_halvings; ++k) {
         ZCHECK(cudaMemcpyAsync(s->alpha.p, alpha.data(), NE * sizeof(double), cudaMemcpyHostToDevice, st));
-        k_axpy_env<<<div_up(s->n_nodes, TB), TB, 0, st>>>(G, s->x.p, dir, s->alpha.p, s->xtrial.p);
+        ZL(k_axpy_env, div_up(s->n_nodes, TB), TB, 0, st)(G, s->x.p, dir, s->alpha.p, s->xtrial.p);
         ZLAUNCH();
         energy(s, s->xtrial.p, s->swept.p, s->swept_env.p);
         bool all = true;
@@ -1090,7 +1098,7 @@ int line_search(zema_scene* s, const double* dir, const std::vector<int>& done_h
         if (!acc[e]) alpha[e] = 0.0;
     if (accepted) *accepted = acc;
     ZCHECK(cudaMemcpyAsync(s->alpha.p, alpha.data(), NE * sizeof(double), cudaMemcpyHostToDevice, st));
-    k_axpy_env<<<div_up(s->n_nodes, TB), TB, 0, st>>>(G, s->x.p, dir, s->alpha.p, s->xtrial.p);
+    ZL(k_axpy_env, div_up(s->n_nodes, TB), TB, 0, st)(G, s->x.p, dir, s->alpha.p, s->xtrial.p);
     ZLAUNCH();
     ZCHECK(cudaMemcpyAsync(s->x.p, s->xtrial.p, 3 * (size_t)s->n_nodes * sizeof(double), cudaMemcpyDeviceToDevice, st));
     s->S.ms_phase[1] += now_ms() - t0;
@@ -1100,7 +1108,7 @@ int line_search(zema_scene* s, const double* dir, const std::vector<int>& done_h
 // lag friction at the current x (= x^t): records, weights, normals, mu lambda
 void lag_friction(zema_scene* s) {
     cudaStream_t st = s->st;
-    k_sv_pos<<<div_up(s->n_sv, TB), TB, 0, st>>>(s->G, s->x.p, s->Xt.p);
+    ZL(k_sv_pos, div_up(s->n_sv, TB), TB, 0, st)(s->G, s->x.p, s->Xt.p);
     ZLAUNCH();
     uint32_t na = active_pairs(s, s->Xt.p, false);
     s->lag.ensure(&s->A, na + 1);
@@ -1109,7 +1117,7 @@ void lag_friction(zema_scene* s) {
     s->lag_c.ensure(&s->A, na + 1);
     if (na) {
         ZCHECK(cudaMemcpyAsync(s->lag.p, s->act.p, na * sizeof(PairRec), cudaMemcpyDeviceToDevice, st));
-        k_lag_friction<<<div_up(na, 128), 128, 0, st>>>(s->G, s->Xt.p, s->lag.p, (int)na, s->kappa.p, s->lag_w.p,
+        ZL(k_lag_friction, div_up(na, 128), 128, 0, st)(s->G, s->Xt.p, s->lag.p, (int)na, s->kappa.p, s->lag_w.p,
                                                          s->lag_n.p, s->lag_c.p);
         ZLAUNCH();
     }
@@ -1156,17 +1164,17 @@ void init_kappa(zema_scene* s) {
     ZCHECK(cudaMemcpyAsync(kmin_cur.data(), s->kappa_min.p, NE * sizeof(double), cudaMemcpyDeviceToHost, st));
     std::vector<double> one(NE, 1.0);
     ZCHECK(cudaMemcpyAsync(s->kappa.p, one.data(), NE * sizeof(double), cudaMemcpyHostToDevice, st));
-    k_sv_pos<<<div_up(s->n_sv, TB), TB, 0, st>>>(s->G, s->x.p, s->X.p);
+    ZL(k_sv_pos, div_up(s->n_sv, TB), TB, 0, st)(s->G, s->x.p, s->X.p);
     ZLAUNCH();
     active_pairs(s, s->X.p, false);
     uint32_t keep_lag = s->n_lag;
     s->n_lag = 0;
     size_t n3 = 3 * (size_t)s->n_nodes;
     grad_hess(s, false, false, false);
-    k_affine_grad_to_row<<<div_up(s->n_aff + 1, 64), 64, 0, st>>>(s->G, s->g.p);
+    ZL(k_affine_grad_to_row, div_up(s->n_aff + 1, 64), 64, 0, st)(s->G, s->g.p);
     ZCHECK(cudaMemcpyAsync(s->r.p, s->g.p, n3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
     grad_hess(s, true, false, false);
-    k_affine_grad_to_row<<<div_up(s->n_aff + 1, 64), 64, 0, st>>>(s->G, s->g.p);
+    ZL(k_affine_grad_to_row, div_up(s->n_aff + 1, 64), 64, 0, st)(s->G, s->g.p);
     ZLAUNCH();
     s->n_lag = keep_lag;
     std::vector<double> ga(n3), ge(n3);
@@ -1175,7 +1183,7 @@ void init_kappa(zema_scene* s) {
     ZCHECK(cudaStreamSynchronize(st));
     for (size_t i = 0; i < n3; ++i) ga[i] -= ge[i];
     ZCHECK(cudaMemcpyAsync(s->z.p, ga.data(), n3 * sizeof(double), cudaMemcpyHostToDevice, st));
-    k_env_dot2<<<red_grid(NE), kRedThreads, 0, st>>>(s->G, s->r.p, s->z.p, s->part2.p, s->part3.p);
+    ZL(k_env_dot2, red_grid(NE), kRedThreads, 0, st)(s->G, s->r.p, s->z.p, s->part2.p, s->part3.p);
     ZLAUNCH();
     std::vector<double> pab((size_t)NE * kChunks), pbb((size_t)NE * kChunks);
     ZCHECK(cudaMemcpyAsync(pab.data(), s->part2.p, pab.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -1223,8 +1231,8 @@ void do_step(zema_scene* s) {
                                cudaMemcpyDeviceToDevice, st));
     // predictor (Eq. 1-3)
     const double* gr = s->P.gravity;
-    k_predict<<<div_up(s->n_nodes, TB), TB, 0, st>>>(G, s->x.p, s->v.p, s->xt.p, s->xhat.p, gr[0], gr[1], gr[2]);
-    if (s->n_aff) k_predict_affine<<<div_up(s->n_aff, 64), 64, 0, st>>>(G, s->xhat.p, gr[0], gr[1], gr[2]);
+    ZL(k_predict, div_up(s->n_nodes, TB), TB, 0, st)(G, s->x.p, s->v.p, s->xt.p, s->xhat.p, gr[0], gr[1], gr[2]);
+    if (s->n_aff) ZL(k_predict_affine, div_up(s->n_aff, 64), 64, 0, st)(G, s->xhat.p, gr[0], gr[1], gr[2]);
     ZLAUNCH();
     bool first = !s->first_step_done;
     init_kappa(s);
@@ -1232,7 +1240,7 @@ void do_step(zema_scene* s) {
     lag_friction(s);
     if (first) {
         // d_min over active pairs at x^t
-        k_sv_pos<<<div_up(s->n_sv, TB), TB, 0, st>>>(G, s->x.p, s->X.p);
+        ZL(k_sv_pos, div_up(s->n_sv, TB), TB, 0, st)(G, s->x.p, s->X.p);
         ZLAUNCH();
         active_pairs(s, s->X.p, true);
         W.dmin_last.assign(NE, INFINITY);
@@ -1244,7 +1252,7 @@ void do_step(zema_scene* s) {
     s->S.ms_phase[0] += now_ms() - t0;
     // warm start: x^t + alpha h v^t, CCD-bounded, kept if the energy does not rise
     W.dirw.ensure(&s->A, n3 + 3);
-    k_scale_dir<<<div_up(s->n_nodes, TB), TB, 0, st>>>(G, s->v.p, s->P.dt, W.dirw.p);
+    ZL(k_scale_dir, div_up(s->n_nodes, TB), TB, 0, st)(G, s->v.p, s->P.dt, W.dirw.p);
     ZLAUNCH();
     std::vector<int> done(NE, 0), acc;
     line_search(s, W.dirw.p, done, true, &acc);
@@ -1254,7 +1262,7 @@ void do_step(zema_scene* s) {
         bool converged = false;
         for (int it = 0; it < s->P.max_newton; ++it) {
             double ta = now_ms();
-            k_sv_pos<<<div_up(s->n_sv, TB), TB, 0, st>>>(G, s->x.p, s->X.p);
+            ZL(k_sv_pos, div_up(s->n_sv, TB), TB, 0, st)(G, s->x.p, s->X.p);
             ZLAUNCH();
             active_pairs(s, s->X.p, true);
             double tb = now_ms();
@@ -1283,7 +1291,7 @@ void do_step(zema_scene* s) {
             // zero the direction of envs that just converged
             for (int e = 0; e < NE; ++e) s->hi[e] = done[e];
             ZCHECK(cudaMemcpyAsync(s->need.p, s->hi, NE * sizeof(int), cudaMemcpyHostToDevice, st));
-            k_mask_env<<<div_up(s->n_nodes, TB), TB, 0, st>>>(G, s->p.p, s->need.p);
+            ZL(k_mask_env, div_up(s->n_nodes, TB), TB, 0, st)(G, s->p.p, s->need.p);
             ZLAUNCH();
             int hv = line_search(s, s->p.p, done, false, nullptr);
             if (hv < 0) fail(ZEMA_ERR_LINESEARCH, "line search found no decrease after 60 halvings");
@@ -1293,7 +1301,7 @@ void do_step(zema_scene* s) {
         // kinematic augmented Lagrangian (Eq. 13)
         if (s->n_aff == 0) break;
         ZCHECK(cudaMemsetAsync(s->need.p, 0, NE * sizeof(int), st));
-        k_al_check<<<div_up(s->n_aff, 64), 64, 0, st>>>(G, s->x.p, kin(s), s->tolv.p, s->need.p);
+        ZL(k_al_check, div_up(s->n_aff, 64), 64, 0, st)(G, s->x.p, kin(s), s->tolv.p, s->need.p);
         ZLAUNCH();
         ZCHECK(cudaMemcpyAsync(s->hi, s->need.p, NE * sizeof(int), cudaMemcpyDeviceToHost, st));
         ZCHECK(cudaStreamSynchronize(st));
@@ -1301,7 +1309,7 @@ void do_step(zema_scene* s) {
         for (int e = 0; e < NE; ++e) any |= s->hi[e] != 0;
         if (!any || rounds >= s->P.max_al_rounds) break;
         ++rounds;
-        k_al_update<<<div_up(s->n_aff, 64), 64, 0, st>>>(G, s->x.p, s->qtarget.p, s->lamA.p, s->need.p);
+        ZL(k_al_update, div_up(s->n_aff, 64), 64, 0, st)(G, s->x.p, s->qtarget.p, s->lamA.p, s->need.p);
         ZLAUNCH();
         for (int e = 0; e < NE; ++e) done[e] = s->hi[e] ? 0 : 1;
     }
@@ -1310,7 +1318,7 @@ void do_step(zema_scene* s) {
     std::vector<double> dm(NE);
     ZCHECK(cudaMemcpyAsync(dm.data(), s->dmin.p, NE * sizeof(double), cudaMemcpyDeviceToHost, st));
     // velocities (Eq. 11)
-    k_velocity<<<div_up(s->n_nodes, TB), TB, 0, st>>>(G, s->x.p, s->xt.p, s->v.p);
+    ZL(k_velocity, div_up(s->n_nodes, TB), TB, 0, st)(G, s->x.p, s->xt.p, s->v.p);
     ZLAUNCH();
     std::vector<double> kap(NE), kmin(NE);
     ZCHECK(cudaMemcpyAsync(kap.data(), s->kappa.p, NE * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -1371,6 +1379,8 @@ int affine_dev_index(const zema_scene* s, int input_idx) {
 // C ABI
 // ===========================================================================
 extern "C" {
+
+long long zema_launch_count(void) { return zema::launch_counter(); }
 
 void zema_default_params(zema_scene_params* p) {
     if (!p) return;
@@ -1489,12 +1499,13 @@ zema_status zema_add_affine_body(zema_scene* s, int32_t env, const double* V_res
 }
 
 zema_status zema_finalize(zema_scene* s) {
+    if (s) set_current_stream(s->st);
     if (!s) return ZEMA_ERR_INVALID_ARG;
     if (s->finalized) return ZEMA_OK;
     ZEMA_TRY(s) {
         build(s);
         // reject initial states with touching primitives
-        k_sv_pos<<<div_up(s->n_sv, TB), TB, 0, s->st>>>(s->G, s->x.p, s->X.p);
+        ZL(k_sv_pos, div_up(s->n_sv, TB), TB, 0, s->st)(s->G, s->x.p, s->X.p);
         ZLAUNCH();
         active_pairs(s, s->X.p, true);
         std::vector<double> dm(s->n_envs);
@@ -1508,6 +1519,7 @@ zema_status zema_finalize(zema_scene* s) {
 }
 
 zema_status zema_set_kinematic_target(zema_scene* s, int32_t body, const double q_target[12]) {
+    if (s) set_current_stream(s->st);
     if (!s || !q_target || body < 0 || body >= (int)s->bodies.size() || s->bodies[body].first != 1)
         return ZEMA_ERR_INVALID_ARG;
     ZEMA_TRY(s) {
@@ -1527,6 +1539,7 @@ zema_status zema_set_kinematic_target(zema_scene* s, int32_t body, const double 
 }
 
 zema_status zema_step(zema_scene* s, int32_t n_steps, zema_step_stats* stats) {
+    if (s) set_current_stream(s->st);
     if (!s || n_steps < 0) return ZEMA_ERR_INVALID_ARG;
     if (!s->finalized) {
         zema_status r = zema_finalize(s);
@@ -1730,6 +1743,7 @@ void zema_destroy_scene(zema_scene* s) {
 }
 
 zema_status zema_eval_energy_grad(zema_scene* s, int32_t apply_predictor, double* energy_out, double* grad) {
+    if (s) set_current_stream(s->st);
     if (!s || !energy_out) return ZEMA_ERR_INVALID_ARG;
     if (!s->finalized) {
         zema_status r = zema_finalize(s);
@@ -1741,20 +1755,20 @@ zema_status zema_eval_energy_grad(zema_scene* s, int32_t apply_predictor, double
         int NE = s->n_envs;
         if (apply_predictor) {
             const double* gr = s->P.gravity;
-            k_predict<<<div_up(s->n_nodes, TB), TB, 0, st>>>(G, s->x.p, s->v.p, s->xt.p, s->xhat.p, gr[0], gr[1], gr[2]);
-            if (s->n_aff) k_predict_affine<<<div_up(s->n_aff, 64), 64, 0, st>>>(G, s->xhat.p, gr[0], gr[1], gr[2]);
+            ZL(k_predict, div_up(s->n_nodes, TB), TB, 0, st)(G, s->x.p, s->v.p, s->xt.p, s->xhat.p, gr[0], gr[1], gr[2]);
+            if (s->n_aff) ZL(k_predict_affine, div_up(s->n_aff, 64), 64, 0, st)(G, s->xhat.p, gr[0], gr[1], gr[2]);
             ZLAUNCH();
             init_kappa(s);
             lag_friction(s);
         }
-        k_sv_pos<<<div_up(s->n_sv, TB), TB, 0, st>>>(G, s->x.p, s->X.p);
+        ZL(k_sv_pos, div_up(s->n_sv, TB), TB, 0, st)(G, s->x.p, s->X.p);
         ZLAUNCH();
         active_pairs(s, s->X.p, false);
         energy(s, s->x.p, s->cand.p, s->m_env.p);
         for (int e = 0; e < NE; ++e) energy_out[e] = s->hd[e];
         if (grad) {
             grad_hess(s, true, true, false);
-            k_affine_grad_to_row<<<div_up(s->n_aff + 1, 64), 64, 0, st>>>(G, s->g.p);
+            ZL(k_affine_grad_to_row, div_up(s->n_aff + 1, 64), 64, 0, st)(G, s->g.p);
             ZLAUNCH();
             std::vector<double> gh(3 * (size_t)s->n_nodes);
             ZCHECK(cudaMemcpyAsync(gh.data(), s->g.p, gh.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -1880,6 +1894,7 @@ zema_status zema_candidates_raw(int64_t nsv, const double* pos0, const double* p
                                 const int32_t* b_class, const int32_t* b_env, int64_t ne, const int32_t* edges,
                                 int64_t nt, const int32_t* tris, double inflate, double cell_size, int64_t cap,
                                 int32_t* pt_out, int32_t* ee_out, int64_t* n_out, void* stream) {
+    set_current_stream((cudaStream_t)stream);
     if (nsv < 0 || nb < 1 || ne < 0 || nt < 0 || !pos0 || !sv_body || !b_class || !b_env || !n_out || !(inflate >= 0))
         return ZEMA_ERR_INVALID_ARG;
     try {
@@ -1910,7 +1925,7 @@ zema_status zema_candidates_raw(int64_t nsv, const double* pos0, const double* p
         v.body_class = T.put(b_class, (size_t)nb);
         int* benv = T.put(b_env, (size_t)nb);
         int* sve = T.put<int>(nullptr, (size_t)nsv + 1);
-        if (nsv) k_sv_env_of<<<div_up(nsv, TB), TB, 0, st>>>(svb, benv, (int)nsv, sve);
+        if (nsv) ZL(k_sv_env_of, div_up(nsv, TB), TB, 0, st)(svb, benv, (int)nsv, sve);
         ZLAUNCH();
         v.sv_env = sve;
         v.edges = (const int2*)T.put(edges, 2 * (size_t)ne);
@@ -1954,6 +1969,7 @@ zema_status zema_candidates_raw(int64_t nsv, const double* pos0, const double* p
 
 zema_status zema_local_barrier(int64_t n, const double* x12, const int32_t* is_ee, const double* eps_x, double dhat,
                                double* e_out, double* g_out, double* H_out, void* stream) {
+    set_current_stream((cudaStream_t)stream);
     if (n < 0 || !x12 || !is_ee || !eps_x || !e_out || !g_out || !H_out || !(dhat > 0)) return ZEMA_ERR_INVALID_ARG;
     if (n == 0) return ZEMA_OK;
     try {
@@ -1966,7 +1982,7 @@ zema_status zema_local_barrier(int64_t n, const double* x12, const int32_t* is_e
         double* g = T.put<double>(nullptr, 12 * (size_t)n);
         double* H = T.put<double>(nullptr, 144 * (size_t)n);
         ZCHECK(cudaFuncSetAttribute(k_local_barrier, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 144 * BR_T * 8));
-        k_local_barrier<<<div_up(n, BR_T), BR_T, 2 * 144 * BR_T * 8, st>>>(dx, de, dp, (int)n, dhat, E, g, H);
+        ZL(k_local_barrier, div_up(n, BR_T), BR_T, 2 * 144 * BR_T * 8, st)(dx, de, dp, (int)n, dhat, E, g, H);
         ZLAUNCH();
         get(e_out, E, n, st);
         get(g_out, g, 12 * n, st);
@@ -1980,6 +1996,7 @@ zema_status zema_local_barrier(int64_t n, const double* x12, const int32_t* is_e
 
 zema_status zema_local_distance(int64_t n, const double* x12, const int32_t* is_ee, double* d2_out, double* w_out,
                                 void* stream) {
+    set_current_stream((cudaStream_t)stream);
     if (n < 0 || !x12 || !is_ee || !d2_out || !w_out) return ZEMA_ERR_INVALID_ARG;
     if (n == 0) return ZEMA_OK;
     try {
@@ -1989,7 +2006,7 @@ zema_status zema_local_distance(int64_t n, const double* x12, const int32_t* is_
         int* de = T.put(is_ee, (size_t)n);
         double* d2 = T.put<double>(nullptr, (size_t)n);
         double* w = T.put<double>(nullptr, 4 * (size_t)n);
-        k_local_distance<<<div_up(n, 128), 128, 0, st>>>(dx, de, (int)n, d2, w);
+        ZL(k_local_distance, div_up(n, 128), 128, 0, st)(dx, de, (int)n, d2, w);
         ZLAUNCH();
         get(d2_out, d2, n, st);
         get(w_out, w, 4 * n, st);
@@ -2002,6 +2019,7 @@ zema_status zema_local_distance(int64_t n, const double* x12, const int32_t* is_
 
 zema_status zema_local_neo_hookean(int64_t n, const double* F9, double mu, double lam, double* psi_out, double* g_out,
                                    double* H_out, void* stream) {
+    set_current_stream((cudaStream_t)stream);
     if (n < 0 || !F9 || !psi_out || !g_out || !H_out) return ZEMA_ERR_INVALID_ARG;
     if (n == 0) return ZEMA_OK;
     try {
@@ -2012,7 +2030,7 @@ zema_status zema_local_neo_hookean(int64_t n, const double* F9, double mu, doubl
         double* g = T.put<double>(nullptr, 9 * (size_t)n);
         double* H = T.put<double>(nullptr, 81 * (size_t)n);
         ZCHECK(cudaFuncSetAttribute(k_local_nh, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 81 * EL_T * 8));
-        k_local_nh<<<div_up(n, EL_T), EL_T, 2 * 81 * EL_T * 8, st>>>(dF, (int)n, mu, lam, ps, g, H);
+        ZL(k_local_nh, div_up(n, EL_T), EL_T, 2 * 81 * EL_T * 8, st)(dF, (int)n, mu, lam, ps, g, H);
         ZLAUNCH();
         get(psi_out, ps, n, st);
         get(g_out, g, 9 * n, st);
@@ -2026,6 +2044,7 @@ zema_status zema_local_neo_hookean(int64_t n, const double* F9, double mu, doubl
 
 zema_status zema_local_accd(int64_t n, const double* x12, const double* p12, const int32_t* is_ee, double* t_out,
                             void* stream) {
+    set_current_stream((cudaStream_t)stream);
     if (n < 0 || !x12 || !p12 || !is_ee || !t_out) return ZEMA_ERR_INVALID_ARG;
     if (n == 0) return ZEMA_OK;
     try {
@@ -2035,7 +2054,7 @@ zema_status zema_local_accd(int64_t n, const double* x12, const double* p12, con
         double* dp = T.put(p12, 12 * (size_t)n);
         int* de = T.put(is_ee, (size_t)n);
         double* t = T.put<double>(nullptr, (size_t)n);
-        k_local_accd<<<div_up(n, 128), 128, 0, st>>>(dx, dp, de, (int)n, t);
+        ZL(k_local_accd, div_up(n, 128), 128, 0, st)(dx, dp, de, (int)n, t);
         ZLAUNCH();
         get(t_out, t, n, st);
         ZCHECK(cudaStreamSynchronize(st));

@@ -267,12 +267,23 @@ def soft_cube(n_vert: int, size: float, origin) -> tuple:
     return lattice_tets(m, size / (n_vert - 1), origin)
 
 
+# Horizontal offsets of the stacked bodies.  With every body centred, resting
+# vertices sit exactly above a triangle edge of the surface below (the floor's
+# and the cube faces' diagonals).  There the per-triangle barrier sum has an
+# unstable symmetric equilibrium, so round-off alone decides on which side a
+# vertex settles.  These offsets keep every resting vertex at least ~10 dhat
+# away from the edges below it.
+C1_SOFT_OFFSET = (0.1, 0.037)
+C1_RIGID_OFFSET = (0.043, -0.061)
+
+
 def scene_c1(n_steps: int = 100) -> Scene:
     """Tiny scene: a 1 m soft cube (5x5x5 vertex grid, 384 tets) whose bottom is
     0.05 m above a fixed affine floor box (3 x 0.2 x 3 m, top at y = 0), with a
     0.3 m affine cube resting on the soft top at a gap of 0.5 dhat."""
     p = Params(dt=0.01, dhat=1e-3, kappa=0.0, eps_v=1e-3, newton_tol_rel=1e-3)
-    X, T = soft_cube(5, 1.0, (-0.5, 0.05, -0.5))
+    ox, oz = C1_SOFT_OFFSET
+    X, T = soft_cube(5, 1.0, (-0.5 + ox, 0.05, -0.5 + oz))
     s = Scene("c1_soft_cube_drop", p, n_steps=n_steps)
     s.tets.append(TetBody(X, T, E=1e5, nu=0.4, rho=1000.0, mu=0.5, name="soft_cube"))
     Vf, Ff = box_surface((3.0, 0.2, 3.0), 1)
@@ -280,7 +291,8 @@ def scene_c1(n_steps: int = 100) -> Scene:
                                 stiffness=1e8, mu=0.5, mode=1, name="floor"))
     Vc, Fc = box_surface((0.3, 0.3, 0.3), 1)
     top = 1.05 + 0.5 * p.dhat + 0.15
-    s.affines.append(AffineBody(Vc, Fc, q_identity((0.0, top, 0.0)), rho=1000.0,
+    rx, rz = C1_RIGID_OFFSET
+    s.affines.append(AffineBody(Vc, Fc, q_identity((ox + rx, top, oz + rz)), rho=1000.0,
                                 stiffness=1e8, mu=0.5, mode=0, name="rigid_cube"))
     return s
 
@@ -454,14 +466,14 @@ def scene_tiny_contact(n_steps: int = 10, mu: float = 0.5) -> Scene:
     """A 3x3x3-vertex soft cube dropped onto a fixed floor with an affine cube
     on top: every pair kind (soft-fixed, soft-affine) in a few hundred DOF."""
     p = Params(dt=0.01)
-    X, T = soft_cube(3, 0.2, (-0.1, 0.01, -0.1))
+    X, T = soft_cube(3, 0.2, (-0.1 + 0.013, 0.01, -0.1 - 0.029))
     s = Scene("tiny_contact", p, n_steps=n_steps)
     s.tets.append(TetBody(X, T, E=1e5, nu=0.4, rho=1000.0, mu=mu))
     Vf, Ff = box_surface((1.0, 0.1, 1.0), 1)
     s.affines.append(AffineBody(Vf, Ff, q_identity((0.0, -0.05, 0.0)), rho=1000.0, stiffness=1e8,
                                 mu=mu, mode=1, name="floor"))
     Vc, Fc = box_surface((0.1, 0.1, 0.1), 2)
-    s.affines.append(AffineBody(Vc, Fc, q_identity((0.03, 0.21 + 0.0005 + 0.05, 0.02)), rho=1000.0,
+    s.affines.append(AffineBody(Vc, Fc, q_identity((0.031, 0.21 + 0.0005 + 0.05, 0.016)), rho=1000.0,
                                 stiffness=1e8, mu=mu, mode=0, name="cube"))
     return s
 

@@ -6,8 +6,10 @@ There is no CPU fallback: without the built library or a GPU, calls raise.
 """
 from __future__ import annotations
 
+import atexit
 import ctypes as C
 import os
+import weakref
 from typing import Optional
 
 import numpy as np
@@ -96,6 +98,10 @@ def lib():
     L.zema_local_distance.argtypes = [C.c_int64, DP, IP, DP, DP, C.c_void_p]
     L.zema_local_neo_hookean.argtypes = [C.c_int64, DP, C.c_double, C.c_double, DP, DP, DP, C.c_void_p]
     L.zema_local_accd.argtypes = [C.c_int64, DP, DP, IP, DP, C.c_void_p]
+    L.zema_launch_count.restype = C.c_longlong
+    L.zema_launch_count.argtypes = []
+    L.zema_profile_kernel.argtypes = [C.c_char_p]
+    L.zema_profile_read.argtypes = [DP, C.POINTER(C.c_longlong), DP]
     _lib = L
     return L
 
@@ -132,6 +138,19 @@ def _torch_alloc(nbytes, stream, ctx):
 def _torch_free(ptr, stream, ctx):
     import torch
     torch.cuda.caching_allocator_delete(ptr)
+
+
+_LIVE = weakref.WeakSet()
+
+
+@atexit.register
+def _close_all():
+    # release device memory while PyTorch is still importable
+    for sc in list(_LIVE):
+        try:
+            sc.close()
+        except Exception:
+            pass
 
 
 _ALLOC = ALLOC_FN(_torch_alloc)
@@ -195,6 +214,7 @@ class Scene:
             self.body_ids.append(bid.value)
         self.n_tet = len(scene.tets)
         self.step_index = 0
+        _LIVE.add(self)
         _check(L.zema_finalize(h), h)
 
     def close(self):
@@ -264,6 +284,16 @@ class Scene:
         a = _d(arr)
         _check(lib().zema_set_state(self.h, body, _dp(a), len(a)), self.h)
 
+    def set_state_ptr(self, body, ptr, n):
+        """zema_set_state from a raw host pointer (e.g. pinned memory)."""
+        _check(lib().zema_set_state(self.h, body, C.cast(C.c_void_p(ptr), DP), n), self.h)
+
+    def get_state_ptr(self, body, ptr, cap):
+        """zema_get_state into a raw host pointer (e.g. pinned memory)."""
+        w = C.c_int64()
+        _check(lib().zema_get_state(self.h, body, C.cast(C.c_void_p(ptr), DP), cap, C.byref(w)), self.h)
+        return w.value
+
     def tet_positions(self, i=0):
         st = self.get_state(self.tet_body_id(i))
         n = len(st) // 6
@@ -296,6 +326,25 @@ class Scene:
         g = np.zeros(n) if grad else None
         _check(lib().zema_eval_energy_grad(self.h, 1 if apply_predictor else 0, _dp(E), _dp(g)), self.h)
         return E, g
+
+
+def launch_count() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(lib().zema_launch_count())
+
+
+def profile_kernel(name: Optional[str]):
+    """Time every launch of one library kernel with CUDA events (None stops)."""
+    lib().zema_profile_kernel(None if name is None else name.encode())
+
+
+def profile_read():
+    """(ms total, launches, algorithmic bytes) since profile_kernel()."""
+    ms = C.c_double()
+    n = C.c_longlong()
+    b = C.c_double()
+    lib().zema_profile_read(C.byref(ms), C.byref(n), C.byref(b))
+    return ms.value, n.value, b.value
 
 
 # ---------------------------------------------------------------------------
