@@ -13,7 +13,8 @@
 
 namespace zema {
 
-constexpr double kMaxCells = 1024.0;
+constexpr double kMaxCells = 1024.0;       // entries spanning more cells stay out of the grid
+constexpr double kMaxQueryCells = 32.0;    // queries spanning more cells run one block per query
 
 struct Box6 {
     double lo[3], hi[3];
@@ -223,8 +224,8 @@ __global__ void k_query(BPView v, int kind, int nq, const double* qbox, const do
         return q < e && ee_ok(v, q, e);
     };
     double nc = box_cells(a, v.inv_cell);
-    if (!(nc <= kMaxCells)) {
-        // oversize query: handled by k_query_big (one block per query)
+    if (!(nc <= kMaxQueryCells)) {
+        // large query: handled by k_query_big (one block per query)
         if (!WRITE) cnt[q] = 0;
         return;
     } else {
@@ -296,12 +297,12 @@ __global__ void k_query_big(BPView v, int kind, const int* qlist, const double* 
     }
 }
 
-// oversize flag of point query boxes
-__global__ void k_point_big(const double* pbox, int n, double inv_cell, uint32_t* flag) {
+// large-query flag of point or edge query boxes
+__global__ void k_query_flag(const double* box, int n, double inv_cell, uint32_t* flag) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    Box6 a = ld_box(pbox + 6 * (size_t)i);
-    flag[i] = box_cells(a, inv_cell) <= kMaxCells ? 0u : 1u;
+    Box6 a = ld_box(box + 6 * (size_t)i);
+    flag[i] = box_cells(a, inv_cell) <= kMaxQueryCells ? 0u : 1u;
 }
 
 static uint64_t pow2_at_least(uint64_t n) {
@@ -327,7 +328,7 @@ void BroadPhase::run(Allocator* A, const BPView& v, cudaStream_t st) {
     eoff.ensure(A, ne + 2);
     flag.ensure(A, (size_t)nt + ne + 2);
     flagoff.ensure(A, (size_t)nt + ne + 4);
-    size_t mx = (size_t)nt + ne + nsv + 16;
+    size_t mx = (size_t)nt + 2 * (size_t)ne + nsv + 16;
     tmp.ensure(A, scan_tmp_size(mx));
     if (nsv) ZL(k_boxes, div_up(nsv, TB), TB, 0, st)(v, 0, nsv, pbox.p, nullptr, nullptr);
     if (ne) ZL(k_boxes, div_up(ne, TB), TB, 0, st)(v, 1, ne, ebox.p, ecnt.p, flag.p + nt);
@@ -384,17 +385,21 @@ void BroadPhase::run(Allocator* A, const BPView& v, cudaStream_t st) {
     qoff_pt.ensure(A, nsv + 2);
     qcnt_ee.ensure(A, ne + 1);
     qoff_ee.ensure(A, ne + 2);
-    // oversize point queries (swept boxes of long moves)
-    pflag.ensure(A, nsv + 1);
-    pflagoff.ensure(A, nsv + 2);
-    if (nsv) ZL(k_point_big, div_up(nsv, TB), TB, 0, st)(pbox.p, nsv, v.inv_cell, pflag.p);
+    // large queries (boxes over kMaxQueryCells cells): points, then edges
+    pflag.ensure(A, (size_t)nsv + ne + 1);
+    pflagoff.ensure(A, (size_t)nsv + ne + 2);
+    if (nsv) ZL(k_query_flag, div_up(nsv, TB), TB, 0, st)(pbox.p, nsv, v.inv_cell, pflag.p);
+    if (ne) ZL(k_query_flag, div_up(ne, TB), TB, 0, st)(ebox.p, ne, v.inv_cell, pflag.p + nsv);
     ZLAUNCH();
-    exclusive_scan(pflag.p, pflagoff.p, nsv, tmp.p, st);
+    exclusive_scan(pflag.p, pflagoff.p, (size_t)nsv + ne, tmp.p, st);
     ZCHECK(cudaMemcpyAsync(h_counts + 6, pflagoff.p + nsv, 4, cudaMemcpyDeviceToHost, st));
+    ZCHECK(cudaMemcpyAsync(h_counts + 7, pflagoff.p + nsv + ne, 4, cudaMemcpyDeviceToHost, st));
     ZCHECK(cudaStreamSynchronize(st));
-    uint32_t nbp = h_counts[6];
+    uint32_t nbp = h_counts[6], nbq = h_counts[7] - h_counts[6];
     big_p.ensure(A, nbp + 1);
+    big_q.ensure(A, nbq + 1);
     if (nsv) ZL(k_compact_flags, div_up(nsv, TB), TB, 0, st)(pflag.p, pflagoff.p, 0u, nsv, big_p.p);
+    if (ne) ZL(k_compact_flags, div_up(ne, TB), TB, 0, st)(pflag.p + nsv, pflagoff.p + nsv, nbp, ne, big_q.p);
     ZLAUNCH();
     if (nsv)
         ZL(k_query<false>, div_up(nsv, TB), TB, 0, st)(v, 0, nsv, pbox.p, tbox.p, TT, big_t.p, (int)nbt, nt,
@@ -403,8 +408,7 @@ void BroadPhase::run(Allocator* A, const BPView& v, cudaStream_t st) {
         ZL(k_query<false>, div_up(ne, TB), TB, 0, st)(v, 1, ne, ebox.p, ebox.p, TE, big_e.p, (int)nbe, ne,
                                                       qcnt_ee.p, nullptr, nullptr);
     if (nbp) ZL(k_query_big<false>, nbp, 256, 0, st)(v, 0, big_p.p, pbox.p, tbox.p, nt, qcnt_pt.p, nullptr, nullptr);
-    // an oversize edge box is oversize both as an entry and as a query
-    if (nbe) ZL(k_query_big<false>, nbe, 256, 0, st)(v, 1, big_e.p, ebox.p, ebox.p, ne, qcnt_ee.p, nullptr, nullptr);
+    if (nbq) ZL(k_query_big<false>, nbq, 256, 0, st)(v, 1, big_q.p, ebox.p, ebox.p, ne, qcnt_ee.p, nullptr, nullptr);
     ZLAUNCH();
     tmp.ensure(A, std::max(scan_tmp_size(mx), E ? radix_tmp_size(E) : 0));
     exclusive_scan(qcnt_pt.p, qoff_pt.p, nsv, tmp.p, st);
@@ -423,7 +427,7 @@ void BroadPhase::run(Allocator* A, const BPView& v, cudaStream_t st) {
         ZL(k_query<true>, div_up(ne, TB), TB, 0, st)(v, 1, ne, ebox.p, ebox.p, TE, big_e.p, (int)nbe, ne, nullptr,
                                                      qoff_ee.p, ee.p);
     if (nbp && n_pt) ZL(k_query_big<true>, nbp, 256, 0, st)(v, 0, big_p.p, pbox.p, tbox.p, nt, nullptr, qoff_pt.p, pt.p);
-    if (nbe && n_ee) ZL(k_query_big<true>, nbe, 256, 0, st)(v, 1, big_e.p, ebox.p, ebox.p, ne, nullptr, qoff_ee.p, ee.p);
+    if (nbq && n_ee) ZL(k_query_big<true>, nbq, 256, 0, st)(v, 1, big_q.p, ebox.p, ebox.p, ne, nullptr, qoff_ee.p, ee.p);
     ZLAUNCH();
 }
 

@@ -29,7 +29,7 @@ struct BroadPhase {
     DBuf<uint64_t> ecell;  // sorted entry cell keys
     DBuf<int> eprim;       // sorted entry primitive ids
     DBuf<uint32_t> bstart, bend;
-    DBuf<int> big_t, big_e, big_p;
+    DBuf<int> big_t, big_e, big_p, big_q;
     DBuf<uint32_t> pflag, pflagoff;
     DBuf<uint32_t> flag, flagoff;
     DBuf<uint32_t> qcnt_pt, qoff_pt, qcnt_ee, qoff_ee;

@@ -41,6 +41,8 @@ struct LaunchScope {
 };
 void set_current_stream(cudaStream_t st);
 void alg_bytes_hint(double bytes);
+// adds algorithmic bytes to the selected kernel after the fact (iterative kernels)
+void alg_bytes_add(const char* name, double bytes);
 #define ZL(kernel, ...) ::zema::LaunchScope(#kernel), kernel<<<__VA_ARGS__>>>
 
 constexpr int kChunks = 32;   // blocks per environment in segmented reductions

@@ -343,6 +343,52 @@ __device__ inline double d2_derivs(const V3* x, bool is_ee, const DistInfo& di, 
 }
 
 // ---------------------------------------------------------------------------
+// PSD projection of a translation-invariant 12x12 stencil Hessian.  Every
+// barrier term depends on the four points only through their differences,
+// so H = T^T K T with T (9 x 12, orthonormal rows: T[k] = -1/2 e_0 + e_{k+1}
+// - 1/6 sum_{j != 0} e_j, each times I3) spanning the translation-free
+// subspace, and the 12x12 projection equals T^T P(K) T with the 9x9
+// K = T H T^T: the same projection with a 9x9 eigenproblem.  H is scaled by
+// `scale` first; V (12x12 scratch) holds K and the projection workspace.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double tcoef(int k, int i) {  // T[k][i] for stencil slot i
+    return i == 0 ? -0.5 : (i == k + 1 ? 5.0 / 6.0 : -1.0 / 6.0);
+}
+
+__device__ inline void project_translation_free(SMat<12> H, SMat<12> V, double scale) {
+    SMat<9> K{V.b, V.ld};
+    // K = T (scale H) T^T, blockwise: K(k a, l b) = sum_ij T[k][i] T[l][j] H(3i + a, 3j + b)
+    for (int k = 0; k < 3; ++k)
+        for (int l = 0; l < 3; ++l)
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) {
+                    double s = 0.0;
+                    for (int i = 0; i < 4; ++i) {
+                        double ti = tcoef(k, i);
+                        double r = 0.0;
+                        for (int j = 0; j < 4; ++j) r += tcoef(l, j) * H(3 * i + a, 3 * j + b);
+                        s += ti * r;
+                    }
+                    K(3 * k + a, 3 * l + b) = scale * s;
+                }
+    SMat<9> Wk{H.b, H.ld};  // H is no longer needed: scratch for the projection
+    psd_project<9>(K, Wk);
+    // H = T^T P(K) T
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j)
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) {
+                    double s = 0.0;
+                    for (int k = 0; k < 3; ++k) {
+                        double r = 0.0;
+                        for (int l = 0; l < 3; ++l) r += K(3 * k + a, 3 * l + b) * tcoef(l, j);
+                        s += tcoef(k, i) * r;
+                    }
+                    H(3 * i + a, 3 * j + b) = s;
+                }
+}
+
+// ---------------------------------------------------------------------------
 // kappa * e * b(d) for one stencil: value, gradient g12 and (PSD-projected)
 // Hessian in H (12x12 slot space); V is scratch for the projection.  Returns
 // false when d >= dhat (inactive).  eps_x <= 0 disables the mollifier.
@@ -411,11 +457,7 @@ __device__ inline bool pair_barrier(const V3* x, bool is_ee, double dhat, double
     }
     E = kappa * b;
     for (int i = 0; i < 12; ++i) g12[i] = kappa * gB[i];
-    if (want_h) {
-        for (int i = 0; i < 12; ++i)
-            for (int j = 0; j < 12; ++j) H(i, j) *= kappa;
-        psd_project<12>(H, V);
-    }
+    if (want_h) project_translation_free(H, V, kappa);
     return true;
 }
 

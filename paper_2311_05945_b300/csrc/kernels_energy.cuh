@@ -346,9 +346,10 @@ __device__ __forceinline__ double pair_eps_x(const Geo& G, const PairRec& r) {
 __global__ void __launch_bounds__(BR_T) k_barrier_gh(Geo G, const double* X, const PairRec* rec, int n,
                                                      const double* kappa_env, double* pH, double* pG) {
     extern __shared__ double sm[];
-    int i = blockIdx.x * BR_T + threadIdx.x;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    SMat<12> H{sm + threadIdx.x, BR_T}, V{sm + 144 * BR_T + threadIdx.x, BR_T};
+    int ld = blockDim.x;
+    SMat<12> H{sm + threadIdx.x, ld}, V{sm + 144 * ld + threadIdx.x, ld};
     PairRec r = rec[i];
     V3 x[4];
     for (int k = 0; k < 4; ++k) x[k] = ld3(X + 3 * (size_t)r.s[k]);

@@ -1,6 +1,8 @@
 // Block-sparse assembly (3x3 blocks over nodes), block-Jacobi preconditioner
 // and the PCG iteration with per-environment scalars.
 #pragma once
+#include <cooperative_groups.h>
+
 #include "kernels_energy.cuh"
 
 namespace zema {
@@ -444,6 +446,191 @@ __global__ void k_pcg_dir(Geo G, PcgVec V, int* conv, int* iters, const double* 
         iters[env] += 1;
         if (done) conv[env] = 1;
     }
+}
+
+// ---------------------------------------------------------------------------
+// Persistent PCG: one cooperative launch runs the whole solve.  Work is cut
+// into tiles (contiguous units of one environment, <= 64 units); blocks loop
+// over tiles, write one partial sum per tile, and after each grid-wide
+// barrier every block recombines the partials of each environment in tile
+// order (identical in all blocks, so alpha, beta and the stop test agree
+// everywhere and results are bit-reproducible).  Per env: the solve stops
+// when |r| <= tol |b|; the launch ends when every env has stopped or after
+// max_iter iterations.
+// ---------------------------------------------------------------------------
+struct Tiles {
+    int n;
+    const int* u0;   // first unit of the tile
+    const int* u1;
+    const int* n0;   // node range of the tile's units
+    const int* n1;
+    const int* env;
+    const int* env_start;  // n_envs + 1 tile offsets
+};
+
+struct PcgArgs {
+    Geo G;
+    Bsr S, C;
+    PcgVec V;
+    const double* b;
+    const double* Minv_s;
+    const double* Minv_a;
+    Tiles T;
+    double* pt_rz;   // per-tile partials
+    double* pt_rz2;
+    double* pt_pq;
+    double* pt_rr;
+    double* pt_bb;
+    int* conv;       // per env: in 1 = skip; out 1 = converged / skipped
+    int* iters;      // per env
+    double tol2;
+    int max_iter;
+};
+
+// sum of one env's tile partials, in tile order; thread-strided over envs
+__device__ __forceinline__ void env_sums(const Tiles& T, const double* part, int n_envs, double* out) {
+    for (int e = threadIdx.x; e < n_envs; e += blockDim.x) {
+        double s = 0.0;
+        for (int t = T.env_start[e]; t < T.env_start[e + 1]; ++t) s += part[t];
+        out[e] = s;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_pcg_persistent(PcgArgs a) {
+    namespace cg = cooperative_groups;
+    cg::grid_group grid = cg::this_grid();
+    extern __shared__ double sm[];
+    const int NE = a.G.n_envs;
+    double* s_rz = sm;            // current r.z per env
+    double* s_bb = sm + NE;       // b.b per env
+    double* s_x = sm + 2 * NE;    // scratch per env (pq, then rz_new)
+    double* s_y = sm + 3 * NE;    // scratch per env (rr)
+    int* s_conv = (int*)(sm + 4 * NE);
+    __shared__ double red[32];
+    __shared__ int s_all;
+    const Geo& G = a.G;
+    PcgVec V = a.V;
+    // init: x = 0, r = b, z = M^-1 r, p = z
+    for (int t = blockIdx.x; t < a.T.n; t += gridDim.x) {
+        int e = a.T.env[t];
+        bool skip = a.conv[e] != 0;
+        double rz = 0.0, bb = 0.0;
+        if (!skip)
+            for (int u = a.T.u0[t] + threadIdx.x; u < a.T.u1[t]; u += blockDim.x) {
+                int kind = G.unit_kind[u], idx = G.unit_idx[u];
+                int n0 = kind == 0 ? idx : G.aff_node0[idx], nn = kind == 0 ? 1 : 4;
+                for (int j = 0; j < 3 * nn; ++j) {
+                    size_t o = 3 * (size_t)n0 + j;
+                    V.r[o] = a.b[o];
+                    V.x[o] = 0.0;
+                }
+                double q1, q2;
+                unit_precond(G, u, a.Minv_s, a.Minv_a, V.r, V.z, q1, q2);
+                for (int j = 0; j < 3 * nn; ++j) V.p[3 * (size_t)n0 + j] = V.z[3 * (size_t)n0 + j];
+                rz += q1;
+                bb += q2;
+            }
+        double r1 = block_sum<256>(rz, red);
+        double r2 = block_sum<256>(bb, red);
+        if (threadIdx.x == 0) {
+            a.pt_rz[t] = r1;
+            a.pt_bb[t] = r2;
+        }
+    }
+    grid.sync();
+    env_sums(a.T, a.pt_rz, NE, s_rz);
+    env_sums(a.T, a.pt_bb, NE, s_bb);
+    for (int e = threadIdx.x; e < NE; e += blockDim.x) s_conv[e] = a.conv[e] || !(s_bb[e] > 0.0);
+    __syncthreads();
+    int it = 0;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            int all = 1;
+            for (int e = 0; e < NE; ++e) all &= s_conv[e];
+            s_all = all;
+        }
+        __syncthreads();
+        if (s_all || it >= a.max_iter) break;
+        // q = A p, partial p.q
+        for (int t = blockIdx.x; t < a.T.n; t += gridDim.x) {
+            int e = a.T.env[t];
+            double s = 0.0;
+            if (!s_conv[e]) {
+                int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+                for (int n = a.T.n0[t] + w; n < a.T.n1[t]; n += blockDim.x >> 5) {
+                    V3 y = spmv_row_warp(a.S, n, V.p, lane) + spmv_row_warp(a.C, n, V.p, lane);
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        y.x += __shfl_xor_sync(0xffffffffu, y.x, o);
+                        y.y += __shfl_xor_sync(0xffffffffu, y.y, o);
+                        y.z += __shfl_xor_sync(0xffffffffu, y.z, o);
+                    }
+                    if (lane == 0) {
+                        st3(V.q + 3 * (size_t)n, y);
+                        s += dot(y, ld3(V.p + 3 * (size_t)n));
+                    }
+                }
+            }
+            double r1 = block_sum<256>(s, red);
+            if (threadIdx.x == 0) a.pt_pq[t] = r1;
+        }
+        grid.sync();
+        env_sums(a.T, a.pt_pq, NE, s_x);
+        __syncthreads();
+        // x += alpha p ; r -= alpha q ; z = M^-1 r ; partial r.z, r.r
+        for (int t = blockIdx.x; t < a.T.n; t += gridDim.x) {
+            int e = a.T.env[t];
+            double rz = 0.0, rr = 0.0;
+            if (!s_conv[e]) {
+                double alpha = s_x[e] > 0.0 ? s_rz[e] / s_x[e] : 0.0;
+                for (int u = a.T.u0[t] + threadIdx.x; u < a.T.u1[t]; u += blockDim.x) {
+                    int kind = G.unit_kind[u], idx = G.unit_idx[u];
+                    int n0 = kind == 0 ? idx : G.aff_node0[idx], nn = kind == 0 ? 1 : 4;
+                    for (int j = 0; j < 3 * nn; ++j) {
+                        size_t o = 3 * (size_t)n0 + j;
+                        V.x[o] += alpha * V.p[o];
+                        V.r[o] -= alpha * V.q[o];
+                    }
+                    double q1, q2;
+                    unit_precond(G, u, a.Minv_s, a.Minv_a, V.r, V.z, q1, q2);
+                    rz += q1;
+                    rr += q2;
+                }
+            }
+            double r1 = block_sum<256>(rz, red);
+            double r2 = block_sum<256>(rr, red);
+            if (threadIdx.x == 0) {
+                a.pt_rz2[t] = r1;
+                a.pt_rr[t] = r2;
+            }
+        }
+        grid.sync();
+        env_sums(a.T, a.pt_rz2, NE, s_x);
+        env_sums(a.T, a.pt_rr, NE, s_y);
+        __syncthreads();
+        // beta, stop test, p = z + beta p
+        for (int t = blockIdx.x; t < a.T.n; t += gridDim.x) {
+            int e = a.T.env[t];
+            if (s_conv[e] || !(s_y[e] > a.tol2 * s_bb[e])) continue;
+            double beta = s_rz[e] != 0.0 ? s_x[e] / s_rz[e] : 0.0;
+            for (int n = a.T.n0[t] + threadIdx.x; n < a.T.n1[t]; n += blockDim.x)
+                for (int j = 0; j < 3; ++j) {
+                    size_t o = 3 * (size_t)n + j;
+                    V.p[o] = V.z[o] + beta * V.p[o];
+                }
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < NE; e += blockDim.x) {
+            if (s_conv[e]) continue;
+            if (blockIdx.x == 0) a.iters[e] += 1;
+            if (!(s_y[e] > a.tol2 * s_bb[e])) s_conv[e] = 1;
+            s_rz[e] = s_x[e];
+        }
+        ++it;
+        grid.sync();
+    }
+    if (blockIdx.x == 0)
+        for (int e = threadIdx.x; e < NE; e += blockDim.x) a.conv[e] = s_conv[e];
 }
 
 }  // namespace zema

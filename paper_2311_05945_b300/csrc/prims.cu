@@ -33,6 +33,11 @@ thread_local cudaStream_t g_stream = nullptr;
 void set_current_stream(cudaStream_t st) { g_stream = st; }
 void alg_bytes_hint(double bytes) { prof().pending = bytes; }
 
+void alg_bytes_add(const char* name, double bytes) {
+    Prof& P = prof();
+    if (P.on && P.name == name) P.bytes += bytes;
+}
+
 LaunchScope::LaunchScope(const char* name) : timed(false) {
     ++launch_counter();
     Prof& P = prof();

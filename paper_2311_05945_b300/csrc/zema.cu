@@ -86,6 +86,9 @@ struct zema_scene {
     // per env
     DBuf<double> kappa, kappa_min, alpha, E, dmin, part, part2, part3, part4, part5, part6, part7;
     DBuf<int> conv, pcg_iters, need, capflag;
+    DBuf<int> tile_u0, tile_u1, tile_n0, tile_n1, tile_env, env_tile_start;
+    DBuf<double> pt_a, pt_b, pt_c, pt_d, pt_e;
+    int n_tiles = 0, pcg_grid = 0;
     DBuf<double> tolv;
     // pair lists
     BroadPhase bp;
@@ -443,6 +446,32 @@ void build(zema_scene* s) {
     }
     env_unit_start[NE] = (int)unit_kind_h.size();
     s->n_units = (int)unit_kind_h.size();
+    // PCG tiles: <= 64 consecutive units of one env and their node range
+    std::vector<int> tu0, tu1, tn0, tn1, tenv, etile(NE + 1, 0);
+    for (int e = 0; e < NE; ++e) {
+        etile[e] = (int)tu0.size();
+        for (int u = env_unit_start[e]; u < env_unit_start[e + 1]; u += 64) {
+            int ue = std::min(u + 64, env_unit_start[e + 1]);
+            auto first_node = [&](int uu) {
+                return unit_kind_h[uu] == 0 ? unit_idx_h[uu] : s->aff_node0_h[aff_perm[unit_idx_h[uu]]];
+            };
+            auto last_node = [&](int uu) { return first_node(uu) + (unit_kind_h[uu] == 0 ? 1 : 4); };
+            tu0.push_back(u);
+            tu1.push_back(ue);
+            tn0.push_back(first_node(u));
+            tn1.push_back(last_node(ue - 1));
+            tenv.push_back(e);
+        }
+    }
+    etile[NE] = (int)tu0.size();
+    s->n_tiles = (int)tu0.size();
+    up(s, s->tile_u0, tu0);
+    up(s, s->tile_u1, tu1);
+    up(s, s->tile_n0, tn0);
+    up(s, s->tile_n1, tn1);
+    up(s, s->tile_env, tenv);
+    up(s, s->env_tile_start, etile);
+    for (DBuf<double>* b : {&s->pt_a, &s->pt_b, &s->pt_c, &s->pt_d, &s->pt_e}) b->ensure(A, s->n_tiles + 1);
     // ---- static pattern
     std::vector<std::vector<int>> rows(nN);
     for (int n = 0; n < nN; ++n) rows[n].push_back(n);
@@ -873,9 +902,13 @@ void grad_hess(zema_scene* s, bool barrier = true, bool friction = true, bool he
     uint32_t nr = na + nl;
     s->pH.ensure(A, 144 * (size_t)nr + 144);
     s->pG.ensure(A, 12 * (size_t)nr + 12);
-    if (na)
-        ZL(k_barrier_gh, div_up(na, BR_T), BR_T, 2 * 144 * BR_T * 8, st)(G, s->X.p, s->act.p, (int)na, s->kappa.p,
-                                                                          s->pH.p, s->pG.p);
+    if (na) {
+        // latency-bound FP64 work: few pairs are spread over many SMs
+        int bt = BR_T;
+        while (bt > 4 && (long long)div_up(na, bt) < 2 * 148) bt >>= 1;
+        ZL(k_barrier_gh, div_up(na, bt), bt, 2 * 144 * bt * 8, st)(G, s->X.p, s->act.p, (int)na, s->kappa.p, s->pH.p,
+                                                                    s->pG.p);
+    }
     if (nl)
         ZL(k_friction_gh, div_up(nl, 128), 128, 0, st)(G, s->X.p, s->Xt.p, lagv(s), s->pH.p + 144 * (size_t)na,
                                                         s->pG.p + 12 * (size_t)na);
@@ -957,7 +990,8 @@ void grad_hess(zema_scene* s, bool barrier = true, bool friction = true, bool he
 }
 
 // ---------------------------------------------------------------------------
-// PCG: solve (S + C) p = -g for every env not flagged in done_h
+// PCG: solve (S + C) p = -g for every env not flagged in done_h (one
+// persistent cooperative launch per solve)
 // ---------------------------------------------------------------------------
 int64_t pcg(zema_scene* s, const std::vector<int>& done_h) {
     cudaStream_t st = s->st;
@@ -971,42 +1005,58 @@ int64_t pcg(zema_scene* s, const std::vector<int>& done_h) {
     for (int e = 0; e < NE; ++e) s->hi[e] = done_h[e];
     ZCHECK(cudaMemcpyAsync(s->conv.p, s->hi, NE * sizeof(int), cudaMemcpyHostToDevice, st));
     ZCHECK(cudaMemsetAsync(s->pcg_iters.p, 0, NE * sizeof(int), st));
-    PcgVec V{s->p.p, s->r.p, s->z.p, s->pp.p, s->q.p};
-    double* rz_a = s->part2.p;
-    double* rz_b = s->part3.p;
-    double* pq = s->part4.p;
-    double* rr = s->part5.p;
-    double* bb = s->part6.p;
-    ZL(k_pcg_init, red_grid(NE), kRedThreads, 0, st)(G, s->b.p, V, s->Minv_s.p, s->Minv_a.p, rz_a, bb);
-    ZLAUNCH();
-    double tol2 = s->P.pcg_rel_tol * s->P.pcg_rel_tol;
-    int it = 0;
-    const int check = 8;
-    while (it < s->P.max_pcg) {
-        // algorithmic bytes of one SpMV: every block (72 B values + 4 B column)
-        // and both row-pointer arrays once, p read and q written once
-        double spmv_bytes = 76.0 * ((double)s->n_sblocks + (double)s->n_cblocks) + 8.0 * (s->n_nodes + 1) +
-                            48.0 * s->n_nodes;
-        for (int k = 0; k < check; ++k) {
-            alg_bytes_hint(spmv_bytes);
-            ZL(k_pcg_spmv, red_grid(NE), kRedThreads, 0, st)(G, S, C, V, s->conv.p, pq);
-            ZL(k_pcg_update, red_grid(NE), kRedThreads, 0, st)(G, V, s->Minv_s.p, s->Minv_a.p, s->conv.p, rz_a, pq,
-                                                               rz_b, rr);
-            ZL(k_pcg_dir, red_grid(NE), kRedThreads, 0, st)(G, V, s->conv.p, s->pcg_iters.p, rz_a, rz_b, rr, bb, tol2);
-            std::swap(rz_a, rz_b);
-            ++it;
-        }
-        ZLAUNCH();
-        ZCHECK(cudaMemcpyAsync(s->hi, s->conv.p, NE * sizeof(int), cudaMemcpyDeviceToHost, st));
-        ZCHECK(cudaStreamSynchronize(st));
-        bool all = true;
-        for (int e = 0; e < NE; ++e) all &= s->hi[e] != 0;
-        if (all) break;
+    PcgArgs a;
+    a.G = G;
+    a.S = S;
+    a.C = C;
+    a.V = PcgVec{s->p.p, s->r.p, s->z.p, s->pp.p, s->q.p};
+    a.b = s->b.p;
+    a.Minv_s = s->Minv_s.p;
+    a.Minv_a = s->Minv_a.p;
+    a.T = Tiles{s->n_tiles, s->tile_u0.p, s->tile_u1.p, s->tile_n0.p, s->tile_n1.p, s->tile_env.p, s->env_tile_start.p};
+    a.pt_rz = s->pt_a.p;
+    a.pt_rz2 = s->pt_b.p;
+    a.pt_pq = s->pt_c.p;
+    a.pt_rr = s->pt_d.p;
+    a.pt_bb = s->pt_e.p;
+    a.conv = s->conv.p;
+    a.iters = s->pcg_iters.p;
+    a.tol2 = s->P.pcg_rel_tol * s->P.pcg_rel_tol;
+    a.max_iter = s->P.max_pcg;
+    size_t smem = 4 * (size_t)NE * sizeof(double) + (size_t)NE * sizeof(int);
+    if (s->pcg_grid == 0) {
+        int dev = 0, nsm = 0, per = 0;
+        ZCHECK(cudaGetDevice(&dev));
+        ZCHECK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        if (smem > 48 * 1024)
+            ZCHECK(cudaFuncSetAttribute(k_pcg_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        ZCHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg_persistent, 256, smem));
+        s->pcg_grid = std::max(1, std::min(s->n_tiles, per * nsm));
     }
+    void* args[] = {&a};
+    {
+        LaunchScope ls("k_pcg_persistent");
+        ZCHECK(cudaLaunchCooperativeKernel((const void*)k_pcg_persistent, dim3(s->pcg_grid), dim3(256), args, smem, st));
+    }
+    ZLAUNCH();
     ZCHECK(cudaMemcpyAsync(s->hi, s->pcg_iters.p, NE * sizeof(int), cudaMemcpyDeviceToHost, st));
     ZCHECK(cudaStreamSynchronize(st));
-    int64_t tot = 0;
-    for (int e = 0; e < NE; ++e) tot += s->hi[e];
+    int64_t tot = 0, mx = 0;
+    for (int e = 0; e < NE; ++e) {
+        tot += s->hi[e];
+        mx = std::max<int64_t>(mx, s->hi[e]);
+    }
+    // Algorithmic bytes of the solve for the live roofline, per iteration:
+    // SpMV reads every block (72 B values + 4 B column), both row-pointer
+    // arrays, p, and writes q; the update reads/writes x and r, reads p and q,
+    // writes z, reads the preconditioner (72 B per soft node, 1152 B per
+    // affine body); the direction update reads z and reads/writes p.
+    {
+        double nn = s->n_nodes;
+        double per_it = 76.0 * ((double)s->n_sblocks + (double)s->n_cblocks) + nn * (8.0 + 48.0 + 168.0 + 72.0) +
+                        72.0 * (nn - 4.0 * s->n_aff) + 1152.0 * s->n_aff;
+        alg_bytes_add("k_pcg_persistent", per_it * (double)tot / std::max(1, NE));
+    }
     // done envs: zero direction
     for (int e = 0; e < NE; ++e) s->hi[e] = done_h[e];
     ZCHECK(cudaMemcpyAsync(s->need.p, s->hi, NE * sizeof(int), cudaMemcpyHostToDevice, st));
