@@ -207,6 +207,34 @@ zema_status zema_candidates_raw(int64_t nsv, const double* pos0, const double* p
                                 double cell_size, int64_t cap, int32_t* pt_out, int32_t* ee_out, int64_t* n_out,
                                 void* stream);
 
+/* zema_candidates_raw for callers that cannot allocate device memory (the
+ * paper has no counterpart: it is a deployment variant of the broad phase).
+ * Callers that record work into a CUDA stream capture, draw all device
+ * memory from a pool fixed in advance, or must not call an allocator inside a
+ * real-time loop cannot use zema_candidates_raw, which allocates scratch.
+ * This entry point allocates nothing: every scratch buffer lives in one
+ * file-scope device array of 64 MiB that each GPU loading the library holds
+ * until the process exits.
+ *  - Inputs (pos0, pos1 nullable, sv_body, b_class, b_env, edges, tris) and
+ *    outputs (pt_out, ee_out: cap pairs of int32 each) are DEVICE pointers;
+ *    n_out (2 counts, may exceed cap: outputs then truncated) is host memory.
+ *    Results equal zema_candidates_raw's, in the same order.
+ *  - cell_size must be > 0 (no default: the default needs a reduction over
+ *    host data).
+ *  - Limits: nsv + ne + nt <= 65536, else ZEMA_ERR_INVALID_ARG; a scene whose
+ *    grid entries and pair lists do not fit the 64 MiB array returns
+ *    ZEMA_ERR_OOM.  Neither case touches the outputs' contents beyond n_out.
+ *  - The first call on a device resolves the array's device address
+ *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  - All calls share the one array and leave their contents in it; calls
+ *    that overlap on the GPU (other streams or threads) race.  The call
+ *    synchronises `stream` before returning. */
+zema_status zema_candidates_raw_noalloc(int64_t nsv, const double* pos0, const double* pos1, const int32_t* sv_body,
+                                        int64_t nb, const int32_t* b_class, const int32_t* b_env, int64_t ne,
+                                        const int32_t* edges, int64_t nt, const int32_t* tris, double inflate,
+                                        double cell_size, int64_t cap, int32_t* pt_out, int32_t* ee_out,
+                                        int64_t* n_out, void* stream);
+
 /* Batched local kernels on host arrays (n stencils):
  * barrier of PT (is_ee 0) or EE stencils x12 (n x 12): energy b (n), gradient
  * (n x 12) and PSD-projected Hessian (n x 144) of kappa * e * b(d) with

@@ -94,6 +94,9 @@ def lib():
     L.zema_eval_energy_grad.argtypes = [C.c_void_p, C.c_int32, DP, DP]
     L.zema_candidates_raw.argtypes = [C.c_int64, DP, DP, IP, C.c_int64, IP, IP, C.c_int64, IP, C.c_int64, IP,
                                       C.c_double, C.c_double, C.c_int64, IP, IP, LP, C.c_void_p]
+    L.zema_candidates_raw_noalloc.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
+                                              C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p, C.c_double,
+                                              C.c_double, C.c_int64, C.c_void_p, C.c_void_p, LP, C.c_void_p]
     L.zema_local_barrier.argtypes = [C.c_int64, DP, IP, DP, C.c_double, DP, DP, DP, C.c_void_p]
     L.zema_local_distance.argtypes = [C.c_int64, DP, IP, DP, DP, C.c_void_p]
     L.zema_local_neo_hookean.argtypes = [C.c_int64, DP, C.c_double, C.c_double, DP, DP, DP, C.c_void_p]
@@ -364,6 +367,27 @@ def candidates_raw(pos0, sv_body, b_class, b_env, edges, tris, inflate, pos1=Non
     if n[0] > cap or n[1] > cap:
         raise ZemaError(1, "candidate capacity exceeded")
     return pt[:n[0]].copy(), ee[:n[1]].copy()
+
+
+def candidates_raw_noalloc(pos0, sv_body, b_class, b_env, edges, tris, inflate, cell_size, pt_out, ee_out,
+                           pos1=None):
+    """zema_candidates_raw_noalloc on CUDA tensors (float64 positions, int32
+    index arrays; pt_out / ee_out int32 (cap, 2) tensors).  Returns the two
+    pair counts; the pairs are in pt_out[:n_pt], ee_out[:n_ee]."""
+    import torch
+
+    def ptr(t):
+        return None if t is None else C.c_void_p(t.data_ptr())
+
+    for t in (pos0, sv_body, b_class, b_env, edges, tris, pt_out, ee_out):
+        assert t.is_cuda and t.is_contiguous()
+    n = np.zeros(2, dtype=np.int64)
+    cap = min(pt_out.shape[0], ee_out.shape[0])
+    _check(lib().zema_candidates_raw_noalloc(pos0.shape[0], ptr(pos0), ptr(pos1), ptr(sv_body), b_class.shape[0],
+                                             ptr(b_class), ptr(b_env), edges.shape[0], ptr(edges), tris.shape[0],
+                                             ptr(tris), inflate, cell_size, cap, ptr(pt_out), ptr(ee_out),
+                                             n.ctypes.data_as(LP), C.c_void_p(torch.cuda.current_stream().cuda_stream)))
+    return int(n[0]), int(n[1])
 
 
 def local_barrier(x12, is_ee, eps_x, dhat):
