@@ -75,29 +75,44 @@ __device__ __forceinline__ double comp(V3 a, int i) { return i == 0 ? a.x : (i =
 // ---------------------------------------------------------------------------
 // Symmetric N x N matrices held per thread in shared memory with a stride:
 // element (i, j) lives at base[(i * N + j) * ld].  Used so that a block of
-// threads keeps one small matrix each without register spills.
+// threads keeps one small matrix each without register spills.  T is double
+// (FP64 path) or float (Hessians of the mixed-precision path).
 // ---------------------------------------------------------------------------
-template <int N>
+template <int N, class T = double>
 struct SMat {
-    double* b;
+    T* b;
     int ld;
-    __device__ __forceinline__ double& operator()(int i, int j) const { return b[(i * N + j) * ld]; }
+    __device__ __forceinline__ T& operator()(int i, int j) const { return b[(i * N + j) * ld]; }
+};
+
+// convergence thresholds of the eigen-solver per precision
+template <class T>
+struct Eps;
+template <>
+struct Eps<double> {
+    static constexpr double off2 = 1e-28;  // off-diagonal mass / diagonal mass at convergence
+    static constexpr double skip = 1e-18;  // rotations below this relative size are skipped
+};
+template <>
+struct Eps<float> {
+    static constexpr float off2 = 1e-12f;
+    static constexpr float skip = 1e-9f;
 };
 
 // Cholesky test: true iff A is positive definite (A untouched, W scratch).
-template <int N>
-__device__ bool is_pd(SMat<N> A, SMat<N> W) {
+template <int N, class T>
+__device__ bool is_pd(SMat<N, T> A, SMat<N, T> W) {
     for (int i = 0; i < N; ++i)
         for (int j = 0; j <= i; ++j) W(i, j) = A(i, j);
     for (int j = 0; j < N; ++j) {
-        double d = W(j, j);
+        T d = W(j, j);
         for (int k = 0; k < j; ++k) d -= W(j, k) * W(j, k);
-        if (!(d > 0.0)) return false;
-        double l = sqrt(d);
+        if (!(d > T(0))) return false;
+        T l = sqrt(d);
         W(j, j) = l;
-        double il = 1.0 / l;
+        T il = T(1) / l;
         for (int i = j + 1; i < N; ++i) {
-            double s = W(i, j);
+            T s = W(i, j);
             for (int k = 0; k < j; ++k) s -= W(i, k) * W(j, k);
             W(i, j) = s * il;
         }
@@ -109,45 +124,44 @@ __device__ bool is_pd(SMat<N> A, SMat<N> W) {
 // by cyclic Jacobi rotations, negative eigenvalues clamped to zero.
 // V is scratch of the same shape.  A matrix that is already positive
 // definite (checked by Cholesky) is left unchanged.
-template <int N>
-__device__ void psd_project(SMat<N> A, SMat<N> V) {
-    if (is_pd<N>(A, V)) return;
+template <int N, class T>
+__device__ void psd_project(SMat<N, T> A, SMat<N, T> V) {
+    if (is_pd<N, T>(A, V)) return;
     for (int i = 0; i < N; ++i)
-        for (int j = 0; j < N; ++j) V(i, j) = (i == j) ? 1.0 : 0.0;
+        for (int j = 0; j < N; ++j) V(i, j) = (i == j) ? T(1) : T(0);
     for (int sweep = 0; sweep < 30; ++sweep) {
-        double off = 0.0, diag = 0.0;
+        T off = 0, diag = 0;
         for (int i = 0; i < N; ++i) {
             diag += A(i, i) * A(i, i);
             for (int j = i + 1; j < N; ++j) off += A(i, j) * A(i, j);
         }
-        // off-diagonal mass below (1e-14)^2 of the diagonal: converged to
-        // round-off (cyclic Jacobi converges quadratically; a tighter test
-        // would never be met in FP64)
-        if (off <= 1e-28 * diag) break;
+        // off-diagonal mass at the rounding floor of T: converged (cyclic
+        // Jacobi converges quadratically; a tighter test would never be met)
+        if (off <= Eps<T>::off2 * diag) break;
         bool rotated = false;
         for (int p = 0; p < N - 1; ++p)
             for (int q = p + 1; q < N; ++q) {
-                double apq = A(p, q);
-                double app = A(p, p), aqq = A(q, q);
-                if (fabs(apq) <= 1e-18 * sqrt(fabs(app * aqq)) || apq == 0.0) continue;
+                T apq = A(p, q);
+                T app = A(p, p), aqq = A(q, q);
+                if (fabs(apq) <= Eps<T>::skip * sqrt(fabs(app * aqq)) || apq == T(0)) continue;
                 rotated = true;
                 // rotation angle that zeroes A(p, q)
-                double tau = (aqq - app) / (2.0 * apq);
-                double t = copysign(1.0, tau) / (fabs(tau) + sqrt(1.0 + tau * tau));
-                double c = rsqrt(1.0 + t * t);
-                double s = t * c;
+                T tau = (aqq - app) / (T(2) * apq);
+                T t = copysign(T(1), tau) / (fabs(tau) + sqrt(T(1) + tau * tau));
+                T c = rsqrt(T(1) + t * t);
+                T s = t * c;
                 for (int k = 0; k < N; ++k) {
-                    double akp = A(k, p), akq = A(k, q);
+                    T akp = A(k, p), akq = A(k, q);
                     A(k, p) = c * akp - s * akq;
                     A(k, q) = s * akp + c * akq;
                 }
                 for (int k = 0; k < N; ++k) {
-                    double apk = A(p, k), aqk = A(q, k);
+                    T apk = A(p, k), aqk = A(q, k);
                     A(p, k) = c * apk - s * aqk;
                     A(q, k) = s * apk + c * aqk;
                 }
                 for (int k = 0; k < N; ++k) {
-                    double vkp = V(k, p), vkq = V(k, q);
+                    T vkp = V(k, p), vkq = V(k, q);
                     V(k, p) = c * vkp - s * vkq;
                     V(k, q) = s * vkp + c * vkq;
                 }
@@ -155,12 +169,12 @@ __device__ void psd_project(SMat<N> A, SMat<N> V) {
         if (!rotated) break;
     }
     // A <- V max(L, 0) V^T ; eigenvalues are on A's diagonal
-    double lam[N];
+    T lam[N];
 #pragma unroll
-    for (int i = 0; i < N; ++i) lam[i] = fmax(A(i, i), 0.0);
+    for (int i = 0; i < N; ++i) lam[i] = fmax(A(i, i), T(0));
     for (int i = 0; i < N; ++i)
         for (int j = i; j < N; ++j) {
-            double s = 0.0;
+            T s = 0;
 #pragma unroll
             for (int k = 0; k < N; ++k) s += V(i, k) * lam[k] * V(j, k);
             A(i, j) = s;

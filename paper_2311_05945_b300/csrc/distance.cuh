@@ -355,8 +355,8 @@ __device__ __forceinline__ double tcoef(int k, int i) {  // T[k][i] for stencil 
     return i == 0 ? -0.5 : (i == k + 1 ? 5.0 / 6.0 : -1.0 / 6.0);
 }
 
-__device__ inline void project_translation_free(SMat<12> H, SMat<12> V, double scale) {
-    SMat<9> K{V.b, V.ld};
+template <class T>
+__device__ inline void project_translation_free(SMat<12> H, double scale, SMat<9, T> K, SMat<9, T> W, T* out) {
     // K = T (scale H) T^T, blockwise: K(k a, l b) = sum_ij T[k][i] T[l][j] H(3i + a, 3j + b)
     for (int k = 0; k < 3; ++k)
         for (int l = 0; l < 3; ++l)
@@ -364,37 +364,35 @@ __device__ inline void project_translation_free(SMat<12> H, SMat<12> V, double s
                 for (int b = 0; b < 3; ++b) {
                     double s = 0.0;
                     for (int i = 0; i < 4; ++i) {
-                        double ti = tcoef(k, i);
                         double r = 0.0;
                         for (int j = 0; j < 4; ++j) r += tcoef(l, j) * H(3 * i + a, 3 * j + b);
-                        s += ti * r;
+                        s += tcoef(k, i) * r;
                     }
-                    K(3 * k + a, 3 * l + b) = scale * s;
+                    K(3 * k + a, 3 * l + b) = (T)(scale * s);
                 }
-    SMat<9> Wk{H.b, H.ld};  // H is no longer needed: scratch for the projection
-    psd_project<9>(K, Wk);
-    // H = T^T P(K) T
+    psd_project<9, T>(K, W);
+    // out = T^T P(K) T (row-major 12x12)
     for (int i = 0; i < 4; ++i)
         for (int j = 0; j < 4; ++j)
             for (int a = 0; a < 3; ++a)
                 for (int b = 0; b < 3; ++b) {
-                    double s = 0.0;
+                    T s = 0;
                     for (int k = 0; k < 3; ++k) {
-                        double r = 0.0;
-                        for (int l = 0; l < 3; ++l) r += K(3 * k + a, 3 * l + b) * tcoef(l, j);
-                        s += tcoef(k, i) * r;
+                        T r = 0;
+                        for (int l = 0; l < 3; ++l) r += K(3 * k + a, 3 * l + b) * (T)tcoef(l, j);
+                        s += (T)tcoef(k, i) * r;
                     }
-                    H(3 * i + a, 3 * j + b) = s;
+                    out[12 * (3 * i + a) + 3 * j + b] = s;
                 }
 }
 
 // ---------------------------------------------------------------------------
-// kappa * e * b(d) for one stencil: value, gradient g12 and (PSD-projected)
-// Hessian in H (12x12 slot space); V is scratch for the projection.  Returns
+// kappa * e * b(d) for one stencil: value, gradient g12 and the Hessian of
+// e * b (without kappa, before projection) in H (12x12 slot space).  Returns
 // false when d >= dhat (inactive).  eps_x <= 0 disables the mollifier.
 // ---------------------------------------------------------------------------
 __device__ inline bool pair_barrier(const V3* x, bool is_ee, double dhat, double kappa, double eps_x,
-                                    double& E, double* g12, SMat<12> H, SMat<12> V, bool want_h) {
+                                    double& E, double* g12, SMat<12> H, bool want_h) {
     DistInfo di = classify(x, is_ee);
     double d = sqrt(di.d2);
     if (!(d < dhat)) return false;
@@ -457,7 +455,6 @@ __device__ inline bool pair_barrier(const V3* x, bool is_ee, double dhat, double
     }
     E = kappa * b;
     for (int i = 0; i < 12; ++i) g12[i] = kappa * gB[i];
-    if (want_h) project_translation_free(H, V, kappa);
     return true;
 }
 

@@ -75,6 +75,114 @@ __device__ inline bool nh_eval(const double* F, double mu, double lam, double& p
     return true;
 }
 
+// ---------------------------------------------------------------------------
+// PSD projection of the Neo-Hookean F-space Hessian from its analytic
+// eigensystem (isotropic energies: Smith, de Goes, Kim 2019).  With the SVD
+// F = U diag(s) V^T (det U = det V = 1, s > 0 since J > 0) and
+// Psi_i = dPsi/ds_i = mu s_i - c / s_i, c = mu - lam ln J:
+//   flip  (u_i v_j^T + u_j v_i^T)/sqrt2 : (Psi_i - Psi_j)/(s_i - s_j) = mu + c/(s_i s_j)
+//   twist (u_i v_j^T - u_j v_i^T)/sqrt2 : (Psi_i + Psi_j)/(s_i + s_j) = mu - c/(s_i s_j)
+//   scaling sum_i a_i u_i v_i^T, a an eigenvector of the 3x3
+//     A_ii = mu + (c + lam)/s_i^2, A_ij = lam/(s_i s_j)
+// H = sum_k max(lambda_k, 0) q_k q_k^T over the nine orthonormal q_k.
+// ---------------------------------------------------------------------------
+// symmetric 3x3 eigen-decomposition by cyclic Jacobi (a overwritten;
+// eigenvalues on its diagonal, eigenvectors in the columns of Q)
+template <class T>
+__device__ inline void sym3_eigen(T a[3][3], T Q[3][3]) {
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) Q[i][j] = i == j ? T(1) : T(0);
+    for (int sweep = 0; sweep < 12; ++sweep) {
+        T off = a[0][1] * a[0][1] + a[0][2] * a[0][2] + a[1][2] * a[1][2];
+        T dg = a[0][0] * a[0][0] + a[1][1] * a[1][1] + a[2][2] * a[2][2];
+        if (off <= Eps<T>::off2 * T(0.01) * dg) break;
+        for (int p = 0; p < 2; ++p)
+            for (int q = p + 1; q < 3; ++q) {
+                T apq = a[p][q];
+                if (apq == T(0)) continue;
+                T tau = (a[q][q] - a[p][p]) / (T(2) * apq);
+                T t = copysign(T(1), tau) / (fabs(tau) + sqrt(T(1) + tau * tau));
+                T cs = rsqrt(T(1) + t * t), sn = t * cs;
+                for (int k = 0; k < 3; ++k) {
+                    T akp = a[k][p], akq = a[k][q];
+                    a[k][p] = cs * akp - sn * akq;
+                    a[k][q] = sn * akp + cs * akq;
+                }
+                for (int k = 0; k < 3; ++k) {
+                    T apk = a[p][k], aqk = a[q][k];
+                    a[p][k] = cs * apk - sn * aqk;
+                    a[q][k] = sn * apk + cs * aqk;
+                }
+                for (int k = 0; k < 3; ++k) {
+                    T qkp = Q[k][p], qkq = Q[k][q];
+                    Q[k][p] = cs * qkp - sn * qkq;
+                    Q[k][q] = sn * qkp + cs * qkq;
+                }
+            }
+    }
+}
+
+// projected H_F into M (9x9, row-major vec(F) indices 3r + c), computed in T;
+// false if J <= 0
+template <class T>
+__device__ inline bool nh_hessian_projected(const double* Fd, double mu_d, double lam_d, SMat<9, T> M) {
+    double Jd = Fd[0] * (Fd[4] * Fd[8] - Fd[5] * Fd[7]) - Fd[1] * (Fd[3] * Fd[8] - Fd[5] * Fd[6]) +
+                Fd[2] * (Fd[3] * Fd[7] - Fd[4] * Fd[6]);
+    if (!(Jd > 0.0)) return false;
+    T F[9];
+    for (int i = 0; i < 9; ++i) F[i] = (T)Fd[i];
+    const T mu = (T)mu_d, lam = (T)lam_d;
+    // V, s from F^T F
+    T C[3][3], V[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) C[i][j] = F[i] * F[j] + F[3 + i] * F[3 + j] + F[6 + i] * F[6 + j];
+    sym3_eigen<T>(C, V);
+    T detV = V[0][0] * (V[1][1] * V[2][2] - V[1][2] * V[2][1]) - V[0][1] * (V[1][0] * V[2][2] - V[1][2] * V[2][0]) +
+             V[0][2] * (V[1][0] * V[2][1] - V[1][1] * V[2][0]);
+    if (detV < T(0))
+        for (int k = 0; k < 3; ++k) V[k][2] = -V[k][2];
+    T sg[3], U[3][3];
+    for (int i = 0; i < 3; ++i) sg[i] = sqrt(fmax(C[i][i], T(0)));
+    for (int i = 0; i < 3; ++i)
+        for (int r = 0; r < 3; ++r) U[r][i] = (F[3 * r] * V[0][i] + F[3 * r + 1] * V[1][i] + F[3 * r + 2] * V[2][i]) / sg[i];
+    T c = (T)(mu_d - lam_d * log(Jd));
+    for (int a = 0; a < 9; ++a)
+        for (int b = 0; b < 9; ++b) M(a, b) = T(0);
+    const T is2 = T(0.70710678118654752440);
+    // twist and flip modes of each pair (i, j)
+    for (int i = 0; i < 2; ++i)
+        for (int j = i + 1; j < 3; ++j) {
+            T ss = sg[i] * sg[j];
+            T lf = fmax(mu + c / ss, T(0)), lt = fmax(mu - c / ss, T(0));
+            if (lf == T(0) && lt == T(0)) continue;
+            T qf[9], qt[9];
+            for (int r = 0; r < 3; ++r)
+                for (int cc = 0; cc < 3; ++cc) {
+                    T x = U[r][i] * V[cc][j], y = U[r][j] * V[cc][i];
+                    qf[3 * r + cc] = is2 * (x + y);
+                    qt[3 * r + cc] = is2 * (x - y);
+                }
+            for (int a = 0; a < 9; ++a)
+                for (int b = 0; b < 9; ++b) M(a, b) += lf * qf[a] * qf[b] + lt * qt[a] * qt[b];
+        }
+    // scaling modes
+    T A[3][3], Qa[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) A[i][j] = i == j ? mu + (c + lam) / (sg[i] * sg[i]) : lam / (sg[i] * sg[j]);
+    sym3_eigen<T>(A, Qa);
+    for (int k = 0; k < 3; ++k) {
+        T lk = fmax(A[k][k], T(0));
+        if (lk == T(0)) continue;
+        T q[9];
+        for (int r = 0; r < 3; ++r)
+            for (int cc = 0; cc < 3; ++cc)
+                q[3 * r + cc] = Qa[0][k] * U[r][0] * V[cc][0] + Qa[1][k] * U[r][1] * V[cc][1] + Qa[2][k] * U[r][2] * V[cc][2];
+        for (int a = 0; a < 9; ++a)
+            for (int b = 0; b < 9; ++b) M(a, b) += lk * q[a] * q[b];
+    }
+    return true;
+}
+
 // D[v][c]: derivative of F_rc with respect to x_{v, r} (rows of Dm^-1; v = 0
 // gets minus their sum)
 __device__ __forceinline__ void dF_coef(const double* Dm, double D[4][3]) {
@@ -99,23 +207,26 @@ __device__ __forceinline__ void tet_F(const Geo& G, const double* x, int t, doub
 
 constexpr int EL_T = 64;
 
-// Elastic gradient and F-space-projected Hessian per tet: 16 blocks (3x3) of
-// h^2 V B^T P(H_F) B and 12 gradient entries h^2 V B^T vec(P) into staging.
-__global__ void __launch_bounds__(EL_T) k_elastic_gh(Geo G, const double* x, double* stage_blk, double* stage_g) {
-    extern __shared__ double sm[];
+// Elastic gradient (FP64) and F-space-projected Hessian (in T) per tet: 16
+// blocks (3x3) of h^2 V B^T P(H_F) B and 12 gradient entries h^2 V B^T vec(P)
+// into staging.
+template <class T>
+__global__ void __launch_bounds__(EL_T) k_elastic_gh(Geo G, const double* x, T* stage_blk, double* stage_g) {
+    extern __shared__ unsigned char smraw[];
+    T* sm = (T*)smraw;
     int t = blockIdx.x * EL_T + threadIdx.x;
     if (t >= G.n_tets) return;
-    SMat<9> H{sm + threadIdx.x, EL_T}, W{sm + 81 * EL_T + threadIdx.x, EL_T};
+    SMat<9, T> H{sm + threadIdx.x, EL_T};
     double F[9], P[9], psi;
-    int4 T;
-    tet_F(G, x, t, F, T);
-    if (!nh_eval(F, G.tmu[t], G.tlam[t], psi, P, &H)) {
+    int4 Tt;
+    tet_F(G, x, t, F, Tt);
+    if (!nh_eval(F, G.tmu[t], G.tlam[t], psi, P, nullptr)) {
         // inverted (never reached at an accepted iterate): zero contribution
-        for (int i = 0; i < 16 * 9; ++i) stage_blk[(size_t)t * 144 + i] = 0.0;
+        for (int i = 0; i < 16 * 9; ++i) stage_blk[(size_t)t * 144 + i] = T(0);
         for (int i = 0; i < 12; ++i) stage_g[(size_t)t * 12 + i] = 0.0;
         return;
     }
-    psd_project<9>(H, W);
+    nh_hessian_projected<T>(F, G.tmu[t], G.tlam[t], H);
     double D[4][3];
     dF_coef(G.Dminv + 9 * (size_t)t, D);
     double w = G.h * G.h * G.tvol[t];
@@ -125,18 +236,22 @@ __global__ void __launch_bounds__(EL_T) k_elastic_gh(Geo G, const double* x, dou
             for (int c = 0; c < 3; ++c) s += P[3 * r + c] * D[v][c];
             stage_g[(size_t)t * 12 + 3 * v + r] = w * s;
         }
+    T Dt[4][3];
+    for (int v = 0; v < 4; ++v)
+        for (int c = 0; c < 3; ++c) Dt[v][c] = (T)D[v][c];
+    T wt = (T)w;
     for (int v = 0; v < 4; ++v)
         for (int u = 0; u < 4; ++u) {
-            double* out = stage_blk + ((size_t)t * 16 + 4 * v + u) * 9;
+            T* out = stage_blk + ((size_t)t * 16 + 4 * v + u) * 9;
             for (int r = 0; r < 3; ++r)
                 for (int s = 0; s < 3; ++s) {
-                    double acc = 0.0;
+                    T acc = 0;
                     for (int c = 0; c < 3; ++c) {
-                        double inner = 0.0;
-                        for (int d = 0; d < 3; ++d) inner += H(3 * r + c, 3 * s + d) * D[u][d];
-                        acc += D[v][c] * inner;
+                        T inner = 0;
+                        for (int d = 0; d < 3; ++d) inner += H(3 * r + c, 3 * s + d) * Dt[u][d];
+                        acc += Dt[v][c] * inner;
                     }
-                    out[3 * r + s] = w * acc;
+                    out[3 * r + s] = wt * acc;
                 }
         }
 }
@@ -239,21 +354,24 @@ __global__ void k_affine_energy(Geo G, const double* x, const double* xhat, AffK
 
 constexpr int AF_T = 32;
 
-// gradient (directly into g, the body's nodes only) and 16 Hessian blocks
+// gradient (FP64, directly into g, the body's nodes only) and 16 Hessian
+// blocks (in T)
+template <class T>
 __global__ void __launch_bounds__(AF_T) k_affine_gh(Geo G, const double* x, const double* xhat, AffKin K,
-                                                    double* stage_blk, double* g) {
-    extern __shared__ double sm[];
+                                                    T* stage_blk, double* g) {
+    extern __shared__ unsigned char smraw[];
+    T* sm = (T*)smraw;
     int b = blockIdx.x * AF_T + threadIdx.x;
     if (b >= G.n_aff) return;
     int mode = G.aff_mode[b];
     int n0 = G.aff_node0[b];
-    double* blk = stage_blk + (size_t)b * 144;
-    for (int i = 0; i < 144; ++i) blk[i] = 0.0;
+    T* blk = stage_blk + (size_t)b * 144;
+    for (int i = 0; i < 144; ++i) blk[i] = T(0);
     if (mode == 1) {
         for (int j = 0; j < 4; ++j) st3(g + 3 * (size_t)(n0 + j), v3(0, 0, 0));
         return;
     }
-    SMat<9> H{sm + threadIdx.x, AF_T}, W{sm + 81 * AF_T + threadIdx.x, AF_T};
+    SMat<9, T> H{sm + threadIdx.x, AF_T}, W{sm + 81 * AF_T + threadIdx.x, AF_T};
     V3 c[4], ch[4];
     for (int j = 0; j < 4; ++j) {
         c[j] = ld3(x + 3 * (size_t)(n0 + j));
@@ -270,10 +388,10 @@ __global__ void __launch_bounds__(AF_T) k_affine_gh(Geo G, const double* x, cons
     }
     // inertia blocks: (0,0) m I ; (j,k) S_jk I
     auto blk_add_diag = [&](int j, int k, double v) {
-        double* o = blk + (4 * j + k) * 9;
-        o[0] += v;
-        o[4] += v;
-        o[8] += v;
+        T* o = blk + (4 * j + k) * 9;
+        o[0] += (T)v;
+        o[4] += (T)v;
+        o[8] += (T)v;
     };
     blk_add_diag(0, 0, m);
     for (int j = 0; j < 3; ++j)
@@ -299,12 +417,12 @@ __global__ void __launch_bounds__(AF_T) k_affine_gh(Geo G, const double* x, cons
                     double v = comp(c[1 + l], a) * comp(c[1 + i], bb);
                     if (a == bb) v += Gm[i][l];
                     if (i == l) v += CC[3 * a + bb];
-                    H(3 * i + a, 3 * l + bb) = 4.0 * w * v;
+                    H(3 * i + a, 3 * l + bb) = (T)(4.0 * w * v);
                 }
-    psd_project<9>(H, W);
+    psd_project<9, T>(H, W);
     for (int i = 0; i < 3; ++i)
         for (int l = 0; l < 3; ++l) {
-            double* o = blk + (4 * (1 + i) + (1 + l)) * 9;
+            T* o = blk + (4 * (1 + i) + (1 + l)) * 9;
             for (int a = 0; a < 3; ++a)
                 for (int bb = 0; bb < 3; ++bb) o[3 * a + bb] += H(3 * i + a, 3 * l + bb);
         }
@@ -343,22 +461,36 @@ __device__ __forceinline__ double pair_eps_x(const Geo& G, const PairRec& r) {
     return 1e-3 * dot(a, a) * dot(b, b);
 }
 
+// Shared memory per thread: the FP64 12x12 Hessian H, then the 9x9 K and its
+// scratch W in T (the projection's precision).
+template <class T>
+__host__ __device__ constexpr size_t barrier_smem_per_thread() {
+    return 144 * sizeof(double) + 162 * sizeof(T);
+}
+
+template <class T>
 __global__ void __launch_bounds__(BR_T) k_barrier_gh(Geo G, const double* X, const PairRec* rec, int n,
-                                                     const double* kappa_env, double* pH, double* pG) {
-    extern __shared__ double sm[];
+                                                     const double* kappa_env, T* pH, double* pG) {
+    extern __shared__ unsigned char smraw[];
+    int ld = blockDim.x;
+    double* shd = (double*)smraw;
+    T* sht = (T*)(smraw + 144 * sizeof(double) * ld);
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    int ld = blockDim.x;
-    SMat<12> H{sm + threadIdx.x, ld}, V{sm + 144 * ld + threadIdx.x, ld};
+    SMat<12> H{shd + threadIdx.x, ld};
+    SMat<9, T> K{sht + threadIdx.x, ld}, W{sht + 81 * ld + threadIdx.x, ld};
     PairRec r = rec[i];
     V3 x[4];
     for (int k = 0; k < 4; ++k) x[k] = ld3(X + 3 * (size_t)r.s[k]);
     double kap = kappa_env[G.sv_env[r.s[0]]];
     double E, g12[12];
-    bool act = pair_barrier(x, r.is_ee != 0, G.dhat, kap, pair_eps_x(G, r), E, g12, H, V, true);
+    bool act = pair_barrier(x, r.is_ee != 0, G.dhat, kap, pair_eps_x(G, r), E, g12, H, true);
     for (int a = 0; a < 12; ++a) pG[(size_t)i * 12 + a] = act ? g12[a] : 0.0;
-    for (int a = 0; a < 12; ++a)
-        for (int b = 0; b < 12; ++b) pH[(size_t)i * 144 + 12 * a + b] = act ? H(a, b) : 0.0;
+    T* out = pH + (size_t)i * 144;
+    if (act)
+        project_translation_free<T>(H, kap, K, W, out);
+    else
+        for (int a = 0; a < 144; ++a) out[a] = T(0);
 }
 
 // barrier energy over a pair list per env (ranges from env_off)
@@ -451,7 +583,8 @@ __global__ void k_friction_energy(Geo G, const double* X, const double* Xt, Lag 
 }
 
 // friction gradient and Hessian (PSD by construction) in stencil space
-__global__ void k_friction_gh(Geo G, const double* X, const double* Xt, Lag L, double* pH, double* pG) {
+template <class T>
+__global__ void k_friction_gh(Geo G, const double* X, const double* Xt, Lag L, T* pH, double* pG) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= L.n_pairs) return;
     double eh = G.eps_v * G.h;
@@ -477,13 +610,13 @@ __global__ void k_friction_gh(Geo G, const double* X, const double* Xt, Lag L, d
             HD[3 * a + b] = c * (a1 * ((a == b ? 1.0 : 0.0) - nv[a] * nv[b]) + a2 * uv[a] * uv[b]);
     }
     const double* w = L.w + (size_t)i * 4;
-    double* Ho = pH + (size_t)i * 144;
+    T* Ho = pH + (size_t)i * 144;
     double* Go = pG + (size_t)i * 12;
     for (int k = 0; k < 4; ++k)
         for (int a = 0; a < 3; ++a) {
             Go[3 * k + a] = w[k] * gD[a];
             for (int l = 0; l < 4; ++l)
-                for (int b = 0; b < 3; ++b) Ho[12 * (3 * k + a) + 3 * l + b] = w[k] * w[l] * HD[3 * a + b];
+                for (int b = 0; b < 3; ++b) Ho[12 * (3 * k + a) + 3 * l + b] = (T)(w[k] * w[l] * HD[3 * a + b]);
         }
 }
 

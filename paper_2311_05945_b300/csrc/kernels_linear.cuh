@@ -11,27 +11,29 @@ namespace zema {
 // Static part: values of the fixed pattern, gathered per block from the tet
 // and affine staging blocks in a fixed order (no atomics).
 // ---------------------------------------------------------------------------
-__global__ void k_static_values(Geo G, int n_blocks, const double* stage, double* S_val) {
+template <class T>
+__global__ void k_static_values(Geo G, int n_blocks, const T* stage, T* S_val) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= n_blocks) return;
-    double s[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    T s[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     for (int k = G.S_src_ptr[b]; k < G.S_src_ptr[b + 1]; ++k) {
-        const double* q = stage + 9 * (size_t)G.S_src[k];
+        const T* q = stage + 9 * (size_t)G.S_src[k];
         for (int i = 0; i < 9; ++i) s[i] += q[i];
     }
     for (int i = 0; i < 9; ++i) S_val[9 * (size_t)b + i] = s[i];
 }
 
 // diagonal blocks: + lumped mass (soft); fixed nodes become identity rows
-__global__ void k_static_diag(Geo G, const int* S_diag, double* S_val) {
+template <class T>
+__global__ void k_static_diag(Geo G, const int* S_diag, T* S_val) {
     int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= G.n_nodes) return;
-    double* o = S_val + 9 * (size_t)S_diag[n];
+    T* o = S_val + 9 * (size_t)S_diag[n];
     if (G.node_fixed[n]) {
-        for (int i = 0; i < 9; ++i) o[i] = (i % 4 == 0) ? 1.0 : 0.0;
+        for (int i = 0; i < 9; ++i) o[i] = (i % 4 == 0) ? T(1) : T(0);
         return;
     }
-    double m = G.node_mass[n];
+    T m = (T)G.node_mass[n];
     o[0] += m;
     o[4] += m;
     o[8] += m;
@@ -78,14 +80,15 @@ __global__ void k_contact_count(Geo G, const PairRec* rec, int n, uint32_t* cnt_
     cnt_g[i] = (uint32_t)P.m;
 }
 
-__global__ void k_contact_emit(Geo G, const PairRec* rec, int n, const double* pH, const double* pG,
+template <class T>
+__global__ void k_contact_emit(Geo G, const PairRec* rec, int n, const T* pH, const double* pG,
                                const uint32_t* off_blk, const uint32_t* off_g, uint64_t* bkey, uint32_t* bval,
-                               double* bstage, uint64_t* gkey, uint32_t* gval, double* gstage) {
+                               T* bstage, uint64_t* gkey, uint32_t* gval, double* gstage) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     PairNodes P;
     pair_nodes(G, rec[i], P);
-    const double* H = pH + (size_t)i * 144;
+    const T* H = pH + (size_t)i * 144;
     const double* gg = pG + (size_t)i * 12;
     uint32_t ob = off_blk[i], og = off_g[i];
     for (int a = 0; a < P.m; ++a) {
@@ -100,13 +103,13 @@ __global__ void k_contact_emit(Geo G, const PairRec* rec, int n, const double* p
         gval[j] = j;
         for (int r = 0; r < 3; ++r) gstage[3 * (size_t)j + r] = s[r];
         for (int b = 0; b < P.m; ++b) {
-            double B[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+            T B[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
             for (int k = 0; k < 4; ++k) {
-                double wa = P.W[a][k];
-                if (wa == 0.0) continue;
+                T wa = (T)P.W[a][k];
+                if (wa == T(0)) continue;
                 for (int l = 0; l < 4; ++l) {
-                    double f = wa * P.W[b][l];
-                    if (f == 0.0) continue;
+                    T f = wa * (T)P.W[b][l];
+                    if (f == T(0)) continue;
                     for (int r = 0; r < 3; ++r)
                         for (int c = 0; c < 3; ++c) B[3 * r + c] += f * H[12 * (3 * k + r) + 3 * l + c];
                 }
@@ -137,15 +140,15 @@ __global__ void k_seg_starts(const uint32_t* head, const uint32_t* hoff, uint32_
 }
 
 // sum W-wide values of each unique key in sorted order (deterministic)
-template <int W>
-__global__ void k_seg_sum(const uint32_t* seg, uint32_t nu, const uint32_t* perm, const double* stage, double* out,
+template <int W, class T>
+__global__ void k_seg_sum(const uint32_t* seg, uint32_t nu, const uint32_t* perm, const T* stage, T* out,
                           const uint64_t* key, uint64_t* ukey) {
     uint32_t u = blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= nu) return;
-    double s[W];
-    for (int q = 0; q < W; ++q) s[q] = 0.0;
+    T s[W];
+    for (int q = 0; q < W; ++q) s[q] = 0;
     for (uint32_t i = seg[u]; i < seg[u + 1]; ++i) {
-        const double* v = stage + (size_t)W * perm[i];
+        const T* v = stage + (size_t)W * perm[i];
         for (int q = 0; q < W; ++q) s[q] += v[q];
     }
     for (int q = 0; q < W; ++q) out[(size_t)W * u + q] = s[q];
@@ -182,27 +185,30 @@ __global__ void k_add_contact_grad(const uint64_t* ukey, const double* gsum, uin
 // Block-Jacobi preconditioner: inverse 3x3 diagonal block per soft node,
 // inverse 12x12 block per affine body.
 // ---------------------------------------------------------------------------
+template <class T>
 struct Bsr {
     const int* rowptr;
     const int* col;
-    const double* val;
+    const T* val;
 };
 
-__device__ __forceinline__ void add_row_blocks(const Bsr& A, int row, int c0, int c1, double* out, int ld, int roff) {
+template <class T>
+__device__ __forceinline__ void add_row_blocks(const Bsr<T>& A, int row, int c0, int c1, T* out, int ld, int roff) {
     for (int k = A.rowptr[row]; k < A.rowptr[row + 1]; ++k) {
         int c = A.col[k];
         if (c < c0 || c >= c1) continue;
-        const double* v = A.val + 9 * (size_t)k;
+        const T* v = A.val + 9 * (size_t)k;
         int co = 3 * (c - c0);
         for (int r = 0; r < 3; ++r)
             for (int q = 0; q < 3; ++q) out[(roff + r) * ld + co + q] += v[3 * r + q];
     }
 }
 
-__device__ inline void inv3(const double* a, double* o) {
-    double c00 = a[4] * a[8] - a[5] * a[7], c01 = a[5] * a[6] - a[3] * a[8], c02 = a[3] * a[7] - a[4] * a[6];
-    double det = a[0] * c00 + a[1] * c01 + a[2] * c02;
-    double id = 1.0 / det;
+template <class T>
+__device__ inline void inv3(const T* a, T* o) {
+    T c00 = a[4] * a[8] - a[5] * a[7], c01 = a[5] * a[6] - a[3] * a[8], c02 = a[3] * a[7] - a[4] * a[6];
+    T det = a[0] * c00 + a[1] * c01 + a[2] * c02;
+    T id = T(1) / det;
     o[0] = c00 * id;
     o[3] = c01 * id;
     o[6] = c02 * id;
@@ -214,49 +220,50 @@ __device__ inline void inv3(const double* a, double* o) {
     o[8] = (a[0] * a[4] - a[1] * a[3]) * id;
 }
 
-__global__ void k_precond(Geo G, Bsr S, Bsr C, double* Minv_s, double* Minv_a) {
+template <class T>
+__global__ void k_precond(Geo G, Bsr<T> S, Bsr<T> C, T* Minv_s, T* Minv_a) {
     int u = blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= G.n_units) return;
     int kind = G.unit_kind[u], idx = G.unit_idx[u];
     if (kind == 0) {
-        double a[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        T a[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
         add_row_blocks(S, idx, idx, idx + 1, a, 3, 0);
         add_row_blocks(C, idx, idx, idx + 1, a, 3, 0);
         inv3(a, Minv_s + 9 * (size_t)idx);
         return;
     }
     int n0 = G.aff_node0[idx];
-    double A[144];
-    for (int i = 0; i < 144; ++i) A[i] = 0.0;
+    T A[144];
+    for (int i = 0; i < 144; ++i) A[i] = 0;
     for (int j = 0; j < 4; ++j) {
         add_row_blocks(S, n0 + j, n0, n0 + 4, A, 12, 3 * j);
         add_row_blocks(C, n0 + j, n0, n0 + 4, A, 12, 3 * j);
     }
     // Gauss-Jordan inverse with partial pivoting (12x12, symmetric positive definite)
-    double I[144];
-    for (int i = 0; i < 144; ++i) I[i] = (i % 13 == 0) ? 1.0 : 0.0;
+    T I[144];
+    for (int i = 0; i < 144; ++i) I[i] = (i % 13 == 0) ? T(1) : T(0);
     for (int c = 0; c < 12; ++c) {
         int pv = c;
         for (int r = c + 1; r < 12; ++r)
             if (fabs(A[12 * r + c]) > fabs(A[12 * pv + c])) pv = r;
         if (pv != c)
             for (int j = 0; j < 12; ++j) {
-                double t = A[12 * c + j];
+                T t = A[12 * c + j];
                 A[12 * c + j] = A[12 * pv + j];
                 A[12 * pv + j] = t;
                 t = I[12 * c + j];
                 I[12 * c + j] = I[12 * pv + j];
                 I[12 * pv + j] = t;
             }
-        double ip = 1.0 / A[12 * c + c];
+        T ip = T(1) / A[12 * c + c];
         for (int j = 0; j < 12; ++j) {
             A[12 * c + j] *= ip;
             I[12 * c + j] *= ip;
         }
         for (int r = 0; r < 12; ++r) {
             if (r == c) continue;
-            double f = A[12 * r + c];
-            if (f == 0.0) continue;
+            T f = A[12 * r + c];
+            if (f == T(0)) continue;
             for (int j = 0; j < 12; ++j) {
                 A[12 * r + j] -= f * A[12 * c + j];
                 I[12 * r + j] -= f * I[12 * c + j];
@@ -281,176 +288,53 @@ __device__ __forceinline__ double sum_chunks(const double* part, int env) {
     return s;
 }
 
-__device__ __forceinline__ V3 spmv_row(const Bsr& A, int row, const double* p) {
+template <class T>
+__device__ __forceinline__ V3 spmv_row_warp(const Bsr<T>& A, int row, const double* p, int lane) {
     V3 y = v3(0, 0, 0);
-    for (int k = A.rowptr[row]; k < A.rowptr[row + 1]; ++k) {
-        const double* v = A.val + 9 * (size_t)k;
+    for (int k = A.rowptr[row] + lane; k < A.rowptr[row + 1]; k += 32) {
+        const T* v = A.val + 9 * (size_t)k;
         V3 pc = ld3(p + 3 * (size_t)A.col[k]);
-        y.x += v[0] * pc.x + v[1] * pc.y + v[2] * pc.z;
-        y.y += v[3] * pc.x + v[4] * pc.y + v[5] * pc.z;
-        y.z += v[6] * pc.x + v[7] * pc.y + v[8] * pc.z;
+        y.x += (double)v[0] * pc.x + (double)v[1] * pc.y + (double)v[2] * pc.z;
+        y.y += (double)v[3] * pc.x + (double)v[4] * pc.y + (double)v[5] * pc.z;
+        y.z += (double)v[6] * pc.x + (double)v[7] * pc.y + (double)v[8] * pc.z;
     }
     return y;
 }
 
 // apply the preconditioner of a unit to r, write z; returns (r.z, r.r)
-__device__ __forceinline__ void unit_precond(const Geo& G, int u, const double* Minv_s, const double* Minv_a,
+template <class T>
+__device__ __forceinline__ void unit_precond(const Geo& G, int u, const T* Minv_s, const T* Minv_a,
                                              const double* r, double* z, double& rz, double& rr) {
     int kind = G.unit_kind[u], idx = G.unit_idx[u];
     rz = 0.0;
     rr = 0.0;
     if (kind == 0) {
         V3 rv = ld3(r + 3 * (size_t)idx);
-        const double* M = Minv_s + 9 * (size_t)idx;
-        V3 zv = v3(M[0] * rv.x + M[1] * rv.y + M[2] * rv.z, M[3] * rv.x + M[4] * rv.y + M[5] * rv.z,
-                   M[6] * rv.x + M[7] * rv.y + M[8] * rv.z);
+        const T* M = Minv_s + 9 * (size_t)idx;
+        double m[9];
+        for (int q = 0; q < 9; ++q) m[q] = (double)M[q];
+        V3 zv = v3(m[0] * rv.x + m[1] * rv.y + m[2] * rv.z, m[3] * rv.x + m[4] * rv.y + m[5] * rv.z,
+                   m[6] * rv.x + m[7] * rv.y + m[8] * rv.z);
         st3(z + 3 * (size_t)idx, zv);
         rz = dot(rv, zv);
         rr = dot(rv, rv);
         return;
     }
     int n0 = G.aff_node0[idx];
-    const double* M = Minv_a + 144 * (size_t)idx;
+    const T* M = Minv_a + 144 * (size_t)idx;
     const double* rb = r + 3 * (size_t)n0;
     for (int i = 0; i < 12; ++i) {
         double s = 0.0;
-        for (int j = 0; j < 12; ++j) s += M[12 * i + j] * rb[j];
+        for (int j = 0; j < 12; ++j) s += (double)M[12 * i + j] * rb[j];
         z[3 * (size_t)n0 + i] = s;
         rz += rb[i] * s;
         rr += rb[i] * rb[i];
     }
 }
 
-// r = b, x = 0, z = M^-1 r; partials of r.z and b.b
-__global__ void k_pcg_init(Geo G, const double* b, PcgVec V, const double* Minv_s, const double* Minv_a,
-                           double* part_rz, double* part_bb) {
-    int env = blockIdx.y;
-    int u0 = G.env_unit_start[env], u1 = G.env_unit_start[env + 1];
-    __shared__ double sh[32];
-    double srz = 0.0, sbb = 0.0;
-    for (int u = u0 + blockIdx.x * blockDim.x + threadIdx.x; u < u1; u += gridDim.x * blockDim.x) {
-        int kind = G.unit_kind[u], idx = G.unit_idx[u];
-        int n0 = kind == 0 ? idx : G.aff_node0[idx], nn = kind == 0 ? 1 : 4;
-        for (int j = 0; j < 3 * nn; ++j) {
-            size_t o = 3 * (size_t)n0 + j;
-            V.r[o] = b[o];
-            V.x[o] = 0.0;
-        }
-        double rz, rr;
-        unit_precond(G, u, Minv_s, Minv_a, V.r, V.z, rz, rr);
-        for (int j = 0; j < 3 * nn; ++j) V.p[3 * (size_t)n0 + j] = V.z[3 * (size_t)n0 + j];
-        srz += rz;
-        sbb += rr;
-    }
-    double a = block_sum<kRedThreads>(srz, sh);
-    double c = block_sum<kRedThreads>(sbb, sh);
-    if (threadIdx.x == 0) {
-        part_rz[(size_t)env * kChunks + blockIdx.x] = a;
-        part_bb[(size_t)env * kChunks + blockIdx.x] = c;
-    }
-}
-
-// q = A p over the env's rows and partial p.q.  One warp per row: lanes
-// stride over the row's blocks and a fixed shuffle tree sums them, so rows
-// with hundreds of contact blocks (affine nodes) do not serialise one thread.
-__device__ __forceinline__ V3 spmv_row_warp(const Bsr& A, int row, const double* p, int lane) {
-    V3 y = v3(0, 0, 0);
-    for (int k = A.rowptr[row] + lane; k < A.rowptr[row + 1]; k += 32) {
-        const double* v = A.val + 9 * (size_t)k;
-        V3 pc = ld3(p + 3 * (size_t)A.col[k]);
-        y.x += v[0] * pc.x + v[1] * pc.y + v[2] * pc.z;
-        y.y += v[3] * pc.x + v[4] * pc.y + v[5] * pc.z;
-        y.z += v[6] * pc.x + v[7] * pc.y + v[8] * pc.z;
-    }
-    return y;
-}
-
-__global__ void k_pcg_spmv(Geo G, Bsr S, Bsr C, PcgVec V, const int* conv, double* part_pq) {
-    int env = blockIdx.y;
-    __shared__ double sh[32];
-    double s = 0.0;
-    if (!conv[env]) {
-        int lane = threadIdx.x & 31;
-        int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-        int nwarps = (gridDim.x * blockDim.x) >> 5;
-        int n0 = G.env_node_start[env], n1 = G.env_node_start[env + 1];
-        for (int n = n0 + warp; n < n1; n += nwarps) {
-            V3 y = spmv_row_warp(S, n, V.p, lane) + spmv_row_warp(C, n, V.p, lane);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                y.x += __shfl_xor_sync(0xffffffffu, y.x, o);
-                y.y += __shfl_xor_sync(0xffffffffu, y.y, o);
-                y.z += __shfl_xor_sync(0xffffffffu, y.z, o);
-            }
-            if (lane == 0) {
-                st3(V.q + 3 * (size_t)n, y);
-                s += dot(y, ld3(V.p + 3 * (size_t)n));
-            }
-        }
-    }
-    double t = block_sum<kRedThreads>(s, sh);
-    if (threadIdx.x == 0) part_pq[(size_t)env * kChunks + blockIdx.x] = t;
-}
-
-// alpha = rz / pq; x += alpha p; r -= alpha q; z = M^-1 r; partial r.z, r.r
-__global__ void k_pcg_update(Geo G, PcgVec V, const double* Minv_s, const double* Minv_a, const int* conv,
-                             const double* part_rz_old, const double* part_pq, double* part_rz, double* part_rr) {
-    int env = blockIdx.y;
-    __shared__ double sh[32];
-    double srz = 0.0, srr = 0.0;
-    if (!conv[env]) {
-        double pq = sum_chunks(part_pq, env);
-        double alpha = pq > 0.0 ? sum_chunks(part_rz_old, env) / pq : 0.0;
-        int u0 = G.env_unit_start[env], u1 = G.env_unit_start[env + 1];
-        for (int u = u0 + blockIdx.x * blockDim.x + threadIdx.x; u < u1; u += gridDim.x * blockDim.x) {
-            int kind = G.unit_kind[u], idx = G.unit_idx[u];
-            int n0 = kind == 0 ? idx : G.aff_node0[idx], nn = kind == 0 ? 1 : 4;
-            for (int j = 0; j < 3 * nn; ++j) {
-                size_t o = 3 * (size_t)n0 + j;
-                V.x[o] += alpha * V.p[o];
-                V.r[o] -= alpha * V.q[o];
-            }
-            double rz, rr;
-            unit_precond(G, u, Minv_s, Minv_a, V.r, V.z, rz, rr);
-            srz += rz;
-            srr += rr;
-        }
-    }
-    double a = block_sum<kRedThreads>(srz, sh);
-    double c = block_sum<kRedThreads>(srr, sh);
-    if (threadIdx.x == 0) {
-        part_rz[(size_t)env * kChunks + blockIdx.x] = a;
-        part_rr[(size_t)env * kChunks + blockIdx.x] = c;
-    }
-}
-
-// beta = rz_new / rz_old; p = z + beta p; convergence |r| <= tol |b|
-__global__ void k_pcg_dir(Geo G, PcgVec V, int* conv, int* iters, const double* part_rz_old,
-                          const double* part_rz, const double* part_rr, const double* part_bb, double tol2) {
-    int env = blockIdx.y;
-    if (conv[env]) return;
-    double rr = sum_chunks(part_rr, env), bb = sum_chunks(part_bb, env);
-    bool done = !(rr > tol2 * bb);
-    if (!done) {
-        double rzo = sum_chunks(part_rz_old, env);
-        double beta = rzo != 0.0 ? sum_chunks(part_rz, env) / rzo : 0.0;
-        int n0 = G.env_node_start[env], n1 = G.env_node_start[env + 1];
-        for (int n = n0 + blockIdx.x * blockDim.x + threadIdx.x; n < n1; n += gridDim.x * blockDim.x)
-            for (int j = 0; j < 3; ++j) {
-                size_t o = 3 * (size_t)n + j;
-                V.p[o] = V.z[o] + beta * V.p[o];
-            }
-    }
-    __syncthreads();
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        iters[env] += 1;
-        if (done) conv[env] = 1;
-    }
-}
-
 // ---------------------------------------------------------------------------
 // Persistent PCG: one cooperative launch runs the whole solve.  Work is cut
-// into tiles (contiguous units of one environment, <= 64 units); blocks loop
+// into tiles (contiguous units of one environment, a few each); blocks loop
 // over tiles, write one partial sum per tile, and after each grid-wide
 // barrier every block recombines the partials of each environment in tile
 // order (identical in all blocks, so alpha, beta and the stop test agree
@@ -468,13 +352,14 @@ struct Tiles {
     const int* env_start;  // n_envs + 1 tile offsets
 };
 
+template <class Real>
 struct PcgArgs {
     Geo G;
-    Bsr S, C;
+    Bsr<Real> S, C;
     PcgVec V;
     const double* b;
-    const double* Minv_s;
-    const double* Minv_a;
+    const Real* Minv_s;
+    const Real* Minv_a;
     Tiles T;
     double* pt_rz;   // per-tile partials
     double* pt_rz2;
@@ -496,7 +381,8 @@ __device__ __forceinline__ void env_sums(const Tiles& T, const double* part, int
     }
 }
 
-__global__ void __launch_bounds__(256) k_pcg_persistent(PcgArgs a) {
+template <class Real>
+__global__ void __launch_bounds__(256) k_pcg_persistent(PcgArgs<Real> a) {
     namespace cg = cooperative_groups;
     cg::grid_group grid = cg::this_grid();
     extern __shared__ double sm[];

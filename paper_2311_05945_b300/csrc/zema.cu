@@ -88,7 +88,7 @@ struct zema_scene {
     DBuf<int> conv, pcg_iters, need, capflag;
     DBuf<int> tile_u0, tile_u1, tile_n0, tile_n1, tile_env, env_tile_start;
     DBuf<double> pt_a, pt_b, pt_c, pt_d, pt_e;
-    int n_tiles = 0, pcg_grid = 0;
+    int n_tiles = 0, pcg_grid = 0, pcg_grid_f = 0;
     DBuf<double> tolv;
     // pair lists
     BroadPhase bp;
@@ -446,12 +446,14 @@ void build(zema_scene* s) {
     }
     env_unit_start[NE] = (int)unit_kind_h.size();
     s->n_units = (int)unit_kind_h.size();
-    // PCG tiles: <= 64 consecutive units of one env and their node range
+    // PCG tiles: <= kTileUnits consecutive units of one env and their node
+    // range (small tiles: the solve's blocks each own a few rows)
+    const int kTileUnits = 16;
     std::vector<int> tu0, tu1, tn0, tn1, tenv, etile(NE + 1, 0);
     for (int e = 0; e < NE; ++e) {
         etile[e] = (int)tu0.size();
-        for (int u = env_unit_start[e]; u < env_unit_start[e + 1]; u += 64) {
-            int ue = std::min(u + 64, env_unit_start[e + 1]);
+        for (int u = env_unit_start[e]; u < env_unit_start[e + 1]; u += kTileUnits) {
+            int ue = std::min(u + kTileUnits, env_unit_start[e + 1]);
             auto first_node = [&](int uu) {
                 return unit_kind_h[uu] == 0 ? unit_idx_h[uu] : s->aff_node0_h[aff_perm[unit_idx_h[uu]]];
             };
@@ -771,9 +773,14 @@ void build(zema_scene* s) {
     G.S_src_ptr = s->S_src_ptr.p;
     G.S_src = s->S_src.p;
     // dynamic shared memory opt-in for the per-thread matrix kernels
-    ZCHECK(cudaFuncSetAttribute(k_elastic_gh, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 81 * EL_T * 8));
-    ZCHECK(cudaFuncSetAttribute(k_barrier_gh, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 144 * BR_T * 8));
-    ZCHECK(cudaFuncSetAttribute(k_affine_gh, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 81 * AF_T * 8));
+    ZCHECK(cudaFuncSetAttribute(k_elastic_gh<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 81 * EL_T * 8));
+    ZCHECK(cudaFuncSetAttribute(k_elastic_gh<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 81 * EL_T * 4));
+    ZCHECK(cudaFuncSetAttribute(k_barrier_gh<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(barrier_smem_per_thread<double>() * BR_T)));
+    ZCHECK(cudaFuncSetAttribute(k_barrier_gh<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(barrier_smem_per_thread<float>() * BR_T)));
+    ZCHECK(cudaFuncSetAttribute(k_affine_gh<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 81 * AF_T * 8));
+    ZCHECK(cudaFuncSetAttribute(k_affine_gh<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 81 * AF_T * 4));
     ZCHECK(cudaStreamSynchronize(st));
     s->finalized = true;
 }
@@ -875,26 +882,31 @@ void energy(zema_scene* s, const double* xe, const PairRec* pairs, const uint32_
 // ---------------------------------------------------------------------------
 // Gradient and Hessian assembly at x; g and the BSR (S, C) are filled.
 // ---------------------------------------------------------------------------
-void grad_hess(zema_scene* s, bool barrier = true, bool friction = true, bool hess = true) {
+// Hessian blocks, staging, BSR values and preconditioner in T (double: FP64
+// path; float: mixed path), gradients always FP64.
+template <class T>
+void grad_hess_t(zema_scene* s, bool barrier, bool friction, bool hess) {
     cudaStream_t st = s->st;
+    T* stage = (T*)s->stage_blk.p;
+    T* S_val = (T*)s->S_val.p;
     Geo& G = s->G;
     Allocator* A = &s->A;
     // per tet: indices 16 B, Dm^-1 72 B, volume and Lame 24 B, positions 96 B
     // in; 16 blocks 1152 B and gradient 96 B out
     alg_bytes_hint(1456.0 * s->n_tets);
     if (s->n_tets)
-        ZL(k_elastic_gh, div_up(s->n_tets, EL_T), EL_T, 2 * 81 * EL_T * 8, st)(G, s->x.p, s->stage_blk.p, s->stage_g.p);
+        ZL(k_elastic_gh<T>, div_up(s->n_tets, EL_T), EL_T, 81 * EL_T * sizeof(T), st)(G, s->x.p, stage, s->stage_g.p);
     ZLAUNCH();
     ZCHECK(cudaMemsetAsync(s->g.p, 0, 3 * (size_t)s->n_nodes * sizeof(double), st));
     if (s->n_aff)
-        ZL(k_affine_gh, div_up(s->n_aff, AF_T), AF_T, 2 * 81 * AF_T * 8, st)(
-            G, s->x.p, s->xhat.p, kin(s), s->stage_blk.p + 144 * (size_t)s->n_tets, s->g.p);
+        ZL(k_affine_gh<T>, div_up(s->n_aff, AF_T), AF_T, 2 * 81 * AF_T * sizeof(T), st)(
+            G, s->x.p, s->xhat.p, kin(s), stage + 144 * (size_t)s->n_tets, s->g.p);
     ZLAUNCH();
     ZL(k_soft_grad, div_up(s->n_nodes, TB), TB, 0, st)(G, s->x.p, s->xhat.p, s->stage_g.p, s->g.p);
     ZLAUNCH();
     if (hess) {
-        ZL(k_static_values, div_up(s->n_sblocks, TB), TB, 0, st)(G, s->n_sblocks, s->stage_blk.p, s->S_val.p);
-        ZL(k_static_diag, div_up(s->n_nodes, TB), TB, 0, st)(G, s->S_diag.p, s->S_val.p);
+        ZL(k_static_values<T>, div_up(s->n_sblocks, TB), TB, 0, st)(G, s->n_sblocks, stage, S_val);
+        ZL(k_static_diag<T>, div_up(s->n_nodes, TB), TB, 0, st)(G, s->S_diag.p, S_val);
         ZLAUNCH();
     }
     // contact records: active barrier pairs then lagged friction pairs
@@ -902,16 +914,17 @@ void grad_hess(zema_scene* s, bool barrier = true, bool friction = true, bool he
     uint32_t nr = na + nl;
     s->pH.ensure(A, 144 * (size_t)nr + 144);
     s->pG.ensure(A, 12 * (size_t)nr + 12);
+    T* pH = (T*)s->pH.p;
     if (na) {
         // latency-bound FP64 work: few pairs are spread over many SMs
         int bt = BR_T;
         while (bt > 4 && (long long)div_up(na, bt) < 2 * 148) bt >>= 1;
-        ZL(k_barrier_gh, div_up(na, bt), bt, 2 * 144 * bt * 8, st)(G, s->X.p, s->act.p, (int)na, s->kappa.p, s->pH.p,
-                                                                    s->pG.p);
+        ZL(k_barrier_gh<T>, div_up(na, bt), bt, barrier_smem_per_thread<T>() * bt, st)(G, s->X.p, s->act.p, (int)na,
+                                                                                         s->kappa.p, pH, s->pG.p);
     }
     if (nl)
-        ZL(k_friction_gh, div_up(nl, 128), 128, 0, st)(G, s->X.p, s->Xt.p, lagv(s), s->pH.p + 144 * (size_t)na,
-                                                        s->pG.p + 12 * (size_t)na);
+        ZL(k_friction_gh<T>, div_up(nl, 128), 128, 0, st)(G, s->X.p, s->Xt.p, lagv(s), pH + 144 * (size_t)na,
+                                                           s->pG.p + 12 * (size_t)na);
     ZLAUNCH();
     // one record list: act then lag
     DBuf<PairRec>& recs = s->swept;  // reuse as scratch for the concatenation
@@ -949,9 +962,9 @@ void grad_hess(zema_scene* s, bool barrier = true, bool friction = true, bool he
     s->gval.ensure(A, ng + 1);
     s->gval2.ensure(A, ng + 1);
     s->gstage.ensure(A, 3 * (size_t)ng + 3);
-    ZL(k_contact_emit, div_up(nr, 128), 128, 0, st)(G, recs.p, (int)nr, s->pH.p, s->pG.p, s->off_blk.p, s->off_g.p,
-                                                     s->bkey.p, s->bval.p, s->bstage.p, s->gkey.p, s->gval.p,
-                                                     s->gstage.p);
+    ZL(k_contact_emit<T>, div_up(nr, 128), 128, 0, st)(G, recs.p, (int)nr, pH, s->pG.p, s->off_blk.p, s->off_g.p,
+                                                        s->bkey.p, s->bval.p, (T*)s->bstage.p, s->gkey.p, s->gval.p,
+                                                        s->gstage.p);
     ZLAUNCH();
     int nbits_node = 1;
     while ((1ll << nbits_node) < (long long)s->n_nodes) ++nbits_node;
@@ -972,7 +985,8 @@ void grad_hess(zema_scene* s, bool barrier = true, bool friction = true, bool he
     uint32_t nu = s->h32[2];
     s->C_val.ensure(A, 9 * (size_t)nu + 9);
     s->C_col.ensure(A, nu + 1);
-    ZL(k_seg_sum<9>, div_up(nu, 128), 128, 0, st)(s->seg.p, nu, s->bval.p, s->bstage.p, s->C_val.p, s->bkey.p, s->ukey.p);
+    ZL((k_seg_sum<9, T>), div_up(nu, 128), 128, 0, st)(s->seg.p, nu, s->bval.p, (const T*)s->bstage.p, (T*)s->C_val.p,
+                                                        s->bkey.p, s->ukey.p);
     ZL(k_contact_rows, div_up(s->n_nodes + 1, TB), TB, 0, st)(s->ukey.p, nu, s->n_nodes, s->C_rowptr.p, s->C_col.p);
     ZLAUNCH();
     s->n_cblocks = nu;
@@ -984,35 +998,46 @@ void grad_hess(zema_scene* s, bool barrier = true, bool friction = true, bool he
     ZCHECK(cudaStreamSynchronize(st));
     uint32_t nug = s->h32[3];
     s->gsum.ensure(A, 3 * (size_t)nug + 3);
-    ZL(k_seg_sum<3>, div_up(nug, 128), 128, 0, st)(s->seg.p, nug, s->gval.p, s->gstage.p, s->gsum.p, s->gkey.p, s->ukey.p);
+    ZL((k_seg_sum<3, double>), div_up(nug, 128), 128, 0, st)(s->seg.p, nug, s->gval.p, s->gstage.p, s->gsum.p,
+                                                              s->gkey.p, s->ukey.p);
     ZL(k_add_contact_grad, div_up(nug, 128), 128, 0, st)(s->ukey.p, s->gsum.p, nug, s->g.p);
     ZLAUNCH();
+}
+
+void grad_hess(zema_scene* s, bool barrier = true, bool friction = true, bool hess = true) {
+    if (s->P.precision == 1)
+        grad_hess_t<float>(s, barrier, friction, hess);
+    else
+        grad_hess_t<double>(s, barrier, friction, hess);
 }
 
 // ---------------------------------------------------------------------------
 // PCG: solve (S + C) p = -g for every env not flagged in done_h (one
 // persistent cooperative launch per solve)
 // ---------------------------------------------------------------------------
-int64_t pcg(zema_scene* s, const std::vector<int>& done_h) {
+template <class T>
+int64_t pcg_t(zema_scene* s, const std::vector<int>& done_h) {
     cudaStream_t st = s->st;
     Geo& G = s->G;
     int NE = s->n_envs;
-    Bsr S{s->S_rowptr.p, s->S_col.p, s->S_val.p};
-    Bsr C{s->C_rowptr.p, s->C_col.p, s->C_val.p};
-    ZL(k_precond, div_up(s->n_units, 128), 128, 0, st)(G, S, C, s->Minv_s.p, s->Minv_a.p);
+    Bsr<T> S{s->S_rowptr.p, s->S_col.p, (const T*)s->S_val.p};
+    Bsr<T> C{s->C_rowptr.p, s->C_col.p, (const T*)s->C_val.p};
+    T* Minv_s = (T*)s->Minv_s.p;
+    T* Minv_a = (T*)s->Minv_a.p;
+    ZL(k_precond<T>, div_up(s->n_units, 128), 128, 0, st)(G, S, C, Minv_s, Minv_a);
     ZL(k_negate, div_up(3 * (size_t)s->n_nodes, TB), TB, 0, st)(s->g.p, s->b.p, 3 * (size_t)s->n_nodes);
     ZLAUNCH();
     for (int e = 0; e < NE; ++e) s->hi[e] = done_h[e];
     ZCHECK(cudaMemcpyAsync(s->conv.p, s->hi, NE * sizeof(int), cudaMemcpyHostToDevice, st));
     ZCHECK(cudaMemsetAsync(s->pcg_iters.p, 0, NE * sizeof(int), st));
-    PcgArgs a;
+    PcgArgs<T> a;
     a.G = G;
     a.S = S;
     a.C = C;
     a.V = PcgVec{s->p.p, s->r.p, s->z.p, s->pp.p, s->q.p};
     a.b = s->b.p;
-    a.Minv_s = s->Minv_s.p;
-    a.Minv_a = s->Minv_a.p;
+    a.Minv_s = Minv_s;
+    a.Minv_a = Minv_a;
     a.T = Tiles{s->n_tiles, s->tile_u0.p, s->tile_u1.p, s->tile_n0.p, s->tile_n1.p, s->tile_env.p, s->env_tile_start.p};
     a.pt_rz = s->pt_a.p;
     a.pt_rz2 = s->pt_b.p;
@@ -1024,19 +1049,20 @@ int64_t pcg(zema_scene* s, const std::vector<int>& done_h) {
     a.tol2 = s->P.pcg_rel_tol * s->P.pcg_rel_tol;
     a.max_iter = s->P.max_pcg;
     size_t smem = 4 * (size_t)NE * sizeof(double) + (size_t)NE * sizeof(int);
-    if (s->pcg_grid == 0) {
+    int& grid = s->P.precision == 1 ? s->pcg_grid_f : s->pcg_grid;
+    if (grid == 0) {
         int dev = 0, nsm = 0, per = 0;
         ZCHECK(cudaGetDevice(&dev));
         ZCHECK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
         if (smem > 48 * 1024)
-            ZCHECK(cudaFuncSetAttribute(k_pcg_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        ZCHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg_persistent, 256, smem));
-        s->pcg_grid = std::max(1, std::min(s->n_tiles, per * nsm));
+            ZCHECK(cudaFuncSetAttribute(k_pcg_persistent<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        ZCHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg_persistent<T>, 256, smem));
+        grid = std::max(1, std::min(s->n_tiles, per * nsm));
     }
     void* args[] = {&a};
     {
         LaunchScope ls("k_pcg_persistent");
-        ZCHECK(cudaLaunchCooperativeKernel((const void*)k_pcg_persistent, dim3(s->pcg_grid), dim3(256), args, smem, st));
+        ZCHECK(cudaLaunchCooperativeKernel((const void*)k_pcg_persistent<T>, dim3(grid), dim3(256), args, smem, st));
     }
     ZLAUNCH();
     ZCHECK(cudaMemcpyAsync(s->hi, s->pcg_iters.p, NE * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1047,14 +1073,15 @@ int64_t pcg(zema_scene* s, const std::vector<int>& done_h) {
         mx = std::max<int64_t>(mx, s->hi[e]);
     }
     // Algorithmic bytes of the solve for the live roofline, per iteration:
-    // SpMV reads every block (72 B values + 4 B column), both row-pointer
+    // SpMV reads every block (9 values + 4 B column), both row-pointer
     // arrays, p, and writes q; the update reads/writes x and r, reads p and q,
-    // writes z, reads the preconditioner (72 B per soft node, 1152 B per
+    // writes z, reads the preconditioner (9 values per soft node, 144 per
     // affine body); the direction update reads z and reads/writes p.
     {
         double nn = s->n_nodes;
-        double per_it = 76.0 * ((double)s->n_sblocks + (double)s->n_cblocks) + nn * (8.0 + 48.0 + 168.0 + 72.0) +
-                        72.0 * (nn - 4.0 * s->n_aff) + 1152.0 * s->n_aff;
+        double bs = 9.0 * sizeof(T) + 4.0;  // one stored block and its column index
+        double per_it = bs * ((double)s->n_sblocks + (double)s->n_cblocks) + nn * (8.0 + 48.0 + 168.0 + 72.0) +
+                        9.0 * sizeof(T) * (nn - 4.0 * s->n_aff) + 144.0 * sizeof(T) * s->n_aff;
         alg_bytes_add("k_pcg_persistent", per_it * (double)tot / std::max(1, NE));
     }
     // done envs: zero direction
@@ -1063,6 +1090,10 @@ int64_t pcg(zema_scene* s, const std::vector<int>& done_h) {
     ZL(k_mask_env, div_up(s->n_nodes, TB), TB, 0, st)(G, s->p.p, s->need.p);
     ZLAUNCH();
     return tot;
+}
+
+int64_t pcg(zema_scene* s, const std::vector<int>& done_h) {
+    return s->P.precision == 1 ? pcg_t<float>(s, done_h) : pcg_t<double>(s, done_h);
 }
 
 // per-env max step component -> s->hd
@@ -1874,19 +1905,24 @@ __global__ void k_sv_env_of(const int* sv_body, const int* b_env, int n, int* sv
 __global__ void __launch_bounds__(BR_T) k_local_barrier(const double* x12, const int* is_ee, const double* eps_x,
                                                         int n, double dhat, double* e_out, double* g_out,
                                                         double* H_out) {
-    extern __shared__ double sm[];
-    int i = blockIdx.x * BR_T + threadIdx.x;
+    extern __shared__ unsigned char smraw[];
+    int ld = blockDim.x;
+    double* shd = (double*)smraw;
+    double* sht = (double*)(smraw + 144 * sizeof(double) * ld);
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    SMat<12> H{sm + threadIdx.x, BR_T}, V{sm + 144 * BR_T + threadIdx.x, BR_T};
+    SMat<12> H{shd + threadIdx.x, ld};
+    SMat<9, double> K{sht + threadIdx.x, ld}, W{sht + 81 * ld + threadIdx.x, ld};
     V3 x[4];
     for (int k = 0; k < 4; ++k) x[k] = ld3(x12 + 12 * (size_t)i + 3 * k);
     double E = 0.0, g[12];
-    bool act = pair_barrier(x, is_ee[i] != 0, dhat, 1.0, eps_x[i], E, g, H, V, true);
+    bool act = pair_barrier(x, is_ee[i] != 0, dhat, 1.0, eps_x[i], E, g, H, true);
     e_out[i] = act ? E : 0.0;
-    for (int a = 0; a < 12; ++a) {
-        g_out[12 * (size_t)i + a] = act ? g[a] : 0.0;
-        for (int b = 0; b < 12; ++b) H_out[144 * (size_t)i + 12 * a + b] = act ? H(a, b) : 0.0;
-    }
+    for (int a = 0; a < 12; ++a) g_out[12 * (size_t)i + a] = act ? g[a] : 0.0;
+    if (act)
+        project_translation_free<double>(H, 1.0, K, W, H_out + 144 * (size_t)i);
+    else
+        for (int a = 0; a < 144; ++a) H_out[144 * (size_t)i + a] = 0.0;
 }
 
 __global__ void k_local_distance(const double* x12, const int* is_ee, int n, double* d2, double* w) {
@@ -1904,13 +1940,13 @@ __global__ void __launch_bounds__(EL_T) k_local_nh(const double* F9, int n, doub
     extern __shared__ double sm[];
     int i = blockIdx.x * EL_T + threadIdx.x;
     if (i >= n) return;
-    SMat<9> M{sm + threadIdx.x, EL_T}, W{sm + 81 * EL_T + threadIdx.x, EL_T};
+    SMat<9> M{sm + threadIdx.x, EL_T};
     double P[9], ps;
-    if (!nh_eval(F9 + 9 * (size_t)i, mu, lam, ps, P, &M)) {
+    if (!nh_eval(F9 + 9 * (size_t)i, mu, lam, ps, P, nullptr)) {
         psi[i] = INFINITY;
         return;
     }
-    psd_project<9>(M, W);
+    nh_hessian_projected<double>(F9 + 9 * (size_t)i, mu, lam, M);
     psi[i] = ps;
     for (int a = 0; a < 9; ++a) {
         g[9 * (size_t)i + a] = P[a];
@@ -2031,8 +2067,9 @@ zema_status zema_local_barrier(int64_t n, const double* x12, const int32_t* is_e
         double* E = T.put<double>(nullptr, (size_t)n);
         double* g = T.put<double>(nullptr, 12 * (size_t)n);
         double* H = T.put<double>(nullptr, 144 * (size_t)n);
-        ZCHECK(cudaFuncSetAttribute(k_local_barrier, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 144 * BR_T * 8));
-        ZL(k_local_barrier, div_up(n, BR_T), BR_T, 2 * 144 * BR_T * 8, st)(dx, de, dp, (int)n, dhat, E, g, H);
+        size_t sm = barrier_smem_per_thread<double>() * BR_T;
+        ZCHECK(cudaFuncSetAttribute(k_local_barrier, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        ZL(k_local_barrier, div_up(n, BR_T), BR_T, sm, st)(dx, de, dp, (int)n, dhat, E, g, H);
         ZLAUNCH();
         get(e_out, E, n, st);
         get(g_out, g, 12 * n, st);

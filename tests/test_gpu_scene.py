@@ -159,3 +159,50 @@ def test_deterministic_rerun():
     a.step(6)
     b.step(6)
     assert np.array_equal(positions(a, sc), positions(b, sc))
+
+
+# ---------------------------------------------------------------------------
+# Mixed precision (FP32 Hessians, stored matrices and preconditioner; FP64
+# gradients, energies, distances, barrier log term, ACCD and convergence):
+# the minimiser is still defined by the FP64 gradient, so the same bounds
+# against the FP64 oracle apply.
+# ---------------------------------------------------------------------------
+def test_mixed_one_step_parity_c1_tight():
+    sc = S.scene_c1()
+    orc = Oracle(sc, tol_scale=1e-2)
+    orc.step(12)
+    gpu = gpu_scene(sc, tol_scale=1e-2, precision=1)
+    transplant(orc, gpu, sc)
+    orc.step(1)
+    gpu.step(1)
+    diag = orc.diag()
+    err = max(np.abs(positions(orc, sc) - positions(gpu, sc)).max(),
+              np.abs(affine_vertex_positions(orc, sc) - affine_vertex_positions(gpu, sc)).max())
+    assert err < 1e-5 * diag, err / diag
+
+
+@pytest.mark.parametrize("name,n_steps", [("tiny", 15), ("c1", 25)])
+def test_mixed_trajectory_parity_tight(name, n_steps):
+    sc = S.scene_tiny_contact(mu=0.5) if name == "tiny" else S.scene_c1()
+    orc = Oracle(sc, tol_scale=1e-2)
+    gpu = gpu_scene(sc, tol_scale=1e-2, precision=1)
+    diag = orc.diag()
+    worst = 0.0
+    for k in range(n_steps):
+        orc.step(1)
+        st = gpu.step(1)
+        err = max(np.abs(orc.tet_positions(0) - gpu.tet_positions(0)).max(),
+                  np.abs(affine_vertex_positions(orc, sc) - affine_vertex_positions(gpu, sc)).max())
+        worst = max(worst, err)
+        assert err < 1e-5 * diag, (k, err / diag)
+        assert st["dmin"] > 0
+    print(f"mixed precision {name}: worst position error vs FP64 oracle {worst / diag:.2e} x bbox diagonal")
+
+
+def test_mixed_deterministic_rerun():
+    sc = S.scene_tiny_contact(mu=0.5)
+    a = gpu_scene(sc, precision=1)
+    b = gpu_scene(sc, precision=1)
+    a.step(6)
+    b.step(6)
+    assert np.array_equal(positions(a, sc), positions(b, sc))
