@@ -85,7 +85,7 @@ __device__ __forceinline__ double box_cells(const Box6& b, double inv) {
 
 // kind: 0 points, 1 edges, 2 tris.  For edges and tris also the grid entry
 // count (0 when oversize) and the oversize flag.
-__global__ void k_boxes(BPView v, int kind, int n, double* box, uint32_t* cnt, uint32_t* big) {
+__global__ void k_boxes(BPView v, int kind, int n, double* box, int* cb, uint32_t* cnt, uint32_t* big) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int ids[3];
@@ -109,6 +109,10 @@ __global__ void k_boxes(BPView v, int kind, int n, double* box, uint32_t* cnt, u
     for (int k = 0; k < 3; ++k) {
         box[6 * (size_t)i + k] = b.lo[k];
         box[6 * (size_t)i + 3 + k] = b.hi[k];
+        // integer cell range (the cell of a coordinate is monotone in it, so
+        // the cell of max(lo_a, lo_b) is max(cell(lo_a), cell(lo_b)))
+        cb[6 * (size_t)i + k] = (int)cell_of(b.lo[k], v.inv_cell);
+        cb[6 * (size_t)i + 3 + k] = (int)cell_of(b.hi[k], v.inv_cell);
     }
     if (cnt) {
         double c = box_cells(b, v.inv_cell);
@@ -119,23 +123,18 @@ __global__ void k_boxes(BPView v, int kind, int n, double* box, uint32_t* cnt, u
 }
 
 // grid entries of one primitive family; bucket keys offset by bucket_base
-__global__ void k_emit_entries(BPView v, int n, const double* box, const uint32_t* off, uint32_t entry_base,
+__global__ void k_emit_entries(BPView v, int n, const int* cb, const uint32_t* off, uint32_t entry_base,
                                uint64_t bucket_base, uint64_t tmask, uint64_t* key, uint32_t* val,
                                uint64_t* cell_tmp, int* prim_tmp, int prim_flag) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     uint32_t o = off[i], e = off[i + 1];
     if (o == e) return;
-    Box6 b = ld_box(box + 6 * (size_t)i);
-    long long c0[3], c1[3];
-    for (int k = 0; k < 3; ++k) {
-        c0[k] = cell_of(b.lo[k], v.inv_cell);
-        c1[k] = cell_of(b.hi[k], v.inv_cell);
-    }
+    const int* c = cb + 6 * (size_t)i;
     uint32_t j = entry_base + o, jend = entry_base + e;
-    for (long long cz = c0[2]; cz <= c1[2]; ++cz)
-        for (long long cy = c0[1]; cy <= c1[1]; ++cy)
-            for (long long cx = c0[0]; cx <= c1[0]; ++cx) {
+    for (int cz = c[2]; cz <= c[5]; ++cz)
+        for (int cy = c[1]; cy <= c[4]; ++cy)
+            for (int cx = c[0]; cx <= c[3]; ++cx) {
                 if (j >= jend) return;  // never taken: the count pass saw the same box
                 uint64_t ck = pack_cell(cx, cy, cz);
                 key[j] = bucket_base + (mix64(ck) & tmask);
@@ -198,18 +197,12 @@ struct Table {
     uint64_t bucket_base, tmask;
 };
 
-// is the current cell the one holding the min corner of the boxes' intersection
-__device__ __forceinline__ bool owns(const Box6& a, const Box6& b, long long cx, long long cy, long long cz,
-                                     double inv) {
-    return cell_of(fmax(a.lo[0], b.lo[0]), inv) == cx && cell_of(fmax(a.lo[1], b.lo[1]), inv) == cy &&
-           cell_of(fmax(a.lo[2], b.lo[2]), inv) == cz;
-}
-
 // kind 0: point queries against the triangle table; kind 1: edge queries
 // against the edge table (only pairs with query < entry).
 template <bool WRITE>
-__global__ void k_query(BPView v, int kind, int nq, const double* qbox, const double* ebox_all, Table T,
-                        const int* big, int nbig, int n_entries_all, uint32_t* cnt, const uint32_t* off, int2* out) {
+__global__ void k_query(BPView v, int kind, int nq, const double* qbox, const double* ebox_all, const int* qcb,
+                        const int* ecb_all, Table T, const int* big, int nbig, int n_entries_all, uint32_t* cnt,
+                        const uint32_t* off, int2* out) {
     int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= nq) return;
     Box6 a = ld_box(qbox + 6 * (size_t)q);
@@ -229,14 +222,11 @@ __global__ void k_query(BPView v, int kind, int nq, const double* qbox, const do
         if (!WRITE) cnt[q] = 0;
         return;
     } else {
-        long long c0[3], c1[3];
-        for (int k = 0; k < 3; ++k) {
-            c0[k] = cell_of(a.lo[k], v.inv_cell);
-            c1[k] = cell_of(a.hi[k], v.inv_cell);
-        }
-        for (long long cz = c0[2]; cz <= c1[2]; ++cz)
-            for (long long cy = c0[1]; cy <= c1[1]; ++cy)
-                for (long long cx = c0[0]; cx <= c1[0]; ++cx) {
+        int qc[6];
+        for (int k = 0; k < 6; ++k) qc[k] = qcb[6 * (size_t)q + k];
+        for (int cz = qc[2]; cz <= qc[5]; ++cz)
+            for (int cy = qc[1]; cy <= qc[4]; ++cy)
+                for (int cx = qc[0]; cx <= qc[3]; ++cx) {
                     uint64_t ck = pack_cell(cx, cy, cz);
                     uint64_t bkt = T.bucket_base + (mix64(ck) & T.tmask);
                     uint32_t s = T.bstart[bkt], f = T.bend[bkt];
@@ -244,8 +234,11 @@ __global__ void k_query(BPView v, int kind, int nq, const double* qbox, const do
                         if (T.ecell[j] != ck) continue;
                         int e = T.eprim[j];
                         if (kind == 1 && e <= q) continue;
+                        // emit only from the cell holding the min corner of the
+                        // boxes' intersection (integer test)
+                        const int* ec = ecb_all + 6 * (size_t)e;
+                        if (max(qc[0], ec[0]) != cx || max(qc[1], ec[1]) != cy || max(qc[2], ec[2]) != cz) continue;
                         Box6 b = ld_box(ebox_all + 6 * (size_t)e);
-                        if (!owns(a, b, cx, cy, cz, v.inv_cell)) continue;
                         if (overlap(a, b) && test(e)) emit(e);
                     }
                 }
@@ -330,9 +323,12 @@ void BroadPhase::run(Allocator* A, const BPView& v, cudaStream_t st) {
     flagoff.ensure(A, (size_t)nt + ne + 4);
     size_t mx = (size_t)nt + 2 * (size_t)ne + nsv + 16;
     tmp.ensure(A, scan_tmp_size(mx));
-    if (nsv) ZL(k_boxes, div_up(nsv, TB), TB, 0, st)(v, 0, nsv, pbox.p, nullptr, nullptr);
-    if (ne) ZL(k_boxes, div_up(ne, TB), TB, 0, st)(v, 1, ne, ebox.p, ecnt.p, flag.p + nt);
-    if (nt) ZL(k_boxes, div_up(nt, TB), TB, 0, st)(v, 2, nt, tbox.p, tcnt.p, flag.p);
+    pcb.ensure(A, 6 * (size_t)nsv + 6);
+    ecb.ensure(A, 6 * (size_t)ne + 6);
+    tcb.ensure(A, 6 * (size_t)nt + 6);
+    if (nsv) ZL(k_boxes, div_up(nsv, TB), TB, 0, st)(v, 0, nsv, pbox.p, pcb.p, nullptr, nullptr);
+    if (ne) ZL(k_boxes, div_up(ne, TB), TB, 0, st)(v, 1, ne, ebox.p, ecb.p, ecnt.p, flag.p + nt);
+    if (nt) ZL(k_boxes, div_up(nt, TB), TB, 0, st)(v, 2, nt, tbox.p, tcb.p, tcnt.p, flag.p);
     ZLAUNCH();
     exclusive_scan(tcnt.p, toff.p, nt, tmp.p, st);
     exclusive_scan(ecnt.p, eoff.p, ne, tmp.p, st);
@@ -367,8 +363,8 @@ void BroadPhase::run(Allocator* A, const BPView& v, cudaStream_t st) {
     bend.ensure(A, Tt + Te);
     ZCHECK(cudaMemsetAsync(bstart.p, 0, (Tt + Te) * sizeof(uint32_t), st));
     ZCHECK(cudaMemsetAsync(bend.p, 0, (Tt + Te) * sizeof(uint32_t), st));
-    if (nt) ZL(k_emit_entries, div_up(nt, TB), TB, 0, st)(v, nt, tbox.p, toff.p, 0, 0, Tt - 1, key.p, val.p, ctmp, ptmp, 0);
-    if (ne) ZL(k_emit_entries, div_up(ne, TB), TB, 0, st)(v, ne, ebox.p, eoff.p, Et, Tt, Te - 1, key.p, val.p, ctmp, ptmp, 0);
+    if (nt) ZL(k_emit_entries, div_up(nt, TB), TB, 0, st)(v, nt, tcb.p, toff.p, 0, 0, Tt - 1, key.p, val.p, ctmp, ptmp, 0);
+    if (ne) ZL(k_emit_entries, div_up(ne, TB), TB, 0, st)(v, ne, ecb.p, eoff.p, Et, Tt, Te - 1, key.p, val.p, ctmp, ptmp, 0);
     ZLAUNCH();
     if (E) {
         int bits = 1;
@@ -402,10 +398,10 @@ void BroadPhase::run(Allocator* A, const BPView& v, cudaStream_t st) {
     if (ne) ZL(k_compact_flags, div_up(ne, TB), TB, 0, st)(pflag.p + nsv, pflagoff.p + nsv, nbp, ne, big_q.p);
     ZLAUNCH();
     if (nsv)
-        ZL(k_query<false>, div_up(nsv, TB), TB, 0, st)(v, 0, nsv, pbox.p, tbox.p, TT, big_t.p, (int)nbt, nt,
+        ZL(k_query<false>, div_up(nsv, TB), TB, 0, st)(v, 0, nsv, pbox.p, tbox.p, pcb.p, tcb.p, TT, big_t.p, (int)nbt, nt,
                                                        qcnt_pt.p, nullptr, nullptr);
     if (ne)
-        ZL(k_query<false>, div_up(ne, TB), TB, 0, st)(v, 1, ne, ebox.p, ebox.p, TE, big_e.p, (int)nbe, ne,
+        ZL(k_query<false>, div_up(ne, TB), TB, 0, st)(v, 1, ne, ebox.p, ebox.p, ecb.p, ecb.p, TE, big_e.p, (int)nbe, ne,
                                                       qcnt_ee.p, nullptr, nullptr);
     if (nbp) ZL(k_query_big<false>, nbp, 256, 0, st)(v, 0, big_p.p, pbox.p, tbox.p, nt, qcnt_pt.p, nullptr, nullptr);
     if (nbq) ZL(k_query_big<false>, nbq, 256, 0, st)(v, 1, big_q.p, ebox.p, ebox.p, ne, qcnt_ee.p, nullptr, nullptr);
@@ -421,10 +417,10 @@ void BroadPhase::run(Allocator* A, const BPView& v, cudaStream_t st) {
     pt.ensure(A, n_pt + 1);
     ee.ensure(A, n_ee + 1);
     if (nsv && n_pt)
-        ZL(k_query<true>, div_up(nsv, TB), TB, 0, st)(v, 0, nsv, pbox.p, tbox.p, TT, big_t.p, (int)nbt, nt, nullptr,
+        ZL(k_query<true>, div_up(nsv, TB), TB, 0, st)(v, 0, nsv, pbox.p, tbox.p, pcb.p, tcb.p, TT, big_t.p, (int)nbt, nt, nullptr,
                                                       qoff_pt.p, pt.p);
     if (ne && n_ee)
-        ZL(k_query<true>, div_up(ne, TB), TB, 0, st)(v, 1, ne, ebox.p, ebox.p, TE, big_e.p, (int)nbe, ne, nullptr,
+        ZL(k_query<true>, div_up(ne, TB), TB, 0, st)(v, 1, ne, ebox.p, ebox.p, ecb.p, ecb.p, TE, big_e.p, (int)nbe, ne, nullptr,
                                                      qoff_ee.p, ee.p);
     if (nbp && n_pt) ZL(k_query_big<true>, nbp, 256, 0, st)(v, 0, big_p.p, pbox.p, tbox.p, nt, nullptr, qoff_pt.p, pt.p);
     if (nbq && n_ee) ZL(k_query_big<true>, nbq, 256, 0, st)(v, 1, big_q.p, ebox.p, ebox.p, ne, nullptr, qoff_ee.p, ee.p);

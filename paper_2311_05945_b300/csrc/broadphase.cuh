@@ -23,6 +23,7 @@ struct BPView {
 struct BroadPhase {
     // boxes
     DBuf<double> pbox, ebox, tbox;  // 6 per primitive: lo xyz, hi xyz
+    DBuf<int> pcb, ecb, tcb;        // 6 per primitive: integer cell range lo xyz, hi xyz
     DBuf<uint32_t> tcnt, toff, ecnt, eoff;
     DBuf<uint64_t> key, key2;
     DBuf<uint32_t> val, val2;

@@ -372,12 +372,26 @@ struct PcgArgs {
     int max_iter;
 };
 
-// sum of one env's tile partials, in tile order; thread-strided over envs
+// Sum of each env's tile partials into out[env].  Few envs: one warp per env,
+// lanes stride over the tiles and a fixed shuffle tree combines them; many
+// envs: one thread per env in tile order.  Every block computes identical
+// values (same order).
 __device__ __forceinline__ void env_sums(const Tiles& T, const double* part, int n_envs, double* out) {
-    for (int e = threadIdx.x; e < n_envs; e += blockDim.x) {
-        double s = 0.0;
-        for (int t = T.env_start[e]; t < T.env_start[e + 1]; ++t) s += part[t];
-        out[e] = s;
+    int nw = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (n_envs <= nw * 4) {
+        for (int e = w; e < n_envs; e += nw) {
+            double s = 0.0;
+            for (int t = T.env_start[e] + lane; t < T.env_start[e + 1]; t += 32) s += part[t];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) out[e] = s;
+        }
+    } else {
+        for (int e = threadIdx.x; e < n_envs; e += blockDim.x) {
+            double s = 0.0;
+            for (int t = T.env_start[e]; t < T.env_start[e + 1]; ++t) s += part[t];
+            out[e] = s;
+        }
     }
 }
 
@@ -426,6 +440,7 @@ __global__ void __launch_bounds__(256) k_pcg_persistent(PcgArgs<Real> a) {
     grid.sync();
     env_sums(a.T, a.pt_rz, NE, s_rz);
     env_sums(a.T, a.pt_bb, NE, s_bb);
+    __syncthreads();
     for (int e = threadIdx.x; e < NE; e += blockDim.x) s_conv[e] = a.conv[e] || !(s_bb[e] > 0.0);
     __syncthreads();
     int it = 0;

@@ -92,7 +92,7 @@ struct zema_scene {
     DBuf<double> tolv;
     // pair lists
     BroadPhase bp;
-    DBuf<PairRec> cand, act, swept, lag;
+    DBuf<PairRec> cand, act, swept, lag, recs;
     DBuf<uint32_t> flag, flagoff, pt_env, ee_env, m_env, act_env, swept_env, lag_env, tmp32;
     DBuf<double> lag_w, lag_n, lag_c, pH, pG;
     uint32_t n_act = 0, n_swept = 0, n_lag = 0;
@@ -820,10 +820,12 @@ uint32_t candidates(zema_scene* s, const double* X0, const double* X1, DBuf<Pair
     return n;
 }
 
-// active pairs (d < dhat) of X: fills s->act / s->act_env, per-env dmin
-uint32_t active_pairs(zema_scene* s, const double* X, bool want_dmin) {
+// Active pairs (d < dhat) at X among the n pairs of `list` (env offsets
+// `list_env`): fills s->act / s->act_env and, if asked, the per-env minimum
+// distance of active pairs.
+uint32_t active_from(zema_scene* s, const double* X, const PairRec* list, const uint32_t* list_env, uint32_t n,
+                     bool want_dmin) {
     cudaStream_t st = s->st;
-    uint32_t n = candidates(s, X, nullptr, s->cand, s->m_env);
     int NE = s->n_envs;
     if (want_dmin) {
         std::vector<double> inf(NE, INFINITY);
@@ -833,21 +835,26 @@ uint32_t active_pairs(zema_scene* s, const double* X, bool want_dmin) {
     s->flagoff.ensure(&s->A, n + 2);
     s->tmp32.ensure(&s->A, scan_tmp_size(n + 1));
     if (n)
-        ZL(k_active_flags, div_up(n, TB), TB, 0, st)(s->G, X, s->cand.p, (int)n, s->flag.p,
-                                                    want_dmin ? s->dmin.p : nullptr);
+        ZL(k_active_flags, div_up(n, TB), TB, 0, st)(s->G, X, list, (int)n, s->flag.p, want_dmin ? s->dmin.p : nullptr);
     ZLAUNCH();
     exclusive_scan(s->flag.p, s->flagoff.p, n, s->tmp32.p, st);
     ZCHECK(cudaMemcpyAsync(s->h32, s->flagoff.p + n, 4, cudaMemcpyDeviceToHost, st));
-    ZL(k_env_gather, div_up(NE + 1, 64), 64, 0, st)(s->flagoff.p, s->m_env.p, NE, s->act_env.p);
+    ZL(k_env_gather, div_up(NE + 1, 64), 64, 0, st)(s->flagoff.p, list_env, NE, s->act_env.p);
     ZLAUNCH();
     ZCHECK(cudaStreamSynchronize(st));
     uint32_t na = s->h32[0];
     s->act.ensure(&s->A, na + 1);
-    if (n) ZL(k_compact_pairs, div_up(n, TB), TB, 0, st)(s->cand.p, s->flag.p, s->flagoff.p, (int)n, s->act.p);
+    if (n) ZL(k_compact_pairs, div_up(n, TB), TB, 0, st)(list, s->flag.p, s->flagoff.p, (int)n, s->act.p);
     ZLAUNCH();
     s->n_act = na;
     s->S.max_active = std::max<int64_t>(s->S.max_active, na);
     return na;
+}
+
+// active pairs of X from a fresh broad phase over X
+uint32_t active_pairs(zema_scene* s, const double* X, bool want_dmin) {
+    uint32_t n = candidates(s, X, nullptr, s->cand, s->m_env);
+    return active_from(s, X, s->cand.p, s->m_env.p, n, want_dmin);
 }
 
 // ---------------------------------------------------------------------------
@@ -927,7 +934,7 @@ void grad_hess_t(zema_scene* s, bool barrier, bool friction, bool hess) {
                                                            s->pG.p + 12 * (size_t)na);
     ZLAUNCH();
     // one record list: act then lag
-    DBuf<PairRec>& recs = s->swept;  // reuse as scratch for the concatenation
+    DBuf<PairRec>& recs = s->recs;
     recs.ensure(A, nr + 1);
     if (na) ZCHECK(cudaMemcpyAsync(recs.p, s->act.p, na * sizeof(PairRec), cudaMemcpyDeviceToDevice, st));
     if (nl) ZCHECK(cudaMemcpyAsync(recs.p + na, s->lag.p, nl * sizeof(PairRec), cudaMemcpyDeviceToDevice, st));
@@ -1345,7 +1352,10 @@ void do_step(zema_scene* s) {
             double ta = now_ms();
             ZL(k_sv_pos, div_up(s->n_sv, TB), TB, 0, st)(G, s->x.p, s->X.p);
             ZLAUNCH();
-            active_pairs(s, s->X.p, true);
+            // x was reached by a line search along the last swept motion (the
+            // warm start or the previous Newton step), so that swept
+            // candidate list contains every pair with d < dhat at x
+            active_from(s, s->X.p, s->swept.p, s->swept_env.p, s->n_swept, true);
             double tb = now_ms();
             s->S.ms_phase[0] += tb - ta;
             grad_hess(s);
