@@ -32,7 +32,7 @@ sys.path.insert(0, ROOT)
 METRIC = "IPC time steps/sec at fixed Newton tol, batched+warm-start vs plain, one B300"
 UNIT = "steps/s"
 WORKLOAD = "parallel-jaw grasp, 1 env: soft ellipsoid 9600 tets + 2 kinematic affine fingers (972 tris each) + fixed floor"
-ROOFLINE_KERNEL = "k_pcg_persistent"
+ROOFLINE_KERNEL = "k_pcg_cluster"
 # DRAM bytes per launch of ROOFLINE_KERNEL from the committed ncu capture
 # (profiles/); None until a capture of the current kernel exists.
 ROOFLINE_TRAFFIC = None

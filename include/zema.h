@@ -71,6 +71,10 @@ typedef struct {
     int32_t precision;     /* 0: FP64 throughout; 1: mixed (FP32 elastic/affine Hessians and matvecs) */
     int32_t n_envs;        /* number of independent environments */
     int32_t warm_start;    /* 0: constant-velocity proposal; 1: learned proposal (needs weights) */
+    int32_t pcg_kind;      /* 0: auto (one thread-block cluster per env when the env's vector fits
+                              in shared memory, else the grid-wide solve); 1: grid-wide
+                              cooperative solve; 2: cluster solve (zema_step returns
+                              ZEMA_ERR_INVALID_ARG when the scene or device cannot run it) */
     void* stream;          /* cudaStream_t used for all work; NULL = legacy default stream */
     zema_alloc_fn alloc;   /* optional device allocator */
     zema_free_fn free;

@@ -1,0 +1,368 @@
+// Block-Jacobi PCG with one thread-block cluster per environment.
+//
+// Each environment's system (a few thousand 3x3 block rows for the grasp
+// workloads) is solved by the CTAs of one cluster.  A CTA owns a contiguous
+// range of the env's soft-node rows, whose x, r and 3x3 preconditioner blocks
+// stay in registers for the whole solve; the last CTA also owns the env's
+// affine bodies (12x12 preconditioner rows in registers).  The rows of the
+// affine bodies, whose contact blocks couple them to every soft node they
+// touch, are split by block range across all CTAs of the cluster.  Every CTA
+// holds the whole env's p in shared memory.  Per iteration:
+//
+//   stage    p_k = z_k + beta p_{k-1} in place over the env (z_k from L2,
+//            written by its owner CTA), so the SpMV gathers p locally;
+//   spmv     q = A p for the owned rows and the affine row shares, partial p.q;
+//   B1       cluster barrier; every CTA sums the CTAs' partials in a fixed
+//            order -> alpha (identical in all CTAs);
+//   update   x += alpha p, r -= alpha q, z = M^-1 r on the owned units (the
+//            affine rows' q: the CTAs' partials summed in rank order),
+//            partial r.z and r.r;
+//   B2       cluster barrier; sums -> beta and the stop test.
+//
+// Two hardware cluster barriers per iteration; inside the loop only z (one
+// store per owned value, one L2 read per env value per CTA) and the matrix
+// (read-only, L1/L2 resident) touch global memory;
+// no grid-wide synchronisation and no atomics: results are bit-reproducible.
+// Real is the arithmetic type of the whole solve, dot products and their
+// cross-CTA sums included (double, or float in the mixed-precision mode: the
+// stop tolerance, 1e-4 of |b|, is far above FP32 rounding, and B300's FP64
+// rate is 1/64 of its FP32 rate).
+#pragma once
+#include <cooperative_groups.h>
+
+#include "kernels_linear.cuh"
+
+namespace zema {
+
+template <class Real>
+struct PcgcArgs {
+    Geo G;
+    Bsr<Real> S, C;
+    const double* b;     // right-hand side, 3 per node
+    double* x_out;       // solution, 3 per node (written for solved envs)
+    Real* z;             // preconditioned residual, 3 per node (exchanged through L2)
+    const Real* Minv_s;  // 9 per soft node
+    const Real* Minv_a;  // 144 per affine body
+    int* conv;           // per env in: 1 = skip; out: 1
+    int* iters;          // per env: iterations run
+    double tol2;
+    int max_iter;
+    int max_env_nodes;   // shared-memory layout bounds
+    int max_rows;        // soft rows owned by one CTA, max over envs
+    int max_aff;         // affine bodies per env, max over envs
+};
+
+constexpr int kPcgcThreads = 512;
+constexpr int kPcgcGroup = 16;  // lanes per row in the SpMV
+constexpr int kPcgcMaxCluster = 16;
+constexpr int kPcgcStageBatch = 4;  // nodes per thread whose loads are issued together
+constexpr int kPcgcOwn = 2;         // soft rows per thread: a CTA owns at most 2 * kPcgcThreads rows
+
+__device__ __forceinline__ float ldcg_r(const float* p) { return __ldcg(p); }
+__device__ __forceinline__ double ldcg_r(const double* p) { return __ldcg(p); }
+
+// Sum of K per-thread values over the CTA, in Real: warp shuffles, then the
+// warps' results by warp 0 (fixed shuffle tree), into out[0..K).
+template <int K, class Real>
+__device__ __forceinline__ void cta_partial(Real (&v)[K], Real* s_w, Real* out) {
+    constexpr int NW = kPcgcThreads / 32;
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+        if (l == 0) s_w[k * NW + w] = v[k];
+    }
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            Real s = l < NW ? s_w[k * NW + l] : Real(0);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (l == 0) out[k] = s;
+        }
+    }
+}
+
+// After a cluster barrier: total[k] = sum over the cluster's CTAs of their
+// part[k], one remote load per lane of warp 0 and a fixed shuffle tree, so
+// every CTA gets the same bits.  Ends with a CTA barrier.
+template <int K, class Real>
+__device__ __forceinline__ void cluster_total(cooperative_groups::cluster_group& cl, const Real* part, Real* total) {
+    if (threadIdx.x < 32) {
+        int cs = (int)cl.num_blocks(), l = threadIdx.x;
+        const Real* rp = l < cs ? cl.map_shared_rank(part, l) : nullptr;
+        Real v[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) v[k] = rp ? rp[k] : Real(0);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+            if (l == 0) total[k] = v[k];
+        }
+    }
+    __syncthreads();
+}
+
+// q for one row: the blocks [s0, s1) of S followed by [c0, c1) of C, the 16
+// lanes of a group striding over both ranges as one; p gathered from the
+// staged env vector.
+template <class Real>
+__device__ __forceinline__ void row_part(const Bsr<Real>& S, const Bsr<Real>& C, int4 g, const Real* s_p, int nb,
+                                         int n_env, int gl, Real& y0, Real& y1, Real& y2) {
+    const int ls = g.y - g.x, n = ls + (g.w - g.z);
+    for (int j = gl; j < n; j += kPcgcGroup) {
+        const bool in_s = j < ls;
+        const int k = in_s ? g.x + j : g.z + (j - ls);
+        const int* colp = in_s ? S.col : C.col;
+        const Real* v = (in_s ? S.val : C.val) + 9 * (size_t)k;
+        unsigned c = (unsigned)(__ldg(colp + k) - nb);
+        if (c >= (unsigned)n_env) continue;  // cannot happen: blocks stay inside one env
+        Real p0 = s_p[3 * c], p1 = s_p[3 * c + 1], p2 = s_p[3 * c + 2];
+        y0 += __ldg(v + 0) * p0 + __ldg(v + 1) * p1 + __ldg(v + 2) * p2;
+        y1 += __ldg(v + 3) * p0 + __ldg(v + 4) * p1 + __ldg(v + 5) * p2;
+        y2 += __ldg(v + 6) * p0 + __ldg(v + 7) * p1 + __ldg(v + 8) * p2;
+    }
+}
+
+template <class Real>
+__device__ __forceinline__ Real group_sum(Real v) {
+#pragma unroll
+    for (int o = kPcgcGroup / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <class Real>
+__global__ void __launch_bounds__(kPcgcThreads) k_pcg_cluster(PcgcArgs<Real> a) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    const Geo& G = a.G;
+    const int cs = (int)cl.num_blocks();
+    const int rank = (int)cl.block_rank();
+    const int e = blockIdx.x / cs;
+    if (e >= G.n_envs) return;       // whole cluster (grid is n_envs * cs)
+    if (a.conv[e] != 0) return;      // whole cluster: env needs no solve
+
+    constexpr int NW = kPcgcThreads / 32;
+    extern __shared__ int4 smi[];
+    int4* s_rng = smi;                 // [max_rows + 4 * max_aff] block ranges of the SpMV tasks in S and C
+    Real* s_w = (Real*)(s_rng + a.max_rows + 4 * a.max_aff);  // [3][NW] warp partials
+    Real* s_part = s_w + 3 * NW;       // [4] this CTA's partials (read by the cluster)
+    Real* s_tot = s_part + 4;          // [4] cluster totals
+    Real* s_p = s_tot + 4;             // [3 * max_env_nodes] p over the whole env
+    Real* s_q = s_p + 3 * (size_t)a.max_env_nodes;  // [3 * max_rows] q of the owned soft rows
+    Real* s_qa = s_q + 3 * (size_t)a.max_rows;      // [12 * max_aff] partial q of the affine rows
+    Real* s_ra = s_qa + 12 * (size_t)a.max_aff;     // [12 * max_aff] r of the affine rows (last rank)
+    Real* zw = a.z;                                 // z, 3 per node, in global memory
+    const Real* __restrict__ zg = a.z;
+
+    const int nb = G.env_node_start[e], nend = G.env_node_start[e + 1], n_env = nend - nb;
+    const int ab0 = G.env_aff_start[e], n_aff = G.env_aff_start[e + 1] - ab0;
+    const int ns1 = n_aff ? G.aff_node0[ab0] : nend;  // soft nodes are [nb, ns1), affine nodes [ns1, nend)
+    const int n_soft = ns1 - nb, n_arow = nend - ns1;
+    const int lo = nb + (int)(((long long)n_soft * rank) / cs);
+    const int hi = nb + (int)(((long long)n_soft * (rank + 1)) / cs);
+    const int n_own = hi - lo;
+    const bool aff_owner = rank == cs - 1;
+    const int tid = threadIdx.x;
+    // thread tid owns soft nodes lo + tid + j * kPcgcThreads (j < kPcgcOwn) and,
+    // in the last rank, component tid of the affine rows (tid < 12 n_aff)
+    const bool own_a = aff_owner && tid < 12 * n_aff;
+
+    // ---- init: x = 0, r = b, z = M^-1 r (x, r and the 3x3 blocks of M^-1
+    // stay in registers for the whole solve); partial r.z and b.b
+    Real xs[kPcgcOwn][3], rs[kPcgcOwn][3], Ms[kPcgcOwn][9];
+    Real xa = 0, ra = 0, Ma[12];
+    {
+        Real acc[2] = {0, 0};
+#pragma unroll
+        for (int j = 0; j < kPcgcOwn; ++j) {
+            const int i = tid + j * kPcgcThreads;
+            if (i >= n_own) continue;
+            const size_t o = 3 * (size_t)(lo + i);
+            const Real* M = a.Minv_s + 9 * (size_t)(lo + i);
+#pragma unroll
+            for (int c = 0; c < 9; ++c) Ms[j][c] = M[c];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                rs[j][c] = (Real)a.b[o + c];
+                xs[j][c] = 0;
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                Real z = Ms[j][3 * c] * rs[j][0] + Ms[j][3 * c + 1] * rs[j][1] + Ms[j][3 * c + 2] * rs[j][2];
+                zw[3 * (size_t)(lo + i) + c] = z;
+                acc[0] += rs[j][c] * z;
+                acc[1] += rs[j][c] * rs[j][c];
+            }
+        }
+        if (own_a) {
+            const int bi = tid / 12, i = tid - 12 * bi;
+            const Real* M = a.Minv_a + 144 * (size_t)(ab0 + bi) + 12 * i;
+#pragma unroll
+            for (int c = 0; c < 12; ++c) Ma[c] = M[c];
+            ra = (Real)a.b[3 * (size_t)ns1 + tid];
+            s_ra[tid] = ra;
+        }
+        __syncthreads();
+        if (own_a) {
+            const int bi = tid / 12;
+            Real z = 0;
+#pragma unroll
+            for (int c = 0; c < 12; ++c) z += Ma[c] * s_ra[12 * bi + c];
+            zw[3 * (size_t)ns1 + tid] = z;
+            acc[0] += ra * z;
+            acc[1] += ra * ra;
+        }
+        cta_partial<2>(acc, s_w, s_part + 1);
+    }
+    // block ranges of this CTA's SpMV tasks (fixed for the solve)
+    const int n_tasks = n_own + n_arow;
+    for (int task = tid; task < n_tasks; task += kPcgcThreads) {
+        int4 g;
+        if (task < n_own) {
+            int row = lo + task;
+            g = make_int4(a.S.rowptr[row], a.S.rowptr[row + 1], a.C.rowptr[row], a.C.rowptr[row + 1]);
+        } else {
+            int row = ns1 + (task - n_own);
+            int k0 = a.S.rowptr[row], len = a.S.rowptr[row + 1] - k0;
+            int c0 = a.C.rowptr[row], clen = a.C.rowptr[row + 1] - c0;
+            g = make_int4(k0 + (int)(((long long)len * rank) / cs), k0 + (int)(((long long)len * (rank + 1)) / cs),
+                          c0 + (int)(((long long)clen * rank) / cs), c0 + (int)(((long long)clen * (rank + 1)) / cs));
+        }
+        s_rng[task] = g;
+    }
+    cl.sync();  // also orders s_rng within the CTA
+    cluster_total<2>(cl, s_part + 1, s_tot + 1);  // s_tot[1] = r.z, s_tot[2] = b.b
+    Real rz = s_tot[1];
+    const Real bb = s_tot[2];
+    const Real stop2 = (Real)a.tol2 * bb;
+    bool done = !(bb > Real(0));
+    Real beta = 0;
+    int it = 0;
+    const int warp = tid >> 5, half = (tid >> 4) & 1, gl = tid & (kPcgcGroup - 1);
+    const int n_groups = kPcgcThreads / kPcgcGroup;
+    while (!done && it < a.max_iter) {
+        // ---- p_k = z_k + beta p_{k-1} over the env, in place (every CTA
+        // holds the same p); z comes from L2, written there by its owner
+        for (int i0 = tid; i0 < n_env; i0 += kPcgcStageBatch * kPcgcThreads) {
+            Real zv[kPcgcStageBatch][3];
+#pragma unroll
+            for (int j = 0; j < kPcgcStageBatch; ++j) {
+                const int i = i0 + j * kPcgcThreads;
+                const Real* src = zg + 3 * (size_t)(nb + (i < n_env ? i : 0));
+#pragma unroll
+                for (int c = 0; c < 3; ++c) zv[j][c] = ldcg_r(src + c);
+            }
+#pragma unroll
+            for (int j = 0; j < kPcgcStageBatch; ++j) {
+                const int i = i0 + j * kPcgcThreads;
+                if (i >= n_env) break;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) s_p[3 * i + c] = it > 0 ? zv[j][c] + beta * s_p[3 * i + c] : zv[j][c];
+            }
+        }
+        __syncthreads();
+        // ---- q = A p: owned soft rows, then this CTA's share of each affine row
+        Real pq[1] = {0};
+        // two 16-lane groups per warp; the loop is uniform over the warp so
+        // that every lane takes part in the shuffles
+        for (int t0 = 2 * warp; t0 < n_tasks; t0 += n_groups) {
+            const int task = t0 + half;
+            const bool valid = task < n_tasks;
+            Real y0 = 0, y1 = 0, y2 = 0;
+            int row = 0;
+            if (valid) {
+                int4 g = s_rng[task];
+                row = task < n_own ? lo + task : ns1 + (task - n_own);
+                row_part(a.S, a.C, g, s_p, nb, n_env, gl, y0, y1, y2);
+            }
+            y0 = group_sum(y0);
+            y1 = group_sum(y1);
+            y2 = group_sum(y2);
+            if (valid && gl == 0) {
+                Real* qd = task < n_own ? s_q + 3 * task : s_qa + 3 * (task - n_own);
+                qd[0] = y0;
+                qd[1] = y1;
+                qd[2] = y2;
+                const Real* pr = s_p + 3 * (row - nb);
+                pq[0] += pr[0] * y0 + pr[1] * y1 + pr[2] * y2;
+            }
+        }
+        cta_partial<1>(pq, s_w, s_part);
+        cl.sync();  // B1
+        cluster_total<1>(cl, s_part, s_tot);
+        const Real pqt = s_tot[0];
+        if (!(pqt > Real(0))) break;  // breakdown (not positive definite): keep x, stop (same in all CTAs)
+        const Real alpha = rz / pqt;
+        // ---- x += alpha p, r -= alpha q, z = M^-1 r on the owned units
+        Real acc[2] = {0, 0};
+#pragma unroll
+        for (int j = 0; j < kPcgcOwn; ++j) {
+            const int i = tid + j * kPcgcThreads;
+            if (i >= n_own) continue;
+            const Real* pr = s_p + 3 * (lo + i - nb);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                xs[j][c] += alpha * pr[c];
+                rs[j][c] -= alpha * s_q[3 * i + c];
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                Real z = Ms[j][3 * c] * rs[j][0] + Ms[j][3 * c + 1] * rs[j][1] + Ms[j][3 * c + 2] * rs[j][2];
+                zw[3 * (size_t)(lo + i) + c] = z;
+                acc[0] += rs[j][c] * z;
+                acc[1] += rs[j][c] * rs[j][c];
+            }
+        }
+        if (own_a) {
+            // q of the affine row component: the CTAs' partials in rank order
+            // (independent remote loads first)
+            Real qv[kPcgcMaxCluster];
+#pragma unroll
+            for (int rk = 0; rk < kPcgcMaxCluster; ++rk) qv[rk] = rk < cs ? cl.map_shared_rank(s_qa, rk)[tid] : Real(0);
+            Real q = 0;
+#pragma unroll
+            for (int rk = 0; rk < kPcgcMaxCluster; ++rk) q += qv[rk];
+            xa += alpha * s_p[3 * (ns1 - nb) + tid];
+            ra -= alpha * q;
+            s_ra[tid] = ra;
+        }
+        __syncthreads();
+        if (own_a) {
+            const int bi = tid / 12;
+            Real z = 0;
+#pragma unroll
+            for (int c = 0; c < 12; ++c) z += Ma[c] * s_ra[12 * bi + c];
+            zw[3 * (size_t)ns1 + tid] = z;
+            acc[0] += ra * z;
+            acc[1] += ra * ra;
+        }
+        cta_partial<2>(acc, s_w, s_part + 1);
+        cl.sync();  // B2
+        cluster_total<2>(cl, s_part + 1, s_tot + 1);
+        const Real rz_new = s_tot[1], rr = s_tot[2];
+        ++it;
+        if (!(rr > stop2)) done = true;
+        beta = rz != Real(0) ? rz_new / rz : Real(0);
+        rz = rz_new;
+    }
+    // solution out (double) for the owned units
+#pragma unroll
+    for (int j = 0; j < kPcgcOwn; ++j) {
+        const int i = tid + j * kPcgcThreads;
+        if (i >= n_own) continue;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) a.x_out[3 * (size_t)(lo + i) + c] = (double)xs[j][c];
+    }
+    if (own_a) a.x_out[3 * (size_t)ns1 + tid] = (double)xa;
+    if (rank == 0 && tid == 0) {
+        a.iters[e] = it;
+        a.conv[e] = 1;
+    }
+    cl.sync();  // no CTA leaves while a partner may still read its shared memory
+}
+
+}  // namespace zema

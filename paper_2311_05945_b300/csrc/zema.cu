@@ -20,6 +20,7 @@
 
 #include "broadphase.cuh"
 #include "kernels_misc.cuh"
+#include "pcg_cluster.cuh"
 
 using namespace zema;
 
@@ -89,6 +90,10 @@ struct zema_scene {
     DBuf<int> tile_u0, tile_u1, tile_n0, tile_n1, tile_env, env_tile_start;
     DBuf<double> pt_a, pt_b, pt_c, pt_d, pt_e;
     int n_tiles = 0, pcg_grid = 0, pcg_grid_f = 0;
+    // cluster PCG: CTAs per env (0 = not chosen yet, -1 = unavailable) and
+    // its shared-memory layout bounds
+    int pcgc_cs[2] = {0, 0};
+    int pcgc_max_env_nodes = 0, pcgc_max_soft = 0, pcgc_max_aff = 0;
     DBuf<double> tolv;
     // pair lists
     BroadPhase bp;
@@ -467,6 +472,13 @@ void build(zema_scene* s) {
     }
     etile[NE] = (int)tu0.size();
     s->n_tiles = (int)tu0.size();
+    for (int e = 0; e < NE; ++e) {
+        int na = env_aff_start[e + 1] - env_aff_start[e];
+        int nsoft = (env_node_start[e + 1] - env_node_start[e]) - 4 * na;
+        s->pcgc_max_env_nodes = std::max(s->pcgc_max_env_nodes, env_node_start[e + 1] - env_node_start[e]);
+        s->pcgc_max_soft = std::max(s->pcgc_max_soft, nsoft);
+        s->pcgc_max_aff = std::max(s->pcgc_max_aff, na);
+    }
     up(s, s->tile_u0, tu0);
     up(s, s->tile_u1, tu1);
     up(s, s->tile_n0, tn0);
@@ -1019,6 +1031,76 @@ void grad_hess(zema_scene* s, bool barrier = true, bool friction = true, bool he
 }
 
 // ---------------------------------------------------------------------------
+// Cluster PCG configuration: CTAs per env ~ one per 128 nodes (at most 16,
+// the largest cluster the device accepts), shared memory for the staged env
+// vector, the owned rows' q and the affine rows' partials.
+// ---------------------------------------------------------------------------
+constexpr size_t kPcgcMaxSmem = 200 * 1024;
+
+int pcgc_max_rows(const zema_scene* s, int cs) { return (s->pcgc_max_soft + cs - 1) / cs + 1; }
+
+template <class T>
+size_t pcgc_smem(const zema_scene* s, int cs) {
+    return ((size_t)pcgc_max_rows(s, cs) + 4 * (size_t)s->pcgc_max_aff) * sizeof(int4) +
+           (3 * (kPcgcThreads / 32) + 8 + 3 * (size_t)s->pcgc_max_env_nodes + 3 * (size_t)pcgc_max_rows(s, cs) +
+            24 * (size_t)s->pcgc_max_aff) *
+               sizeof(T);
+}
+
+template <class T>
+void pcgc_config(const zema_scene* s, int cs, cudaLaunchConfig_t& cfg, cudaLaunchAttribute* at) {
+    cfg.gridDim = dim3((unsigned)(cs * s->n_envs));
+    cfg.blockDim = dim3(kPcgcThreads);
+    cfg.dynamicSmemBytes = pcgc_smem<T>(s, cs);
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+}
+
+// CTAs per env for the cluster solve, or -1 when it cannot run (env vector
+// too large for shared memory, no cluster launch on this device).
+template <class T>
+int pcgc_choose(zema_scene* s) {
+    int want = std::min(16, std::max(1, (s->pcgc_max_env_nodes + 127) / 128));
+    // the env's vector must fit in shared memory, a CTA's rows in its
+    // threads' registers, the affine rows in one CTA
+    if (pcgc_smem<T>(s, 16) > kPcgcMaxSmem || 12 * s->pcgc_max_aff > kPcgcThreads) return -1;
+    ZCHECK(cudaFuncSetAttribute(k_pcg_cluster<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPcgcMaxSmem));
+    if (want > 8) {
+        if (cudaFuncSetAttribute(k_pcg_cluster<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+            cudaGetLastError();
+            want = 8;
+        }
+    }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    pcgc_config<T>(s, want, cfg, at);
+    int maxcs = 0;
+    if (cudaOccupancyMaxPotentialClusterSize(&maxcs, k_pcg_cluster<T>, &cfg) != cudaSuccess || maxcs < 1) {
+        cudaGetLastError();
+        return -1;
+    }
+    int cs = std::min(want, maxcs);
+    if (pcgc_max_rows(s, cs) > kPcgcOwn * kPcgcThreads || pcgc_smem<T>(s, cs) > kPcgcMaxSmem) return -1;
+    pcgc_config<T>(s, cs, cfg, at);
+    // the rest of the SM's shared/L1 storage stays L1 for the matrix rows
+    int dev = 0, smem_sm = 0;
+    ZCHECK(cudaGetDevice(&dev));
+    ZCHECK(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    int pct = (int)std::min<size_t>(100, (100 * (cfg.dynamicSmemBytes + 2048) + smem_sm - 1) / std::max(1, smem_sm));
+    ZCHECK(cudaFuncSetAttribute(k_pcg_cluster<T>, cudaFuncAttributePreferredSharedMemoryCarveout, pct));
+    int ncl = 0;
+    if (cudaOccupancyMaxActiveClusters(&ncl, k_pcg_cluster<T>, &cfg) != cudaSuccess || ncl < 1) {
+        cudaGetLastError();
+        return -1;
+    }
+    return cs;
+}
+
+// ---------------------------------------------------------------------------
 // PCG: solve (S + C) p = -g for every env not flagged in done_h (one
 // persistent cooperative launch per solve)
 // ---------------------------------------------------------------------------
@@ -1037,39 +1119,71 @@ int64_t pcg_t(zema_scene* s, const std::vector<int>& done_h) {
     for (int e = 0; e < NE; ++e) s->hi[e] = done_h[e];
     ZCHECK(cudaMemcpyAsync(s->conv.p, s->hi, NE * sizeof(int), cudaMemcpyHostToDevice, st));
     ZCHECK(cudaMemsetAsync(s->pcg_iters.p, 0, NE * sizeof(int), st));
-    PcgArgs<T> a;
-    a.G = G;
-    a.S = S;
-    a.C = C;
-    a.V = PcgVec{s->p.p, s->r.p, s->z.p, s->pp.p, s->q.p};
-    a.b = s->b.p;
-    a.Minv_s = Minv_s;
-    a.Minv_a = Minv_a;
-    a.T = Tiles{s->n_tiles, s->tile_u0.p, s->tile_u1.p, s->tile_n0.p, s->tile_n1.p, s->tile_env.p, s->env_tile_start.p};
-    a.pt_rz = s->pt_a.p;
-    a.pt_rz2 = s->pt_b.p;
-    a.pt_pq = s->pt_c.p;
-    a.pt_rr = s->pt_d.p;
-    a.pt_bb = s->pt_e.p;
-    a.conv = s->conv.p;
-    a.iters = s->pcg_iters.p;
-    a.tol2 = s->P.pcg_rel_tol * s->P.pcg_rel_tol;
-    a.max_iter = s->P.max_pcg;
-    size_t smem = 4 * (size_t)NE * sizeof(double) + (size_t)NE * sizeof(int);
-    int& grid = s->P.precision == 1 ? s->pcg_grid_f : s->pcg_grid;
-    if (grid == 0) {
-        int dev = 0, nsm = 0, per = 0;
-        ZCHECK(cudaGetDevice(&dev));
-        ZCHECK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-        if (smem > 48 * 1024)
-            ZCHECK(cudaFuncSetAttribute(k_pcg_persistent<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        ZCHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg_persistent<T>, 256, smem));
-        grid = std::max(1, std::min(s->n_tiles, per * nsm));
-    }
-    void* args[] = {&a};
-    {
-        LaunchScope ls("k_pcg_persistent");
-        ZCHECK(cudaLaunchCooperativeKernel((const void*)k_pcg_persistent<T>, dim3(grid), dim3(256), args, smem, st));
+    const int pi = s->P.precision == 1 ? 1 : 0;
+    if (s->P.pcg_kind != 1 && s->pcgc_cs[pi] == 0) s->pcgc_cs[pi] = pcgc_choose<T>(s);
+    if (s->P.pcg_kind == 2 && s->pcgc_cs[pi] < 0)
+        fail(ZEMA_ERR_INVALID_ARG, "cluster PCG unavailable for this scene on this device");
+    const bool use_cluster = s->P.pcg_kind != 1 && s->pcgc_cs[pi] > 0;
+    const char* kname = use_cluster ? "k_pcg_cluster" : "k_pcg_persistent";
+    if (use_cluster) {
+        const int cs = s->pcgc_cs[pi];
+        PcgcArgs<T> c;
+        c.G = G;
+        c.S = S;
+        c.C = C;
+        c.b = s->b.p;
+        c.x_out = s->p.p;
+        c.z = (T*)s->z.p;
+        c.Minv_s = Minv_s;
+        c.Minv_a = Minv_a;
+        c.conv = s->conv.p;
+        c.iters = s->pcg_iters.p;
+        c.tol2 = s->P.pcg_rel_tol * s->P.pcg_rel_tol;
+        c.max_iter = s->P.max_pcg;
+        c.max_env_nodes = s->pcgc_max_env_nodes;
+        c.max_rows = pcgc_max_rows(s, cs);
+        c.max_aff = s->pcgc_max_aff;
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        pcgc_config<T>(s, cs, cfg, at);
+        cfg.stream = st;
+        LaunchScope ls("k_pcg_cluster");
+        ZCHECK(cudaLaunchKernelEx(&cfg, k_pcg_cluster<T>, c));
+    } else {
+        PcgArgs<T> a;
+        a.G = G;
+        a.S = S;
+        a.C = C;
+        a.V = PcgVec{s->p.p, s->r.p, s->z.p, s->pp.p, s->q.p};
+        a.b = s->b.p;
+        a.Minv_s = Minv_s;
+        a.Minv_a = Minv_a;
+        a.T = Tiles{s->n_tiles, s->tile_u0.p, s->tile_u1.p, s->tile_n0.p, s->tile_n1.p, s->tile_env.p, s->env_tile_start.p};
+        a.pt_rz = s->pt_a.p;
+        a.pt_rz2 = s->pt_b.p;
+        a.pt_pq = s->pt_c.p;
+        a.pt_rr = s->pt_d.p;
+        a.pt_bb = s->pt_e.p;
+        a.conv = s->conv.p;
+        a.iters = s->pcg_iters.p;
+        a.tol2 = s->P.pcg_rel_tol * s->P.pcg_rel_tol;
+        a.max_iter = s->P.max_pcg;
+        size_t smem = 4 * (size_t)NE * sizeof(double) + (size_t)NE * sizeof(int);
+        int& grid = s->P.precision == 1 ? s->pcg_grid_f : s->pcg_grid;
+        if (grid == 0) {
+            int dev = 0, nsm = 0, per = 0;
+            ZCHECK(cudaGetDevice(&dev));
+            ZCHECK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+            if (smem > 48 * 1024)
+                ZCHECK(cudaFuncSetAttribute(k_pcg_persistent<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            ZCHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg_persistent<T>, 256, smem));
+            grid = std::max(1, std::min(s->n_tiles, per * nsm));
+        }
+        void* args[] = {&a};
+        {
+            LaunchScope ls("k_pcg_persistent");
+            ZCHECK(cudaLaunchCooperativeKernel((const void*)k_pcg_persistent<T>, dim3(grid), dim3(256), args, smem, st));
+        }
     }
     ZLAUNCH();
     ZCHECK(cudaMemcpyAsync(s->hi, s->pcg_iters.p, NE * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1084,12 +1198,17 @@ int64_t pcg_t(zema_scene* s, const std::vector<int>& done_h) {
     // arrays, p, and writes q; the update reads/writes x and r, reads p and q,
     // writes z, reads the preconditioner (9 values per soft node, 144 per
     // affine body); the direction update reads z and reads/writes p.
+    // The cluster solve keeps q on chip and recomputes p while staging it:
+    // per node it reads z and p_{k-1}, writes p_k, reads/writes x and r and
+    // writes z (24 values of the solve's type), plus the row pointers.
     {
         double nn = s->n_nodes;
         double bs = 9.0 * sizeof(T) + 4.0;  // one stored block and its column index
-        double per_it = bs * ((double)s->n_sblocks + (double)s->n_cblocks) + nn * (8.0 + 48.0 + 168.0 + 72.0) +
-                        9.0 * sizeof(T) * (nn - 4.0 * s->n_aff) + 144.0 * sizeof(T) * s->n_aff;
-        alg_bytes_add("k_pcg_persistent", per_it * (double)tot / std::max(1, NE));
+        double pre = 9.0 * sizeof(T) * (nn - 4.0 * s->n_aff) + 144.0 * sizeof(T) * s->n_aff;
+        double per_it = use_cluster
+                            ? bs * ((double)s->n_sblocks + (double)s->n_cblocks) + nn * (8.0 + 24.0 * sizeof(T)) + pre
+                            : bs * ((double)s->n_sblocks + (double)s->n_cblocks) + nn * (8.0 + 48.0 + 168.0 + 72.0) + pre;
+        alg_bytes_add(kname, per_it * (double)tot / std::max(1, NE));
     }
     // done envs: zero direction
     for (int e = 0; e < NE; ++e) s->hi[e] = done_h[e];
@@ -1491,7 +1610,8 @@ void zema_default_params(zema_scene_params* p) {
 
 zema_status zema_create_scene(const zema_scene_params* params, zema_scene** out) {
     if (!params || !out) return ZEMA_ERR_INVALID_ARG;
-    if (!(params->dt > 0) || !(params->dhat > 0) || params->n_envs < 1 || !(params->eps_v > 0))
+    if (!(params->dt > 0) || !(params->dhat > 0) || params->n_envs < 1 || !(params->eps_v > 0) ||
+        params->pcg_kind < 0 || params->pcg_kind > 2)
         return ZEMA_ERR_INVALID_ARG;
     zema_scene* s = new (std::nothrow) zema_scene();
     if (!s) return ZEMA_ERR_OOM;

@@ -33,7 +33,7 @@ class Params(C.Structure):
         ("dt", C.c_double), ("dhat", C.c_double), ("kappa", C.c_double), ("eps_v", C.c_double),
         ("newton_tol_rel", C.c_double), ("gravity", C.c_double * 3), ("pcg_rel_tol", C.c_double),
         ("max_newton", C.c_int32), ("max_pcg", C.c_int32), ("max_al_rounds", C.c_int32),
-        ("precision", C.c_int32), ("n_envs", C.c_int32), ("warm_start", C.c_int32),
+        ("precision", C.c_int32), ("n_envs", C.c_int32), ("warm_start", C.c_int32), ("pcg_kind", C.c_int32),
         ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p),
     ]
 
@@ -173,7 +173,7 @@ class Scene:
     """A scene of the seeded generators loaded into the library."""
 
     def __init__(self, scene: _scenes.Scene, precision: Optional[int] = None, tol_scale: float = 1.0,
-                 torch_alloc: bool = True, kappa: Optional[float] = None):
+                 torch_alloc: bool = True, kappa: Optional[float] = None, pcg_kind: int = 0):
         L = lib()
         p = scene.params
         P = Params()
@@ -191,6 +191,7 @@ class Scene:
         P.max_al_rounds = p.max_al_rounds
         P.precision = p.precision if precision is None else precision
         P.n_envs = scene.n_envs
+        P.pcg_kind = pcg_kind
         P.stream = _stream()
         if torch_alloc:
             P.alloc = _ALLOC
