@@ -343,6 +343,207 @@ __device__ inline double d2_derivs(const V3* x, bool is_ee, const DistInfo& di, 
 }
 
 // ---------------------------------------------------------------------------
+// Hessian of f = d^2 in the arithmetic type T (float in the mixed-precision
+// mode).  The reduced vectors (differences of the stencil's points) are
+// formed in FP64 and then rounded to T, so no cancellation happens in T; the
+// formulas are those of d2_derivs above.
+// ---------------------------------------------------------------------------
+template <class T>
+struct V3t {
+    T x, y, z;
+};
+template <class T>
+__device__ __forceinline__ V3t<T> to_t(V3 v) {
+    return V3t<T>{(T)v.x, (T)v.y, (T)v.z};
+}
+template <class T>
+__device__ __forceinline__ T dot_t(V3t<T> a, V3t<T> b) {
+    return a.x * b.x + a.y * b.y + a.z * b.z;
+}
+template <class T>
+__device__ __forceinline__ V3t<T> cross_t(V3t<T> a, V3t<T> b) {
+    return V3t<T>{a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+template <class T>
+__device__ __forceinline__ void outer_t(T* M, V3t<T> a, V3t<T> b, T s) {
+    T av[3] = {a.x, a.y, a.z}, bv[3] = {b.x, b.y, b.z};
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) M[3 * i + j] += s * av[i] * bv[j];
+}
+template <class T>
+__device__ __forceinline__ void add_diag_t(T* M, T s) {
+    M[0] += s;
+    M[4] += s;
+    M[8] += s;
+}
+template <class T>
+__device__ __forceinline__ void add_skew_t(T* M, V3t<T> v, T s) {  // M += s [v]x
+    M[1] += -s * v.z;
+    M[2] += s * v.y;
+    M[3] += s * v.z;
+    M[5] += -s * v.x;
+    M[6] += -s * v.y;
+    M[7] += s * v.x;
+}
+template <class T>
+__device__ __forceinline__ void zero9_t(T* M) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) M[i] = T(0);
+}
+template <class T>
+__device__ __forceinline__ void scatter_block_t(SMat<12, T> H, const Red& R, int k, int l, const T* M, T sc) {
+    for (int i = 0; i < 4; ++i) {
+        int ci = R.C[k][i];
+        if (!ci) continue;
+        for (int j = 0; j < 4; ++j) {
+            int cj = R.C[l][j];
+            if (!cj) continue;
+            T f = sc * (T)(ci * cj);
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = 0; b < 3; ++b) H(3 * i + a, 3 * j + b) += f * M[3 * a + b];
+        }
+    }
+}
+// Hessian blocks of N = |a x b|^2
+template <class T>
+__device__ __forceinline__ void cross_norm_hess_t(V3t<T> a, V3t<T> b, T* Haa, T* Hbb, T* Hab) {
+    T aa = dot_t(a, a), bb = dot_t(b, b), ab = dot_t(a, b);
+    zero9_t(Haa);
+    add_diag_t(Haa, T(2) * bb);
+    outer_t(Haa, b, b, T(-2));
+    zero9_t(Hbb);
+    add_diag_t(Hbb, T(2) * aa);
+    outer_t(Hbb, a, a, T(-2));
+    zero9_t(Hab);
+    outer_t(Hab, a, b, T(4));
+    outer_t(Hab, b, a, T(-2));
+    add_diag_t(Hab, T(-2) * ab);
+}
+
+// reduced variables of the classified type (coefficients in R)
+__device__ __forceinline__ void reduced_vars(const V3* x, bool is_ee, const DistInfo& di, Red& R, V3* v) {
+    for (int k = 0; k < 3; ++k)
+        for (int i = 0; i < 4; ++i) R.C[k][i] = 0;
+    if (di.type == DT_PP) {
+        R.m = 1;
+        R.C[0][di.s[0]] = 1;
+        R.C[0][di.s[1]] = -1;
+        v[0] = x[di.s[0]] - x[di.s[1]];
+    } else if (di.type == DT_PE) {
+        R.m = 2;
+        R.C[0][di.s[0]] = 1;
+        R.C[0][di.s[1]] = -1;
+        R.C[1][di.s[2]] = 1;
+        R.C[1][di.s[1]] = -1;
+        v[0] = x[di.s[0]] - x[di.s[1]];
+        v[1] = x[di.s[2]] - x[di.s[1]];
+    } else if (!is_ee) {
+        R.m = 3;
+        R.C[0][0] = 1;
+        R.C[0][1] = -1;
+        R.C[1][2] = 1;
+        R.C[1][1] = -1;
+        R.C[2][3] = 1;
+        R.C[2][1] = -1;
+        v[0] = x[0] - x[1];
+        v[1] = x[2] - x[1];
+        v[2] = x[3] - x[1];
+    } else {
+        R.m = 3;
+        R.C[0][0] = 1;
+        R.C[0][2] = -1;
+        R.C[1][1] = 1;
+        R.C[1][0] = -1;
+        R.C[2][3] = 1;
+        R.C[2][2] = -1;
+        v[0] = x[0] - x[2];
+        v[1] = x[1] - x[0];
+        v[2] = x[3] - x[2];
+    }
+}
+
+// slot-space Hessian of f = d^2 accumulated into H (zero on entry), in T
+template <class T>
+__device__ inline void d2_hess_t(const V3* x, bool is_ee, const DistInfo& di, SMat<12, T> H) {
+    Red R;
+    V3 v[3];
+    reduced_vars(x, is_ee, di, R, v);
+    T M[9];
+    if (di.type == DT_PP) {
+        zero9_t(M);
+        add_diag_t(M, T(2));
+        scatter_block_t(H, R, 0, 0, M, T(1));
+        return;
+    }
+    if (di.type == DT_PE) {
+        V3t<T> r = to_t<T>(v[0]), e = to_t<T>(v[1]);
+        T L = dot_t(e, e), s = dot_t(r, e), iL = T(1) / L;
+        zero9_t(M);
+        add_diag_t(M, T(2));
+        outer_t(M, e, e, T(-2) * iL);
+        scatter_block_t(H, R, 0, 0, M, T(1));
+        T Hre[9];
+        zero9_t(Hre);
+        outer_t(Hre, e, r, T(-2) * iL);
+        add_diag_t(Hre, T(-2) * s * iL);
+        outer_t(Hre, e, e, T(4) * s * iL * iL);
+        scatter_block_t(H, R, 0, 1, Hre, T(1));
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) M[3 * j + i] = Hre[3 * i + j];
+        scatter_block_t(H, R, 1, 0, M, T(1));
+        zero9_t(M);
+        outer_t(M, r, r, T(-2) * iL);
+        outer_t(M, r, e, T(4) * s * iL * iL);
+        outer_t(M, e, r, T(4) * s * iL * iL);
+        add_diag_t(M, T(2) * s * s * iL * iL);
+        outer_t(M, e, e, T(-8) * s * s * iL * iL * iL);
+        scatter_block_t(H, R, 1, 1, M, T(1));
+        return;
+    }
+    // plane (PT) or line-line (EE): f = (r . (a x b))^2 / |a x b|^2
+    V3t<T> r = to_t<T>(v[0]), a = to_t<T>(v[1]), b = to_t<T>(v[2]);
+    V3t<T> n = cross_t(a, b);
+    T N = dot_t(n, n), s = dot_t(r, n);
+    T aa = dot_t(a, a), bb = dot_t(b, b), ab = dot_t(a, b);
+    V3t<T> Na{T(2) * (bb * a.x - ab * b.x), T(2) * (bb * a.y - ab * b.y), T(2) * (bb * a.z - ab * b.z)};
+    V3t<T> Nb{T(2) * (aa * b.x - ab * a.x), T(2) * (aa * b.y - ab * a.y), T(2) * (aa * b.z - ab * a.z)};
+    V3t<T> S[3] = {n, cross_t(b, r), cross_t(r, a)};
+    V3t<T> Ng[3] = {V3t<T>{0, 0, 0}, Na, Nb};
+    T Haa[9], Hbb[9], Hab[9];
+    cross_norm_hess_t(a, b, Haa, Hbb, Hab);
+    const T iN = T(1) / N, iN2 = iN * iN, iN3 = iN2 * iN;
+    const T cs = T(2) * s * iN, cn = -s * s * iN2;
+    for (int k = 0; k < 3; ++k)
+        for (int l = 0; l < 3; ++l) {
+            zero9_t(M);
+            outer_t(M, S[k], S[l], T(2) * iN);
+            outer_t(M, S[k], Ng[l], T(-2) * s * iN2);
+            outer_t(M, Ng[k], S[l], T(-2) * s * iN2);
+            outer_t(M, Ng[k], Ng[l], T(2) * s * s * iN3);
+            if (k == 0 && l == 1) add_skew_t(M, b, -cs);
+            if (k == 1 && l == 0) add_skew_t(M, b, cs);
+            if (k == 0 && l == 2) add_skew_t(M, a, cs);
+            if (k == 2 && l == 0) add_skew_t(M, a, -cs);
+            if (k == 1 && l == 2) add_skew_t(M, r, -cs);
+            if (k == 2 && l == 1) add_skew_t(M, r, cs);
+            if (k == 1 && l == 1)
+                for (int q = 0; q < 9; ++q) M[q] += cn * Haa[q];
+            if (k == 2 && l == 2)
+                for (int q = 0; q < 9; ++q) M[q] += cn * Hbb[q];
+            if (k == 1 && l == 2)
+                for (int q = 0; q < 9; ++q) M[q] += cn * Hab[q];
+            if (k == 2 && l == 1)
+                for (int i = 0; i < 3; ++i)
+                    for (int j = 0; j < 3; ++j) M[3 * i + j] += cn * Hab[3 * j + i];
+            scatter_block_t(H, R, k, l, M, T(1));
+        }
+}
+
+// ---------------------------------------------------------------------------
 // PSD projection of a translation-invariant 12x12 stencil Hessian.  Every
 // barrier term depends on the four points only through their differences,
 // so H = T^T K T with T (9 x 12, orthonormal rows: T[k] = -1/2 e_0 + e_{k+1}
@@ -356,19 +557,20 @@ __device__ __forceinline__ double tcoef(int k, int i) {  // T[k][i] for stencil 
 }
 
 template <class T>
-__device__ inline void project_translation_free(SMat<12> H, double scale, SMat<9, T> K, SMat<9, T> W, T* out) {
+__device__ inline void project_translation_free(SMat<12, T> H, double scale, SMat<9, T> K, SMat<9, T> W, T* out) {
     // K = T (scale H) T^T, blockwise: K(k a, l b) = sum_ij T[k][i] T[l][j] H(3i + a, 3j + b)
+    const T sc = (T)scale;
     for (int k = 0; k < 3; ++k)
         for (int l = 0; l < 3; ++l)
             for (int a = 0; a < 3; ++a)
                 for (int b = 0; b < 3; ++b) {
-                    double s = 0.0;
+                    T s = 0;
                     for (int i = 0; i < 4; ++i) {
-                        double r = 0.0;
-                        for (int j = 0; j < 4; ++j) r += tcoef(l, j) * H(3 * i + a, 3 * j + b);
-                        s += tcoef(k, i) * r;
+                        T r = 0;
+                        for (int j = 0; j < 4; ++j) r += (T)tcoef(l, j) * H(3 * i + a, 3 * j + b);
+                        s += (T)tcoef(k, i) * r;
                     }
-                    K(3 * k + a, 3 * l + b) = (T)(scale * s);
+                    K(3 * k + a, 3 * l + b) = sc * s;
                 }
     psd_project<9, T>(K, W);
     // out = T^T P(K) T (row-major 12x12)
@@ -387,20 +589,19 @@ __device__ inline void project_translation_free(SMat<12> H, double scale, SMat<9
 }
 
 // ---------------------------------------------------------------------------
-// kappa * e * b(d) for one stencil: value, gradient g12 and the Hessian of
-// e * b (without kappa, before projection) in H (12x12 slot space).  Returns
-// false when d >= dhat (inactive).  eps_x <= 0 disables the mollifier.
+// kappa * e * b(d) for one stencil: value, gradient g12 (FP64) and the
+// Hessian of e * b (without kappa, before projection) in H (12x12 slot space,
+// arithmetic type T).  Returns false when d >= dhat (inactive).  eps_x <= 0
+// disables the mollifier.
 // ---------------------------------------------------------------------------
+template <class T>
 __device__ inline bool pair_barrier(const V3* x, bool is_ee, double dhat, double kappa, double eps_x,
-                                    double& E, double* g12, SMat<12> H, bool want_h) {
+                                    double& E, double* g12, SMat<12, T> H, bool want_h) {
     DistInfo di = classify(x, is_ee);
     double d = sqrt(di.d2);
     if (!(d < dhat)) return false;
-    if (want_h)
-        for (int i = 0; i < 12; ++i)
-            for (int j = 0; j < 12; ++j) H(i, j) = 0.0;
     double gf[12];
-    double f = d2_derivs(x, is_ee, di, gf, H, want_h);
+    double f = d2_derivs(x, is_ee, di, gf, SMat<12>{nullptr, 0}, false);
     (void)f;
     double b, b1, b2;
     barrier_d012(d, dhat, b, b1, b2);
@@ -409,9 +610,16 @@ __device__ inline bool pair_barrier(const V3* x, bool is_ee, double dhat, double
     double cb = b2 / (4.0 * d * d) - b1 / (4.0 * d * d * d);
     double gB[12];
     for (int i = 0; i < 12; ++i) gB[i] = ca * gf[i];
-    if (want_h)
+    if (want_h) {
         for (int i = 0; i < 12; ++i)
-            for (int j = 0; j < 12; ++j) H(i, j) = ca * H(i, j) + cb * gf[i] * gf[j];
+            for (int j = 0; j < 12; ++j) H(i, j) = T(0);
+        d2_hess_t<T>(x, is_ee, di, H);
+        const T cat = (T)ca, cbt = (T)cb;
+        for (int i = 0; i < 12; ++i) {
+            const T gi = cbt * (T)gf[i];
+            for (int j = 0; j < 12; ++j) H(i, j) = cat * H(i, j) + gi * (T)gf[j];
+        }
+    }
     double e = 1.0;
     if (is_ee && eps_x > 0.0) {
         V3 a = x[1] - x[0], bb = x[3] - x[2];
@@ -431,23 +639,28 @@ __device__ inline bool pair_barrier(const V3* x, bool is_ee, double dhat, double
             R.C[1][3] = 1;
             R.C[1][2] = -1;
             V3 Na, Nb;
-            double Haa[9], Hbb[9], Hab[9];
-            cross_norm_derivs(a, bb, Na, Nb, want_h ? Haa : nullptr, Hbb, Hab);
+            double Hd[9];
+            cross_norm_derivs(a, bb, Na, Nb, nullptr, Hd, Hd);
             double gc[12];
             for (int i = 0; i < 12; ++i) gc[i] = 0.0;
             scatter_grad(gc, R, 0, Na, 1.0);
             scatter_grad(gc, R, 1, Nb, 1.0);
             if (want_h) {
                 // H <- e H_B + b (e2 gc gc^T + e1 d2c) + e1 (gc gB^T + gB gc^T)
+                const T et = (T)e, be2 = (T)(b * e2), e1t = (T)e1;
                 for (int i = 0; i < 12; ++i)
                     for (int j = 0; j < 12; ++j)
-                        H(i, j) = e * H(i, j) + b * e2 * gc[i] * gc[j] + e1 * (gc[i] * gB[j] + gB[i] * gc[j]);
-                double T[9];
-                transpose9(Hab, T);
-                scatter_block(H, R, 0, 0, Haa, b * e1);
-                scatter_block(H, R, 1, 1, Hbb, b * e1);
-                scatter_block(H, R, 0, 1, Hab, b * e1);
-                scatter_block(H, R, 1, 0, T, b * e1);
+                        H(i, j) = et * H(i, j) + be2 * (T)gc[i] * (T)gc[j] +
+                                  e1t * ((T)gc[i] * (T)gB[j] + (T)gB[i] * (T)gc[j]);
+                T Haa[9], Hbb[9], Hab[9], Hba[9];
+                cross_norm_hess_t(to_t<T>(a), to_t<T>(bb), Haa, Hbb, Hab);
+                for (int i = 0; i < 3; ++i)
+                    for (int j = 0; j < 3; ++j) Hba[3 * j + i] = Hab[3 * i + j];
+                const T be1 = (T)(b * e1);
+                scatter_block_t(H, R, 0, 0, Haa, be1);
+                scatter_block_t(H, R, 1, 1, Hbb, be1);
+                scatter_block_t(H, R, 0, 1, Hab, be1);
+                scatter_block_t(H, R, 1, 0, Hba, be1);
             }
             for (int i = 0; i < 12; ++i) gB[i] = e * gB[i] + b * e1 * gc[i];
             b = e * b;

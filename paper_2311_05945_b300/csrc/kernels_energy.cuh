@@ -2,6 +2,7 @@
 // per-element gradients and PSD-projected Hessians written to staging
 // buffers, and energy-only evaluations reduced per environment.
 #pragma once
+#include "barrier_coop.cuh"
 #include "distance.cuh"
 #include "scene.cuh"
 
@@ -452,7 +453,6 @@ __global__ void __launch_bounds__(AF_T) k_affine_gh(Geo G, const double* x, cons
 // Contact barrier (Eq. 4-8) per active pair: gradient and projected Hessian
 // in the 12-dim stencil space.
 // ---------------------------------------------------------------------------
-constexpr int BR_T = 32;
 
 __device__ __forceinline__ double pair_eps_x(const Geo& G, const PairRec& r) {
     if (!r.is_ee) return 0.0;
@@ -461,36 +461,38 @@ __device__ __forceinline__ double pair_eps_x(const Geo& G, const PairRec& r) {
     return 1e-3 * dot(a, a) * dot(b, b);
 }
 
-// Shared memory per thread: the FP64 12x12 Hessian H, then the 9x9 K and its
-// scratch W in T (the projection's precision).
+// Barrier gradient (FP64) and PSD-projected Hessian (T) of the active pairs,
+// one pair per half-warp (see barrier_coop.cuh).
 template <class T>
-__host__ __device__ constexpr size_t barrier_smem_per_thread() {
-    return 144 * sizeof(double) + 162 * sizeof(T);
-}
-
-template <class T>
-__global__ void __launch_bounds__(BR_T) k_barrier_gh(Geo G, const double* X, const PairRec* rec, int n,
-                                                     const double* kappa_env, T* pH, double* pG) {
-    extern __shared__ unsigned char smraw[];
-    int ld = blockDim.x;
-    double* shd = (double*)smraw;
-    T* sht = (T*)(smraw + 144 * sizeof(double) * ld);
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    SMat<12> H{shd + threadIdx.x, ld};
-    SMat<9, T> K{sht + threadIdx.x, ld}, W{sht + 81 * ld + threadIdx.x, ld};
-    PairRec r = rec[i];
-    V3 x[4];
-    for (int k = 0; k < 4; ++k) x[k] = ld3(X + 3 * (size_t)r.s[k]);
-    double kap = kappa_env[G.sv_env[r.s[0]]];
-    double E, g12[12];
-    bool act = pair_barrier(x, r.is_ee != 0, G.dhat, kap, pair_eps_x(G, r), E, g12, H, true);
-    for (int a = 0; a < 12; ++a) pG[(size_t)i * 12 + a] = act ? g12[a] : 0.0;
+__global__ void __launch_bounds__(kCoopLanes * kCoopPairs) k_barrier_gh(Geo G, const double* X, const PairRec* rec,
+                                                                       int n, const double* kappa_env, T* pH,
+                                                                       double* pG) {
+    __shared__ T sm[kCoopPairs][kCoopSmem];
+    const int grp = threadIdx.x / kCoopLanes, lane = threadIdx.x & (kCoopLanes - 1);
+    const int i = blockIdx.x * kCoopPairs + grp;
+    if (i >= n) return;  // the whole half-warp
+    const unsigned mask = 0xFFFFu << (threadIdx.x & 16);
+    T* H = sm[grp];
+    int act = 0;
+    double kap = 0.0;
+    if (lane == 0) {
+        PairRec r = rec[i];
+        V3 x[4];
+        for (int k = 0; k < 4; ++k) x[k] = ld3(X + 3 * (size_t)r.s[k]);
+        kap = kappa_env[G.sv_env[r.s[0]]];
+        double E, g12[12];
+        act = pair_barrier<T>(x, r.is_ee != 0, G.dhat, kap, pair_eps_x(G, r), E, g12, SMat<12, T>{H, 1}, true);
+        for (int a = 0; a < 12; ++a) pG[(size_t)i * 12 + a] = act ? g12[a] : 0.0;
+    }
+    act = __shfl_sync(mask, act, 0, kCoopLanes);
+    kap = __shfl_sync(mask, kap, 0, kCoopLanes);
     T* out = pH + (size_t)i * 144;
-    if (act)
-        project_translation_free<T>(H, kap, K, W, out);
-    else
-        for (int a = 0; a < 144; ++a) out[a] = T(0);
+    if (!act) {
+        for (int e = lane; e < 144; e += kCoopLanes) out[e] = T(0);
+        return;
+    }
+    __syncwarp(mask);
+    coop_project<T>(H, H + 144, H + 244, kap, out, mask);
 }
 
 // barrier energy over a pair list per env (ranges from env_off)

@@ -787,10 +787,6 @@ void build(zema_scene* s) {
     // dynamic shared memory opt-in for the per-thread matrix kernels
     ZCHECK(cudaFuncSetAttribute(k_elastic_gh<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 81 * EL_T * 8));
     ZCHECK(cudaFuncSetAttribute(k_elastic_gh<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 81 * EL_T * 4));
-    ZCHECK(cudaFuncSetAttribute(k_barrier_gh<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(barrier_smem_per_thread<double>() * BR_T)));
-    ZCHECK(cudaFuncSetAttribute(k_barrier_gh<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(barrier_smem_per_thread<float>() * BR_T)));
     ZCHECK(cudaFuncSetAttribute(k_affine_gh<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 81 * AF_T * 8));
     ZCHECK(cudaFuncSetAttribute(k_affine_gh<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 81 * AF_T * 4));
     ZCHECK(cudaStreamSynchronize(st));
@@ -935,11 +931,8 @@ void grad_hess_t(zema_scene* s, bool barrier, bool friction, bool hess) {
     s->pG.ensure(A, 12 * (size_t)nr + 12);
     T* pH = (T*)s->pH.p;
     if (na) {
-        // latency-bound FP64 work: few pairs are spread over many SMs
-        int bt = BR_T;
-        while (bt > 4 && (long long)div_up(na, bt) < 2 * 148) bt >>= 1;
-        ZL(k_barrier_gh<T>, div_up(na, bt), bt, barrier_smem_per_thread<T>() * bt, st)(G, s->X.p, s->act.p, (int)na,
-                                                                                         s->kappa.p, pH, s->pG.p);
+        ZL(k_barrier_gh<T>, div_up(na, kCoopPairs), kCoopLanes * kCoopPairs, 0, st)(G, s->X.p, s->act.p, (int)na,
+                                                                                 s->kappa.p, pH, s->pG.p);
     }
     if (nl)
         ZL(k_friction_gh<T>, div_up(nl, 128), 128, 0, st)(G, s->X.p, s->Xt.p, lagv(s), pH + 144 * (size_t)na,
@@ -2032,27 +2025,32 @@ __global__ void k_sv_env_of(const int* sv_body, const int* b_env, int n, int* sv
     if (i < n) sv_env[i] = b_env[sv_body[i]];
 }
 
-__global__ void __launch_bounds__(BR_T) k_local_barrier(const double* x12, const int* is_ee, const double* eps_x,
-                                                        int n, double dhat, double* e_out, double* g_out,
-                                                        double* H_out) {
-    extern __shared__ unsigned char smraw[];
-    int ld = blockDim.x;
-    double* shd = (double*)smraw;
-    double* sht = (double*)(smraw + 144 * sizeof(double) * ld);
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(kCoopLanes * kCoopPairs) k_local_barrier(const double* x12, const int* is_ee,
+                                                                           const double* eps_x, int n, double dhat,
+                                                                           double* e_out, double* g_out,
+                                                                           double* H_out) {
+    __shared__ double sm[kCoopPairs][kCoopSmem];
+    const int grp = threadIdx.x / kCoopLanes, lane = threadIdx.x & (kCoopLanes - 1);
+    const int i = blockIdx.x * kCoopPairs + grp;
     if (i >= n) return;
-    SMat<12> H{shd + threadIdx.x, ld};
-    SMat<9, double> K{sht + threadIdx.x, ld}, W{sht + 81 * ld + threadIdx.x, ld};
-    V3 x[4];
-    for (int k = 0; k < 4; ++k) x[k] = ld3(x12 + 12 * (size_t)i + 3 * k);
-    double E = 0.0, g[12];
-    bool act = pair_barrier(x, is_ee[i] != 0, dhat, 1.0, eps_x[i], E, g, H, true);
-    e_out[i] = act ? E : 0.0;
-    for (int a = 0; a < 12; ++a) g_out[12 * (size_t)i + a] = act ? g[a] : 0.0;
-    if (act)
-        project_translation_free<double>(H, 1.0, K, W, H_out + 144 * (size_t)i);
-    else
-        for (int a = 0; a < 144; ++a) H_out[144 * (size_t)i + a] = 0.0;
+    const unsigned mask = 0xFFFFu << (threadIdx.x & 16);
+    double* H = sm[grp];
+    int act = 0;
+    if (lane == 0) {
+        V3 x[4];
+        for (int k = 0; k < 4; ++k) x[k] = ld3(x12 + 12 * (size_t)i + 3 * k);
+        double E = 0.0, g[12];
+        act = pair_barrier<double>(x, is_ee[i] != 0, dhat, 1.0, eps_x[i], E, g, SMat<12>{H, 1}, true);
+        e_out[i] = act ? E : 0.0;
+        for (int a = 0; a < 12; ++a) g_out[12 * (size_t)i + a] = act ? g[a] : 0.0;
+    }
+    act = __shfl_sync(mask, act, 0, kCoopLanes);
+    if (!act) {
+        for (int e = lane; e < 144; e += kCoopLanes) H_out[144 * (size_t)i + e] = 0.0;
+        return;
+    }
+    __syncwarp(mask);
+    coop_project<double>(H, H + 144, H + 244, 1.0, H_out + 144 * (size_t)i, mask);
 }
 
 __global__ void k_local_distance(const double* x12, const int* is_ee, int n, double* d2, double* w) {
@@ -2197,9 +2195,7 @@ zema_status zema_local_barrier(int64_t n, const double* x12, const int32_t* is_e
         double* E = T.put<double>(nullptr, (size_t)n);
         double* g = T.put<double>(nullptr, 12 * (size_t)n);
         double* H = T.put<double>(nullptr, 144 * (size_t)n);
-        size_t sm = barrier_smem_per_thread<double>() * BR_T;
-        ZCHECK(cudaFuncSetAttribute(k_local_barrier, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        ZL(k_local_barrier, div_up(n, BR_T), BR_T, sm, st)(dx, de, dp, (int)n, dhat, E, g, H);
+        ZL(k_local_barrier, div_up(n, kCoopPairs), kCoopLanes * kCoopPairs, 0, st)(dx, de, dp, (int)n, dhat, E, g, H);
         ZLAUNCH();
         get(e_out, E, n, st);
         get(g_out, g, 12 * n, st);
