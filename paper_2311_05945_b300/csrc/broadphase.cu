@@ -122,27 +122,30 @@ __global__ void k_boxes(BPView v, int kind, int n, double* box, int* cb, uint32_
     }
 }
 
-// grid entries of one primitive family; bucket keys offset by bucket_base
+// grid entries of one primitive family; bucket keys offset by bucket_base.
+// kEmitLanes lanes per primitive, each taking every kEmitLanes-th cell of the
+// box in x-fastest order (the entry order of the serial loop).
+constexpr int kEmitLanes = 8;
 __global__ void k_emit_entries(BPView v, int n, const int* cb, const uint32_t* off, uint32_t entry_base,
                                uint64_t bucket_base, uint64_t tmask, uint64_t* key, uint32_t* val,
                                uint64_t* cell_tmp, int* prim_tmp, int prim_flag) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = (int)(gt / kEmitLanes), l = (int)(gt % kEmitLanes);
     if (i >= n) return;
-    uint32_t o = off[i], e = off[i + 1];
+    const uint32_t o = off[i], e = off[i + 1];
     if (o == e) return;
     const int* c = cb + 6 * (size_t)i;
-    uint32_t j = entry_base + o, jend = entry_base + e;
-    for (int cz = c[2]; cz <= c[5]; ++cz)
-        for (int cy = c[1]; cy <= c[4]; ++cy)
-            for (int cx = c[0]; cx <= c[3]; ++cx) {
-                if (j >= jend) return;  // never taken: the count pass saw the same box
-                uint64_t ck = pack_cell(cx, cy, cz);
-                key[j] = bucket_base + (mix64(ck) & tmask);
-                val[j] = j;
-                cell_tmp[j] = ck;
-                prim_tmp[j] = i | prim_flag;
-                ++j;
-            }
+    const uint32_t nx = (uint32_t)(c[3] - c[0] + 1), ny = (uint32_t)(c[4] - c[1] + 1);
+    for (uint32_t t = l; t < e - o; t += kEmitLanes) {
+        const uint32_t txy = t % (nx * ny);
+        const int cx = c[0] + (int)(txy % nx), cy = c[1] + (int)(txy / nx), cz = c[2] + (int)(t / (nx * ny));
+        const uint32_t j = entry_base + o + t;
+        uint64_t ck = pack_cell(cx, cy, cz);
+        key[j] = bucket_base + (mix64(ck) & tmask);
+        val[j] = j;
+        cell_tmp[j] = ck;
+        prim_tmp[j] = i | prim_flag;
+    }
 }
 
 __global__ void k_gather_entries(const uint32_t* val, const uint64_t* cell_tmp, const int* prim_tmp, uint64_t* ecell,
@@ -198,58 +201,78 @@ struct Table {
 };
 
 // kind 0: point queries against the triangle table; kind 1: edge queries
-// against the edge table (only pairs with query < entry).
+// against the edge table (only pairs with query < entry).  kQueryLanes lanes
+// per query stride over each cell's bucket; a ballot places the group's hits
+// in entry order, so the output is the serial visiting order (cells in
+// z, y, x order, entries in table order, then the oversize list).
+constexpr int kQueryLanes = 16;
 template <bool WRITE>
 __global__ void k_query(BPView v, int kind, int nq, const double* qbox, const double* ebox_all, const int* qcb,
                         const int* ecb_all, Table T, const int* big, int nbig, int n_entries_all, uint32_t* cnt,
                         const uint32_t* off, int2* out) {
-    int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= nq) return;
+    const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int q = (int)(gt / kQueryLanes), l = (int)(gt % kQueryLanes);
+    if (q >= nq) return;  // the whole group
+    const unsigned gshift = threadIdx.x & 16u;
+    const unsigned gmask = 0xFFFFu << gshift;
     Box6 a = ld_box(qbox + 6 * (size_t)q);
-    uint32_t c = 0;
-    uint32_t o = WRITE ? off[q] : 0u;
-    auto emit = [&](int e) {
-        if (WRITE) out[o + c] = make_int2(q, e);
-        ++c;
+    double nc = box_cells(a, v.inv_cell);
+    if (!(nc <= kMaxQueryCells)) {
+        // large query: handled by k_query_big (one block per query)
+        if (!WRITE && l == 0) cnt[q] = 0;
+        return;
+    }
+    uint32_t c = 0;  // hits so far, the same in all lanes of the group
+    const uint32_t o = WRITE ? off[q] : 0u;
+    auto emit = [&](bool hit, int e) {
+        const unsigned b = (__ballot_sync(gmask, hit) >> gshift) & 0xFFFFu;
+        if (WRITE && hit) out[o + c + __popc(b & ((1u << l) - 1u))] = make_int2(q, e);
+        c += __popc(b);
     };
     auto test = [&](int e) -> bool {
         if (kind == 0) return pt_ok(v, q, e);
         return q < e && ee_ok(v, q, e);
     };
-    double nc = box_cells(a, v.inv_cell);
-    if (!(nc <= kMaxQueryCells)) {
-        // large query: handled by k_query_big (one block per query)
-        if (!WRITE) cnt[q] = 0;
-        return;
-    } else {
-        int qc[6];
-        for (int k = 0; k < 6; ++k) qc[k] = qcb[6 * (size_t)q + k];
-        for (int cz = qc[2]; cz <= qc[5]; ++cz)
-            for (int cy = qc[1]; cy <= qc[4]; ++cy)
-                for (int cx = qc[0]; cx <= qc[3]; ++cx) {
-                    uint64_t ck = pack_cell(cx, cy, cz);
-                    uint64_t bkt = T.bucket_base + (mix64(ck) & T.tmask);
-                    uint32_t s = T.bstart[bkt], f = T.bend[bkt];
-                    for (uint32_t j = s; j < f; ++j) {
-                        if (T.ecell[j] != ck) continue;
-                        int e = T.eprim[j];
-                        if (kind == 1 && e <= q) continue;
+    int qc[6];
+    for (int k = 0; k < 6; ++k) qc[k] = qcb[6 * (size_t)q + k];
+    for (int cz = qc[2]; cz <= qc[5]; ++cz)
+        for (int cy = qc[1]; cy <= qc[4]; ++cy)
+            for (int cx = qc[0]; cx <= qc[3]; ++cx) {
+                uint64_t ck = pack_cell(cx, cy, cz);
+                uint64_t bkt = T.bucket_base + (mix64(ck) & T.tmask);
+                const uint32_t s = T.bstart[bkt], f = T.bend[bkt];
+                for (uint32_t j0 = s; j0 < f; j0 += kQueryLanes) {
+                    const uint32_t j = j0 + l;
+                    bool hit = false;
+                    int e = 0;
+                    if (j < f && T.ecell[j] == ck) {
+                        e = T.eprim[j];
                         // emit only from the cell holding the min corner of the
                         // boxes' intersection (integer test)
                         const int* ec = ecb_all + 6 * (size_t)e;
-                        if (max(qc[0], ec[0]) != cx || max(qc[1], ec[1]) != cy || max(qc[2], ec[2]) != cz) continue;
-                        Box6 b = ld_box(ebox_all + 6 * (size_t)e);
-                        if (overlap(a, b) && test(e)) emit(e);
+                        if (!(kind == 1 && e <= q) && max(qc[0], ec[0]) == cx && max(qc[1], ec[1]) == cy &&
+                            max(qc[2], ec[2]) == cz) {
+                            Box6 b = ld_box(ebox_all + 6 * (size_t)e);
+                            hit = overlap(a, b) && test(e);
+                        }
                     }
+                    emit(hit, e);
                 }
-        for (int k = 0; k < nbig; ++k) {
-            int e = big[k];
-            if (kind == 1 && e <= q) continue;
-            Box6 b = ld_box(ebox_all + 6 * (size_t)e);
-            if (overlap(a, b) && test(e)) emit(e);
+            }
+    for (int k0 = 0; k0 < nbig; k0 += kQueryLanes) {
+        const int k = k0 + l;
+        bool hit = false;
+        int e = 0;
+        if (k < nbig) {
+            e = big[k];
+            if (!(kind == 1 && e <= q)) {
+                Box6 b = ld_box(ebox_all + 6 * (size_t)e);
+                hit = overlap(a, b) && test(e);
+            }
         }
+        emit(hit, e);
     }
-    if (!WRITE) cnt[q] = c;
+    if (!WRITE && l == 0) cnt[q] = c;
 }
 
 // Oversize queries (boxes over kMaxCells cells): one block per query; thread
@@ -363,8 +386,8 @@ void BroadPhase::run(Allocator* A, const BPView& v, cudaStream_t st) {
     bend.ensure(A, Tt + Te);
     ZCHECK(cudaMemsetAsync(bstart.p, 0, (Tt + Te) * sizeof(uint32_t), st));
     ZCHECK(cudaMemsetAsync(bend.p, 0, (Tt + Te) * sizeof(uint32_t), st));
-    if (nt) ZL(k_emit_entries, div_up(nt, TB), TB, 0, st)(v, nt, tcb.p, toff.p, 0, 0, Tt - 1, key.p, val.p, ctmp, ptmp, 0);
-    if (ne) ZL(k_emit_entries, div_up(ne, TB), TB, 0, st)(v, ne, ecb.p, eoff.p, Et, Tt, Te - 1, key.p, val.p, ctmp, ptmp, 0);
+    if (nt) ZL(k_emit_entries, div_up((size_t)nt * kEmitLanes, TB), TB, 0, st)(v, nt, tcb.p, toff.p, 0, 0, Tt - 1, key.p, val.p, ctmp, ptmp, 0);
+    if (ne) ZL(k_emit_entries, div_up((size_t)ne * kEmitLanes, TB), TB, 0, st)(v, ne, ecb.p, eoff.p, Et, Tt, Te - 1, key.p, val.p, ctmp, ptmp, 0);
     ZLAUNCH();
     if (E) {
         int bits = 1;
@@ -398,10 +421,10 @@ void BroadPhase::run(Allocator* A, const BPView& v, cudaStream_t st) {
     if (ne) ZL(k_compact_flags, div_up(ne, TB), TB, 0, st)(pflag.p + nsv, pflagoff.p + nsv, nbp, ne, big_q.p);
     ZLAUNCH();
     if (nsv)
-        ZL(k_query<false>, div_up(nsv, TB), TB, 0, st)(v, 0, nsv, pbox.p, tbox.p, pcb.p, tcb.p, TT, big_t.p, (int)nbt, nt,
+        ZL(k_query<false>, div_up((size_t)nsv * kQueryLanes, TB), TB, 0, st)(v, 0, nsv, pbox.p, tbox.p, pcb.p, tcb.p, TT, big_t.p, (int)nbt, nt,
                                                        qcnt_pt.p, nullptr, nullptr);
     if (ne)
-        ZL(k_query<false>, div_up(ne, TB), TB, 0, st)(v, 1, ne, ebox.p, ebox.p, ecb.p, ecb.p, TE, big_e.p, (int)nbe, ne,
+        ZL(k_query<false>, div_up((size_t)ne * kQueryLanes, TB), TB, 0, st)(v, 1, ne, ebox.p, ebox.p, ecb.p, ecb.p, TE, big_e.p, (int)nbe, ne,
                                                       qcnt_ee.p, nullptr, nullptr);
     if (nbp) ZL(k_query_big<false>, nbp, 256, 0, st)(v, 0, big_p.p, pbox.p, tbox.p, nt, qcnt_pt.p, nullptr, nullptr);
     if (nbq) ZL(k_query_big<false>, nbq, 256, 0, st)(v, 1, big_q.p, ebox.p, ebox.p, ne, qcnt_ee.p, nullptr, nullptr);
@@ -417,10 +440,10 @@ void BroadPhase::run(Allocator* A, const BPView& v, cudaStream_t st) {
     pt.ensure(A, n_pt + 1);
     ee.ensure(A, n_ee + 1);
     if (nsv && n_pt)
-        ZL(k_query<true>, div_up(nsv, TB), TB, 0, st)(v, 0, nsv, pbox.p, tbox.p, pcb.p, tcb.p, TT, big_t.p, (int)nbt, nt, nullptr,
+        ZL(k_query<true>, div_up((size_t)nsv * kQueryLanes, TB), TB, 0, st)(v, 0, nsv, pbox.p, tbox.p, pcb.p, tcb.p, TT, big_t.p, (int)nbt, nt, nullptr,
                                                       qoff_pt.p, pt.p);
     if (ne && n_ee)
-        ZL(k_query<true>, div_up(ne, TB), TB, 0, st)(v, 1, ne, ebox.p, ebox.p, ecb.p, ecb.p, TE, big_e.p, (int)nbe, ne, nullptr,
+        ZL(k_query<true>, div_up((size_t)ne * kQueryLanes, TB), TB, 0, st)(v, 1, ne, ebox.p, ebox.p, ecb.p, ecb.p, TE, big_e.p, (int)nbe, ne, nullptr,
                                                      qoff_ee.p, ee.p);
     if (nbp && n_pt) ZL(k_query_big<true>, nbp, 256, 0, st)(v, 0, big_p.p, pbox.p, tbox.p, nt, nullptr, qoff_pt.p, pt.p);
     if (nbq && n_ee) ZL(k_query_big<true>, nbq, 256, 0, st)(v, 1, big_q.p, ebox.p, ebox.p, ne, nullptr, qoff_ee.p, ee.p);
