@@ -80,18 +80,24 @@ __global__ void k_contact_count(Geo G, const PairRec* rec, int n, uint32_t* cnt_
     cnt_g[i] = (uint32_t)P.m;
 }
 
+// Per pair: its gradient per node and its m x m node blocks B_ab = sum_kl
+// W[a][k] W[b][l] H_kl (slot Hessian blocks weighted by the nodes' slot
+// weights), staged with their (row, col) keys.  kEmitPairLanes lanes per
+// pair, each taking every kEmitPairLanes-th block.
+constexpr int kEmitPairLanes = 8;
 template <class T>
 __global__ void k_contact_emit(Geo G, const PairRec* rec, int n, const T* pH, const double* pG,
                                const uint32_t* off_blk, const uint32_t* off_g, uint64_t* bkey, uint32_t* bval,
                                T* bstage, uint64_t* gkey, uint32_t* gval, double* gstage) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = (int)(gt / kEmitPairLanes), l = (int)(gt % kEmitPairLanes);
     if (i >= n) return;
     PairNodes P;
     pair_nodes(G, rec[i], P);
     const T* H = pH + (size_t)i * 144;
     const double* gg = pG + (size_t)i * 12;
-    uint32_t ob = off_blk[i], og = off_g[i];
-    for (int a = 0; a < P.m; ++a) {
+    const uint32_t ob = off_blk[i], og = off_g[i];
+    for (int a = l; a < P.m; a += kEmitPairLanes) {
         double s[3] = {0, 0, 0};
         for (int k = 0; k < 4; ++k) {
             double w = P.W[a][k];
@@ -102,23 +108,24 @@ __global__ void k_contact_emit(Geo G, const PairRec* rec, int n, const T* pH, co
         gkey[j] = (uint64_t)P.node[a];
         gval[j] = j;
         for (int r = 0; r < 3; ++r) gstage[3 * (size_t)j + r] = s[r];
-        for (int b = 0; b < P.m; ++b) {
-            T B[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-            for (int k = 0; k < 4; ++k) {
-                T wa = (T)P.W[a][k];
-                if (wa == T(0)) continue;
-                for (int l = 0; l < 4; ++l) {
-                    T f = wa * (T)P.W[b][l];
-                    if (f == T(0)) continue;
-                    for (int r = 0; r < 3; ++r)
-                        for (int c = 0; c < 3; ++c) B[3 * r + c] += f * H[12 * (3 * k + r) + 3 * l + c];
-                }
+    }
+    for (int t = l; t < P.m * P.m; t += kEmitPairLanes) {
+        const int a = t / P.m, b = t - a * P.m;
+        T B[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        for (int k = 0; k < 4; ++k) {
+            T wa = (T)P.W[a][k];
+            if (wa == T(0)) continue;
+            for (int q = 0; q < 4; ++q) {
+                T f = wa * (T)P.W[b][q];
+                if (f == T(0)) continue;
+                for (int r = 0; r < 3; ++r)
+                    for (int c = 0; c < 3; ++c) B[3 * r + c] += f * H[12 * (3 * k + r) + 3 * q + c];
             }
-            uint32_t jb = ob + a * P.m + b;
-            bkey[jb] = (uint64_t)P.node[a] * (uint64_t)G.n_nodes + (uint64_t)P.node[b];
-            bval[jb] = jb;
-            for (int q = 0; q < 9; ++q) bstage[9 * (size_t)jb + q] = B[q];
         }
+        const uint32_t jb = ob + t;
+        bkey[jb] = (uint64_t)P.node[a] * (uint64_t)G.n_nodes + (uint64_t)P.node[b];
+        bval[jb] = jb;
+        for (int q = 0; q < 9; ++q) bstage[9 * (size_t)jb + q] = B[q];
     }
 }
 
@@ -139,20 +146,38 @@ __global__ void k_seg_starts(const uint32_t* head, const uint32_t* hoff, uint32_
     if (head[i]) seg[hoff[i]] = i;
 }
 
-// sum W-wide values of each unique key in sorted order (deterministic)
+// Sum the W-wide values of each unique key (deterministic).  One warp per
+// key: lanes stride over the key's sorted segment and a fixed shuffle tree
+// combines them, so the long segments (blocks between an affine body's nodes
+// collect one contribution per pair touching the body) do not serialise.
 template <int W, class T>
 __global__ void k_seg_sum(const uint32_t* seg, uint32_t nu, const uint32_t* perm, const T* stage, T* out,
                           const uint64_t* key, uint64_t* ukey) {
-    uint32_t u = blockIdx.x * blockDim.x + threadIdx.x;
-    if (u >= nu) return;
+    const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t u = (uint32_t)(gt >> 5);
+    const int l = threadIdx.x & 31;
+    if (u >= nu) return;  // the whole warp
     T s[W];
+#pragma unroll
     for (int q = 0; q < W; ++q) s[q] = 0;
-    for (uint32_t i = seg[u]; i < seg[u + 1]; ++i) {
+    const uint32_t b = seg[u], e = seg[u + 1];
+    for (uint32_t i = b + l; i < e; i += 32) {
         const T* v = stage + (size_t)W * perm[i];
+#pragma unroll
         for (int q = 0; q < W; ++q) s[q] += v[q];
     }
-    for (int q = 0; q < W; ++q) out[(size_t)W * u + q] = s[q];
-    ukey[u] = key[seg[u]];
+#pragma unroll
+    for (int q = 0; q < W; ++q) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s[q] += __shfl_xor_sync(0xffffffffu, s[q], o);
+    }
+    if (l < W) {
+        T r = s[0];
+#pragma unroll
+        for (int q = 1; q < W; ++q) r = (l == q) ? s[q] : r;
+        out[(size_t)W * u + l] = r;
+    }
+    if (l == 0) ukey[u] = key[b];
 }
 
 // contact BSR: row pointers and columns from the unique (row, col) keys

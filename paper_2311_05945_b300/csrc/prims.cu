@@ -101,11 +101,12 @@ int zema_profile_read(double* ms_total, long long* launches, double* alg_bytes) 
 namespace zema {
 
 constexpr int SCAN_T = 256;
-constexpr int SCAN_PER = 4;
+constexpr int SCAN_PER = 16;
 constexpr int SCAN_TILE = SCAN_T * SCAN_PER;
 
-// per-block exclusive scan of SCAN_TILE elements; block totals to sums
-__global__ void k_scan_block(const uint32_t* in, uint32_t* out, size_t n, uint32_t* sums) {
+// per-block exclusive scan of SCAN_TILE elements; block totals to sums; a
+// single-block scan also writes the total to out[n] when `total` is set
+__global__ void k_scan_block(const uint32_t* in, uint32_t* out, size_t n, uint32_t* sums, int total) {
     __shared__ uint32_t wsum[SCAN_T / 32];
     size_t base = (size_t)blockIdx.x * SCAN_TILE + (size_t)threadIdx.x * SCAN_PER;
     uint32_t v[SCAN_PER];
@@ -134,7 +135,10 @@ __global__ void k_scan_block(const uint32_t* in, uint32_t* out, size_t n, uint32
             if (lane >= o) wi += t;
         }
         if (lane < SCAN_T / 32) wsum[lane] = wi - ws;  // exclusive warp offsets
-        if (lane == SCAN_T / 32 - 1) sums[blockIdx.x] = wi;
+        if (lane == SCAN_T / 32 - 1) {
+            sums[blockIdx.x] = wi;
+            if (total) out[n] = wi;
+        }
     }
     __syncthreads();
     uint32_t run = wsum[w] + inc - s;
@@ -145,22 +149,17 @@ __global__ void k_scan_block(const uint32_t* in, uint32_t* out, size_t n, uint32
     }
 }
 
-__global__ void k_scan_add(uint32_t* out, size_t n, const uint32_t* offs) {
+// adds the scanned block offsets; the last block's thread 0 also writes the
+// total to out[n] when `total` is set
+__global__ void k_scan_add(uint32_t* out, size_t n, const uint32_t* offs, const uint32_t* sums, int total) {
     size_t i = (size_t)blockIdx.x * SCAN_TILE + threadIdx.x;
     uint32_t o = offs[blockIdx.x];
     for (int k = 0; k < SCAN_PER; ++k, i += SCAN_T)
         if (i < n) out[i] += o;
+    if (total && threadIdx.x == 0 && blockIdx.x == gridDim.x - 1) out[n] = o + sums[blockIdx.x];
 }
 
-__global__ void k_set_total(uint32_t* out, size_t n, const uint32_t* in, const uint32_t* scanned_sums,
-                            int last_block) {
-    // out[n] = exclusive(n-1) + in[n-1]
-    if (n == 0) {
-        out[0] = 0;
-        return;
-    }
-    out[n] = out[n - 1] + in[n - 1];
-}
+__global__ void k_set_total_zero(uint32_t* out) { out[0] = 0; }
 
 size_t scan_tmp_size(size_t n) {
     size_t total = 0;
@@ -173,24 +172,27 @@ size_t scan_tmp_size(size_t n) {
     return total + 2 * SCAN_TILE + 8;
 }
 
-static void scan_rec(const uint32_t* in, uint32_t* out, size_t n, uint32_t* tmp, cudaStream_t st) {
-    if (n == 0) return;
+static void scan_rec(const uint32_t* in, uint32_t* out, size_t n, uint32_t* tmp, int total, cudaStream_t st) {
     size_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
     uint32_t* sums = tmp;
     uint32_t* soff = tmp + nb + 1;
-    ZL(k_scan_block, (unsigned)nb, SCAN_T, 0, st)(in, out, n, sums);
+    ZL(k_scan_block, (unsigned)nb, SCAN_T, 0, st)(in, out, n, sums, total && nb == 1);
     ZLAUNCH();
     if (nb > 1) {
-        scan_rec(sums, soff, nb, tmp + 2 * nb + 2, st);
-        ZL(k_scan_add, (unsigned)nb, SCAN_T, 0, st)(out, n, soff);
+        scan_rec(sums, soff, nb, tmp + 2 * nb + 2, 0, st);
+        ZL(k_scan_add, (unsigned)nb, SCAN_T, 0, st)(out, n, soff, sums, total);
         ZLAUNCH();
     }
 }
 
+// out[0..n) = exclusive scan of in, out[n] = total
 void exclusive_scan(const uint32_t* in, uint32_t* out, size_t n, uint32_t* tmp, cudaStream_t st) {
-    scan_rec(in, out, n, tmp, st);
-    ZL(k_set_total, 1, 1, 0, st)(out, n, in, nullptr, 0);
-    ZLAUNCH();
+    if (n == 0) {
+        ZL(k_set_total_zero, 1, 1, 0, st)(out);
+        ZLAUNCH();
+        return;
+    }
+    scan_rec(in, out, n, tmp, 1, st);
 }
 
 // ---------------------------------------------------------------------------

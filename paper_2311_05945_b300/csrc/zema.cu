@@ -974,7 +974,7 @@ void grad_hess_t(zema_scene* s, bool barrier, bool friction, bool hess) {
     s->gval.ensure(A, ng + 1);
     s->gval2.ensure(A, ng + 1);
     s->gstage.ensure(A, 3 * (size_t)ng + 3);
-    ZL(k_contact_emit<T>, div_up(nr, 128), 128, 0, st)(G, recs.p, (int)nr, pH, s->pG.p, s->off_blk.p, s->off_g.p,
+    ZL(k_contact_emit<T>, div_up((long long)nr * kEmitPairLanes, 128), 128, 0, st)(G, recs.p, (int)nr, pH, s->pG.p, s->off_blk.p, s->off_g.p,
                                                         s->bkey.p, s->bval.p, (T*)s->bstage.p, s->gkey.p, s->gval.p,
                                                         s->gstage.p);
     ZLAUNCH();
@@ -997,7 +997,7 @@ void grad_hess_t(zema_scene* s, bool barrier, bool friction, bool hess) {
     uint32_t nu = s->h32[2];
     s->C_val.ensure(A, 9 * (size_t)nu + 9);
     s->C_col.ensure(A, nu + 1);
-    ZL((k_seg_sum<9, T>), div_up(nu, 128), 128, 0, st)(s->seg.p, nu, s->bval.p, (const T*)s->bstage.p, (T*)s->C_val.p,
+    ZL((k_seg_sum<9, T>), div_up(32 * (long long)nu, 128), 128, 0, st)(s->seg.p, nu, s->bval.p, (const T*)s->bstage.p, (T*)s->C_val.p,
                                                         s->bkey.p, s->ukey.p);
     ZL(k_contact_rows, div_up(s->n_nodes + 1, TB), TB, 0, st)(s->ukey.p, nu, s->n_nodes, s->C_rowptr.p, s->C_col.p);
     ZLAUNCH();
@@ -1010,7 +1010,7 @@ void grad_hess_t(zema_scene* s, bool barrier, bool friction, bool hess) {
     ZCHECK(cudaStreamSynchronize(st));
     uint32_t nug = s->h32[3];
     s->gsum.ensure(A, 3 * (size_t)nug + 3);
-    ZL((k_seg_sum<3, double>), div_up(nug, 128), 128, 0, st)(s->seg.p, nug, s->gval.p, s->gstage.p, s->gsum.p,
+    ZL((k_seg_sum<3, double>), div_up(32 * (long long)nug, 128), 128, 0, st)(s->seg.p, nug, s->gval.p, s->gstage.p, s->gsum.p,
                                                               s->gkey.p, s->ukey.p);
     ZL(k_add_contact_grad, div_up(nug, 128), 128, 0, st)(s->ukey.p, s->gsum.p, nug, s->g.p);
     ZLAUNCH();
