@@ -504,26 +504,34 @@ __device__ inline void d2_hess_t(const V3* x, bool is_ee, const DistInfo& di, SM
         scatter_block_t(H, R, 1, 1, M, T(1));
         return;
     }
-    // plane (PT) or line-line (EE): f = (r . (a x b))^2 / |a x b|^2
-    V3t<T> r = to_t<T>(v[0]), a = to_t<T>(v[1]), b = to_t<T>(v[2]);
-    V3t<T> n = cross_t(a, b);
-    T N = dot_t(n, n), s = dot_t(r, n);
-    T aa = dot_t(a, a), bb = dot_t(b, b), ab = dot_t(a, b);
-    V3t<T> Na{T(2) * (bb * a.x - ab * b.x), T(2) * (bb * a.y - ab * b.y), T(2) * (bb * a.z - ab * b.z)};
-    V3t<T> Nb{T(2) * (aa * b.x - ab * a.x), T(2) * (aa * b.y - ab * a.y), T(2) * (aa * b.z - ab * a.z)};
-    V3t<T> S[3] = {n, cross_t(b, r), cross_t(r, a)};
-    V3t<T> Ng[3] = {V3t<T>{0, 0, 0}, Na, Nb};
+    // plane (PT) or line-line (EE): f = (r . (a x b))^2 / |a x b|^2.  With
+    // n = a x b, N = |n|^2, s = r . n the Hessian blocks carry 1/N, s/N^2 and
+    // s^2/N^3, which leave FP32's range for nearly parallel edges.  They are
+    // formed in FP64 on vectors normalised by q = 1/|n| (S_k q, Ng_k q^2,
+    // s q = the signed distance), so every value rounded to T is of the size
+    // of the Hessian entries themselves.
+    const V3 rd = v[0], ad = v[1], bd = v[2];
+    const V3 nd = cross(ad, bd);
+    const double Nd = dot(nd, nd), qd = 1.0 / sqrt(Nd), sh = dot(rd, nd) * qd;
+    const double aad = dot(ad, ad), bbd = dot(bd, bd), abd = dot(ad, bd);
+    const V3 Sd[3] = {nd, cross(bd, rd), cross(rd, ad)};
+    V3t<T> Sh[3], Ngh[3];
+    for (int k = 0; k < 3; ++k) Sh[k] = to_t<T>(qd * Sd[k]);
+    Ngh[0] = V3t<T>{0, 0, 0};
+    Ngh[1] = to_t<T>((2.0 * qd * qd) * (bbd * ad - abd * bd));
+    Ngh[2] = to_t<T>((2.0 * qd * qd) * (aad * bd - abd * ad));
+    const V3t<T> r = to_t<T>(rd), a = to_t<T>(ad), b = to_t<T>(bd);
     T Haa[9], Hbb[9], Hab[9];
     cross_norm_hess_t(a, b, Haa, Hbb, Hab);
-    const T iN = T(1) / N, iN2 = iN * iN, iN3 = iN2 * iN;
-    const T cs = T(2) * s * iN, cn = -s * s * iN2;
+    const T c2 = (T)(-2.0 * sh), c3 = (T)(2.0 * sh * sh);
+    const T cs = (T)(2.0 * sh * qd), cn = (T)(-sh * sh * qd * qd);
     for (int k = 0; k < 3; ++k)
         for (int l = 0; l < 3; ++l) {
             zero9_t(M);
-            outer_t(M, S[k], S[l], T(2) * iN);
-            outer_t(M, S[k], Ng[l], T(-2) * s * iN2);
-            outer_t(M, Ng[k], S[l], T(-2) * s * iN2);
-            outer_t(M, Ng[k], Ng[l], T(2) * s * s * iN3);
+            outer_t(M, Sh[k], Sh[l], T(2));
+            outer_t(M, Sh[k], Ngh[l], c2);
+            outer_t(M, Ngh[k], Sh[l], c2);
+            outer_t(M, Ngh[k], Ngh[l], c3);
             if (k == 0 && l == 1) add_skew_t(M, b, -cs);
             if (k == 1 && l == 0) add_skew_t(M, b, cs);
             if (k == 0 && l == 2) add_skew_t(M, a, cs);

@@ -483,11 +483,18 @@ __global__ void __launch_bounds__(kCoopLanes * kCoopPairs) k_barrier_gh(Geo G, c
         double E, g12[12];
         act = pair_barrier<T>(x, r.is_ee != 0, G.dhat, kap, pair_eps_x(G, r), E, g12, SMat<12, T>{H, 1}, true);
         for (int a = 0; a < 12; ++a) pG[(size_t)i * 12 + a] = act ? g12[a] : 0.0;
+        // a Hessian outside T's range (degenerate stencil) is left out: the
+        // pair still contributes its exact FP64 gradient
+        if (act) {
+            bool finite = true;
+            for (int a = 0; a < 144; ++a) finite &= isfinite(H[a]);
+            if (!finite) act = 2;
+        }
     }
     act = __shfl_sync(mask, act, 0, kCoopLanes);
     kap = __shfl_sync(mask, kap, 0, kCoopLanes);
     T* out = pH + (size_t)i * 144;
-    if (!act) {
+    if (act != 1) {
         for (int e = lane; e < 144; e += kCoopLanes) out[e] = T(0);
         return;
     }

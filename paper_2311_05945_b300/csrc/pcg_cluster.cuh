@@ -43,7 +43,7 @@ struct PcgcArgs {
     Real* z;             // preconditioned residual, 3 per node (exchanged through L2)
     const Real* Minv_s;  // 9 per soft node
     const Real* Minv_a;  // 144 per affine body
-    int* conv;           // per env in: 1 = skip; out: 1
+    int* conv;           // per env in: 1 = skip; out: 1, or 2 after a non-finite value
     int* iters;          // per env: iterations run
     double tol2;
     int max_iter;
@@ -239,7 +239,8 @@ __global__ void __launch_bounds__(kPcgcThreads) k_pcg_cluster(PcgcArgs<Real> a) 
     Real rz = s_tot[1];
     const Real bb = s_tot[2];
     const Real stop2 = (Real)a.tol2 * bb;
-    bool done = !(bb > Real(0));
+    bool bad = !isfinite(bb);
+    bool done = bad || !(bb > Real(0));
     Real beta = 0;
     int it = 0;
     const int warp = tid >> 5, half = (tid >> 4) & 1, gl = tid & (kPcgcGroup - 1);
@@ -295,7 +296,10 @@ __global__ void __launch_bounds__(kPcgcThreads) k_pcg_cluster(PcgcArgs<Real> a) 
         cl.sync();  // B1
         cluster_total<1>(cl, s_part, s_tot);
         const Real pqt = s_tot[0];
-        if (!(pqt > Real(0))) break;  // breakdown (not positive definite): keep x, stop (same in all CTAs)
+        if (!(pqt > Real(0))) {  // breakdown: keep x and stop (same in all CTAs); non-finite is an error
+            bad = !isfinite(pqt);
+            break;
+        }
         const Real alpha = rz / pqt;
         // ---- x += alpha p, r -= alpha q, z = M^-1 r on the owned units
         Real acc[2] = {0, 0};
@@ -345,6 +349,7 @@ __global__ void __launch_bounds__(kPcgcThreads) k_pcg_cluster(PcgcArgs<Real> a) 
         cluster_total<2>(cl, s_part + 1, s_tot + 1);
         const Real rz_new = s_tot[1], rr = s_tot[2];
         ++it;
+        if (!isfinite(rr)) bad = done = true;
         if (!(rr > stop2)) done = true;
         beta = rz != Real(0) ? rz_new / rz : Real(0);
         rz = rz_new;
@@ -360,7 +365,7 @@ __global__ void __launch_bounds__(kPcgcThreads) k_pcg_cluster(PcgcArgs<Real> a) 
     if (own_a) a.x_out[3 * (size_t)ns1 + tid] = (double)xa;
     if (rank == 0 && tid == 0) {
         a.iters[e] = it;
-        a.conv[e] = 1;
+        a.conv[e] = bad ? 2 : 1;  // 2: non-finite right-hand side or matrix
     }
     cl.sync();  // no CTA leaves while a partner may still read its shared memory
 }

@@ -1180,7 +1180,11 @@ int64_t pcg_t(zema_scene* s, const std::vector<int>& done_h) {
     }
     ZLAUNCH();
     ZCHECK(cudaMemcpyAsync(s->hi, s->pcg_iters.p, NE * sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (use_cluster) ZCHECK(cudaMemcpyAsync(s->hi + NE, s->conv.p, NE * sizeof(int), cudaMemcpyDeviceToHost, st));
     ZCHECK(cudaStreamSynchronize(st));
+    if (use_cluster)
+        for (int e = 0; e < NE; ++e)
+            if (s->hi[NE + e] == 2) fail(ZEMA_ERR_NONFINITE, "non-finite value in the linear solve");
     int64_t tot = 0, mx = 0;
     for (int e = 0; e < NE; ++e) {
         tot += s->hi[e];

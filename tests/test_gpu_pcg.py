@@ -116,3 +116,21 @@ def test_batched_deterministic_and_kinds_agree():
         # the two solver forms differ in summation order and vector precision:
         # equal to within the (tightened) Newton tolerance
         assert np.abs(pa - pc).max() < 1e-5 * a_diag[e]
+
+
+def test_c2_mixed_follows_fp64_through_first_contact():
+    # the full-size grasp: fine meshes put nearly parallel edge pairs in
+    # contact, whose Hessian factors leave FP32's range unless normalised;
+    # the mixed mode must take real Newton steps and follow the FP64 run
+    sc = S.scene_c2()
+    a = gpu_scene(sc, precision=0)
+    b = gpu_scene(sc, precision=1)
+    diag = Oracle(sc).diag()
+    for k in range(20):
+        sa = a.step(1)
+        sb = b.step(1)
+        assert sb["al_rounds"] < sc.params.max_al_rounds, (k, sb)
+        if sa["newton_iters"] > 0:
+            assert sb["newton_iters"] > 0 and sb["pcg_iters"] > 0, (k, sa, sb)
+    err = np.abs(env_positions(a, sc, 0) - env_positions(b, sc, 0)).max()
+    assert err < 1e-4 * diag, err / diag
