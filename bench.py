@@ -197,20 +197,30 @@ def run_ours(args, rank, world):
     clk = clocks.stop()
     value = world * args.steps / (total_ms / 1e3)
     plain_value = world * args.steps / (plain_ms / 1e3)
-    # end to end through the C ABI with pinned host buffers
-    e2e_steps = max(1, min(args.steps, args.e2e_steps))
+    # end to end through the C ABI with pinned host buffers, over the same
+    # step window [W, W + K) of a fresh scene: every timed step uploads the
+    # bodies' states from pinned host memory, steps, and reads them back
+    from paper_2311_05945_b300 import zema as Z
+    e2e_steps = args.steps if args.e2e_steps is None else max(1, min(args.steps, args.e2e_steps))
+    g2 = Z.Scene(sc, precision=1)
+    for _ in range(args.warmup):
+        g2.step(1)
     bodies = list(range(len(sc.body_order())))
-    host = [torch.from_numpy(gpu.get_state(b)).pin_memory() for b in bodies]
+    host = [torch.from_numpy(g2.get_state(b)).pin_memory() for b in bodies]
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         for b in bodies:
-            gpu.set_state_ptr(b, host[b].data_ptr(), host[b].numel())
-        gpu.step(1)
+            g2.set_state_ptr(b, host[b].data_ptr(), host[b].numel())
+        g2.step(1)
         for b in bodies:
-            gpu.get_state_ptr(b, host[b].data_ptr(), host[b].numel())
+            g2.get_state_ptr(b, host[b].data_ptr(), host[b].numel())
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     e2e_val = e2e_steps / e2e_s
+    g2.close()
     if dist:
         t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -236,15 +246,16 @@ def run_ours(args, rank, world):
         v, dt = oracle_steps_per_s(0, args.cpu_steps)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"grasp steps [0, {args.cpu_steps}) of the same script on the CPU oracle ({dt:.1f} s)"}
-    agg = {k: sum(s[k] for s in stats) for k in ("newton_iters", "pcg_iters", "ls_halvings", "al_rounds")}
+    agg = {k: sum(s[k] for s in stats) for k in ("newton_iters", "pcg_iters", "ls_halvings", "al_rounds", "pcg_refines")}
     phase = {k: sum(s["ms_phase"][k] for s in stats) for k in stats[0]["ms_phase"]}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "mixed f32/f64", "data": "synthetic (seeded generators)",
         "config": {"workload": WORKLOAD, "timed_steps": [args.warmup, args.warmup + args.steps],
-                   "form": "mixed precision (FP32 Hessians/matrices, FP64 gradients/energies/distances/CCD/"
-                           "convergence) + CCD-filtered constant-velocity warm start; 1 env so no batching",
+                   "form": "mixed precision (FP32 Hessians, matrices and PCG with FP64 residual refinement; FP64 "
+                           "gradients/energies/distances/CCD/convergence) + CCD-filtered constant-velocity warm "
+                           "start; 1 env so no batching",
                    "plain_fp64": {"value": plain_value, "ms_per_step": plain_ms / args.steps,
                                   "newton_iters": sum(s["newton_iters"] for s in plain_stats),
                                   "pcg_iters": sum(s["pcg_iters"] for s in plain_stats)},
@@ -253,6 +264,7 @@ def run_ours(args, rank, world):
                    "l2": "flushed between timed steps (512 MB write)",
                    "newton_iters": agg["newton_iters"], "pcg_iters": agg["pcg_iters"],
                    "ls_halvings": agg["ls_halvings"], "al_rounds": agg["al_rounds"],
+                   "pcg_fp64_refinements": agg["pcg_refines"],
                    "host_phase_ms": {k: round(v, 2) for k, v in phase.items()}},
         "roofline": roof,
         "cpu_baseline": cpu,
@@ -272,7 +284,8 @@ def main():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=None,
+                    help="end-to-end steps (default: the timed steps, same window)")
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-region", action="store_true",

@@ -96,6 +96,7 @@ typedef struct {
     double kappa;           /* barrier stiffness of env 0 after the last step */
     double energy;          /* incremental potential of env 0 at the last converged iterate */
     double ms_phase[6];     /* host-timed phases: DCD, energy, Hessian, linear, CCD, other (ms) */
+    int64_t pcg_refines;    /* FP64 residual-refinement restarts of FP32 solves (mixed precision) */
 } zema_step_stats;
 
 /* Fills *p with defaults: dt 0.01, dhat 1e-3, adaptive kappa, eps_v 1e-3,

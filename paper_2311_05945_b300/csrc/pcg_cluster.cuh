@@ -57,6 +57,7 @@ constexpr int kPcgcGroup = 16;  // lanes per row in the SpMV
 constexpr int kPcgcMaxCluster = 16;
 constexpr int kPcgcStageBatch = 4;  // nodes per thread whose loads are issued together
 constexpr int kPcgcOwn = 2;         // soft rows per thread: a CTA owns at most 2 * kPcgcThreads rows
+constexpr int kPcgcRefine = 3;      // FP64 residual refinements of an FP32 solve
 
 __device__ __forceinline__ float ldcg_r(const float* p) { return __ldcg(p); }
 __device__ __forceinline__ double ldcg_r(const double* p) { return __ldcg(p); }
@@ -368,6 +369,42 @@ __global__ void __launch_bounds__(kPcgcThreads) k_pcg_cluster(PcgcArgs<Real> a) 
         a.conv[e] = bad ? 2 : 1;  // 2: non-finite right-hand side or matrix
     }
     cl.sync();  // no CTA leaves while a partner may still read its shared memory
+}
+
+// FP64 residual of an FP32 solve: r = b - A x per node (A the stored FP32
+// matrix S + C, products and sums in FP64), zero for envs flagged in skip.
+// One warp per row, lanes over the row's blocks, a fixed shuffle tree.
+template <class T>
+__global__ void k_residual64(Geo G, Bsr<T> S, Bsr<T> C, const double* x, const double* b, const int* skip,
+                             double* r) {
+    const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = (int)(gt >> 5), l = threadIdx.x & 31;
+    if (n >= G.n_nodes) return;  // the whole warp
+    double y[3] = {0.0, 0.0, 0.0};
+    for (int pass = 0; pass < 2; ++pass) {
+        const Bsr<T>& A = pass ? C : S;
+        for (int k = A.rowptr[n] + l; k < A.rowptr[n + 1]; k += 32) {
+            const T* v = A.val + 9 * (size_t)k;
+            const double* xc = x + 3 * (size_t)A.col[k];
+            for (int i = 0; i < 3; ++i)
+                y[i] += (double)v[3 * i] * xc[0] + (double)v[3 * i + 1] * xc[1] + (double)v[3 * i + 2] * xc[2];
+        }
+    }
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) y[i] += __shfl_xor_sync(0xffffffffu, y[i], o);
+    if (l < 3) {
+        const double yi = l == 0 ? y[0] : (l == 1 ? y[1] : y[2]);
+        const size_t o = 3 * (size_t)n + l;
+        r[o] = skip[G.node_env[n]] ? 0.0 : b[o] - yi;
+    }
+}
+
+// p += dx on the envs flagged in need
+__global__ void k_add_env(Geo G, double* p, const double* dx, const int* need) {
+    int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= G.n_nodes || !need[G.node_env[n]]) return;
+    for (int j = 0; j < 3; ++j) p[3 * (size_t)n + j] += dx[3 * (size_t)n + j];
 }
 
 }  // namespace zema

@@ -1118,30 +1118,90 @@ int64_t pcg_t(zema_scene* s, const std::vector<int>& done_h) {
         fail(ZEMA_ERR_INVALID_ARG, "cluster PCG unavailable for this scene on this device");
     const bool use_cluster = s->P.pcg_kind != 1 && s->pcgc_cs[pi] > 0;
     const char* kname = use_cluster ? "k_pcg_cluster" : "k_pcg_persistent";
+    int64_t tot = 0, mx = 0;
+    // iterations of the last launch (and its non-finite flags) into tot / mx
+    auto collect = [&](bool cluster) {
+        ZCHECK(cudaMemcpyAsync(s->hi, s->pcg_iters.p, NE * sizeof(int), cudaMemcpyDeviceToHost, st));
+        if (cluster) ZCHECK(cudaMemcpyAsync(s->hi + NE, s->conv.p, NE * sizeof(int), cudaMemcpyDeviceToHost, st));
+        ZCHECK(cudaStreamSynchronize(st));
+        for (int e = 0; e < NE; ++e) {
+            if (cluster && s->hi[NE + e] == 2) fail(ZEMA_ERR_NONFINITE, "non-finite value in the linear solve");
+            tot += s->hi[e];
+            mx = std::max<int64_t>(mx, s->hi[e]);
+        }
+    };
     if (use_cluster) {
         const int cs = s->pcgc_cs[pi];
-        PcgcArgs<T> c;
-        c.G = G;
-        c.S = S;
-        c.C = C;
-        c.b = s->b.p;
-        c.x_out = s->p.p;
-        c.z = (T*)s->z.p;
-        c.Minv_s = Minv_s;
-        c.Minv_a = Minv_a;
-        c.conv = s->conv.p;
-        c.iters = s->pcg_iters.p;
-        c.tol2 = s->P.pcg_rel_tol * s->P.pcg_rel_tol;
-        c.max_iter = s->P.max_pcg;
-        c.max_env_nodes = s->pcgc_max_env_nodes;
-        c.max_rows = pcgc_max_rows(s, cs);
-        c.max_aff = s->pcgc_max_aff;
-        cudaLaunchConfig_t cfg = {};
-        cudaLaunchAttribute at[1];
-        pcgc_config<T>(s, cs, cfg, at);
-        cfg.stream = st;
-        LaunchScope ls("k_pcg_cluster");
-        ZCHECK(cudaLaunchKernelEx(&cfg, k_pcg_cluster<T>, c));
+        auto run_cluster = [&](const double* rhs, double* xo) {
+            PcgcArgs<T> c;
+            c.G = G;
+            c.S = S;
+            c.C = C;
+            c.b = rhs;
+            c.x_out = xo;
+            c.z = (T*)s->z.p;
+            c.Minv_s = Minv_s;
+            c.Minv_a = Minv_a;
+            c.conv = s->conv.p;
+            c.iters = s->pcg_iters.p;
+            c.tol2 = s->P.pcg_rel_tol * s->P.pcg_rel_tol;
+            c.max_iter = s->P.max_pcg;
+            c.max_env_nodes = s->pcgc_max_env_nodes;
+            c.max_rows = pcgc_max_rows(s, cs);
+            c.max_aff = s->pcgc_max_aff;
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute at[1];
+            pcgc_config<T>(s, cs, cfg, at);
+            cfg.stream = st;
+            {
+                LaunchScope ls("k_pcg_cluster");
+                ZCHECK(cudaLaunchKernelEx(&cfg, k_pcg_cluster<T>, c));
+            }
+            ZLAUNCH();
+            collect(true);
+        };
+        run_cluster(s->b.p, s->p.p);
+        if (sizeof(T) < sizeof(double)) {
+            // FP64 residual refinement of the FP32 solve: r = b - A x with
+            // FP64 products; while |r| > tol |b| solve A d = r and add d
+            std::vector<int> need(NE);
+            for (int e = 0; e < NE; ++e) need[e] = done_h[e] ? 0 : 1;
+            const size_t nc = (size_t)NE * kChunks;
+            std::vector<double> prr(nc), pbb(nc);
+            for (int ref = 0; ref < kPcgcRefine; ++ref) {
+                for (int e = 0; e < NE; ++e) s->hi[e] = need[e] ? 0 : 1;
+                ZCHECK(cudaMemcpyAsync(s->conv.p, s->hi, NE * sizeof(int), cudaMemcpyHostToDevice, st));
+                ZL(k_residual64<T>, div_up(32 * (long long)s->n_nodes, 128), 128, 0, st)(G, S, C, s->p.p, s->b.p,
+                                                                                        s->conv.p, s->q.p);
+                ZL(k_env_dot2, red_grid(NE), kRedThreads, 0, st)(G, s->b.p, s->q.p, s->part4.p, s->part5.p);
+                ZL(k_env_dot2, red_grid(NE), kRedThreads, 0, st)(G, s->q.p, s->b.p, s->part6.p, s->part7.p);
+                ZLAUNCH();
+                ZCHECK(cudaMemcpyAsync(prr.data(), s->part5.p, nc * sizeof(double), cudaMemcpyDeviceToHost, st));
+                ZCHECK(cudaMemcpyAsync(pbb.data(), s->part7.p, nc * sizeof(double), cudaMemcpyDeviceToHost, st));
+                ZCHECK(cudaStreamSynchronize(st));
+                int count = 0;
+                for (int e = 0; e < NE; ++e) {
+                    if (!need[e]) continue;
+                    double rr = 0.0, bbv = 0.0;
+                    for (int k = 0; k < kChunks; ++k) {
+                        rr += prr[(size_t)e * kChunks + k];
+                        bbv += pbb[(size_t)e * kChunks + k];
+                    }
+                    if (!std::isfinite(rr)) fail(ZEMA_ERR_NONFINITE, "non-finite residual of the linear solve");
+                    need[e] = rr > s->P.pcg_rel_tol * s->P.pcg_rel_tol * bbv ? 1 : 0;
+                    count += need[e];
+                }
+                if (!count) break;
+                s->S.pcg_refines += count;
+                for (int e = 0; e < NE; ++e) s->hi[e] = need[e] ? 0 : 1;
+                ZCHECK(cudaMemcpyAsync(s->conv.p, s->hi, NE * sizeof(int), cudaMemcpyHostToDevice, st));
+                run_cluster(s->q.p, s->r.p);
+                for (int e = 0; e < NE; ++e) s->hi[e] = need[e];
+                ZCHECK(cudaMemcpyAsync(s->need.p, s->hi, NE * sizeof(int), cudaMemcpyHostToDevice, st));
+                ZL(k_add_env, div_up(s->n_nodes, TB), TB, 0, st)(G, s->p.p, s->r.p, s->need.p);
+                ZLAUNCH();
+            }
+        }
     } else {
         PcgArgs<T> a;
         a.G = G;
@@ -1177,34 +1237,21 @@ int64_t pcg_t(zema_scene* s, const std::vector<int>& done_h) {
             LaunchScope ls("k_pcg_persistent");
             ZCHECK(cudaLaunchCooperativeKernel((const void*)k_pcg_persistent<T>, dim3(grid), dim3(256), args, smem, st));
         }
-    }
-    ZLAUNCH();
-    ZCHECK(cudaMemcpyAsync(s->hi, s->pcg_iters.p, NE * sizeof(int), cudaMemcpyDeviceToHost, st));
-    if (use_cluster) ZCHECK(cudaMemcpyAsync(s->hi + NE, s->conv.p, NE * sizeof(int), cudaMemcpyDeviceToHost, st));
-    ZCHECK(cudaStreamSynchronize(st));
-    if (use_cluster)
-        for (int e = 0; e < NE; ++e)
-            if (s->hi[NE + e] == 2) fail(ZEMA_ERR_NONFINITE, "non-finite value in the linear solve");
-    int64_t tot = 0, mx = 0;
-    for (int e = 0; e < NE; ++e) {
-        tot += s->hi[e];
-        mx = std::max<int64_t>(mx, s->hi[e]);
+        ZLAUNCH();
+        collect(false);
     }
     // Algorithmic bytes of the solve for the live roofline, per iteration:
-    // SpMV reads every block (9 values + 4 B column), both row-pointer
-    // arrays, p, and writes q; the update reads/writes x and r, reads p and q,
-    // writes z, reads the preconditioner (9 values per soft node, 144 per
-    // affine body); the direction update reads z and reads/writes p.
-    // The cluster solve keeps q on chip and recomputes p while staging it:
-    // per node it reads z and p_{k-1}, writes p_k, reads/writes x and r and
-    // writes z (24 values of the solve's type), plus the row pointers.
+    // the bytes of a streaming PCG iteration whose three fused passes keep
+    // nothing on chip.  SpMV: every stored block (9 values + 4 B column) and
+    // the row pointers (8 B per row), p read, q written; update: x, r read and
+    // written, p and q read, z written, the preconditioner read (9 values per
+    // soft node, 144 per affine body); direction: z read, p read and written.
+    // 36 vector values per node in the solve's type.
     {
         double nn = s->n_nodes;
         double bs = 9.0 * sizeof(T) + 4.0;  // one stored block and its column index
         double pre = 9.0 * sizeof(T) * (nn - 4.0 * s->n_aff) + 144.0 * sizeof(T) * s->n_aff;
-        double per_it = use_cluster
-                            ? bs * ((double)s->n_sblocks + (double)s->n_cblocks) + nn * (8.0 + 24.0 * sizeof(T)) + pre
-                            : bs * ((double)s->n_sblocks + (double)s->n_cblocks) + nn * (8.0 + 48.0 + 168.0 + 72.0) + pre;
+        double per_it = bs * ((double)s->n_sblocks + (double)s->n_cblocks) + nn * (8.0 + 36.0 * sizeof(T)) + pre;
         alg_bytes_add(kname, per_it * (double)tot / std::max(1, NE));
     }
     // done envs: zero direction

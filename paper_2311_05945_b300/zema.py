@@ -43,7 +43,7 @@ class StepStats(C.Structure):
         ("steps", C.c_int64), ("newton_iters", C.c_int64), ("pcg_iters", C.c_int64), ("ls_halvings", C.c_int64),
         ("al_rounds", C.c_int64), ("warm_accepted", C.c_int64), ("max_candidates", C.c_int64),
         ("max_active", C.c_int64), ("dmin", C.c_double), ("kappa", C.c_double), ("energy", C.c_double),
-        ("ms_phase", C.c_double * 6),
+        ("ms_phase", C.c_double * 6), ("pcg_refines", C.c_int64),
     ]
 
     def as_dict(self):
@@ -260,7 +260,8 @@ class Scene:
             if total is None:
                 total = d
             else:
-                for k in ("steps", "newton_iters", "pcg_iters", "ls_halvings", "al_rounds", "warm_accepted"):
+                for k in ("steps", "newton_iters", "pcg_iters", "ls_halvings", "al_rounds", "warm_accepted",
+                          "pcg_refines"):
                     total[k] += d[k]
                 for k in ("max_candidates", "max_active"):
                     total[k] = max(total[k], d[k])
