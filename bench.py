@@ -33,9 +33,10 @@ METRIC = "IPC time steps/sec at fixed Newton tol, batched+warm-start vs plain, o
 UNIT = "steps/s"
 WORKLOAD = "parallel-jaw grasp, 1 env: soft ellipsoid 9600 tets + 2 kinematic affine fingers (972 tris each) + fixed floor"
 ROOFLINE_KERNEL = "k_pcg_cluster"
-# DRAM bytes per launch of ROOFLINE_KERNEL from the committed ncu capture
-# (profiles/); None until a capture of the current kernel exists.
-ROOFLINE_TRAFFIC = None
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# ROOFLINE_KERNEL from an ncu capture of the first solve of grasp step 20
+# (a launch of the bench's average length); None once the kernel changes.
+ROOFLINE_TRAFFIC = 1.364e6
 
 
 def measured_peaks():
