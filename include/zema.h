@@ -257,6 +257,37 @@ zema_status zema_local_neo_hookean(int64_t n, const double* F9, double mu, doubl
 zema_status zema_local_accd(int64_t n, const double* x12, const double* p12, const int32_t* is_ee,
                             double* t_out, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Small MLPs for the learned Newton warm start (the paper has no learned
+ * component; this is an addition to the method).  A network maps
+ * dims[0] -> dims[1] -> ... -> dims[n_layers] with ReLU after every layer but
+ * the last.  Parameters are FP32 master copies, laid out layer by layer as
+ * W_l (dims[l] x dims[l+1], row-major) followed by b_l (dims[l+1]); products
+ * run on the tensor cores with BF16 operands and FP32 accumulation.  All
+ * x / y / t pointers are device pointers (row-major, n rows); the network
+ * owns its device memory.  Every call is stream-ordered on `stream` and
+ * returns after its work completed.  Training is bit-reproducible (all
+ * reductions in a fixed order).
+ * ------------------------------------------------------------------------ */
+typedef struct zema_mlp zema_mlp;
+/* dims: n_layers + 1 widths (1..4096), n_layers 1..16; weights He-uniform from
+ * a SplitMix64 stream seeded with `seed`, biases zero. */
+zema_status zema_mlp_create(const int32_t* dims, int32_t n_layers, uint64_t seed, void* stream, zema_mlp** out);
+void zema_mlp_destroy(zema_mlp* m);
+zema_status zema_mlp_n_params(const zema_mlp* m, int64_t* n);
+/* copies the FP32 parameters to / from host memory (cap / n = n_params) */
+zema_status zema_mlp_get_params(const zema_mlp* m, float* host_out, int64_t cap);
+zema_status zema_mlp_set_params(zema_mlp* m, const float* host_in, int64_t n);
+/* y = net(x) */
+zema_status zema_mlp_forward(zema_mlp* m, const float* x, int64_t n, float* y);
+/* mean squared error of net(x) against t (mean over all n x dims[L]
+ * entries) and its gradient with respect to the parameters (to host) */
+zema_status zema_mlp_gradient(zema_mlp* m, const float* x, const float* t, int64_t n, float* grad_host, int64_t cap,
+                              double* loss);
+/* one AdamW step (decoupled weight decay) on the mean squared error of one batch */
+zema_status zema_mlp_train_step(zema_mlp* m, const float* x, const float* t, int64_t n, float lr, float beta1,
+                                float beta2, float eps, float weight_decay, double* loss);
+
 #ifdef __cplusplus
 }
 #endif

@@ -105,6 +105,17 @@ def lib():
     L.zema_launch_count.argtypes = []
     L.zema_profile_kernel.argtypes = [C.c_char_p]
     L.zema_profile_read.argtypes = [DP, C.POINTER(C.c_longlong), DP]
+    FP = C.POINTER(C.c_float)
+    L.zema_mlp_create.argtypes = [IP, C.c_int32, C.c_uint64, C.c_void_p, C.POINTER(C.c_void_p)]
+    L.zema_mlp_destroy.argtypes = [C.c_void_p]
+    L.zema_mlp_destroy.restype = None
+    L.zema_mlp_n_params.argtypes = [C.c_void_p, LP]
+    L.zema_mlp_get_params.argtypes = [C.c_void_p, FP, C.c_int64]
+    L.zema_mlp_set_params.argtypes = [C.c_void_p, FP, C.c_int64]
+    L.zema_mlp_forward.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]
+    L.zema_mlp_gradient.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, FP, C.c_int64, DP]
+    L.zema_mlp_train_step.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_float, C.c_float,
+                                      C.c_float, C.c_float, C.c_float, DP]
     _lib = L
     return L
 
@@ -427,3 +438,64 @@ def local_accd(x12, p12, is_ee):
     t = np.zeros(n)
     _check(lib().zema_local_accd(n, _dp(x), _dp(p), _ip(ie), _dp(t), _stream()))
     return t
+
+
+class Mlp:
+    """A tensor-core MLP of the library (dims[0] -> ... -> dims[-1], ReLU
+    between layers).  Inputs and targets are CUDA float32 tensors."""
+
+    def __init__(self, dims, seed: int = 0):
+        L = lib()
+        self.dims = [int(d) for d in dims]
+        d = np.array(self.dims, dtype=np.int32)
+        h = C.c_void_p()
+        _check(L.zema_mlp_create(_ip(d), len(self.dims) - 1, C.c_uint64(seed), _stream(), C.byref(h)))
+        self.h = h
+        n = C.c_int64()
+        _check(L.zema_mlp_n_params(h, C.byref(n)))
+        self.n_params = n.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().zema_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self) -> np.ndarray:
+        out = np.zeros(self.n_params, dtype=np.float32)
+        _check(lib().zema_mlp_get_params(self.h, out.ctypes.data_as(C.POINTER(C.c_float)), self.n_params))
+        return out
+
+    def set_params(self, theta):
+        a = np.ascontiguousarray(theta, dtype=np.float32)
+        _check(lib().zema_mlp_set_params(self.h, a.ctypes.data_as(C.POINTER(C.c_float)), len(a)))
+
+    @staticmethod
+    def _dev(x):
+        import torch
+        assert x.is_cuda and x.dtype == torch.float32 and x.is_contiguous()
+        return C.c_void_p(x.data_ptr())
+
+    def forward(self, x):
+        import torch
+        y = torch.empty((x.shape[0], self.dims[-1]), dtype=torch.float32, device=x.device)
+        _check(lib().zema_mlp_forward(self.h, self._dev(x), x.shape[0], self._dev(y)))
+        return y
+
+    def gradient(self, x, t):
+        g = np.zeros(self.n_params, dtype=np.float32)
+        loss = C.c_double()
+        _check(lib().zema_mlp_gradient(self.h, self._dev(x), self._dev(t), x.shape[0],
+                                       g.ctypes.data_as(C.POINTER(C.c_float)), self.n_params, C.byref(loss)))
+        return loss.value, g
+
+    def train_step(self, x, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0):
+        loss = C.c_double()
+        _check(lib().zema_mlp_train_step(self.h, self._dev(x), self._dev(t), x.shape[0], lr, beta1, beta2, eps,
+                                         weight_decay, C.byref(loss)))
+        return loss.value

@@ -1,0 +1,38 @@
+"""Pins of the CPU reference MLP (warm-start network): central finite
+differences of the loss, and the vanishing gradient at the least-squares
+optimum of a single linear layer."""
+import numpy as np
+
+from oracle import mlp_ref
+
+
+def test_reference_gradient_matches_central_differences():
+    rng = np.random.default_rng(3)
+    dims = [5, 7, 6, 2]
+    n_par = sum(dims[l] * dims[l + 1] + dims[l + 1] for l in range(len(dims) - 1))
+    theta = rng.normal(size=n_par) * 0.7
+    x = rng.normal(size=(9, dims[0]))
+    t = rng.normal(size=(9, dims[-1]))
+    loss, g = mlp_ref.loss_and_grad(theta, dims, x, t)
+    h = 1e-6
+    fd = np.zeros_like(theta)
+    for i in range(n_par):
+        e = np.zeros_like(theta)
+        e[i] = h
+        fd[i] = (mlp_ref.loss_and_grad(theta + e, dims, x, t)[0] - mlp_ref.loss_and_grad(theta - e, dims, x, t)[0]) / (2 * h)
+    assert np.abs(fd - g).max() < 1e-6 * max(1.0, np.abs(g).max())
+    assert loss > 0
+
+
+def test_reference_gradient_vanishes_at_least_squares_optimum():
+    rng = np.random.default_rng(4)
+    x = rng.normal(size=(40, 3))
+    t = rng.normal(size=(40, 2))
+    xa = np.hstack([x, np.ones((40, 1))])
+    sol, *_ = np.linalg.lstsq(xa, t, rcond=None)
+    theta = np.concatenate([sol[:3].ravel(), sol[3]])
+    _, g = mlp_ref.loss_and_grad(theta, [3, 2], x, t)
+    assert np.abs(g).max() < 1e-12
+    # and away from it the loss is larger
+    l0 = mlp_ref.loss_and_grad(theta, [3, 2], x, t)[0]
+    assert mlp_ref.loss_and_grad(theta + 1e-3, [3, 2], x, t)[0] > l0
