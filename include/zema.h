@@ -97,6 +97,8 @@ typedef struct {
     double energy;          /* incremental potential of env 0 at the last converged iterate */
     double ms_phase[6];     /* host-timed phases: DCD, energy, Hessian, linear, CCD, other (ms) */
     int64_t pcg_refines;    /* FP64 residual-refinement restarts of FP32 solves (mixed precision) */
+    int64_t warm_learned;   /* accepted learned warm-start corrections (per env step) */
+    int64_t warm_fallback;  /* steps redone from the constant-velocity start after Newton failed from the learned one */
 } zema_step_stats;
 
 /* Fills *p with defaults: dt 0.01, dhat 1e-3, adaptive kappa, eps_v 1e-3,
@@ -256,6 +258,32 @@ zema_status zema_local_neo_hookean(int64_t n, const double* F9, double mu, doubl
 /* Additive CCD step bound t in (0, 1] of n stencils moving by p12 (s = 0.1). */
 zema_status zema_local_accd(int64_t n, const double* x12, const double* p12, const int32_t* is_ee,
                             double* t_out, void* stream);
+
+/* Learned Newton warm start (an addition to the method).  The network maps
+ * 13 features of a soft vertex at the step's start to its predicted
+ * displacement over the step, both scaled by s = h^2 |g| (the features:
+ * position relative to the body centroid over the body's rest
+ * half-diagonal; h v / s; (xhat - x) / s; nearest active pair distance over
+ * dhat, capped at 1; that pair's unit normal pointing away from the other
+ * primitive, or 0), and it predicts the displacement beyond the
+ * constant-velocity one h v.  With params.warm_start = 1 the step first takes
+ * the constant-velocity proposal x^t + alpha h v (CCD-bounded, kept only if
+ * the energy does not rise), then the predicted correction of the soft
+ * vertices the same way, kept only if it lowers the energy further; Newton
+ * then runs to the same tolerance.  If Newton or its line search fails from
+ * that start, the step is redone from x^t with the constant-velocity start
+ * only, so the plain method decides every step the learned start cannot.
+ *
+ * zema_load_warmstart: blob = uint32 magic 0x5357455A, uint32 n_layers,
+ * uint32 dims[n_layers + 1] (dims[0] = 13, dims[n_layers] = 3), then the
+ * float32 parameters in the zema_mlp layout.  The scene copies the blob. */
+zema_status zema_load_warmstart(zema_scene* s, const void* blob, int64_t bytes);
+/* While recording, every following step writes the features of its soft
+ * vertices (rows x 13) and their scaled displacement over the step (rows x 3)
+ * into the caller's device buffers (rows = soft vertex count; the library's
+ * node order: environments in order, bodies in the order they were added).
+ * NULL / NULL stops.  cap_rows below the soft vertex count is an error. */
+zema_status zema_record_warmstart(zema_scene* s, float* features, float* targets, int64_t cap_rows);
 
 /* ------------------------------------------------------------------------
  * Small MLPs for the learned Newton warm start (the paper has no learned

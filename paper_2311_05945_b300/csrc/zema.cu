@@ -20,7 +20,9 @@
 
 #include "broadphase.cuh"
 #include "kernels_misc.cuh"
+#include "mlp.cuh"
 #include "pcg_cluster.cuh"
+#include "warmstart.cuh"
 
 using namespace zema;
 
@@ -117,8 +119,19 @@ struct zema_scene {
     // per-step scratch
     DBuf<double> dirw, lam_save;
     std::vector<double> dmin_last;
+    // learned warm start: network, soft-vertex list (node order) with their
+    // tet body, per-body node range / rest half-diagonal / centroid, features
+    Mlp* ws_net = nullptr;
+    int ws_ns = 0, ws_nb = 0;
+    DBuf<int> ws_soft, ws_body, tb_node0, tb_nv;
+    DBuf<double> tb_R, tb_c;
+    DBuf<unsigned long long> ws_best;
+    DBuf<float> ws_feat, ws_out;
+    float* rec_feat = nullptr;  // caller's device buffers while recording
+    float* rec_targ = nullptr;
 
     ~zema_scene() {
+        delete ws_net;
         if (h32) cudaFreeHost(h32);
         if (hd) cudaFreeHost(hd);
         if (hi) cudaFreeHost(hi);
@@ -724,6 +737,44 @@ void build(zema_scene* s) {
     if (!s->h32) ZCHECK(cudaMallocHost(&s->h32, 64 * sizeof(uint32_t)));
     if (!s->hd) ZCHECK(cudaMallocHost(&s->hd, (8 * (size_t)NE + 64) * sizeof(double)));
     if (!s->hi) ZCHECK(cudaMallocHost(&s->hi, (4 * (size_t)NE + 64) * sizeof(int)));
+    // learned warm start: soft vertices in node order, their body, per-body
+    // node range and rest half-diagonal
+    {
+        std::vector<int> tb0, tbn, node_tb(nN, -1);
+        std::vector<double> tbR;
+        for (size_t b = 0; b < s->tin.size(); ++b) {
+            const int n0 = s->tet_body_node0[b], nv = (int)(s->tin[b].X.size() / 3);
+            tb0.push_back(n0);
+            tbn.push_back(nv);
+            double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+            for (int k = 0; k < nv; ++k)
+                for (int j = 0; j < 3; ++j) {
+                    lo[j] = std::min(lo[j], s->tin[b].X[3 * k + j]);
+                    hi[j] = std::max(hi[j], s->tin[b].X[3 * k + j]);
+                }
+            double d2 = 0.0;
+            for (int j = 0; j < 3; ++j) d2 += (hi[j] - lo[j]) * (hi[j] - lo[j]);
+            tbR.push_back(std::max(0.5 * std::sqrt(d2), 1e-12));
+            for (int k = 0; k < nv; ++k) node_tb[n0 + k] = (int)b;
+        }
+        std::vector<int> soft, sbody;
+        for (int n = 0; n < nN; ++n)
+            if (node_tb[n] >= 0) {
+                soft.push_back(n);
+                sbody.push_back(node_tb[n]);
+            }
+        s->ws_ns = (int)soft.size();
+        s->ws_nb = (int)tb0.size();
+        up(s, s->ws_soft, soft);
+        up(s, s->ws_body, sbody);
+        up(s, s->tb_node0, tb0);
+        up(s, s->tb_nv, tbn);
+        up(s, s->tb_R, tbR);
+        s->tb_c.ensure(A, 3 * (size_t)s->ws_nb + 3);
+        s->ws_best.ensure(A, (size_t)nN + 1);
+        s->ws_feat.ensure(A, (size_t)kWsFeatures * s->ws_ns + kWsFeatures);
+        s->ws_out.ensure(A, (size_t)kWsOutputs * s->ws_ns + kWsOutputs);
+    }
     // kappa: user value or pending rule
     std::vector<double> kap(NE, s->P.kappa > 0 ? s->P.kappa : 0.0);
     up(s, s->kappa, kap);
@@ -1282,9 +1333,10 @@ void step_norm(zema_scene* s) {
 // E(x + alpha dir) <= E(x) per env.  On success x is advanced.  Returns the
 // number of halvings, or -1 when an env fails.
 int line_search(zema_scene* s, const double* dir, const std::vector<int>& done_h, bool warm,
-                std::vector<int>* accepted) {
-    // warm-start proposals get a single energy check, Newton steps up to 60 halvings
-    const int max_halvings = warm ? 0 : 60;
+                std::vector<int>* accepted, int warm_halvings = 0) {
+    // warm-start proposals get warm_halvings halvings (default: a single energy
+    // check), Newton steps up to 60
+    const int max_halvings = warm ? warm_halvings : 60;
     cudaStream_t st = s->st;
     Geo& G = s->G;
     int NE = s->n_envs;
@@ -1468,6 +1520,32 @@ __global__ void k_scale_dir(Geo G, const double* v, double h, double* d) {
     for (int j = 0; j < 3; ++j) d[3 * (size_t)n + j] = G.node_fixed[n] ? 0.0 : h * v[3 * (size_t)n + j];
 }
 
+// free-fall displacement of one step, the scale of the warm-start network's
+// displacement features and outputs
+double ws_scale(const zema_scene* s) {
+    const double* g = s->P.gravity;
+    const double gn = std::sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+    return s->P.dt * s->P.dt * (gn > 0.0 ? gn : 9.81);
+}
+
+// warm-start features of the soft vertices at x^t into s->ws_feat (needs the
+// predictor and the lagged pairs of this step)
+void ws_features(zema_scene* s) {
+    cudaStream_t st = s->st;
+    if (!s->ws_ns) return;
+    ZCHECK(cudaMemsetAsync(s->ws_best.p, 0xFF, (size_t)s->n_nodes * sizeof(unsigned long long), st));
+    ZL(k_ws_centroid, s->ws_nb, kRedThreads, 0, st)(s->x.p, s->tb_node0.p, s->tb_nv.p, s->tb_c.p);
+    if (s->n_lag)
+        ZL(k_ws_nearest, div_up(s->n_lag, 128), 128, 0, st)(s->G, s->Xt.p, s->lag.p, s->lag_w.p, (int)s->n_lag,
+                                                           s->ws_best.p);
+    ZL(k_ws_features, div_up(s->ws_ns, 128), 128, 0, st)(s->G, s->ws_soft.p, s->ws_body.p, s->ws_ns, s->x.p, s->v.p,
+                                                        s->xhat.p, s->tb_c.p, s->tb_R.p, s->ws_best.p, s->lag.p,
+                                                        s->lag_w.p, s->lag_n.p, s->P.dt, ws_scale(s), s->ws_feat.p);
+    ZLAUNCH();
+}
+
+void restore_step(zema_scene* s);
+
 // One time step of every environment.
 void do_step(zema_scene* s) {
     zema_scene& W = *s;
@@ -1501,71 +1579,110 @@ void do_step(zema_scene* s) {
         s->first_step_done = true;
     }
     s->S.ms_phase[0] += now_ms() - t0;
-    // warm start: x^t + alpha h v^t, CCD-bounded, kept if the energy does not rise
+    // warm start: x^t + alpha h v^t, CCD-bounded, kept if the energy does not
+    // rise; with the learned network, its predicted correction s y is then
+    // applied the same way from there (CCD-bounded, kept only if it lowers the
+    // energy further), so the learned start is never worse in energy than
+    // the constant-velocity one
     W.dirw.ensure(&s->A, n3 + 3);
-    ZL(k_scale_dir, div_up(s->n_nodes, TB), TB, 0, st)(G, s->v.p, s->P.dt, W.dirw.p);
-    ZLAUNCH();
-    std::vector<int> done(NE, 0), acc;
-    line_search(s, W.dirw.p, done, true, &acc);
-    for (int e = 0; e < NE; ++e) s->S.warm_accepted += acc[e];
-    int rounds = 0;
-    for (;;) {
-        bool converged = false;
-        for (int it = 0; it < s->P.max_newton; ++it) {
-            double ta = now_ms();
-            ZL(k_sv_pos, div_up(s->n_sv, TB), TB, 0, st)(G, s->x.p, s->X.p);
+    const bool learned = s->P.warm_start == 1 && s->ws_net && s->ws_ns;
+    if (learned || s->rec_feat) ws_features(s);
+    if (s->rec_feat && s->ws_ns)
+        ZCHECK(cudaMemcpyAsync(s->rec_feat, s->ws_feat.p, (size_t)kWsFeatures * s->ws_ns * sizeof(float),
+                               cudaMemcpyDeviceToDevice, st));
+    if (learned) s->ws_net->forward(s->ws_feat.p, s->ws_ns, s->ws_out.p);
+    // one attempt at the step from x^t: warm start, then Newton with the
+    // kinematic augmented-Lagrangian rounds; returns the AL rounds
+    auto solve = [&](bool use_learned) -> int {
+        ZL(k_scale_dir, div_up(s->n_nodes, TB), TB, 0, st)(G, s->v.p, s->P.dt, W.dirw.p);
+        ZLAUNCH();
+        std::vector<int> done(NE, 0), acc;
+        line_search(s, W.dirw.p, done, true, &acc);
+        if (use_learned) {
+            ZCHECK(cudaMemsetAsync(W.dirw.p, 0, n3 * sizeof(double), st));
+            ZL(k_ws_direction, div_up(s->ws_ns, 128), 128, 0, st)(s->ws_soft.p, s->ws_ns, s->ws_out.p, ws_scale(s),
+                                                                 W.dirw.p);
             ZLAUNCH();
-            // x was reached by a line search along the last swept motion (the
-            // warm start or the previous Newton step), so that swept
-            // candidate list contains every pair with d < dhat at x
-            active_from(s, s->X.p, s->swept.p, s->swept_env.p, s->n_swept, true);
-            double tb = now_ms();
-            s->S.ms_phase[0] += tb - ta;
-            grad_hess(s);
-            ZCHECK(cudaStreamSynchronize(st));
-            double tc = now_ms();
-            s->S.ms_phase[2] += tc - tb;
-            s->S.pcg_iters += pcg(s, done);
-            step_norm(s);
-            s->S.ms_phase[3] += now_ms() - tc;
-            bool all = true;
-            for (int e = 0; e < NE; ++e) {
-                if (done[e]) continue;
-                if (s->hd[e] <= s->tol_h[e]) {
-                    done[e] = 1;
-                } else {
-                    all = false;
-                    s->S.newton_iters += 1;
-                }
-            }
-            if (all) {
-                converged = true;
-                break;
-            }
-            // zero the direction of envs that just converged
-            for (int e = 0; e < NE; ++e) s->hi[e] = done[e];
-            ZCHECK(cudaMemcpyAsync(s->need.p, s->hi, NE * sizeof(int), cudaMemcpyHostToDevice, st));
-            ZL(k_mask_env, div_up(s->n_nodes, TB), TB, 0, st)(G, s->p.p, s->need.p);
-            ZLAUNCH();
-            int hv = line_search(s, s->p.p, done, false, nullptr);
-            if (hv < 0) fail(ZEMA_ERR_LINESEARCH, "line search found no decrease after 60 halvings");
-            s->S.ls_halvings += hv;
+            std::vector<int> acc2;
+            line_search(s, W.dirw.p, done, true, &acc2, kWsHalvings);
+            for (int e = 0; e < NE; ++e) s->S.warm_learned += acc2[e];
         }
-        if (!converged) fail(ZEMA_ERR_NEWTON_MAXITER, "Newton did not converge within max_newton iterations");
-        // kinematic augmented Lagrangian (Eq. 13)
-        if (s->n_aff == 0) break;
-        ZCHECK(cudaMemsetAsync(s->need.p, 0, NE * sizeof(int), st));
-        ZL(k_al_check, div_up(s->n_aff, 64), 64, 0, st)(G, s->x.p, kin(s), s->tolv.p, s->need.p);
-        ZLAUNCH();
-        ZCHECK(cudaMemcpyAsync(s->hi, s->need.p, NE * sizeof(int), cudaMemcpyDeviceToHost, st));
-        ZCHECK(cudaStreamSynchronize(st));
-        bool any = false;
-        for (int e = 0; e < NE; ++e) any |= s->hi[e] != 0;
-        if (!any || rounds >= s->P.max_al_rounds) break;
-        ++rounds;
-        ZL(k_al_update, div_up(s->n_aff, 64), 64, 0, st)(G, s->x.p, s->qtarget.p, s->lamA.p, s->need.p);
-        ZLAUNCH();
-        for (int e = 0; e < NE; ++e) done[e] = s->hi[e] ? 0 : 1;
+        for (int e = 0; e < NE; ++e) s->S.warm_accepted += acc[e];
+        int rounds = 0;
+        for (;;) {
+            bool converged = false;
+            for (int it = 0; it < s->P.max_newton; ++it) {
+                double ta = now_ms();
+                ZL(k_sv_pos, div_up(s->n_sv, TB), TB, 0, st)(G, s->x.p, s->X.p);
+                ZLAUNCH();
+                // x was reached by a line search along the last swept motion (the
+                // warm start or the previous Newton step), so that swept
+                // candidate list contains every pair with d < dhat at x
+                active_from(s, s->X.p, s->swept.p, s->swept_env.p, s->n_swept, true);
+                double tb = now_ms();
+                s->S.ms_phase[0] += tb - ta;
+                grad_hess(s);
+                ZCHECK(cudaStreamSynchronize(st));
+                double tc = now_ms();
+                s->S.ms_phase[2] += tc - tb;
+                s->S.pcg_iters += pcg(s, done);
+                step_norm(s);
+                s->S.ms_phase[3] += now_ms() - tc;
+                bool all = true;
+                for (int e = 0; e < NE; ++e) {
+                    if (done[e]) continue;
+                    if (s->hd[e] <= s->tol_h[e]) {
+                        done[e] = 1;
+                    } else {
+                        all = false;
+                        s->S.newton_iters += 1;
+                    }
+                }
+                if (all) {
+                    converged = true;
+                    break;
+                }
+                // zero the direction of envs that just converged
+                for (int e = 0; e < NE; ++e) s->hi[e] = done[e];
+                ZCHECK(cudaMemcpyAsync(s->need.p, s->hi, NE * sizeof(int), cudaMemcpyHostToDevice, st));
+                ZL(k_mask_env, div_up(s->n_nodes, TB), TB, 0, st)(G, s->p.p, s->need.p);
+                ZLAUNCH();
+                int hv = line_search(s, s->p.p, done, false, nullptr);
+                if (hv < 0) fail(ZEMA_ERR_LINESEARCH, "line search found no decrease after 60 halvings");
+                s->S.ls_halvings += hv;
+            }
+            if (!converged) fail(ZEMA_ERR_NEWTON_MAXITER, "Newton did not converge within max_newton iterations");
+            // kinematic augmented Lagrangian (Eq. 13)
+            if (s->n_aff == 0) break;
+            ZCHECK(cudaMemsetAsync(s->need.p, 0, NE * sizeof(int), st));
+            ZL(k_al_check, div_up(s->n_aff, 64), 64, 0, st)(G, s->x.p, kin(s), s->tolv.p, s->need.p);
+            ZLAUNCH();
+            ZCHECK(cudaMemcpyAsync(s->hi, s->need.p, NE * sizeof(int), cudaMemcpyDeviceToHost, st));
+            ZCHECK(cudaStreamSynchronize(st));
+            bool any = false;
+            for (int e = 0; e < NE; ++e) any |= s->hi[e] != 0;
+            if (!any || rounds >= s->P.max_al_rounds) break;
+            ++rounds;
+            ZL(k_al_update, div_up(s->n_aff, 64), 64, 0, st)(G, s->x.p, s->qtarget.p, s->lamA.p, s->need.p);
+            ZLAUNCH();
+            for (int e = 0; e < NE; ++e) done[e] = s->hi[e] ? 0 : 1;
+        }
+        return rounds;
+    };
+    int rounds = 0;
+    if (learned) {
+        try {
+            rounds = solve(true);
+        } catch (const ZemaError& e) {
+            if (e.status != ZEMA_ERR_NEWTON_MAXITER && e.status != ZEMA_ERR_LINESEARCH) throw;
+            // the learned start did not converge: plain Newton from the
+            // constant-velocity start decides the step
+            restore_step(s);
+            s->S.warm_fallback += 1;
+            rounds = solve(false);
+        }
+    } else {
+        rounds = solve(false);
     }
     s->S.al_rounds += rounds;
     // d_min at the accepted state (last active-pair pass) and energy of env 0
@@ -1574,6 +1691,11 @@ void do_step(zema_scene* s) {
     // velocities (Eq. 11)
     ZL(k_velocity, div_up(s->n_nodes, TB), TB, 0, st)(G, s->x.p, s->xt.p, s->v.p);
     ZLAUNCH();
+    if (s->rec_targ && s->ws_ns) {
+        ZL(k_ws_target, div_up(s->ws_ns, 128), 128, 0, st)(s->ws_soft.p, s->ws_ns, s->x.p, s->xt.p, s->ws_feat.p,
+                                                          ws_scale(s), s->rec_targ);
+        ZLAUNCH();
+    }
     std::vector<double> kap(NE), kmin(NE);
     ZCHECK(cudaMemcpyAsync(kap.data(), s->kappa.p, NE * sizeof(double), cudaMemcpyDeviceToHost, st));
     ZCHECK(cudaMemcpyAsync(kmin.data(), s->kappa_min.p, NE * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -1987,6 +2109,46 @@ zema_status zema_set_kappa(zema_scene* s, int32_t env, double kappa, double kapp
         return ZEMA_OK;
     }
     ZEMA_CATCH(s)
+}
+
+zema_status zema_load_warmstart(zema_scene* s, const void* blob, int64_t bytes) {
+    if (!s || !blob || bytes < 12) return ZEMA_ERR_INVALID_ARG;
+    const uint32_t* h = (const uint32_t*)blob;
+    if (h[0] != 0x5357455Au) return ZEMA_ERR_INVALID_ARG;
+    const uint32_t L = h[1];
+    if (L < 1 || L > 16 || bytes < (int64_t)(4 * (L + 3))) return ZEMA_ERR_INVALID_ARG;
+    std::vector<int> dims(L + 1);
+    for (uint32_t l = 0; l <= L; ++l) dims[l] = (int)h[2 + l];
+    if (dims[0] != kWsFeatures || dims[L] != kWsOutputs) return ZEMA_ERR_INVALID_ARG;
+    size_t np = 0;
+    for (uint32_t l = 0; l < L; ++l) {
+        if (dims[l] < 1 || dims[l] > 4096 || dims[l + 1] < 1 || dims[l + 1] > 4096) return ZEMA_ERR_INVALID_ARG;
+        np += (size_t)dims[l] * dims[l + 1] + dims[l + 1];
+    }
+    if (bytes != (int64_t)(4 * (L + 3) + 4 * np)) return ZEMA_ERR_INVALID_ARG;
+    ZEMA_TRY(s) {
+        Mlp* net = new Mlp(dims, 0, s->st);
+        const float* th = (const float*)(h + 3 + L);
+        ZCHECK(cudaMemcpyAsync(net->theta.p, th, np * sizeof(float), cudaMemcpyHostToDevice, s->st));
+        net->refresh_bf16();
+        ZCHECK(cudaStreamSynchronize(s->st));
+        delete s->ws_net;
+        s->ws_net = net;
+        return ZEMA_OK;
+    }
+    ZEMA_CATCH(s)
+}
+
+zema_status zema_record_warmstart(zema_scene* s, float* features, float* targets, int64_t cap_rows) {
+    if (!s || (features == nullptr) != (targets == nullptr)) return ZEMA_ERR_INVALID_ARG;
+    if (!s->finalized) {
+        zema_status r = zema_finalize(s);
+        if (r != ZEMA_OK) return r;
+    }
+    if (features && cap_rows < s->ws_ns) return ZEMA_ERR_INVALID_ARG;
+    s->rec_feat = features;
+    s->rec_targ = targets;
+    return ZEMA_OK;
 }
 
 const char* zema_last_error(const zema_scene* s) { return s ? s->err.c_str() : "null scene"; }

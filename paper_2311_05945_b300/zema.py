@@ -43,7 +43,8 @@ class StepStats(C.Structure):
         ("steps", C.c_int64), ("newton_iters", C.c_int64), ("pcg_iters", C.c_int64), ("ls_halvings", C.c_int64),
         ("al_rounds", C.c_int64), ("warm_accepted", C.c_int64), ("max_candidates", C.c_int64),
         ("max_active", C.c_int64), ("dmin", C.c_double), ("kappa", C.c_double), ("energy", C.c_double),
-        ("ms_phase", C.c_double * 6), ("pcg_refines", C.c_int64),
+        ("ms_phase", C.c_double * 6), ("pcg_refines", C.c_int64), ("warm_learned", C.c_int64),
+        ("warm_fallback", C.c_int64),
     ]
 
     def as_dict(self):
@@ -106,6 +107,8 @@ def lib():
     L.zema_profile_kernel.argtypes = [C.c_char_p]
     L.zema_profile_read.argtypes = [DP, C.POINTER(C.c_longlong), DP]
     FP = C.POINTER(C.c_float)
+    L.zema_load_warmstart.argtypes = [C.c_void_p, C.c_void_p, C.c_int64]
+    L.zema_record_warmstart.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]
     L.zema_mlp_create.argtypes = [IP, C.c_int32, C.c_uint64, C.c_void_p, C.POINTER(C.c_void_p)]
     L.zema_mlp_destroy.argtypes = [C.c_void_p]
     L.zema_mlp_destroy.restype = None
@@ -184,7 +187,8 @@ class Scene:
     """A scene of the seeded generators loaded into the library."""
 
     def __init__(self, scene: _scenes.Scene, precision: Optional[int] = None, tol_scale: float = 1.0,
-                 torch_alloc: bool = True, kappa: Optional[float] = None, pcg_kind: int = 0):
+                 torch_alloc: bool = True, kappa: Optional[float] = None, pcg_kind: int = 0,
+                 warm_start: int = 0):
         L = lib()
         p = scene.params
         P = Params()
@@ -203,6 +207,7 @@ class Scene:
         P.precision = p.precision if precision is None else precision
         P.n_envs = scene.n_envs
         P.pcg_kind = pcg_kind
+        P.warm_start = warm_start
         P.stream = _stream()
         if torch_alloc:
             P.alloc = _ALLOC
@@ -243,6 +248,21 @@ class Scene:
         except Exception:
             pass
 
+    def load_warmstart(self, dims, theta):
+        """Load the learned warm-start network (dims[0] = 13, dims[-1] = 3)."""
+        blob = warmstart_blob(dims, theta)
+        _check(lib().zema_load_warmstart(self.h, blob.ctypes.data_as(C.c_void_p), blob.nbytes), self.h)
+
+    def record_warmstart(self, features=None, targets=None):
+        """Record features (rows x 13) and scaled step displacements (rows x 3)
+        of the soft vertices into CUDA float32 tensors during later steps."""
+        if features is None:
+            _check(lib().zema_record_warmstart(self.h, None, None, 0), self.h)
+            return
+        rows = min(features.shape[0], targets.shape[0])
+        _check(lib().zema_record_warmstart(self.h, C.c_void_p(features.data_ptr()), C.c_void_p(targets.data_ptr()),
+                                           rows), self.h)
+
     def tet_body_id(self, i):
         return self.body_ids[i]
 
@@ -272,7 +292,7 @@ class Scene:
                 total = d
             else:
                 for k in ("steps", "newton_iters", "pcg_iters", "ls_halvings", "al_rounds", "warm_accepted",
-                          "pcg_refines"):
+                          "pcg_refines", "warm_learned", "warm_fallback"):
                     total[k] += d[k]
                 for k in ("max_candidates", "max_active"):
                     total[k] = max(total[k], d[k])
@@ -499,3 +519,23 @@ class Mlp:
         _check(lib().zema_mlp_train_step(self.h, self._dev(x), self._dev(t), x.shape[0], lr, beta1, beta2, eps,
                                          weight_decay, C.byref(loss)))
         return loss.value
+
+
+WARMSTART_MAGIC = 0x5357455A
+
+
+def warmstart_blob(dims, theta) -> np.ndarray:
+    """The byte layout zema_load_warmstart reads, as a uint8 array."""
+    dims = [int(d) for d in dims]
+    head = np.array([WARMSTART_MAGIC, len(dims) - 1] + dims, dtype=np.uint32)
+    return np.concatenate([head.view(np.uint8), np.ascontiguousarray(theta, dtype=np.float32).view(np.uint8)])
+
+
+def read_warmstart_blob(blob: bytes):
+    """(dims, theta) from a warm-start blob."""
+    h = np.frombuffer(blob, dtype=np.uint32)
+    assert h[0] == WARMSTART_MAGIC
+    L = int(h[1])
+    dims = [int(d) for d in h[2:3 + L]]
+    theta = np.frombuffer(blob, dtype=np.float32, offset=4 * (3 + L)).copy()
+    return dims, theta
