@@ -83,8 +83,19 @@ __device__ __forceinline__ double box_cells(const Box6& b, double inv) {
     return n;
 }
 
+// env of primitive i of kind 0 (surface vertex), 1 (edge), 2 (triangle)
+__device__ __forceinline__ int prim_env(const BPView& v, int kind, int i) {
+    const int sv = kind == 0 ? i : (kind == 1 ? v.edges[i].x : v.tris[i].x);
+    return v.sv_env[sv];
+}
+
+__device__ __forceinline__ bool prim_skipped(const BPView& v, int kind, int i) {
+    return v.env_skip && v.env_skip[prim_env(v, kind, i)];
+}
+
 // kind: 0 points, 1 edges, 2 tris.  For edges and tris also the grid entry
-// count (0 when oversize) and the oversize flag.
+// count (0 when oversize) and the oversize flag.  Primitives of skipped envs
+// get an empty box and no entries.
 __global__ void k_boxes(BPView v, int kind, int n, double* box, int* cb, uint32_t* cnt, uint32_t* big) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -104,6 +115,19 @@ __global__ void k_boxes(BPView v, int kind, int n, double* box, int* cb, uint32_
         ids[1] = t.y;
         ids[2] = t.z;
         m = 3;
+    }
+    if (prim_skipped(v, kind, i)) {
+        for (int k = 0; k < 3; ++k) {
+            box[6 * (size_t)i + k] = INFINITY;
+            box[6 * (size_t)i + 3 + k] = -INFINITY;
+            cb[6 * (size_t)i + k] = 1;
+            cb[6 * (size_t)i + 3 + k] = 0;
+        }
+        if (cnt) {
+            cnt[i] = 0u;
+            big[i] = 0u;
+        }
+        return;
     }
     Box6 b = prim_box(v, ids, m);
     for (int k = 0; k < 3; ++k) {
@@ -213,6 +237,10 @@ __global__ void k_query(BPView v, int kind, int nq, const double* qbox, const do
     const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int q = (int)(gt / kQueryLanes), l = (int)(gt % kQueryLanes);
     if (q >= nq) return;  // the whole group
+    if (prim_skipped(v, kind, q)) {
+        if (!WRITE && l == 0) cnt[q] = 0;
+        return;
+    }
     const unsigned gshift = threadIdx.x & 16u;
     const unsigned gmask = 0xFFFFu << gshift;
     Box6 a = ld_box(qbox + 6 * (size_t)q);
@@ -313,12 +341,16 @@ __global__ void k_query_big(BPView v, int kind, const int* qlist, const double* 
     }
 }
 
-// large-query flag of point or edge query boxes
-__global__ void k_query_flag(const double* box, int n, double inv_cell, uint32_t* flag) {
+// large-query flag of point or edge query boxes (never for skipped envs)
+__global__ void k_query_flag(BPView v, int kind, const double* box, int n, uint32_t* flag) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    if (prim_skipped(v, kind, i)) {
+        flag[i] = 0u;
+        return;
+    }
     Box6 a = ld_box(box + 6 * (size_t)i);
-    flag[i] = box_cells(a, inv_cell) <= kMaxQueryCells ? 0u : 1u;
+    flag[i] = box_cells(a, v.inv_cell) <= kMaxQueryCells ? 0u : 1u;
 }
 
 static uint64_t pow2_at_least(uint64_t n) {
@@ -407,8 +439,8 @@ void BroadPhase::run(Allocator* A, const BPView& v, cudaStream_t st) {
     // large queries (boxes over kMaxQueryCells cells): points, then edges
     pflag.ensure(A, (size_t)nsv + ne + 1);
     pflagoff.ensure(A, (size_t)nsv + ne + 2);
-    if (nsv) ZL(k_query_flag, div_up(nsv, TB), TB, 0, st)(pbox.p, nsv, v.inv_cell, pflag.p);
-    if (ne) ZL(k_query_flag, div_up(ne, TB), TB, 0, st)(ebox.p, ne, v.inv_cell, pflag.p + nsv);
+    if (nsv) ZL(k_query_flag, div_up(nsv, TB), TB, 0, st)(v, 0, pbox.p, nsv, pflag.p);
+    if (ne) ZL(k_query_flag, div_up(ne, TB), TB, 0, st)(v, 1, ebox.p, ne, pflag.p + nsv);
     ZLAUNCH();
     exclusive_scan(pflag.p, pflagoff.p, (size_t)nsv + ne, tmp.p, st);
     ZCHECK(cudaMemcpyAsync(h_counts + 6, pflagoff.p + nsv, 4, cudaMemcpyDeviceToHost, st));

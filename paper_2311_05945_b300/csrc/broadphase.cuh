@@ -18,6 +18,7 @@ struct BPView {
     const int3* tris;
     double infl;
     double inv_cell;
+    const int* env_skip = nullptr;  // nullable, per env: 1 = leave the env's primitives out
 };
 
 struct BroadPhase {

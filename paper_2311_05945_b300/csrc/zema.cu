@@ -88,7 +88,7 @@ struct zema_scene {
     DBuf<double> qtarget, lamA;
     // per env
     DBuf<double> kappa, kappa_min, alpha, E, dmin, part, part2, part3, part4, part5, part6, part7;
-    DBuf<int> conv, pcg_iters, need, capflag;
+    DBuf<int> conv, pcg_iters, need, capflag, skip;
     DBuf<int> tile_u0, tile_u1, tile_n0, tile_n1, tile_env, env_tile_start;
     DBuf<double> pt_a, pt_b, pt_c, pt_d, pt_e;
     int n_tiles = 0, pcg_grid = 0, pcg_grid_f = 0;
@@ -730,7 +730,7 @@ void build(zema_scene* s) {
     for (DBuf<double>* b : {&s->kappa, &s->kappa_min, &s->alpha, &s->E, &s->dmin}) b->ensure(A, NE + 1);
     for (DBuf<double>* b : {&s->part, &s->part2, &s->part3, &s->part4, &s->part5, &s->part6, &s->part7})
         b->ensure(A, (size_t)ET_COUNT * NE * kChunks + 8);
-    for (DBuf<int>* b : {&s->conv, &s->pcg_iters, &s->need}) b->ensure(A, NE + 1);
+    for (DBuf<int>* b : {&s->conv, &s->pcg_iters, &s->need, &s->skip}) b->ensure(A, NE + 1);
     s->capflag.ensure(A, 1);
     for (DBuf<uint32_t>* b : {&s->pt_env, &s->ee_env, &s->m_env, &s->act_env, &s->swept_env, &s->lag_env})
         b->ensure(A, NE + 2);
@@ -849,7 +849,15 @@ void build(zema_scene* s) {
 // ---------------------------------------------------------------------------
 // Broad phase over X0 (-> X1) and merge into env-ordered PairRec `out` with
 // env offsets; returns the count.
-uint32_t candidates(zema_scene* s, const double* X0, const double* X1, DBuf<PairRec>& out, DBuf<uint32_t>& env_off) {
+__global__ void k_reset_dmin(double* dmin, int n, const int* keep) {
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n && !(keep && keep[e])) dmin[e] = INFINITY;
+}
+
+// Candidate pairs (static boxes of X0, or swept X0 -> X1) into `out` with
+// per-env offsets; envs flagged in env_skip contribute no pairs.
+uint32_t candidates(zema_scene* s, const double* X0, const double* X1, DBuf<PairRec>& out, DBuf<uint32_t>& env_off,
+                    const int* env_skip = nullptr) {
     cudaStream_t st = s->st;
     BPView v;
     v.nsv = s->n_sv;
@@ -864,6 +872,7 @@ uint32_t candidates(zema_scene* s, const double* X0, const double* X1, DBuf<Pair
     v.tris = s->tris.p;
     v.infl = 0.5 * s->P.dhat;
     v.inv_cell = 1.0 / s->cell;
+    v.env_skip = env_skip;
     s->bp.run(&s->A, v, st);
     uint32_t n = s->bp.n_pt + s->bp.n_ee;
     out.ensure(&s->A, n + 1);
@@ -883,12 +892,14 @@ uint32_t candidates(zema_scene* s, const double* X0, const double* X1, DBuf<Pair
 // `list_env`): fills s->act / s->act_env and, if asked, the per-env minimum
 // distance of active pairs.
 uint32_t active_from(zema_scene* s, const double* X, const PairRec* list, const uint32_t* list_env, uint32_t n,
-                     bool want_dmin) {
+                     bool want_dmin, const int* dmin_keep = nullptr) {
     cudaStream_t st = s->st;
     int NE = s->n_envs;
     if (want_dmin) {
-        std::vector<double> inf(NE, INFINITY);
-        ZCHECK(cudaMemcpyAsync(s->dmin.p, inf.data(), NE * sizeof(double), cudaMemcpyHostToDevice, st));
+        // d_min restarts at infinity except for envs flagged in dmin_keep
+        // (converged envs whose pairs the list no longer holds)
+        ZL(k_reset_dmin, div_up(NE, 64), 64, 0, st)(s->dmin.p, NE, dmin_keep);
+        ZLAUNCH();
     }
     s->flag.ensure(&s->A, n + 1);
     s->flagoff.ensure(&s->A, n + 2);
@@ -1351,7 +1362,15 @@ int line_search(zema_scene* s, const double* dir, const std::vector<int>& done_h
     // X1 is overwritten by energy(); keep the swept end positions in q (scratch)
     s->q.ensure(&s->A, std::max<size_t>(3 * (size_t)s->n_nodes + 3, 3 * (size_t)s->n_sv + 3));
     ZCHECK(cudaMemcpyAsync(s->q.p, s->X1.p, 3 * (size_t)s->n_sv * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    uint32_t ns = candidates(s, s->X.p, s->q.p, s->swept, s->swept_env);
+    // converged envs take no step: their primitives stay out of the swept
+    // broad phase and the ACCD
+    bool any_done = false;
+    for (int e = 0; e < NE; ++e) any_done |= done_h[e] != 0;
+    if (any_done) {
+        for (int e = 0; e < NE; ++e) s->hi[e] = done_h[e] ? 1 : 0;
+        ZCHECK(cudaMemcpyAsync(s->skip.p, s->hi, NE * sizeof(int), cudaMemcpyHostToDevice, st));
+    }
+    uint32_t ns = candidates(s, s->X.p, s->q.p, s->swept, s->swept_env, any_done ? s->skip.p : nullptr);
     s->n_swept = ns;
     ZCHECK(cudaMemsetAsync(s->capflag.p, 0, sizeof(int), st));
     if (ns) ZL(k_accd, div_up(ns, 128), 128, 0, st)(G, s->X.p, s->q.p, s->swept.p, (int)ns, s->alpha.p, s->capflag.p);
@@ -1618,7 +1637,9 @@ void do_step(zema_scene* s) {
                 // x was reached by a line search along the last swept motion (the
                 // warm start or the previous Newton step), so that swept
                 // candidate list contains every pair with d < dhat at x
-                active_from(s, s->X.p, s->swept.p, s->swept_env.p, s->n_swept, true);
+                for (int e = 0; e < NE; ++e) s->hi[e] = done[e] ? 1 : 0;
+                ZCHECK(cudaMemcpyAsync(s->skip.p, s->hi, NE * sizeof(int), cudaMemcpyHostToDevice, st));
+                active_from(s, s->X.p, s->swept.p, s->swept_env.p, s->n_swept, true, s->skip.p);
                 double tb = now_ms();
                 s->S.ms_phase[0] += tb - ta;
                 grad_hess(s);
@@ -1666,6 +1687,13 @@ void do_step(zema_scene* s) {
             ZL(k_al_update, div_up(s->n_aff, 64), 64, 0, st)(G, s->x.p, s->qtarget.p, s->lamA.p, s->need.p);
             ZLAUNCH();
             for (int e = 0; e < NE; ++e) done[e] = s->hi[e] ? 0 : 1;
+            // the resuming envs may have been left out of the last swept list:
+            // candidates at x (static boxes) for them
+            for (int e = 0; e < NE; ++e) s->hi[e] = done[e];
+            ZCHECK(cudaMemcpyAsync(s->skip.p, s->hi, NE * sizeof(int), cudaMemcpyHostToDevice, st));
+            ZL(k_sv_pos, div_up(s->n_sv, TB), TB, 0, st)(G, s->x.p, s->X.p);
+            ZLAUNCH();
+            s->n_swept = candidates(s, s->X.p, nullptr, s->swept, s->swept_env, s->skip.p);
         }
         return rounds;
     };
