@@ -259,6 +259,21 @@ zema_status zema_local_neo_hookean(int64_t n, const double* F9, double mu, doubl
 zema_status zema_local_accd(int64_t n, const double* x12, const double* p12, const int32_t* is_ee,
                             double* t_out, void* stream);
 
+/* Autotuner of the linear solve's launch schedule (the paper has no
+ * counterpart).  The next solve of the scene times the cluster solve of that
+ * step's system with every valid number of CTAs per environment (1, 2, 4, 8,
+ * 16: best of two runs each, results discarded) and keeps the fastest for
+ * the rest of the scene's life; that solve and every later one use it.  A
+ * scene that is never tuned uses about one CTA per 128 nodes (at most 16)
+ * and is bit-reproducible run to run; tuning picks by measured time, so two
+ * tuned scenes may differ in rounding. */
+zema_status zema_autotune(zema_scene* s);
+/* The cluster size in use (0: not chosen yet, -1: grid-wide solve) for
+ * precision 0 (FP64) or 1 (mixed), and the autotuner's measurements:
+ * candidate sizes and solve times in ms (up to cap entries; *n = count). */
+zema_status zema_get_tuning(const zema_scene* s, int32_t precision, int32_t* cluster_size, int32_t* cand, float* ms,
+                            int32_t cap, int32_t* n);
+
 /* Learned Newton warm start (an addition to the method).  The network maps
  * 13 features of a soft vertex at the step's start to its predicted
  * displacement over the step, both scaled by s = h^2 |g| (the features:

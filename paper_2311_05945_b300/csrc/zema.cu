@@ -95,6 +95,8 @@ struct zema_scene {
     // cluster PCG: CTAs per env (0 = not chosen yet, -1 = unavailable) and
     // its shared-memory layout bounds
     int pcgc_cs[2] = {0, 0};
+    bool pcgc_tune[2] = {false, false};  // autotune the cluster size at the next solve
+    std::vector<std::pair<int, float>> pcgc_tuned[2];  // (cluster size, solve ms) measured by the autotuner
     int pcgc_max_env_nodes = 0, pcgc_max_soft = 0, pcgc_max_aff = 0;
     DBuf<double> tolv;
     // pair lists
@@ -1155,6 +1157,22 @@ int pcgc_choose(zema_scene* s) {
     return cs;
 }
 
+// whether cluster size cs can run the cluster solve of this scene
+template <class T>
+bool pcgc_valid(zema_scene* s, int cs) {
+    if (cs < 1 || cs > 16 || pcgc_max_rows(s, cs) > kPcgcOwn * kPcgcThreads || pcgc_smem<T>(s, cs) > kPcgcMaxSmem)
+        return false;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    pcgc_config<T>(s, cs, cfg, at);
+    int ncl = 0;
+    if (cudaOccupancyMaxActiveClusters(&ncl, k_pcg_cluster<T>, &cfg) != cudaSuccess || ncl < 1) {
+        cudaGetLastError();
+        return false;
+    }
+    return true;
+}
+
 // ---------------------------------------------------------------------------
 // PCG: solve (S + C) p = -g for every env not flagged in done_h (one
 // persistent cooperative launch per solve)
@@ -1171,7 +1189,7 @@ int64_t pcg_t(zema_scene* s, const std::vector<int>& done_h) {
     ZL(k_precond<T>, div_up(s->n_units, 128), 128, 0, st)(G, S, C, Minv_s, Minv_a);
     ZL(k_negate, div_up(3 * (size_t)s->n_nodes, TB), TB, 0, st)(s->g.p, s->b.p, 3 * (size_t)s->n_nodes);
     ZLAUNCH();
-    for (int e = 0; e < NE; ++e) s->hi[e] = done_h[e];
+    for (int e = 0; e < NE; ++e) s->hi[e] = s->hi[3 * NE + e] = done_h[e];
     ZCHECK(cudaMemcpyAsync(s->conv.p, s->hi, NE * sizeof(int), cudaMemcpyHostToDevice, st));
     ZCHECK(cudaMemsetAsync(s->pcg_iters.p, 0, NE * sizeof(int), st));
     const int pi = s->P.precision == 1 ? 1 : 0;
@@ -1193,8 +1211,8 @@ int64_t pcg_t(zema_scene* s, const std::vector<int>& done_h) {
         }
     };
     if (use_cluster) {
-        const int cs = s->pcgc_cs[pi];
-        auto run_cluster = [&](const double* rhs, double* xo) {
+        // one cluster solve with cs CTAs per env (launch only)
+        auto launch_cluster = [&](const double* rhs, double* xo, int cs) {
             PcgcArgs<T> c;
             c.G = G;
             c.S = S;
@@ -1220,6 +1238,44 @@ int64_t pcg_t(zema_scene* s, const std::vector<int>& done_h) {
                 ZCHECK(cudaLaunchKernelEx(&cfg, k_pcg_cluster<T>, c));
             }
             ZLAUNCH();
+        };
+        if (s->pcgc_tune[pi]) {
+            // autotuner: time the solve of this system with every valid cluster
+            // size (results discarded, best of two runs each) and keep the
+            // fastest; the solve below then uses it
+            s->pcgc_tune[pi] = false;
+            s->pcgc_tuned[pi].clear();
+            cudaEvent_t e0, e1;
+            ZCHECK(cudaEventCreate(&e0));
+            ZCHECK(cudaEventCreate(&e1));
+            float best = INFINITY;
+            int best_cs = s->pcgc_cs[pi];
+            for (int cs = 1; cs <= 16; cs *= 2) {
+                if (!pcgc_valid<T>(s, cs)) continue;
+                float ms = INFINITY;
+                for (int rep = 0; rep < 2; ++rep) {
+                    ZCHECK(cudaMemcpyAsync(s->conv.p, s->hi + 3 * NE, NE * sizeof(int), cudaMemcpyHostToDevice, st));
+                    ZCHECK(cudaEventRecord(e0, st));
+                    launch_cluster(s->b.p, s->r.p, cs);
+                    ZCHECK(cudaEventRecord(e1, st));
+                    ZCHECK(cudaEventSynchronize(e1));
+                    float t = 0.0f;
+                    ZCHECK(cudaEventElapsedTime(&t, e0, e1));
+                    ms = std::min(ms, t);
+                }
+                s->pcgc_tuned[pi].push_back({cs, ms});
+                if (ms < best) {
+                    best = ms;
+                    best_cs = cs;
+                }
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            s->pcgc_cs[pi] = best_cs;
+            ZCHECK(cudaMemcpyAsync(s->conv.p, s->hi + 3 * NE, NE * sizeof(int), cudaMemcpyHostToDevice, st));
+        }
+        auto run_cluster = [&](const double* rhs, double* xo) {
+            launch_cluster(rhs, xo, s->pcgc_cs[pi]);
             collect(true);
         };
         run_cluster(s->b.p, s->p.p);
@@ -2176,6 +2232,25 @@ zema_status zema_record_warmstart(zema_scene* s, float* features, float* targets
     if (features && cap_rows < s->ws_ns) return ZEMA_ERR_INVALID_ARG;
     s->rec_feat = features;
     s->rec_targ = targets;
+    return ZEMA_OK;
+}
+
+zema_status zema_autotune(zema_scene* s) {
+    if (!s) return ZEMA_ERR_INVALID_ARG;
+    s->pcgc_tune[0] = s->pcgc_tune[1] = true;
+    return ZEMA_OK;
+}
+
+zema_status zema_get_tuning(const zema_scene* s, int32_t precision, int32_t* cluster_size, int32_t* cand,
+                            float* ms, int32_t cap, int32_t* n) {
+    if (!s || !cluster_size || precision < 0 || precision > 1) return ZEMA_ERR_INVALID_ARG;
+    *cluster_size = s->pcgc_cs[precision];
+    const auto& t = s->pcgc_tuned[precision];
+    if (n) *n = (int32_t)t.size();
+    for (int i = 0; i < (int)t.size() && i < cap; ++i) {
+        if (cand) cand[i] = t[i].first;
+        if (ms) ms[i] = t[i].second;
+    }
     return ZEMA_OK;
 }
 

@@ -108,6 +108,8 @@ def lib():
     L.zema_profile_read.argtypes = [DP, C.POINTER(C.c_longlong), DP]
     FP = C.POINTER(C.c_float)
     L.zema_load_warmstart.argtypes = [C.c_void_p, C.c_void_p, C.c_int64]
+    L.zema_autotune.argtypes = [C.c_void_p]
+    L.zema_get_tuning.argtypes = [C.c_void_p, C.c_int32, IP, IP, FP, C.c_int32, IP]
     L.zema_record_warmstart.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]
     L.zema_mlp_create.argtypes = [IP, C.c_int32, C.c_uint64, C.c_void_p, C.POINTER(C.c_void_p)]
     L.zema_mlp_destroy.argtypes = [C.c_void_p]
@@ -247,6 +249,20 @@ class Scene:
             self.close()
         except Exception:
             pass
+
+    def autotune(self):
+        """Tune the linear solve's CTAs per environment at the next solve."""
+        _check(lib().zema_autotune(self.h), self.h)
+
+    def tuning(self, precision=None):
+        """(cluster size in use, {candidate: solve ms}) of the autotuner."""
+        p = self._P.precision if precision is None else precision
+        cs, n = C.c_int32(), C.c_int32()
+        cand = np.zeros(8, dtype=np.int32)
+        ms = np.zeros(8, dtype=np.float32)
+        _check(lib().zema_get_tuning(self.h, p, C.byref(cs), _ip(cand), ms.ctypes.data_as(C.POINTER(C.c_float)), 8,
+                                     C.byref(n)), self.h)
+        return cs.value, {int(cand[i]): float(ms[i]) for i in range(n.value)}
 
     def load_warmstart(self, dims, theta):
         """Load the learned warm-start network (dims[0] = 13, dims[-1] = 3)."""

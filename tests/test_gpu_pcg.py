@@ -134,3 +134,22 @@ def test_c2_mixed_follows_fp64_through_first_contact():
             assert sb["newton_iters"] > 0 and sb["pcg_iters"] > 0, (k, sa, sb)
     err = np.abs(env_positions(a, sc, 0) - env_positions(b, sc, 0)).max()
     assert err < 1e-4 * diag, err / diag
+
+
+def test_autotuned_cluster_solve_keeps_parity():
+    # the autotuner times every valid cluster size on one system, keeps the
+    # fastest, and the tuned solve still matches the oracle's step
+    sc = S.scene_c1()
+    orc = Oracle(sc, tol_scale=1e-2)
+    orc.step(12)
+    gpu = gpu_scene(sc, tol_scale=1e-2, precision=1)
+    transplant(orc, gpu, sc)
+    gpu.autotune()
+    orc.step(1)
+    gpu.step(1)
+    cs, measured = gpu.tuning()
+    assert cs in measured and len(measured) >= 2
+    assert measured[cs] == min(measured.values())
+    diag = orc.diag()
+    err = np.abs(env_positions(orc, sc, 0) - env_positions(gpu, sc, 0)).max()
+    assert err < 1e-5 * diag, err / diag
