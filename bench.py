@@ -97,15 +97,26 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def build_scene():
+def build_scene(args=None, rank=0, world=1):
+    """The rank's scene: the single-env grasp, or its share of the batched
+    grasp (contiguous env range balanced by tet count; env i keeps seed
+    1000 + i whatever the sharding)."""
     from paper_2311_05945_b300 import scenes
-    return scenes.scene_c2()
+    if args is None or args.workload == "c2":
+        return scenes.scene_c2()
+    from paper_2311_05945_b300.sharding import shard_envs
+    full = scenes.scene_c3(n_envs=args.envs, n_steps=args.warmup + args.steps)
+    w = [0] * args.envs
+    for b in full.tets:
+        w[b.env] += len(b.tets)
+    a, b = shard_envs(w, world)[rank]
+    return scenes.scene_c3(n_envs=b - a, n_steps=args.warmup + args.steps, seed0=1000 + a)
 
 
-def oracle_steps_per_s(n_warm, n_steps):
+def oracle_steps_per_s(n_warm, n_steps, sc=None):
     """The CPU oracle, as it stands, on the same workload (single core)."""
     from oracle.oracle import Oracle
-    sc = build_scene()
+    sc = build_scene() if sc is None else sc
     o = Oracle(sc)
     if n_warm:
         o.step(n_warm)
@@ -143,7 +154,8 @@ def time_form(args, world, dist, precision, profile_kernel=None):
 
     from paper_2311_05945_b300 import zema as Z
 
-    sc = build_scene()
+    rank = int(os.environ.get("RANK", "0"))
+    sc = build_scene(args, rank, world)
     gpu = Z.Scene(sc, precision=precision)
     st = torch.cuda.current_stream()
     for k in range(args.warmup):
@@ -175,10 +187,8 @@ def time_form(args, world, dist, precision, profile_kernel=None):
     prof = Z.profile_read() if profile_kernel else None
     Z.profile_kernel(None)
     total_ms = sum(a.elapsed_time(b) for a, b in ev)
-    if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    from paper_2311_05945_b300.sharding import max_over_ranks
+    total_ms = max_over_ranks(total_ms, dist, "cuda")
     gpu.tuned = gpu.tuning()
     return sc, gpu, total_ms, stats, launches, prof
 
@@ -199,8 +209,11 @@ def run_ours(args, rank, world):
     clocks.start()
     sc, gpu, total_ms, stats, launches, prof = time_form(args, world, dist, 1, ROOFLINE_KERNEL)
     clk = clocks.stop()
-    value = world * args.steps / (total_ms / 1e3)
-    plain_value = world * args.steps / (plain_ms / 1e3)
+    from paper_2311_05945_b300.sharding import max_over_ranks
+    envs_per_rank = sc.n_envs
+    units = world * envs_per_rank if args.workload == "c3" else world
+    value = units * args.steps / (total_ms / 1e3)
+    plain_value = units * args.steps / (plain_ms / 1e3)
     # end to end through the C ABI with pinned host buffers, over the same
     # step window [W, W + K) of a fresh scene: every timed step uploads the
     # bodies' states from pinned host memory, steps, and reads them back
@@ -223,12 +236,8 @@ def run_ours(args, rank, world):
             g2.get_state_ptr(b, host[b].data_ptr(), host[b].numel())
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    e2e_val = e2e_steps / e2e_s
+    e2e_val = units * e2e_steps / max_over_ranks(e2e_s, dist, "cuda")
     g2.close()
-    if dist:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_val = world * e2e_steps / float(t.item())
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -245,26 +254,36 @@ def run_ours(args, rank, world):
                 "peak_source": "measured" if peaks else "fallback",
                 "alg_bytes_per_launch": per_launch_bytes, "avg_launch_us": 1e3 * k_ms / k_launches,
                 "launches": k_launches, "share_of_step_time": k_ms / total_ms if world == 1 else None}
+    unit = "env-steps/s" if args.workload == "c3" else UNIT
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        v, dt = oracle_steps_per_s(0, args.cpu_steps)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"grasp steps [0, {args.cpu_steps}) of the same script on the CPU oracle ({dt:.1f} s)"}
+        if args.workload == "c3":
+            from paper_2311_05945_b300 import scenes
+            v, dt = oracle_steps_per_s(0, 1, scenes.scene_c3(n_envs=1, n_steps=2))
+            sample = f"env 0 of the batch (seed 1000), step 0, on the CPU oracle ({dt:.1f} s)"
+        else:
+            v, dt = oracle_steps_per_s(0, args.cpu_steps)
+            sample = f"grasp steps [0, {args.cpu_steps}) of the same script on the CPU oracle ({dt:.1f} s)"
+        cpu = {"value": v, "unit": unit, "cores": 1, "kind": "oracle", "sample": sample}
     agg = {k: sum(s[k] for s in stats) for k in ("newton_iters", "pcg_iters", "ls_halvings", "al_rounds", "pcg_refines")}
     phase = {k: sum(s["ms_phase"][k] for s in stats) for k in stats[0]["ms_phase"]}
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "metric": METRIC, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "mixed f32/f64", "data": "synthetic (seeded generators)",
-        "config": {"workload": WORKLOAD, "timed_steps": [args.warmup, args.warmup + args.steps],
+        "config": {"workload": WORKLOAD if args.workload == "c2" else
+                   f"batched parallel-jaw grasp, {args.envs} envs (ellipsoid/torus/box, 2k-20k tets log-uniform, "
+                   f"E 1e4-1e6, mu 0.3-1.0), one launch per phase over all envs; {envs_per_rank} envs per rank",
+                   "timed_steps": [args.warmup, args.warmup + args.steps],
                    "form": "mixed precision (FP32 Hessians, matrices and PCG with FP64 residual refinement; FP64 "
                            "gradients/energies/distances/CCD/convergence) + CCD-filtered constant-velocity warm "
-                           "start; 1 env so no batching",
+                           "start" + ("; 1 env so no batching" if args.workload == "c2" else "; all envs batched"),
                    "plain_fp64": {"value": plain_value, "ms_per_step": plain_ms / args.steps,
                                   "newton_iters": sum(s["newton_iters"] for s in plain_stats),
                                   "pcg_iters": sum(s["pcg_iters"] for s in plain_stats)},
                    "speedup_vs_plain": value / plain_value,
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "parallelism": (f"replicas x{world}" if args.workload == "c2" else f"envs sharded over {world} ranks")
+                   if world > 1 else "single GPU",
                    "l2": "flushed between timed steps (512 MB write)",
                    "newton_iters": agg["newton_iters"], "pcg_iters": agg["pcg_iters"],
                    "ls_halvings": agg["ls_halvings"], "al_rounds": agg["al_rounds"],
@@ -274,7 +293,7 @@ def run_ours(args, rank, world):
                    "host_phase_ms": {k: round(v, 2) for k, v in phase.items()}},
         "roofline": roof,
         "cpu_baseline": cpu,
-        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": state_bytes(sc),
+        "e2e": {"value": e2e_val, "unit": unit, "h2d_bytes_per_step": state_bytes(sc),
                 "d2h_bytes_per_step": state_bytes(sc)},
         "gpu_launches": launches,
         "clocks": clk,
@@ -290,6 +309,9 @@ def main():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3"],
+                    help="c2: the single-env grasp (headline); c3: the batched grasp, env-steps/s")
+    ap.add_argument("--envs", type=int, default=256, help="envs of the batched grasp (c3)")
     ap.add_argument("--e2e-steps", type=int, default=None,
                     help="end-to-end steps (default: the timed steps, same window)")
     ap.add_argument("--cpu-steps", type=int, default=2)

@@ -46,6 +46,7 @@ struct PcgcArgs {
     int* conv;           // per env in: 1 = skip; out: 1, or 2 after a non-finite value
     int* iters;          // per env: iterations run
     double tol2;
+    const double* tol2_env;  // nullable: per-env |r|^2 / |b|^2 stop ratio instead of tol2
     int max_iter;
     int max_env_nodes;   // shared-memory layout bounds
     int max_rows;        // soft rows owned by one CTA, max over envs
@@ -239,7 +240,7 @@ __global__ void __launch_bounds__(kPcgcThreads) k_pcg_cluster(PcgcArgs<Real> a) 
     cluster_total<2>(cl, s_part + 1, s_tot + 1);  // s_tot[1] = r.z, s_tot[2] = b.b
     Real rz = s_tot[1];
     const Real bb = s_tot[2];
-    const Real stop2 = (Real)a.tol2 * bb;
+    const Real stop2 = (Real)(a.tol2_env ? a.tol2_env[e] : a.tol2) * bb;
     bool bad = !isfinite(bb);
     bool done = bad || !(bb > Real(0));
     Real beta = 0;

@@ -87,6 +87,7 @@ struct zema_scene {
     DBuf<double> x, v, xt, xhat, p, xtrial, g, b, r, z, pp, q, X, Xt, X1, stage_blk, stage_g, S_val, Minv_s, Minv_a;
     DBuf<double> qtarget, lamA;
     // per env
+    DBuf<double> tol2_env;
     DBuf<double> kappa, kappa_min, alpha, E, dmin, part, part2, part3, part4, part5, part6, part7;
     DBuf<int> conv, pcg_iters, need, capflag, skip;
     DBuf<int> tile_u0, tile_u1, tile_n0, tile_n1, tile_env, env_tile_start;
@@ -729,7 +730,7 @@ void build(zema_scene* s) {
     s->S_val.ensure(A, 9 * (size_t)s->n_sblocks + 9);
     s->Minv_s.ensure(A, 9 * (size_t)nN + 9);
     s->Minv_a.ensure(A, 144 * (size_t)s->n_aff + 144);
-    for (DBuf<double>* b : {&s->kappa, &s->kappa_min, &s->alpha, &s->E, &s->dmin}) b->ensure(A, NE + 1);
+    for (DBuf<double>* b : {&s->kappa, &s->kappa_min, &s->alpha, &s->E, &s->dmin, &s->tol2_env}) b->ensure(A, NE + 1);
     for (DBuf<double>* b : {&s->part, &s->part2, &s->part3, &s->part4, &s->part5, &s->part6, &s->part7})
         b->ensure(A, (size_t)ET_COUNT * NE * kChunks + 8);
     for (DBuf<int>* b : {&s->conv, &s->pcg_iters, &s->need, &s->skip}) b->ensure(A, NE + 1);
@@ -1212,7 +1213,7 @@ int64_t pcg_t(zema_scene* s, const std::vector<int>& done_h) {
     };
     if (use_cluster) {
         // one cluster solve with cs CTAs per env (launch only)
-        auto launch_cluster = [&](const double* rhs, double* xo, int cs) {
+        auto launch_cluster = [&](const double* rhs, double* xo, int cs, const double* tol2_env = nullptr) {
             PcgcArgs<T> c;
             c.G = G;
             c.S = S;
@@ -1225,6 +1226,7 @@ int64_t pcg_t(zema_scene* s, const std::vector<int>& done_h) {
             c.conv = s->conv.p;
             c.iters = s->pcg_iters.p;
             c.tol2 = s->P.pcg_rel_tol * s->P.pcg_rel_tol;
+            c.tol2_env = tol2_env;
             c.max_iter = s->P.max_pcg;
             c.max_env_nodes = s->pcgc_max_env_nodes;
             c.max_rows = pcgc_max_rows(s, cs);
@@ -1274,8 +1276,8 @@ int64_t pcg_t(zema_scene* s, const std::vector<int>& done_h) {
             s->pcgc_cs[pi] = best_cs;
             ZCHECK(cudaMemcpyAsync(s->conv.p, s->hi + 3 * NE, NE * sizeof(int), cudaMemcpyHostToDevice, st));
         }
-        auto run_cluster = [&](const double* rhs, double* xo) {
-            launch_cluster(rhs, xo, s->pcgc_cs[pi]);
+        auto run_cluster = [&](const double* rhs, double* xo, const double* tol2_env = nullptr) {
+            launch_cluster(rhs, xo, s->pcgc_cs[pi], tol2_env);
             collect(true);
         };
         run_cluster(s->b.p, s->p.p);
@@ -1298,7 +1300,9 @@ int64_t pcg_t(zema_scene* s, const std::vector<int>& done_h) {
                 ZCHECK(cudaMemcpyAsync(pbb.data(), s->part7.p, nc * sizeof(double), cudaMemcpyDeviceToHost, st));
                 ZCHECK(cudaStreamSynchronize(st));
                 int count = 0;
+                const double tol2 = s->P.pcg_rel_tol * s->P.pcg_rel_tol;
                 for (int e = 0; e < NE; ++e) {
+                    s->hd[e] = tol2;
                     if (!need[e]) continue;
                     double rr = 0.0, bbv = 0.0;
                     for (int k = 0; k < kChunks; ++k) {
@@ -1306,14 +1310,18 @@ int64_t pcg_t(zema_scene* s, const std::vector<int>& done_h) {
                         bbv += pbb[(size_t)e * kChunks + k];
                     }
                     if (!std::isfinite(rr)) fail(ZEMA_ERR_NONFINITE, "non-finite residual of the linear solve");
-                    need[e] = rr > s->P.pcg_rel_tol * s->P.pcg_rel_tol * bbv ? 1 : 0;
+                    need[e] = rr > tol2 * bbv ? 1 : 0;
                     count += need[e];
+                    // the correction d only has to bring |r - A d| under
+                    // tol |b|: stop its solve at half of that, relative to |r|
+                    if (need[e]) s->hd[e] = std::min(0.25, 0.25 * tol2 * bbv / rr);
                 }
                 if (!count) break;
                 s->S.pcg_refines += count;
                 for (int e = 0; e < NE; ++e) s->hi[e] = need[e] ? 0 : 1;
                 ZCHECK(cudaMemcpyAsync(s->conv.p, s->hi, NE * sizeof(int), cudaMemcpyHostToDevice, st));
-                run_cluster(s->q.p, s->r.p);
+                ZCHECK(cudaMemcpyAsync(s->tol2_env.p, s->hd, NE * sizeof(double), cudaMemcpyHostToDevice, st));
+                run_cluster(s->q.p, s->r.p, s->tol2_env.p);
                 for (int e = 0; e < NE; ++e) s->hi[e] = need[e];
                 ZCHECK(cudaMemcpyAsync(s->need.p, s->hi, NE * sizeof(int), cudaMemcpyHostToDevice, st));
                 ZL(k_add_env, div_up(s->n_nodes, TB), TB, 0, st)(G, s->p.p, s->r.p, s->need.p);
