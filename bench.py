@@ -36,7 +36,7 @@ ROOFLINE_KERNEL = "k_pcg_cluster"
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
 # ROOFLINE_KERNEL from an ncu capture of the first solve of grasp step 20
 # (a launch of the bench's average length); None once the kernel changes.
-ROOFLINE_TRAFFIC = 1.364e6
+ROOFLINE_TRAFFIC = None
 
 
 def measured_peaks():

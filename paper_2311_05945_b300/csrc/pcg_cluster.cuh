@@ -51,14 +51,22 @@ struct PcgcArgs {
     int max_env_nodes;   // shared-memory layout bounds
     int max_rows;        // soft rows owned by one CTA, max over envs
     int max_aff;         // affine bodies per env, max over envs
+    int slice_cap;       // blocks of a CTA's matrix slice that fit in shared memory (0: never staged)
+    int chunk_cap;       // SpMV chunks a CTA can hold (more: one task per row instead)
 };
 
 constexpr int kPcgcThreads = 512;
-constexpr int kPcgcGroup = 16;  // lanes per row in the SpMV
+constexpr int kPcgcGroup = 4;   // lanes per row in the SpMV (8 rows per warp at a time)
 constexpr int kPcgcMaxCluster = 16;
-constexpr int kPcgcStageBatch = 4;  // nodes per thread whose loads are issued together
+constexpr int kPcgcStageBatch = 16;  // values of z per thread whose loads are issued together
 constexpr int kPcgcOwn = 2;         // soft rows per thread: a CTA owns at most 2 * kPcgcThreads rows
 constexpr int kPcgcRefine = 3;      // FP64 residual refinements of an FP32 solve
+constexpr int kPcgcChunk = 8;       // blocks per SpMV chunk
+// values per node of the staged p vector
+template <class Real>
+__host__ __device__ constexpr int pcgc_pstride() {
+    return 3;
+}
 
 __device__ __forceinline__ float ldcg_r(const float* p) { return __ldcg(p); }
 __device__ __forceinline__ double ldcg_r(const double* p) { return __ldcg(p); }
@@ -110,23 +118,71 @@ __device__ __forceinline__ void cluster_total(cooperative_groups::cluster_group&
 
 // q for one row: the blocks [s0, s1) of S followed by [c0, c1) of C, the 16
 // lanes of a group striding over both ranges as one; p gathered from the
-// staged env vector.
+// staged env vector.  S and C are the global BSR arrays, or both the CTA's
+// slice in shared memory (generic loads serve either).
 template <class Real>
-__device__ __forceinline__ void row_part(const Bsr<Real>& S, const Bsr<Real>& C, int4 g, const Real* s_p, int nb,
-                                         int n_env, int gl, Real& y0, Real& y1, Real& y2) {
-    const int ls = g.y - g.x, n = ls + (g.w - g.z);
-    for (int j = gl; j < n; j += kPcgcGroup) {
-        const bool in_s = j < ls;
-        const int k = in_s ? g.x + j : g.z + (j - ls);
-        const int* colp = in_s ? S.col : C.col;
-        const Real* v = (in_s ? S.val : C.val) + 9 * (size_t)k;
-        unsigned c = (unsigned)(__ldg(colp + k) - nb);
-        if (c >= (unsigned)n_env) continue;  // cannot happen: blocks stay inside one env
-        Real p0 = s_p[3 * c], p1 = s_p[3 * c + 1], p2 = s_p[3 * c + 2];
-        y0 += __ldg(v + 0) * p0 + __ldg(v + 1) * p1 + __ldg(v + 2) * p2;
-        y1 += __ldg(v + 3) * p0 + __ldg(v + 4) * p1 + __ldg(v + 5) * p2;
-        y2 += __ldg(v + 6) * p0 + __ldg(v + 7) * p1 + __ldg(v + 8) * p2;
+__device__ __forceinline__ void block_fma(const Bsr<Real>& S, const Bsr<Real>& C, int4 g, int ls, int j,
+                                          const Real* s_p, int nb, int n_env, Real& y0, Real& y1, Real& y2) {
+    constexpr int PS = pcgc_pstride<Real>();
+    const bool in_s = j < ls;
+    const int k = in_s ? g.x + j : g.z + (j - ls);
+    const unsigned c = (unsigned)((in_s ? S.col : C.col)[k] - nb);
+    if (c >= (unsigned)n_env) return;  // cannot happen: blocks stay inside one env
+    const Real* v = (in_s ? S.val : C.val) + 9 * (size_t)k;
+    const Real p0 = s_p[PS * c], p1 = s_p[PS * c + 1], p2 = s_p[PS * c + 2];
+    y0 += v[0] * p0 + v[1] * p1 + v[2] * p2;
+    y1 += v[3] * p0 + v[4] * p1 + v[5] * p2;
+    y2 += v[6] * p0 + v[7] * p1 + v[8] * p2;
+}
+
+// a block of the staged FP32 slice: 12 floats (the 9 values, the column as
+// int bits, 2 pad) read as three 16-byte vectors
+__device__ __forceinline__ void block_fma4(const float4* blk, const float* sp, int nb, int n_env, float& y0,
+                                           float& y1, float& y2) {
+    const float4 a = blk[0], b = blk[1], c4 = blk[2];
+    const unsigned c = (unsigned)(__float_as_int(c4.y) - nb);
+    if (c >= (unsigned)n_env) return;  // cannot happen: blocks stay inside one env
+    const float p0 = sp[3 * c], p1 = sp[3 * c + 1], p2 = sp[3 * c + 2];
+    y0 += a.x * p0 + a.y * p1 + a.z * p2;
+    y1 += a.w * p0 + b.x * p1 + b.y * p2;
+    y2 += b.z * p0 + b.w * p1 + c4.x * p2;
+}
+
+// blocks [jb, je) of a row of the staged slice (local S range, then local C range)
+__device__ __forceinline__ void row_part4(const float4* slice, int4 g, int jb, int je, const float* sp, int nb,
+                                          int n_env, int gl, float& y0, float& y1, float& y2) {
+    const int ls = g.y - g.x;
+    float u0 = 0, u1 = 0, u2 = 0;
+    int j = jb + gl;
+    for (; j + kPcgcGroup < je; j += 2 * kPcgcGroup) {
+        const int k0 = j < ls ? g.x + j : g.z + (j - ls);
+        const int j1 = j + kPcgcGroup;
+        const int k1 = j1 < ls ? g.x + j1 : g.z + (j1 - ls);
+        block_fma4(slice + 3 * (size_t)k0, sp, nb, n_env, y0, y1, y2);
+        block_fma4(slice + 3 * (size_t)k1, sp, nb, n_env, u0, u1, u2);
     }
+    if (j < je) block_fma4(slice + 3 * (size_t)(j < ls ? g.x + j : g.z + (j - ls)), sp, nb, n_env, y0, y1, y2);
+    y0 += u0;
+    y1 += u1;
+    y2 += u2;
+}
+
+// blocks [jb, je) of the row's combined index space (S range, then C range)
+template <class Real>
+__device__ __forceinline__ void row_part(const Bsr<Real>& S, const Bsr<Real>& C, int4 g, int jb, int je,
+                                         const Real* s_p, int nb, int n_env, int gl, Real& y0, Real& y1, Real& y2) {
+    const int ls = g.y - g.x, n = je;
+    // two blocks per iteration (independent accumulators), summed in a fixed order
+    Real u0 = 0, u1 = 0, u2 = 0;
+    int j = jb + gl;
+    for (; j + kPcgcGroup < n; j += 2 * kPcgcGroup) {
+        block_fma(S, C, g, ls, j, s_p, nb, n_env, y0, y1, y2);
+        block_fma(S, C, g, ls, j + kPcgcGroup, s_p, nb, n_env, u0, u1, u2);
+    }
+    if (j < n) block_fma(S, C, g, ls, j, s_p, nb, n_env, y0, y1, y2);
+    y0 += u0;
+    y1 += u1;
+    y2 += u2;
 }
 
 template <class Real>
@@ -137,7 +193,7 @@ __device__ __forceinline__ Real group_sum(Real v) {
 }
 
 template <class Real>
-__global__ void __launch_bounds__(kPcgcThreads) k_pcg_cluster(PcgcArgs<Real> a) {
+__global__ void __launch_bounds__(kPcgcThreads, 1) k_pcg_cluster(PcgcArgs<Real> a) {
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
     const Geo& G = a.G;
@@ -149,14 +205,22 @@ __global__ void __launch_bounds__(kPcgcThreads) k_pcg_cluster(PcgcArgs<Real> a) 
 
     constexpr int NW = kPcgcThreads / 32;
     extern __shared__ int4 smi[];
-    int4* s_rng = smi;                 // [max_rows + 4 * max_aff] block ranges of the SpMV tasks in S and C
-    Real* s_w = (Real*)(s_rng + a.max_rows + 4 * a.max_aff);  // [3][NW] warp partials
+    const int max_tasks = a.max_rows + 4 * a.max_aff;
+    int4* s_rng = smi;                         // [max_tasks] block ranges of the SpMV tasks in S and C
+    int4* s_chunk = s_rng + max_tasks;         // [chunk_cap] (task, first, end) of each SpMV chunk
+    int* s_cpre = (int*)(s_chunk + a.chunk_cap);  // [max_tasks + 1] first chunk of each task
+    Real* s_w = (Real*)(s_cpre + ((max_tasks + 4) & ~3));  // [3][NW] warp partials
     Real* s_part = s_w + 3 * NW;       // [4] this CTA's partials (read by the cluster)
     Real* s_tot = s_part + 4;          // [4] cluster totals
-    Real* s_p = s_tot + 4;             // [3 * max_env_nodes] p over the whole env
-    Real* s_q = s_p + 3 * (size_t)a.max_env_nodes;  // [3 * max_rows] q of the owned soft rows
+    constexpr int PS = pcgc_pstride<Real>();
+    Real* s_p = s_tot + 4;             // [PS * max_env_nodes] p over the whole env (16-byte aligned)
+    Real* s_q = s_p + PS * (size_t)a.max_env_nodes;  // [3 * max_rows] q of the owned soft rows
     Real* s_qa = s_q + 3 * (size_t)a.max_rows;      // [12 * max_aff] partial q of the affine rows
     Real* s_ra = s_qa + 12 * (size_t)a.max_aff;     // [12 * max_aff] r of the affine rows (last rank)
+    Real* s_cpart = s_ra + 12 * (size_t)a.max_aff;  // [3 * chunk_cap] SpMV chunk partial products
+    // [12 * slice_cap] this CTA's matrix blocks (S then C), FP32 only, 16-byte aligned
+    float* s_mval = (float*)(((uintptr_t)(s_cpart + 3 * (size_t)a.chunk_cap) + 15) & ~(uintptr_t)15);
+    __shared__ int s_staged;
     Real* zw = a.z;                                 // z, 3 per node, in global memory
     const Real* __restrict__ zg = a.z;
 
@@ -164,8 +228,40 @@ __global__ void __launch_bounds__(kPcgcThreads) k_pcg_cluster(PcgcArgs<Real> a) 
     const int ab0 = G.env_aff_start[e], n_aff = G.env_aff_start[e + 1] - ab0;
     const int ns1 = n_aff ? G.aff_node0[ab0] : nend;  // soft nodes are [nb, ns1), affine nodes [ns1, nend)
     const int n_soft = ns1 - nb, n_arow = nend - ns1;
-    const int lo = nb + (int)(((long long)n_soft * rank) / cs);
-    const int hi = nb + (int)(((long long)n_soft * (rank + 1)) / cs);
+    // soft rows per CTA, balanced by the rows' stored blocks (static and
+    // contact, plus 2 per row for its fixed cost) when no CTA then owns more
+    // than max_rows rows, else an equal split; every CTA finds the same
+    // boundaries (binary searches over the same prefix sums)
+    __shared__ int s_bounds[kPcgcMaxCluster + 1];
+    if (threadIdx.x == 0) {
+        auto cum = [&](int row) -> long long {
+            return (long long)a.S.rowptr[row] + a.C.rowptr[row] + 2ll * row;
+        };
+        const long long c0 = cum(nb), tot = cum(ns1) - c0;
+        bool ok = true;
+        s_bounds[0] = nb;
+        for (int r = 1; r <= cs; ++r) {
+            int b = ns1;
+            if (r < cs) {
+                const long long target = (tot * r) / cs;
+                int l = s_bounds[r - 1], h = ns1;  // first row with cum - c0 >= target
+                while (l < h) {
+                    const int m = (l + h) >> 1;
+                    if (cum(m) - c0 < target)
+                        l = m + 1;
+                    else
+                        h = m;
+                }
+                b = l;
+            }
+            s_bounds[r] = b;
+            ok &= b - s_bounds[r - 1] <= a.max_rows - 1;
+        }
+        if (!ok)
+            for (int r = 0; r <= cs; ++r) s_bounds[r] = nb + (int)(((long long)n_soft * r) / cs);
+    }
+    __syncthreads();
+    const int lo = s_bounds[rank], hi = s_bounds[rank + 1];
     const int n_own = hi - lo;
     const bool aff_owner = rank == cs - 1;
     const int tid = threadIdx.x;
@@ -236,7 +332,89 @@ __global__ void __launch_bounds__(kPcgcThreads) k_pcg_cluster(PcgcArgs<Real> a) 
         }
         s_rng[task] = g;
     }
-    cl.sync();  // also orders s_rng within the CTA
+    // the CTA's matrix slice (fixed during the solve) into shared memory when
+    // it fits: the soft rows' S and C ranges are contiguous, the affine row
+    // shares follow; s_rng then holds offsets into the staged arrays
+    __syncthreads();
+    const int S0 = a.S.rowptr[lo], nS = a.S.rowptr[hi] - S0;
+    const int C0 = a.C.rowptr[lo], nC = a.C.rowptr[hi] - C0;
+    if (tid == 0) {
+        long long tot = (long long)nS + nC;
+        for (int t = n_own; t < n_tasks; ++t) tot += (s_rng[t].y - s_rng[t].x) + (s_rng[t].w - s_rng[t].z);
+        s_staged = tot <= a.slice_cap ? 1 : 0;
+    }
+    __syncthreads();
+    const bool staged = s_staged != 0;
+    if (staged) {
+        // block b of the slice: 12 floats, values at 12 b + 0..8, column at 12 b + 9
+        auto put = [&](const Bsr<Real>& M, int k0, int n, int off) {
+            for (int i = tid; i < 9 * n; i += kPcgcThreads) {
+                const int b = i / 9;
+                s_mval[12 * (size_t)(off + b) + (i - 9 * b)] = (float)M.val[9 * (size_t)k0 + i];
+            }
+            for (int i = tid; i < n; i += kPcgcThreads) {
+                s_mval[12 * (size_t)(off + i) + 9] = __int_as_float(M.col[k0 + i]);
+                s_mval[12 * (size_t)(off + i) + 10] = 0.0f;
+                s_mval[12 * (size_t)(off + i) + 11] = 0.0f;
+            }
+        };
+        put(a.S, S0, nS, 0);
+        put(a.C, C0, nC, nS);
+        // affine shares, in task order after the soft rows' blocks
+        int off = nS + nC;
+        for (int t = n_own; t < n_tasks; ++t) {
+            const int4 g = s_rng[t];
+            const int ls = g.y - g.x, lc = g.w - g.z;
+            put(a.S, g.x, ls, off);
+            put(a.C, g.z, lc, off + ls);
+            off += ls + lc;
+        }
+        __syncthreads();
+        // ranges into the staged arrays (S part, then C part of the same arrays)
+        for (int task = tid; task < n_own; task += kPcgcThreads) {
+            const int row = lo + task;
+            s_rng[task] = make_int4(a.S.rowptr[row] - S0, a.S.rowptr[row + 1] - S0, nS + a.C.rowptr[row] - C0,
+                                    nS + a.C.rowptr[row + 1] - C0);
+        }
+        if (tid == 0) {
+            int o = nS + nC;
+            for (int t = n_own; t < n_tasks; ++t) {
+                const int4 g = s_rng[t];
+                const int ls = g.y - g.x, lc = g.w - g.z;
+                s_rng[t] = make_int4(o, o + ls, o + ls, o + ls + lc);
+                o += ls + lc;
+            }
+        }
+    }
+    const float4* slice4 = reinterpret_cast<const float4*>(s_mval);
+    const float* sp4 = reinterpret_cast<const float*>(s_p);
+    // SpMV work in chunks of at most kPcgcChunk blocks, spread over all lane
+    // groups whatever the row lengths; each row's chunk products are summed
+    // in chunk order afterwards
+    __shared__ int s_nchunks;
+    __syncthreads();
+    if (tid == 0) {
+        int c = 0;
+        for (int t = 0; t < n_tasks; ++t) {
+            const int4 g = s_rng[t];
+            const int len = (g.y - g.x) + (g.w - g.z);
+            s_cpre[t] = c;
+            c += len > 0 ? (len + kPcgcChunk - 1) / kPcgcChunk : 1;
+        }
+        s_cpre[n_tasks] = c;
+        s_nchunks = c;
+    }
+    __syncthreads();
+    const int n_chunks = s_nchunks;
+    const bool chunked = n_chunks <= a.chunk_cap;
+    if (chunked)
+        for (int t = tid; t < n_tasks; t += kPcgcThreads) {
+            const int4 g = s_rng[t];
+            const int len = (g.y - g.x) + (g.w - g.z);
+            for (int c = s_cpre[t], j = 0; c < s_cpre[t + 1]; ++c, j += kPcgcChunk)
+                s_chunk[c] = make_int4(t, j, min(len, j + kPcgcChunk), 0);
+        }
+    cl.sync();  // also orders s_rng, the chunks and the staged slice within the CTA
     cluster_total<2>(cl, s_part + 1, s_tot + 1);  // s_tot[1] = r.z, s_tot[2] = b.b
     Real rz = s_tot[1];
     const Real bb = s_tot[2];
@@ -245,42 +423,94 @@ __global__ void __launch_bounds__(kPcgcThreads) k_pcg_cluster(PcgcArgs<Real> a) 
     bool done = bad || !(bb > Real(0));
     Real beta = 0;
     int it = 0;
-    const int warp = tid >> 5, half = (tid >> 4) & 1, gl = tid & (kPcgcGroup - 1);
+    constexpr int kGroupsPerWarp = 32 / kPcgcGroup;
+    const int warp = tid >> 5, sub = (tid & 31) / kPcgcGroup, gl = tid & (kPcgcGroup - 1);
     const int n_groups = kPcgcThreads / kPcgcGroup;
     while (!done && it < a.max_iter) {
         // ---- p_k = z_k + beta p_{k-1} over the env, in place (every CTA
         // holds the same p); z comes from L2, written there by its owner
-        for (int i0 = tid; i0 < n_env; i0 += kPcgcStageBatch * kPcgcThreads) {
-            Real zv[kPcgcStageBatch][3];
+        // (the env's 3 n_env values as one flat range: kPcgcStageBatch
+        // independent loads per thread, one L2 round trip for small envs)
+        const int n3e = 3 * n_env;
+        const Real* __restrict__ zs = zg + 3 * (size_t)nb;
+        for (int i0 = tid; i0 < n3e; i0 += kPcgcStageBatch * kPcgcThreads) {
+            Real zv[kPcgcStageBatch];
 #pragma unroll
             for (int j = 0; j < kPcgcStageBatch; ++j) {
                 const int i = i0 + j * kPcgcThreads;
-                const Real* src = zg + 3 * (size_t)(nb + (i < n_env ? i : 0));
-#pragma unroll
-                for (int c = 0; c < 3; ++c) zv[j][c] = ldcg_r(src + c);
+                zv[j] = ldcg_r(zs + (i < n3e ? i : 0));
             }
 #pragma unroll
             for (int j = 0; j < kPcgcStageBatch; ++j) {
                 const int i = i0 + j * kPcgcThreads;
-                if (i >= n_env) break;
-#pragma unroll
-                for (int c = 0; c < 3; ++c) s_p[3 * i + c] = it > 0 ? zv[j][c] + beta * s_p[3 * i + c] : zv[j][c];
+                if (i < n3e) s_p[i] = it > 0 ? zv[j] + beta * s_p[i] : zv[j];
             }
         }
         __syncthreads();
         // ---- q = A p: owned soft rows, then this CTA's share of each affine row
         Real pq[1] = {0};
-        // two 16-lane groups per warp; the loop is uniform over the warp so
-        // that every lane takes part in the shuffles
-        for (int t0 = 2 * warp; t0 < n_tasks; t0 += n_groups) {
-            const int task = t0 + half;
+        // kGroupsPerWarp groups of kPcgcGroup lanes per warp; the loops are
+        // uniform over the warp so that every lane takes part in the shuffles
+        if (chunked) {
+            for (int c0 = kGroupsPerWarp * warp; c0 < n_chunks; c0 += n_groups) {
+                const int ci = c0 + sub;
+                const bool valid = ci < n_chunks;
+                Real y0 = 0, y1 = 0, y2 = 0;
+                if (valid) {
+                    const int4 ch = s_chunk[ci];
+                    const int4 g = s_rng[ch.x];
+                    if constexpr (sizeof(Real) == sizeof(float)) {
+                        if (staged)
+                            row_part4(slice4, g, ch.y, ch.z, sp4, nb, n_env, gl, y0, y1, y2);
+                        else
+                            row_part(a.S, a.C, g, ch.y, ch.z, s_p, nb, n_env, gl, y0, y1, y2);
+                    } else {
+                        row_part(a.S, a.C, g, ch.y, ch.z, s_p, nb, n_env, gl, y0, y1, y2);
+                    }
+                }
+                y0 = group_sum(y0);
+                y1 = group_sum(y1);
+                y2 = group_sum(y2);
+                if (valid && gl == 0) {
+                    s_cpart[3 * ci] = y0;
+                    s_cpart[3 * ci + 1] = y1;
+                    s_cpart[3 * ci + 2] = y2;
+                }
+            }
+            __syncthreads();
+            for (int t = tid; t < n_tasks; t += kPcgcThreads) {
+                Real y0 = 0, y1 = 0, y2 = 0;
+                for (int c = s_cpre[t]; c < s_cpre[t + 1]; ++c) {
+                    y0 += s_cpart[3 * c];
+                    y1 += s_cpart[3 * c + 1];
+                    y2 += s_cpart[3 * c + 2];
+                }
+                const int row = t < n_own ? lo + t : ns1 + (t - n_own);
+                Real* qd = t < n_own ? s_q + 3 * t : s_qa + 3 * (t - n_own);
+                qd[0] = y0;
+                qd[1] = y1;
+                qd[2] = y2;
+                const Real* pr = s_p + PS * (row - nb);
+                pq[0] += pr[0] * y0 + pr[1] * y1 + pr[2] * y2;
+            }
+        } else
+        for (int t0 = kGroupsPerWarp * warp; t0 < n_tasks; t0 += n_groups) {
+            const int task = t0 + sub;
             const bool valid = task < n_tasks;
             Real y0 = 0, y1 = 0, y2 = 0;
             int row = 0;
             if (valid) {
                 int4 g = s_rng[task];
                 row = task < n_own ? lo + task : ns1 + (task - n_own);
-                row_part(a.S, a.C, g, s_p, nb, n_env, gl, y0, y1, y2);
+                const int len = (g.y - g.x) + (g.w - g.z);
+                if constexpr (sizeof(Real) == sizeof(float)) {
+                    if (staged)
+                        row_part4(slice4, g, 0, len, sp4, nb, n_env, gl, y0, y1, y2);
+                    else
+                        row_part(a.S, a.C, g, 0, len, s_p, nb, n_env, gl, y0, y1, y2);
+                } else {
+                    row_part(a.S, a.C, g, 0, len, s_p, nb, n_env, gl, y0, y1, y2);
+                }
             }
             y0 = group_sum(y0);
             y1 = group_sum(y1);
@@ -290,7 +520,7 @@ __global__ void __launch_bounds__(kPcgcThreads) k_pcg_cluster(PcgcArgs<Real> a) 
                 qd[0] = y0;
                 qd[1] = y1;
                 qd[2] = y2;
-                const Real* pr = s_p + 3 * (row - nb);
+                const Real* pr = s_p + PS * (row - nb);
                 pq[0] += pr[0] * y0 + pr[1] * y1 + pr[2] * y2;
             }
         }
@@ -309,7 +539,7 @@ __global__ void __launch_bounds__(kPcgcThreads) k_pcg_cluster(PcgcArgs<Real> a) 
         for (int j = 0; j < kPcgcOwn; ++j) {
             const int i = tid + j * kPcgcThreads;
             if (i >= n_own) continue;
-            const Real* pr = s_p + 3 * (lo + i - nb);
+            const Real* pr = s_p + PS * (lo + i - nb);
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 xs[j][c] += alpha * pr[c];
@@ -332,7 +562,7 @@ __global__ void __launch_bounds__(kPcgcThreads) k_pcg_cluster(PcgcArgs<Real> a) 
             Real q = 0;
 #pragma unroll
             for (int rk = 0; rk < kPcgcMaxCluster; ++rk) q += qv[rk];
-            xa += alpha * s_p[3 * (ns1 - nb) + tid];
+            xa += alpha * s_p[PS * (ns1 - nb + tid / 3) + tid % 3];
             ra -= alpha * q;
             s_ra[tid] = ra;
         }

@@ -99,6 +99,8 @@ struct zema_scene {
     bool pcgc_tune[2] = {false, false};  // autotune the cluster size at the next solve
     std::vector<std::pair<int, float>> pcgc_tuned[2];  // (cluster size, solve ms) measured by the autotuner
     int pcgc_max_env_nodes = 0, pcgc_max_soft = 0, pcgc_max_aff = 0;
+    std::vector<int> S_rowptr_h;  // host copy of the static pattern's row pointers
+    std::map<std::pair<int, int>, int> pcgc_cap;  // (value size, CTAs per env) -> staged slice capacity
     DBuf<double> tolv;
     // pair lists
     BroadPhase bp;
@@ -580,6 +582,7 @@ void build(zema_scene* s) {
     up(s, s->node_tet_ptr, ntp);
     up(s, s->node_tet_idx, nti);
     up(s, s->S_rowptr, S_rowptr_h);
+    s->S_rowptr_h = S_rowptr_h;
     up(s, s->S_col, S_col_h);
     up(s, s->S_src_ptr, S_src_ptr_h);
     up(s, s->S_src, S_src_h);
@@ -1095,14 +1098,67 @@ void grad_hess(zema_scene* s, bool barrier = true, bool friction = true, bool he
 // ---------------------------------------------------------------------------
 constexpr size_t kPcgcMaxSmem = 200 * 1024;
 
-int pcgc_max_rows(const zema_scene* s, int cs) { return (s->pcgc_max_soft + cs - 1) / cs + 1; }
+// rows a CTA may own (the solve balances rows by their blocks within this
+// bound): twice the equal share, at most what its threads hold in registers
+int pcgc_max_rows(const zema_scene* s, int cs) {
+    return std::min(2 * ((s->pcgc_max_soft + cs - 1) / cs) + 1, kPcgcOwn * kPcgcThreads + 1);
+}
+
+// SpMV chunks a CTA can hold (0: one task per row; chunking measured slower
+// on the grasp workloads, so it is off)
+int pcgc_chunk_cap(const zema_scene*, int) { return 0; }
+
+template <class T>
+size_t pcgc_smem_base(const zema_scene* s, int cs) {
+    const size_t tasks = (size_t)pcgc_max_rows(s, cs) + 4 * (size_t)s->pcgc_max_aff, ch = pcgc_chunk_cap(s, cs);
+    return (tasks + ch) * sizeof(int4) + ((tasks + 4) & ~(size_t)3) * sizeof(int) +
+           (3 * (kPcgcThreads / 32) + 8 + pcgc_pstride<T>() * (size_t)s->pcgc_max_env_nodes +
+            3 * (size_t)pcgc_max_rows(s, cs) + 24 * (size_t)s->pcgc_max_aff + 3 * ch) *
+               sizeof(T) +
+           16;  // alignment of the staged slice
+}
+
+// Blocks of a CTA's matrix slice that the solve may stage in shared memory:
+// all the space left under the budget, when that holds the largest static
+// slice (soft rows' S blocks and the CTA's share of the affine rows') with
+// room for contact blocks; 0 (the solve reads the matrix from L1/L2) if not.
+template <class T>
+int pcgc_slice_cap(const zema_scene* cs_scene, int cs) {
+    zema_scene* s = const_cast<zema_scene*>(cs_scene);
+    const auto key = std::make_pair((int)sizeof(T), cs);
+    auto hit = s->pcgc_cap.find(key);
+    if (hit != s->pcgc_cap.end()) return hit->second;
+    if (sizeof(T) != sizeof(float)) {  // the slice is staged in FP32 solves only
+        s->pcgc_cap[key] = 0;
+        return 0;
+    }
+    const std::vector<int>& rp = s->S_rowptr_h;
+    long long mx = 0;
+    for (int e = 0; e < s->n_envs; ++e) {
+        const int nb = s->env_node_start_h[e], nend = s->env_node_start_h[e + 1];
+        const int ns1 = nend - 4 * (s->env_aff_start_h[e + 1] - s->env_aff_start_h[e]);
+        const int n_soft = ns1 - nb;
+        for (int r = 0; r < cs; ++r) {
+            const int lo = nb + (int)(((long long)n_soft * r) / cs), hi = nb + (int)(((long long)n_soft * (r + 1)) / cs);
+            long long c = rp[hi] - rp[lo];
+            for (int n = ns1; n < nend; ++n) {
+                const long long len = rp[n + 1] - rp[n];
+                c += (len * (r + 1)) / cs - (len * r) / cs;
+            }
+            mx = std::max(mx, c);
+        }
+    }
+    const size_t per = 12 * sizeof(float);  // a block: 9 values, its column, 2 pad
+    const size_t base = pcgc_smem_base<T>(s, cs);
+    const long long avail = base >= kPcgcMaxSmem ? 0 : (long long)((kPcgcMaxSmem - base) / per);
+    const int cap = avail >= mx + mx / 4 + 128 ? (int)avail : 0;
+    s->pcgc_cap[key] = cap;
+    return cap;
+}
 
 template <class T>
 size_t pcgc_smem(const zema_scene* s, int cs) {
-    return ((size_t)pcgc_max_rows(s, cs) + 4 * (size_t)s->pcgc_max_aff) * sizeof(int4) +
-           (3 * (kPcgcThreads / 32) + 8 + 3 * (size_t)s->pcgc_max_env_nodes + 3 * (size_t)pcgc_max_rows(s, cs) +
-            24 * (size_t)s->pcgc_max_aff) *
-               sizeof(T);
+    return pcgc_smem_base<T>(s, cs) + (size_t)pcgc_slice_cap<T>(s, cs) * 12 * sizeof(float);
 }
 
 template <class T>
@@ -1125,7 +1181,7 @@ int pcgc_choose(zema_scene* s) {
     int want = std::min(16, std::max(1, (s->pcgc_max_env_nodes + 127) / 128));
     // the env's vector must fit in shared memory, a CTA's rows in its
     // threads' registers, the affine rows in one CTA
-    if (pcgc_smem<T>(s, 16) > kPcgcMaxSmem || 12 * s->pcgc_max_aff > kPcgcThreads) return -1;
+    if (pcgc_smem_base<T>(s, 16) > kPcgcMaxSmem || 12 * s->pcgc_max_aff > kPcgcThreads) return -1;
     ZCHECK(cudaFuncSetAttribute(k_pcg_cluster<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPcgcMaxSmem));
     if (want > 8) {
         if (cudaFuncSetAttribute(k_pcg_cluster<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
@@ -1142,7 +1198,7 @@ int pcgc_choose(zema_scene* s) {
         return -1;
     }
     int cs = std::min(want, maxcs);
-    if (pcgc_max_rows(s, cs) > kPcgcOwn * kPcgcThreads || pcgc_smem<T>(s, cs) > kPcgcMaxSmem) return -1;
+    if ((s->pcgc_max_soft + cs - 1) / cs > kPcgcOwn * kPcgcThreads || pcgc_smem<T>(s, cs) > kPcgcMaxSmem) return -1;
     pcgc_config<T>(s, cs, cfg, at);
     // the rest of the SM's shared/L1 storage stays L1 for the matrix rows
     int dev = 0, smem_sm = 0;
@@ -1161,7 +1217,8 @@ int pcgc_choose(zema_scene* s) {
 // whether cluster size cs can run the cluster solve of this scene
 template <class T>
 bool pcgc_valid(zema_scene* s, int cs) {
-    if (cs < 1 || cs > 16 || pcgc_max_rows(s, cs) > kPcgcOwn * kPcgcThreads || pcgc_smem<T>(s, cs) > kPcgcMaxSmem)
+    if (cs < 1 || cs > 16 || (s->pcgc_max_soft + cs - 1) / cs > kPcgcOwn * kPcgcThreads ||
+        pcgc_smem<T>(s, cs) > kPcgcMaxSmem)
         return false;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute at[1];
@@ -1231,6 +1288,8 @@ int64_t pcg_t(zema_scene* s, const std::vector<int>& done_h) {
             c.max_env_nodes = s->pcgc_max_env_nodes;
             c.max_rows = pcgc_max_rows(s, cs);
             c.max_aff = s->pcgc_max_aff;
+            c.slice_cap = pcgc_slice_cap<T>(s, cs);
+            c.chunk_cap = pcgc_chunk_cap(s, cs);
             cudaLaunchConfig_t cfg = {};
             cudaLaunchAttribute at[1];
             pcgc_config<T>(s, cs, cfg, at);
