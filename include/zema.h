@@ -321,6 +321,12 @@ zema_status zema_mlp_n_params(const zema_mlp* m, int64_t* n);
 /* copies the FP32 parameters to / from host memory (cap / n = n_params) */
 zema_status zema_mlp_get_params(const zema_mlp* m, float* host_out, int64_t cap);
 zema_status zema_mlp_set_params(zema_mlp* m, const float* host_in, int64_t n);
+/* Tensor-core path of the forward products: 0 (default) the fifth-generation
+ * tensor cores (tcgen05.mma, accumulators in tensor memory) for layers with
+ * dims[l] <= 128 and dims[l+1] <= 256, 1 the warp-level mma.sync kernel.
+ * Backward products always use the warp-level kernel.  A tcgen05 product
+ * whose completion wait times out makes the call return ZEMA_ERR_CUDA. */
+zema_status zema_mlp_set_kernel(zema_mlp* m, int32_t kind);
 /* y = net(x) */
 zema_status zema_mlp_forward(zema_mlp* m, const float* x, int64_t n, float* y);
 /* mean squared error of net(x) against t (mean over all n x dims[L]

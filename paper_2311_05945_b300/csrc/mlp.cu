@@ -4,6 +4,7 @@
 #include <string>
 
 #include "mlp.cuh"
+#include "mlp_tc.cuh"
 
 namespace zema {
 
@@ -122,6 +123,14 @@ __global__ void k_f32_to_bf16(const float* a, bf16* b, size_t n) {
     if (i < n) b[i] = __float2bfloat16(a[i]);
 }
 
+// W (k x n, row-major) -> W^T (n x k, row-major) in BF16
+__global__ void k_transpose_bf16(const float* w, int k, int n, bf16* wt) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= k * n) return;
+    const int r = i / n, c = i - r * n;
+    wt[(size_t)c * k + r] = __float2bfloat16(w[i]);
+}
+
 __global__ void k_fill_bf16(bf16* b, size_t n, float v) {
     size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) b[i] = __float2bfloat16(v);
@@ -185,6 +194,28 @@ int gemm(cudaStream_t st, int M, int N, int K, const bf16* A, int lda, const bf1
     return splits;
 }
 
+// forward product on tcgen05 (K <= 128, N <= 256): persistent CTAs, two per SM
+template <int EPI>
+void gemm_tc(cudaStream_t st, int M, int N, int K, const bf16* X, int ldx, const bf16* Wt, int ldwt, GemmOut o,
+             int* err) {
+    if (M <= 0 || N <= 0) return;
+    const int kp = (K + 15) & ~15, np = (N + 15) & ~15;
+    const size_t smem = (size_t)(kTcM + np) * kp * 2;
+    static int nsm = 0;
+    if (!nsm) {
+        int dev = 0;
+        ZCHECK(cudaGetDevice(&dev));
+        ZCHECK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        ZCHECK(cudaFuncSetAttribute(k_gemm_tc<kEpiHidden>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+        ZCHECK(cudaFuncSetAttribute(k_gemm_tc<kEpiOut>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+    }
+    const int grid = std::min(div_up(M, kTcM), 2 * nsm);
+    ZL(k_gemm_tc<EPI>, grid, kTcThreads, smem, st)(M, N, K, X, ldx, Wt, ldwt, o, err);
+    ZLAUNCH();
+}
+
+bool tc_fits(int K, int N) { return K <= 128 && N <= 256; }
+
 // splits of a K-reduction of length K so that a 1 x 2 (or 2 x 2) tile grid
 // still fills the GPU
 int splits_for(int64_t K) { return (int)std::min<int64_t>(256, std::max<int64_t>(1, K / 512)); }
@@ -207,6 +238,9 @@ Mlp::Mlp(const std::vector<int>& d, uint64_t seed, cudaStream_t s) : dims(d), st
     m.ensure(&A, n_params);
     v.ensure(&A, n_params);
     theta_bf.ensure(&A, n_params);
+    theta_t.ensure(&A, n_params);
+    tc_err.ensure(&A, 1);
+    ZCHECK(cudaMemsetAsync(tc_err.p, 0, sizeof(int), st));
     // He-uniform weights from SplitMix64 (last layer scaled by 0.1), zero biases
     std::vector<float> init(n_params, 0.0f);
     uint64_t rs = seed;
@@ -235,6 +269,15 @@ Mlp::~Mlp() {
 
 void Mlp::refresh_bf16() {
     ZL(k_f32_to_bf16, div_up(n_params, 256), 256, 0, st)(theta.p, theta_bf.p, n_params);
+    refresh_t();
+    ZLAUNCH();
+}
+
+// the transposed BF16 weights read by the tcgen05 products
+void Mlp::refresh_t() {
+    for (int l = 0; l < layers(); ++l)
+        ZL(k_transpose_bf16, div_up(dims[l] * dims[l + 1], 256), 256, 0, st)(theta.p + w_off[l], dims[l], dims[l + 1],
+                                                                              theta_t.p + w_off[l]);
     ZLAUNCH();
 }
 
@@ -272,14 +315,21 @@ void Mlp::forward(const float* x, int64_t n, float* y_out) {
         o.bias = theta.p + b_off[l];
         o.ld = N;
         const bf16* W = theta_bf.p + w_off[l];
+        const bool tc = use_tc && tc_fits(K, N);
         if (l + 1 < L) {
             o.f = z[l]->p;
             o.h = h[l]->p;
-            gemm<false, false, kEpiHidden>(st, (int)n, N, K, in, K, W, N, o);
+            if (tc)
+                gemm_tc<kEpiHidden>(st, (int)n, N, K, in, K, theta_t.p + w_off[l], K, o, tc_err.p);
+            else
+                gemm<false, false, kEpiHidden>(st, (int)n, N, K, in, K, W, N, o);
             in = h[l]->p;
         } else {
             o.f = y_out ? y_out : y.p;
-            gemm<false, false, kEpiOut>(st, (int)n, N, K, in, K, W, N, o);
+            if (tc)
+                gemm_tc<kEpiOut>(st, (int)n, N, K, in, K, theta_t.p + w_off[l], K, o, tc_err.p);
+            else
+                gemm<false, false, kEpiOut>(st, (int)n, N, K, in, K, W, N, o);
         }
     }
 }
@@ -332,6 +382,7 @@ void Mlp::adamw(float lr, float b1, float b2, float eps, float wd) {
     ZL(k_adamw, div_up(n_params, 256), 256, 0, st)(theta.p, grad.p, m.p, v.p, n_params, lr, b1, b2, eps, wd, c1, c2,
                                                   theta_bf.p);
     ZLAUNCH();
+    if (use_tc) refresh_t();
 }
 
 }  // namespace zema
@@ -400,12 +451,30 @@ extern "C" zema_status zema_mlp_set_params(zema_mlp* m, const float* in, int64_t
     }
 }
 
+static void check_tc(zema::Mlp* net) {
+    int e = 0;
+    ZCHECK(cudaMemcpyAsync(&e, net->tc_err.p, sizeof(int), cudaMemcpyDeviceToHost, net->st));
+    ZCHECK(cudaStreamSynchronize(net->st));
+    if (e) throw ZemaError{ZEMA_ERR_CUDA, "tensor-core product did not complete"};
+}
+
+extern "C" zema_status zema_mlp_set_kernel(zema_mlp* m, int32_t kind) {
+    if (!m || kind < 0 || kind > 1) return ZEMA_ERR_INVALID_ARG;
+    try {
+        m->net->use_tc = kind == 0 ? 1 : 0;
+        if (m->net->use_tc) m->net->refresh_t();
+        return ZEMA_OK;
+    } catch (const ZemaError& e) {
+        return mlp_status(e);
+    }
+}
+
 extern "C" zema_status zema_mlp_forward(zema_mlp* m, const float* x, int64_t n, float* y) {
     if (!m || n < 0 || (n && (!x || !y))) return ZEMA_ERR_INVALID_ARG;
     if (n == 0) return ZEMA_OK;
     try {
         m->net->forward(x, n, y);
-        ZCHECK(cudaStreamSynchronize(m->net->st));
+        check_tc(m->net);
         return ZEMA_OK;
     } catch (const ZemaError& e) {
         return mlp_status(e);
@@ -417,6 +486,7 @@ extern "C" zema_status zema_mlp_gradient(zema_mlp* m, const float* x, const floa
     if (!m || !x || !t || n < 1 || !grad || cap < (int64_t)m->net->n_params) return ZEMA_ERR_INVALID_ARG;
     try {
         double l = m->net->backward(x, t, n);
+        check_tc(m->net);
         ZCHECK(cudaMemcpyAsync(grad, m->net->grad.p, m->net->n_params * sizeof(float), cudaMemcpyDeviceToHost,
                                m->net->st));
         ZCHECK(cudaStreamSynchronize(m->net->st));
@@ -433,6 +503,7 @@ extern "C" zema_status zema_mlp_train_step(zema_mlp* m, const float* x, const fl
         return ZEMA_ERR_INVALID_ARG;
     try {
         double l = m->net->backward(x, t, n);
+        check_tc(m->net);
         m->net->adamw(lr, beta1, beta2, eps, weight_decay);
         if (loss) *loss = l;
         return ZEMA_OK;

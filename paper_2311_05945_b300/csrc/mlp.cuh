@@ -42,7 +42,7 @@ struct Mlp {
     cudaStream_t st = nullptr;
     Allocator A;
     DBuf<float> theta, grad, m, v, part;  // master weights, gradient, AdamW moments, split partials
-    DBuf<bf16> theta_bf, ones;
+    DBuf<bf16> theta_bf, theta_t, ones;  // BF16 weights; theta_t: each W_l transposed (out x in)
     // activations (for n rows): per hidden layer pre-activation (f32) and
     // activation (bf16), the input and output, two gradient buffers
     std::vector<DBuf<float>*> z;
@@ -51,12 +51,15 @@ struct Mlp {
     DBuf<float> y, loss_part;
     int64_t cap_rows = 0;
     int64_t step = 0;
+    int use_tc = 1;          // forward products on tcgen05 (0: warp-level mma.sync)
+    DBuf<int> tc_err;        // set by a tcgen05 product whose completion wait timed out
 
     Mlp(const std::vector<int>& d, uint64_t seed, cudaStream_t s);
     ~Mlp();
     int layers() const { return (int)dims.size() - 1; }
     void ensure_rows(int64_t n);
     void refresh_bf16();
+    void refresh_t();
     // y (n x out, f32, device) = net(x) for x (n x in, f32, device)
     void forward(const float* x, int64_t n, float* y_out);
     // MSE loss of net(x) against t, gradient into `grad`; returns the loss

@@ -118,6 +118,7 @@ def lib():
     L.zema_mlp_get_params.argtypes = [C.c_void_p, FP, C.c_int64]
     L.zema_mlp_set_params.argtypes = [C.c_void_p, FP, C.c_int64]
     L.zema_mlp_forward.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]
+    L.zema_mlp_set_kernel.argtypes = [C.c_void_p, C.c_int32]
     L.zema_mlp_gradient.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, FP, C.c_int64, DP]
     L.zema_mlp_train_step.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_float, C.c_float,
                                       C.c_float, C.c_float, C.c_float, DP]
@@ -501,6 +502,10 @@ class Mlp:
             self.close()
         except Exception:
             pass
+
+    def set_kernel(self, kind: int):
+        """0: tcgen05 forward products (default), 1: warp-level mma.sync."""
+        _check(lib().zema_mlp_set_kernel(self.h, kind))
 
     def get_params(self) -> np.ndarray:
         out = np.zeros(self.n_params, dtype=np.float32)

@@ -68,3 +68,18 @@ def test_training_reduces_loss_and_is_reproducible():
     (f0, l0, p0), (f1, l1, p1) = runs
     assert l0 < 0.2 * f0, (f0, l0)
     assert np.array_equal(p0, p1)
+
+
+@pytest.mark.parametrize("n", [1, 200, 5000])
+def test_tcgen05_forward_matches_warp_mma(n):
+    # the fifth-generation tensor-core forward (accumulators in tensor memory)
+    # against the warp-level mma.sync kernel on the same BF16 operands
+    from paper_2311_05945_b300.zema import Mlp
+    net = Mlp(DIMS, seed=4)
+    x, t, xd, td = data(n, 3)
+    y_tc = net.forward(xd).cpu().numpy()
+    net.set_kernel(1)
+    y_mma = net.forward(xd).cpu().numpy()
+    assert np.abs(y_tc - y_mma).max() <= 2e-3 * max(1e-6, np.abs(y_mma).max())
+    yb, _ = mlp_ref.forward(net.get_params(), DIMS, x, bf16=True)
+    assert np.abs(y_tc - yb).max() <= 2e-3 * max(1e-6, np.abs(yb).max())
