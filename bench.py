@@ -34,9 +34,10 @@ UNIT = "steps/s"
 WORKLOAD = "parallel-jaw grasp, 1 env: soft ellipsoid 9600 tets + 2 kinematic affine fingers (972 tris each) + fixed floor"
 ROOFLINE_KERNEL = "k_pcg_cluster"
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
-# ROOFLINE_KERNEL from an ncu capture of the first solve of grasp step 20
-# (a launch of the bench's average length); None once the kernel changes.
-ROOFLINE_TRAFFIC = None
+# ROOFLINE_KERNEL per workload, from an ncu capture: c2, the first solve of
+# grasp step 20 (751.9 us, near the bench's 705 us average launch); None where
+# no capture was taken or once the kernel changes.
+ROOFLINE_TRAFFIC = {"c2": 1384448 + 8448, "c3": None}
 
 
 def measured_peaks():
@@ -250,7 +251,7 @@ def run_ours(args, rank, world):
         per_launch_bytes = k_bytes / k_launches
         achieved = per_launch_bytes / (k_ms / k_launches / 1e3) / 1e9
         roof = {"kernel": ROOFLINE_KERNEL, "bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
-                "frac": achieved / peak_gbs, "traffic": ROOFLINE_TRAFFIC,
+                "frac": achieved / peak_gbs, "traffic": ROOFLINE_TRAFFIC.get(args.workload),
                 "peak_source": "measured" if peaks else "fallback",
                 "alg_bytes_per_launch": per_launch_bytes, "avg_launch_us": 1e3 * k_ms / k_launches,
                 "launches": k_launches, "share_of_step_time": k_ms / total_ms if world == 1 else None}
