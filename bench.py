@@ -12,6 +12,11 @@ ACCD line search, velocity update).  Timed steps are steps [W, W + K) of the
 grasp script after W warm-up steps.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                [--workload c2|c3|c5]
+
+--workload c3 times the batched grasp (env-steps/s); --workload c5 the dense
+soft-rigid pile (8 soft bodies of ~60k tets, 20 affine spheres and tori, a
+fixed bin), one scene too large for a cluster solve.
 
 One JSON line on rank 0.  Under torchrun each rank steps its own replica of
 the workload (environments are independent: weak scaling, no collective in
@@ -33,11 +38,13 @@ METRIC = "IPC time steps/sec at fixed Newton tol, batched+warm-start vs plain, o
 UNIT = "steps/s"
 WORKLOAD = "parallel-jaw grasp, 1 env: soft ellipsoid 9600 tets + 2 kinematic affine fingers (972 tris each) + fixed floor"
 ROOFLINE_KERNEL = "k_pcg_cluster"
+# the grid-wide solve of the scenes too large for one cluster
+ROOFLINE_KERNEL_BY_WORKLOAD = {"c2": "k_pcg_cluster", "c3": "k_pcg_cluster", "c5": "k_pcg_persistent"}
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
 # ROOFLINE_KERNEL per workload, from an ncu capture: c2, the first solve of
 # grasp step 20 (751.9 us, near the bench's 705 us average launch); None where
 # no capture was taken or once the kernel changes.
-ROOFLINE_TRAFFIC = {"c2": 1384448 + 8448, "c3": None}
+ROOFLINE_TRAFFIC = {"c2": 1384448 + 8448, "c3": None, "c5": None}
 
 
 def measured_peaks():
@@ -105,6 +112,9 @@ def build_scene(args=None, rank=0, world=1):
     from paper_2311_05945_b300 import scenes
     if args is None or args.workload == "c2":
         return scenes.scene_c2()
+    if args.workload == "c5":
+        # one scene: every rank steps its own replica
+        return scenes.scene_c5(n_steps=args.warmup + args.steps, tets_per_body=args.c5_tets)
     from paper_2311_05945_b300.sharding import shard_envs
     full = scenes.scene_c3(n_envs=args.envs, n_steps=args.warmup + args.steps)
     w = [0] * args.envs
@@ -208,7 +218,8 @@ def run_ours(args, rank, world):
     # headline: mixed precision + warm start; clocks sampled while it runs
     clocks = Clocks(local)
     clocks.start()
-    sc, gpu, total_ms, stats, launches, prof = time_form(args, world, dist, 1, ROOFLINE_KERNEL)
+    sc, gpu, total_ms, stats, launches, prof = time_form(args, world, dist, 1,
+                                                         ROOFLINE_KERNEL_BY_WORKLOAD[args.workload])
     clk = clocks.stop()
     from paper_2311_05945_b300.sharding import max_over_ranks
     envs_per_rank = sc.n_envs
@@ -250,7 +261,7 @@ def run_ours(args, rank, world):
     if k_launches:
         per_launch_bytes = k_bytes / k_launches
         achieved = per_launch_bytes / (k_ms / k_launches / 1e3) / 1e9
-        roof = {"kernel": ROOFLINE_KERNEL, "bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
+        roof = {"kernel": ROOFLINE_KERNEL_BY_WORKLOAD[args.workload], "bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
                 "frac": achieved / peak_gbs, "traffic": ROOFLINE_TRAFFIC.get(args.workload),
                 "peak_source": "measured" if peaks else "fallback",
                 "alg_bytes_per_launch": per_launch_bytes, "avg_launch_us": 1e3 * k_ms / k_launches,
@@ -258,7 +269,16 @@ def run_ours(args, rank, world):
     unit = "env-steps/s" if args.workload == "c3" else UNIT
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        if args.workload == "c3":
+        if args.workload == "c5":
+            # the oracle's brute-force pair search is quadratic in the surface
+            # size: one step of the full pile does not fit the sample bound,
+            # so the sample is the same pile generator at 300 tets per body
+            from paper_2311_05945_b300 import scenes
+            small = scenes.scene_c5(n_steps=2, tets_per_body=300, n_seg=8, bin_subdiv=1)
+            v, dt = oracle_steps_per_s(0, 1, small)
+            sample = (f"step 0 of the same pile generator at 300 tets per body, 8 x 8 affine meshes, unsplit bin "
+                      f"faces, on the CPU oracle ({dt:.1f} s)")
+        elif args.workload == "c3":
             from paper_2311_05945_b300 import scenes
             v, dt = oracle_steps_per_s(0, 1, scenes.scene_c3(n_envs=1, n_steps=2))
             sample = f"env 0 of the batch (seed 1000), step 0, on the CPU oracle ({dt:.1f} s)"
@@ -273,17 +293,21 @@ def run_ours(args, rank, world):
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "mixed f32/f64", "data": "synthetic (seeded generators)",
         "config": {"workload": WORKLOAD if args.workload == "c2" else
-                   f"batched parallel-jaw grasp, {args.envs} envs (ellipsoid/torus/box, 2k-20k tets log-uniform, "
-                   f"E 1e4-1e6, mu 0.3-1.0), one launch per phase over all envs; {envs_per_rank} envs per rank",
+                   (f"dense soft-rigid pile: {sum(len(b.tets) for b in sc.tets)} tets in {len(sc.tets)} soft bodies "
+                    f"+ {sum(1 for a in sc.affines if a.mode == 0)} affine spheres/tori "
+                    f"({max(len(a.F) for a in sc.affines)} tris max) in a fixed 5-box bin, one scene"
+                    if args.workload == "c5" else
+                    f"batched parallel-jaw grasp, {args.envs} envs (ellipsoid/torus/box, 2k-20k tets log-uniform, "
+                    f"E 1e4-1e6, mu 0.3-1.0), one launch per phase over all envs; {envs_per_rank} envs per rank"),
                    "timed_steps": [args.warmup, args.warmup + args.steps],
                    "form": "mixed precision (FP32 Hessians, matrices and PCG with FP64 residual refinement; FP64 "
                            "gradients/energies/distances/CCD/convergence) + CCD-filtered constant-velocity warm "
-                           "start" + ("; 1 env so no batching" if args.workload == "c2" else "; all envs batched"),
+                           "start" + ("; all envs batched" if args.workload == "c3" else "; 1 env so no batching"),
                    "plain_fp64": {"value": plain_value, "ms_per_step": plain_ms / args.steps,
                                   "newton_iters": sum(s["newton_iters"] for s in plain_stats),
                                   "pcg_iters": sum(s["pcg_iters"] for s in plain_stats)},
                    "speedup_vs_plain": value / plain_value,
-                   "parallelism": (f"replicas x{world}" if args.workload == "c2" else f"envs sharded over {world} ranks")
+                   "parallelism": (f"envs sharded over {world} ranks" if args.workload == "c3" else f"replicas x{world}")
                    if world > 1 else "single GPU",
                    "l2": "flushed between timed steps (512 MB write)",
                    "newton_iters": agg["newton_iters"], "pcg_iters": agg["pcg_iters"],
@@ -310,8 +334,10 @@ def main():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3"],
-                    help="c2: the single-env grasp (headline); c3: the batched grasp, env-steps/s")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c5"],
+                    help="c2: the single-env grasp (headline); c3: the batched grasp, env-steps/s; "
+                         "c5: the dense soft-rigid pile")
+    ap.add_argument("--c5-tets", type=int, default=60000, help="tets per soft body of the pile (c5)")
     ap.add_argument("--envs", type=int, default=256, help="envs of the batched grasp (c3)")
     ap.add_argument("--e2e-steps", type=int, default=None,
                     help="end-to-end steps (default: the timed steps, same window)")

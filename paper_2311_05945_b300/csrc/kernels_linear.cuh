@@ -303,70 +303,30 @@ __global__ void k_precond(Geo G, Bsr<T> S, Bsr<T> C, T* Minv_s, T* Minv_a) {
 // and every block recombines them in the same order, so all blocks see the
 // same alpha / beta and results are bit-reproducible.
 // ---------------------------------------------------------------------------
-struct PcgVec {
-    double *x, *r, *z, *p, *q;
-};
-
-__device__ __forceinline__ double sum_chunks(const double* part, int env) {
-    double s = 0.0;
-    for (int c = 0; c < kChunks; ++c) s += part[(size_t)env * kChunks + c];
-    return s;
-}
-
-template <class T>
-__device__ __forceinline__ V3 spmv_row_warp(const Bsr<T>& A, int row, const double* p, int lane) {
-    V3 y = v3(0, 0, 0);
-    for (int k = A.rowptr[row] + lane; k < A.rowptr[row + 1]; k += 32) {
-        const T* v = A.val + 9 * (size_t)k;
-        V3 pc = ld3(p + 3 * (size_t)A.col[k]);
-        y.x += (double)v[0] * pc.x + (double)v[1] * pc.y + (double)v[2] * pc.z;
-        y.y += (double)v[3] * pc.x + (double)v[4] * pc.y + (double)v[5] * pc.z;
-        y.z += (double)v[6] * pc.x + (double)v[7] * pc.y + (double)v[8] * pc.z;
-    }
-    return y;
-}
-
-// apply the preconditioner of a unit to r, write z; returns (r.z, r.r)
-template <class T>
-__device__ __forceinline__ void unit_precond(const Geo& G, int u, const T* Minv_s, const T* Minv_a,
-                                             const double* r, double* z, double& rz, double& rr) {
-    int kind = G.unit_kind[u], idx = G.unit_idx[u];
-    rz = 0.0;
-    rr = 0.0;
-    if (kind == 0) {
-        V3 rv = ld3(r + 3 * (size_t)idx);
-        const T* M = Minv_s + 9 * (size_t)idx;
-        double m[9];
-        for (int q = 0; q < 9; ++q) m[q] = (double)M[q];
-        V3 zv = v3(m[0] * rv.x + m[1] * rv.y + m[2] * rv.z, m[3] * rv.x + m[4] * rv.y + m[5] * rv.z,
-                   m[6] * rv.x + m[7] * rv.y + m[8] * rv.z);
-        st3(z + 3 * (size_t)idx, zv);
-        rz = dot(rv, zv);
-        rr = dot(rv, rv);
-        return;
-    }
-    int n0 = G.aff_node0[idx];
-    const T* M = Minv_a + 144 * (size_t)idx;
-    const double* rb = r + 3 * (size_t)n0;
-    for (int i = 0; i < 12; ++i) {
-        double s = 0.0;
-        for (int j = 0; j < 12; ++j) s += (double)M[12 * i + j] * rb[j];
-        z[3 * (size_t)n0 + i] = s;
-        rz += rb[i] * s;
-        rr += rb[i] * rb[i];
-    }
-}
-
 // ---------------------------------------------------------------------------
-// Persistent PCG: one cooperative launch runs the whole solve.  Work is cut
-// into tiles (contiguous units of one environment, a few each); blocks loop
-// over tiles, write one partial sum per tile, and after each grid-wide
-// barrier every block recombines the partials of each environment in tile
-// order (identical in all blocks, so alpha, beta and the stop test agree
-// everywhere and results are bit-reproducible).  Per env: the solve stops
-// when |r| <= tol |b|; the launch ends when every env has stopped or after
-// max_iter iterations.
+// Persistent PCG: one cooperative launch runs the whole solve (the path for
+// envs too large for one cluster).  Work is cut into tiles: runs of soft
+// units of one environment (sized at build so that there are a few tiles per
+// SM), and one tile per affine body, whose four rows collect the contact
+// blocks of every vertex touching the body and can be thousands of blocks
+// long.  Blocks loop over tiles, write one partial sum per tile, and after
+// each grid-wide barrier every block recombines the partials of each
+// environment in tile order (identical in all blocks, so alpha, beta and the
+// stop test agree everywhere and results are bit-reproducible).  Per env: the
+// solve stops when |r| <= tol |b|, or on breakdown (p.Ap <= 0: x kept; a
+// non-finite value marks the env with 2); the launch ends when every env has
+// stopped or after max_iter iterations.
+//
+// The iteration runs in the matrix's type (FP32 in the mixed form, where the
+// caller refines the result against FP64 residuals); the partial sums are
+// combined in FP64.  Two grid barriers per iteration: the new direction
+// p_k = z_k + beta p_{k-1} is formed on the fly inside the product (p
+// double-buffered: the product reads p_{k-1} and z_k of its columns, the
+// row's owner stores p_k), so a separate direction pass and its barrier are
+// not needed.
 // ---------------------------------------------------------------------------
+constexpr int kPcgRowLanes = 4;  // lanes per soft row in the product
+
 struct Tiles {
     int n;
     const int* u0;   // first unit of the tile
@@ -381,8 +341,9 @@ template <class Real>
 struct PcgArgs {
     Geo G;
     Bsr<Real> S, C;
-    PcgVec V;
-    const double* b;
+    const double* b;   // right-hand side (FP64)
+    double* x_out;     // solution (FP64)
+    Real *x, *r, *z, *p, *p2, *q;  // work vectors, 3 n_nodes each
     const Real* Minv_s;
     const Real* Minv_a;
     Tiles T;
@@ -391,33 +352,97 @@ struct PcgArgs {
     double* pt_pq;
     double* pt_rr;
     double* pt_bb;
-    int* conv;       // per env: in 1 = skip; out 1 = converged / skipped
+    int* conv;       // per env: in 1 = skip; out 1 = stopped, 2 = non-finite
     int* iters;      // per env
     double tol2;
+    const double* tol2_env;  // per-env tolerance (squared, relative), or null
     int max_iter;
 };
 
-// Sum of each env's tile partials into out[env].  Few envs: one warp per env,
-// lanes stride over the tiles and a fixed shuffle tree combines them; many
-// envs: one thread per env in tile order.  Every block computes identical
-// values (same order).
-__device__ __forceinline__ void env_sums(const Tiles& T, const double* part, int n_envs, double* out) {
-    int nw = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (n_envs <= nw * 4) {
-        for (int e = w; e < n_envs; e += nw) {
-            double s = 0.0;
-            for (int t = T.env_start[e] + lane; t < T.env_start[e + 1]; t += 32) s += part[t];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) out[e] = s;
+// Sum of each env's tile partials into out[env], identical in every block
+// (same order).  Few envs: the whole block strides over an env's tiles and a
+// fixed tree combines the threads; many envs: one thread per env in tile order.
+__device__ __forceinline__ void env_sums(const Tiles& T, const double* part, int n_envs, double* out,
+                                         double* red) {
+    if (n_envs <= 8) {
+        for (int e = 0; e < n_envs; ++e) {
+            double s0 = 0.0, s1 = 0.0;
+            const int t0 = T.env_start[e], t1 = T.env_start[e + 1];
+            int t = t0 + threadIdx.x;
+            for (; t + (int)blockDim.x < t1; t += 2 * blockDim.x) {
+                s0 += __ldcg(part + t);
+                s1 += __ldcg(part + t + blockDim.x);
+            }
+            if (t < t1) s0 += __ldcg(part + t);
+            const double v = block_sum<256>(s0 + s1, red);
+            if (threadIdx.x == 0) out[e] = v;
         }
     } else {
         for (int e = threadIdx.x; e < n_envs; e += blockDim.x) {
             double s = 0.0;
-            for (int t = T.env_start[e]; t < T.env_start[e + 1]; ++t) s += part[t];
+            for (int t = T.env_start[e]; t < T.env_start[e + 1]; ++t) s += __ldcg(part + t);
             out[e] = s;
         }
     }
+}
+
+// the tile is one affine body (its first node in n0)
+__device__ __forceinline__ bool pcg_aff_tile(const Geo& G, const Tiles& T, int t) {
+    const int u = T.u0[t];
+    return T.u1[t] == u + 1 && G.unit_kind[u] == 1;
+}
+
+// component c of the direction at node n: z + beta p_old (beta = 0: z alone)
+template <class Real>
+__device__ __forceinline__ Real pcg_dir(const Real* z, const Real* pold, Real beta, size_t o) {
+    Real v = z[o];
+    if (beta != Real(0)) v += beta * pold[o];
+    return v;
+}
+
+// blocks k0, k0 + step, ... < k1 of a row of A times the direction
+template <class Real>
+__device__ __forceinline__ void pcg_row_part(const Bsr<Real>& A, int k0, int k1, int step, const Real* z,
+                                             const Real* pold, Real beta, Real y[3]) {
+    for (int k = k0; k < k1; k += step) {
+        const Real* v = A.val + 9 * (size_t)k;
+        const size_t c = 3 * (size_t)A.col[k];
+        const Real p0 = pcg_dir(z, pold, beta, c), p1 = pcg_dir(z, pold, beta, c + 1),
+                   p2 = pcg_dir(z, pold, beta, c + 2);
+        y[0] += v[0] * p0 + v[1] * p1 + v[2] * p2;
+        y[1] += v[3] * p0 + v[4] * p1 + v[5] * p2;
+        y[2] += v[6] * p0 + v[7] * p1 + v[8] * p2;
+    }
+}
+
+// soft unit: z = M r on one node; returns r.z and r.r
+template <class Real>
+__device__ __forceinline__ void pcg_soft_precond(const Real* Minv_s, int n, const Real* r, Real* z, double& rz,
+                                                 double& rr) {
+    const Real* M = Minv_s + 9 * (size_t)n;
+    const Real r0 = r[3 * (size_t)n], r1 = r[3 * (size_t)n + 1], r2 = r[3 * (size_t)n + 2];
+    const Real z0 = M[0] * r0 + M[1] * r1 + M[2] * r2;
+    const Real z1 = M[3] * r0 + M[4] * r1 + M[5] * r2;
+    const Real z2 = M[6] * r0 + M[7] * r1 + M[8] * r2;
+    z[3 * (size_t)n] = z0;
+    z[3 * (size_t)n + 1] = z1;
+    z[3 * (size_t)n + 2] = z2;
+    rz += (double)(r0 * z0 + r1 * z1 + r2 * z2);
+    rr += (double)(r0 * r0 + r1 * r1 + r2 * r2);
+}
+
+// affine unit, 12 threads: thread i computes row i of z = M r (12 x 12)
+template <class Real>
+__device__ __forceinline__ void pcg_aff_precond(const Real* Minv_a, int body, int n0, const Real* r, Real* z, int i,
+                                                double& rz, double& rr) {
+    const Real* M = Minv_a + 144 * (size_t)body;
+    const Real* rb = r + 3 * (size_t)n0;
+    Real zi = 0;
+#pragma unroll
+    for (int j = 0; j < 12; ++j) zi += M[12 * i + j] * rb[j];
+    z[3 * (size_t)n0 + i] = zi;
+    rz += (double)(rb[i] * zi);
+    rr += (double)(rb[i] * rb[i]);
 }
 
 template <class Real>
@@ -430,133 +455,198 @@ __global__ void __launch_bounds__(256) k_pcg_persistent(PcgArgs<Real> a) {
     double* s_bb = sm + NE;       // b.b per env
     double* s_x = sm + 2 * NE;    // scratch per env (pq, then rz_new)
     double* s_y = sm + 3 * NE;    // scratch per env (rr)
-    int* s_conv = (int*)(sm + 4 * NE);
+    double* s_beta = sm + 4 * NE; // beta of the next direction per env
+    int* s_conv = (int*)(sm + 5 * NE);  // 0 running, 1 stopped, 2 non-finite
     __shared__ double red[32];
     __shared__ int s_all;
     const Geo& G = a.G;
-    PcgVec V = a.V;
-    // init: x = 0, r = b, z = M^-1 r, p = z
+    const int tid = threadIdx.x;
+    // init: x = 0, r = b, z = M^-1 r, previous direction 0
     for (int t = blockIdx.x; t < a.T.n; t += gridDim.x) {
-        int e = a.T.env[t];
-        bool skip = a.conv[e] != 0;
+        const int e = a.T.env[t];
         double rz = 0.0, bb = 0.0;
-        if (!skip)
-            for (int u = a.T.u0[t] + threadIdx.x; u < a.T.u1[t]; u += blockDim.x) {
-                int kind = G.unit_kind[u], idx = G.unit_idx[u];
-                int n0 = kind == 0 ? idx : G.aff_node0[idx], nn = kind == 0 ? 1 : 4;
-                for (int j = 0; j < 3 * nn; ++j) {
-                    size_t o = 3 * (size_t)n0 + j;
-                    V.r[o] = a.b[o];
-                    V.x[o] = 0.0;
+        if (a.conv[e] == 0) {
+            if (pcg_aff_tile(G, a.T, t)) {
+                const int n0 = a.T.n0[t];
+                if (tid < 12) {
+                    const size_t o = 3 * (size_t)n0 + tid;
+                    a.r[o] = (Real)a.b[o];
+                    a.x[o] = Real(0);
+                    a.p2[o] = Real(0);
+                    bb = a.b[o] * a.b[o];
                 }
-                double q1, q2;
-                unit_precond(G, u, a.Minv_s, a.Minv_a, V.r, V.z, q1, q2);
-                for (int j = 0; j < 3 * nn; ++j) V.p[3 * (size_t)n0 + j] = V.z[3 * (size_t)n0 + j];
-                rz += q1;
-                bb += q2;
+                __syncthreads();
+                double rr_unused = 0.0;
+                if (tid < 12) pcg_aff_precond(a.Minv_a, G.unit_idx[a.T.u0[t]], n0, a.r, a.z, tid, rz, rr_unused);
+            } else {
+                for (int n = a.T.n0[t] + tid; n < a.T.n1[t]; n += blockDim.x) {
+                    for (int c = 0; c < 3; ++c) {
+                        const size_t o = 3 * (size_t)n + c;
+                        a.r[o] = (Real)a.b[o];
+                        a.x[o] = Real(0);
+                        a.p2[o] = Real(0);
+                        bb += a.b[o] * a.b[o];
+                    }
+                    double rr_unused = 0.0;
+                    pcg_soft_precond(a.Minv_s, n, a.r, a.z, rz, rr_unused);
+                }
             }
-        double r1 = block_sum<256>(rz, red);
-        double r2 = block_sum<256>(bb, red);
-        if (threadIdx.x == 0) {
+        }
+        const double r1 = block_sum<256>(rz, red);
+        const double r2 = block_sum<256>(bb, red);
+        if (tid == 0) {
             a.pt_rz[t] = r1;
             a.pt_bb[t] = r2;
         }
     }
     grid.sync();
-    env_sums(a.T, a.pt_rz, NE, s_rz);
-    env_sums(a.T, a.pt_bb, NE, s_bb);
+    env_sums(a.T, a.pt_rz, NE, s_rz, red);
+    env_sums(a.T, a.pt_bb, NE, s_bb, red);
     __syncthreads();
-    for (int e = threadIdx.x; e < NE; e += blockDim.x) s_conv[e] = a.conv[e] || !(s_bb[e] > 0.0);
+    for (int e = tid; e < NE; e += blockDim.x) {
+        const bool fin = isfinite(s_bb[e]) && isfinite(s_rz[e]);
+        s_conv[e] = a.conv[e] ? 1 : (!fin ? 2 : (s_bb[e] > 0.0 ? 0 : 1));
+        s_beta[e] = 0.0;
+    }
     __syncthreads();
+    Real* pold = a.p2;  // p_{k-1}
+    Real* pcur = a.p;   // p_k, written this iteration
+    const int sub = tid % kPcgRowLanes, grp = tid / kPcgRowLanes;
+    const int rows_per_pass = blockDim.x / kPcgRowLanes;
     int it = 0;
     for (;;) {
-        if (threadIdx.x == 0) {
+        if (tid == 0) {
             int all = 1;
-            for (int e = 0; e < NE; ++e) all &= s_conv[e];
+            for (int e = 0; e < NE; ++e) all &= s_conv[e] != 0;
             s_all = all;
         }
         __syncthreads();
         if (s_all || it >= a.max_iter) break;
-        // q = A p, partial p.q
+        // p = z + beta p_old (own rows stored), q = A p, partial p.q
         for (int t = blockIdx.x; t < a.T.n; t += gridDim.x) {
-            int e = a.T.env[t];
+            const int e = a.T.env[t];
             double s = 0.0;
             if (!s_conv[e]) {
-                int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-                for (int n = a.T.n0[t] + w; n < a.T.n1[t]; n += blockDim.x >> 5) {
-                    V3 y = spmv_row_warp(a.S, n, V.p, lane) + spmv_row_warp(a.C, n, V.p, lane);
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) {
-                        y.x += __shfl_xor_sync(0xffffffffu, y.x, o);
-                        y.y += __shfl_xor_sync(0xffffffffu, y.y, o);
-                        y.z += __shfl_xor_sync(0xffffffffu, y.z, o);
+                const Real beta = (Real)s_beta[e];
+                const int n0 = a.T.n0[t], n1 = a.T.n1[t];
+                if (pcg_aff_tile(G, a.T, t)) {
+                    // four long rows: the whole block on each, fixed-tree sums
+                    for (int n = n0; n < n1; ++n) {
+                        Real y[3] = {0, 0, 0};
+                        pcg_row_part(a.S, a.S.rowptr[n] + tid, a.S.rowptr[n + 1], (int)blockDim.x, a.z, pold, beta, y);
+                        pcg_row_part(a.C, a.C.rowptr[n] + tid, a.C.rowptr[n + 1], (int)blockDim.x, a.z, pold, beta, y);
+                        double yt[3];
+                        for (int c = 0; c < 3; ++c) yt[c] = block_sum<256>((double)y[c], red);
+                        if (tid == 0) {
+                            for (int c = 0; c < 3; ++c) {
+                                const size_t o = 3 * (size_t)n + c;
+                                const Real pn = pcg_dir(a.z, pold, beta, o);
+                                pcur[o] = pn;
+                                a.q[o] = (Real)yt[c];
+                                s += (double)pn * yt[c];
+                            }
+                        }
                     }
-                    if (lane == 0) {
-                        st3(V.q + 3 * (size_t)n, y);
-                        s += dot(y, ld3(V.p + 3 * (size_t)n));
+                } else {
+                    // soft rows: kPcgRowLanes lanes per row; the row loop is
+                    // uniform over the block so every lane reaches the shuffles
+                    for (int nb = n0; nb < n1; nb += rows_per_pass) {
+                        const int n = nb + grp;
+                        Real y[3] = {0, 0, 0};
+                        if (n < n1) {
+                            pcg_row_part(a.S, a.S.rowptr[n] + sub, a.S.rowptr[n + 1], kPcgRowLanes, a.z, pold, beta, y);
+                            pcg_row_part(a.C, a.C.rowptr[n] + sub, a.C.rowptr[n + 1], kPcgRowLanes, a.z, pold, beta, y);
+                        }
+#pragma unroll
+                        for (int o = kPcgRowLanes / 2; o > 0; o >>= 1)
+                            for (int c = 0; c < 3; ++c) y[c] += __shfl_xor_sync(0xffffffffu, y[c], o);
+                        if (n < n1 && sub == 0) {
+                            Real d = 0;
+                            for (int c = 0; c < 3; ++c) {
+                                const size_t o = 3 * (size_t)n + c;
+                                const Real pn = pcg_dir(a.z, pold, beta, o);
+                                pcur[o] = pn;
+                                a.q[o] = y[c];
+                                d += pn * y[c];
+                            }
+                            s += (double)d;
+                        }
                     }
                 }
             }
-            double r1 = block_sum<256>(s, red);
-            if (threadIdx.x == 0) a.pt_pq[t] = r1;
+            const double r1 = block_sum<256>(s, red);
+            if (tid == 0) a.pt_pq[t] = r1;
         }
         grid.sync();
-        env_sums(a.T, a.pt_pq, NE, s_x);
+        env_sums(a.T, a.pt_pq, NE, s_x, red);
+        __syncthreads();
+        // breakdown (p.Ap <= 0): stop with x kept; non-finite: mark the env
+        for (int e = tid; e < NE; e += blockDim.x)
+            if (!s_conv[e] && !(s_x[e] > 0.0)) s_conv[e] = isfinite(s_x[e]) ? 1 : 2;
         __syncthreads();
         // x += alpha p ; r -= alpha q ; z = M^-1 r ; partial r.z, r.r
         for (int t = blockIdx.x; t < a.T.n; t += gridDim.x) {
-            int e = a.T.env[t];
+            const int e = a.T.env[t];
             double rz = 0.0, rr = 0.0;
             if (!s_conv[e]) {
-                double alpha = s_x[e] > 0.0 ? s_rz[e] / s_x[e] : 0.0;
-                for (int u = a.T.u0[t] + threadIdx.x; u < a.T.u1[t]; u += blockDim.x) {
-                    int kind = G.unit_kind[u], idx = G.unit_idx[u];
-                    int n0 = kind == 0 ? idx : G.aff_node0[idx], nn = kind == 0 ? 1 : 4;
-                    for (int j = 0; j < 3 * nn; ++j) {
-                        size_t o = 3 * (size_t)n0 + j;
-                        V.x[o] += alpha * V.p[o];
-                        V.r[o] -= alpha * V.q[o];
+                const Real alpha = (Real)(s_rz[e] / s_x[e]);
+                if (pcg_aff_tile(G, a.T, t)) {
+                    const int n0 = a.T.n0[t];
+                    if (tid < 12) {
+                        const size_t o = 3 * (size_t)n0 + tid;
+                        a.x[o] += alpha * pcur[o];
+                        a.r[o] -= alpha * a.q[o];
                     }
-                    double q1, q2;
-                    unit_precond(G, u, a.Minv_s, a.Minv_a, V.r, V.z, q1, q2);
-                    rz += q1;
-                    rr += q2;
+                    __syncthreads();
+                    if (tid < 12) pcg_aff_precond(a.Minv_a, G.unit_idx[a.T.u0[t]], n0, a.r, a.z, tid, rz, rr);
+                } else {
+                    for (int n = a.T.n0[t] + tid; n < a.T.n1[t]; n += blockDim.x) {
+                        for (int c = 0; c < 3; ++c) {
+                            const size_t o = 3 * (size_t)n + c;
+                            a.x[o] += alpha * pcur[o];
+                            a.r[o] -= alpha * a.q[o];
+                        }
+                        pcg_soft_precond(a.Minv_s, n, a.r, a.z, rz, rr);
+                    }
                 }
             }
-            double r1 = block_sum<256>(rz, red);
-            double r2 = block_sum<256>(rr, red);
-            if (threadIdx.x == 0) {
+            const double r1 = block_sum<256>(rz, red);
+            const double r2 = block_sum<256>(rr, red);
+            if (tid == 0) {
                 a.pt_rz2[t] = r1;
                 a.pt_rr[t] = r2;
             }
         }
         grid.sync();
-        env_sums(a.T, a.pt_rz2, NE, s_x);
-        env_sums(a.T, a.pt_rr, NE, s_y);
+        env_sums(a.T, a.pt_rz2, NE, s_x, red);
+        env_sums(a.T, a.pt_rr, NE, s_y, red);
         __syncthreads();
-        // beta, stop test, p = z + beta p
-        for (int t = blockIdx.x; t < a.T.n; t += gridDim.x) {
-            int e = a.T.env[t];
-            if (s_conv[e] || !(s_y[e] > a.tol2 * s_bb[e])) continue;
-            double beta = s_rz[e] != 0.0 ? s_x[e] / s_rz[e] : 0.0;
-            for (int n = a.T.n0[t] + threadIdx.x; n < a.T.n1[t]; n += blockDim.x)
-                for (int j = 0; j < 3; ++j) {
-                    size_t o = 3 * (size_t)n + j;
-                    V.p[o] = V.z[o] + beta * V.p[o];
-                }
-        }
-        __syncthreads();
-        for (int e = threadIdx.x; e < NE; e += blockDim.x) {
+        // stop test and the next beta per env
+        for (int e = tid; e < NE; e += blockDim.x) {
             if (s_conv[e]) continue;
             if (blockIdx.x == 0) a.iters[e] += 1;
-            if (!(s_y[e] > a.tol2 * s_bb[e])) s_conv[e] = 1;
+            const double tol2 = a.tol2_env ? a.tol2_env[e] : a.tol2;
+            if (!isfinite(s_y[e]) || !isfinite(s_x[e]))
+                s_conv[e] = 2;
+            else if (!(s_y[e] > tol2 * s_bb[e]))
+                s_conv[e] = 1;
+            s_beta[e] = s_rz[e] != 0.0 ? s_x[e] / s_rz[e] : 0.0;
             s_rz[e] = s_x[e];
         }
+        Real* tmp = pold;
+        pold = pcur;
+        pcur = tmp;
         ++it;
-        grid.sync();
     }
+    // x out in FP64 (envs that were skipped on entry are left untouched)
+    for (int t = blockIdx.x; t < a.T.n; t += gridDim.x) {
+        const int e = a.T.env[t];
+        if (a.conv[e]) continue;
+        for (int o = 3 * a.T.n0[t] + tid; o < 3 * a.T.n1[t]; o += blockDim.x) a.x_out[o] = (double)a.x[o];
+    }
+    grid.sync();
     if (blockIdx.x == 0)
-        for (int e = threadIdx.x; e < NE; e += blockDim.x) a.conv[e] = s_conv[e];
+        for (int e = tid; e < NE; e += blockDim.x) a.conv[e] = s_conv[e] == 2 ? 2 : 1;
 }
 
 }  // namespace zema

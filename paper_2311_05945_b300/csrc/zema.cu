@@ -85,6 +85,7 @@ struct zema_scene {
     DBuf<int3> tris;
     // state
     DBuf<double> x, v, xt, xhat, p, xtrial, g, b, r, z, pp, q, X, Xt, X1, stage_blk, stage_g, S_val, Minv_s, Minv_a;
+    DBuf<double> pcg_work;  // work vectors of the grid-wide solve (6 x 3 n_nodes of the solve's type)
     DBuf<double> qtarget, lamA;
     // per env
     DBuf<double> tol2_env;
@@ -469,14 +470,26 @@ void build(zema_scene* s) {
     }
     env_unit_start[NE] = (int)unit_kind_h.size();
     s->n_units = (int)unit_kind_h.size();
-    // PCG tiles: <= kTileUnits consecutive units of one env and their node
-    // range (small tiles: the solve's blocks each own a few rows)
-    const int kTileUnits = 16;
+    // PCG tiles of the grid-wide solve: <= kTileUnits consecutive soft units
+    // of one env and their node range, about four tiles per SM over the whole
+    // scene (16 to 256 units, so a block's threads each own about one unit),
+    // and one tile per affine unit
+    int kTileUnits = 16;
+    {
+        int dev = 0, nsm = 148;
+        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        cudaGetLastError();
+        const int want = (int)((unit_kind_h.size() + 4 * (size_t)nsm - 1) / (4 * (size_t)nsm));
+        kTileUnits = std::max(16, std::min(256, want));
+    }
     std::vector<int> tu0, tu1, tn0, tn1, tenv, etile(NE + 1, 0);
     for (int e = 0; e < NE; ++e) {
         etile[e] = (int)tu0.size();
-        for (int u = env_unit_start[e]; u < env_unit_start[e + 1]; u += kTileUnits) {
-            int ue = std::min(u + kTileUnits, env_unit_start[e + 1]);
+        // runs of <= kTileUnits soft units; every affine unit a tile of its own
+        for (int u = env_unit_start[e], ue; u < env_unit_start[e + 1]; u = ue) {
+            ue = u + 1;
+            if (unit_kind_h[u] == 0)
+                while (ue < env_unit_start[e + 1] && ue - u < kTileUnits && unit_kind_h[ue] == 0) ++ue;
             auto first_node = [&](int uu) {
                 return unit_kind_h[uu] == 0 ? unit_idx_h[uu] : s->aff_node0_h[aff_perm[unit_idx_h[uu]]];
             };
@@ -1258,142 +1271,64 @@ int64_t pcg_t(zema_scene* s, const std::vector<int>& done_h) {
     const char* kname = use_cluster ? "k_pcg_cluster" : "k_pcg_persistent";
     int64_t tot = 0, mx = 0;
     // iterations of the last launch (and its non-finite flags) into tot / mx
-    auto collect = [&](bool cluster) {
+    auto collect = [&]() {
         ZCHECK(cudaMemcpyAsync(s->hi, s->pcg_iters.p, NE * sizeof(int), cudaMemcpyDeviceToHost, st));
-        if (cluster) ZCHECK(cudaMemcpyAsync(s->hi + NE, s->conv.p, NE * sizeof(int), cudaMemcpyDeviceToHost, st));
+        ZCHECK(cudaMemcpyAsync(s->hi + NE, s->conv.p, NE * sizeof(int), cudaMemcpyDeviceToHost, st));
         ZCHECK(cudaStreamSynchronize(st));
         for (int e = 0; e < NE; ++e) {
-            if (cluster && s->hi[NE + e] == 2) fail(ZEMA_ERR_NONFINITE, "non-finite value in the linear solve");
+            if (s->hi[NE + e] == 2) fail(ZEMA_ERR_NONFINITE, "non-finite value in the linear solve");
             tot += s->hi[e];
             mx = std::max<int64_t>(mx, s->hi[e]);
         }
     };
-    if (use_cluster) {
-        // one cluster solve with cs CTAs per env (launch only)
-        auto launch_cluster = [&](const double* rhs, double* xo, int cs, const double* tol2_env = nullptr) {
-            PcgcArgs<T> c;
-            c.G = G;
-            c.S = S;
-            c.C = C;
-            c.b = rhs;
-            c.x_out = xo;
-            c.z = (T*)s->z.p;
-            c.Minv_s = Minv_s;
-            c.Minv_a = Minv_a;
-            c.conv = s->conv.p;
-            c.iters = s->pcg_iters.p;
-            c.tol2 = s->P.pcg_rel_tol * s->P.pcg_rel_tol;
-            c.tol2_env = tol2_env;
-            c.max_iter = s->P.max_pcg;
-            c.max_env_nodes = s->pcgc_max_env_nodes;
-            c.max_rows = pcgc_max_rows(s, cs);
-            c.max_aff = s->pcgc_max_aff;
-            c.slice_cap = pcgc_slice_cap<T>(s, cs);
-            c.chunk_cap = pcgc_chunk_cap(s, cs);
-            cudaLaunchConfig_t cfg = {};
-            cudaLaunchAttribute at[1];
-            pcgc_config<T>(s, cs, cfg, at);
-            cfg.stream = st;
-            {
-                LaunchScope ls("k_pcg_cluster");
-                ZCHECK(cudaLaunchKernelEx(&cfg, k_pcg_cluster<T>, c));
-            }
-            ZLAUNCH();
-        };
-        if (s->pcgc_tune[pi]) {
-            // autotuner: time the solve of this system with every valid cluster
-            // size (results discarded, best of two runs each) and keep the
-            // fastest; the solve below then uses it
-            s->pcgc_tune[pi] = false;
-            s->pcgc_tuned[pi].clear();
-            cudaEvent_t e0, e1;
-            ZCHECK(cudaEventCreate(&e0));
-            ZCHECK(cudaEventCreate(&e1));
-            float best = INFINITY;
-            int best_cs = s->pcgc_cs[pi];
-            for (int cs = 1; cs <= 16; cs *= 2) {
-                if (!pcgc_valid<T>(s, cs)) continue;
-                float ms = INFINITY;
-                for (int rep = 0; rep < 2; ++rep) {
-                    ZCHECK(cudaMemcpyAsync(s->conv.p, s->hi + 3 * NE, NE * sizeof(int), cudaMemcpyHostToDevice, st));
-                    ZCHECK(cudaEventRecord(e0, st));
-                    launch_cluster(s->b.p, s->r.p, cs);
-                    ZCHECK(cudaEventRecord(e1, st));
-                    ZCHECK(cudaEventSynchronize(e1));
-                    float t = 0.0f;
-                    ZCHECK(cudaEventElapsedTime(&t, e0, e1));
-                    ms = std::min(ms, t);
-                }
-                s->pcgc_tuned[pi].push_back({cs, ms});
-                if (ms < best) {
-                    best = ms;
-                    best_cs = cs;
-                }
-            }
-            cudaEventDestroy(e0);
-            cudaEventDestroy(e1);
-            s->pcgc_cs[pi] = best_cs;
-            ZCHECK(cudaMemcpyAsync(s->conv.p, s->hi + 3 * NE, NE * sizeof(int), cudaMemcpyHostToDevice, st));
+    // one cluster solve with cs CTAs per env (launch only)
+    auto launch_cluster = [&](const double* rhs, double* xo, int cs, const double* tol2_env = nullptr) {
+        PcgcArgs<T> c;
+        c.G = G;
+        c.S = S;
+        c.C = C;
+        c.b = rhs;
+        c.x_out = xo;
+        c.z = (T*)s->z.p;
+        c.Minv_s = Minv_s;
+        c.Minv_a = Minv_a;
+        c.conv = s->conv.p;
+        c.iters = s->pcg_iters.p;
+        c.tol2 = s->P.pcg_rel_tol * s->P.pcg_rel_tol;
+        c.tol2_env = tol2_env;
+        c.max_iter = s->P.max_pcg;
+        c.max_env_nodes = s->pcgc_max_env_nodes;
+        c.max_rows = pcgc_max_rows(s, cs);
+        c.max_aff = s->pcgc_max_aff;
+        c.slice_cap = pcgc_slice_cap<T>(s, cs);
+        c.chunk_cap = pcgc_chunk_cap(s, cs);
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        pcgc_config<T>(s, cs, cfg, at);
+        cfg.stream = st;
+        {
+            LaunchScope ls("k_pcg_cluster");
+            ZCHECK(cudaLaunchKernelEx(&cfg, k_pcg_cluster<T>, c));
         }
-        auto run_cluster = [&](const double* rhs, double* xo, const double* tol2_env = nullptr) {
-            launch_cluster(rhs, xo, s->pcgc_cs[pi], tol2_env);
-            collect(true);
-        };
-        run_cluster(s->b.p, s->p.p);
-        if (sizeof(T) < sizeof(double)) {
-            // FP64 residual refinement of the FP32 solve: r = b - A x with
-            // FP64 products; while |r| > tol |b| solve A d = r and add d
-            std::vector<int> need(NE);
-            for (int e = 0; e < NE; ++e) need[e] = done_h[e] ? 0 : 1;
-            const size_t nc = (size_t)NE * kChunks;
-            std::vector<double> prr(nc), pbb(nc);
-            for (int ref = 0; ref < kPcgcRefine; ++ref) {
-                for (int e = 0; e < NE; ++e) s->hi[e] = need[e] ? 0 : 1;
-                ZCHECK(cudaMemcpyAsync(s->conv.p, s->hi, NE * sizeof(int), cudaMemcpyHostToDevice, st));
-                ZL(k_residual64<T>, div_up(32 * (long long)s->n_nodes, 128), 128, 0, st)(G, S, C, s->p.p, s->b.p,
-                                                                                        s->conv.p, s->q.p);
-                ZL(k_env_dot2, red_grid(NE), kRedThreads, 0, st)(G, s->b.p, s->q.p, s->part4.p, s->part5.p);
-                ZL(k_env_dot2, red_grid(NE), kRedThreads, 0, st)(G, s->q.p, s->b.p, s->part6.p, s->part7.p);
-                ZLAUNCH();
-                ZCHECK(cudaMemcpyAsync(prr.data(), s->part5.p, nc * sizeof(double), cudaMemcpyDeviceToHost, st));
-                ZCHECK(cudaMemcpyAsync(pbb.data(), s->part7.p, nc * sizeof(double), cudaMemcpyDeviceToHost, st));
-                ZCHECK(cudaStreamSynchronize(st));
-                int count = 0;
-                const double tol2 = s->P.pcg_rel_tol * s->P.pcg_rel_tol;
-                for (int e = 0; e < NE; ++e) {
-                    s->hd[e] = tol2;
-                    if (!need[e]) continue;
-                    double rr = 0.0, bbv = 0.0;
-                    for (int k = 0; k < kChunks; ++k) {
-                        rr += prr[(size_t)e * kChunks + k];
-                        bbv += pbb[(size_t)e * kChunks + k];
-                    }
-                    if (!std::isfinite(rr)) fail(ZEMA_ERR_NONFINITE, "non-finite residual of the linear solve");
-                    need[e] = rr > tol2 * bbv ? 1 : 0;
-                    count += need[e];
-                    // the correction d only has to bring |r - A d| under
-                    // tol |b|: stop its solve at half of that, relative to |r|
-                    if (need[e]) s->hd[e] = std::min(0.25, 0.25 * tol2 * bbv / rr);
-                }
-                if (!count) break;
-                s->S.pcg_refines += count;
-                for (int e = 0; e < NE; ++e) s->hi[e] = need[e] ? 0 : 1;
-                ZCHECK(cudaMemcpyAsync(s->conv.p, s->hi, NE * sizeof(int), cudaMemcpyHostToDevice, st));
-                ZCHECK(cudaMemcpyAsync(s->tol2_env.p, s->hd, NE * sizeof(double), cudaMemcpyHostToDevice, st));
-                run_cluster(s->q.p, s->r.p, s->tol2_env.p);
-                for (int e = 0; e < NE; ++e) s->hi[e] = need[e];
-                ZCHECK(cudaMemcpyAsync(s->need.p, s->hi, NE * sizeof(int), cudaMemcpyHostToDevice, st));
-                ZL(k_add_env, div_up(s->n_nodes, TB), TB, 0, st)(G, s->p.p, s->r.p, s->need.p);
-                ZLAUNCH();
-            }
-        }
-    } else {
+        ZLAUNCH();
+    };
+    // one grid-wide solve (cooperative launch; launch only)
+    auto launch_grid = [&](const double* rhs, double* xo, const double* tol2_env) {
         PcgArgs<T> a;
         a.G = G;
         a.S = S;
         a.C = C;
-        a.V = PcgVec{s->p.p, s->r.p, s->z.p, s->pp.p, s->q.p};
-        a.b = s->b.p;
+        a.b = rhs;
+        a.x_out = xo;
+        const size_t nv = 3 * (size_t)s->n_nodes;
+        s->pcg_work.ensure(&s->A, 6 * nv);
+        T* w = (T*)s->pcg_work.p;
+        a.x = w;
+        a.r = w + nv;
+        a.z = w + 2 * nv;
+        a.p = w + 3 * nv;
+        a.p2 = w + 4 * nv;
+        a.q = w + 5 * nv;
         a.Minv_s = Minv_s;
         a.Minv_a = Minv_a;
         a.T = Tiles{s->n_tiles, s->tile_u0.p, s->tile_u1.p, s->tile_n0.p, s->tile_n1.p, s->tile_env.p, s->env_tile_start.p};
@@ -1405,8 +1340,9 @@ int64_t pcg_t(zema_scene* s, const std::vector<int>& done_h) {
         a.conv = s->conv.p;
         a.iters = s->pcg_iters.p;
         a.tol2 = s->P.pcg_rel_tol * s->P.pcg_rel_tol;
+        a.tol2_env = tol2_env;
         a.max_iter = s->P.max_pcg;
-        size_t smem = 4 * (size_t)NE * sizeof(double) + (size_t)NE * sizeof(int);
+        size_t smem = 5 * (size_t)NE * sizeof(double) + (size_t)NE * sizeof(int);
         int& grid = s->P.precision == 1 ? s->pcg_grid_f : s->pcg_grid;
         if (grid == 0) {
             int dev = 0, nsm = 0, per = 0;
@@ -1423,7 +1359,99 @@ int64_t pcg_t(zema_scene* s, const std::vector<int>& done_h) {
             ZCHECK(cudaLaunchCooperativeKernel((const void*)k_pcg_persistent<T>, dim3(grid), dim3(256), args, smem, st));
         }
         ZLAUNCH();
-        collect(false);
+    };
+    if (use_cluster && s->pcgc_tune[pi]) {
+        // autotuner: time the solve of this system with every valid cluster
+        // size (results discarded, best of two runs each) and keep the
+        // fastest; the solve below then uses it
+        s->pcgc_tune[pi] = false;
+        s->pcgc_tuned[pi].clear();
+        cudaEvent_t e0, e1;
+        ZCHECK(cudaEventCreate(&e0));
+        ZCHECK(cudaEventCreate(&e1));
+        float best = INFINITY;
+        int best_cs = s->pcgc_cs[pi];
+        for (int cs = 1; cs <= 16; cs *= 2) {
+            if (!pcgc_valid<T>(s, cs)) continue;
+            float ms = INFINITY;
+            for (int rep = 0; rep < 2; ++rep) {
+                ZCHECK(cudaMemcpyAsync(s->conv.p, s->hi + 3 * NE, NE * sizeof(int), cudaMemcpyHostToDevice, st));
+                ZCHECK(cudaEventRecord(e0, st));
+                launch_cluster(s->b.p, s->r.p, cs);
+                ZCHECK(cudaEventRecord(e1, st));
+                ZCHECK(cudaEventSynchronize(e1));
+                float t = 0.0f;
+                ZCHECK(cudaEventElapsedTime(&t, e0, e1));
+                ms = std::min(ms, t);
+            }
+            s->pcgc_tuned[pi].push_back({cs, ms});
+            if (ms < best) {
+                best = ms;
+                best_cs = cs;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        s->pcgc_cs[pi] = best_cs;
+        ZCHECK(cudaMemcpyAsync(s->conv.p, s->hi + 3 * NE, NE * sizeof(int), cudaMemcpyHostToDevice, st));
+    }
+    // one solve of the selected form, then its statistics
+    auto run_solve = [&](const double* rhs, double* xo, const double* tol2_env = nullptr) {
+        // envs skipped by this solve must not count the previous solve's iterations
+        ZCHECK(cudaMemsetAsync(s->pcg_iters.p, 0, NE * sizeof(int), st));
+        if (use_cluster)
+            launch_cluster(rhs, xo, s->pcgc_cs[pi], tol2_env);
+        else
+            launch_grid(rhs, xo, tol2_env);
+        collect();
+    };
+    run_solve(s->b.p, s->p.p);
+    if (sizeof(T) < sizeof(double)) {
+        // FP64 residual refinement of the FP32 solve: r = b - A x with
+        // FP64 products; while |r| > tol |b| solve A d = r and add d
+        std::vector<int> need(NE);
+        for (int e = 0; e < NE; ++e) need[e] = done_h[e] ? 0 : 1;
+        const size_t nc = (size_t)NE * kChunks;
+        std::vector<double> prr(nc), pbb(nc);
+        for (int ref = 0; ref < kPcgcRefine; ++ref) {
+            for (int e = 0; e < NE; ++e) s->hi[e] = need[e] ? 0 : 1;
+            ZCHECK(cudaMemcpyAsync(s->conv.p, s->hi, NE * sizeof(int), cudaMemcpyHostToDevice, st));
+            ZL(k_residual64<T>, div_up(32 * (long long)s->n_nodes, 128), 128, 0, st)(G, S, C, s->p.p, s->b.p,
+                                                                                    s->conv.p, s->q.p);
+            ZL(k_env_dot2, red_grid(NE), kRedThreads, 0, st)(G, s->b.p, s->q.p, s->part4.p, s->part5.p);
+            ZL(k_env_dot2, red_grid(NE), kRedThreads, 0, st)(G, s->q.p, s->b.p, s->part6.p, s->part7.p);
+            ZLAUNCH();
+            ZCHECK(cudaMemcpyAsync(prr.data(), s->part5.p, nc * sizeof(double), cudaMemcpyDeviceToHost, st));
+            ZCHECK(cudaMemcpyAsync(pbb.data(), s->part7.p, nc * sizeof(double), cudaMemcpyDeviceToHost, st));
+            ZCHECK(cudaStreamSynchronize(st));
+            int count = 0;
+            const double tol2 = s->P.pcg_rel_tol * s->P.pcg_rel_tol;
+            for (int e = 0; e < NE; ++e) {
+                s->hd[e] = tol2;
+                if (!need[e]) continue;
+                double rr = 0.0, bbv = 0.0;
+                for (int k = 0; k < kChunks; ++k) {
+                    rr += prr[(size_t)e * kChunks + k];
+                    bbv += pbb[(size_t)e * kChunks + k];
+                }
+                if (!std::isfinite(rr)) fail(ZEMA_ERR_NONFINITE, "non-finite residual of the linear solve");
+                need[e] = rr > tol2 * bbv ? 1 : 0;
+                count += need[e];
+                // the correction d only has to bring |r - A d| under
+                // tol |b|: stop its solve at half of that, relative to |r|
+                if (need[e]) s->hd[e] = std::min(0.25, 0.25 * tol2 * bbv / rr);
+            }
+            if (!count) break;
+            s->S.pcg_refines += count;
+            for (int e = 0; e < NE; ++e) s->hi[e] = need[e] ? 0 : 1;
+            ZCHECK(cudaMemcpyAsync(s->conv.p, s->hi, NE * sizeof(int), cudaMemcpyHostToDevice, st));
+            ZCHECK(cudaMemcpyAsync(s->tol2_env.p, s->hd, NE * sizeof(double), cudaMemcpyHostToDevice, st));
+            run_solve(s->q.p, s->r.p, s->tol2_env.p);
+            for (int e = 0; e < NE; ++e) s->hi[e] = need[e];
+            ZCHECK(cudaMemcpyAsync(s->need.p, s->hi, NE * sizeof(int), cudaMemcpyHostToDevice, st));
+            ZL(k_add_env, div_up(s->n_nodes, TB), TB, 0, st)(G, s->p.p, s->r.p, s->need.p);
+            ZLAUNCH();
+        }
     }
     // Algorithmic bytes of the solve for the live roofline, per iteration:
     // the bytes of a streaming PCG iteration whose three fused passes keep

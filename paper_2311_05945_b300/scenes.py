@@ -338,9 +338,10 @@ def _solid(kind, size_scale, spacing):
     raise ValueError(kind)
 
 
-def _spacing_for_count(kind, target_tets, size_scale=1.0):
-    """Lattice spacing whose kept-cell count x 6 is closest to target_tets."""
-    lo, hi = 5e-4, 2e-2
+def _spacing_for_count(kind, target_tets, size_scale=1.0, hi=2e-2):
+    """Lattice spacing whose kept-cell count x 6 is closest to target_tets
+    (bisection over [5e-4, hi])."""
+    lo = 5e-4
     for _ in range(40):
         mid = math.sqrt(lo * hi)
         m, _ = _solid(kind, size_scale, mid)
@@ -500,4 +501,158 @@ def random_state_scene(seed: int, n_soft: int = 3, n_aff: int = 2) -> Scene:
             V, F = box_surface((0.15, 0.15, 0.15), 2)
             s.affines.append(AffineBody(V, F, q_identity(base + 0.075), rho=1000.0, stiffness=1e8,
                                         mu=0.5, mode=0))
+    return s
+
+
+# ----------------------------------------------------------------------------
+# Dense soft-rigid pile
+# ----------------------------------------------------------------------------
+def uv_sphere_surface(radii, n_seg: int = 32, n_ring: int = 32):
+    """Closed, outward-oriented UV sphere (ellipsoid of semi-axes radii): two
+    poles on +-y and n_ring - 1 rings of n_seg vertices; 2 n_seg (n_ring - 1)
+    triangles (1984 for 32 x 32)."""
+    a, b, c = [float(r) for r in radii]
+    V = [(0.0, b, 0.0)]
+    for i in range(1, n_ring):
+        th = math.pi * i / n_ring
+        for j in range(n_seg):
+            ph = 2.0 * math.pi * j / n_seg
+            V.append((a * math.sin(th) * math.cos(ph), b * math.cos(th), c * math.sin(th) * math.sin(ph)))
+    V.append((0.0, -b, 0.0))
+    south = len(V) - 1
+
+    def ring(i, j):
+        return 1 + (i - 1) * n_seg + (j % n_seg)
+
+    F = []
+    for j in range(n_seg):
+        F.append((0, ring(1, j + 1), ring(1, j)))
+    for i in range(1, n_ring - 1):
+        for j in range(n_seg):
+            p, q, r, s = ring(i, j), ring(i, j + 1), ring(i + 1, j + 1), ring(i + 1, j)
+            F.append((p, q, r))
+            F.append((p, r, s))
+    for j in range(n_seg):
+        F.append((south, ring(n_ring - 1, j), ring(n_ring - 1, j + 1)))
+    return np.array(V, dtype=np.float64), np.array(F, dtype=np.int32)
+
+
+def torus_surface(R: float, r: float, n_u: int = 32, n_v: int = 32):
+    """Closed, outward-oriented torus about the y axis (major radius R, tube
+    radius r): n_u x n_v vertices, 2 n_u n_v triangles (2048 for 32 x 32)."""
+    V = []
+    for i in range(n_u):
+        u = 2.0 * math.pi * i / n_u
+        for j in range(n_v):
+            v = 2.0 * math.pi * j / n_v
+            rho = R + r * math.cos(v)
+            V.append((rho * math.cos(u), r * math.sin(v), rho * math.sin(u)))
+
+    def vid(i, j):
+        return (i % n_u) * n_v + (j % n_v)
+
+    F = []
+    for i in range(n_u):
+        for j in range(n_v):
+            p, q, s, t = vid(i, j), vid(i + 1, j), vid(i + 1, j + 1), vid(i, j + 1)
+            F.append((p, s, q))
+            F.append((p, t, s))
+    return np.array(V, dtype=np.float64), np.array(F, dtype=np.int32)
+
+
+def rotation_from_uniforms(u1: float, u2: float, u3: float) -> np.ndarray:
+    """Uniformly distributed rotation matrix from three uniforms in [0, 1)
+    (Shoemake's unit-quaternion construction)."""
+    s1, s2 = math.sqrt(1.0 - u1), math.sqrt(u1)
+    w, x, y, z = (s2 * math.cos(2 * math.pi * u3), s1 * math.sin(2 * math.pi * u2),
+                  s1 * math.cos(2 * math.pi * u2), s2 * math.sin(2 * math.pi * u3))
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - z * w), 2 * (x * z + y * w)],
+                     [2 * (x * y + z * w), 1 - 2 * (x * x + z * z), 2 * (y * z - x * w)],
+                     [2 * (x * z - y * w), 2 * (y * z + x * w), 1 - 2 * (x * x + y * y)]])
+
+
+def _yaw(theta: float) -> np.ndarray:
+    c, s = math.cos(theta), math.sin(theta)
+    return np.array([[c, 0.0, s], [0.0, 1.0, 0.0], [-s, 0.0, c]])
+
+
+def scene_c5(n_steps: int = 200, tets_per_body: int = 60000, n_soft: int = 8, n_convex: int = 10,
+             n_nonconvex: int = 10, n_seg: int = 32, seed: int = 5, precision: int = 1,
+             bin_subdiv: int = 4, gap: float = 0.01) -> Scene:
+    """Dense soft-rigid pile: an open-top 1 m rigid bin of 5 fixed 2 cm thick
+    boxes, n_soft soft lattice bodies (ellipsoid, torus or box, ~0.2 m,
+    tets_per_body tets each, E = 1e5, nu = 0.4), n_convex affine UV spheres
+    (n_seg x n_seg, seeded anisotropic radii in [0.06, 0.1] m and rotation) and
+    n_nonconvex affine tori (n_seg x n_seg, R = 0.07 m, r = 0.025 m, seeded
+    rotation), all rho = 1000 and stiffness 1e8.  The bodies start at rest in
+    seeded distinct slots of a 3 x 3 x L lattice (0.333 m cells across the
+    bin, layers 0.25 m apart, the lowest `gap` above the floor) and drop.
+    mu = 0.5, dt = 0.01.  Each bin box face is split bin_subdiv x bin_subdiv.
+
+    Newton is capped at 1000 iterations here instead of 100: when kilogram
+    rigid bodies land on soft meshes of 0.1 g vertices, single steps take up
+    to ~80 projected-Newton iterations (most of them line-search limited),
+    whatever the linear-solve tolerance or precision."""
+    p = Params(dt=0.01, dhat=1e-3, kappa=0.0, eps_v=1e-3, newton_tol_rel=1e-3, precision=precision,
+               max_newton=1000)
+    s = Scene("c5_dense_pile", p, n_steps=n_steps)
+    wall_t, H = 0.02, 1.0
+    # bin: floor (top at y = 0) and four walls standing 1 mm above it; the
+    # x-walls span the floor's depth, the z-walls fit between them
+    Vb, Fb = box_surface((1.0 + 2 * wall_t, wall_t, 1.0 + 2 * wall_t), bin_subdiv)
+    s.affines.append(AffineBody(Vb, Fb, q_identity((0.0, -0.5 * wall_t, 0.0)), rho=1000.0, stiffness=1e8,
+                                mu=0.5, mode=1, name="bin_floor"))
+    for sx in (-1, 1):
+        V, F = box_surface((wall_t, H, 1.0 + 2 * wall_t), bin_subdiv)
+        s.affines.append(AffineBody(V, F, q_identity((sx * (0.5 + 0.5 * wall_t), 0.001 + 0.5 * H, 0.0)),
+                                    rho=1000.0, stiffness=1e8, mu=0.5, mode=1, name=f"bin_wall_x{sx:+d}"))
+    for sz in (-1, 1):
+        V, F = box_surface((1.0 - 0.002, H, wall_t), bin_subdiv)
+        s.affines.append(AffineBody(V, F, q_identity((0.0, 0.001 + 0.5 * H, sz * (0.5 + 0.5 * wall_t))),
+                                    rho=1000.0, stiffness=1e8, mu=0.5, mode=1, name=f"bin_wall_z{sz:+d}"))
+    n_bodies = n_soft + n_convex + n_nonconvex
+    layers = max(1, (n_bodies + 8) // 9)
+    slots = [(l, i, k) for l in range(layers) for i in range(3) for k in range(3)]
+    u = uniform01(seed, 8 * n_bodies + len(slots) + n_bodies)
+    # the lowest n_bodies slots (seeded order within a layer), dealt to the
+    # bodies in a seeded permutation so that kinds mix across layers
+    lowest = sorted(range(len(slots)), key=lambda t: (slots[t][0], u[t]))[:n_bodies]
+    perm = np.argsort(u[len(slots):len(slots) + n_bodies], kind="stable")
+    order = [lowest[int(perm[b])] for b in range(n_bodies)]
+    u = u[len(slots) + n_bodies:]
+    cell, pitch, base0 = 1.0 / 3.0, 0.25, gap
+
+    def place(Xw, slot):
+        l, i, k = slots[slot]
+        lo, hi = Xw.min(0), Xw.max(0)
+        target = np.array([(i - 1) * cell, base0 + l * pitch, (k - 1) * cell])
+        centre = np.array([0.5 * (lo[0] + hi[0]), lo[1], 0.5 * (lo[2] + hi[2])])
+        return target - centre
+
+    kinds = ["ellipsoid", "torus", "box"]
+    for b in range(n_bodies):
+        ub = u[8 * b:8 * b + 8]
+        slot = order[b]
+        if b < n_soft:
+            kind = kinds[min(2, int(ub[0] * 3))]
+            sp = _spacing_for_count(kind, tets_per_body, 2.5, hi=0.1)
+            m, org = _solid(kind, 2.5, sp)
+            X, T = lattice_tets(m, sp, org)
+            X = jitter_interior(X, T, sp, 0.1, seed * 1000 + b)
+            X = X @ _yaw(2 * math.pi * ub[1]).T
+            X = X + place(X, slot)
+            s.tets.append(TetBody(X, T, E=1e5, nu=0.4, rho=1000.0, mu=0.5, name=f"soft_{kind}{b}"))
+            continue
+        if b < n_soft + n_convex:
+            V, F = uv_sphere_surface(0.06 + 0.04 * ub[2:5], n_seg, n_seg)
+            name = f"sphere{b}"
+        else:
+            V, F = torus_surface(0.07, 0.025, n_seg, n_seg)
+            name = f"torus{b}"
+        Rm = rotation_from_uniforms(ub[5], ub[6], ub[7])
+        Xw = V @ Rm.T
+        q = np.zeros(12)
+        q[0:3] = place(Xw, slot)
+        q[3:12] = Rm.reshape(-1)
+        s.affines.append(AffineBody(V, F, q, rho=1000.0, stiffness=1e8, mu=0.5, mode=0, name=name))
     return s
