@@ -317,9 +317,11 @@ __global__ void k_precond(Geo G, Bsr<T> S, Bsr<T> C, T* Minv_s, T* Minv_a) {
 // non-finite value marks the env with 2); the launch ends when every env has
 // stopped or after max_iter iterations.
 //
-// The iteration runs in the matrix's type (FP32 in the mixed form, where the
-// caller refines the result against FP64 residuals); the partial sums are
-// combined in FP64.  Two grid barriers per iteration: the new direction
+// The iteration runs in the matrix's type, its partial sums included (FP32 in
+// the mixed form, where the caller refines the result against FP64
+// residuals: B300's FP64 pipe is a small fraction of its FP32 rate, and
+// FP64 tree sums over every tile in every block would cost more than the
+// product itself).  Two grid barriers per iteration: the new direction
 // p_k = z_k + beta p_{k-1} is formed on the fly inside the product (p
 // double-buffered: the product reads p_{k-1} and z_k of its columns, the
 // row's owner stores p_k), so a separate direction pass and its barrier are
@@ -347,11 +349,11 @@ struct PcgArgs {
     const Real* Minv_s;
     const Real* Minv_a;
     Tiles T;
-    double* pt_rz;   // per-tile partials
-    double* pt_rz2;
-    double* pt_pq;
-    double* pt_rr;
-    double* pt_bb;
+    Real* pt_rz;     // per-tile partials
+    Real* pt_rz2;
+    Real* pt_pq;
+    Real* pt_rr;
+    Real* pt_bb;
     int* conv;       // per env: in 1 = skip; out 1 = stopped, 2 = non-finite
     int* iters;      // per env
     double tol2;
@@ -362,11 +364,29 @@ struct PcgArgs {
 // Sum of each env's tile partials into out[env], identical in every block
 // (same order).  Few envs: the whole block strides over an env's tiles and a
 // fixed tree combines the threads; many envs: one thread per env in tile order.
-__device__ __forceinline__ void env_sums(const Tiles& T, const double* part, int n_envs, double* out,
-                                         double* red) {
+// fixed-tree block sum in the solve's type (the result is valid in thread 0)
+template <class Real>
+__device__ __forceinline__ Real pcg_block_sum(Real v, Real* sh) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    Real r = 0;
+    if (w == 0) {
+        r = l < (int)(blockDim.x >> 5) ? sh[l] : Real(0);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    }
+    __syncthreads();
+    return r;
+}
+
+template <class Real>
+__device__ __forceinline__ void env_sums(const Tiles& T, const Real* part, int n_envs, double* out, Real* red) {
     if (n_envs <= 8) {
         for (int e = 0; e < n_envs; ++e) {
-            double s0 = 0.0, s1 = 0.0;
+            Real s0 = 0, s1 = 0;
             const int t0 = T.env_start[e], t1 = T.env_start[e + 1];
             int t = t0 + threadIdx.x;
             for (; t + (int)blockDim.x < t1; t += 2 * blockDim.x) {
@@ -374,14 +394,63 @@ __device__ __forceinline__ void env_sums(const Tiles& T, const double* part, int
                 s1 += __ldcg(part + t + blockDim.x);
             }
             if (t < t1) s0 += __ldcg(part + t);
-            const double v = block_sum<256>(s0 + s1, red);
-            if (threadIdx.x == 0) out[e] = v;
+            const Real v = pcg_block_sum<Real>(s0 + s1, red);
+            if (threadIdx.x == 0) out[e] = (double)v;
         }
     } else {
         for (int e = threadIdx.x; e < n_envs; e += blockDim.x) {
-            double s = 0.0;
+            Real s = 0;
             for (int t = T.env_start[e]; t < T.env_start[e + 1]; ++t) s += __ldcg(part + t);
-            out[e] = s;
+            out[e] = (double)s;
+        }
+    }
+}
+
+// env_sums of two partial arrays in one pass (the result pairs in outa, outb)
+template <class Real>
+__device__ __forceinline__ void env_sums2(const Tiles& T, const Real* pa, const Real* pb, int n_envs, double* outa,
+                                          double* outb, Real* red) {
+    if (n_envs <= 8) {
+        for (int e = 0; e < n_envs; ++e) {
+            Real sa = 0, sb = 0;
+            for (int t = T.env_start[e] + threadIdx.x; t < T.env_start[e + 1]; t += blockDim.x) {
+                sa += __ldcg(pa + t);
+                sb += __ldcg(pb + t);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                sa += __shfl_xor_sync(0xffffffffu, sa, o);
+                sb += __shfl_xor_sync(0xffffffffu, sb, o);
+            }
+            const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+            if (l == 0) {
+                red[w] = sa;
+                red[nw + w] = sb;
+            }
+            __syncthreads();
+            if (w == 0) {
+                Real ra = l < nw ? red[l] : Real(0), rb = l < nw ? red[nw + l] : Real(0);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    ra += __shfl_xor_sync(0xffffffffu, ra, o);
+                    rb += __shfl_xor_sync(0xffffffffu, rb, o);
+                }
+                if (l == 0) {
+                    outa[e] = (double)ra;
+                    outb[e] = (double)rb;
+                }
+            }
+            __syncthreads();
+        }
+    } else {
+        for (int e = threadIdx.x; e < n_envs; e += blockDim.x) {
+            Real sa = 0, sb = 0;
+            for (int t = T.env_start[e]; t < T.env_start[e + 1]; ++t) {
+                sa += __ldcg(pa + t);
+                sb += __ldcg(pb + t);
+            }
+            outa[e] = (double)sa;
+            outb[e] = (double)sb;
         }
     }
 }
@@ -400,25 +469,34 @@ __device__ __forceinline__ Real pcg_dir(const Real* z, const Real* pold, Real be
     return v;
 }
 
-// blocks k0, k0 + step, ... < k1 of a row of A times the direction
+// blocks k0, k0 + step, ... < k1 of a row of A times the direction; four
+// blocks per round so that their column and direction loads overlap
 template <class Real>
 __device__ __forceinline__ void pcg_row_part(const Bsr<Real>& A, int k0, int k1, int step, const Real* z,
                                              const Real* pold, Real beta, Real y[3]) {
-    for (int k = k0; k < k1; k += step) {
-        const Real* v = A.val + 9 * (size_t)k;
-        const size_t c = 3 * (size_t)A.col[k];
-        const Real p0 = pcg_dir(z, pold, beta, c), p1 = pcg_dir(z, pold, beta, c + 1),
-                   p2 = pcg_dir(z, pold, beta, c + 2);
-        y[0] += v[0] * p0 + v[1] * p1 + v[2] * p2;
-        y[1] += v[3] * p0 + v[4] * p1 + v[5] * p2;
-        y[2] += v[6] * p0 + v[7] * p1 + v[8] * p2;
+    constexpr int U = 4;
+    for (int k = k0; k < k1; k += U * step) {
+        int c[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) c[u] = k + u * step < k1 ? A.col[k + u * step] : -1;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (c[u] < 0) continue;
+            const Real* v = A.val + 9 * (size_t)(k + u * step);
+            const size_t o = 3 * (size_t)c[u];
+            const Real p0 = pcg_dir(z, pold, beta, o), p1 = pcg_dir(z, pold, beta, o + 1),
+                       p2 = pcg_dir(z, pold, beta, o + 2);
+            y[0] += v[0] * p0 + v[1] * p1 + v[2] * p2;
+            y[1] += v[3] * p0 + v[4] * p1 + v[5] * p2;
+            y[2] += v[6] * p0 + v[7] * p1 + v[8] * p2;
+        }
     }
 }
 
 // soft unit: z = M r on one node; returns r.z and r.r
 template <class Real>
-__device__ __forceinline__ void pcg_soft_precond(const Real* Minv_s, int n, const Real* r, Real* z, double& rz,
-                                                 double& rr) {
+__device__ __forceinline__ void pcg_soft_precond(const Real* Minv_s, int n, const Real* r, Real* z, Real& rz,
+                                                 Real& rr) {
     const Real* M = Minv_s + 9 * (size_t)n;
     const Real r0 = r[3 * (size_t)n], r1 = r[3 * (size_t)n + 1], r2 = r[3 * (size_t)n + 2];
     const Real z0 = M[0] * r0 + M[1] * r1 + M[2] * r2;
@@ -427,22 +505,22 @@ __device__ __forceinline__ void pcg_soft_precond(const Real* Minv_s, int n, cons
     z[3 * (size_t)n] = z0;
     z[3 * (size_t)n + 1] = z1;
     z[3 * (size_t)n + 2] = z2;
-    rz += (double)(r0 * z0 + r1 * z1 + r2 * z2);
-    rr += (double)(r0 * r0 + r1 * r1 + r2 * r2);
+    rz += r0 * z0 + r1 * z1 + r2 * z2;
+    rr += r0 * r0 + r1 * r1 + r2 * r2;
 }
 
 // affine unit, 12 threads: thread i computes row i of z = M r (12 x 12)
 template <class Real>
 __device__ __forceinline__ void pcg_aff_precond(const Real* Minv_a, int body, int n0, const Real* r, Real* z, int i,
-                                                double& rz, double& rr) {
+                                                Real& rz, Real& rr) {
     const Real* M = Minv_a + 144 * (size_t)body;
     const Real* rb = r + 3 * (size_t)n0;
     Real zi = 0;
 #pragma unroll
     for (int j = 0; j < 12; ++j) zi += M[12 * i + j] * rb[j];
     z[3 * (size_t)n0 + i] = zi;
-    rz += (double)(rb[i] * zi);
-    rr += (double)(rb[i] * rb[i]);
+    rz += rb[i] * zi;
+    rr += rb[i] * rb[i];
 }
 
 template <class Real>
@@ -455,45 +533,49 @@ __global__ void __launch_bounds__(256) k_pcg_persistent(PcgArgs<Real> a) {
     double* s_bb = sm + NE;       // b.b per env
     double* s_x = sm + 2 * NE;    // scratch per env (pq, then rz_new)
     double* s_y = sm + 3 * NE;    // scratch per env (rr)
-    double* s_beta = sm + 4 * NE; // beta of the next direction per env
-    int* s_conv = (int*)(sm + 5 * NE);  // 0 running, 1 stopped, 2 non-finite
-    __shared__ double red[32];
+    Real* s_alpha = reinterpret_cast<Real*>(sm + 4 * NE);  // this iteration's alpha per env
+    Real* s_beta = s_alpha + NE;                             // beta of the next direction per env
+    int* s_conv = reinterpret_cast<int*>(s_beta + NE);       // 0 running, 1 stopped, 2 non-finite
+    __shared__ double red_d[32];
+    Real* red = reinterpret_cast<Real*>(red_d);
     __shared__ int s_all;
     const Geo& G = a.G;
     const int tid = threadIdx.x;
     // init: x = 0, r = b, z = M^-1 r, previous direction 0
     for (int t = blockIdx.x; t < a.T.n; t += gridDim.x) {
         const int e = a.T.env[t];
-        double rz = 0.0, bb = 0.0;
+        Real rz = 0, bb = 0;
         if (a.conv[e] == 0) {
             if (pcg_aff_tile(G, a.T, t)) {
                 const int n0 = a.T.n0[t];
                 if (tid < 12) {
                     const size_t o = 3 * (size_t)n0 + tid;
-                    a.r[o] = (Real)a.b[o];
+                    const Real bo = (Real)a.b[o];
+                    a.r[o] = bo;
                     a.x[o] = Real(0);
                     a.p2[o] = Real(0);
-                    bb = a.b[o] * a.b[o];
+                    bb = bo * bo;
                 }
                 __syncthreads();
-                double rr_unused = 0.0;
+                Real rr_unused = 0;
                 if (tid < 12) pcg_aff_precond(a.Minv_a, G.unit_idx[a.T.u0[t]], n0, a.r, a.z, tid, rz, rr_unused);
             } else {
                 for (int n = a.T.n0[t] + tid; n < a.T.n1[t]; n += blockDim.x) {
                     for (int c = 0; c < 3; ++c) {
                         const size_t o = 3 * (size_t)n + c;
-                        a.r[o] = (Real)a.b[o];
+                        const Real bo = (Real)a.b[o];
+                        a.r[o] = bo;
                         a.x[o] = Real(0);
                         a.p2[o] = Real(0);
-                        bb += a.b[o] * a.b[o];
+                        bb += bo * bo;
                     }
-                    double rr_unused = 0.0;
+                    Real rr_unused = 0;
                     pcg_soft_precond(a.Minv_s, n, a.r, a.z, rz, rr_unused);
                 }
             }
         }
-        const double r1 = block_sum<256>(rz, red);
-        const double r2 = block_sum<256>(bb, red);
+        const Real r1 = pcg_block_sum<Real>(rz, red);
+        const Real r2 = pcg_block_sum<Real>(bb, red);
         if (tid == 0) {
             a.pt_rz[t] = r1;
             a.pt_bb[t] = r2;
@@ -506,7 +588,7 @@ __global__ void __launch_bounds__(256) k_pcg_persistent(PcgArgs<Real> a) {
     for (int e = tid; e < NE; e += blockDim.x) {
         const bool fin = isfinite(s_bb[e]) && isfinite(s_rz[e]);
         s_conv[e] = a.conv[e] ? 1 : (!fin ? 2 : (s_bb[e] > 0.0 ? 0 : 1));
-        s_beta[e] = 0.0;
+        s_beta[e] = Real(0);
     }
     __syncthreads();
     Real* pold = a.p2;  // p_{k-1}
@@ -525,28 +607,38 @@ __global__ void __launch_bounds__(256) k_pcg_persistent(PcgArgs<Real> a) {
         // p = z + beta p_old (own rows stored), q = A p, partial p.q
         for (int t = blockIdx.x; t < a.T.n; t += gridDim.x) {
             const int e = a.T.env[t];
-            double s = 0.0;
+            Real s = 0;
             if (!s_conv[e]) {
-                const Real beta = (Real)s_beta[e];
+                const Real beta = s_beta[e];
                 const int n0 = a.T.n0[t], n1 = a.T.n1[t];
                 if (pcg_aff_tile(G, a.T, t)) {
-                    // four long rows: the whole block on each, fixed-tree sums
-                    for (int n = n0; n < n1; ++n) {
-                        Real y[3] = {0, 0, 0};
-                        pcg_row_part(a.S, a.S.rowptr[n] + tid, a.S.rowptr[n + 1], (int)blockDim.x, a.z, pold, beta, y);
-                        pcg_row_part(a.C, a.C.rowptr[n] + tid, a.C.rowptr[n + 1], (int)blockDim.x, a.z, pold, beta, y);
-                        double yt[3];
-                        for (int c = 0; c < 3; ++c) yt[c] = block_sum<256>((double)y[c], red);
-                        if (tid == 0) {
-                            for (int c = 0; c < 3; ++c) {
-                                const size_t o = 3 * (size_t)n + c;
-                                const Real pn = pcg_dir(a.z, pold, beta, o);
-                                pcur[o] = pn;
-                                a.q[o] = (Real)yt[c];
-                                s += (double)pn * yt[c];
-                            }
+                    // four long rows at once, 64 threads (two warps) each:
+                    // strided partial products, a shuffle tree per warp,
+                    // then the two warps of a row added in a fixed order
+                    const int row = tid >> 6, l64 = tid & 63, w = tid >> 5;
+                    const int n = n0 + row;
+                    Real y[3] = {0, 0, 0};
+                    if (n < n1) {
+                        pcg_row_part(a.S, a.S.rowptr[n] + l64, a.S.rowptr[n + 1], 64, a.z, pold, beta, y);
+                        pcg_row_part(a.C, a.C.rowptr[n] + l64, a.C.rowptr[n + 1], 64, a.z, pold, beta, y);
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1)
+                        for (int c = 0; c < 3; ++c) y[c] += __shfl_xor_sync(0xffffffffu, y[c], o);
+                    if ((tid & 31) == 0)
+                        for (int c = 0; c < 3; ++c) red[3 * w + c] = y[c];
+                    __syncthreads();
+                    if (l64 == 0 && n < n1) {
+                        for (int c = 0; c < 3; ++c) {
+                            const size_t o = 3 * (size_t)n + c;
+                            const Real yc = red[3 * w + c] + red[3 * (w + 1) + c];
+                            const Real pn = pcg_dir(a.z, pold, beta, o);
+                            pcur[o] = pn;
+                            a.q[o] = yc;
+                            s += pn * yc;
                         }
                     }
+                    __syncthreads();
                 } else {
                     // soft rows: kPcgRowLanes lanes per row; the row loop is
                     // uniform over the block so every lane reaches the shuffles
@@ -569,27 +661,33 @@ __global__ void __launch_bounds__(256) k_pcg_persistent(PcgArgs<Real> a) {
                                 a.q[o] = y[c];
                                 d += pn * y[c];
                             }
-                            s += (double)d;
+                            s += d;
                         }
                     }
                 }
             }
-            const double r1 = block_sum<256>(s, red);
+            const Real r1 = pcg_block_sum<Real>(s, red);
             if (tid == 0) a.pt_pq[t] = r1;
         }
         grid.sync();
         env_sums(a.T, a.pt_pq, NE, s_x, red);
         __syncthreads();
-        // breakdown (p.Ap <= 0): stop with x kept; non-finite: mark the env
-        for (int e = tid; e < NE; e += blockDim.x)
-            if (!s_conv[e] && !(s_x[e] > 0.0)) s_conv[e] = isfinite(s_x[e]) ? 1 : 2;
+        // breakdown (p.Ap <= 0): stop with x kept; non-finite: mark the env;
+        // otherwise alpha, once per env
+        for (int e = tid; e < NE; e += blockDim.x) {
+            if (s_conv[e]) continue;
+            if (!(s_x[e] > 0.0))
+                s_conv[e] = isfinite(s_x[e]) ? 1 : 2;
+            else
+                s_alpha[e] = (Real)(s_rz[e] / s_x[e]);
+        }
         __syncthreads();
         // x += alpha p ; r -= alpha q ; z = M^-1 r ; partial r.z, r.r
         for (int t = blockIdx.x; t < a.T.n; t += gridDim.x) {
             const int e = a.T.env[t];
-            double rz = 0.0, rr = 0.0;
+            Real rz = 0, rr = 0;
             if (!s_conv[e]) {
-                const Real alpha = (Real)(s_rz[e] / s_x[e]);
+                const Real alpha = s_alpha[e];
                 if (pcg_aff_tile(G, a.T, t)) {
                     const int n0 = a.T.n0[t];
                     if (tid < 12) {
@@ -610,16 +708,15 @@ __global__ void __launch_bounds__(256) k_pcg_persistent(PcgArgs<Real> a) {
                     }
                 }
             }
-            const double r1 = block_sum<256>(rz, red);
-            const double r2 = block_sum<256>(rr, red);
+            const Real r1 = pcg_block_sum<Real>(rz, red);
+            const Real r2 = pcg_block_sum<Real>(rr, red);
             if (tid == 0) {
                 a.pt_rz2[t] = r1;
                 a.pt_rr[t] = r2;
             }
         }
         grid.sync();
-        env_sums(a.T, a.pt_rz2, NE, s_x, red);
-        env_sums(a.T, a.pt_rr, NE, s_y, red);
+        env_sums2(a.T, a.pt_rz2, a.pt_rr, NE, s_x, s_y, red);
         __syncthreads();
         // stop test and the next beta per env
         for (int e = tid; e < NE; e += blockDim.x) {
@@ -630,7 +727,7 @@ __global__ void __launch_bounds__(256) k_pcg_persistent(PcgArgs<Real> a) {
                 s_conv[e] = 2;
             else if (!(s_y[e] > tol2 * s_bb[e]))
                 s_conv[e] = 1;
-            s_beta[e] = s_rz[e] != 0.0 ? s_x[e] / s_rz[e] : 0.0;
+            s_beta[e] = (Real)(s_rz[e] != 0.0 ? s_x[e] / s_rz[e] : 0.0);
             s_rz[e] = s_x[e];
         }
         Real* tmp = pold;

@@ -470,16 +470,25 @@ void build(zema_scene* s) {
     }
     env_unit_start[NE] = (int)unit_kind_h.size();
     s->n_units = (int)unit_kind_h.size();
-    // PCG tiles of the grid-wide solve: <= kTileUnits consecutive soft units
-    // of one env and their node range, about four tiles per SM over the whole
-    // scene (16 to 256 units, so a block's threads each own about one unit),
-    // and one tile per affine unit
+    // PCG tiles of the grid-wide solve: one tile per affine unit, and runs of
+    // <= kTileUnits consecutive soft units of one env with their node range,
+    // sized so that all tiles together fill the resident blocks of the
+    // cooperative launch once (every SM gets the same number of blocks; 16 to
+    // 256 units, so a block's threads each own about one unit)
     int kTileUnits = 16;
     {
-        int dev = 0, nsm = 148;
-        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        int dev = 0, nsm = 148, per_f = 4, per_d = 4;
+        if (cudaGetDevice(&dev) == cudaSuccess) {
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_f, k_pcg_persistent<float>, 256, 4096);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_d, k_pcg_persistent<double>, 256, 4096);
+        }
         cudaGetLastError();
-        const int want = (int)((unit_kind_h.size() + 4 * (size_t)nsm - 1) / (4 * (size_t)nsm));
+        size_t n_soft_units = 0;
+        for (int k : unit_kind_h) n_soft_units += k == 0;
+        const long long slots = (long long)std::max(1, std::min(per_f, per_d)) * nsm - (long long)s->n_aff;
+        const size_t soft_tiles = (size_t)std::max(1LL, slots);
+        const int want = (int)((n_soft_units + soft_tiles - 1) / soft_tiles);
         kTileUnits = std::max(16, std::min(256, want));
     }
     std::vector<int> tu0, tu1, tn0, tn1, tenv, etile(NE + 1, 0);
@@ -1332,17 +1341,17 @@ int64_t pcg_t(zema_scene* s, const std::vector<int>& done_h) {
         a.Minv_s = Minv_s;
         a.Minv_a = Minv_a;
         a.T = Tiles{s->n_tiles, s->tile_u0.p, s->tile_u1.p, s->tile_n0.p, s->tile_n1.p, s->tile_env.p, s->env_tile_start.p};
-        a.pt_rz = s->pt_a.p;
-        a.pt_rz2 = s->pt_b.p;
-        a.pt_pq = s->pt_c.p;
-        a.pt_rr = s->pt_d.p;
-        a.pt_bb = s->pt_e.p;
+        a.pt_rz = (T*)s->pt_a.p;
+        a.pt_rz2 = (T*)s->pt_b.p;
+        a.pt_pq = (T*)s->pt_c.p;
+        a.pt_rr = (T*)s->pt_d.p;
+        a.pt_bb = (T*)s->pt_e.p;
         a.conv = s->conv.p;
         a.iters = s->pcg_iters.p;
         a.tol2 = s->P.pcg_rel_tol * s->P.pcg_rel_tol;
         a.tol2_env = tol2_env;
         a.max_iter = s->P.max_pcg;
-        size_t smem = 5 * (size_t)NE * sizeof(double) + (size_t)NE * sizeof(int);
+        size_t smem = 4 * (size_t)NE * sizeof(double) + 2 * (size_t)NE * sizeof(T) + (size_t)NE * sizeof(int);
         int& grid = s->P.precision == 1 ? s->pcg_grid_f : s->pcg_grid;
         if (grid == 0) {
             int dev = 0, nsm = 0, per = 0;
