@@ -289,9 +289,20 @@ zema_status zema_get_tuning(const zema_scene* s, int32_t precision, int32_t* clu
  * that start, the step is redone from x^t with the constant-velocity start
  * only, so the plain method decides every step the learned start cannot.
  *
+ * A second network, per dynamic affine body, maps 40 features of the body
+ * (the columns of A; the centre of mass relative to the env's initial
+ * bounding-box centre over its diagonal; h qdot / s and (qhat - q) / s, the A
+ * parts times the body's rest half-diagonal R; the nearest active pair
+ * touching the body over dhat, capped at 1, and its normal pointing away from
+ * the other primitive) to the change of q beyond h qdot in the same units
+ * (12).  Its correction joins the soft vertices' in the same CCD-bounded,
+ * energy-checked proposal.
+ *
  * zema_load_warmstart: blob = uint32 magic 0x5357455A, uint32 n_layers,
- * uint32 dims[n_layers + 1] (dims[0] = 13, dims[n_layers] = 3), then the
- * float32 parameters in the zema_mlp layout.  The scene copies the blob. */
+ * uint32 dims[n_layers + 1], then the float32 parameters in the zema_mlp
+ * layout.  dims[0] = 13 and dims[n_layers] = 3 load the per-vertex network;
+ * dims[0] = 40 and dims[n_layers] = 12 the per-body network; any other shape
+ * is ZEMA_ERR_INVALID_ARG.  The scene copies the blob. */
 zema_status zema_load_warmstart(zema_scene* s, const void* blob, int64_t bytes);
 /* While recording, every following step writes the features of its soft
  * vertices (rows x 13) and their scaled displacement over the step (rows x 3)
@@ -299,6 +310,12 @@ zema_status zema_load_warmstart(zema_scene* s, const void* blob, int64_t bytes);
  * node order: environments in order, bodies in the order they were added).
  * NULL / NULL stops.  cap_rows below the soft vertex count is an error. */
 zema_status zema_record_warmstart(zema_scene* s, float* features, float* targets, int64_t cap_rows);
+/* The same for the dynamic affine bodies: features (rows x 40) and the
+ * scaled change of q beyond h qdot (rows x 12), rows = dynamic affine body
+ * count in the library's order (environments in order, bodies in the order
+ * they were added).  NULL / NULL stops; cap_rows below the count is an
+ * error. */
+zema_status zema_record_warmstart_affine(zema_scene* s, float* features, float* targets, int64_t cap_rows);
 
 /* ------------------------------------------------------------------------
  * Small MLPs for the learned Newton warm start (the paper has no learned

@@ -16,6 +16,20 @@
 // kept only if the energy does not rise, so the learned start is never worse
 // in energy than the constant-velocity one; Newton then runs to the same
 // tolerance.
+//
+// Features of dynamic affine body b (40 values, FP32), for the per-body
+// network; q = (p, c1, c2, c3) with the c_k the columns of A:
+//   c1, c2, c3                 orientation (9)
+//   (p - c_env) / D_env        position relative to the env's rest bounding
+//                              box centre, over its diagonal (3)
+//   h qdot / s                 constant-velocity displacement (12)
+//   (qhat - q) / s             displacement to the inertial target (12)
+//   min(d / dhat, 1), n        nearest active pair touching the body and its
+//                              normal pointing away from the other primitive (4)
+// where the A parts are multiplied by the body's rest half-diagonal R_b, so
+// that every displacement is in metres of surface motion before the scaling
+// by s.  The network predicts the step's change of q beyond h qdot in the
+// same units (12 outputs).
 #pragma once
 #include "kernels_energy.cuh"
 
@@ -23,7 +37,18 @@ namespace zema {
 
 constexpr int kWsFeatures = 13;
 constexpr int kWsOutputs = 3;
+constexpr int kWsAffFeatures = 40;
+constexpr int kWsAffOutputs = 12;
 constexpr int kWsHalvings = 0;  // halvings of the learned correction (a single energy check)
+
+// sign of a pair's normal seen from node n (+1: the normal points away from
+// the other primitive), 0 when the node takes no part with nonzero weight
+__device__ __forceinline__ float ws_side(const Geo& G, const PairRec& r, const double* w4, int n, bool aff) {
+    float sg = 0.0f;
+    for (int k = 0; k < 4; ++k)
+        if ((G.sv_aff[r.s[k]] != 0) == aff && G.sv_node[r.s[k]] == n && w4[k] != 0.0) sg = w4[k] > 0.0 ? 1.0f : -1.0f;
+    return sg;
+}
 
 // centroid of each tet body at x: one block per body, fixed-order sums
 __global__ void k_ws_centroid(const double* x, const int* node0, const int* nv, double* c) {
@@ -51,8 +76,8 @@ __global__ void k_ws_nearest(Geo G, const double* X, const PairRec* rec, const d
     const unsigned long long key = ((unsigned long long)__float_as_uint(d) << 32) | (unsigned)i;
     for (int k = 0; k < 4; ++k) {
         const int sv = r.s[k];
-        if (w[4 * (size_t)i + k] == 0.0 || G.sv_aff[sv]) continue;
-        atomicMin(best + G.sv_node[sv], key);
+        if (w[4 * (size_t)i + k] == 0.0) continue;
+        atomicMin(best + G.sv_node[sv], key);  // soft: its node; affine: the body's first node
     }
 }
 
@@ -76,17 +101,78 @@ __global__ void k_ws_features(Geo G, const int* soft, const int* sbody, int ns, 
     if (key != ~0ull) {
         const unsigned p = (unsigned)(key & 0xffffffffull);
         dn = fminf(__uint_as_float((unsigned)(key >> 32)) / (float)G.dhat, 1.0f);
-        const PairRec r = rec[p];
-        float sg = 0.0f;
-        for (int k = 0; k < 4; ++k)
-            if (!G.sv_aff[r.s[k]] && G.sv_node[r.s[k]] == n && w[4 * (size_t)p + k] != 0.0)
-                sg = w[4 * (size_t)p + k] > 0.0 ? 1.0f : -1.0f;
+        const float sg = ws_side(G, rec[p], w + 4 * (size_t)p, n, false);
         for (int j = 0; j < 3; ++j) nv[j] = sg * (float)nrm[3 * (size_t)p + j];
     }
     o[9] = dn;
     o[10] = nv[0];
     o[11] = nv[1];
     o[12] = nv[2];
+}
+
+__global__ void k_ws_aff_features(Geo G, const int* aff, int na, const double* x, const double* v, const double* xhat,
+                                  const double* Rb, const double* env_c, const double* env_d,
+                                  const unsigned long long* best, const PairRec* rec, const double* w,
+                                  const double* nrm, double h, double sc, float* f) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= na) return;
+    const int a = aff[i], n0 = G.aff_node0[a], e = G.node_env[n0];
+    float* o = f + (size_t)kWsAffFeatures * i;
+    const double is = 1.0 / sc, R = Rb[i];
+    for (int k = 1; k < 4; ++k)
+        for (int j = 0; j < 3; ++j) o[3 * (k - 1) + j] = (float)x[3 * (size_t)(n0 + k) + j];
+    for (int j = 0; j < 3; ++j) o[9 + j] = (float)((x[3 * (size_t)n0 + j] - env_c[3 * e + j]) / env_d[e]);
+    for (int k = 0; k < 4; ++k) {
+        const double m = k == 0 ? is : R * is;
+        for (int j = 0; j < 3; ++j) {
+            const size_t q = 3 * (size_t)(n0 + k) + j;
+            o[12 + 3 * k + j] = (float)(v[q] * h * m);
+            o[24 + 3 * k + j] = (float)((xhat[q] - x[q]) * m);
+        }
+    }
+    const unsigned long long key = best[n0];
+    float dn = 1.0f, nv[3] = {0.0f, 0.0f, 0.0f};
+    if (key != ~0ull) {
+        const unsigned p = (unsigned)(key & 0xffffffffull);
+        dn = fminf(__uint_as_float((unsigned)(key >> 32)) / (float)G.dhat, 1.0f);
+        const float sg = ws_side(G, rec[p], w + 4 * (size_t)p, n0, true);
+        for (int j = 0; j < 3; ++j) nv[j] = sg * (float)nrm[3 * (size_t)p + j];
+    }
+    o[36] = dn;
+    o[37] = nv[0];
+    o[38] = nv[1];
+    o[39] = nv[2];
+}
+
+// correction direction of the dynamic affine bodies: dir(q) += s y, the A
+// part divided by R_b
+__global__ void k_ws_aff_direction(Geo G, const int* aff, int na, const double* Rb, const float* out, double sc,
+                                   double* dir) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= na) return;
+    const int n0 = G.aff_node0[aff[i]];
+    for (int k = 0; k < 4; ++k) {
+        const double m = k == 0 ? sc : sc / Rb[i];
+        for (int j = 0; j < 3; ++j)
+            dir[3 * (size_t)(n0 + k) + j] += m * (double)out[(size_t)kWsAffOutputs * i + 3 * k + j];
+    }
+}
+
+// training target of the per-body network: the change of q beyond h qdot^t
+// in the feature units (features 12..23 hold h qdot^t in those units)
+__global__ void k_ws_aff_target(Geo G, const int* aff, int na, const double* Rb, const double* x1, const double* x0,
+                                const float* feat, double sc, float* t) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= na) return;
+    const int n0 = G.aff_node0[aff[i]];
+    for (int k = 0; k < 4; ++k) {
+        const double m = k == 0 ? 1.0 / sc : Rb[i] / sc;
+        for (int j = 0; j < 3; ++j) {
+            const size_t q = 3 * (size_t)(n0 + k) + j;
+            t[(size_t)kWsAffOutputs * i + 3 * k + j] =
+                (float)((x1[q] - x0[q]) * m - (double)feat[(size_t)kWsAffFeatures * i + 12 + 3 * k + j]);
+        }
+    }
 }
 
 // correction direction of the soft vertices: dir += s y

@@ -128,7 +128,13 @@ struct zema_scene {
     // learned warm start: network, soft-vertex list (node order) with their
     // tet body, per-body node range / rest half-diagonal / centroid, features
     Mlp* ws_net = nullptr;
-    int ws_ns = 0, ws_nb = 0;
+    Mlp* ws_anet = nullptr;  // per dynamic affine body (40 -> 12)
+    int ws_ns = 0, ws_nb = 0, ws_na = 0;
+    DBuf<int> ws_aff;                       // dynamic affine bodies (device index)
+    DBuf<double> ws_aR, ws_envc, ws_envd;   // their rest half-diagonals; env bbox centres and diagonals
+    DBuf<float> ws_afeat, ws_aout;
+    float* rec_afeat = nullptr;  // caller's device buffers while recording the affine rows
+    float* rec_atarg = nullptr;
     DBuf<int> ws_soft, ws_body, tb_node0, tb_nv;
     DBuf<double> tb_R, tb_c;
     DBuf<unsigned long long> ws_best;
@@ -138,6 +144,7 @@ struct zema_scene {
 
     ~zema_scene() {
         delete ws_net;
+        delete ws_anet;
         if (h32) cudaFreeHost(h32);
         if (hd) cudaFreeHost(hd);
         if (hi) cudaFreeHost(hi);
@@ -714,8 +721,9 @@ void build(zema_scene* s) {
         for (int k = 0; k < 12; ++k) qt_h[12 * a + k] = s->ain[aff_perm[a]].q0[k];
     up(s, s->qtarget, qt_h);
     up(s, s->lamA, lam_h);
-    // ---- per-env bbox diagonal of the initial state
+    // ---- per-env bbox diagonal (and centre) of the initial state
     s->diag_h.assign(NE, 0.0);
+    std::vector<double> envc_h(3 * (size_t)NE, 0.0);
     for (int e = 0; e < NE; ++e) {
         double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
         auto acc = [&](const double* p) {
@@ -739,7 +747,10 @@ void build(zema_scene* s) {
                 }
             }
         double d2 = 0.0;
-        for (int j = 0; j < 3; ++j) d2 += (hi[j] - lo[j]) * (hi[j] - lo[j]);
+        for (int j = 0; j < 3; ++j) {
+            d2 += (hi[j] - lo[j]) * (hi[j] - lo[j]);
+            envc_h[3 * e + j] = 0.5 * (lo[j] + hi[j]);
+        }
         s->diag_h[e] = std::sqrt(d2);
     }
     s->tol_h.assign(NE, 0.0);
@@ -802,6 +813,31 @@ void build(zema_scene* s) {
         s->ws_best.ensure(A, (size_t)nN + 1);
         s->ws_feat.ensure(A, (size_t)kWsFeatures * s->ws_ns + kWsFeatures);
         s->ws_out.ensure(A, (size_t)kWsOutputs * s->ws_ns + kWsOutputs);
+        // dynamic affine bodies for the per-body network
+        std::vector<int> aff;
+        std::vector<double> aR, envd(s->diag_h);
+        for (int a = 0; a < s->n_aff; ++a) {
+            const AffIn& B = s->ain[aff_perm[a]];
+            if (B.mode != 0) continue;
+            double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+            for (size_t k = 0; k < B.V.size() / 3; ++k)
+                for (int j = 0; j < 3; ++j) {
+                    lo[j] = std::min(lo[j], B.V[3 * k + j]);
+                    hi[j] = std::max(hi[j], B.V[3 * k + j]);
+                }
+            double d2 = 0.0;
+            for (int j = 0; j < 3; ++j) d2 += (hi[j] - lo[j]) * (hi[j] - lo[j]);
+            aff.push_back(a);
+            aR.push_back(std::max(0.5 * std::sqrt(d2), 1e-12));
+        }
+        for (double& d : envd) d = std::max(d, 1e-12);
+        s->ws_na = (int)aff.size();
+        up(s, s->ws_aff, aff);
+        up(s, s->ws_aR, aR);
+        up(s, s->ws_envc, envc_h);
+        up(s, s->ws_envd, envd);
+        s->ws_afeat.ensure(A, (size_t)kWsAffFeatures * s->ws_na + kWsAffFeatures);
+        s->ws_aout.ensure(A, (size_t)kWsAffOutputs * s->ws_na + kWsAffOutputs);
     }
     // kappa: user value or pending rule
     std::vector<double> kap(NE, s->P.kappa > 0 ? s->P.kappa : 0.0);
@@ -1504,9 +1540,10 @@ void step_norm(zema_scene* s) {
 // E(x + alpha dir) <= E(x) per env.  On success x is advanced.  Returns the
 // number of halvings, or -1 when an env fails.
 int line_search(zema_scene* s, const double* dir, const std::vector<int>& done_h, bool warm,
-                std::vector<int>* accepted, int warm_halvings = 0) {
+                std::vector<int>* accepted, int warm_halvings = 0, bool strict = false) {
     // warm-start proposals get warm_halvings halvings (default: a single energy
-    // check), Newton steps up to 60
+    // check), Newton steps up to 60; strict: a step must lower the energy
+    // (the learned correction), otherwise it may also keep it equal
     const int max_halvings = warm ? warm_halvings : 60;
     cudaStream_t st = s->st;
     Geo& G = s->G;
@@ -1558,7 +1595,7 @@ int line_search(zema_scene* s, const double* dir, const std::vector<int>& done_h
         bool all = true;
         for (int e = 0; e < NE; ++e) {
             if (acc[e]) continue;
-            if (s->hd[e] <= E0[e]) {
+            if (strict ? s->hd[e] < E0[e] : s->hd[e] <= E0[e]) {
                 acc[e] = 1;
             } else if (k < max_halvings) {
                 alpha[e] *= 0.5;
@@ -1707,19 +1744,28 @@ double ws_scale(const zema_scene* s) {
     return s->P.dt * s->P.dt * (gn > 0.0 ? gn : 9.81);
 }
 
-// warm-start features of the soft vertices at x^t into s->ws_feat (needs the
-// predictor and the lagged pairs of this step)
+// warm-start features at x^t of the soft vertices into s->ws_feat and of the
+// dynamic affine bodies into s->ws_afeat (needs the predictor and the lagged
+// pairs of this step)
 void ws_features(zema_scene* s) {
     cudaStream_t st = s->st;
-    if (!s->ws_ns) return;
+    if (!s->ws_ns && !s->ws_na) return;
     ZCHECK(cudaMemsetAsync(s->ws_best.p, 0xFF, (size_t)s->n_nodes * sizeof(unsigned long long), st));
-    ZL(k_ws_centroid, s->ws_nb, kRedThreads, 0, st)(s->x.p, s->tb_node0.p, s->tb_nv.p, s->tb_c.p);
     if (s->n_lag)
         ZL(k_ws_nearest, div_up(s->n_lag, 128), 128, 0, st)(s->G, s->Xt.p, s->lag.p, s->lag_w.p, (int)s->n_lag,
                                                            s->ws_best.p);
-    ZL(k_ws_features, div_up(s->ws_ns, 128), 128, 0, st)(s->G, s->ws_soft.p, s->ws_body.p, s->ws_ns, s->x.p, s->v.p,
-                                                        s->xhat.p, s->tb_c.p, s->tb_R.p, s->ws_best.p, s->lag.p,
-                                                        s->lag_w.p, s->lag_n.p, s->P.dt, ws_scale(s), s->ws_feat.p);
+    if (s->ws_ns) {
+        ZL(k_ws_centroid, s->ws_nb, kRedThreads, 0, st)(s->x.p, s->tb_node0.p, s->tb_nv.p, s->tb_c.p);
+        ZL(k_ws_features, div_up(s->ws_ns, 128), 128, 0, st)(s->G, s->ws_soft.p, s->ws_body.p, s->ws_ns, s->x.p,
+                                                            s->v.p, s->xhat.p, s->tb_c.p, s->tb_R.p, s->ws_best.p,
+                                                            s->lag.p, s->lag_w.p, s->lag_n.p, s->P.dt, ws_scale(s),
+                                                            s->ws_feat.p);
+    }
+    if (s->ws_na)
+        ZL(k_ws_aff_features, div_up(s->ws_na, 64), 64, 0, st)(s->G, s->ws_aff.p, s->ws_na, s->x.p, s->v.p,
+                                                              s->xhat.p, s->ws_aR.p, s->ws_envc.p, s->ws_envd.p,
+                                                              s->ws_best.p, s->lag.p, s->lag_w.p, s->lag_n.p,
+                                                              s->P.dt, ws_scale(s), s->ws_afeat.p);
     ZLAUNCH();
 }
 
@@ -1764,12 +1810,18 @@ void do_step(zema_scene* s) {
     // energy further), so the learned start is never worse in energy than
     // the constant-velocity one
     W.dirw.ensure(&s->A, n3 + 3);
-    const bool learned = s->P.warm_start == 1 && s->ws_net && s->ws_ns;
-    if (learned || s->rec_feat) ws_features(s);
+    const bool learned_soft = s->P.warm_start == 1 && s->ws_net && s->ws_ns;
+    const bool learned_aff = s->P.warm_start == 1 && s->ws_anet && s->ws_na;
+    const bool learned = learned_soft || learned_aff;
+    if (learned || s->rec_feat || s->rec_afeat) ws_features(s);
     if (s->rec_feat && s->ws_ns)
         ZCHECK(cudaMemcpyAsync(s->rec_feat, s->ws_feat.p, (size_t)kWsFeatures * s->ws_ns * sizeof(float),
                                cudaMemcpyDeviceToDevice, st));
-    if (learned) s->ws_net->forward(s->ws_feat.p, s->ws_ns, s->ws_out.p);
+    if (s->rec_afeat && s->ws_na)
+        ZCHECK(cudaMemcpyAsync(s->rec_afeat, s->ws_afeat.p, (size_t)kWsAffFeatures * s->ws_na * sizeof(float),
+                               cudaMemcpyDeviceToDevice, st));
+    if (learned_soft) s->ws_net->forward(s->ws_feat.p, s->ws_ns, s->ws_out.p);
+    if (learned_aff) s->ws_anet->forward(s->ws_afeat.p, s->ws_na, s->ws_aout.p);
     // one attempt at the step from x^t: warm start, then Newton with the
     // kinematic augmented-Lagrangian rounds; returns the AL rounds
     auto solve = [&](bool use_learned) -> int {
@@ -1779,11 +1831,15 @@ void do_step(zema_scene* s) {
         line_search(s, W.dirw.p, done, true, &acc);
         if (use_learned) {
             ZCHECK(cudaMemsetAsync(W.dirw.p, 0, n3 * sizeof(double), st));
-            ZL(k_ws_direction, div_up(s->ws_ns, 128), 128, 0, st)(s->ws_soft.p, s->ws_ns, s->ws_out.p, ws_scale(s),
-                                                                 W.dirw.p);
+            if (learned_soft)
+                ZL(k_ws_direction, div_up(s->ws_ns, 128), 128, 0, st)(s->ws_soft.p, s->ws_ns, s->ws_out.p,
+                                                                     ws_scale(s), W.dirw.p);
+            if (learned_aff)
+                ZL(k_ws_aff_direction, div_up(s->ws_na, 64), 64, 0, st)(G, s->ws_aff.p, s->ws_na, s->ws_aR.p,
+                                                                       s->ws_aout.p, ws_scale(s), W.dirw.p);
             ZLAUNCH();
             std::vector<int> acc2;
-            line_search(s, W.dirw.p, done, true, &acc2, kWsHalvings);
+            line_search(s, W.dirw.p, done, true, &acc2, kWsHalvings, true);
             for (int e = 0; e < NE; ++e) s->S.warm_learned += acc2[e];
         }
         for (int e = 0; e < NE; ++e) s->S.warm_accepted += acc[e];
@@ -1882,6 +1938,11 @@ void do_step(zema_scene* s) {
     if (s->rec_targ && s->ws_ns) {
         ZL(k_ws_target, div_up(s->ws_ns, 128), 128, 0, st)(s->ws_soft.p, s->ws_ns, s->x.p, s->xt.p, s->ws_feat.p,
                                                           ws_scale(s), s->rec_targ);
+        ZLAUNCH();
+    }
+    if (s->rec_atarg && s->ws_na) {
+        ZL(k_ws_aff_target, div_up(s->ws_na, 64), 64, 0, st)(G, s->ws_aff.p, s->ws_na, s->ws_aR.p, s->x.p, s->xt.p,
+                                                            s->ws_afeat.p, ws_scale(s), s->rec_atarg);
         ZLAUNCH();
     }
     std::vector<double> kap(NE), kmin(NE);
@@ -2307,7 +2368,8 @@ zema_status zema_load_warmstart(zema_scene* s, const void* blob, int64_t bytes) 
     if (L < 1 || L > 16 || bytes < (int64_t)(4 * (L + 3))) return ZEMA_ERR_INVALID_ARG;
     std::vector<int> dims(L + 1);
     for (uint32_t l = 0; l <= L; ++l) dims[l] = (int)h[2 + l];
-    if (dims[0] != kWsFeatures || dims[L] != kWsOutputs) return ZEMA_ERR_INVALID_ARG;
+    const bool per_body = dims[0] == kWsAffFeatures && dims[L] == kWsAffOutputs;
+    if (!per_body && (dims[0] != kWsFeatures || dims[L] != kWsOutputs)) return ZEMA_ERR_INVALID_ARG;
     size_t np = 0;
     for (uint32_t l = 0; l < L; ++l) {
         if (dims[l] < 1 || dims[l] > 4096 || dims[l + 1] < 1 || dims[l + 1] > 4096) return ZEMA_ERR_INVALID_ARG;
@@ -2320,8 +2382,9 @@ zema_status zema_load_warmstart(zema_scene* s, const void* blob, int64_t bytes) 
         ZCHECK(cudaMemcpyAsync(net->theta.p, th, np * sizeof(float), cudaMemcpyHostToDevice, s->st));
         net->refresh_bf16();
         ZCHECK(cudaStreamSynchronize(s->st));
-        delete s->ws_net;
-        s->ws_net = net;
+        Mlp*& slot = per_body ? s->ws_anet : s->ws_net;
+        delete slot;
+        slot = net;
         return ZEMA_OK;
     }
     ZEMA_CATCH(s)
@@ -2336,6 +2399,18 @@ zema_status zema_record_warmstart(zema_scene* s, float* features, float* targets
     if (features && cap_rows < s->ws_ns) return ZEMA_ERR_INVALID_ARG;
     s->rec_feat = features;
     s->rec_targ = targets;
+    return ZEMA_OK;
+}
+
+zema_status zema_record_warmstart_affine(zema_scene* s, float* features, float* targets, int64_t cap_rows) {
+    if (!s || (features == nullptr) != (targets == nullptr)) return ZEMA_ERR_INVALID_ARG;
+    if (!s->finalized) {
+        zema_status r = zema_finalize(s);
+        if (r != ZEMA_OK) return r;
+    }
+    if (features && cap_rows < s->ws_na) return ZEMA_ERR_INVALID_ARG;
+    s->rec_afeat = features;
+    s->rec_atarg = targets;
     return ZEMA_OK;
 }
 

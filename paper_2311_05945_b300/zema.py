@@ -111,6 +111,7 @@ def lib():
     L.zema_autotune.argtypes = [C.c_void_p]
     L.zema_get_tuning.argtypes = [C.c_void_p, C.c_int32, IP, IP, FP, C.c_int32, IP]
     L.zema_record_warmstart.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]
+    L.zema_record_warmstart_affine.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]
     L.zema_mlp_create.argtypes = [IP, C.c_int32, C.c_uint64, C.c_void_p, C.POINTER(C.c_void_p)]
     L.zema_mlp_destroy.argtypes = [C.c_void_p]
     L.zema_mlp_destroy.restype = None
@@ -266,7 +267,8 @@ class Scene:
         return cs.value, {int(cand[i]): float(ms[i]) for i in range(n.value)}
 
     def load_warmstart(self, dims, theta):
-        """Load the learned warm-start network (dims[0] = 13, dims[-1] = 3)."""
+        """Load a learned warm-start network: per soft vertex (dims[0] = 13,
+        dims[-1] = 3) or per dynamic affine body (dims[0] = 40, dims[-1] = 12)."""
         blob = warmstart_blob(dims, theta)
         _check(lib().zema_load_warmstart(self.h, blob.ctypes.data_as(C.c_void_p), blob.nbytes), self.h)
 
@@ -279,6 +281,16 @@ class Scene:
         rows = min(features.shape[0], targets.shape[0])
         _check(lib().zema_record_warmstart(self.h, C.c_void_p(features.data_ptr()), C.c_void_p(targets.data_ptr()),
                                            rows), self.h)
+
+    def record_warmstart_affine(self, features=None, targets=None):
+        """Record features (rows x 40) and scaled changes of q (rows x 12) of
+        the dynamic affine bodies into CUDA float32 tensors during later steps."""
+        if features is None:
+            _check(lib().zema_record_warmstart_affine(self.h, None, None, 0), self.h)
+            return
+        rows = min(features.shape[0], targets.shape[0])
+        _check(lib().zema_record_warmstart_affine(self.h, C.c_void_p(features.data_ptr()),
+                                                  C.c_void_p(targets.data_ptr()), rows), self.h)
 
     def tet_body_id(self, i):
         return self.body_ids[i]
