@@ -161,6 +161,46 @@ __global__ void k_scan_add(uint32_t* out, size_t n, const uint32_t* offs, const 
 
 __global__ void k_set_total_zero(uint32_t* out) { out[0] = 0; }
 
+// one CTA scans n <= SCAN1_T * SCAN1_PER elements (each thread a contiguous
+// run of ceil(n / SCAN1_T)), out[n] = total: one launch instead of the
+// three of the multi-block scan for mid-sized arrays
+constexpr int SCAN1_T = 1024;
+constexpr int SCAN1_PER = 32;
+__global__ void __launch_bounds__(SCAN1_T) k_scan_single(const uint32_t* in, uint32_t* out, int n) {
+    __shared__ uint32_t wsum[SCAN1_T / 32];
+    const int per = (n + SCAN1_T - 1) / SCAN1_T;
+    const int b = threadIdx.x * per, e = min(n, b + per);
+    uint32_t s = 0;
+    for (int i = b; i < e; ++i) s += in[i];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t inc = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) wsum[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        const uint32_t ws = wsum[lane];
+        uint32_t wi = ws;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += t;
+        }
+        wsum[lane] = wi - ws;  // exclusive warp offsets
+        if (lane == 31) out[n] = wi;
+    }
+    __syncthreads();
+    uint32_t run = wsum[w] + inc - s;
+    for (int i = b; i < e; ++i) {
+        const uint32_t v = in[i];
+        out[i] = run;
+        run += v;
+    }
+}
+
 size_t scan_tmp_size(size_t n) {
     size_t total = 0;
     size_t m = n;
@@ -189,6 +229,11 @@ static void scan_rec(const uint32_t* in, uint32_t* out, size_t n, uint32_t* tmp,
 void exclusive_scan(const uint32_t* in, uint32_t* out, size_t n, uint32_t* tmp, cudaStream_t st) {
     if (n == 0) {
         ZL(k_set_total_zero, 1, 1, 0, st)(out);
+        ZLAUNCH();
+        return;
+    }
+    if (n > SCAN_TILE && n <= (size_t)SCAN1_T * SCAN1_PER) {
+        ZL(k_scan_single, 1, SCAN1_T, 0, st)(in, out, (int)n);
         ZLAUNCH();
         return;
     }

@@ -100,3 +100,39 @@ def test_empty_and_deterministic():
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])  # same order, run to run
     pt, ee = Z.candidates_raw(P[:0], svb[:0], bc, be, e[:0], t[:0], 0.01)
     assert len(pt) == 0 and len(ee) == 0
+
+
+def scene_surface(s):
+    """Surface positions and connectivity of a scene's initial state."""
+    o = __import__("oracle.oracle", fromlist=["Oracle"]).Oracle(s)
+    sv, e, t = o.surface()
+    soft = np.concatenate([o.tet_positions(i) for i in range(len(s.tets))])
+    P = np.zeros((len(sv), 3))
+    for i, (b, aff, idx) in enumerate(sv):
+        kind, k = s.body_order()[b]
+        if kind == "tet":
+            P[i] = soft[idx]
+        else:
+            q = o.get_state(b)[:12]
+            P[i] = q[3:].reshape(3, 3) @ s.affines[k].V[idx] + q[:3]
+    order = s.body_order()
+    bclass = np.array([0 if k == "tet" else 1 + s.affines[i].mode for k, i in order], dtype=np.int32)
+    benv = np.array([s.tets[i].env if k == "tet" else s.affines[i].env for k, i in order], dtype=np.int32)
+    return P, sv[:, 0].copy(), bclass, benv, e, t
+
+
+@pytest.mark.parametrize("name", ["c2", "c3x4"])
+def test_large_surfaces_bit_exact(name):
+    # ~10k primitives (the grasp: counts and flags scanned by the single-CTA
+    # scan) and ~40k (four batched envs: the multi-block scan)
+    from paper_2311_05945_b300 import zema as Z
+    s = S.scene_c2() if name == "c2" else S.scene_c3(n_envs=4, n_steps=1)
+    P, svb, bc, be, e, t = scene_surface(s)
+    n_prims = len(t) + len(e)
+    assert (4096 < n_prims <= 32768) if name == "c2" else n_prims > 32768
+    for infl in (1e-3, 4e-3):
+        pt, ee = Z.candidates_raw(P, svb, bc, be, e, t, infl)
+        spt, see = oracle_sets(P, svb, bc, be, e, t, infl)
+        assert set(map(tuple, pt)) == spt and len(pt) == len(spt)
+        assert set(map(tuple, ee)) == see and len(ee) == len(see)
+    assert len(spt) > 0
