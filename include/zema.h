@@ -304,6 +304,16 @@ zema_status zema_get_tuning(const zema_scene* s, int32_t precision, int32_t* clu
  * dims[0] = 40 and dims[n_layers] = 12 the per-body network; any other shape
  * is ZEMA_ERR_INVALID_ARG.  The scene copies the blob. */
 zema_status zema_load_warmstart(zema_scene* s, const void* blob, int64_t bytes);
+/* Contact force sensing (paper Sec. "Contact Force Sensing"): for every body
+ * (caller ids 0..n_bodies-1) the resultant barrier contact force at the
+ * current state, forces[3 b .. 3 b + 2] = (1 / h^2) sum over the body's
+ * surface vertices v of dB/dx_v, in newtons.  B is the barrier term of the
+ * incremental potential (kappa e b(d) over the pairs with d < dhat, found by
+ * a fresh broad phase at the current positions); the force the contacts
+ * exert on the body is the negative of this vector.  Friction is not
+ * included.  cap (doubles) below 3 n_bodies is ZEMA_ERR_INVALID_ARG. */
+zema_status zema_contact_forces(zema_scene* s, double* forces, int64_t cap);
+
 /* While recording, every following step writes the features of its soft
  * vertices (rows x 13) and their scaled displacement over the step (rows x 3)
  * into the caller's device buffers (rows = soft vertex count; the library's

@@ -518,6 +518,38 @@ __global__ void k_barrier_energy(Geo G, const double* X, const PairRec* rec, con
         part_slot(part, ET_BARRIER, G.n_envs, env));
 }
 
+// Contact force sensing: per body b (one block), the sum over b's surface
+// vertices of the barrier gradient dB/dx_v of the active pairs of b's env,
+// divided by h^2 (B is the h^2-scaled barrier of the incremental potential,
+// so the result is in newtons; the force the contacts exert on the body is
+// its negative).  Fixed-order block sum: bit-reproducible.
+__global__ void k_body_contact_force(Geo G, const double* X, const PairRec* rec, const uint32_t* env_off,
+                                     const int* body_env, const double* kappa_env, double inv_h2, double* force) {
+    __shared__ double sh[32];
+    const int b = blockIdx.x, e = body_env[b];
+    const double kap = kappa_env[e];
+    double f[3] = {0.0, 0.0, 0.0};
+    for (int i = (int)env_off[e] + threadIdx.x; i < (int)env_off[e + 1]; i += blockDim.x) {
+        const PairRec r = rec[i];
+        bool touch = false;
+        for (int k = 0; k < 4; ++k) touch |= G.sv_body[r.s[k]] == b;
+        if (!touch) continue;
+        V3 x[4];
+        for (int k = 0; k < 4; ++k) x[k] = ld3(X + 3 * (size_t)r.s[k]);
+        double E, g12[12];
+        if (!pair_barrier<double>(x, r.is_ee != 0, G.dhat, kap, pair_eps_x(G, r), E, g12, SMat<12, double>{nullptr, 0},
+                                  false))
+            continue;
+        for (int k = 0; k < 4; ++k)
+            if (G.sv_body[r.s[k]] == b)
+                for (int j = 0; j < 3; ++j) f[j] += g12[3 * k + j];
+    }
+    for (int j = 0; j < 3; ++j) {
+        const double t = block_sum<128>(f[j], sh);
+        if (threadIdx.x == 0) force[3 * b + j] = t * inv_h2;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Lagged friction (Eq. 9-10)
 // ---------------------------------------------------------------------------

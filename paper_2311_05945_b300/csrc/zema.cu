@@ -133,6 +133,8 @@ struct zema_scene {
     DBuf<int> ws_aff;                       // dynamic affine bodies (device index)
     DBuf<double> ws_aR, ws_envc, ws_envd;   // their rest half-diagonals; env bbox centres and diagonals
     DBuf<float> ws_afeat, ws_aout;
+    DBuf<int> body_env;      // env of every body (caller ids), for force sensing
+    DBuf<double> body_force;
     float* rec_afeat = nullptr;  // caller's device buffers while recording the affine rows
     float* rec_atarg = nullptr;
     DBuf<int> ws_soft, ws_body, tb_node0, tb_nv;
@@ -2400,6 +2402,37 @@ zema_status zema_record_warmstart(zema_scene* s, float* features, float* targets
     s->rec_feat = features;
     s->rec_targ = targets;
     return ZEMA_OK;
+}
+
+zema_status zema_contact_forces(zema_scene* s, double* forces, int64_t cap) {
+    if (s) set_current_stream(s->st);
+    if (!s || !forces || cap < 3 * (int64_t)s->bodies.size()) return ZEMA_ERR_INVALID_ARG;
+    if (!s->finalized) {
+        zema_status r = zema_finalize(s);
+        if (r != ZEMA_OK) return r;
+    }
+    ZEMA_TRY(s) {
+        cudaStream_t st = s->st;
+        const int nb = (int)s->bodies.size();
+        if (s->body_env.cap == 0) {
+            std::vector<int> be(nb);
+            for (int b = 0; b < nb; ++b)
+                be[b] = s->bodies[b].first == 0 ? s->tin[s->bodies[b].second].env : s->ain[s->bodies[b].second].env;
+            up(s, s->body_env, be);
+        }
+        s->body_force.ensure(&s->A, 3 * (size_t)nb + 3);
+        // active pairs at the current positions (fresh broad phase)
+        ZL(k_sv_pos, div_up(s->n_sv, TB), TB, 0, st)(s->G, s->x.p, s->X.p);
+        ZLAUNCH();
+        active_pairs(s, s->X.p, false);
+        ZL(k_body_contact_force, nb, 128, 0, st)(s->G, s->X.p, s->act.p, s->act_env.p, s->body_env.p, s->kappa.p,
+                                                1.0 / (s->P.dt * s->P.dt), s->body_force.p);
+        ZLAUNCH();
+        ZCHECK(cudaMemcpyAsync(forces, s->body_force.p, 3 * (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+        ZCHECK(cudaStreamSynchronize(st));
+        return ZEMA_OK;
+    }
+    ZEMA_CATCH(s)
 }
 
 zema_status zema_record_warmstart_affine(zema_scene* s, float* features, float* targets, int64_t cap_rows) {

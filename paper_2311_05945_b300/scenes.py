@@ -243,6 +243,8 @@ class Scene:
     n_steps: int = 1
     # script(step) -> {affine index: q_target (12,)} for the state at step+1
     script: Optional[Callable[[int], Dict[int, np.ndarray]]] = None
+    # grasp scenes: (affine index, closing sign along z, q0) of every finger
+    fingers: list = field(default_factory=list)
 
     def body_order(self):
         """(kind, index) in the order bodies are added: tets first, then affines."""
@@ -423,6 +425,7 @@ def scene_c2(n_steps: int = 300, finger_subdiv: int = 9, precision: int = 0) -> 
     fingers = grasp_env(s, 0, "ellipsoid", 0.004, seed=2, E=5e4, nu=0.45, mu=0.8,
                         offset=(0.0, 0.0, 0.0), finger_subdiv=finger_subdiv)
     s.script = grasp_script(fingers, p.dt)
+    s.fingers = fingers
     return s
 
 
@@ -447,6 +450,7 @@ def scene_c3(n_envs: int = 256, n_steps: int = 200, min_tets=2000, max_tets=2000
         allf += grasp_env(s, i, kind, sp, seed=seed0 + i, E=E, nu=0.45, mu=mu,
                           offset=(0.5 * i, 0.0, 0.0), finger_subdiv=finger_subdiv)
     s.script = grasp_script(allf, p.dt)
+    s.fingers = allf
     return s
 
 

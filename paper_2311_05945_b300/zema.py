@@ -112,6 +112,7 @@ def lib():
     L.zema_get_tuning.argtypes = [C.c_void_p, C.c_int32, IP, IP, FP, C.c_int32, IP]
     L.zema_record_warmstart.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]
     L.zema_record_warmstart_affine.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]
+    L.zema_contact_forces.argtypes = [C.c_void_p, DP, C.c_int64]
     L.zema_mlp_create.argtypes = [IP, C.c_int32, C.c_uint64, C.c_void_p, C.POINTER(C.c_void_p)]
     L.zema_mlp_destroy.argtypes = [C.c_void_p]
     L.zema_mlp_destroy.restype = None
@@ -282,6 +283,15 @@ class Scene:
         _check(lib().zema_record_warmstart(self.h, C.c_void_p(features.data_ptr()), C.c_void_p(targets.data_ptr()),
                                            rows), self.h)
 
+    def contact_forces(self) -> np.ndarray:
+        """(n_bodies, 3) barrier contact force of every body at the current
+        state, in newtons (gradient convention: the force on the body is the
+        negative)."""
+        n = len(self.body_ids)
+        out = np.zeros(3 * n, dtype=np.float64)
+        _check(lib().zema_contact_forces(self.h, _dp(out), out.size), self.h)
+        return out.reshape(n, 3)
+
     def record_warmstart_affine(self, features=None, targets=None):
         """Record features (rows x 40) and scaled changes of q (rows x 12) of
         the dynamic affine bodies into CUDA float32 tensors during later steps."""
@@ -297,6 +307,11 @@ class Scene:
 
     def affine_body_id(self, i):
         return self.body_ids[self.n_tet + i]
+
+    def set_kinematic_target(self, affine_index, q):
+        """Target state q (12,) of a kinematic affine body for the next step."""
+        qq = _d(q)
+        _check(lib().zema_set_kinematic_target(self.h, self.affine_body_id(affine_index), _dp(qq)), self.h)
 
     def apply_script(self):
         if self.scene.script is None:
