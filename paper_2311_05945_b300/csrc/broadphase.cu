@@ -216,6 +216,38 @@ __device__ __forceinline__ bool ee_ok(const BPView& v, int a, int b) {
     return pair_ok(v, A.x, B.x);
 }
 
+// env of a query (kind 0: point, 1: edge)
+__device__ __forceinline__ int query_env(const BPView& v, int kind, int q) {
+    return v.sv_env[kind == 0 ? q : v.edges[q].x];
+}
+
+// entry range [lo, hi) of a query's env (kind 0 queries meet triangles, kind
+// 1 edges); the whole table when the primitives are not ordered by env
+__device__ __forceinline__ void env_entries(const BPView& v, int kind, int q, int n_all, int& lo, int& hi) {
+    const int* st = kind == 0 ? v.env_tri_start : v.env_edge_start;
+    if (!st) {
+        lo = 0;
+        hi = n_all;
+        return;
+    }
+    const int e = query_env(v, kind, q);
+    lo = st[e];
+    hi = st[e + 1];
+}
+
+// first index k of the ascending list a[0..n) with a[k] >= x
+__device__ __forceinline__ int lower_bound_i(const int* a, int n, int x) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int m = (lo + hi) >> 1;
+        if (a[m] < x)
+            lo = m + 1;
+        else
+            hi = m;
+    }
+    return lo;
+}
+
 struct Table {
     const uint64_t* ecell;
     const int* eprim;
@@ -287,11 +319,19 @@ __global__ void k_query(BPView v, int kind, int nq, const double* qbox, const do
                     emit(hit, e);
                 }
             }
-    for (int k0 = 0; k0 < nbig; k0 += kQueryLanes) {
+    // the oversize entries (ascending ids) of the query's env
+    int b_lo = 0, b_hi = nbig;
+    if (v.env_tri_start) {
+        int lo, hi;
+        env_entries(v, kind, q, n_entries_all, lo, hi);
+        b_lo = lower_bound_i(big, nbig, lo);
+        b_hi = lower_bound_i(big, nbig, hi);
+    }
+    for (int k0 = b_lo; k0 < b_hi; k0 += kQueryLanes) {
         const int k = k0 + l;
         bool hit = false;
         int e = 0;
-        if (k < nbig) {
+        if (k < b_hi) {
             e = big[k];
             if (!(kind == 1 && e <= q)) {
                 Box6 b = ld_box(ebox_all + 6 * (size_t)e);
@@ -304,16 +344,19 @@ __global__ void k_query(BPView v, int kind, int nq, const double* qbox, const do
 }
 
 // Oversize queries (boxes over kMaxCells cells): one block per query; thread
-// t tests the contiguous entry range [t c, (t + 1) c) so that a block scan of
-// the per-thread counts gives each match its position in entry order.
+// t tests the contiguous entry range [lo + t c, lo + (t + 1) c) of the query's
+// env (the whole table without env ranges) so that a block scan of the
+// per-thread counts gives each match its position in entry order.
 template <bool WRITE>
 __global__ void k_query_big(BPView v, int kind, const int* qlist, const double* qbox, const double* ebox_all,
                             int n_entries_all, uint32_t* cnt, const uint32_t* off, int2* out) {
     __shared__ uint32_t sc[256];
     int q = qlist[blockIdx.x];
     Box6 a = ld_box(qbox + 6 * (size_t)q);
-    int chunk = (n_entries_all + blockDim.x - 1) / blockDim.x;
-    int e0 = threadIdx.x * chunk, e1 = min(e0 + chunk, n_entries_all);
+    int lo, hi;
+    env_entries(v, kind, q, n_entries_all, lo, hi);  // other envs' entries never pair
+    int chunk = (hi - lo + (int)blockDim.x - 1) / (int)blockDim.x;
+    int e0 = lo + threadIdx.x * chunk, e1 = min(e0 + chunk, hi);
     auto hit = [&](int e) -> bool {
         if (kind == 1 && e <= q) return false;
         Box6 b = ld_box(ebox_all + 6 * (size_t)e);

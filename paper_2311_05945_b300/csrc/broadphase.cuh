@@ -19,6 +19,11 @@ struct BPView {
     double infl;
     double inv_cell;
     const int* env_skip = nullptr;  // nullable, per env: 1 = leave the env's primitives out
+    // nullable (both or neither): n_envs + 1 offsets of each env's triangles
+    // and edges when the primitives are ordered by env; oversize queries and
+    // the oversize-entry lists are then searched within the query's env only
+    const int* env_tri_start = nullptr;
+    const int* env_edge_start = nullptr;
 };
 
 struct BroadPhase {

@@ -75,6 +75,7 @@ struct zema_scene {
 
     // device geometry
     DBuf<int> node_env, env_node_start, env_tet_start, env_aff_start, env_unit_start, env_sv_start, env_edge_start;
+    DBuf<int> env_tri_start;  // surface triangles are ordered by env too
     DBuf<uint8_t> node_fixed, sv_aff;
     DBuf<double> node_mass, Dminv, tvol, tmu, tlam, aff_m, aff_S, aff_vol, aff_stiff, aff_com, sv_x0, sv_rest,
         body_mu, edge_rest2;
@@ -335,7 +336,7 @@ void build(zema_scene* s) {
     std::vector<double> sv_rest_h, sv_x0_h;
     std::vector<int2> edges_h;
     std::vector<int3> tris_h;
-    std::vector<int> env_sv_start(NE + 1, 0), env_edge_start(NE + 1, 0);
+    std::vector<int> env_sv_start(NE + 1, 0), env_edge_start(NE + 1, 0), env_tri_start(NE + 1, 0);
     std::vector<int> body_id_of_tet(s->tin.size()), body_id_of_aff(s->ain.size());
     for (size_t b = 0; b < s->bodies.size(); ++b) {
         if (s->bodies[b].first == 0)
@@ -420,10 +421,12 @@ void build(zema_scene* s) {
             std::sort(ed.begin(), ed.end());
             ed.erase(std::unique(ed.begin(), ed.end()), ed.end());
             for (auto& pr : ed) edges_h.push_back(make_int2(pr.first, pr.second));
+            env_tri_start[e] = (int)tris_h.size();
             for (auto& t : etris) tris_h.push_back(t);
         }
         env_sv_start[NE] = (int)sv_node_h.size();
         env_edge_start[NE] = (int)edges_h.size();
+        env_tri_start[NE] = (int)tris_h.size();
     }
     s->n_sv = (int)sv_node_h.size();
     s->n_edges = (int)edges_h.size();
@@ -593,6 +596,7 @@ void build(zema_scene* s) {
     up(s, s->env_unit_start, env_unit_start);
     up(s, s->env_sv_start, env_sv_start);
     up(s, s->env_edge_start, env_edge_start);
+    up(s, s->env_tri_start, env_tri_start);
     up(s, s->tets, tets_h);
     up(s, s->tmu, tmu_h);
     up(s, s->tlam, tlam_h);
@@ -939,6 +943,8 @@ uint32_t candidates(zema_scene* s, const double* X0, const double* X1, DBuf<Pair
     v.infl = 0.5 * s->P.dhat;
     v.inv_cell = 1.0 / s->cell;
     v.env_skip = env_skip;
+    v.env_tri_start = s->env_tri_start.p;
+    v.env_edge_start = s->env_edge_start.p;
     s->bp.run(&s->A, v, st);
     uint32_t n = s->bp.n_pt + s->bp.n_ee;
     out.ensure(&s->A, n + 1);
