@@ -304,6 +304,25 @@ zema_status zema_get_tuning(const zema_scene* s, int32_t precision, int32_t* clu
  * dims[0] = 40 and dims[n_layers] = 12 the per-body network; any other shape
  * is ZEMA_ERR_INVALID_ARG.  The scene copies the blob. */
 zema_status zema_load_warmstart(zema_scene* s, const void* blob, int64_t bytes);
+/* Material of a tet body (paper Sec. "Constitutive Models"), before the
+ * scene is finalized: 0 Neo-Hookean (the default; Psi = mu/2 (tr F^T F - 3) -
+ * mu ln J + lam/2 (ln J)^2, +inf for J <= 0), 1 St. Venant-Kirchhoff
+ * (Psi = mu E:E + lam/2 tr(E)^2 with E = (F^T F - I)/2, finite for every F;
+ * its F-space Hessian is PSD-projected by Jacobi rotations).  Other models or
+ * a non-tet body: ZEMA_ERR_INVALID_ARG. */
+zema_status zema_set_material(zema_scene* s, int32_t body, int32_t model);
+
+/* Spring constraints (paper Sec. "Spring Constraints") on vertices of a tet
+ * body: the term h^2 k |x_v - target_v|^2 per listed vertex (a potential
+ * energy, scaled by h^2 like the elastic term, so k is in N/m and the spring
+ * force is 2 k (x - target)).  verts: n body-local vertex indices; targets:
+ * n x 3 positions; both copied.  Replaces the body's springs (n = 0 removes
+ * them).  Allowed before or after finalize and between steps.  A non-tet
+ * body, an index out of range, k < 0 or a non-finite value:
+ * ZEMA_ERR_INVALID_ARG. */
+zema_status zema_set_springs(zema_scene* s, int32_t body, const int32_t* verts, int64_t n, const double* targets,
+                             double k);
+
 /* Contact force sensing (paper Sec. "Contact Force Sensing"): for every body
  * (caller ids 0..n_bodies-1) the resultant barrier contact force at the
  * current state, forces[3 b .. 3 b + 2] = (1 / h^2) sum over the body's

@@ -513,6 +513,22 @@ bool nh_psi(const double* F9, double mu, double lam, D2<9>& out) {
     return true;
 }
 
+// St. Venant-Kirchhoff energy density in F-space: Green strain
+// E = (F^T F - I) / 2, Psi = mu E:E + lambda/2 tr(E)^2 (finite for every F)
+D2<9> stvk_psi(const double* F9, double mu, double lam) {
+    D2<9> F[9];
+    for (int i = 0; i < 9; ++i) F[i] = var<9>(F9[i], i);
+    D2<9> ee = cst<9>(0.0), tr = cst<9>(0.0);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            D2<9> c = F[i] * F[j] + F[3 + i] * F[3 + j] + F[6 + i] * F[6 + j];
+            D2<9> Eij = 0.5 * (c + (i == j ? -1.0 : 0.0));
+            ee = ee + Eij * Eij;
+            if (i == j) tr = tr + Eij;
+        }
+    return mu * ee + (0.5 * lam) * (tr * tr);
+}
+
 // Affine orthogonality energy |A A^T - I|_F^2 (9 variables, A row-major)
 D2<9> ortho(const double* A9) {
     D2<9> A[9];
@@ -549,6 +565,7 @@ struct Affine {
 struct SoftBody {
     int env, v0, nv, t0, nt;
     double mu_l, lam_l, mu, rho;
+    int model = 0;  // 0 Neo-Hookean, 1 St. Venant-Kirchhoff
 };
 
 struct SV {
@@ -579,6 +596,7 @@ struct Scene {
     int n_envs = 1;
     // soft
     std::vector<double> X, x, v, xt, xhat, mass;
+    std::vector<double> spring_k, spring_x;  // per soft vertex: spring stiffness (0: none) and target
     std::vector<int> tets, vert_body;
     std::vector<double> Dminv, tvol;
     std::vector<int> tet_body;
@@ -1052,6 +1070,16 @@ double env_energy(const Scene& S, int env, const EnvDofs& D, const State& st, co
             if (Y && opt.grad) Y->g[o + k] += m * d;
             if (Y && opt.hess) Y->H.push_back(Trip{o + k, o + k, m});
         }
+        // spring constraint: a potential energy, so scaled by h^2 like the
+        // elastic term: h^2 k |x - x_target|^2
+        const double ks = S.spring_k.empty() ? 0.0 : S.spring_k[i];
+        if (ks > 0.0)
+            for (int k = 0; k < 3; ++k) {
+                double r = st.x[3 * i + k] - S.spring_x[3 * i + k];
+                E += h2 * ks * r * r;
+                if (Y && opt.grad) Y->g[o + k] += 2.0 * h2 * ks * r;
+                if (Y && opt.hess) Y->H.push_back(Trip{o + k, o + k, 2.0 * h2 * ks});
+            }
     }
     // elasticity (Eq. 1, h^2 Phi)
     for (size_t t = 0; t < S.tet_body.size(); ++t) {
@@ -1060,7 +1088,10 @@ double env_energy(const Scene& S, int env, const EnvDofs& D, const State& st, co
         double F[9];
         def_grad(S, (int)t, st.x, F);
         D2<9> psi;
-        if (!nh_psi(F, S.soft[sb].mu_l, S.soft[sb].lam_l, psi)) return INF;
+        if (S.soft[sb].model == 1)
+            psi = stvk_psi(F, S.soft[sb].mu_l, S.soft[sb].lam_l);
+        else if (!nh_psi(F, S.soft[sb].mu_l, S.soft[sb].lam_l, psi))
+            return INF;
         double w = h2 * S.tvol[t];
         E += w * psi.v;
         if (Y && (opt.grad || opt.hess)) {
@@ -1805,6 +1836,37 @@ int orc_add_affine_body(void* s, int env, const double* V, long nv, const int* F
     return body;
 }
 
+// material of a soft body: 0 Neo-Hookean, 1 St. Venant-Kirchhoff
+int orc_set_material(void* s, int body, int model) {
+    Scene& S = *(Scene*)s;
+    if (S.finalized || body < 0 || body >= (int)S.bodies.size() || S.bodies[body].first != 0 || model < 0 ||
+        model > 1)
+        return -E_INVALID;
+    S.soft[S.bodies[body].second].model = model;
+    return 0;
+}
+
+// springs of a soft body (body-local vertices), replacing the body's springs
+int orc_set_springs(void* s, int body, const int* verts, long n, const double* targets, double k) {
+    Scene& S = *(Scene*)s;
+    if (body < 0 || body >= (int)S.bodies.size() || S.bodies[body].first != 0 || n < 0 || !(k >= 0.0))
+        return -E_INVALID;
+    const SoftBody& B = S.soft[S.bodies[body].second];
+    const size_t nvt = S.X.size() / 3;
+    if (S.spring_k.size() < nvt) {
+        S.spring_k.resize(nvt, 0.0);
+        S.spring_x.resize(3 * nvt, 0.0);
+    }
+    for (int i = 0; i < B.nv; ++i) S.spring_k[B.v0 + i] = 0.0;
+    for (long i = 0; i < n; ++i) {
+        if (verts[i] < 0 || verts[i] >= B.nv) return -E_INVALID;
+        const int g = B.v0 + verts[i];
+        S.spring_k[g] = k;
+        for (int j = 0; j < 3; ++j) S.spring_x[3 * g + j] = targets[3 * i + j];
+    }
+    return 0;
+}
+
 int orc_finalize(void* s) {
     Scene& S = *(Scene*)s;
     if (S.finalized) return -E_INVALID;
@@ -2167,6 +2229,20 @@ double orc_f1(double y, double eh) { return f1(y, eh); }
 double orc_nh(const double* F9, double mu, double lam, int project, double* g9, double* H81) {
     D2<9> p;
     if (!nh_psi(F9, mu, lam, p)) return INF;
+    if (g9)
+        for (int i = 0; i < 9; ++i) g9[i] = p.g[i];
+    if (H81) {
+        for (int i = 0; i < 9; ++i)
+            for (int j = 0; j < 9; ++j) H81[9 * i + j] = p.h[i][j];
+        if (project) psd_project(9, H81);
+    }
+    return p.v;
+}
+
+// St. Venant-Kirchhoff Psi(F) with F-space gradient (9) and Hessian (81,
+// projected if asked)
+double orc_stvk(const double* F9, double mu, double lam, int project, double* g9, double* H81) {
+    D2<9> p = stvk_psi(F9, mu, lam);
     if (g9)
         for (int i = 0; i < 9; ++i) g9[i] = p.g[i];
     if (H81) {

@@ -28,6 +28,8 @@ def lib():
         L.orc_add_affine_body.argtypes = [C.c_void_p, C.c_int, dp, C.c_long, ip, C.c_long, dp, dp,
                                           C.c_double, C.c_double, C.c_double, C.c_int]
         L.orc_finalize.argtypes = [C.c_void_p]
+        L.orc_set_material.argtypes = [C.c_void_p, C.c_int, C.c_int]
+        L.orc_set_springs.argtypes = [C.c_void_p, C.c_int, ip, C.c_long, dp, C.c_double]
         L.orc_set_kinematic_target.argtypes = [C.c_void_p, C.c_int, dp]
         L.orc_step.argtypes = [C.c_void_p, C.c_int, dp]
         L.orc_get_state.restype = C.c_long
@@ -60,6 +62,8 @@ def lib():
             getattr(L, f).argtypes = [C.c_double, C.c_double]
         L.orc_nh.restype = C.c_double
         L.orc_nh.argtypes = [dp, C.c_double, C.c_double, C.c_int, dp, dp]
+        L.orc_stvk.restype = C.c_double
+        L.orc_stvk.argtypes = [dp, C.c_double, C.c_double, C.c_int, dp, dp]
         L.orc_ortho.restype = C.c_double
         L.orc_ortho.argtypes = [dp, dp, dp]
         L.orc_accd.restype = C.c_double
@@ -121,6 +125,11 @@ class Oracle:
             if r < 0:
                 raise OracleError(f"add body failed: {r}")
             self.body_ids.append(r)
+        for i, b in enumerate(scene.tets):
+            if b.model and L.orc_set_material(self.h, self.body_ids[i], int(b.model)) != 0:
+                raise OracleError("set material failed")
+        for (i, verts, targets, k) in scene.springs:
+            self.set_springs(i, verts, targets, k)
         if L.orc_finalize(self.h) != 0:
             raise OracleError("finalize failed")
         self.n_tet = len(scene.tets)
@@ -130,6 +139,14 @@ class Oracle:
         if getattr(self, "h", None):
             lib().orc_destroy(self.h)
             self.h = None
+
+    def set_springs(self, tet_index, verts, targets, k):
+        """Springs h^2 k |x - target|^2 on body-local vertices of a soft body
+        (replacing its springs)."""
+        v = np.ascontiguousarray(verts, dtype=np.int32)
+        t = _d(targets)
+        if lib().orc_set_springs(self.h, self.body_ids[tet_index], _ip(v), len(v), _dp(t), float(k)) != 0:
+            raise OracleError("set springs failed")
 
     def affine_body_id(self, i):
         return self.body_ids[self.n_tet + i]
@@ -278,6 +295,14 @@ def nh(F, mu, lam, project=False):
     g = np.zeros(9)
     H = np.zeros(81)
     v = lib().orc_nh(_dp(F), mu, lam, int(project), _dp(g), _dp(H))
+    return v, g, H.reshape(9, 9)
+
+
+def stvk(F, mu, lam, project=False):
+    F = _d(np.asarray(F, dtype=np.float64).ravel())
+    g = np.zeros(9)
+    H = np.zeros(81)
+    v = lib().orc_stvk(_dp(F), mu, lam, int(project), _dp(g), _dp(H))
     return v, g, H.reshape(9, 9)
 
 

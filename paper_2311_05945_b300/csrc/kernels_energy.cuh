@@ -195,6 +195,70 @@ __device__ __forceinline__ void dF_coef(const double* Dm, double D[4][3]) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// St. Venant-Kirchhoff density (a material choice of the paper's soft
+// solids): E = (F^T F - I) / 2, Psi = mu E:E + lam/2 tr(E)^2, first Piola
+// stress P = F S with S = 2 mu E + lam tr(E) I.  Defined for every F
+// (no barrier against inversion).
+// ---------------------------------------------------------------------------
+__device__ inline void stvk_eval(const double* F, double mu, double lam, double& psi, double* P) {
+    double E[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double c = 0.0;
+            for (int k = 0; k < 3; ++k) c += F[3 * k + i] * F[3 * k + j];
+            E[3 * i + j] = 0.5 * (c - (i == j ? 1.0 : 0.0));
+        }
+    const double tr = E[0] + E[4] + E[8];
+    double ee = 0.0;
+    for (int i = 0; i < 9; ++i) ee += E[i] * E[i];
+    psi = mu * ee + 0.5 * lam * tr * tr;
+    if (!P) return;
+    double S[9];
+    for (int i = 0; i < 9; ++i) S[i] = 2.0 * mu * E[i] + (i % 4 == 0 ? lam * tr : 0.0);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double v = 0.0;
+            for (int k = 0; k < 3; ++k) v += F[3 * i + k] * S[3 * k + j];
+            P[3 * i + j] = v;
+        }
+}
+
+// F-space Hessian of StVK, column (a, b) = dP for dF = e_a e_b^T:
+//   dP = dF S + F dS, dS = 2 mu dE + lam tr(dE) I,
+//   dE_ij = (delta_ib F_aj + F_ai delta_jb) / 2, tr(dE) = F_ab;
+// then projected onto the PSD cone (cyclic Jacobi: the StVK Hessian has no
+// simple closed eigensystem).  W is 81 values of scratch.
+template <class T>
+__device__ inline void stvk_hessian_projected(const double* F, double mu, double lam, SMat<9, T> H, T* W) {
+    double E[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double c = 0.0;
+            for (int k = 0; k < 3; ++k) c += F[3 * k + i] * F[3 * k + j];
+            E[3 * i + j] = 0.5 * (c - (i == j ? 1.0 : 0.0));
+        }
+    const double tr = E[0] + E[4] + E[8];
+    double S[9];
+    for (int i = 0; i < 9; ++i) S[i] = 2.0 * mu * E[i] + (i % 4 == 0 ? lam * tr : 0.0);
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            double dS[9];
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) {
+                    const double dE = 0.5 * ((i == b ? F[3 * a + j] : 0.0) + (j == b ? F[3 * a + i] : 0.0));
+                    dS[3 * i + j] = 2.0 * mu * dE + (i == j ? lam * F[3 * a + b] : 0.0);
+                }
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) {
+                    double v = i == a ? S[3 * b + j] : 0.0;
+                    for (int k = 0; k < 3; ++k) v += F[3 * i + k] * dS[3 * k + j];
+                    H(3 * i + j, 3 * a + b) = (T)v;
+                }
+        }
+    psd_project<9, T>(H, SMat<9, T>{W, 1});
+}
+
 __device__ __forceinline__ void tet_F(const Geo& G, const double* x, int t, double* F, int4& T) {
     T = G.tets[t];
     V3 x0 = ld3(x + 3 * (size_t)T.x), x1 = ld3(x + 3 * (size_t)T.y), x2 = ld3(x + 3 * (size_t)T.z),
@@ -221,13 +285,19 @@ __global__ void __launch_bounds__(EL_T) k_elastic_gh(Geo G, const double* x, T* 
     double F[9], P[9], psi;
     int4 Tt;
     tet_F(G, x, t, F, Tt);
-    if (!nh_eval(F, G.tmu[t], G.tlam[t], psi, P, nullptr)) {
-        // inverted (never reached at an accepted iterate): zero contribution
-        for (int i = 0; i < 16 * 9; ++i) stage_blk[(size_t)t * 144 + i] = T(0);
-        for (int i = 0; i < 12; ++i) stage_g[(size_t)t * 12 + i] = 0.0;
-        return;
+    if (G.tmodel[t] == 1) {
+        T W[81];
+        stvk_eval(F, G.tmu[t], G.tlam[t], psi, P);
+        stvk_hessian_projected<T>(F, G.tmu[t], G.tlam[t], H, W);
+    } else {
+        if (!nh_eval(F, G.tmu[t], G.tlam[t], psi, P, nullptr)) {
+            // inverted (never reached at an accepted iterate): zero contribution
+            for (int i = 0; i < 16 * 9; ++i) stage_blk[(size_t)t * 144 + i] = T(0);
+            for (int i = 0; i < 12; ++i) stage_g[(size_t)t * 12 + i] = 0.0;
+            return;
+        }
+        nh_hessian_projected<T>(F, G.tmu[t], G.tlam[t], H);
     }
-    nh_hessian_projected<T>(F, G.tmu[t], G.tlam[t], H);
     double D[4][3];
     dF_coef(G.Dminv + 9 * (size_t)t, D);
     double w = G.h * G.h * G.tvol[t];
@@ -267,7 +337,13 @@ __global__ void k_soft_energy(Geo G, const double* x, const double* xhat, double
             double m = G.node_mass[n];
             if (m == 0.0) return 0.0;
             V3 d = ld3(x + 3 * (size_t)n) - ld3(xhat + 3 * (size_t)n);
-            return 0.5 * m * dot(d, d);
+            double e = 0.5 * m * dot(d, d);
+            if (G.spring_k && G.spring_k[n] > 0.0) {
+                // spring constraint: h^2 k |x - x_target|^2
+                V3 r = ld3(x + 3 * (size_t)n) - ld3(G.spring_x + 3 * (size_t)n);
+                e += G.h * G.h * G.spring_k[n] * dot(r, r);
+            }
+            return e;
         },
         part_slot(part, ET_INERTIA, G.n_envs, env));
     int t0 = G.env_tet_start[env], t1 = G.env_tet_start[env + 1];
@@ -277,7 +353,10 @@ __global__ void k_soft_energy(Geo G, const double* x, const double* xhat, double
             double F[9], psi;
             int4 T;
             tet_F(G, x, t, F, T);
-            if (!nh_eval(F, G.tmu[t], G.tlam[t], psi, nullptr, nullptr)) return INFINITY;
+            if (G.tmodel[t] == 1)
+                stvk_eval(F, G.tmu[t], G.tlam[t], psi, nullptr);
+            else if (!nh_eval(F, G.tmu[t], G.tlam[t], psi, nullptr, nullptr))
+                return INFINITY;
             return G.h * G.h * G.tvol[t] * psi;
         },
         part_slot(part, ET_ELASTIC, G.n_envs, env));
@@ -291,6 +370,8 @@ __global__ void k_soft_grad(Geo G, const double* x, const double* xhat, const do
     if (m == 0.0) return;  // affine node
     V3 d = ld3(x + 3 * (size_t)n) - ld3(xhat + 3 * (size_t)n);
     V3 s = m * d;
+    if (G.spring_k && G.spring_k[n] > 0.0)
+        s = s + (2.0 * G.h * G.h * G.spring_k[n]) * (ld3(x + 3 * (size_t)n) - ld3(G.spring_x + 3 * (size_t)n));
     for (int k = G.node_tet_ptr[n]; k < G.node_tet_ptr[n + 1]; ++k) {
         int e = G.node_tet_idx[k];  // tet * 4 + local
         s = s + ld3(stage_g + 3 * (size_t)e);

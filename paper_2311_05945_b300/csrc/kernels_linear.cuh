@@ -33,7 +33,9 @@ __global__ void k_static_diag(Geo G, const int* S_diag, T* S_val) {
         for (int i = 0; i < 9; ++i) o[i] = (i % 4 == 0) ? T(1) : T(0);
         return;
     }
-    T m = (T)G.node_mass[n];
+    double md = G.node_mass[n];
+    if (md != 0.0 && G.spring_k) md += 2.0 * G.h * G.h * G.spring_k[n];  // spring: 2 h^2 k I
+    T m = (T)md;
     o[0] += m;
     o[4] += m;
     o[8] += m;

@@ -33,6 +33,10 @@ struct TetIn {
     std::vector<double> X, x0, v0;
     std::vector<int> T;
     double E, nu, rho, mu;
+    int model = 0;                    // 0 Neo-Hookean, 1 St. Venant-Kirchhoff
+    std::vector<int> spring_v;        // springs: body-local vertex, target (3 each), stiffness
+    std::vector<double> spring_x;
+    double spring_k = 0.0;
 };
 struct AffIn {
     int env, mode;
@@ -76,6 +80,9 @@ struct zema_scene {
     // device geometry
     DBuf<int> node_env, env_node_start, env_tet_start, env_aff_start, env_unit_start, env_sv_start, env_edge_start;
     DBuf<int> env_tri_start;  // surface triangles are ordered by env too
+    DBuf<uint8_t> tmodel;
+    DBuf<double> spring_k, spring_x;  // per node (allocated with the first spring)
+    bool has_springs = false;
     DBuf<uint8_t> node_fixed, sv_aff;
     DBuf<double> node_mass, Dminv, tvol, tmu, tlam, aff_m, aff_S, aff_vol, aff_stiff, aff_com, sv_x0, sv_rest,
         body_mu, edge_rest2;
@@ -235,6 +242,32 @@ __global__ void k_affine_mass(const double* V, const int* F, const int* f_ptr, c
 // ---------------------------------------------------------------------------
 // finalize: layout, topology, static pattern, uploads
 // ---------------------------------------------------------------------------
+// device spring arrays of a tet body from its TetIn (zero stiffness elsewhere)
+void upload_springs(zema_scene* s, int tb) {
+    const TetIn& B = s->tin[tb];
+    const size_t nN = (size_t)s->n_nodes;
+    if (!s->has_springs) {
+        s->spring_k.ensure(&s->A, nN + 1);
+        s->spring_x.ensure(&s->A, 3 * nN + 3);
+        ZCHECK(cudaMemsetAsync(s->spring_k.p, 0, (nN + 1) * sizeof(double), s->st));
+        ZCHECK(cudaMemsetAsync(s->spring_x.p, 0, (3 * nN + 3) * sizeof(double), s->st));
+        s->has_springs = true;
+        s->G.spring_k = s->spring_k.p;
+        s->G.spring_x = s->spring_x.p;
+    }
+    const int n0 = s->tet_body_node0[tb], nv = (int)(B.X.size() / 3);
+    std::vector<double> k(nv, 0.0), x(3 * (size_t)nv, 0.0);
+    for (size_t i = 0; i < B.spring_v.size(); ++i) {
+        const int v = B.spring_v[i];
+        k[v] = B.spring_k;
+        for (int j = 0; j < 3; ++j) x[3 * (size_t)v + j] = B.spring_x[3 * i + j];
+    }
+    ZCHECK(cudaMemcpyAsync(s->spring_k.p + n0, k.data(), nv * sizeof(double), cudaMemcpyHostToDevice, s->st));
+    ZCHECK(cudaMemcpyAsync(s->spring_x.p + 3 * (size_t)n0, x.data(), 3 * (size_t)nv * sizeof(double),
+                           cudaMemcpyHostToDevice, s->st));
+    ZCHECK(cudaStreamSynchronize(s->st));
+}
+
 void build(zema_scene* s) {
     cudaStream_t st = s->st;
     Allocator* A = &s->A;
@@ -254,6 +287,7 @@ void build(zema_scene* s) {
     std::vector<uint8_t> node_fixed_h;
     std::vector<int4> tets_h;
     std::vector<double> trho_h, tmu_h, tlam_h, xrest_h, x_h, v_h;
+    std::vector<uint8_t> tmodel_h;
     std::vector<int> aff_perm;  // affine device index -> input index
     {
         size_t ti = 0, ai = 0;
@@ -281,6 +315,7 @@ void build(zema_scene* s) {
                     trho_h.push_back(B.rho);
                     tmu_h.push_back(mu);
                     tlam_h.push_back(lam);
+                    tmodel_h.push_back((uint8_t)B.model);
                 }
             }
             env_aff_start[e] = (int)aff_perm.size();
@@ -600,6 +635,7 @@ void build(zema_scene* s) {
     up(s, s->tets, tets_h);
     up(s, s->tmu, tmu_h);
     up(s, s->tlam, tlam_h);
+    up(s, s->tmodel, tmodel_h);
     up(s, s->aff_node0, aff_node0_dev);
     up(s, s->aff_mode, aff_mode_dev);
     up(s, s->unit_kind, unit_kind_h);
@@ -874,6 +910,9 @@ void build(zema_scene* s) {
     G.tvol = s->tvol.p;
     G.tmu = s->tmu.p;
     G.tlam = s->tlam.p;
+    G.tmodel = s->tmodel.p;
+    G.spring_k = s->has_springs ? s->spring_k.p : nullptr;
+    G.spring_x = s->spring_x.p;
     G.env_tet_start = s->env_tet_start.p;
     G.aff_node0 = s->aff_node0.p;
     G.aff_mode = s->aff_mode.p;
@@ -911,6 +950,8 @@ void build(zema_scene* s) {
     ZCHECK(cudaFuncSetAttribute(k_affine_gh<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 81 * AF_T * 8));
     ZCHECK(cudaFuncSetAttribute(k_affine_gh<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 81 * AF_T * 4));
     ZCHECK(cudaStreamSynchronize(st));
+    for (size_t b = 0; b < s->tin.size(); ++b)
+        if (!s->tin[b].spring_v.empty()) upload_springs(s, (int)b);
     s->finalized = true;
 }
 
@@ -2408,6 +2449,39 @@ zema_status zema_record_warmstart(zema_scene* s, float* features, float* targets
     s->rec_feat = features;
     s->rec_targ = targets;
     return ZEMA_OK;
+}
+
+zema_status zema_set_material(zema_scene* s, int32_t body, int32_t model) {
+    if (!s || body < 0 || body >= (int)s->bodies.size() || s->bodies[body].first != 0 || model < 0 || model > 1)
+        return ZEMA_ERR_INVALID_ARG;
+    if (s->finalized) return ZEMA_ERR_INVALID_ARG;
+    s->tin[s->bodies[body].second].model = model;
+    return ZEMA_OK;
+}
+
+zema_status zema_set_springs(zema_scene* s, int32_t body, const int32_t* verts, int64_t n, const double* targets,
+                             double k) {
+    if (s) set_current_stream(s->st);
+    if (!s || body < 0 || body >= (int)s->bodies.size() || s->bodies[body].first != 0 || n < 0 ||
+        (n > 0 && (!verts || !targets)) || !(k >= 0.0) || !std::isfinite(k))
+        return ZEMA_ERR_INVALID_ARG;
+    const int tb = s->bodies[body].second;
+    TetIn& B = s->tin[tb];
+    const int nv = (int)(B.X.size() / 3);
+    for (int64_t i = 0; i < n; ++i) {
+        if (verts[i] < 0 || verts[i] >= nv) return ZEMA_ERR_INVALID_ARG;
+        for (int j = 0; j < 3; ++j)
+            if (!std::isfinite(targets[3 * i + j])) return ZEMA_ERR_INVALID_ARG;
+    }
+    B.spring_v.assign(verts, verts + n);
+    B.spring_x.assign(targets, targets + 3 * n);
+    B.spring_k = n > 0 ? k : 0.0;
+    if (!s->finalized) return ZEMA_OK;
+    ZEMA_TRY(s) {
+        upload_springs(s, tb);
+        return ZEMA_OK;
+    }
+    ZEMA_CATCH(s)
 }
 
 zema_status zema_contact_forces(zema_scene* s, double* forces, int64_t cap) {

@@ -217,6 +217,7 @@ class TetBody:
     x0: Optional[np.ndarray] = None
     v0: Optional[np.ndarray] = None
     name: str = "soft"
+    model: int = 0              # 0 Neo-Hookean, 1 St. Venant-Kirchhoff
 
 
 @dataclass
@@ -245,6 +246,8 @@ class Scene:
     script: Optional[Callable[[int], Dict[int, np.ndarray]]] = None
     # grasp scenes: (affine index, closing sign along z, q0) of every finger
     fingers: list = field(default_factory=list)
+    # spring constraints: (tet body index, body-local vertices, targets (n, 3), k [N/m])
+    springs: list = field(default_factory=list)
 
     def body_order(self):
         """(kind, index) in the order bodies are added: tets first, then affines."""

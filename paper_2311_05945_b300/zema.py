@@ -113,6 +113,8 @@ def lib():
     L.zema_record_warmstart.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]
     L.zema_record_warmstart_affine.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]
     L.zema_contact_forces.argtypes = [C.c_void_p, DP, C.c_int64]
+    L.zema_set_material.argtypes = [C.c_void_p, C.c_int32, C.c_int32]
+    L.zema_set_springs.argtypes = [C.c_void_p, C.c_int32, IP, C.c_int64, DP, C.c_double]
     L.zema_mlp_create.argtypes = [IP, C.c_int32, C.c_uint64, C.c_void_p, C.POINTER(C.c_void_p)]
     L.zema_mlp_destroy.argtypes = [C.c_void_p]
     L.zema_mlp_destroy.restype = None
@@ -240,6 +242,11 @@ class Scene:
         self.n_tet = len(scene.tets)
         self.step_index = 0
         _LIVE.add(self)
+        for i, b in enumerate(scene.tets):
+            if b.model:
+                _check(L.zema_set_material(h, self.body_ids[i], int(b.model)), h)
+        for (i, verts, targets, k) in scene.springs:
+            self.set_springs(i, verts, targets, k)
         _check(L.zema_finalize(h), h)
 
     def close(self):
@@ -282,6 +289,13 @@ class Scene:
         rows = min(features.shape[0], targets.shape[0])
         _check(lib().zema_record_warmstart(self.h, C.c_void_p(features.data_ptr()), C.c_void_p(targets.data_ptr()),
                                            rows), self.h)
+
+    def set_springs(self, tet_index, verts, targets, k):
+        """Spring constraints h^2 k |x - target|^2 on body-local vertices of a
+        soft body (replacing its springs; allowed between steps)."""
+        v = _i(verts)
+        t = _d(targets)
+        _check(lib().zema_set_springs(self.h, self.body_ids[tet_index], _ip(v), len(v), _dp(t), float(k)), self.h)
 
     def contact_forces(self) -> np.ndarray:
         """(n_bodies, 3) barrier contact force of every body at the current

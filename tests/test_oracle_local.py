@@ -326,3 +326,35 @@ def test_accd_conservative(seed, is_ee):
     # distance at t is at least s = 0.1 of the initial one
     d0 = np.sqrt(O.stencil_d2(x, is_ee)[0])
     assert np.sqrt(O.stencil_d2(x + t * p, is_ee)[0]) >= 0.1 * d0 * (1 - 1e-9) or t == 1.0
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_stvk_closed_forms_and_fd(seed):
+    # St. Venant-Kirchhoff: zero energy and stress at any rotation; uniaxial
+    # stretch diag(s, 1, 1) has E = diag(e, 0, 0) with e = (s^2 - 1)/2, so
+    # Psi = (mu + lam/2) e^2, S = diag((2 mu + lam) e, lam e, lam e) and
+    # P = F S = diag(s (2 mu + lam) e, lam e, lam e);
+    # finite differences of Psi and of the gradient; finite and PSD after
+    # projection also for an inverted F (StVK has no inversion barrier)
+    mu, lam = 3.5e4, 3.1e5
+    R = rot(seed)
+    psi, g, _ = O.stvk(R, mu, lam)
+    assert abs(psi) < 1e-9 * mu and np.abs(g).max() < 1e-9 * mu
+    for s in (0.7, 1.0, 1.3):
+        e = 0.5 * (s * s - 1.0)
+        psi, g, _ = O.stvk(np.diag([s, 1.0, 1.0]), mu, lam)
+        assert abs(psi - (mu + 0.5 * lam) * e * e) <= 1e-12 * max(1.0, abs(psi))
+        P = np.diag([s * (2.0 * mu + lam) * e, lam * e, lam * e]).ravel()
+        assert np.abs(g - P).max() <= 1e-9 * mu
+    F = np.eye(3) + 0.2 * np.random.default_rng(seed).standard_normal((3, 3))
+    f = lambda y: O.stvk(y, mu, lam)[0]
+    gf = lambda y: O.stvk(y, mu, lam)[1]
+    psi, g, H = O.stvk(F, mu, lam)
+    assert rel(g, fd_grad(f, F.ravel())) < 1e-6
+    assert rel(H, fd_hess(gf, F.ravel())) < 1e-5
+    Fi = F.copy()
+    Fi[:, 0] *= -1
+    psi_i, _, Hp = O.stvk(Fi, mu, lam, project=True)
+    assert np.isfinite(psi_i)
+    ev = np.linalg.eigvalsh(Hp)
+    assert ev.min() >= -1e-9 * np.abs(ev).max()

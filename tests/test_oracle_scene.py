@@ -262,3 +262,40 @@ def test_brute_candidates_match_numpy_definition():
     edge_index = {tuple(x): i for i, x in enumerate(e)}
     got_ee = set((edge_index[(a, b)], edge_index[(c, d)]) for a, b, c, d in ee)
     assert got_ee == ref_ee and len(ref_ee) > 0
+
+
+def spring_scene(model=0):
+    """A 3x3x3-vertex soft cube in free fall with springs pulling four of its
+    vertices towards targets 1 cm off their rest positions."""
+    p = S.Params(dt=0.01)
+    s = S.Scene("springs", p)
+    X, T = S.soft_cube(3, 0.2, (0.0, 1.0, 0.0))
+    s.tets.append(S.TetBody(X, T, E=1e5, nu=0.4, rho=1000.0, mu=0.3, model=model))
+    verts = np.array([0, 4, 13, 26], dtype=np.int32)
+    targets = X[verts] + np.array([0.01, -0.01, 0.005])
+    s.springs.append((0, verts, targets, 2.0e3))
+    return s, verts, targets
+
+
+@pytest.mark.parametrize("model", [0, 1])
+def test_spring_forces_balance_momentum(model):
+    # springs are a potential h^2 k |x - t|^2: at a converged step the soft
+    # body's momentum balance has only inertia, gravity and springs (elastic
+    # forces cancel inside the body): sum_v m_v (x_v - xhat_v) / h^2 +
+    # sum_springs 2 k (x_v - t_v) = 0
+    s, verts, targets = spring_scene(model)
+    o = Oracle(s, tol_scale=1e-4)
+    m = o.lumped_mass()
+    h = s.params.dt
+    g = np.array(s.params.gravity)
+    for _ in range(3):
+        st0 = o.get_state(0)
+        n = len(s.tets[0].X)
+        x0, v0 = st0[:3 * n].reshape(-1, 3), st0[3 * n:].reshape(-1, 3)
+        o.step(1)
+        x1 = o.tet_positions()
+        xhat = x0 + h * v0 + h * h * g
+        inertia = (m[:, None] * (x1 - xhat)).sum(0) / (h * h)
+        spring = (2.0 * 2.0e3 * (x1[verts] - targets)).sum(0)
+        scale = np.abs(spring).max() + np.abs(inertia).max()
+        assert np.abs(inertia + spring).max() < 1e-6 * scale
