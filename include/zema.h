@@ -255,6 +255,11 @@ zema_status zema_local_distance(int64_t n, const double* x12, const int32_t* is_
  * (81) of n deformation gradients F (row-major). */
 zema_status zema_local_neo_hookean(int64_t n, const double* F9, double mu, double lam, double* psi_out,
                                    double* g_out, double* H_out, void* stream);
+/* The same for any material: model 0 Neo-Hookean, 1 St. Venant-Kirchhoff,
+ * 2 fixed corotated (zema_set_material); psi = +inf (and g, H untouched)
+ * where the model is undefined (J <= 0 for 0 and 2). */
+zema_status zema_local_elastic(int64_t n, const double* F9, double mu, double lam, int32_t model, double* psi_out,
+                               double* g_out, double* H_out, void* stream);
 /* Additive CCD step bound t in (0, 1] of n stencils moving by p12 (s = 0.1). */
 zema_status zema_local_accd(int64_t n, const double* x12, const double* p12, const int32_t* is_ee,
                             double* t_out, void* stream);
@@ -307,9 +312,11 @@ zema_status zema_load_warmstart(zema_scene* s, const void* blob, int64_t bytes);
 /* Material of a tet body (paper Sec. "Constitutive Models"), before the
  * scene is finalized: 0 Neo-Hookean (the default; Psi = mu/2 (tr F^T F - 3) -
  * mu ln J + lam/2 (ln J)^2, +inf for J <= 0), 1 St. Venant-Kirchhoff
- * (Psi = mu E:E + lam/2 tr(E)^2 with E = (F^T F - I)/2, finite for every F;
- * its F-space Hessian is PSD-projected by Jacobi rotations).  Other models or
- * a non-tet body: ZEMA_ERR_INVALID_ARG. */
+ * (Psi = mu E:E + lam/2 tr(E)^2 with E = (F^T F - I)/2, finite for every F),
+ * 2 fixed corotated (Psi = mu |F - R|^2 + lam/2 (J - 1)^2, R the polar
+ * rotation of F; +inf for J <= 0 so that R is a proper rotation).  The
+ * F-space Hessians of 1 and 2 are PSD-projected by Jacobi rotations.  Other
+ * models or a non-tet body: ZEMA_ERR_INVALID_ARG. */
 zema_status zema_set_material(zema_scene* s, int32_t body, int32_t model);
 
 /* Spring constraints (paper Sec. "Spring Constraints") on vertices of a tet

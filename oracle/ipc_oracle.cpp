@@ -529,6 +529,50 @@ D2<9> stvk_psi(const double* F9, double mu, double lam) {
     return mu * ee + (0.5 * lam) * (tr * tr);
 }
 
+// Fixed-corotated energy density: Psi = mu |F - R|^2 + lambda/2 (J - 1)^2
+// with R the rotation of the polar decomposition F = R S, computed by
+// Newton's iteration R <- (R + R^-T)/2 from R = F carried out on dual numbers
+// (so the derivatives of R are those of the converged iteration); J <= 0 is
+// not admitted (false), so R is a proper rotation.
+bool fcr_psi(const double* F9, double mu, double lam, D2<9>& out) {
+    D2<9> F[9];
+    for (int i = 0; i < 9; ++i) F[i] = var<9>(F9[i], i);
+    auto det3 = [](const D2<9>* A) {
+        return A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+               A[2] * (A[3] * A[7] - A[4] * A[6]);
+    };
+    D2<9> J = det3(F);
+    if (!(J.v > 0.0)) return false;
+    D2<9> R[9];
+    for (int i = 0; i < 9; ++i) R[i] = F[i];
+    int extra = -1;
+    for (int it = 0; it < 80 && extra != 0; ++it) {
+        // R^-T = cof(R) / det(R)
+        D2<9> Cf[9] = {R[4] * R[8] - R[5] * R[7], R[5] * R[6] - R[3] * R[8], R[3] * R[7] - R[4] * R[6],
+                       R[2] * R[7] - R[1] * R[8], R[0] * R[8] - R[2] * R[6], R[1] * R[6] - R[0] * R[7],
+                       R[1] * R[5] - R[2] * R[4], R[2] * R[3] - R[0] * R[5], R[0] * R[4] - R[1] * R[3]};
+        D2<9> d = det3(R);
+        double diff = 0.0;
+        for (int i = 0; i < 9; ++i) {
+            D2<9> r = 0.5 * (R[i] + Cf[i] / d);
+            diff = std::max(diff, std::fabs(r.v - R[i].v));
+            R[i] = r;
+        }
+        // a few more iterations once the value has converged, for the
+        // derivative parts
+        if (extra < 0 && diff < 1e-15) extra = 4;
+        if (extra > 0) --extra;
+    }
+    D2<9> s = cst<9>(0.0);
+    for (int i = 0; i < 9; ++i) {
+        D2<9> e = F[i] - R[i];
+        s = s + e * e;
+    }
+    D2<9> jm = J + (-1.0);
+    out = mu * s + (0.5 * lam) * (jm * jm);
+    return true;
+}
+
 // Affine orthogonality energy |A A^T - I|_F^2 (9 variables, A row-major)
 D2<9> ortho(const double* A9) {
     D2<9> A[9];
@@ -565,7 +609,7 @@ struct Affine {
 struct SoftBody {
     int env, v0, nv, t0, nt;
     double mu_l, lam_l, mu, rho;
-    int model = 0;  // 0 Neo-Hookean, 1 St. Venant-Kirchhoff
+    int model = 0;  // 0 Neo-Hookean, 1 St. Venant-Kirchhoff, 2 fixed corotated
 };
 
 struct SV {
@@ -1090,7 +1134,9 @@ double env_energy(const Scene& S, int env, const EnvDofs& D, const State& st, co
         D2<9> psi;
         if (S.soft[sb].model == 1)
             psi = stvk_psi(F, S.soft[sb].mu_l, S.soft[sb].lam_l);
-        else if (!nh_psi(F, S.soft[sb].mu_l, S.soft[sb].lam_l, psi))
+        else if (S.soft[sb].model == 2) {
+            if (!fcr_psi(F, S.soft[sb].mu_l, S.soft[sb].lam_l, psi)) return INF;
+        } else if (!nh_psi(F, S.soft[sb].mu_l, S.soft[sb].lam_l, psi))
             return INF;
         double w = h2 * S.tvol[t];
         E += w * psi.v;
@@ -1836,11 +1882,11 @@ int orc_add_affine_body(void* s, int env, const double* V, long nv, const int* F
     return body;
 }
 
-// material of a soft body: 0 Neo-Hookean, 1 St. Venant-Kirchhoff
+// material of a soft body: 0 Neo-Hookean, 1 St. Venant-Kirchhoff, 2 fixed corotated
 int orc_set_material(void* s, int body, int model) {
     Scene& S = *(Scene*)s;
     if (S.finalized || body < 0 || body >= (int)S.bodies.size() || S.bodies[body].first != 0 || model < 0 ||
-        model > 1)
+        model > 2)
         return -E_INVALID;
     S.soft[S.bodies[body].second].model = model;
     return 0;
@@ -2243,6 +2289,20 @@ double orc_nh(const double* F9, double mu, double lam, int project, double* g9, 
 // projected if asked)
 double orc_stvk(const double* F9, double mu, double lam, int project, double* g9, double* H81) {
     D2<9> p = stvk_psi(F9, mu, lam);
+    if (g9)
+        for (int i = 0; i < 9; ++i) g9[i] = p.g[i];
+    if (H81) {
+        for (int i = 0; i < 9; ++i)
+            for (int j = 0; j < 9; ++j) H81[9 * i + j] = p.h[i][j];
+        if (project) psd_project(9, H81);
+    }
+    return p.v;
+}
+
+// fixed-corotated Psi(F) (+inf for J <= 0) with gradient and Hessian
+double orc_fcr(const double* F9, double mu, double lam, int project, double* g9, double* H81) {
+    D2<9> p;
+    if (!fcr_psi(F9, mu, lam, p)) return INF;
     if (g9)
         for (int i = 0; i < 9; ++i) g9[i] = p.g[i];
     if (H81) {

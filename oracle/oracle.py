@@ -62,6 +62,8 @@ def lib():
             getattr(L, f).argtypes = [C.c_double, C.c_double]
         L.orc_nh.restype = C.c_double
         L.orc_nh.argtypes = [dp, C.c_double, C.c_double, C.c_int, dp, dp]
+        L.orc_fcr.restype = C.c_double
+        L.orc_fcr.argtypes = [dp, C.c_double, C.c_double, C.c_int, dp, dp]
         L.orc_stvk.restype = C.c_double
         L.orc_stvk.argtypes = [dp, C.c_double, C.c_double, C.c_int, dp, dp]
         L.orc_ortho.restype = C.c_double
@@ -303,6 +305,14 @@ def stvk(F, mu, lam, project=False):
     g = np.zeros(9)
     H = np.zeros(81)
     v = lib().orc_stvk(_dp(F), mu, lam, int(project), _dp(g), _dp(H))
+    return v, g, H.reshape(9, 9)
+
+
+def fcr(F, mu, lam, project=False):
+    F = _d(np.asarray(F, dtype=np.float64).ravel())
+    g = np.zeros(9)
+    H = np.zeros(81)
+    v = lib().orc_fcr(_dp(F), mu, lam, int(project), _dp(g), _dp(H))
     return v, g, H.reshape(9, 9)
 
 

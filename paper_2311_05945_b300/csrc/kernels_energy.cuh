@@ -259,6 +259,113 @@ __device__ inline void stvk_hessian_projected(const double* F, double mu, double
     psd_project<9, T>(H, SMat<9, T>{W, 1});
 }
 
+// ---------------------------------------------------------------------------
+// Fixed-corotated density (a material choice of the paper's soft solids):
+// Psi = mu |F - R|^2 + lam/2 (J - 1)^2 with R the rotation of the polar
+// decomposition F = R S, here for J > 0 only (J <= 0: +inf, as for
+// Neo-Hookean, so R is always a proper rotation).
+// P = 2 mu (F - R) + lam (J - 1) cof(F).
+// ---------------------------------------------------------------------------
+__device__ inline void cof3(const double* A, double* C) {
+    C[0] = A[4] * A[8] - A[5] * A[7];
+    C[1] = A[5] * A[6] - A[3] * A[8];
+    C[2] = A[3] * A[7] - A[4] * A[6];
+    C[3] = A[2] * A[7] - A[1] * A[8];
+    C[4] = A[0] * A[8] - A[2] * A[6];
+    C[5] = A[1] * A[6] - A[0] * A[7];
+    C[6] = A[1] * A[5] - A[2] * A[4];
+    C[7] = A[2] * A[3] - A[0] * A[5];
+    C[8] = A[0] * A[4] - A[1] * A[3];
+}
+
+// rotation of the polar decomposition by Newton's iteration
+// R <- (R + R^-T) / 2 from R = F (quadratic convergence for det F > 0)
+__device__ inline bool polar_rotation(const double* F, double* R) {
+    for (int i = 0; i < 9; ++i) R[i] = F[i];
+    for (int it = 0; it < 60; ++it) {
+        double C[9];
+        cof3(R, C);
+        const double det = R[0] * C[0] + R[1] * C[1] + R[2] * C[2];
+        if (!(det > 0.0)) return false;
+        double diff = 0.0;
+        for (int i = 0; i < 9; ++i) {
+            const double r = 0.5 * (R[i] + C[i] / det);
+            diff = fmax(diff, fabs(r - R[i]));
+            R[i] = r;
+        }
+        if (diff < 1e-15) break;
+    }
+    return true;
+}
+
+__device__ inline bool fcr_eval(const double* F, double mu, double lam, double& psi, double* P) {
+    double C[9], R[9];
+    cof3(F, C);
+    const double J = F[0] * C[0] + F[1] * C[1] + F[2] * C[2];
+    if (!(J > 0.0) || !polar_rotation(F, R)) return false;
+    double d2 = 0.0;
+    for (int i = 0; i < 9; ++i) d2 += (F[i] - R[i]) * (F[i] - R[i]);
+    psi = mu * d2 + 0.5 * lam * (J - 1.0) * (J - 1.0);
+    if (P)
+        for (int i = 0; i < 9; ++i) P[i] = 2.0 * mu * (F[i] - R[i]) + lam * (J - 1.0) * C[i];
+    return true;
+}
+
+// F-space Hessian of the fixed-corotated density, column (a, b) for
+// dF = e_a e_b^T:  2 mu (dF - dR) + lam cof(F) cof(F)_ab + lam (J - 1) dcof,
+// with dcof_ij = eps_iak eps_jbn F_kn and the rotation's differential
+// dR = R [w]x, w = (tr(S) I - S)^-1 axial(R^T dF - dF^T R), S = R^T F (from
+// R^T dF - dF^T R = w S + S w for the skew w = R^T dR); symmetrised, then
+// projected onto the PSD cone by Jacobi rotations.  J > 0 is assumed.
+template <class T>
+__device__ inline void fcr_hessian_projected(const double* F, double mu, double lam, SMat<9, T> H, T* W) {
+    double C[9], R[9], S[9], M[9], Mi[9];
+    cof3(F, C);
+    const double J = F[0] * C[0] + F[1] * C[1] + F[2] * C[2];
+    polar_rotation(F, R);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double v = 0.0;
+            for (int k = 0; k < 3; ++k) v += R[3 * k + i] * F[3 * k + j];
+            S[3 * i + j] = v;
+        }
+    for (int i = 0; i < 3; ++i)
+        for (int j = i + 1; j < 3; ++j) S[3 * i + j] = S[3 * j + i] = 0.5 * (S[3 * i + j] + S[3 * j + i]);
+    const double trS = S[0] + S[4] + S[8];
+    for (int i = 0; i < 9; ++i) M[i] = (i % 4 == 0 ? trS : 0.0) - S[i];
+    double Cm[9];
+    cof3(M, Cm);
+    const double detM = M[0] * Cm[0] + M[1] * Cm[1] + M[2] * Cm[2];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) Mi[3 * i + j] = Cm[3 * j + i] / detM;  // inverse = adjugate / det
+    double Hd[81];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            // K = A - A^T with A = R^T dF, A_pq = R_ap delta_qb
+            double K[9];
+            for (int p = 0; p < 3; ++p)
+                for (int q = 0; q < 3; ++q) K[3 * p + q] = (q == b ? R[3 * a + p] : 0.0) - (p == b ? R[3 * a + q] : 0.0);
+            const double k[3] = {K[7], K[2], K[3]};  // axial vector of the skew K
+            double w[3];
+            for (int i = 0; i < 3; ++i) w[i] = Mi[3 * i] * k[0] + Mi[3 * i + 1] * k[1] + Mi[3 * i + 2] * k[2];
+            const double Om[9] = {0.0, -w[2], w[1], w[2], 0.0, -w[0], -w[1], w[0], 0.0};
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) {
+                    double dR = 0.0;
+                    for (int k2 = 0; k2 < 3; ++k2) dR += R[3 * i + k2] * Om[3 * k2 + j];
+                    double dcof = 0.0;
+                    for (int k2 = 0; k2 < 3; ++k2)
+                        for (int n = 0; n < 3; ++n) dcof += lc(i, a, k2) * lc(j, b, n) * F[3 * k2 + n];
+                    const double dF = (i == a && j == b) ? 1.0 : 0.0;
+                    Hd[9 * (3 * i + j) + 3 * a + b] =
+                        2.0 * mu * (dF - dR) + lam * C[3 * i + j] * C[3 * a + b] + lam * (J - 1.0) * dcof;
+                }
+        }
+    for (int r = 0; r < 9; ++r)
+        for (int c = 0; c < 9; ++c) H(r, c) = (T)(0.5 * (Hd[9 * r + c] + Hd[9 * c + r]));
+    psd_project<9, T>(H, SMat<9, T>{W, 1});
+}
+
 __device__ __forceinline__ void tet_F(const Geo& G, const double* x, int t, double* F, int4& T) {
     T = G.tets[t];
     V3 x0 = ld3(x + 3 * (size_t)T.x), x1 = ld3(x + 3 * (size_t)T.y), x2 = ld3(x + 3 * (size_t)T.z),
@@ -289,6 +396,14 @@ __global__ void __launch_bounds__(EL_T) k_elastic_gh(Geo G, const double* x, T* 
         T W[81];
         stvk_eval(F, G.tmu[t], G.tlam[t], psi, P);
         stvk_hessian_projected<T>(F, G.tmu[t], G.tlam[t], H, W);
+    } else if (G.tmodel[t] == 2) {
+        if (!fcr_eval(F, G.tmu[t], G.tlam[t], psi, P)) {
+            for (int i = 0; i < 16 * 9; ++i) stage_blk[(size_t)t * 144 + i] = T(0);
+            for (int i = 0; i < 12; ++i) stage_g[(size_t)t * 12 + i] = 0.0;
+            return;
+        }
+        T W[81];
+        fcr_hessian_projected<T>(F, G.tmu[t], G.tlam[t], H, W);
     } else {
         if (!nh_eval(F, G.tmu[t], G.tlam[t], psi, P, nullptr)) {
             // inverted (never reached at an accepted iterate): zero contribution
@@ -355,7 +470,9 @@ __global__ void k_soft_energy(Geo G, const double* x, const double* xhat, double
             tet_F(G, x, t, F, T);
             if (G.tmodel[t] == 1)
                 stvk_eval(F, G.tmu[t], G.tlam[t], psi, nullptr);
-            else if (!nh_eval(F, G.tmu[t], G.tlam[t], psi, nullptr, nullptr))
+            else if (G.tmodel[t] == 2) {
+                if (!fcr_eval(F, G.tmu[t], G.tlam[t], psi, nullptr)) return INFINITY;
+            } else if (!nh_eval(F, G.tmu[t], G.tlam[t], psi, nullptr, nullptr))
                 return INFINITY;
             return G.h * G.h * G.tvol[t] * psi;
         },

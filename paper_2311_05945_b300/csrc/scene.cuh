@@ -30,7 +30,7 @@ struct Geo {
     const double* tvol;             // rest volume
     const double* tmu;              // Lame mu
     const double* tlam;             // Lame lambda
-    const uint8_t* tmodel;          // material per tet: 0 Neo-Hookean, 1 St. Venant-Kirchhoff
+    const uint8_t* tmodel;          // material per tet: 0 Neo-Hookean, 1 St. Venant-Kirchhoff, 2 fixed corotated
     const double* spring_k;         // per node: spring stiffness (N/m, 0: none); null when no springs
     const double* spring_x;         // per node: spring target (3)
     const int* env_tet_start;

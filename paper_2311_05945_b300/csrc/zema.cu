@@ -33,7 +33,7 @@ struct TetIn {
     std::vector<double> X, x0, v0;
     std::vector<int> T;
     double E, nu, rho, mu;
-    int model = 0;                    // 0 Neo-Hookean, 1 St. Venant-Kirchhoff
+    int model = 0;                    // 0 Neo-Hookean, 1 St. Venant-Kirchhoff, 2 fixed corotated
     std::vector<int> spring_v;        // springs: body-local vertex, target (3 each), stiffness
     std::vector<double> spring_x;
     double spring_k = 0.0;
@@ -2452,7 +2452,7 @@ zema_status zema_record_warmstart(zema_scene* s, float* features, float* targets
 }
 
 zema_status zema_set_material(zema_scene* s, int32_t body, int32_t model) {
-    if (!s || body < 0 || body >= (int)s->bodies.size() || s->bodies[body].first != 0 || model < 0 || model > 1)
+    if (!s || body < 0 || body >= (int)s->bodies.size() || s->bodies[body].first != 0 || model < 0 || model > 2)
         return ZEMA_ERR_INVALID_ARG;
     if (s->finalized) return ZEMA_ERR_INVALID_ARG;
     s->tin[s->bodies[body].second].model = model;
@@ -2690,6 +2690,37 @@ __global__ void __launch_bounds__(EL_T) k_local_nh(const double* F9, int n, doub
     }
 }
 
+// any material: density, first Piola stress and PSD-projected F-space Hessian
+__global__ void __launch_bounds__(EL_T) k_local_elastic(const double* F9, int n, double mu, double lam, int model,
+                                                        double* psi, double* g, double* H) {
+    extern __shared__ double sm[];
+    int i = blockIdx.x * EL_T + threadIdx.x;
+    if (i >= n) return;
+    SMat<9> M{sm + threadIdx.x, EL_T};
+    const double* F = F9 + 9 * (size_t)i;
+    double P[9], ps, W[81];
+    bool ok = true;
+    if (model == 1) {
+        stvk_eval(F, mu, lam, ps, P);
+        stvk_hessian_projected<double>(F, mu, lam, M, W);
+    } else if (model == 2) {
+        ok = fcr_eval(F, mu, lam, ps, P);
+        if (ok) fcr_hessian_projected<double>(F, mu, lam, M, W);
+    } else {
+        ok = nh_eval(F, mu, lam, ps, P, nullptr);
+        if (ok) nh_hessian_projected<double>(F, mu, lam, M);
+    }
+    if (!ok) {
+        psi[i] = INFINITY;
+        return;
+    }
+    psi[i] = ps;
+    for (int a = 0; a < 9; ++a) {
+        g[9 * (size_t)i + a] = P[a];
+        for (int b = 0; b < 9; ++b) H[81 * (size_t)i + 9 * a + b] = M(a, b);
+    }
+}
+
 __global__ void k_local_accd(const double* x12, const double* p12, const int* is_ee, int n, double* t) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -2852,6 +2883,31 @@ zema_status zema_local_neo_hookean(int64_t n, const double* F9, double mu, doubl
         double* H = T.put<double>(nullptr, 81 * (size_t)n);
         ZCHECK(cudaFuncSetAttribute(k_local_nh, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 81 * EL_T * 8));
         ZL(k_local_nh, div_up(n, EL_T), EL_T, 2 * 81 * EL_T * 8, st)(dF, (int)n, mu, lam, ps, g, H);
+        ZLAUNCH();
+        get(psi_out, ps, n, st);
+        get(g_out, g, 9 * n, st);
+        get(H_out, H, 81 * n, st);
+        ZCHECK(cudaStreamSynchronize(st));
+        return ZEMA_OK;
+    } catch (const ZemaError& e) {
+        return status_of(e);
+    }
+}
+
+zema_status zema_local_elastic(int64_t n, const double* F9, double mu, double lam, int32_t model, double* psi_out,
+                               double* g_out, double* H_out, void* stream) {
+    set_current_stream((cudaStream_t)stream);
+    if (n < 0 || !F9 || !psi_out || !g_out || !H_out || model < 0 || model > 2) return ZEMA_ERR_INVALID_ARG;
+    if (n == 0) return ZEMA_OK;
+    try {
+        cudaStream_t st = (cudaStream_t)stream;
+        Temp T(st);
+        double* dF = T.put(F9, 9 * (size_t)n);
+        double* ps = T.put<double>(nullptr, (size_t)n);
+        double* g = T.put<double>(nullptr, 9 * (size_t)n);
+        double* H = T.put<double>(nullptr, 81 * (size_t)n);
+        ZCHECK(cudaFuncSetAttribute(k_local_elastic, cudaFuncAttributeMaxDynamicSharedMemorySize, 81 * EL_T * 8));
+        ZL(k_local_elastic, div_up(n, EL_T), EL_T, 81 * EL_T * 8, st)(dF, (int)n, mu, lam, model, ps, g, H);
         ZLAUNCH();
         get(psi_out, ps, n, st);
         get(g_out, g, 9 * n, st);

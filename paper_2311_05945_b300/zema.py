@@ -101,6 +101,7 @@ def lib():
     L.zema_local_barrier.argtypes = [C.c_int64, DP, IP, DP, C.c_double, DP, DP, DP, C.c_void_p]
     L.zema_local_distance.argtypes = [C.c_int64, DP, IP, DP, DP, C.c_void_p]
     L.zema_local_neo_hookean.argtypes = [C.c_int64, DP, C.c_double, C.c_double, DP, DP, DP, C.c_void_p]
+    L.zema_local_elastic.argtypes = [C.c_int64, DP, C.c_double, C.c_double, C.c_int32, DP, DP, DP, C.c_void_p]
     L.zema_local_accd.argtypes = [C.c_int64, DP, DP, IP, DP, C.c_void_p]
     L.zema_launch_count.restype = C.c_longlong
     L.zema_launch_count.argtypes = []
@@ -505,6 +506,14 @@ def local_neo_hookean(F, mu, lam):
     n = len(F)
     psi, g, H = np.zeros(n), np.zeros((n, 9)), np.zeros((n, 9, 9))
     _check(lib().zema_local_neo_hookean(n, _dp(F), mu, lam, _dp(psi), _dp(g), _dp(H), _stream()))
+    return psi, g, H
+
+
+def local_elastic(F, mu, lam, model):
+    F = _d(np.asarray(F).reshape(-1, 9))
+    n = len(F)
+    psi, g, H = np.zeros(n), np.zeros((n, 9)), np.zeros((n, 9, 9))
+    _check(lib().zema_local_elastic(n, _dp(F), mu, lam, int(model), _dp(psi), _dp(g), _dp(H), _stream()))
     return psi, g, H
 
 

@@ -73,6 +73,30 @@ def test_neo_hookean_matches_oracle():
         assert np.abs(H[i] - Hr).max() <= 1e-8 * max(1.0, np.abs(Hr).max())
 
 
+@pytest.mark.parametrize("model", [1, 2])
+def test_other_materials_match_oracle(model):
+    # St. Venant-Kirchhoff (1) and fixed corotated (2): density, stress and
+    # PSD-projected F-space Hessian against the oracle's forward-mode
+    # derivatives (for 2 through the polar iteration, on the GPU the closed
+    # differential of the polar rotation)
+    from paper_2311_05945_b300 import zema as Z
+    rng = np.random.default_rng(7 + model)
+    Fs = np.eye(3)[None] + 0.35 * rng.standard_normal((400, 3, 3))
+    Fs = Fs[np.linalg.det(Fs) > 0.05]
+    mu, lam = 3.4e4, 3.1e5
+    psi, P, H = Z.local_elastic(Fs, mu, lam, model)
+    ref = O.stvk if model == 1 else O.fcr
+    for i in range(len(Fs)):
+        v, g, Hr = ref(Fs[i], mu, lam, project=True)
+        assert abs(psi[i] - v) <= 1e-10 * max(1.0, abs(v))
+        assert np.abs(P[i] - g).max() <= 1e-9 * max(1.0, np.abs(g).max())
+        assert np.abs(H[i] - Hr).max() <= 1e-7 * max(1.0, np.abs(Hr).max()), i
+    if model == 2:
+        Fi = Fs[0].copy()
+        Fi[:, 0] *= -1
+        assert Z.local_elastic(Fi[None], mu, lam, 2)[0][0] == np.inf
+
+
 @pytest.mark.parametrize("is_ee", [0, 1])
 def test_accd_matches_oracle(is_ee):
     from paper_2311_05945_b300 import zema as Z

@@ -1,4 +1,4 @@
-"""St. Venant-Kirchhoff soft bodies and spring constraints on the GPU,
+"""St. Venant-Kirchhoff and fixed-corotated soft bodies and spring constraints on the GPU,
 against the oracle: the incremental potential and its gradient at the same
 state, and short trajectories at tight tolerance (with contact and with
 springs moved between steps)."""
@@ -21,16 +21,16 @@ def spring_scene(model=1):
     return s
 
 
-def stvk_contact_scene():
+def contact_scene(model=1):
     s = S.scene_tiny_contact(mu=0.5)
-    s.tets[0].model = 1
+    s.tets[0].model = model
     return s
 
 
-@pytest.mark.parametrize("which", ["springs", "contact"])
+@pytest.mark.parametrize("which", ["springs", "contact", "contact_fcr"])
 def test_energy_and_gradient_match_oracle(which):
     from paper_2311_05945_b300.zema import Scene
-    sc = spring_scene() if which == "springs" else stvk_contact_scene()
+    sc = spring_scene() if which == "springs" else contact_scene(2 if which == "contact_fcr" else 1)
     orc = Oracle(sc)
     orc.step(6)
     orc.prepare(0, friction=True)
@@ -52,10 +52,11 @@ def test_energy_and_gradient_match_oracle(which):
     gpu.close()
 
 
-@pytest.mark.parametrize("which,precision", [("springs", 0), ("contact", 0), ("contact", 1)])
+@pytest.mark.parametrize("which,precision", [("springs", 0), ("contact", 0), ("contact", 1), ("contact_fcr", 0),
+                                             ("contact_fcr", 1)])
 def test_trajectory_matches_oracle(which, precision):
     from paper_2311_05945_b300.zema import Scene
-    sc = spring_scene() if which == "springs" else stvk_contact_scene()
+    sc = spring_scene() if which == "springs" else contact_scene(2 if which == "contact_fcr" else 1)
     orc = Oracle(sc, tol_scale=1e-2)
     gpu = Scene(sc, tol_scale=1e-2, precision=precision)
     diag = orc.diag()

@@ -358,3 +358,33 @@ def test_stvk_closed_forms_and_fd(seed):
     assert np.isfinite(psi_i)
     ev = np.linalg.eigvalsh(Hp)
     assert ev.min() >= -1e-9 * np.abs(ev).max()
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_fixed_corotated_closed_forms_and_fd(seed):
+    # fixed corotated: zero energy and stress at any rotation; for
+    # F = Q diag(s, 1, 1) the polar rotation is Q, Psi = (mu + lam/2)(s - 1)^2
+    # and P = Q diag((2 mu + lam)(s - 1), lam (s - 1) s, lam (s - 1) s);
+    # finite differences of Psi and of the gradient; +inf for J <= 0
+    mu, lam = 3.5e4, 3.1e5
+    Q = rot(seed)
+    psi, g, _ = O.fcr(Q, mu, lam)
+    assert abs(psi) < 1e-9 * mu and np.abs(g).max() < 1e-9 * mu
+    for s in (0.7, 1.3):
+        psi, g, _ = O.fcr(Q @ np.diag([s, 1.0, 1.0]), mu, lam)
+        assert abs(psi - (mu + 0.5 * lam) * (s - 1.0) ** 2) <= 1e-10 * psi
+        P = Q @ np.diag([(2.0 * mu + lam) * (s - 1.0), lam * (s - 1.0) * s, lam * (s - 1.0) * s])
+        assert np.abs(g - P.ravel()).max() <= 1e-8 * mu
+    F = np.eye(3) + 0.2 * np.random.default_rng(seed).standard_normal((3, 3))
+    assert np.linalg.det(F) > 0
+    f = lambda y: O.fcr(y, mu, lam)[0]
+    gf = lambda y: O.fcr(y, mu, lam)[1]
+    psi, g, H = O.fcr(F, mu, lam)
+    assert rel(g, fd_grad(f, F.ravel())) < 1e-6
+    assert rel(H, fd_hess(gf, F.ravel())) < 1e-5
+    _, _, Hp = O.fcr(F, mu, lam, project=True)
+    ev = np.linalg.eigvalsh(Hp)
+    assert ev.min() >= -1e-9 * np.abs(ev).max()
+    Fi = F.copy()
+    Fi[:, 0] *= -1
+    assert O.fcr(Fi, mu, lam)[0] == np.inf

@@ -277,7 +277,7 @@ def spring_scene(model=0):
     return s, verts, targets
 
 
-@pytest.mark.parametrize("model", [0, 1])
+@pytest.mark.parametrize("model", [0, 1, 2])
 def test_spring_forces_balance_momentum(model):
     # springs are a potential h^2 k |x - t|^2: at a converged step the soft
     # body's momentum balance has only inertia, gravity and springs (elastic
