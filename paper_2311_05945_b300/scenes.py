@@ -663,3 +663,32 @@ def scene_c5(n_steps: int = 200, tets_per_body: int = 60000, n_soft: int = 8, n_
         q[3:12] = Rm.reshape(-1)
         s.affines.append(AffineBody(V, F, q, rho=1000.0, stiffness=1e8, mu=0.5, mode=0, name=name))
     return s
+
+
+# ----------------------------------------------------------------------------
+# Runtime over rigid-mesh resolution
+# ----------------------------------------------------------------------------
+RESOLUTION_SEGMENTS = (26, 46, 105, 138, 279)  # UV spheres of 652 ... 77,564 vertices
+
+
+def scene_resolution(n_seg: int, n_steps: int = 60, precision: int = 1, spacing: float = 0.01) -> Scene:
+    """An affine sphere (radius 5 cm, n_seg x n_seg UV mesh: n_seg (n_seg - 1)
+    + 2 vertices, 2 n_seg (n_seg - 1) triangles) dropped from 2 mm onto a soft
+    box (12 x 4 x 12 cm lattice of the given spacing, E = 1e5, nu = 0.4)
+    resting on a fixed floor; mu = 0.5, dt = 0.01.  The system's DOF do not
+    depend on n_seg: the sphere is 12 of them at every resolution."""
+    p = Params(dt=0.01, dhat=1e-3, kappa=0.0, eps_v=1e-3, newton_tol_rel=1e-3, precision=precision)
+    s = Scene(f"resolution_{n_seg}", p, n_steps=n_steps)
+    m, org = box_mask((0.12, 0.04, 0.12), spacing)
+    X, T = lattice_tets(m, spacing, org)
+    X = X - np.array([0.0, X[:, 1].min() - 0.5 * p.dhat, 0.0])
+    s.tets.append(TetBody(X, T, E=1e5, nu=0.4, rho=1000.0, mu=0.5, name="soft_box"))
+    Vf, Ff = box_surface((0.4, 0.02, 0.4), 1)
+    s.affines.append(AffineBody(Vf, Ff, q_identity((0.0, -0.01, 0.0)), rho=1000.0, stiffness=1e8, mu=0.5,
+                                mode=1, name="floor"))
+    V, F = uv_sphere_surface((0.05, 0.05, 0.05), n_seg, n_seg)
+    top = X[:, 1].max() + 0.002 + 0.05
+    # offset so that no sphere vertex sits exactly above a lattice vertex
+    s.affines.append(AffineBody(V, F, q_identity((0.0131, top, -0.0077)), rho=1000.0, stiffness=1e8, mu=0.5,
+                                mode=0, name="sphere"))
+    return s
