@@ -330,6 +330,26 @@ zema_status zema_set_material(zema_scene* s, int32_t body, int32_t model);
 zema_status zema_set_springs(zema_scene* s, int32_t body, const int32_t* verts, int64_t n, const double* targets,
                              double k);
 
+/* Prismatic joint (paper Sec. "Joint Constraints") between two affine bodies
+ * of one env, at least one of them dynamic, before the scene is finalized.
+ * The joint keeps the bodies' relative orientation at its initial value and
+ * lets body 2's copy of body 1's initial centre of mass move only along the
+ * axis, a unit vector fixed in body 1 (`axis` in world coordinates at the
+ * initial state).  It adds kappa |c|^2 - lambda . c to the incremental
+ * potential with the 12-vector
+ *   c = ( A1 B1 - A2 B2 ,  r x (A1 d1) ),
+ * B_b the inverse of body b's initial A, d1 the axis in body 1's frame and r
+ * the difference of the two bodies' images of the joint point; with both
+ * initial A = I this is the paper's |A1 - A2|^2 + |((A1 c + p1) - (A2 c +
+ * p2)) x (A1 d)|^2.  kappa <= 0 picks 1e3 x the mean of the two masses.
+ * lambda starts at 0 and follows the augmented-Lagrangian rounds of the
+ * kinematic bodies (lambda <- lambda - 2 kappa c while the rotation part
+ * exceeds newton_tol_rel x dt or the slide part the Newton step
+ * tolerance).  Its Hessian enters Newton as 2 kappa J^T J (Gauss-Newton,
+ * PSD).  joint_id (nullable) receives the joint's index. */
+zema_status zema_add_prismatic_joint(zema_scene* s, int32_t body1, int32_t body2, const double axis[3],
+                                     double kappa, int32_t* joint_id);
+
 /* Contact force sensing (paper Sec. "Contact Force Sensing"): for every body
  * (caller ids 0..n_bodies-1) the resultant barrier contact force at the
  * current state, forces[3 b .. 3 b + 2] = (1 / h^2) sum over the body's

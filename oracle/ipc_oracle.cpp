@@ -60,6 +60,7 @@
 #include <map>
 #include <string>
 #include <tuple>
+#include <array>
 #include <vector>
 
 namespace {
@@ -126,6 +127,11 @@ D2<N> operator*(double s, const D2<N>& a) {
         for (int j = 0; j < N; ++j) r.h[i][j] = s * a.h[i][j];
     }
     return r;
+}
+
+template <int N>
+D2<N> operator*(const D2<N>& a, double s) {
+    return s * a;
 }
 
 template <int N>
@@ -606,6 +612,17 @@ struct Affine {
     int sv0;  // first surface vertex
 };
 
+// Prismatic joint between two affine bodies, constants at the initial state
+// in the caller's frame (x = A y + p): B_b = A_b(0)^-1, y_b the joint point
+// (body 1's initial centre of mass) in body b's rest frame, d1 the axis in
+// body 1's rest frame.
+struct Joint {
+    int a1, a2, env;
+    double kappa;
+    double B1[9], B2[9], y1[3], y2[3], d1[3];
+    double lam[12];
+};
+
 struct SoftBody {
     int env, v0, nv, t0, nt;
     double mu_l, lam_l, mu, rho;
@@ -647,6 +664,7 @@ struct Scene {
     std::vector<SoftBody> soft;
     // affine
     std::vector<Affine> aff;
+    std::vector<Joint> joints;
     // bodies: global id -> (kind, index)
     std::vector<std::pair<int, int>> bodies;
     // surface
@@ -1095,6 +1113,30 @@ struct EvalOpt {
 // Total incremental potential of env at state st.  Contact terms use `pairs`
 // (all candidate pairs; only those with d < dhat contribute).  Returns +inf
 // for an inverted tet or a non-positive distance.
+// joint constraint c (12) from the two bodies' q = (p, rows of A):
+// c = (A1 B1 - A2 B2 , r x a), r = (A1 y1 + p1) - (A2 y2 + p2), a = A1 d1
+template <class T>
+void joint_constraint(const Joint& J, const T* q1, const T* q2, T* c) {
+    auto A1 = [&](int i, int k) { return q1[3 + 3 * i + k]; };
+    auto A2 = [&](int i, int k) { return q2[3 + 3 * i + k]; };
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            T v = (A1(i, 0) * J.B1[j] + A1(i, 1) * J.B1[3 + j]) + A1(i, 2) * J.B1[6 + j];
+            v = v - ((A2(i, 0) * J.B2[j] + A2(i, 1) * J.B2[3 + j]) + A2(i, 2) * J.B2[6 + j]);
+            c[3 * i + j] = v;
+        }
+    T r[3], a[3];
+    for (int i = 0; i < 3; ++i) {
+        T w1 = q1[i] + ((A1(i, 0) * J.y1[0] + A1(i, 1) * J.y1[1]) + A1(i, 2) * J.y1[2]);
+        T w2 = q2[i] + ((A2(i, 0) * J.y2[0] + A2(i, 1) * J.y2[1]) + A2(i, 2) * J.y2[2]);
+        r[i] = w1 - w2;
+        a[i] = (A1(i, 0) * J.d1[0] + A1(i, 1) * J.d1[1]) + A1(i, 2) * J.d1[2];
+    }
+    c[9] = r[1] * a[2] - r[2] * a[1];
+    c[10] = r[2] * a[0] - r[0] * a[2];
+    c[11] = r[0] * a[1] - r[1] * a[0];
+}
+
 double env_energy(const Scene& S, int env, const EnvDofs& D, const State& st, const std::vector<Pair>& pairs,
                   Sys* Y, EvalOpt opt, int* n_active = nullptr, double* dmin = nullptr) {
     const double h = S.P.dt, h2 = h * h;
@@ -1207,6 +1249,45 @@ double env_energy(const Scene& S, int env, const EnvDofs& D, const State& st, co
                 E += 0.5 * kA * d * d - sm * A.lamA[i] * d;
                 if (Y && opt.grad) Y->g[o + i] += kA * d - sm * A.lamA[i];
                 if (Y && opt.hess) Y->H.push_back(Trip{o + i, o + i, kA});
+            }
+        }
+    }
+    // prismatic joints: kappa |c|^2 - lambda . c over the free bodies' DOFs
+    // (fixed bodies enter as constants); exact Hessian, PSD-projected
+    for (const Joint& J : S.joints) {
+        if (J.env != env) continue;
+        const int o1 = D.aff_dof[J.a1], o2 = D.aff_dof[J.a2];
+        D2<24> v1[12], v2[12];
+        for (int k = 0; k < 12; ++k) {
+            v1[k] = o1 >= 0 ? var<24>(st.q[12 * J.a1 + k], k) : cst<24>(st.q[12 * J.a1 + k]);
+            v2[k] = o2 >= 0 ? var<24>(st.q[12 * J.a2 + k], 12 + k) : cst<24>(st.q[12 * J.a2 + k]);
+        }
+        D2<24> c[12];
+        joint_constraint(J, v1, v2, c);
+        D2<24> e = cst<24>(0.0);
+        for (int m = 0; m < 12; ++m) e = e + (J.kappa * (c[m] * c[m]) + (-J.lam[m]) * c[m]);
+        E += e.v;
+        if (Y && (opt.grad || opt.hess)) {
+            int idx[24], off[24], nf = 0;
+            for (int k = 0; k < 12; ++k)
+                if (o1 >= 0) {
+                    idx[nf] = k;
+                    off[nf++] = o1 + k;
+                }
+            for (int k = 0; k < 12; ++k)
+                if (o2 >= 0) {
+                    idx[nf] = 12 + k;
+                    off[nf++] = o2 + k;
+                }
+            if (opt.grad)
+                for (int a = 0; a < nf; ++a) Y->g[off[a]] += e.g[idx[a]];
+            if (opt.hess) {
+                std::vector<double> Hf((size_t)nf * nf);
+                for (int a = 0; a < nf; ++a)
+                    for (int b = 0; b < nf; ++b) Hf[(size_t)a * nf + b] = e.h[idx[a]][idx[b]];
+                psd_project(nf, Hf.data());
+                for (int a = 0; a < nf; ++a)
+                    for (int b = 0; b < nf; ++b) Y->H.push_back(Trip{off[a], off[b], Hf[(size_t)a * nf + b]});
             }
         }
     }
@@ -1739,6 +1820,16 @@ int step_env(Scene& S, int env, StepStats& ss) {
             for (int k = 0; k < 12; ++k) m = std::max(m, std::fabs(A.q[k] - A.qtarget[k]));
             if (m > tol) any = true;
         }
+        // prismatic joints: rotation part within tol_rel h, slide part
+        // within the step tolerance
+        std::vector<std::array<double, 12>> jc(S.joints.size());
+        for (size_t j = 0; j < S.joints.size(); ++j) {
+            const Joint& J = S.joints[j];
+            if (J.env != env) continue;
+            joint_constraint(J, S.aff[J.a1].q, S.aff[J.a2].q, jc[j].data());
+            for (int m = 0; m < 12; ++m)
+                if (std::fabs(jc[j][m]) > (m < 9 ? S.P.tol_rel * h : tol)) any = true;
+        }
         if (!any || rounds >= S.P.max_al_rounds) break;
         ++rounds;
         for (size_t a = 0; a < S.aff.size(); ++a) {
@@ -1746,6 +1837,11 @@ int step_env(Scene& S, int env, StepStats& ss) {
             if (A.env != env || A.mode != 2) continue;
             double kA = 1e3 * A.m, sm = std::sqrt(A.m);
             for (int k = 0; k < 12; ++k) A.lamA[k] -= kA * (A.q[k] - A.qtarget[k]) / sm;
+        }
+        for (size_t j = 0; j < S.joints.size(); ++j) {
+            Joint& J = S.joints[j];
+            if (J.env != env) continue;
+            for (int m = 0; m < 12; ++m) J.lam[m] -= 2.0 * J.kappa * jc[j][m];
         }
     }
     ss.al_rounds = rounds;
@@ -1880,6 +1976,61 @@ int orc_add_affine_body(void* s, int env, const double* V, long nv, const int* F
     S.aff.push_back(A);
     S.bodies.push_back({1, (int)S.aff.size() - 1});
     return body;
+}
+
+// prismatic joint between two affine bodies (axis in world coordinates at the
+// initial state; kappa <= 0: 1e3 x the mean of the two masses)
+int orc_add_prismatic_joint(void* s, int body1, int body2, const double* axis, double kappa) {
+    Scene& S = *(Scene*)s;
+    const int nb = (int)S.bodies.size();
+    if (S.finalized || body1 < 0 || body1 >= nb || body2 < 0 || body2 >= nb || body1 == body2 ||
+        S.bodies[body1].first != 1 || S.bodies[body2].first != 1)
+        return -E_INVALID;
+    Joint J;
+    J.a1 = S.bodies[body1].second;
+    J.a2 = S.bodies[body2].second;
+    const Affine &A1 = S.aff[J.a1], &A2 = S.aff[J.a2];
+    if (A1.env != A2.env) return -E_INVALID;
+    J.env = A1.env;
+    J.kappa = kappa > 0.0 ? kappa : 1e3 * 0.5 * (A1.m + A2.m);
+    auto inv = [](const double* M, double* I) {
+        double C[9] = {M[4] * M[8] - M[5] * M[7], M[5] * M[6] - M[3] * M[8], M[3] * M[7] - M[4] * M[6],
+                       M[2] * M[7] - M[1] * M[8], M[0] * M[8] - M[2] * M[6], M[1] * M[6] - M[0] * M[7],
+                       M[1] * M[5] - M[2] * M[4], M[2] * M[3] - M[0] * M[5], M[0] * M[4] - M[1] * M[3]};
+        double d = M[0] * C[0] + M[1] * C[1] + M[2] * C[2];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) I[3 * i + j] = C[3 * j + i] / d;
+        return d;
+    };
+    if (!(inv(A1.q + 3, J.B1) > 0.0) || !(inv(A2.q + 3, J.B2) > 0.0)) return -E_INVALID;
+    // body 1's centre of mass (rest frame: first moment over mass) in the world
+    double w0[3];
+    for (int i = 0; i < 3; ++i) {
+        w0[i] = A1.q[i];
+        for (int k = 0; k < 3; ++k) w0[i] += A1.q[3 + 3 * i + k] * A1.M[3 + k] / A1.m;
+    }
+    double n = std::sqrt(axis[0] * axis[0] + axis[1] * axis[1] + axis[2] * axis[2]);
+    if (!(n > 0.0)) return -E_INVALID;
+    for (int i = 0; i < 3; ++i) {
+        J.y1[i] = J.y2[i] = J.d1[i] = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            J.y1[i] += J.B1[3 * i + k] * (w0[k] - A1.q[k]);
+            J.y2[i] += J.B2[3 * i + k] * (w0[k] - A2.q[k]);
+            J.d1[i] += J.B1[3 * i + k] * axis[k] / n;
+        }
+    }
+    for (int m = 0; m < 12; ++m) J.lam[m] = 0.0;
+    S.joints.push_back(J);
+    return (int)S.joints.size() - 1;
+}
+
+// the 12 constraint values of joint j at the current state
+int orc_joint_constraint(void* s, int j, double* c) {
+    Scene& S = *(Scene*)s;
+    if (j < 0 || j >= (int)S.joints.size()) return -E_INVALID;
+    const Joint& J = S.joints[j];
+    joint_constraint(J, S.aff[J.a1].q, S.aff[J.a2].q, c);
+    return 0;
 }
 
 // material of a soft body: 0 Neo-Hookean, 1 St. Venant-Kirchhoff, 2 fixed corotated

@@ -29,6 +29,8 @@ def lib():
                                           C.c_double, C.c_double, C.c_double, C.c_int]
         L.orc_finalize.argtypes = [C.c_void_p]
         L.orc_set_material.argtypes = [C.c_void_p, C.c_int, C.c_int]
+        L.orc_add_prismatic_joint.argtypes = [C.c_void_p, C.c_int, C.c_int, dp, C.c_double]
+        L.orc_joint_constraint.argtypes = [C.c_void_p, C.c_int, dp]
         L.orc_set_springs.argtypes = [C.c_void_p, C.c_int, ip, C.c_long, dp, C.c_double]
         L.orc_set_kinematic_target.argtypes = [C.c_void_p, C.c_int, dp]
         L.orc_step.argtypes = [C.c_void_p, C.c_int, dp]
@@ -132,6 +134,11 @@ class Oracle:
                 raise OracleError("set material failed")
         for (i, verts, targets, k) in scene.springs:
             self.set_springs(i, verts, targets, k)
+        for (a1, a2, axis, kappa) in scene.joints:
+            ax = _d(axis)
+            if L.orc_add_prismatic_joint(self.h, self.affine_body_id(a1), self.affine_body_id(a2), _dp(ax),
+                                         float(kappa)) < 0:
+                raise OracleError("add joint failed")
         if L.orc_finalize(self.h) != 0:
             raise OracleError("finalize failed")
         self.n_tet = len(scene.tets)
@@ -151,7 +158,14 @@ class Oracle:
             raise OracleError("set springs failed")
 
     def affine_body_id(self, i):
-        return self.body_ids[self.n_tet + i]
+        return self.body_ids[len(self.scene.tets) + i]
+
+    def joint_constraint(self, j):
+        """The 12 constraint values of prismatic joint j at the current state."""
+        c = np.zeros(12)
+        if lib().orc_joint_constraint(self.h, j, _dp(c)) != 0:
+            raise OracleError("no such joint")
+        return c
 
     def tet_body_id(self, i):
         return self.body_ids[i]

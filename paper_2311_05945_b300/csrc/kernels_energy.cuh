@@ -9,7 +9,7 @@
 namespace zema {
 
 // Energy terms reduced per environment (partial sums per block chunk).
-enum ETerm { ET_INERTIA = 0, ET_ELASTIC = 1, ET_AFFINE = 2, ET_BARRIER = 3, ET_FRICTION = 4, ET_COUNT = 5 };
+enum ETerm { ET_INERTIA = 0, ET_ELASTIC = 1, ET_AFFINE = 2, ET_BARRIER = 3, ET_FRICTION = 4, ET_JOINT = 5, ET_COUNT = 6 };
 
 // Sum over i in [lo, hi) of f(i) by block (chunk = blockIdx.x) of env
 // blockIdx.y, fixed order; thread 0 writes the block's partial.
@@ -746,6 +746,138 @@ __global__ void k_body_contact_force(Geo G, const double* X, const PairRec* rec,
         const double t = block_sum<128>(f[j], sh);
         if (threadIdx.x == 0) force[3 * b + j] = t * inv_h2;
     }
+}
+
+// ---------------------------------------------------------------------------
+// Prismatic joint (paper Sec. "Joint Constraints"): constraint vector
+//   c = ( vec(A1 B1 - A2 B2) , r x (A1 d1) ),  r = P1 + A1 u1 - P2 - A2 u2,
+// zero when the relative orientation is the initial one and the joint point
+// of body 2 stays on body 1's axis (with both initial A = I this is the
+// paper's |A1 - A2|^2 + |((A1 c + p1) - (A2 c + p2)) x (A1 d)|^2 term).
+// Energy kappa |c|^2 - lambda . c (augmented Lagrangian).  Jm: dc/dq over
+// the 24 DOF, body 1's nodes (P, columns of A) then body 2's.
+// ---------------------------------------------------------------------------
+__device__ inline void joint_eval(const JointDev& J, const double* x, double* c, double (*Jm)[24]) {
+    double P1[3], P2[3], A1[9], A2[9];
+    for (int i = 0; i < 3; ++i) {
+        P1[i] = x[3 * (size_t)J.n1 + i];
+        P2[i] = x[3 * (size_t)J.n2 + i];
+        for (int k = 0; k < 3; ++k) {
+            A1[3 * i + k] = x[3 * (size_t)(J.n1 + 1 + k) + i];
+            A2[3 * i + k] = x[3 * (size_t)(J.n2 + 1 + k) + i];
+        }
+    }
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double v = 0.0;
+            for (int k = 0; k < 3; ++k) v += A1[3 * i + k] * J.B1[3 * k + j] - A2[3 * i + k] * J.B2[3 * k + j];
+            c[3 * i + j] = v;
+        }
+    double r[3], a[3];
+    for (int i = 0; i < 3; ++i) {
+        r[i] = P1[i] - P2[i];
+        a[i] = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            r[i] += A1[3 * i + k] * J.u1[k] - A2[3 * i + k] * J.u2[k];
+            a[i] += A1[3 * i + k] * J.d1[k];
+        }
+    }
+    c[9] = r[1] * a[2] - r[2] * a[1];
+    c[10] = r[2] * a[0] - r[0] * a[2];
+    c[11] = r[0] * a[1] - r[1] * a[0];
+    if (!Jm) return;
+    for (int m = 0; m < 12; ++m)
+        for (int q = 0; q < 24; ++q) Jm[m][q] = 0.0;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            for (int k = 0; k < 3; ++k) {
+                Jm[3 * i + j][3 + 3 * k + i] += J.B1[3 * k + j];
+                Jm[3 * i + j][15 + 3 * k + i] -= J.B2[3 * k + j];
+            }
+    // d(r x a) = -[a]x dr + [r]x da
+    const double Ax[9] = {0.0, -a[2], a[1], a[2], 0.0, -a[0], -a[1], a[0], 0.0};
+    const double Rx[9] = {0.0, -r[2], r[1], r[2], 0.0, -r[0], -r[1], r[0], 0.0};
+    for (int m = 0; m < 3; ++m)
+        for (int i = 0; i < 3; ++i) {
+            Jm[9 + m][i] = -Ax[3 * m + i];
+            Jm[9 + m][12 + i] = Ax[3 * m + i];
+            for (int k = 0; k < 3; ++k) {
+                Jm[9 + m][3 + 3 * k + i] = -Ax[3 * m + i] * J.u1[k] + Rx[3 * m + i] * J.d1[k];
+                Jm[9 + m][15 + 3 * k + i] = Ax[3 * m + i] * J.u2[k];
+            }
+        }
+}
+
+__device__ inline double joint_energy(const Geo& G, const double* x, int j) {
+    const JointDev J = G.joints[j];
+    double c[12];
+    joint_eval(J, x, c, nullptr);
+    double e = 0.0;
+    for (int m = 0; m < 12; ++m) e += J.kappa * c[m] * c[m] - G.lamJ[12 * (size_t)j + m] * c[m];
+    return e;
+}
+
+__global__ void k_joint_energy(Geo G, const double* x, double* part) {
+    const int env = blockIdx.y;
+    chunk_sum(
+        G.env_joint_start[env], G.env_joint_start[env + 1], [&](int j) -> double { return joint_energy(G, x, j); },
+        part_slot(part, ET_JOINT, G.n_envs, env));
+}
+
+// gradient J^T (2 kappa c - lambda) added to the bodies' free nodes, and the
+// Gauss-Newton Hessian 2 kappa J^T J (PSD by construction) as 8 x 8 node
+// blocks into staging; one thread, joints in order (deterministic sums)
+template <class T>
+__global__ void k_joint_gh(Geo G, const double* x, T* stage, double* g) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    for (int j = 0; j < G.n_joints; ++j) {
+        const JointDev J = G.joints[j];
+        double c[12], Jm[12][24], w[12];
+        joint_eval(J, x, c, Jm);
+        for (int m = 0; m < 12; ++m) w[m] = 2.0 * J.kappa * c[m] - G.lamJ[12 * (size_t)j + m];
+        for (int q = 0; q < 24; ++q) {
+            const bool body2 = q >= 12;
+            if (body2 ? J.fix2 : J.fix1) continue;
+            double v = 0.0;
+            for (int m = 0; m < 12; ++m) v += Jm[m][q] * w[m];
+            const int n = (body2 ? J.n2 : J.n1) + (q % 12) / 3;
+            g[3 * (size_t)n + q % 3] += v;
+        }
+        T* out = stage + (size_t)j * 64 * 9;
+        for (int a = 0; a < 8; ++a)
+            for (int b = 0; b < 8; ++b)
+                for (int r = 0; r < 3; ++r)
+                    for (int cc = 0; cc < 3; ++cc) {
+                        double v = 0.0;
+                        for (int m = 0; m < 12; ++m) v += Jm[m][3 * a + r] * Jm[m][3 * b + cc];
+                        out[(8 * a + b) * 9 + 3 * r + cc] = (T)(2.0 * J.kappa * v);
+                    }
+    }
+}
+
+// AL round test: |c| of the rotation part above tol_rel h, or of the slide
+// part above the env's step tolerance, asks for another round
+__global__ void k_joint_check(Geo G, const double* x, const double* tol_env, double tol_rel, int* need_env) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= G.n_joints) return;
+    const JointDev J = G.joints[j];
+    double c[12];
+    joint_eval(J, x, c, nullptr);
+    double mr = 0.0, ms = 0.0;
+    for (int m = 0; m < 9; ++m) mr = fmax(mr, fabs(c[m]));
+    for (int m = 9; m < 12; ++m) ms = fmax(ms, fabs(c[m]));
+    if (mr > tol_rel * G.h || ms > tol_env[J.env]) atomicMax(&need_env[J.env], 1);
+}
+
+// multiplier update lambda <- lambda - 2 kappa c for envs that need a round
+__global__ void k_joint_update(Geo G, const double* x, double* lamJ, const int* need_env) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= G.n_joints) return;
+    const JointDev J = G.joints[j];
+    if (!need_env[J.env]) return;
+    double c[12];
+    joint_eval(J, x, c, nullptr);
+    for (int m = 0; m < 12; ++m) lamJ[12 * (size_t)j + m] -= 2.0 * J.kappa * c[m];
 }
 
 // ---------------------------------------------------------------------------

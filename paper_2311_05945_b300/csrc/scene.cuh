@@ -16,6 +16,18 @@
 
 namespace zema {
 
+// A prismatic joint between two affine bodies (paper Sec. "Joint
+// Constraints"): constants fixed at the scene's initial state.
+struct JointDev {
+    int n1, n2;          // first node of each body (p', then the columns of A)
+    int fix1, fix2;      // body fixed (Dirichlet): its nodes take no gradient
+    int env;
+    double kappa;        // penalty stiffness
+    double B1[9], B2[9]; // inverses of each body's initial A (row-major)
+    double u1[3], u2[3]; // joint point minus the body's centre of mass, body rest frame
+    double d1[3];        // unit axis in body 1's rest frame
+};
+
 struct Geo {
     int n_nodes, n_soft, n_aff, n_tets, n_sv, n_edges, n_tris, n_envs, n_units, n_bodies;
     double h, dhat, eps_v;
@@ -43,6 +55,11 @@ struct Geo {
     const double* aff_stiff;
     const double* aff_com;          // 3: centre of mass in the caller's rest frame
     const int* env_aff_start;
+    // prismatic joints, ordered by env
+    int n_joints;
+    const JointDev* joints;
+    const int* env_joint_start;
+    const double* lamJ;             // 12 AL multipliers per joint
     // units of the block-Jacobi preconditioner: a soft node or an affine body
     const int* unit_kind;           // 0 soft node, 1 affine body
     const int* unit_idx;

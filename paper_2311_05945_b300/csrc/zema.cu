@@ -38,6 +38,11 @@ struct TetIn {
     std::vector<double> spring_x;
     double spring_k = 0.0;
 };
+struct JointIn {
+    int a1, a2;       // affine input indices
+    double axis[3];   // unit axis in world coordinates at the initial state
+    double kappa;     // <= 0: 1e3 x the mean of the two bodies' masses
+};
 struct AffIn {
     int env, mode;
     std::vector<double> V;
@@ -95,6 +100,11 @@ struct zema_scene {
     DBuf<double> x, v, xt, xhat, p, xtrial, g, b, r, z, pp, q, X, Xt, X1, stage_blk, stage_g, S_val, Minv_s, Minv_a;
     DBuf<double> pcg_work;  // work vectors of the grid-wide solve (6 x 3 n_nodes of the solve's type)
     DBuf<double> qtarget, lamA;
+    std::vector<JointIn> jin;
+    DBuf<JointDev> joints;
+    DBuf<int> env_joint_start;
+    DBuf<double> lamJ, lamJ_save;
+    std::vector<int> joint_order;  // device joint -> input joint
     // per env
     DBuf<double> tol2_env;
     DBuf<double> kappa, kappa_min, alpha, E, dmin, part, part2, part3, part4, part5, part6, part7;
@@ -590,6 +600,27 @@ void build(zema_scene* s) {
         for (int i = 0; i < 4; ++i)
             for (int j = 0; j < 4; ++j) rows[n0 + i].push_back(n0 + j);
     }
+    // prismatic joints: ordered by env; every pair of free nodes of the two
+    // bodies couples (8 x 8 blocks per joint)
+    s->joint_order.clear();
+    for (int e = 0; e < NE; ++e)
+        for (size_t j = 0; j < s->jin.size(); ++j)
+            if (s->ain[s->jin[j].a1].env == e) s->joint_order.push_back((int)j);
+    auto joint_nodes = [&](int jd, int* nodes) {
+        const JointIn& J = s->jin[s->joint_order[jd]];
+        const int n1 = s->aff_node0_h[J.a1], n2 = s->aff_node0_h[J.a2];
+        for (int k = 0; k < 4; ++k) {
+            nodes[k] = s->ain[J.a1].mode == 1 ? -1 : n1 + k;
+            nodes[4 + k] = s->ain[J.a2].mode == 1 ? -1 : n2 + k;
+        }
+    };
+    for (int jd = 0; jd < (int)s->joint_order.size(); ++jd) {
+        int nodes[8];
+        joint_nodes(jd, nodes);
+        for (int i = 0; i < 8; ++i)
+            for (int j = 0; j < 8; ++j)
+                if (nodes[i] >= 0 && nodes[j] >= 0) rows[nodes[i]].push_back(nodes[j]);
+    }
     std::vector<int> S_rowptr_h(nN + 1, 0), S_col_h, S_diag_h(nN);
     for (int n = 0; n < nN; ++n) {
         std::sort(rows[n].begin(), rows[n].end());
@@ -615,6 +646,14 @@ void build(zema_scene* s) {
         int n0 = aff_node0_dev[a];
         for (int i = 0; i < 4; ++i)
             for (int j = 0; j < 4; ++j) src[blk(n0 + i, n0 + j)].push_back(16 * s->n_tets + 16 * a + 4 * i + j);
+    }
+    for (int jd = 0; jd < (int)s->joint_order.size(); ++jd) {
+        int nodes[8];
+        joint_nodes(jd, nodes);
+        for (int i = 0; i < 8; ++i)
+            for (int j = 0; j < 8; ++j)
+                if (nodes[i] >= 0 && nodes[j] >= 0)
+                    src[blk(nodes[i], nodes[j])].push_back(16 * (s->n_tets + s->n_aff) + 64 * jd + 8 * i + j);
     }
     std::vector<int> S_src_ptr_h(s->n_sblocks + 1, 0), S_src_h;
     for (int k = 0; k < s->n_sblocks; ++k) {
@@ -731,6 +770,64 @@ void build(zema_scene* s) {
     up(s, s->aff_S, aff_S_h);
     up(s, s->aff_stiff, aff_stiff_h);
     up(s, s->aff_com, aff_com_dev);
+    // joint constants at the initial state
+    {
+        const int NJ = (int)s->joint_order.size();
+        std::vector<JointDev> jd(NJ);
+        std::vector<int> ejs(NE + 1, 0);
+        auto inv3 = [](const double* M, double* I) {
+            double C[9] = {M[4] * M[8] - M[5] * M[7], M[5] * M[6] - M[3] * M[8], M[3] * M[7] - M[4] * M[6],
+                           M[2] * M[7] - M[1] * M[8], M[0] * M[8] - M[2] * M[6], M[1] * M[6] - M[0] * M[7],
+                           M[1] * M[5] - M[2] * M[4], M[2] * M[3] - M[0] * M[5], M[0] * M[4] - M[1] * M[3]};
+            const double d = M[0] * C[0] + M[1] * C[1] + M[2] * C[2];
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) I[3 * i + j] = C[3 * j + i] / d;
+            return d;
+        };
+        for (int k = 0; k < NJ; ++k) {
+            const JointIn& J = s->jin[s->joint_order[k]];
+            const AffIn& B1 = s->ain[J.a1];
+            const AffIn& B2 = s->ain[J.a2];
+            JointDev& D = jd[k];
+            D.n1 = s->aff_node0_h[J.a1];
+            D.n2 = s->aff_node0_h[J.a2];
+            D.fix1 = B1.mode == 1;
+            D.fix2 = B2.mode == 1;
+            D.env = B1.env;
+            D.kappa = J.kappa > 0.0 ? J.kappa : 1e3 * 0.5 * (s->aff_m_in[J.a1] + s->aff_m_in[J.a2]);
+            const double* A1 = B1.q0 + 3;  // A by rows
+            const double* A2 = B2.q0 + 3;
+            if (!(inv3(A1, D.B1) > 0.0) || !(inv3(A2, D.B2) > 0.0))
+                fail(ZEMA_ERR_INVALID_ARG, "a jointed body's initial A is not invertible with det > 0");
+            // joint point: body 1's centre of mass at the initial state
+            double P1[3], P2[3];
+            for (int i = 0; i < 3; ++i) {
+                P1[i] = B1.q0[i];
+                P2[i] = B2.q0[i];
+                for (int j = 0; j < 3; ++j) {
+                    P1[i] += A1[3 * i + j] * s->aff_com_h[3 * J.a1 + j];
+                    P2[i] += A2[3 * i + j] * s->aff_com_h[3 * J.a2 + j];
+                }
+            }
+            for (int i = 0; i < 3; ++i) {
+                D.u1[i] = 0.0;
+                D.u2[i] = 0.0;
+                D.d1[i] = 0.0;
+                for (int j = 0; j < 3; ++j) {
+                    D.u2[i] += D.B2[3 * i + j] * (P1[j] - P2[j]);
+                    D.d1[i] += D.B1[3 * i + j] * J.axis[j];
+                }
+            }
+            ejs[D.env + 1] += 1;
+        }
+        for (int e = 0; e < NE; ++e) ejs[e + 1] += ejs[e];
+        s->joints.ensure(A, NJ + 1);
+        if (NJ) ZCHECK(cudaMemcpy(s->joints.p, jd.data(), NJ * sizeof(JointDev), cudaMemcpyHostToDevice));
+        up(s, s->env_joint_start, ejs);
+        std::vector<double> lz(12 * (size_t)NJ + 12, 0.0);
+        up(s, s->lamJ, lz);
+        s->lamJ_save.ensure(A, 12 * (size_t)NJ + 12);
+    }
     // surface rest positions relative to the centre of mass (affine)
     sv_x0_h.assign(3 * (size_t)s->n_sv, 0.0);
     for (int i = 0; i < s->n_sv; ++i)
@@ -803,7 +900,7 @@ void build(zema_scene* s) {
     for (DBuf<double>* b : {&s->xt, &s->xhat, &s->p, &s->xtrial, &s->g, &s->b, &s->r, &s->z, &s->pp, &s->q})
         b->ensure(A, n3);
     for (DBuf<double>* b : {&s->X, &s->Xt, &s->X1}) b->ensure(A, 3 * (size_t)s->n_sv + 3);
-    s->stage_blk.ensure(A, 144 * ((size_t)s->n_tets + s->n_aff) + 9);
+    s->stage_blk.ensure(A, 144 * ((size_t)s->n_tets + s->n_aff) + 576 * s->jin.size() + 9);
     s->stage_g.ensure(A, 12 * (size_t)s->n_tets + 12);
     s->S_val.ensure(A, 9 * (size_t)s->n_sblocks + 9);
     s->Minv_s.ensure(A, 9 * (size_t)nN + 9);
@@ -922,6 +1019,10 @@ void build(zema_scene* s) {
     G.aff_stiff = s->aff_stiff.p;
     G.aff_com = s->aff_com.p;
     G.env_aff_start = s->env_aff_start.p;
+    G.n_joints = (int)s->joint_order.size();
+    G.joints = s->joints.p;
+    G.env_joint_start = s->env_joint_start.p;
+    G.lamJ = s->lamJ.p;
     G.unit_kind = s->unit_kind.p;
     G.unit_idx = s->unit_idx.p;
     G.env_unit_start = s->env_unit_start.p;
@@ -1063,6 +1164,7 @@ void energy(zema_scene* s, const double* xe, const PairRec* pairs, const uint32_
         ZL(k_barrier_energy, red_grid(NE), kRedThreads, 0, st)(s->G, s->X1.p, pairs, poff, s->kappa.p, s->part.p);
     if (friction && s->n_lag)
         ZL(k_friction_energy, red_grid(NE), kRedThreads, 0, st)(s->G, s->X1.p, s->Xt.p, lagv(s), s->part.p);
+    if (s->G.n_joints) ZL(k_joint_energy, red_grid(NE), kRedThreads, 0, st)(s->G, xe, s->part.p);
     ZL(k_energy_total, div_up(NE, 64), 64, 0, st)(s->part.p, ET_COUNT, NE, s->E.p);
     ZLAUNCH();
     ZCHECK(cudaMemcpyAsync(s->hd, s->E.p, NE * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -1094,6 +1196,10 @@ void grad_hess_t(zema_scene* s, bool barrier, bool friction, bool hess) {
     ZLAUNCH();
     ZL(k_soft_grad, div_up(s->n_nodes, TB), TB, 0, st)(G, s->x.p, s->xhat.p, s->stage_g.p, s->g.p);
     ZLAUNCH();
+    if (G.n_joints) {
+        ZL(k_joint_gh<T>, 1, 32, 0, st)(G, s->x.p, stage + 144 * ((size_t)s->n_tets + s->n_aff), s->g.p);
+        ZLAUNCH();
+    }
     if (hess) {
         ZL(k_static_values<T>, div_up(s->n_sblocks, TB), TB, 0, st)(G, s->n_sblocks, stage, S_val);
         ZL(k_static_diag<T>, div_up(s->n_nodes, TB), TB, 0, st)(G, s->S_diag.p, S_val);
@@ -1832,6 +1938,9 @@ void do_step(zema_scene* s) {
     if (s->n_aff)
         ZCHECK(cudaMemcpyAsync(W.lam_save.p, s->lamA.p, 12 * (size_t)s->n_aff * sizeof(double),
                                cudaMemcpyDeviceToDevice, st));
+    if (G.n_joints)
+        ZCHECK(cudaMemcpyAsync(W.lamJ_save.p, s->lamJ.p, 12 * (size_t)G.n_joints * sizeof(double),
+                               cudaMemcpyDeviceToDevice, st));
     // predictor (Eq. 1-3)
     const double* gr = s->P.gravity;
     ZL(k_predict, div_up(s->n_nodes, TB), TB, 0, st)(G, s->x.p, s->v.p, s->xt.p, s->xhat.p, gr[0], gr[1], gr[2]);
@@ -1942,6 +2051,9 @@ void do_step(zema_scene* s) {
             if (s->n_aff == 0) break;
             ZCHECK(cudaMemsetAsync(s->need.p, 0, NE * sizeof(int), st));
             ZL(k_al_check, div_up(s->n_aff, 64), 64, 0, st)(G, s->x.p, kin(s), s->tolv.p, s->need.p);
+            if (G.n_joints)
+                ZL(k_joint_check, div_up(G.n_joints, 64), 64, 0, st)(G, s->x.p, s->tolv.p, s->P.newton_tol_rel,
+                                                                    s->need.p);
             ZLAUNCH();
             ZCHECK(cudaMemcpyAsync(s->hi, s->need.p, NE * sizeof(int), cudaMemcpyDeviceToHost, st));
             ZCHECK(cudaStreamSynchronize(st));
@@ -1950,6 +2062,8 @@ void do_step(zema_scene* s) {
             if (!any || rounds >= s->P.max_al_rounds) break;
             ++rounds;
             ZL(k_al_update, div_up(s->n_aff, 64), 64, 0, st)(G, s->x.p, s->qtarget.p, s->lamA.p, s->need.p);
+            if (G.n_joints)
+                ZL(k_joint_update, div_up(G.n_joints, 64), 64, 0, st)(G, s->x.p, s->lamJ.p, s->need.p);
             ZLAUNCH();
             for (int e = 0; e < NE; ++e) done[e] = s->hi[e] ? 0 : 1;
             // the resuming envs may have been left out of the last swept list:
@@ -2020,6 +2134,9 @@ void restore_step(zema_scene* s) {
     cudaMemcpyAsync(s->x.p, s->xt.p, n3 * sizeof(double), cudaMemcpyDeviceToDevice, st);
     if (s->n_aff && W.lam_save.p)
         cudaMemcpyAsync(s->lamA.p, W.lam_save.p, 12 * (size_t)s->n_aff * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    if (s->G.n_joints && W.lamJ_save.p)
+        cudaMemcpyAsync(s->lamJ.p, W.lamJ_save.p, 12 * (size_t)s->G.n_joints * sizeof(double),
+                        cudaMemcpyDeviceToDevice, st);
     cudaStreamSynchronize(st);
 }
 
@@ -2170,6 +2287,39 @@ zema_status zema_add_affine_body(zema_scene* s, int32_t env, const double* V_res
     s->ain.push_back(std::move(B));
     s->bodies.push_back({1, (int)s->ain.size() - 1});
     if (body_id) *body_id = (int32_t)s->bodies.size() - 1;
+    return ZEMA_OK;
+}
+
+zema_status zema_add_prismatic_joint(zema_scene* s, int32_t body1, int32_t body2, const double axis[3],
+                                     double kappa, int32_t* joint_id) {
+    if (!s) return ZEMA_ERR_INVALID_ARG;
+    if (s->finalized) {
+        s->err = "joints must be added before the first step";
+        return ZEMA_ERR_STATE;
+    }
+    const int nb = (int)s->bodies.size();
+    if (body1 < 0 || body1 >= nb || body2 < 0 || body2 >= nb || body1 == body2 || !axis ||
+        s->bodies[body1].first != 1 || s->bodies[body2].first != 1 || !std::isfinite(kappa)) {
+        s->err = "a prismatic joint needs two distinct affine bodies and an axis";
+        return ZEMA_ERR_INVALID_ARG;
+    }
+    JointIn J;
+    J.a1 = s->bodies[body1].second;
+    J.a2 = s->bodies[body2].second;
+    const AffIn &B1 = s->ain[J.a1], &B2 = s->ain[J.a2];
+    if (B1.env != B2.env || (B1.mode != 0 && B2.mode != 0)) {
+        s->err = "jointed bodies must share an env and at least one must be dynamic";
+        return ZEMA_ERR_INVALID_ARG;
+    }
+    const double n = std::sqrt(axis[0] * axis[0] + axis[1] * axis[1] + axis[2] * axis[2]);
+    if (!(n > 0.0) || !std::isfinite(n)) {
+        s->err = "joint axis must be a nonzero finite vector";
+        return ZEMA_ERR_INVALID_ARG;
+    }
+    for (int i = 0; i < 3; ++i) J.axis[i] = axis[i] / n;
+    J.kappa = kappa;
+    s->jin.push_back(J);
+    if (joint_id) *joint_id = (int32_t)s->jin.size() - 1;
     return ZEMA_OK;
 }
 

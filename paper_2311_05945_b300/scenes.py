@@ -248,6 +248,8 @@ class Scene:
     fingers: list = field(default_factory=list)
     # spring constraints: (tet body index, body-local vertices, targets (n, 3), k [N/m])
     springs: list = field(default_factory=list)
+    # prismatic joints: (affine index 1, affine index 2, world axis at t = 0, kappa; <= 0: default)
+    joints: list = field(default_factory=list)
 
     def body_order(self):
         """(kind, index) in the order bodies are added: tets first, then affines."""
@@ -691,4 +693,22 @@ def scene_resolution(n_seg: int, n_steps: int = 60, precision: int = 1, spacing:
     # offset so that no sphere vertex sits exactly above a lattice vertex
     s.affines.append(AffineBody(V, F, q_identity((0.0131, top, -0.0077)), rho=1000.0, stiffness=1e8, mu=0.5,
                                 mode=0, name="sphere"))
+    return s
+
+
+def scene_joint(axis=(0.0, 1.0, 0.0), fixed_base: bool = True, gravity=(0.0, -9.81, 0.0), n_steps: int = 10,
+                base_velocity=(0.0, 0.0, 0.0)) -> Scene:
+    """Two 0.1 m affine boxes 0.1 m apart along x (no contact), joined by a
+    prismatic joint along `axis`: body 1 (the base) fixed or dynamic with an
+    initial velocity, body 2 dynamic and at rest."""
+    p = Params(dt=0.01, gravity=gravity)
+    s = Scene("joint", p, n_steps=n_steps)
+    V, F = box_surface((0.1, 0.1, 0.1), 1)
+    qd = np.zeros(12)
+    qd[0:3] = base_velocity
+    s.affines.append(AffineBody(V, F, q_identity((0.0, 1.0, 0.0)), rho=1000.0, stiffness=1e8, mu=0.5,
+                                mode=1 if fixed_base else 0, qdot0=qd, name="base"))
+    s.affines.append(AffineBody(V, F, q_identity((0.2, 1.0, 0.0)), rho=1000.0, stiffness=1e8, mu=0.5, mode=0,
+                                name="slider"))
+    s.joints.append((0, 1, np.array(axis, dtype=np.float64), 0.0))
     return s

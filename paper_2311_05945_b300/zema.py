@@ -115,6 +115,7 @@ def lib():
     L.zema_record_warmstart_affine.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]
     L.zema_contact_forces.argtypes = [C.c_void_p, DP, C.c_int64]
     L.zema_set_material.argtypes = [C.c_void_p, C.c_int32, C.c_int32]
+    L.zema_add_prismatic_joint.argtypes = [C.c_void_p, C.c_int32, C.c_int32, DP, C.c_double, IP]
     L.zema_set_springs.argtypes = [C.c_void_p, C.c_int32, IP, C.c_int64, DP, C.c_double]
     L.zema_mlp_create.argtypes = [IP, C.c_int32, C.c_uint64, C.c_void_p, C.POINTER(C.c_void_p)]
     L.zema_mlp_destroy.argtypes = [C.c_void_p]
@@ -248,6 +249,10 @@ class Scene:
                 _check(L.zema_set_material(h, self.body_ids[i], int(b.model)), h)
         for (i, verts, targets, k) in scene.springs:
             self.set_springs(i, verts, targets, k)
+        for (a1, a2, axis, kappa) in scene.joints:
+            ax = _d(axis)
+            _check(L.zema_add_prismatic_joint(h, self.affine_body_id(a1), self.affine_body_id(a2), _dp(ax),
+                                              float(kappa), None), h)
         _check(L.zema_finalize(h), h)
 
     def close(self):

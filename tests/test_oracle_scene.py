@@ -299,3 +299,56 @@ def test_spring_forces_balance_momentum(model):
         spring = (2.0 * 2.0e3 * (x1[verts] - targets)).sum(0)
         scale = np.abs(spring).max() + np.abs(inertia).max()
         assert np.abs(inertia + spring).max() < 1e-6 * scale
+
+
+def test_joint_constraint_zero_along_axis_only():
+    # the constraint vanishes at the initial state and when body 2 moves
+    # along the axis; a sideways move d of body 2 gives |slide part| = |d|
+    # (r = -d, axis unit), and a relative rotation gives a nonzero rotation part
+    s = S.scene_joint(axis=(1.0, 0.0, 0.0), fixed_base=False, gravity=(0.0, 0.0, 0.0))
+    o = Oracle(s)
+    assert np.abs(o.joint_constraint(0)).max() < 1e-15
+    st = o.get_state(1)
+    for d, along in (((0.05, 0.0, 0.0), True), ((0.0, 0.03, 0.0), False), ((0.0, 0.0, -0.02), False)):
+        x = st.copy()
+        x[0:3] += d
+        o.set_state(1, x)
+        c = o.joint_constraint(0)
+        assert np.abs(c[:9]).max() < 1e-15
+        if along:
+            assert np.abs(c[9:]).max() < 1e-15
+        else:
+            assert abs(np.linalg.norm(c[9:]) - np.linalg.norm(d)) < 1e-15
+    x = st.copy()
+    th = 0.01
+    x[3:12] = np.array([[np.cos(th), -np.sin(th), 0.0], [np.sin(th), np.cos(th), 0.0], [0.0, 0.0, 1.0]]).ravel()
+    o.set_state(1, x)
+    assert np.abs(o.joint_constraint(0)[:9]).max() > 0.5 * th
+
+
+def test_joint_along_gravity_is_free_fall():
+    # fixed base, axis along gravity: the slider's free fall keeps c = 0, so
+    # the joint exerts no force and the motion is the exact free fall
+    s = S.scene_joint(axis=(0.0, 1.0, 0.0), fixed_base=True)
+    o = Oracle(s, tol_scale=1e-3)
+    q0 = o.affine_q(1).copy()
+    o.step(5)
+    h, g, n = s.params.dt, s.params.gravity[1], 5
+    q = o.affine_q(1)
+    assert abs(q[1] - q0[1] - h * h * g * n * (n + 1) / 2) < 1e-9
+    assert np.abs(np.delete(q - q0, 1)).max() < 1e-9
+
+
+def test_joint_across_gravity_holds_the_slider():
+    # fixed base, axis horizontal: gravity acts across the axis, and after
+    # the augmented-Lagrangian rounds the slide part of c (the slider's drop)
+    # stays within the Newton step tolerance
+    s = S.scene_joint(axis=(1.0, 0.0, 0.0), fixed_base=True)
+    o = Oracle(s)
+    tol = s.params.newton_tol_rel * o.diag() * s.params.dt
+    for _ in range(5):
+        o.step(1)
+        c = o.joint_constraint(0)
+        assert np.abs(c[9:]).max() <= tol
+        assert np.abs(c[:9]).max() <= s.params.newton_tol_rel * s.params.dt
+    assert abs(o.affine_q(1)[1] - 1.0) < 5 * tol
