@@ -343,45 +343,127 @@ __global__ void k_query(BPView v, int kind, int nq, const double* qbox, const do
     if (!WRITE && l == 0) cnt[q] = c;
 }
 
-// Oversize queries (boxes over kMaxCells cells): one block per query; thread
-// t tests the contiguous entry range [lo + t c, lo + (t + 1) c) of the query's
-// env (the whole table without env ranges) so that a block scan of the
-// per-thread counts gives each match its position in entry order.
-template <bool WRITE>
-__global__ void k_query_big(BPView v, int kind, const int* qlist, const double* qbox, const double* ebox_all,
-                            int n_entries_all, uint32_t* cnt, const uint32_t* off, int2* out) {
-    __shared__ uint32_t sc[256];
-    int q = qlist[blockIdx.x];
-    Box6 a = ld_box(qbox + 6 * (size_t)q);
-    int lo, hi;
-    env_entries(v, kind, q, n_entries_all, lo, hi);  // other envs' entries never pair
-    int chunk = (hi - lo + (int)blockDim.x - 1) / (int)blockDim.x;
-    int e0 = lo + threadIdx.x * chunk, e1 = min(e0 + chunk, hi);
-    auto hit = [&](int e) -> bool {
-        if (kind == 1 && e <= q) return false;
-        Box6 b = ld_box(ebox_all + 6 * (size_t)e);
-        if (!overlap(a, b)) return false;
-        return kind == 0 ? pt_ok(v, q, e) : ee_ok(v, q, e);
-    };
-    uint32_t c = 0;
-    for (int e = e0; e < e1; ++e) c += hit(e) ? 1u : 0u;
+// Block-wide placement: each thread counts the hits of its items, an
+// exclusive scan in thread order gives each thread its first output slot, and
+// a second pass writes (so the output is in item order).  Returns the total.
+template <bool WRITE, class Count, class Write>
+__device__ __forceinline__ uint32_t block_place(uint32_t* sc, uint32_t base, Count count, Write write) {
+    const uint32_t c = count();
     sc[threadIdx.x] = c;
     __syncthreads();
     if (threadIdx.x == 0) {
         uint32_t run = 0;
         for (int t = 0; t < (int)blockDim.x; ++t) {
-            uint32_t x = sc[t];
+            const uint32_t x = sc[t];
             sc[t] = run;
             run += x;
         }
-        if (!WRITE) cnt[q] = run;
+        sc[blockDim.x] = run;
     }
     __syncthreads();
-    if (WRITE) {
-        uint32_t o = off[q] + sc[threadIdx.x];
-        for (int e = e0; e < e1; ++e)
-            if (hit(e)) out[o++] = make_int2(q, e);
+    if (WRITE) write(base + sc[threadIdx.x]);
+    const uint32_t total = sc[blockDim.x];
+    __syncthreads();
+    return total;
+}
+
+// Oversize queries (boxes over kMaxQueryCells cells): one block per query.
+//  - Up to kWalkCells cells, and at most a quarter as many cells as the env
+//    has entries: the block walks the query's cells (thread t a
+//    contiguous run of them in z, y, x order) through the grid exactly as
+//    k_query does, then the oversize-entry list of the query's env; hits in
+//    cell order, then list order.
+//  - Otherwise: thread t tests the contiguous entry range [lo + t c,
+//    lo + (t + 1) c) of the query's env (the whole table without env ranges);
+//    hits in entry order.
+constexpr double kWalkCells = 8192.0;
+template <bool WRITE>
+__global__ void k_query_big(BPView v, int kind, const int* qlist, const double* qbox, const double* ebox_all,
+                            int n_entries_all, uint32_t* cnt, const uint32_t* off, int2* out, const int* qcb,
+                            const int* ecb_all, Table T, const int* big, int nbig) {
+    __shared__ uint32_t sc[257];
+    const int q = qlist[blockIdx.x];
+    const Box6 a = ld_box(qbox + 6 * (size_t)q);
+    const uint32_t base = WRITE ? off[q] : 0u;
+    auto test = [&](int e) -> bool {
+        if (kind == 1 && e <= q) return false;
+        Box6 b = ld_box(ebox_all + 6 * (size_t)e);
+        if (!overlap(a, b)) return false;
+        return kind == 0 ? pt_ok(v, q, e) : ee_ok(v, q, e);
+    };
+    const double ncell = box_cells(a, v.inv_cell);
+    int lo, hi;
+    env_entries(v, kind, q, n_entries_all, lo, hi);  // other envs' entries never pair
+    // walk the cells only where that is clearly less work than the scan
+    if (ncell <= kWalkCells && 4.0 * ncell <= (double)(hi - lo)) {
+        int qc[6];
+        for (int k = 0; k < 6; ++k) qc[k] = qcb[6 * (size_t)q + k];
+        const int nx = qc[3] - qc[0] + 1, ny = qc[4] - qc[1] + 1, nz = qc[5] - qc[2] + 1;
+        const int nc = nx * ny * nz;
+        const int chunk = (nc + (int)blockDim.x - 1) / (int)blockDim.x;
+        const int c0 = threadIdx.x * chunk, c1 = min(c0 + chunk, nc);
+        // hits of one grid cell (linear index li), emitted through f
+        auto cell_hits = [&](int li, auto f) {
+            const int cx = qc[0] + li % nx, cy = qc[1] + (li / nx) % ny, cz = qc[2] + li / (nx * ny);
+            const uint64_t ck = pack_cell(cx, cy, cz);
+            const uint64_t bkt = T.bucket_base + (mix64(ck) & T.tmask);
+            const uint32_t s0 = T.bstart[bkt], s1 = T.bend[bkt];
+            for (uint32_t j = s0; j < s1; ++j) {
+                if (T.ecell[j] != ck) continue;
+                const int e = T.eprim[j];
+                if (kind == 1 && e <= q) continue;
+                const int* ec = ecb_all + 6 * (size_t)e;
+                // emit only from the cell holding the min corner of the boxes' intersection
+                if (max(qc[0], ec[0]) != cx || max(qc[1], ec[1]) != cy || max(qc[2], ec[2]) != cz) continue;
+                if (test(e)) f(e);
+            }
+        };
+        const uint32_t n_grid = block_place<WRITE>(
+            sc, base,
+            [&]() {
+                uint32_t c = 0;
+                for (int li = c0; li < c1; ++li) cell_hits(li, [&](int) { ++c; });
+                return c;
+            },
+            [&](uint32_t o) {
+                for (int li = c0; li < c1; ++li) cell_hits(li, [&](int e) { out[o++] = make_int2(q, e); });
+            });
+        // oversize entries (not in the grid), ascending ids, the query's env
+        int b_lo = 0, b_hi = nbig;
+        if (v.env_tri_start) {
+            b_lo = lower_bound_i(big, nbig, lo);
+            b_hi = lower_bound_i(big, nbig, hi);
+        }
+        const int bchunk = (b_hi - b_lo + (int)blockDim.x - 1) / (int)blockDim.x;
+        const int k0 = b_lo + threadIdx.x * bchunk, k1 = min(k0 + bchunk, b_hi);
+        const uint32_t n_big = block_place<WRITE>(
+            sc, base + n_grid,
+            [&]() {
+                uint32_t c = 0;
+                for (int k = k0; k < k1; ++k) c += test(big[k]) ? 1u : 0u;
+                return c;
+            },
+            [&](uint32_t o) {
+                for (int k = k0; k < k1; ++k)
+                    if (test(big[k])) out[o++] = make_int2(q, big[k]);
+            });
+        if (!WRITE && threadIdx.x == 0) cnt[q] = n_grid + n_big;
+        return;
     }
+    const int chunk = (hi - lo + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int e0 = lo + threadIdx.x * chunk, e1 = min(e0 + chunk, hi);
+    const uint32_t n = block_place<WRITE>(
+        sc, base,
+        [&]() {
+            uint32_t c = 0;
+            for (int e = e0; e < e1; ++e) c += test(e) ? 1u : 0u;
+            return c;
+        },
+        [&](uint32_t o) {
+            for (int e = e0; e < e1; ++e)
+                if (test(e)) out[o++] = make_int2(q, e);
+        });
+    if (!WRITE && threadIdx.x == 0) cnt[q] = n;
 }
 
 // large-query flag of point or edge query boxes (never for skipped envs)
@@ -501,8 +583,12 @@ void BroadPhase::run(Allocator* A, const BPView& v, cudaStream_t st) {
     if (ne)
         ZL(k_query<false>, div_up((size_t)ne * kQueryLanes, TB), TB, 0, st)(v, 1, ne, ebox.p, ebox.p, ecb.p, ecb.p, TE, big_e.p, (int)nbe, ne,
                                                       qcnt_ee.p, nullptr, nullptr);
-    if (nbp) ZL(k_query_big<false>, nbp, 256, 0, st)(v, 0, big_p.p, pbox.p, tbox.p, nt, qcnt_pt.p, nullptr, nullptr);
-    if (nbq) ZL(k_query_big<false>, nbq, 256, 0, st)(v, 1, big_q.p, ebox.p, ebox.p, ne, qcnt_ee.p, nullptr, nullptr);
+    if (nbp)
+        ZL(k_query_big<false>, nbp, 256, 0, st)(v, 0, big_p.p, pbox.p, tbox.p, nt, qcnt_pt.p, nullptr, nullptr, pcb.p,
+                                                tcb.p, TT, big_t.p, (int)nbt);
+    if (nbq)
+        ZL(k_query_big<false>, nbq, 256, 0, st)(v, 1, big_q.p, ebox.p, ebox.p, ne, qcnt_ee.p, nullptr, nullptr, ecb.p,
+                                                ecb.p, TE, big_e.p, (int)nbe);
     ZLAUNCH();
     tmp.ensure(A, std::max(scan_tmp_size(mx), E ? radix_tmp_size(E) : 0));
     exclusive_scan(qcnt_pt.p, qoff_pt.p, nsv, tmp.p, st);
@@ -520,8 +606,12 @@ void BroadPhase::run(Allocator* A, const BPView& v, cudaStream_t st) {
     if (ne && n_ee)
         ZL(k_query<true>, div_up((size_t)ne * kQueryLanes, TB), TB, 0, st)(v, 1, ne, ebox.p, ebox.p, ecb.p, ecb.p, TE, big_e.p, (int)nbe, ne, nullptr,
                                                      qoff_ee.p, ee.p);
-    if (nbp && n_pt) ZL(k_query_big<true>, nbp, 256, 0, st)(v, 0, big_p.p, pbox.p, tbox.p, nt, nullptr, qoff_pt.p, pt.p);
-    if (nbq && n_ee) ZL(k_query_big<true>, nbq, 256, 0, st)(v, 1, big_q.p, ebox.p, ebox.p, ne, nullptr, qoff_ee.p, ee.p);
+    if (nbp && n_pt)
+        ZL(k_query_big<true>, nbp, 256, 0, st)(v, 0, big_p.p, pbox.p, tbox.p, nt, nullptr, qoff_pt.p, pt.p, pcb.p, tcb.p,
+                                               TT, big_t.p, (int)nbt);
+    if (nbq && n_ee)
+        ZL(k_query_big<true>, nbq, 256, 0, st)(v, 1, big_q.p, ebox.p, ebox.p, ne, nullptr, qoff_ee.p, ee.p, ecb.p, ecb.p,
+                                               TE, big_e.p, (int)nbe);
     ZLAUNCH();
 }
 

@@ -121,12 +121,20 @@ def scene_surface(s):
     return P, sv[:, 0].copy(), bclass, benv, e, t
 
 
-@pytest.mark.parametrize("name", ["c2", "c3x4"])
+@pytest.mark.parametrize("name", ["c2", "c3x4", "mixed_scale"])
 def test_large_surfaces_bit_exact(name):
     # ~10k primitives (the grasp: counts and flags scanned by the single-CTA
-    # scan) and ~40k (four batched envs: the multi-block scan)
+    # scan), ~40k (four batched envs: the multi-block scan), and a 1 cm soft
+    # box under a finely meshed sphere, where the grid cell follows the
+    # sphere's 1.5 mm edges and the box's edges become oversize queries that
+    # walk the grid cells
     from paper_2311_05945_b300 import zema as Z
-    s = S.scene_c2() if name == "c2" else S.scene_c3(n_envs=4, n_steps=1)
+    if name == "c2":
+        s = S.scene_c2()
+    elif name == "c3x4":
+        s = S.scene_c3(n_envs=4, n_steps=1)
+    else:
+        s = S.scene_resolution(105, n_steps=1)
     P, svb, bc, be, e, t = scene_surface(s)
     n_prims = len(t) + len(e)
     assert (4096 < n_prims <= 32768) if name == "c2" else n_prims > 32768
