@@ -1212,8 +1212,14 @@ void grad_hess_t(zema_scene* s, bool barrier, bool friction, bool hess) {
     s->pG.ensure(A, 12 * (size_t)nr + 12);
     T* pH = (T*)s->pH.p;
     if (na) {
-        ZL(k_barrier_gh<T>, div_up(na, kCoopPairs), kCoopLanes * kCoopPairs, 0, st)(G, s->X.p, s->act.p, (int)na,
-                                                                                 s->kappa.p, pH, s->pG.p);
+        // few pairs: a half-warp per pair keeps many warps busy; many pairs:
+        // 32 per warp issues the FP64 part once per 32 pairs
+        if (na >= (uint32_t)kWarpLayoutMinPairs)
+            ZL(k_barrier_gh<T>, div_up(na, kWarpPairs), kWarpPairs, 0, st)(G, s->X.p, s->act.p, (int)na, s->kappa.p,
+                                                                          pH, s->pG.p);
+        else
+            ZL(k_barrier_gh_half<T>, div_up(na, kCoopPairs), kCoopLanes * kCoopPairs, 0, st)(
+                G, s->X.p, s->act.p, (int)na, s->kappa.p, pH, s->pG.p);
     }
     if (nl)
         ZL(k_friction_gh<T>, div_up(nl, 128), 128, 0, st)(G, s->X.p, s->Xt.p, lagv(s), pH + 144 * (size_t)na,
@@ -2783,32 +2789,17 @@ __global__ void k_sv_env_of(const int* sv_body, const int* b_env, int n, int* sv
     if (i < n) sv_env[i] = b_env[sv_body[i]];
 }
 
-__global__ void __launch_bounds__(kCoopLanes * kCoopPairs) k_local_barrier(const double* x12, const int* is_ee,
-                                                                           const double* eps_x, int n, double dhat,
-                                                                           double* e_out, double* g_out,
-                                                                           double* H_out) {
-    __shared__ double sm[kCoopPairs][kCoopSmem];
-    const int grp = threadIdx.x / kCoopLanes, lane = threadIdx.x & (kCoopLanes - 1);
-    const int i = blockIdx.x * kCoopPairs + grp;
-    if (i >= n) return;
-    const unsigned mask = 0xFFFFu << (threadIdx.x & 16);
-    double* H = sm[grp];
-    int act = 0;
-    if (lane == 0) {
-        V3 x[4];
+// the scene's barrier kernel on caller stencils (kappa = 1)
+__global__ void __launch_bounds__(kWarpPairs) k_local_barrier(const double* x12, const int* is_ee,
+                                                             const double* eps_x, int n, double dhat,
+                                                             double* e_out, double* g_out, double* H_out) {
+    auto load = [&](int i, V3* x, int& ee, double& eps, double& kap) {
         for (int k = 0; k < 4; ++k) x[k] = ld3(x12 + 12 * (size_t)i + 3 * k);
-        double E = 0.0, g[12];
-        act = pair_barrier<double>(x, is_ee[i] != 0, dhat, 1.0, eps_x[i], E, g, SMat<12>{H, 1}, true);
-        e_out[i] = act ? E : 0.0;
-        for (int a = 0; a < 12; ++a) g_out[12 * (size_t)i + a] = act ? g[a] : 0.0;
-    }
-    act = __shfl_sync(mask, act, 0, kCoopLanes);
-    if (!act) {
-        for (int e = lane; e < 144; e += kCoopLanes) H_out[144 * (size_t)i + e] = 0.0;
-        return;
-    }
-    __syncwarp(mask);
-    coop_project<double>(H, H + 144, H + 244, 1.0, H_out + 144 * (size_t)i, mask);
+        ee = is_ee[i];
+        eps = eps_x[i];
+        kap = 1.0;
+    };
+    barrier_gh_warp<double>(n, load, dhat, H_out, g_out, e_out);
 }
 
 __global__ void k_local_distance(const double* x12, const int* is_ee, int n, double* d2, double* w) {
@@ -2984,7 +2975,7 @@ zema_status zema_local_barrier(int64_t n, const double* x12, const int32_t* is_e
         double* E = T.put<double>(nullptr, (size_t)n);
         double* g = T.put<double>(nullptr, 12 * (size_t)n);
         double* H = T.put<double>(nullptr, 144 * (size_t)n);
-        ZL(k_local_barrier, div_up(n, kCoopPairs), kCoopLanes * kCoopPairs, 0, st)(dx, de, dp, (int)n, dhat, E, g, H);
+        ZL(k_local_barrier, div_up(n, kWarpPairs), kWarpPairs, 0, st)(dx, de, dp, (int)n, dhat, E, g, H);
         ZLAUNCH();
         get(e_out, E, n, st);
         get(g_out, g, 12 * n, st);
