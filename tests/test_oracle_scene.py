@@ -1,7 +1,9 @@
 """Scene-level pins of the oracle: analytic free fall, closed-form mass
 properties, finite differences of the complete incremental potential,
 monotone Newton energies, intersection-free trajectories (independent
-triangle-triangle tests), momentum conservation and Coulomb sliding."""
+triangle-triangle tests), momentum conservation, Coulomb sliding on flat
+ground and down a slope, static friction below the friction angle, kinematic
+target tracking by the augmented Lagrangian and the barrier-stiffness floor."""
 import numpy as np
 import pytest
 
@@ -352,3 +354,124 @@ def test_joint_across_gravity_holds_the_slider():
         assert np.abs(c[9:]).max() <= tol
         assert np.abs(c[:9]).max() <= s.params.newton_tol_rel * s.params.dt
     assert abs(o.affine_q(1)[1] - 1.0) < 5 * tol
+
+
+def _rz(theta):
+    c, s = np.cos(theta), np.sin(theta)
+    return np.array([[c, -s, 0.0], [s, c, 0.0], [0.0, 0.0, 1.0]])
+
+
+def _block_on_slope(theta, mu):
+    # a fixed slab rotated by theta about z and a flat block resting on its top
+    # face (gap 2 mm along the slope normal), both with friction coefficient mu
+    p = S.Params(dt=0.01)
+    s = S.Scene("slope", p)
+    R = _rz(theta)
+    Vf, Ff = S.box_surface((4.0, 0.1, 4.0), 1)
+    qf = np.zeros(12)
+    qf[3:] = R.reshape(-1)
+    s.affines.append(S.AffineBody(Vf, Ff, qf, rho=1000.0, stiffness=1e8, mu=mu, mode=1))
+    V, F = S.box_surface((0.2, 0.04, 0.2), 1)
+    qb = np.zeros(12)
+    qb[:3] = R @ np.array([0.3, 0.05 + 0.02 + 0.002, 0.1])
+    qb[3:] = R.reshape(-1)
+    s.affines.append(S.AffineBody(V, F, qb, rho=1000.0, stiffness=1e8, mu=mu))
+    return s
+
+
+@pytest.mark.parametrize("mu", [0.1, 0.2])
+def test_sliding_down_a_slope(mu):
+    # Eq. 9-10 with the normal force of the barrier (Eq. 4): on a slope of
+    # angle theta with mu < tan(theta) the block slides with the closed-form
+    # acceleration g (sin(theta) - mu cos(theta)) along the downhill direction
+    # -(cos(theta), sin(theta), 0).  A wrong normal-force scale, a friction
+    # term that ignores the slope's normal, or a sign error changes it.
+    theta = 0.3
+    s = _block_on_slope(theta, mu)
+    o = Oracle(s, tol_scale=1e-2)
+    down = -np.array([np.cos(theta), np.sin(theta), 0.0])
+    vs = []
+    touched = 0
+    for k in range(24):
+        st = o.step(1)
+        touched += st[0, 0, 3] > 0
+        vs.append(o.get_state(1)[12:15] @ down)
+    assert touched >= 20
+    a = (vs[23] - vs[11]) / (12 * s.params.dt)
+    a_ref = 9.81 * (np.sin(theta) - mu * np.cos(theta))
+    assert abs(a - a_ref) < 0.02 * a_ref, (a, a_ref, vs)
+
+
+def test_block_sticks_on_a_slope_below_the_friction_angle():
+    # mu > tan(theta): static friction holds the block.  The smoothed friction
+    # of Eq. 10 lets it creep, but only below eps_v (the speed at which f1
+    # saturates), since the force needed is below mu N.
+    theta = 0.3
+    s = _block_on_slope(theta, 0.5)
+    o = Oracle(s, tol_scale=1e-3)
+    speeds = []
+    for k in range(30):
+        st = o.step(1)
+        assert st[0, 0, 3] > 0 or k < 3
+        speeds.append(np.linalg.norm(o.get_state(1)[12:15]))
+    assert max(speeds[10:]) < s.params.eps_v, speeds
+
+
+def _kinematic_scene(max_al_rounds):
+    # a kinematic box whose target starts at rest and moves at 5 m/s along x
+    # while turning at 2 rad/s about z, plus a fixed slab far below it
+    p = S.Params(dt=0.01, max_al_rounds=max_al_rounds)
+    s = S.Scene("kinematic", p)
+    V, F = S.box_surface((0.1, 0.1, 0.1), 1)
+    s.affines.append(S.AffineBody(V, F, S.q_identity((0.0, 0.5, 0.0)), rho=1000.0, stiffness=1e8, mu=0.0,
+                                  mode=2))
+    Vf, Ff = S.box_surface((1.0, 0.1, 1.0), 1)
+    s.affines.append(S.AffineBody(Vf, Ff, S.q_identity((0.0, -0.05, 0.0)), rho=1000.0, stiffness=1e8,
+                                  mu=0.0, mode=1))
+
+    def target(n):
+        q = np.zeros(12)
+        t = (n + 1) * p.dt
+        q[:3] = (5.0 * t, 0.5, 0.0)
+        q[3:] = _rz(2.0 * t).reshape(-1)
+        return q
+
+    s.script = lambda n: {0: target(n)}
+    return s, target
+
+
+def test_kinematic_body_tracks_its_target():
+    # Eq. 13: the augmented Lagrangian drives a kinematic body onto its
+    # scripted target.  The penalty kappa_A = 1e3 m alone leaves the body
+    # behind by about 1e-3 of the gap between the inertial prediction and the
+    # target (5 cm on the first step, above the Newton tolerance); the
+    # multiplier update removes that lag, so after every step max |q - q~| is
+    # within the tolerance, translation and A block alike.  A sign error in the
+    # update doubles the lag instead.
+    s, target = _kinematic_scene(10)
+    o = Oracle(s)
+    tol = s.params.newton_tol_rel * o.diag() * s.params.dt
+    rounds = 0
+    for n in range(6):
+        st = o.step(1)
+        rounds += st[0, 0, 2]
+        q = o.affine_q(0)
+        assert np.abs(q - target(n)).max() <= tol, (n, q - target(n))
+    assert rounds > 0
+
+    # the same scene with the multiplier switched off misses the first target
+    s0, _ = _kinematic_scene(0)
+    o0 = Oracle(s0)
+    o0.step(1)
+    assert np.abs(o0.affine_q(0) - target(0)).max() > tol
+
+
+def test_kappa_min_is_a_thousand_mean_lumped_masses():
+    # the adaptive barrier stiffness floor: 1e3 x the mean lumped soft-vertex mass
+    s = S.scene_c1()
+    o = Oracle(s)
+    m = o.lumped_mass()
+    o.step(1)  # kappa is set at the first step
+    assert abs(o.kappa_min() - 1e3 * m.mean()) < 1e-12 * o.kappa_min()
+    k = o.kappa()
+    assert o.kappa_min() <= k <= 100 * o.kappa_min()
