@@ -712,3 +712,54 @@ def scene_joint(axis=(0.0, 1.0, 0.0), fixed_base: bool = True, gravity=(0.0, -9.
                                 name="slider"))
     s.joints.append((0, 1, np.array(axis, dtype=np.float64), 0.0))
     return s
+
+
+def rotation_z(theta: float) -> np.ndarray:
+    """Rotation by theta (rad) about +z."""
+    c, s = np.cos(theta), np.sin(theta)
+    return np.array([[c, -s, 0.0], [s, c, 0.0], [0.0, 0.0, 1.0]])
+
+
+def scene_slope(theta: float = 0.3, mu: float = 0.1, n_steps: int = 24, precision: int = 0) -> Scene:
+    """A fixed 4 m slab rotated by theta about z and a 0.2 x 0.04 x 0.2 m
+    block (1000 kg/m^3) resting on its top face, 2 mm above it along the slope
+    normal; both bodies have friction coefficient mu.  The downhill direction
+    is -(cos theta, sin theta, 0)."""
+    p = Params(dt=0.01, precision=precision)
+    s = Scene("slope", p, n_steps=n_steps)
+    R = rotation_z(theta)
+    Vf, Ff = box_surface((4.0, 0.1, 4.0), 1)
+    qf = np.zeros(12)
+    qf[3:] = R.reshape(-1)
+    s.affines.append(AffineBody(Vf, Ff, qf, rho=1000.0, stiffness=1e8, mu=mu, mode=1, name="slope"))
+    V, F = box_surface((0.2, 0.04, 0.2), 1)
+    qb = np.zeros(12)
+    qb[:3] = R @ np.array([0.3, 0.05 + 0.02 + 0.002, 0.1])
+    qb[3:] = R.reshape(-1)
+    s.affines.append(AffineBody(V, F, qb, rho=1000.0, stiffness=1e8, mu=mu, name="block"))
+    return s
+
+
+def kinematic_track_target(n: int, dt: float = 0.01, speed: float = 5.0, omega: float = 2.0) -> np.ndarray:
+    """Target q at the end of step n of `scene_kinematic_track`: from (0, 0.5,
+    0) along +x at `speed` m/s, turning about z at `omega` rad/s."""
+    q = np.zeros(12)
+    t = (n + 1) * dt
+    q[:3] = (speed * t, 0.5, 0.0)
+    q[3:] = rotation_z(omega * t).reshape(-1)
+    return q
+
+
+def scene_kinematic_track(max_al_rounds: int = 10, n_steps: int = 6, precision: int = 0) -> Scene:
+    """A kinematic 0.1 m box, at rest at (0, 0.5, 0), scripted onto
+    `kinematic_track_target`, plus a fixed slab 0.45 m below it (no contact)."""
+    p = Params(dt=0.01, max_al_rounds=max_al_rounds, precision=precision)
+    s = Scene("kinematic_track", p, n_steps=n_steps)
+    V, F = box_surface((0.1, 0.1, 0.1), 1)
+    s.affines.append(AffineBody(V, F, q_identity((0.0, 0.5, 0.0)), rho=1000.0, stiffness=1e8, mu=0.0, mode=2,
+                                name="kinematic"))
+    Vf, Ff = box_surface((1.0, 0.1, 1.0), 1)
+    s.affines.append(AffineBody(Vf, Ff, q_identity((0.0, -0.05, 0.0)), rho=1000.0, stiffness=1e8, mu=0.0,
+                                mode=1, name="slab"))
+    s.script = lambda n: {0: kinematic_track_target(n, p.dt)}
+    return s

@@ -11,6 +11,8 @@ from oracle import oracle as O
 from oracle.oracle import Oracle
 from paper_2311_05945_b300 import scenes as S
 
+from geometry import tri_tri_intersect
+
 
 def test_free_fall_analytic():
     # Eq. 1 / Eq. 2 with no contact: the minimiser of the IP is the predictor,
@@ -108,27 +110,6 @@ def test_full_energy_gradient_fd():
     assert err < 1e-5, err
     ev = np.linalg.eigvalsh(0.5 * (H + H.T))
     assert ev.min() > 0  # projected Hessian plus mass terms: SPD
-
-
-def tri_tri_intersect(P, T1, T2):
-    """Independent FP64 test: does any edge of one triangle cross the other."""
-    def orient(a, b, c, d):
-        return np.einsum("...i,...i->...", np.cross(b - a, c - a), d - a)
-
-    def seg_tri(p, q, a, b, c):
-        s1, s2 = orient(a, b, c, p), orient(a, b, c, q)
-        o1, o2, o3 = orient(p, q, a, b), orient(p, q, b, c), orient(p, q, c, a)
-        cross = (s1 * s2 <= 0)
-        same = ((o1 >= 0) & (o2 >= 0) & (o3 >= 0)) | ((o1 <= 0) & (o2 <= 0) & (o3 <= 0))
-        return cross & same
-
-    A = P[T1]
-    B = P[T2]
-    hit = np.zeros(len(T1), dtype=bool)
-    for (i, j) in ((0, 1), (1, 2), (2, 0)):
-        hit |= seg_tri(A[:, i], A[:, j], B[:, 0], B[:, 1], B[:, 2])
-        hit |= seg_tri(B[:, i], B[:, j], A[:, 0], A[:, 1], A[:, 2])
-    return hit
 
 
 def surface_world(o, s):
@@ -356,29 +337,6 @@ def test_joint_across_gravity_holds_the_slider():
     assert abs(o.affine_q(1)[1] - 1.0) < 5 * tol
 
 
-def _rz(theta):
-    c, s = np.cos(theta), np.sin(theta)
-    return np.array([[c, -s, 0.0], [s, c, 0.0], [0.0, 0.0, 1.0]])
-
-
-def _block_on_slope(theta, mu):
-    # a fixed slab rotated by theta about z and a flat block resting on its top
-    # face (gap 2 mm along the slope normal), both with friction coefficient mu
-    p = S.Params(dt=0.01)
-    s = S.Scene("slope", p)
-    R = _rz(theta)
-    Vf, Ff = S.box_surface((4.0, 0.1, 4.0), 1)
-    qf = np.zeros(12)
-    qf[3:] = R.reshape(-1)
-    s.affines.append(S.AffineBody(Vf, Ff, qf, rho=1000.0, stiffness=1e8, mu=mu, mode=1))
-    V, F = S.box_surface((0.2, 0.04, 0.2), 1)
-    qb = np.zeros(12)
-    qb[:3] = R @ np.array([0.3, 0.05 + 0.02 + 0.002, 0.1])
-    qb[3:] = R.reshape(-1)
-    s.affines.append(S.AffineBody(V, F, qb, rho=1000.0, stiffness=1e8, mu=mu))
-    return s
-
-
 @pytest.mark.parametrize("mu", [0.1, 0.2])
 def test_sliding_down_a_slope(mu):
     # Eq. 9-10 with the normal force of the barrier (Eq. 4): on a slope of
@@ -387,7 +345,7 @@ def test_sliding_down_a_slope(mu):
     # -(cos(theta), sin(theta), 0).  A wrong normal-force scale, a friction
     # term that ignores the slope's normal, or a sign error changes it.
     theta = 0.3
-    s = _block_on_slope(theta, mu)
+    s = S.scene_slope(theta, mu)
     o = Oracle(s, tol_scale=1e-2)
     down = -np.array([np.cos(theta), np.sin(theta), 0.0])
     vs = []
@@ -407,7 +365,7 @@ def test_block_sticks_on_a_slope_below_the_friction_angle():
     # of Eq. 10 lets it creep, but only below eps_v (the speed at which f1
     # saturates), since the force needed is below mu N.
     theta = 0.3
-    s = _block_on_slope(theta, 0.5)
+    s = S.scene_slope(theta, 0.5, n_steps=30)
     o = Oracle(s, tol_scale=1e-3)
     speeds = []
     for k in range(30):
@@ -415,29 +373,6 @@ def test_block_sticks_on_a_slope_below_the_friction_angle():
         assert st[0, 0, 3] > 0 or k < 3
         speeds.append(np.linalg.norm(o.get_state(1)[12:15]))
     assert max(speeds[10:]) < s.params.eps_v, speeds
-
-
-def _kinematic_scene(max_al_rounds):
-    # a kinematic box whose target starts at rest and moves at 5 m/s along x
-    # while turning at 2 rad/s about z, plus a fixed slab far below it
-    p = S.Params(dt=0.01, max_al_rounds=max_al_rounds)
-    s = S.Scene("kinematic", p)
-    V, F = S.box_surface((0.1, 0.1, 0.1), 1)
-    s.affines.append(S.AffineBody(V, F, S.q_identity((0.0, 0.5, 0.0)), rho=1000.0, stiffness=1e8, mu=0.0,
-                                  mode=2))
-    Vf, Ff = S.box_surface((1.0, 0.1, 1.0), 1)
-    s.affines.append(S.AffineBody(Vf, Ff, S.q_identity((0.0, -0.05, 0.0)), rho=1000.0, stiffness=1e8,
-                                  mu=0.0, mode=1))
-
-    def target(n):
-        q = np.zeros(12)
-        t = (n + 1) * p.dt
-        q[:3] = (5.0 * t, 0.5, 0.0)
-        q[3:] = _rz(2.0 * t).reshape(-1)
-        return q
-
-    s.script = lambda n: {0: target(n)}
-    return s, target
 
 
 def test_kinematic_body_tracks_its_target():
@@ -448,7 +383,7 @@ def test_kinematic_body_tracks_its_target():
     # multiplier update removes that lag, so after every step max |q - q~| is
     # within the tolerance, translation and A block alike.  A sign error in the
     # update doubles the lag instead.
-    s, target = _kinematic_scene(10)
+    s, target = S.scene_kinematic_track(10), S.kinematic_track_target
     o = Oracle(s)
     tol = s.params.newton_tol_rel * o.diag() * s.params.dt
     rounds = 0
@@ -460,7 +395,7 @@ def test_kinematic_body_tracks_its_target():
     assert rounds > 0
 
     # the same scene with the multiplier switched off misses the first target
-    s0, _ = _kinematic_scene(0)
+    s0 = S.scene_kinematic_track(0)
     o0 = Oracle(s0)
     o0.step(1)
     assert np.abs(o0.affine_q(0) - target(0)).max() > tol
