@@ -247,57 +247,106 @@ __device__ inline void inv3(const T* a, T* o) {
     o[8] = (a[0] * a[4] - a[1] * a[3]) * id;
 }
 
+// Inverse 3x3 diagonal blocks of the soft units (one thread each); affine
+// units are left to k_precond_aff.
 template <class T>
-__global__ void k_precond(Geo G, Bsr<T> S, Bsr<T> C, T* Minv_s, T* Minv_a) {
+__global__ void k_precond(Geo G, Bsr<T> S, Bsr<T> C, T* Minv_s) {
     int u = blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= G.n_units) return;
     int kind = G.unit_kind[u], idx = G.unit_idx[u];
-    if (kind == 0) {
-        T a[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-        add_row_blocks(S, idx, idx, idx + 1, a, 3, 0);
-        add_row_blocks(C, idx, idx, idx + 1, a, 3, 0);
-        inv3(a, Minv_s + 9 * (size_t)idx);
-        return;
+    if (kind != 0) return;
+    T a[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    add_row_blocks(S, idx, idx, idx + 1, a, 3, 0);
+    add_row_blocks(C, idx, idx, idx + 1, a, 3, 0);
+    inv3(a, Minv_s + 9 * (size_t)idx);
+}
+
+// Blocks of row `row` whose columns lie in [c0, c1), for rows whose columns
+// are sorted (the static pattern and the contact matrix both are): a binary
+// search for c0, then at most c1 - c0 blocks.
+template <class T>
+__device__ __forceinline__ void add_row_blocks_sorted(const Bsr<T>& A, int row, int c0, int c1, T* out, int ld,
+                                                      int roff) {
+    int lo = A.rowptr[row], hi = A.rowptr[row + 1];
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (A.col[mid] < c0)
+            lo = mid + 1;
+        else
+            hi = mid;
     }
-    int n0 = G.aff_node0[idx];
-    T A[144];
-    for (int i = 0; i < 144; ++i) A[i] = 0;
-    for (int j = 0; j < 4; ++j) {
-        add_row_blocks(S, n0 + j, n0, n0 + 4, A, 12, 3 * j);
-        add_row_blocks(C, n0 + j, n0, n0 + 4, A, 12, 3 * j);
+    for (int k = lo, e = A.rowptr[row + 1]; k < e; ++k) {
+        int c = A.col[k];
+        if (c >= c1) break;
+        const T* v = A.val + 9 * (size_t)k;
+        int co = 3 * (c - c0);
+        for (int r = 0; r < 3; ++r)
+            for (int q = 0; q < 3; ++q) out[(roff + r) * ld + co + q] += v[3 * r + q];
     }
-    // Gauss-Jordan inverse with partial pivoting (12x12, symmetric positive definite)
-    T I[144];
-    for (int i = 0; i < 144; ++i) I[i] = (i % 13 == 0) ? T(1) : T(0);
+}
+
+constexpr int kPrecondAffWarps = 4;  // affine bodies per CTA of k_precond_aff
+
+// Inverse 12x12 diagonal block of every affine body: one warp per body,
+// Gauss-Jordan with partial pivoting on [A | I].  Lane j < 24 holds column j
+// of [A | I] (its 12 rows in registers); the pivot column's lane picks the
+// pivot row, and the pivot value and the elimination factors (column c of
+// each row) are broadcast by shuffles.  Pivot rule and arithmetic per entry
+// are those of a serial Gauss-Jordan: row c scaled by 1 / pivot, then
+// row r -= A[r][c] * row c for every r != c.
+template <class T>
+__global__ void __launch_bounds__(32 * kPrecondAffWarps) k_precond_aff(Geo G, Bsr<T> S, Bsr<T> C, T* Minv_a) {
+    __shared__ double sbuf[kPrecondAffWarps * 144];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int idx = blockIdx.x * kPrecondAffWarps + w;
+    if (idx >= G.n_aff) return;  // uniform over the warp
+    T* sA = reinterpret_cast<T*>(sbuf) + 144 * w;
+    for (int i = lane; i < 144; i += 32) sA[i] = T(0);
+    __syncwarp();
+    const int n0 = G.aff_node0[idx];
+    if (lane < 4) {
+        // row n0 + lane: static blocks, then contact blocks (the serial order)
+        add_row_blocks_sorted(S, n0 + lane, n0, n0 + 4, sA, 12, 3 * lane);
+        add_row_blocks_sorted(C, n0 + lane, n0, n0 + 4, sA, 12, 3 * lane);
+    }
+    __syncwarp();
+    T a[12];
+#pragma unroll
+    for (int r = 0; r < 12; ++r)
+        a[r] = lane < 12 ? sA[12 * r + lane] : (lane - 12 == r ? T(1) : T(0));
+#pragma unroll
     for (int c = 0; c < 12; ++c) {
+        // pivot: largest |A[r][c]|, r >= c, first one on ties (lane c decides)
         int pv = c;
+        T best = fabs(a[c]);
+#pragma unroll
         for (int r = c + 1; r < 12; ++r)
-            if (fabs(A[12 * r + c]) > fabs(A[12 * pv + c])) pv = r;
-        if (pv != c)
-            for (int j = 0; j < 12; ++j) {
-                T t = A[12 * c + j];
-                A[12 * c + j] = A[12 * pv + j];
-                A[12 * pv + j] = t;
-                t = I[12 * c + j];
-                I[12 * c + j] = I[12 * pv + j];
-                I[12 * pv + j] = t;
+            if (fabs(a[r]) > best) {
+                best = fabs(a[r]);
+                pv = r;
             }
-        T ip = T(1) / A[12 * c + c];
-        for (int j = 0; j < 12; ++j) {
-            A[12 * c + j] *= ip;
-            I[12 * c + j] *= ip;
-        }
+        pv = __shfl_sync(0xffffffffu, pv, c);
+#pragma unroll
+        for (int r = c + 1; r < 12; ++r)
+            if (r == pv) {
+                T t = a[c];
+                a[c] = a[r];
+                a[r] = t;
+            }
+        const T ip = T(1) / __shfl_sync(0xffffffffu, a[c], c);
+        a[c] *= ip;
+#pragma unroll
         for (int r = 0; r < 12; ++r) {
             if (r == c) continue;
-            T f = A[12 * r + c];
-            if (f == T(0)) continue;
-            for (int j = 0; j < 12; ++j) {
-                A[12 * r + j] -= f * A[12 * c + j];
-                I[12 * r + j] -= f * I[12 * c + j];
-            }
+            const T f = __shfl_sync(0xffffffffu, a[r], c);
+            a[r] -= f * a[c];
         }
     }
-    for (int i = 0; i < 144; ++i) Minv_a[144 * (size_t)idx + i] = I[i];
+    if (lane >= 12 && lane < 24) {
+        T* o = Minv_a + 144 * (size_t)idx + (lane - 12);
+#pragma unroll
+        for (int r = 0; r < 12; ++r) o[12 * r] = a[r];
+    }
 }
 
 // ---------------------------------------------------------------------------

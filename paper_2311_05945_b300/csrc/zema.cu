@@ -1463,7 +1463,9 @@ int64_t pcg_t(zema_scene* s, const std::vector<int>& done_h) {
     Bsr<T> C{s->C_rowptr.p, s->C_col.p, (const T*)s->C_val.p};
     T* Minv_s = (T*)s->Minv_s.p;
     T* Minv_a = (T*)s->Minv_a.p;
-    ZL(k_precond<T>, div_up(s->n_units, 128), 128, 0, st)(G, S, C, Minv_s, Minv_a);
+    ZL(k_precond<T>, div_up(s->n_units, 128), 128, 0, st)(G, S, C, Minv_s);
+    if (s->n_aff)
+        ZL(k_precond_aff<T>, div_up(s->n_aff, kPrecondAffWarps), 32 * kPrecondAffWarps, 0, st)(G, S, C, Minv_a);
     ZL(k_negate, div_up(3 * (size_t)s->n_nodes, TB), TB, 0, st)(s->g.p, s->b.p, 3 * (size_t)s->n_nodes);
     ZLAUNCH();
     for (int e = 0; e < NE; ++e) s->hi[e] = s->hi[3 * NE + e] = done_h[e];
