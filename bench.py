@@ -137,20 +137,59 @@ def oracle_steps_per_s(n_warm, n_steps, sc=None):
     return n_steps / dt, dt
 
 
+def workload_name(args, sc, envs_per_rank):
+    """The config's workload string (the same for both arms)."""
+    if args.workload == "c2":
+        return WORKLOAD
+    if args.workload == "c5":
+        return (f"dense soft-rigid pile: {sum(len(b.tets) for b in sc.tets)} tets in {len(sc.tets)} soft bodies "
+                f"+ {sum(1 for a in sc.affines if a.mode == 0)} affine spheres/tori "
+                f"({max(len(a.F) for a in sc.affines)} tris max) in a fixed 5-box bin, one scene")
+    return (f"batched parallel-jaw grasp, {args.envs} envs (ellipsoid/torus/box, 2k-20k tets log-uniform, "
+            f"E 1e4-1e6, mu 0.3-1.0), one launch per phase over all envs; {envs_per_rank} envs per rank")
+
+
+def oracle_sample(args, n_warm, n_steps):
+    """Time the CPU oracle, as it stands, on a bounded sample of the workload:
+    returns (value in the workload's unit, seconds, description)."""
+    from paper_2311_05945_b300 import scenes
+    if args.workload == "c5":
+        # the oracle's brute-force pair search is quadratic in the surface
+        # size: one step of the full pile does not fit the sample bound, so
+        # the sample is the same pile generator at 300 tets per body
+        small = scenes.scene_c5(n_steps=2, tets_per_body=300, n_seg=8, bin_subdiv=1)
+        v, dt = oracle_steps_per_s(0, 1, small)
+        return v, dt, (f"step 0 of the same pile generator at 300 tets per body, 8 x 8 affine meshes, unsplit "
+                       f"bin faces, on the CPU oracle ({dt:.1f} s)")
+    if args.workload == "c3":
+        v, dt = oracle_steps_per_s(0, 1, scenes.scene_c3(n_envs=1, n_steps=2))
+        return v, dt, f"env 0 of the batch (seed 1000), step 0, on the CPU oracle ({dt:.1f} s)"
+    v, dt = oracle_steps_per_s(n_warm, n_steps)
+    return v, dt, (f"grasp steps [{n_warm}, {n_warm + n_steps}) of the same script on the CPU oracle "
+                   f"({dt:.1f} s)")
+
+
 def run_reference(args, rank):
     if rank != 0:
         return
-    n_warm = min(args.warmup, 1)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    # the GPU arm times steps [W, W + K) of the grasp script: step the oracle
+    # untimed to W (capped so that the run stays within a few minutes), then
+    # time up to 3 steps of the same window
+    n_warm = min(args.warmup, 40)
     n_steps = max(1, min(args.steps, 3))
-    v, dt = oracle_steps_per_s(n_warm, n_steps)
-    sample = f"grasp steps [{n_warm}, {n_warm + n_steps}) of the script on the CPU oracle ({dt:.1f} s)"
+    unit = "env-steps/s" if args.workload == "c3" else UNIT
+    sc = None if args.workload == "c2" else build_scene(args, 0, world)
+    name = workload_name(args, sc, sc.n_envs if sc is not None else 1)
+    v, dt, sample = oracle_sample(args, n_warm, n_steps)
     line = {
-        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": n_steps,
-        "warmup": n_warm, "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "impl": "reference", "metric": METRIC, "value": v, "unit": unit, "n_gpus": args.gpus,
+        "steps": n_steps if args.workload == "c2" else 1, "warmup": n_warm if args.workload == "c2" else 0,
+        "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic (seeded generators)",
-        "config": {"workload": WORKLOAD, "form": "CPU oracle: serial FP64, brute-force pairs, direct/CG solve"},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
-        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "config": {"workload": name, "form": "CPU oracle: serial FP64, brute-force pairs, direct/CG solve"},
+        "cpu_baseline": {"value": v, "unit": unit, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
@@ -269,22 +308,7 @@ def run_ours(args, rank, world):
     unit = "env-steps/s" if args.workload == "c3" else UNIT
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        if args.workload == "c5":
-            # the oracle's brute-force pair search is quadratic in the surface
-            # size: one step of the full pile does not fit the sample bound,
-            # so the sample is the same pile generator at 300 tets per body
-            from paper_2311_05945_b300 import scenes
-            small = scenes.scene_c5(n_steps=2, tets_per_body=300, n_seg=8, bin_subdiv=1)
-            v, dt = oracle_steps_per_s(0, 1, small)
-            sample = (f"step 0 of the same pile generator at 300 tets per body, 8 x 8 affine meshes, unsplit bin "
-                      f"faces, on the CPU oracle ({dt:.1f} s)")
-        elif args.workload == "c3":
-            from paper_2311_05945_b300 import scenes
-            v, dt = oracle_steps_per_s(0, 1, scenes.scene_c3(n_envs=1, n_steps=2))
-            sample = f"env 0 of the batch (seed 1000), step 0, on the CPU oracle ({dt:.1f} s)"
-        else:
-            v, dt = oracle_steps_per_s(0, args.cpu_steps)
-            sample = f"grasp steps [0, {args.cpu_steps}) of the same script on the CPU oracle ({dt:.1f} s)"
+        v, dt, sample = oracle_sample(args, 0, args.cpu_steps)
         cpu = {"value": v, "unit": unit, "cores": 1, "kind": "oracle", "sample": sample}
     agg = {k: sum(s[k] for s in stats) for k in ("newton_iters", "pcg_iters", "ls_halvings", "al_rounds", "pcg_refines")}
     phase = {k: sum(s["ms_phase"][k] for s in stats) for k in stats[0]["ms_phase"]}
@@ -292,13 +316,7 @@ def run_ours(args, rank, world):
         "metric": METRIC, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "mixed f32/f64", "data": "synthetic (seeded generators)",
-        "config": {"workload": WORKLOAD if args.workload == "c2" else
-                   (f"dense soft-rigid pile: {sum(len(b.tets) for b in sc.tets)} tets in {len(sc.tets)} soft bodies "
-                    f"+ {sum(1 for a in sc.affines if a.mode == 0)} affine spheres/tori "
-                    f"({max(len(a.F) for a in sc.affines)} tris max) in a fixed 5-box bin, one scene"
-                    if args.workload == "c5" else
-                    f"batched parallel-jaw grasp, {args.envs} envs (ellipsoid/torus/box, 2k-20k tets log-uniform, "
-                    f"E 1e4-1e6, mu 0.3-1.0), one launch per phase over all envs; {envs_per_rank} envs per rank"),
+        "config": {"workload": workload_name(args, sc, envs_per_rank),
                    "timed_steps": [args.warmup, args.warmup + args.steps],
                    "form": "mixed precision (FP32 Hessians, matrices and PCG with FP64 residual refinement; FP64 "
                            "gradients/energies/distances/CCD/convergence) + CCD-filtered constant-velocity warm "
