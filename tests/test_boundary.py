@@ -37,3 +37,20 @@ def test_product_path_does_not_import_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert not pat.search(txt), f
+
+
+def test_product_path_fails_loudly_without_a_gpu():
+    # no CPU fallback: where no CUDA device is visible, building a scene and
+    # calling a local entry point raise instead of returning CPU results
+    import numpy as np
+    import pytest
+    import torch
+
+    from paper_2311_05945_b300 import scenes as S
+    from paper_2311_05945_b300 import zema as Z
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is visible")
+    with pytest.raises(RuntimeError):
+        Z.Scene(S.scene_tiny_contact())
+    with pytest.raises(RuntimeError):
+        Z.local_distance(np.zeros((2, 12)), 0)
