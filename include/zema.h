@@ -43,10 +43,11 @@ typedef enum {
     ZEMA_ERR_INVERTED_INPUT = 5,
     ZEMA_ERR_NEWTON_MAXITER = 6,
     ZEMA_ERR_LINESEARCH = 7,
-    ZEMA_ERR_PCG_MAXITER = 8,
+    ZEMA_ERR_PCG_MAXITER = 8,    /* reserved: a solve that reaches max_pcg returns its last
+                                    iterate, which the Newton step test and the line search judge */
     ZEMA_ERR_NONFINITE = 9,
-    ZEMA_ERR_FAULT_INJECTED = 10,
-    ZEMA_ERR_STATE = 11
+    ZEMA_ERR_FAULT_INJECTED = 10, /* reserved: the library injects no faults */
+    ZEMA_ERR_STATE = 11           /* call not allowed in the scene's current state */
 } zema_status;
 
 typedef struct zema_scene zema_scene; /* opaque; owns all of its device memory */
@@ -68,7 +69,9 @@ typedef struct {
     int32_t max_newton;    /* Newton iteration cap per solve */
     int32_t max_pcg;       /* PCG iteration cap per solve */
     int32_t max_al_rounds; /* kinematic augmented-Lagrangian rounds per step */
-    int32_t precision;     /* 0: FP64 throughout; 1: mixed (FP32 elastic/affine Hessians and matvecs) */
+    int32_t precision;     /* 0: FP64 throughout; 1: mixed (FP32 Hessians, stored matrices,
+                              preconditioner and PCG with FP64 residual refinement; FP64
+                              gradients, energies, distances, ACCD and convergence test) */
     int32_t n_envs;        /* number of independent environments */
     int32_t warm_start;    /* 0: constant-velocity proposal; 1: learned proposal (needs weights) */
     int32_t pcg_kind;      /* 0: auto (one thread-block cluster per env when the env's vector fits
@@ -141,7 +144,13 @@ zema_status zema_finalize(zema_scene* s);
  * step (Eq. 13). */
 zema_status zema_set_kinematic_target(zema_scene* s, int32_t body, const double q_target[12]);
 
-/* Advances n_steps time steps (Eq. 11).  stats may be NULL. */
+/* Advances n_steps time steps (Eq. 11).  stats may be NULL.  Errors:
+ * ZEMA_ERR_NEWTON_MAXITER (no convergence within max_newton iterations),
+ * ZEMA_ERR_LINESEARCH (no energy decrease after 60 halvings),
+ * ZEMA_ERR_NONFINITE (a non-finite value in the linear solve),
+ * ZEMA_ERR_INTERSECTING_INPUT (at the first step, as zema_finalize),
+ * ZEMA_ERR_OOM, ZEMA_ERR_CUDA.  The state then stays at the last completed
+ * step. */
 zema_status zema_step(zema_scene* s, int32_t n_steps, zema_step_stats* stats);
 
 /* State of one body into a caller-owned host buffer of cap doubles.
@@ -173,7 +182,7 @@ zema_status zema_set_kappa(zema_scene* s, int32_t env, double kappa, double kapp
 long long zema_launch_count(void);
 
 /* Live timing of one kernel for roofline reports: zema_profile_kernel(name)
- * selects the library kernel (by its function name, e.g. "k_pcg_spmv"; NULL
+ * selects the library kernel (by its function name, e.g. "k_pcg_cluster"; NULL
  * stops timing) and clears the totals; afterwards every launch of it is
  * bracketed by CUDA events on the stream it runs on.  zema_profile_read
  * returns the summed event time (ms), the number of timed launches and the
