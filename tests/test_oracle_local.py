@@ -388,3 +388,24 @@ def test_fixed_corotated_closed_forms_and_fd(seed):
     Fi = F.copy()
     Fi[:, 0] *= -1
     assert O.fcr(Fi, mu, lam)[0] == np.inf
+
+
+@pytest.mark.parametrize("phi", [0.02, 0.1, 0.3, 0.7, 1.2])
+def test_ee_mollifier_closed_form(phi):
+    # IPC's edge-edge mollifier (reading c6): the EE barrier is e(c) b(d) with
+    # c = |ea x eb|^2 and e = (c/eps_x)(2 - c/eps_x) for c < eps_x, else 1.
+    # Two edges of length 2 crossing at height h (closest points at both
+    # midpoints, d = h for any angle phi between them): c = 16 sin^2(phi).
+    dh, h = 1.0, 0.3
+    u = np.array([np.cos(phi), np.sin(phi), 0.0])
+    x = np.concatenate([[-1.0, 0, 0], [1.0, 0, 0], [0, 0, h] - u, [0, 0, h] + u])
+    c = 16.0 * np.sin(phi) ** 2
+    for eps_x in (0.5, 2.0, 8.0):
+        r = c / eps_x
+        e = r * (2.0 - r) if r < 1.0 else 1.0
+        b = O.pair_barrier(x, 1, dh, eps_x, project=False)[0]
+        assert abs(b - e * O.barrier(h, dh)) <= 1e-12 * O.barrier(h, dh), (phi, eps_x, b, e)
+    # point-triangle pairs carry no mollifier: a point at height h above the
+    # interior of a triangle gives exactly b(h)
+    pt = np.concatenate([[0.2, 0.2, h], [0, 0, 0], [1.0, 0, 0], [0, 1.0, 0]])
+    assert abs(O.pair_barrier(pt, 0, dh, 1.0, project=False)[0] - O.barrier(h, dh)) <= 1e-12 * O.barrier(h, dh)
