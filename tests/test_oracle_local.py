@@ -259,6 +259,31 @@ def test_neo_hookean_rest_and_fd(seed):
     assert O.nh(Fi, mu, lam)[0] == np.inf
 
 
+@pytest.mark.parametrize("s", [0.7, 1.0, 1.3])
+def test_neo_hookean_closed_forms(s):
+    # the Neo-Hookean density of reading c9 at two deformations with closed
+    # forms: uniaxial stretch F = diag(s, 1, 1), J = s:
+    #   Psi = mu/2 (s^2 - 1) - mu ln s + lam/2 (ln s)^2,
+    #   P = mu (F - F^-T) + lam ln J F^-T = diag(mu (s - 1/s) + lam ln(s)/s, lam ln s, lam ln s);
+    # uniform scaling F = s I, J = s^3:
+    #   Psi = 3 mu/2 (s^2 - 1) - 3 mu ln s + 9 lam/2 (ln s)^2.
+    # Each term is checked separately by switching mu or lam off, and the
+    # density is invariant under a rotation applied from the left.
+    for mu, lam in ((3.5e4, 0.0), (0.0, 3.1e5), (3.5e4, 3.1e5)):
+        F = np.diag([s, 1.0, 1.0])
+        psi, g, _ = O.nh(F, mu, lam)
+        ref = mu / 2 * (s * s - 1) - mu * np.log(s) + lam / 2 * np.log(s) ** 2
+        assert abs(psi - ref) <= 1e-12 * max(1.0, abs(ref)), (mu, lam, psi, ref)
+        P = np.diag([mu * (s - 1 / s) + lam * np.log(s) / s, lam * np.log(s), lam * np.log(s)])
+        assert np.abs(g.reshape(3, 3) - P).max() <= 1e-9 * max(1.0, np.abs(P).max())
+        psi_s = O.nh(s * np.eye(3), mu, lam)[0]
+        ref_s = 1.5 * mu * (s * s - 1) - 3 * mu * np.log(s) + 4.5 * lam * np.log(s) ** 2
+        assert abs(psi_s - ref_s) <= 1e-12 * max(1.0, abs(ref_s))
+        Fg = np.eye(3) + 0.2 * np.random.default_rng(7).standard_normal((3, 3))
+        psi_g = O.nh(Fg, mu, lam)[0]
+        assert abs(O.nh(rot(3) @ Fg, mu, lam)[0] - psi_g) <= 1e-12 * max(1.0, abs(psi_g))
+
+
 @pytest.mark.parametrize("seed", range(6))
 def test_ortho_energy(seed):
     R = rot(seed + 10)
