@@ -47,9 +47,9 @@
  *   kinematic AL: kappa_A = 1e3 m_b, multiplier update after Newton converges
  *   when max |q - q~| > tol, at most max_al_rounds rounds.
  *
- * Parity unpinned: nothing in the paper prints a worked example or a
- * trajectory, so every function here is pinned by mathematics (finite
- * differences, closed forms, brute force, invariants) in the tests.
+ * Pins: the paper prints no worked example or trajectory, so no stored value
+ * comes from it.  Every function here is pinned instead by mathematics in the
+ * tests: closed forms, brute force, finite differences and invariants.
  */
 #include <algorithm>
 #include <cmath>

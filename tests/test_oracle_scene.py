@@ -3,7 +3,8 @@ properties, finite differences of the complete incremental potential,
 monotone Newton energies, intersection-free trajectories (independent
 triangle-triangle tests), momentum conservation, Coulomb sliding on flat
 ground and down a slope, static friction below the friction angle, kinematic
-target tracking by the augmented Lagrangian and the barrier-stiffness floor."""
+target tracking by the augmented Lagrangian, the barrier-stiffness floor and
+the initial gradient-balance stiffness (clamped and unclamped)."""
 import numpy as np
 import pytest
 
@@ -410,3 +411,33 @@ def test_kappa_min_is_a_thousand_mean_lumped_masses():
     assert abs(o.kappa_min() - 1e3 * m.mean()) < 1e-12 * o.kappa_min()
     k = o.kappa()
     assert o.kappa_min() <= k <= 100 * o.kappa_min()
+
+
+@pytest.mark.parametrize("name", ["tiny", "c1"])
+def test_initial_kappa_balances_gradients(name):
+    # reading c2: at the first step kappa = clamp(-gE . gB / |gB|^2, kappa_min,
+    # 100 kappa_min), gE the gradient of the potential without the barrier and
+    # gB the barrier gradient at unit stiffness, both at x^t.  Here both come
+    # from the full potential's gradient at two stiffnesses (it is affine in
+    # kappa without friction): gB = g(2) - g(1), gE = g(1) - gB.
+    s = S.scene_tiny_contact(mu=0.5) if name == "tiny" else S.scene_c1()
+    if name == "c1":
+        o0 = Oracle(s)
+        o0.step(12)  # in contact
+        states = [o0.get_state(b) for b in range(len(s.body_order()))]
+    o = Oracle(s)
+    if name == "c1":
+        for b, x in enumerate(states):
+            o.set_state(b, x)
+    o.prepare(0, friction=False)  # predictor, then the stiffness rule
+    k0, kmin = o.kappa(), o.kappa_min()
+    y = o.dofs()
+    grads = []
+    for k in (1.0, 2.0):
+        o.set_kappa(0, k, kmin)
+        grads.append(o.eval(y, grad=True)[1])
+    gB = grads[1] - grads[0]
+    gE = grads[0] - gB
+    assert np.linalg.norm(gB) > 0
+    ref = min(max(-(gE @ gB) / (gB @ gB), kmin), 100 * kmin)
+    assert abs(k0 - ref) <= 1e-9 * ref, (k0, ref, kmin)
