@@ -4,7 +4,8 @@ monotone Newton energies, intersection-free trajectories (independent
 triangle-triangle tests), momentum conservation, Coulomb sliding on flat
 ground and down a slope, static friction below the friction angle, kinematic
 target tracking by the augmented Lagrangian, the barrier-stiffness floor and
-the initial gradient-balance stiffness (clamped and unclamped)."""
+the initial gradient-balance stiffness (clamped and unclamped) and its
+doubling rule."""
 import numpy as np
 import pytest
 
@@ -441,3 +442,28 @@ def test_initial_kappa_balances_gradients(name):
     assert np.linalg.norm(gB) > 0
     ref = min(max(-(gE @ gB) / (gB @ gB), kmin), 100 * kmin)
     assert abs(k0 - ref) <= 1e-9 * ref, (k0, ref, kmin)
+
+
+@pytest.mark.parametrize("kmin", [0.05, 7.5e-6])
+def test_kappa_doubles_when_contact_closes_below_a_tenth_of_dhat(kmin):
+    # reading c2, after each step: kappa <- min(2 kappa, 1e4 kappa_min) when
+    # the step's d_min is below 0.1 dhat and below the previous step's d_min,
+    # else unchanged.  A deliberately weak barrier (kappa = 0.05) lets the
+    # contact close below 0.1 dhat; with kappa_min = 7.5e-6 the cap 1e4
+    # kappa_min = 0.075 binds on the first doubling.
+    s = S.scene_tiny_contact(mu=0.5)
+    o = Oracle(s)
+    o.set_kappa(0, 0.05, kmin)
+    st = o.step(12)
+    d, k = st[:, 0, 4], st[:, 0, 6]
+    dhat = s.params.dhat
+    d_prev, k_prev, doubled = np.inf, 0.05, 0
+    for dk, kk in zip(d, k):
+        if dk < 0.1 * dhat and dk < d_prev:
+            expect = min(2 * k_prev, 1e4 * kmin)
+            doubled += 1
+        else:
+            expect = k_prev
+        assert kk == expect, (dk / dhat, kk, expect)
+        d_prev, k_prev = dk, kk
+    assert doubled >= 1
