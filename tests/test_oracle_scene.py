@@ -85,6 +85,37 @@ def test_affine_mass_box(ext, center):
                 assert np.abs(M[3 + 3 * i:6 + 3 * i, 3 + 3 * j:6 + 3 * j]).max() < 1e-15
 
 
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_affine_mass_tetrahedron(seed):
+    # M_b (Eq. 2) of a single tetrahedron, skewed and off the origin, against
+    # the closed form of its moments: m = rho V, integral rho x0 = m c with c
+    # the vertex mean, integral rho x0 x0^T = rho V / 20 (sum v v^T + s s^T)
+    # with s the vertex sum.  Unlike an axis-aligned box, every entry of the
+    # second moment is nonzero, so a transposed or misplaced term shows.
+    rng = np.random.default_rng(40 + seed)
+    v = rng.standard_normal((4, 3)) * 0.3 + rng.standard_normal(3)
+    if np.linalg.det(np.stack([v[1] - v[0], v[2] - v[0], v[3] - v[0]], 1)) < 0:
+        v[[1, 2]] = v[[2, 1]]
+    F = np.array([[0, 2, 1], [0, 1, 3], [0, 3, 2], [1, 2, 3]], dtype=np.int32)
+    vol = np.linalg.det(np.stack([v[1] - v[0], v[2] - v[0], v[3] - v[0]], 1)) / 6.0
+    tri = v[F]
+    assert abs(np.einsum("ij,ij->i", tri[:, 0], np.cross(tri[:, 1], tri[:, 2])).sum() / 6.0 - vol) < 1e-12
+    rho = 900.0
+    s = S.Scene("tet", S.Params())
+    s.affines.append(S.AffineBody(v, F, S.q_identity((0, 0, 0)), rho=rho, stiffness=1e8, mu=0.5))
+    o = Oracle(s)
+    M, m, V = o.affine_mass(0)
+    assert abs(V - vol) <= 1e-12 * vol and abs(m - rho * vol) <= 1e-12 * rho * vol
+    c = v.mean(0)
+    sv = v.sum(0)
+    Sref = rho * vol / 20.0 * (v.T @ v + np.outer(sv, sv))
+    scale = np.abs(Sref).max()
+    for i in range(3):
+        assert abs(M[i, i] - m) <= 1e-12 * m
+        assert np.allclose(M[i, 3 + 3 * i:6 + 3 * i], m * c, rtol=0, atol=1e-12 * m * np.abs(c).max())
+        assert np.allclose(M[3 + 3 * i:6 + 3 * i, 3 + 3 * i:6 + 3 * i], Sref, rtol=0, atol=1e-12 * scale)
+
+
 def _advance(o, n):
     for _ in range(n):
         o.step(1)
