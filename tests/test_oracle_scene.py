@@ -498,3 +498,31 @@ def test_kappa_doubles_when_contact_closes_below_a_tenth_of_dhat(kmin):
         assert kk == expect, (dk / dhat, kk, expect)
         d_prev, k_prev = dk, kk
     assert doubled >= 1
+
+
+@pytest.mark.parametrize("scale", [0.9, 1.15])
+def test_uniformly_scaled_cube_elastic_energy(scale):
+    # the scene-level elastic term h^2 sum_e V_e Psi(F_e) (Eq. 1, reading c9)
+    # of a soft cube scaled uniformly by s about the origin, at rest and with
+    # no gravity: every F_e = s I, so the whole potential is
+    # h^2 V Psi(s I) = h^2 V (3 mu/2 (s^2 - 1) - 3 mu ln s + 9 lam/2 (ln s)^2),
+    # with mu = E / (2 (1 + nu)) and lam = E nu / ((1 + nu)(1 - 2 nu)).  This
+    # pins the rest shapes, the volumes, the Lame parameters and the h^2.
+    p = S.Params(dt=0.01, gravity=(0.0, 0.0, 0.0))
+    s = S.Scene("scaled", p)
+    X, T = S.soft_cube(4, 0.3, (-0.15, -0.15, -0.15))
+    Ey, nu = 2e5, 0.35
+    s.tets.append(S.TetBody(X, T, E=Ey, nu=nu, rho=1000.0, mu=0.5))
+    o = Oracle(s)
+    st = o.get_state(0)
+    n = len(X)
+    st[:3 * n] = (scale * X).ravel()
+    st[3 * n:] = 0.0
+    o.set_state(0, st)
+    o.prepare(0)
+    E = o.eval(o.dofs())[0]
+    mu = Ey / (2 * (1 + nu))
+    lam = Ey * nu / ((1 + nu) * (1 - 2 * nu))
+    ls = np.log(scale)
+    ref = p.dt ** 2 * 0.3 ** 3 * (1.5 * mu * (scale ** 2 - 1) - 3 * mu * ls + 4.5 * lam * ls ** 2)
+    assert abs(E - ref) <= 1e-10 * abs(ref), (E, ref)
