@@ -526,3 +526,27 @@ def test_uniformly_scaled_cube_elastic_energy(scale):
     ls = np.log(scale)
     ref = p.dt ** 2 * 0.3 ** 3 * (1.5 * mu * (scale ** 2 - 1) - 3 * mu * ls + 4.5 * lam * ls ** 2)
     assert abs(E - ref) <= 1e-10 * abs(ref), (E, ref)
+
+
+@pytest.mark.parametrize("scale", [0.98, 1.03])
+def test_scaled_affine_body_orthogonality_energy(scale):
+    # the affine term h^2 lambda V |A A^T - I|_F^2 (Eq. 2) of a box at rest
+    # with A = s R (R a rotation) and no gravity: A A^T = s^2 I, so the whole
+    # potential is h^2 lambda V 3 (s^2 - 1)^2.  This pins the body volume, the
+    # stiffness and the h^2 of the affine term.
+    p = S.Params(dt=0.01, gravity=(0.0, 0.0, 0.0))
+    s = S.Scene("scaled_affine", p)
+    ext = (0.2, 0.3, 0.5)
+    V, F = S.box_surface(ext, 2)
+    lam = 1e8
+    s.affines.append(S.AffineBody(V, F, S.q_identity((0.1, 0.2, 0.3)), rho=800.0, stiffness=lam, mu=0.5))
+    o = Oracle(s)
+    R = S.rotation_from_uniforms(0.3, 0.6, 0.9)
+    st = o.get_state(0)
+    st[3:12] = (scale * R).reshape(-1)
+    st[12:] = 0.0
+    o.set_state(0, st)
+    o.prepare(0)
+    E = o.eval(o.dofs())[0]
+    ref = p.dt ** 2 * lam * np.prod(ext) * 3 * (scale ** 2 - 1) ** 2
+    assert abs(E - ref) <= 1e-9 * abs(ref), (E, ref)
