@@ -550,3 +550,22 @@ def test_scaled_affine_body_orthogonality_energy(scale):
     E = o.eval(o.dofs())[0]
     ref = p.dt ** 2 * lam * np.prod(ext) * 3 * (scale ** 2 - 1) ** 2
     assert abs(E - ref) <= 1e-9 * abs(ref), (E, ref)
+
+
+def test_kinematic_penalty_energy():
+    # reading c13 of Eq. 13 before any multiplier update (lambda_A = 0): a
+    # kinematic body at rest with no gravity, its target offset by delta,
+    # carries exactly kappa_A / 2 |q - q~|^2 with kappa_A = 1e3 m.
+    p = S.Params(dt=0.01, gravity=(0.0, 0.0, 0.0))
+    s = S.Scene("kin_penalty", p)
+    V, F = S.box_surface((0.1, 0.2, 0.3), 1)
+    q0 = S.q_identity((0.0, 0.5, 0.0))
+    s.affines.append(S.AffineBody(V, F, q0, rho=1000.0, stiffness=1e8, mu=0.0, mode=2))
+    delta = np.array([0.01, -0.02, 0.005, 0.001, 0.0, -0.002, 0.0, 0.003, 0.0, 0.001, 0.0, 0.0])
+    s.script = lambda n: {0: q0 + delta}
+    o = Oracle(s)
+    o.prepare(0)
+    E = o.eval(o.dofs())[0]
+    m = 1000.0 * 0.1 * 0.2 * 0.3
+    ref = 0.5 * 1e3 * m * delta @ delta
+    assert abs(E - ref) <= 1e-10 * ref, (E, ref)
