@@ -569,3 +569,27 @@ def test_kinematic_penalty_energy():
     m = 1000.0 * 0.1 * 0.2 * 0.3
     ref = 0.5 * 1e3 * m * delta @ delta
     assert abs(E - ref) <= 1e-10 * ref, (E, ref)
+
+
+def test_inertia_at_the_start_of_a_step():
+    # Eq. 1-3 at x = x^t, no deformation: only inertia remains,
+    # 1/2 sum m |x^t - x^hat|^2 = 1/2 M |h v + h^2 g|^2 for a soft cube and an
+    # affine box (far apart) translating with the same velocity v, M their
+    # total mass.  This pins the predictor and both mass models.
+    p = S.Params(dt=0.01)
+    s = S.Scene("inertia", p)
+    X, T = S.soft_cube(3, 0.2, (0.0, 0.0, 0.0))
+    v = np.array([0.3, -0.7, 1.1])
+    s.tets.append(S.TetBody(X, T, E=1e5, nu=0.4, rho=1200.0, mu=0.5, v0=np.tile(v, (len(X), 1))))
+    Vb, Fb = S.box_surface((0.1, 0.2, 0.3), 1)
+    qd = np.zeros(12)
+    qd[:3] = v
+    s.affines.append(S.AffineBody(Vb, Fb, S.q_identity((2.0, 0.0, 0.0)), rho=800.0, stiffness=1e8, mu=0.5,
+                                  qdot0=qd))
+    o = Oracle(s)
+    o.prepare(0)
+    E = o.eval(o.dofs())[0]
+    M = 1200.0 * 0.2 ** 3 + 800.0 * 0.1 * 0.2 * 0.3
+    w = p.dt * v + p.dt ** 2 * np.array(p.gravity)
+    ref = 0.5 * M * w @ w
+    assert abs(E - ref) <= 1e-10 * ref, (E, ref)
