@@ -54,3 +54,19 @@ def test_product_path_fails_loudly_without_a_gpu():
         Z.Scene(S.scene_tiny_contact())
     with pytest.raises(RuntimeError):
         Z.local_distance(np.zeros((2, 12)), 0)
+
+
+def test_default_params_match_the_header():
+    # zema_default_params is host-only: its values are the ones include/zema.h
+    # documents, read through the binding's structure layout
+    from paper_2311_05945_b300.zema import Params
+    L = ctypes.CDLL(zbuild.build())
+    L.zema_default_params.argtypes = [ctypes.POINTER(Params)]
+    p = Params()
+    L.zema_default_params(ctypes.byref(p))
+    assert (p.dt, p.dhat, p.eps_v, p.newton_tol_rel, p.pcg_rel_tol) == (0.01, 1e-3, 1e-3, 1e-3, 1e-4)
+    assert p.kappa <= 0.0  # adaptive
+    assert tuple(p.gravity) == (0.0, -9.81, 0.0)
+    assert (p.max_newton, p.max_pcg, p.max_al_rounds) == (100, 10000, 10)
+    assert (p.precision, p.n_envs, p.warm_start, p.pcg_kind) == (0, 1, 0, 0)
+    assert not p.stream and not p.alloc and not p.free
