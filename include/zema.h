@@ -129,7 +129,12 @@ zema_status zema_add_tet_body(zema_scene* s, int32_t env, const double* X_rest, 
  * V_rest (nv x 3, caller's rest frame) / F (nf x 3); q0 and qdot0 (12 each,
  * qdot0 NULL = 0); density rho; stiffness = lambda of the orthogonality
  * energy; mode 0 dynamic, 1 fixed, 2 kinematic (driven to the target of
- * zema_set_kinematic_target by the augmented-Lagrangian term of Eq. 13). */
+ * zema_set_kinematic_target by the augmented-Lagrangian term of Eq. 13).
+ * ZEMA_ERR_INVALID_ARG when a face index is out of range, a face is
+ * degenerate, the surface is not closed and consistently oriented (every
+ * edge shared by two faces that traverse it in opposite directions), or its
+ * signed volume is not positive (faces pointing inward); ZEMA_ERR_STATE after
+ * the first step. */
 zema_status zema_add_affine_body(zema_scene* s, int32_t env, const double* V_rest, int64_t nv,
                                  const int32_t* F, int64_t nf, const double q0[12], const double qdot0[12],
                                  double rho, double stiffness, double mu_friction, int32_t mode,

@@ -2285,6 +2285,44 @@ zema_status zema_add_affine_body(zema_scene* s, int32_t env, const double* V_res
             s->err = "face index out of range";
             return ZEMA_ERR_INVALID_ARG;
         }
+    // The mass properties integrate over the enclosed volume (Eq. 2), so the
+    // surface must be closed and consistently oriented: every directed edge
+    // appears once and its reverse once (each edge borders two faces that
+    // traverse it in opposite directions), and the signed volume is positive
+    // (faces point outward).
+    {
+        std::vector<uint64_t> de;
+        de.reserve(3 * (size_t)nf);
+        for (int64_t f = 0; f < nf; ++f)
+            for (int k = 0; k < 3; ++k) {
+                const uint32_t a = (uint32_t)B.F[3 * f + k], b = (uint32_t)B.F[3 * f + (k + 1) % 3];
+                if (a == b) {
+                    s->err = "degenerate face in affine body mesh";
+                    return ZEMA_ERR_INVALID_ARG;
+                }
+                de.push_back(((uint64_t)a << 32) | b);
+            }
+        std::sort(de.begin(), de.end());
+        bool ok = std::adjacent_find(de.begin(), de.end()) == de.end();
+        for (size_t i = 0; ok && i < de.size(); ++i)
+            ok = std::binary_search(de.begin(), de.end(), (de[i] << 32) | (de[i] >> 32));
+        if (!ok) {
+            s->err = "affine body mesh is not closed and consistently oriented";
+            return ZEMA_ERR_INVALID_ARG;
+        }
+        double vol6 = 0.0;
+        for (int64_t f = 0; f < nf; ++f) {
+            const double* p0 = &B.V[3 * (size_t)B.F[3 * f]];
+            const double* p1 = &B.V[3 * (size_t)B.F[3 * f + 1]];
+            const double* p2 = &B.V[3 * (size_t)B.F[3 * f + 2]];
+            vol6 += p0[0] * (p1[1] * p2[2] - p1[2] * p2[1]) - p0[1] * (p1[0] * p2[2] - p1[2] * p2[0]) +
+                    p0[2] * (p1[0] * p2[1] - p1[1] * p2[0]);
+        }
+        if (!(vol6 > 0.0)) {
+            s->err = "affine body mesh encloses no volume (faces not outward?)";
+            return ZEMA_ERR_INVALID_ARG;
+        }
+    }
     for (int k = 0; k < 12; ++k) {
         B.q0[k] = q0[k];
         B.qd0[k] = qdot0 ? qdot0[k] : 0.0;

@@ -70,3 +70,67 @@ def test_default_params_match_the_header():
     assert (p.max_newton, p.max_pcg, p.max_al_rounds) == (100, 10000, 10)
     assert (p.precision, p.n_envs, p.warm_start, p.pcg_kind) == (0, 1, 0, 0)
     assert not p.stream and not p.alloc and not p.free
+
+
+def _affine_adder():
+    from paper_2311_05945_b300.zema import Params
+    L = ctypes.CDLL(zbuild.build())
+    DP, IP = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)
+    L.zema_default_params.argtypes = [ctypes.POINTER(Params)]
+    L.zema_create_scene.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_void_p)]
+    L.zema_add_affine_body.argtypes = [ctypes.c_void_p, ctypes.c_int32, DP, ctypes.c_int64, IP, ctypes.c_int64, DP,
+                                       DP, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int32, IP]
+    L.zema_destroy_scene.argtypes = [ctypes.c_void_p]
+    p = Params()
+    L.zema_default_params(ctypes.byref(p))
+    h = ctypes.c_void_p()
+    # scene creation and body addition are host-only: no GPU needed
+    assert L.zema_create_scene(ctypes.byref(p), ctypes.byref(h)) == 0
+
+    def add(V, F):
+        import numpy as np
+        V = np.ascontiguousarray(V, dtype=np.float64)
+        F = np.ascontiguousarray(F, dtype=np.int32)
+        q = np.zeros(12)
+        q[[3, 7, 11]] = 1.0
+        bid = ctypes.c_int32()
+        return L.zema_add_affine_body(h, 0, V.ctypes.data_as(DP), len(V), F.ctypes.data_as(IP), len(F),
+                                      q.ctypes.data_as(DP), None, 1000.0, 1e8, 0.5, 0, ctypes.byref(bid))
+
+    return add, lambda: L.zema_destroy_scene(h)
+
+
+def test_affine_mesh_must_be_closed_and_outward():
+    # Eq. 2's mass properties integrate over the enclosed volume: open,
+    # inconsistently oriented, inward or degenerate surfaces are rejected
+    # with ZEMA_ERR_INVALID_ARG at add time
+    import numpy as np
+
+    from paper_2311_05945_b300 import scenes as S
+    add, close = _affine_adder()
+    V, F = S.box_surface((0.1, 0.2, 0.3), 2)
+    assert add(V, F) == 0
+    assert add(V, F[:-1]) == 1                      # one face missing: open
+    assert add(V, F[:, ::-1]) == 1                  # every face reversed: inward
+    Fm = F.copy()
+    Fm[0] = Fm[0, ::-1]
+    assert add(V, Fm) == 1                          # one face flipped
+    Fd = F.copy()
+    Fd[0, 1] = Fd[0, 0]
+    assert add(V, Fd) == 1                          # degenerate face
+    Vs, Fs = S.uv_sphere_surface((0.1, 0.1, 0.1), 12, 12)
+    assert add(Vs, Fs) == 0
+    assert add(np.vstack([V, Vs + 1.0]), np.vstack([F, Fs + len(V)])) == 0  # two closed shells
+    close()
+
+
+def test_generated_affine_meshes_are_accepted():
+    from paper_2311_05945_b300 import scenes as S
+    add, close = _affine_adder()
+    scenes = [S.scene_c1(), S.scene_c2(), S.scene_c3(n_envs=4), S.scene_c5(tets_per_body=300), S.scene_joint(),
+              S.scene_slope(), S.scene_kinematic_track(), S.scene_free_fall(), S.scene_tiny_contact()]
+    scenes += [S.scene_resolution(n) for n in S.RESOLUTION_SEGMENTS[:3]]
+    for sc in scenes:
+        for a in sc.affines:
+            assert add(a.V, a.F) == 0, sc.name
+    close()
