@@ -129,7 +129,12 @@ def test_generated_affine_meshes_are_accepted():
     add, close = _affine_adder()
     scenes = [S.scene_c1(), S.scene_c2(), S.scene_c3(n_envs=4), S.scene_c5(tets_per_body=300), S.scene_joint(),
               S.scene_slope(), S.scene_kinematic_track(), S.scene_free_fall(), S.scene_tiny_contact()]
-    scenes += [S.scene_resolution(n) for n in S.RESOLUTION_SEGMENTS[:3]]
+    scenes += [S.scene_resolution(n) for n in S.RESOLUTION_SEGMENTS]
+    # the pile variants the GPU tests, the benchmark and the training script build
+    scenes += [S.scene_c5(n_steps=2, tets_per_body=100, n_soft=2, n_convex=1, n_nonconvex=1, n_seg=6, bin_subdiv=1),
+               S.scene_c5(n_steps=2, tets_per_body=300, n_soft=2, n_convex=2, n_nonconvex=2, n_seg=8, bin_subdiv=1),
+               S.scene_c5(n_steps=2, tets_per_body=300, n_seg=8, bin_subdiv=1),
+               S.scene_c5(n_steps=2, tets_per_body=300, n_soft=4, n_convex=6, n_nonconvex=6, n_seg=16, bin_subdiv=2)]
     for sc in scenes:
         for a in sc.affines:
             assert add(a.V, a.F) == 0, sc.name
