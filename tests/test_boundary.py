@@ -139,3 +139,36 @@ def test_generated_affine_meshes_are_accepted():
         for a in sc.affines:
             assert add(a.V, a.F) == 0, sc.name
     close()
+
+
+def test_tet_body_arguments_checked_at_add_time():
+    # host-side checks of zema_add_tet_body: positive orientation (else
+    # ZEMA_ERR_INVERTED_INPUT), index range, Poisson ratio in [0, 0.5), env
+    import numpy as np
+
+    from paper_2311_05945_b300.zema import Params
+    L = ctypes.CDLL(zbuild.build())
+    DP, IP = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)
+    L.zema_default_params.argtypes = [ctypes.POINTER(Params)]
+    L.zema_create_scene.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_void_p)]
+    L.zema_add_tet_body.argtypes = [ctypes.c_void_p, ctypes.c_int32, DP, ctypes.c_int64, IP, ctypes.c_int64, DP, DP,
+                                    ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, IP]
+    L.zema_destroy_scene.argtypes = [ctypes.c_void_p]
+    p = Params()
+    L.zema_default_params(ctypes.byref(p))
+    h = ctypes.c_void_p()
+    assert L.zema_create_scene(ctypes.byref(p), ctypes.byref(h)) == 0
+    X = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], dtype=np.float64)
+    bid = ctypes.c_int32()
+
+    def add(T, env=0, nu=0.4):
+        T = np.ascontiguousarray(T, dtype=np.int32)
+        return L.zema_add_tet_body(h, env, X.ctypes.data_as(DP), len(X), T.ctypes.data_as(IP), len(T), None, None,
+                                   1e5, nu, 1000.0, 0.5, ctypes.byref(bid))
+
+    assert add([[0, 1, 2, 3]]) == 0
+    assert add([[0, 2, 1, 3]]) == 5          # negative orientation
+    assert add([[0, 1, 2, 7]]) == 1          # index out of range
+    assert add([[0, 1, 2, 3]], nu=0.5) == 1  # incompressible limit
+    assert add([[0, 1, 2, 3]], env=1) == 1   # one env only
+    L.zema_destroy_scene(h)
