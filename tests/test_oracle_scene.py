@@ -593,3 +593,43 @@ def test_inertia_at_the_start_of_a_step():
     w = p.dt * v + p.dt ** 2 * np.array(p.gravity)
     ref = 0.5 * M * w @ w
     assert abs(E - ref) <= 1e-10 * ref, (E, ref)
+
+
+def _tet_surface(v):
+    """A tetrahedron as a closed, outward triangle mesh."""
+    F = np.array([[0, 2, 1], [0, 1, 3], [0, 3, 2], [1, 2, 3]], dtype=np.int32)
+    if np.linalg.det(np.stack([v[1] - v[0], v[2] - v[0], v[3] - v[0]], 1)) < 0:
+        F = F[:, ::-1].copy()
+    return np.asarray(v, dtype=float), F
+
+
+@pytest.mark.parametrize("gap", [0.2e-3, 0.5e-3, 0.9e-3])
+def test_single_contact_barrier_and_friction_energy(gap):
+    # one active pair at the scene level: the tip of a small affine tetrahedron
+    # at height gap < dhat over the interior of a fixed tetrahedron's top face,
+    # every other feature far beyond dhat; at rest, no gravity.  Without
+    # friction the potential is kappa b(gap) (Eq. 4-5, no mollifier for a
+    # point-triangle pair); with friction lagged at this state it adds
+    # mu lambda f0(0) = mu kappa |b'(gap)| eps_v h / 3 (Eq. 9-10, readings c3
+    # and c4), with mu the smaller of the two bodies' coefficients.
+    p = S.Params(dt=0.01, gravity=(0.0, 0.0, 0.0))
+    s = S.Scene("one_pair", p)
+    Vf, Ff = _tet_surface(np.array([[-1.0, 0, -1], [1.0, 0, -1], [0, 0, 1.5], [0, -1.0, 0]]))
+    s.affines.append(S.AffineBody(Vf, Ff, S.q_identity((0, 0, 0)), rho=1000.0, stiffness=1e8, mu=0.7, mode=1))
+    tip = np.array([0.1, gap, 0.1])
+    Vt, Ft = _tet_surface(np.array([tip, tip + [-0.05, 0.1, -0.05], tip + [0.05, 0.1, -0.05],
+                                    tip + [0.0, 0.1, 0.06]]))
+    s.affines.append(S.AffineBody(Vt, Ft, S.q_identity((0, 0, 0)), rho=1000.0, stiffness=1e8, mu=0.4))
+    dh = p.dhat
+    b = -(gap - dh) ** 2 * np.log(gap / dh)
+    b1 = -2 * (gap - dh) * np.log(gap / dh) - (gap - dh) ** 2 / gap
+    o = Oracle(s)
+    o.prepare(0, friction=False)
+    kappa = o.kappa()
+    E, _, _, na = o.eval(o.dofs(), grad=True)
+    assert na == 1
+    assert abs(E - kappa * b) <= 1e-12 * kappa * b, (E, kappa * b)
+    o.prepare(0, friction=True)
+    E = o.eval(o.dofs())[0]
+    ref = kappa * b + 0.4 * kappa * abs(b1) * p.eps_v * p.dt / 3
+    assert abs(E - ref) <= 1e-12 * ref, (E, ref)
