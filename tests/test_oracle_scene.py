@@ -633,3 +633,41 @@ def test_single_contact_barrier_and_friction_energy(gap):
     E = o.eval(o.dofs())[0]
     ref = kappa * b + 0.4 * kappa * abs(b1) * p.eps_v * p.dt / 3
     assert abs(E - ref) <= 1e-12 * ref, (E, ref)
+
+
+@pytest.mark.parametrize("phi", [0.5, 0.02])
+def test_single_edge_edge_contact_energy(phi):
+    # one active edge-edge pair at the scene level: the top edge of a fixed
+    # tetrahedron along x and the bottom edge of a free one at height gap,
+    # turned by phi about y, crossing at their midpoints; all other features
+    # stay beyond dhat.  The potential is kappa e(c) b(gap) with IPC's
+    # mollifier (reading c6): c = |ea x eb|^2 = 0.04^2 sin^2(phi) against
+    # eps_x = 1e-3 |ea|^2 |eb|^2 = 1.6e-6 at rest, so e = 1 at phi = 0.5 and
+    # e = r (2 - r), r = c / eps_x, at phi = 0.02.  Lagged friction adds
+    # mu kappa e |b'(gap)| eps_v h / 3.
+    gap = 0.5e-3
+    p = S.Params(dt=0.01, gravity=(0.0, 0.0, 0.0))
+    s = S.Scene("one_ee_pair", p)
+    Va, Fa = _tet_surface(np.array([[-0.1, 0, 0], [0.1, 0, 0], [0, -0.1, -0.1], [0, -0.1, 0.1]]))
+    s.affines.append(S.AffineBody(Va, Fa, S.q_identity((0, 0, 0)), rho=1000.0, stiffness=1e8, mu=0.6, mode=1))
+    d = np.array([np.cos(phi), 0.0, np.sin(phi)])
+    nrm = np.array([-np.sin(phi), 0.0, np.cos(phi)])
+    top = np.array([0.0, gap + 0.1, 0.0])
+    Vb, Fb = _tet_surface(np.array([[0, gap, 0] - 0.1 * d, [0, gap, 0] + 0.1 * d, top - 0.1 * nrm, top + 0.1 * nrm]))
+    s.affines.append(S.AffineBody(Vb, Fb, S.q_identity((0, 0, 0)), rho=1000.0, stiffness=1e8, mu=0.3))
+    dh = p.dhat
+    c = 0.04 ** 2 * np.sin(phi) ** 2
+    r = c / 1.6e-6
+    e = r * (2 - r) if r < 1 else 1.0
+    b = -(gap - dh) ** 2 * np.log(gap / dh)
+    b1 = -2 * (gap - dh) * np.log(gap / dh) - (gap - dh) ** 2 / gap
+    o = Oracle(s)
+    o.prepare(0, friction=False)
+    kappa = o.kappa()
+    E, _, _, na = o.eval(o.dofs(), grad=True)
+    assert na == 1
+    assert abs(E - kappa * e * b) <= 1e-9 * kappa * e * b, (E, kappa * e * b, e)
+    o.prepare(0, friction=True)
+    E = o.eval(o.dofs())[0]
+    ref = kappa * e * b + 0.3 * kappa * e * abs(b1) * p.eps_v * p.dt / 3
+    assert abs(E - ref) <= 1e-9 * ref, (E, ref)
