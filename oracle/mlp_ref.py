@@ -7,8 +7,9 @@ layout: per layer l, W_l (dims[l] x dims[l+1], row-major) then b_l.  The
 computation runs in the dtype of the inputs (float32 for the parity checks,
 float64 for the finite-difference pins).  The paper has no learned
 component, so nothing in it pins this code; it is pinned by central finite
-differences of the loss and by the least-squares optimum of a single linear
-layer, where the gradient must vanish.
+differences of the loss, by the least-squares optimum of a single linear
+layer, where the gradient must vanish, and its bfloat16 rounding by a library
+float32 -> bfloat16 conversion.
 """
 import numpy as np
 

@@ -1,6 +1,7 @@
 """Pins of the CPU reference MLP (warm-start network): central finite
-differences of the loss, and the vanishing gradient at the least-squares
-optimum of a single linear layer."""
+differences of the loss, the vanishing gradient at the least-squares
+optimum of a single linear layer, and bfloat16 rounding against a library
+conversion."""
 import numpy as np
 
 from oracle import mlp_ref
@@ -36,3 +37,17 @@ def test_reference_gradient_vanishes_at_least_squares_optimum():
     # and away from it the loss is larger
     l0 = mlp_ref.loss_and_grad(theta, [3, 2], x, t)[0]
     assert mlp_ref.loss_and_grad(theta + 1e-3, [3, 2], x, t)[0] > l0
+
+
+def test_bf16_rounding_matches_a_library_conversion():
+    # the reference's bfloat16 rounding (nearest, ties to even) against
+    # torch's float32 -> bfloat16 conversion on random and tie values
+    import torch
+    rng = np.random.default_rng(5)
+    a = (rng.standard_normal(100000) * np.exp(rng.uniform(-20, 20, 100000))).astype(np.float32)
+    ties = np.array([1 + 2 ** -8, 1 + 3 * 2 ** -8, -(1 + 2 ** -8), 3.0 + 2 ** -7], dtype=np.float32)
+    a = np.concatenate([a, ties, np.float32([0.0, -0.0, 1e-40, 3.4e38])])
+    ref = torch.from_numpy(a).to(torch.bfloat16).to(torch.float32).numpy()
+    out = mlp_ref.round_bf16(a)
+    assert np.array_equal(out.view(np.uint32), ref.view(np.uint32))
+    assert out[-8] == 1.0 and out[-7] == np.float32(1 + 2 ** -6)  # ties go to the even significand
