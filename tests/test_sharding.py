@@ -38,7 +38,7 @@ def _worker(rank, world, port, out):
 
 
 def test_two_gloo_ranks_shard_and_reduce():
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()  # no fork of this (threaded) process
     out = mgr.dict()
     port = 29500 + (os.getpid() % 1000)
     mp.spawn(_worker, args=(2, port, out), nprocs=2, join=True)
