@@ -671,3 +671,29 @@ def test_single_edge_edge_contact_energy(phi):
     E = o.eval(o.dofs())[0]
     ref = kappa * e * b + 0.3 * kappa * e * abs(b1) * p.eps_v * p.dt / 3
     assert abs(E - ref) <= 1e-9 * ref, (E, ref)
+
+
+def test_spring_energy_and_force_at_rest():
+    # spring constraints h^2 k |x - target|^2 on body-local vertices of the
+    # second soft body (its local indices must map to its own vertices): at
+    # the rest shape, at rest, with no gravity, the potential is
+    # h^2 k sum |delta|^2 and the gradient 2 h^2 k delta on those vertices only
+    p = S.Params(dt=0.01, gravity=(0.0, 0.0, 0.0))
+    s = S.Scene("springs_at_rest", p)
+    X0, T0 = S.soft_cube(3, 0.2, (0.0, 0.0, 0.0))
+    X1, T1 = S.soft_cube(3, 0.2, (1.0, 0.0, 0.0))
+    s.tets.append(S.TetBody(X0, T0, E=1e5, nu=0.4, rho=1000.0, mu=0.3))
+    s.tets.append(S.TetBody(X1, T1, E=1e5, nu=0.4, rho=1000.0, mu=0.3))
+    verts = np.array([2, 11, 20], dtype=np.int32)
+    delta = np.array([[0.01, 0.0, 0.0], [0.0, -0.02, 0.0], [0.003, 0.004, 0.0]])
+    k = 3.0e3
+    s.springs.append((1, verts, X1[verts] - delta, k))
+    o = Oracle(s)
+    o.prepare(0)
+    E, g, _, _ = o.eval(o.dofs(), grad=True)
+    h2 = p.dt ** 2
+    assert abs(E - h2 * k * (delta ** 2).sum()) <= 1e-12 * h2 * k * (delta ** 2).sum()
+    G = g[:3 * (len(X0) + len(X1))].reshape(-1, 3)
+    ref = np.zeros_like(G)
+    ref[len(X0) + verts] = 2 * h2 * k * delta
+    assert np.abs(G - ref).max() <= 1e-12 * np.abs(ref).max()
