@@ -500,19 +500,24 @@ def test_kappa_doubles_when_contact_closes_below_a_tenth_of_dhat(kmin):
     assert doubled >= 1
 
 
+@pytest.mark.parametrize("model", [0, 1, 2])
 @pytest.mark.parametrize("scale", [0.9, 1.15])
-def test_uniformly_scaled_cube_elastic_energy(scale):
-    # the scene-level elastic term h^2 sum_e V_e Psi(F_e) (Eq. 1, reading c9)
-    # of a soft cube scaled uniformly by s about the origin, at rest and with
-    # no gravity: every F_e = s I, so the whole potential is
-    # h^2 V Psi(s I) = h^2 V (3 mu/2 (s^2 - 1) - 3 mu ln s + 9 lam/2 (ln s)^2),
-    # with mu = E / (2 (1 + nu)) and lam = E nu / ((1 + nu)(1 - 2 nu)).  This
-    # pins the rest shapes, the volumes, the Lame parameters and the h^2.
+def test_uniformly_scaled_cube_elastic_energy(scale, model):
+    # the scene-level elastic term h^2 sum_e V_e Psi(F_e) (Eq. 1) of a soft
+    # cube scaled uniformly by s about the origin, at rest and with no
+    # gravity: every F_e = s I, so the whole potential is h^2 V Psi(s I), with
+    # mu = E / (2 (1 + nu)) and lam = E nu / ((1 + nu)(1 - 2 nu)) and, per
+    # material (reading c9 and the two optional models):
+    #   Neo-Hookean         3 mu/2 (s^2 - 1) - 3 mu ln s + 9 lam/2 (ln s)^2,
+    #   St. Venant-Kirchhoff 3 mu e^2 + 9 lam/2 e^2 with e = (s^2 - 1)/2,
+    #   fixed corotated     3 mu (s - 1)^2 + lam/2 (s^3 - 1)^2.
+    # This pins the rest shapes, the volumes, the Lame parameters, the h^2 and
+    # the per-body material switch.
     p = S.Params(dt=0.01, gravity=(0.0, 0.0, 0.0))
     s = S.Scene("scaled", p)
     X, T = S.soft_cube(4, 0.3, (-0.15, -0.15, -0.15))
     Ey, nu = 2e5, 0.35
-    s.tets.append(S.TetBody(X, T, E=Ey, nu=nu, rho=1000.0, mu=0.5))
+    s.tets.append(S.TetBody(X, T, E=Ey, nu=nu, rho=1000.0, mu=0.5, model=model))
     o = Oracle(s)
     st = o.get_state(0)
     n = len(X)
@@ -523,8 +528,11 @@ def test_uniformly_scaled_cube_elastic_energy(scale):
     E = o.eval(o.dofs())[0]
     mu = Ey / (2 * (1 + nu))
     lam = Ey * nu / ((1 + nu) * (1 - 2 * nu))
-    ls = np.log(scale)
-    ref = p.dt ** 2 * 0.3 ** 3 * (1.5 * mu * (scale ** 2 - 1) - 3 * mu * ls + 4.5 * lam * ls ** 2)
+    ls, e = np.log(scale), 0.5 * (scale ** 2 - 1)
+    psi = (1.5 * mu * (scale ** 2 - 1) - 3 * mu * ls + 4.5 * lam * ls ** 2,
+           3 * mu * e ** 2 + 4.5 * lam * e ** 2,
+           3 * mu * (scale - 1) ** 2 + 0.5 * lam * (scale ** 3 - 1) ** 2)[model]
+    ref = p.dt ** 2 * 0.3 ** 3 * psi
     assert abs(E - ref) <= 1e-10 * abs(ref), (E, ref)
 
 
