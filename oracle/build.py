@@ -1,6 +1,9 @@
 """Build the CPU oracle shared library (test infrastructure only).
 
-g++ -O2, strict IEEE FP64 (no fast-math, no FMA contraction), serial.
+g++ -O2, strict IEEE FP64 (no fast-math, no FMA contraction), with OpenMP
+for the loops whose iterations are independent.  The library runs on one
+thread unless orc_set_threads asks for more, and every sum stays serial in
+index order, so results are bit-identical for any thread count.
 """
 import os
 import subprocess
@@ -16,7 +19,7 @@ def build(force: bool = False) -> str:
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
         return LIB
     cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
-           "-Wall", "-Wno-unused-function", "-o", LIB + ".tmp", SRC]
+           "-fopenmp", "-Wall", "-Wno-unused-function", "-o", LIB + ".tmp", SRC]
     subprocess.run(cmd, check=True)
     os.replace(LIB + ".tmp", LIB)
     return LIB

@@ -62,6 +62,25 @@
 #include <tuple>
 #include <array>
 #include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+// Loops whose iterations write only their own slots run in parallel when the
+// library is built with OpenMP; every sum over them is then taken serially,
+// in index order, afterwards, so results are bit-identical to a serial run
+// for any thread count.
+// The thread count is the library's own (orc_set_threads, 1 at load), so
+// the process-wide OpenMP setting of other libraries is left alone.
+static int g_orc_threads = 1;
+#ifdef _OPENMP
+#define ORC_PRAGMA(x) _Pragma(#x)
+#define ORC_PARALLEL_FOR ORC_PRAGMA(omp parallel for schedule(static) num_threads(g_orc_threads))
+#define ORC_PARALLEL_FOR_DYNAMIC ORC_PRAGMA(omp parallel for schedule(dynamic, 8) num_threads(g_orc_threads))
+#else
+#define ORC_PARALLEL_FOR
+#define ORC_PARALLEL_FOR_DYNAMIC
+#endif
 
 namespace {
 
@@ -839,31 +858,42 @@ void candidate_pairs(const Scene& S, int env, const std::vector<P3>& P0, const s
         return b;
     };
     std::vector<Box> tb(nt), eb(ne), pb(ns);
-    for (size_t t = 0; t < nt; ++t) tb[t] = bx(&S.tris[3 * t], 3);
-    for (size_t e = 0; e < ne; ++e) eb[e] = bx(&S.edges[2 * e], 2);
-    for (size_t s = 0; s < ns; ++s) {
+    ORC_PARALLEL_FOR
+    for (long t = 0; t < (long)nt; ++t) tb[t] = bx(&S.tris[3 * t], 3);
+    ORC_PARALLEL_FOR
+    for (long e = 0; e < (long)ne; ++e) eb[e] = bx(&S.edges[2 * e], 2);
+    ORC_PARALLEL_FOR
+    for (long s = 0; s < (long)ns; ++s) {
         int id = (int)s;
         pb[s] = bx(&id, 1);
     }
-    for (size_t s = 0; s < ns; ++s) {
+    // every query primitive's pairs go to a list of its own, concatenated in
+    // query order afterwards: the same list, in the same order, whatever the
+    // thread count
+    std::vector<std::vector<Pair>> lp(ns), le(ne);
+    ORC_PARALLEL_FOR_DYNAMIC
+    for (long s = 0; s < (long)ns; ++s) {
         if (body_env(S, S.sv[s].body) != env) continue;
         for (size_t t = 0; t < nt; ++t) {
             const int* T = &S.tris[3 * t];
             if (!pt_valid(S, (int)s, T)) continue;
             if (!overlap(pb[s], tb[t])) continue;
-            out.push_back(Pair{0, {(int)s, T[0], T[1], T[2]}});
+            lp[s].push_back(Pair{0, {(int)s, T[0], T[1], T[2]}});
         }
     }
-    for (size_t a = 0; a < ne; ++a) {
+    ORC_PARALLEL_FOR_DYNAMIC
+    for (long a = 0; a < (long)ne; ++a) {
         const int* A = &S.edges[2 * a];
         if (body_env(S, S.sv[A[0]].body) != env) continue;
         for (size_t b = a + 1; b < ne; ++b) {
             const int* B = &S.edges[2 * b];
             if (!ee_valid(S, A, B)) continue;
             if (!overlap(eb[a], eb[b])) continue;
-            out.push_back(Pair{1, {A[0], A[1], B[0], B[1]}});
+            le[a].push_back(Pair{1, {A[0], A[1], B[0], B[1]}});
         }
     }
+    for (const auto& l : lp) out.insert(out.end(), l.begin(), l.end());
+    for (const auto& l : le) out.insert(out.end(), l.begin(), l.end());
 }
 
 void stencil(const std::vector<P3>& P, const Pair& pr, double* x12) {
@@ -919,6 +949,7 @@ bool dense_solve(int n, const std::vector<Trip>& T, const std::vector<double>& b
         if (!(s > 0.0)) return false;
         double l = std::sqrt(s);
         A[(size_t)j * n + j] = l;
+        ORC_PARALLEL_FOR
         for (int i = j + 1; i < n; ++i) {
             double t = A[(size_t)i * n + j];
             for (int k = 0; k < j; ++k) t -= A[(size_t)i * n + k] * A[(size_t)j * n + k];
@@ -992,6 +1023,7 @@ bool cg_solve(int n, const std::vector<Trip>& T, const std::vector<double>& b, c
     }
     for (int i = 0; i < n; ++i) rp[i + 1] += rp[i];
     auto spmv = [&](const std::vector<double>& in, std::vector<double>& o) {
+        ORC_PARALLEL_FOR
         for (int i = 0; i < n; ++i) {
             double s = 0.0;
             for (int k = rp[i]; k < rp[i + 1]; ++k) s += vv[k] * in[ci[k]];
@@ -1010,7 +1042,8 @@ bool cg_solve(int n, const std::vector<Trip>& T, const std::vector<double>& b, c
         inv[bi] = A;
     }
     auto prec = [&](const std::vector<double>& r, std::vector<double>& z) {
-        for (size_t bi = 0; bi < blk_off.size(); ++bi) {
+        ORC_PARALLEL_FOR
+        for (long bi = 0; bi < (long)blk_off.size(); ++bi) {
             int o = blk_off[bi], m = blk_n[bi];
             for (int i = 0; i < m; ++i) {
                 double s = 0.0;
@@ -1167,40 +1200,67 @@ double env_energy(const Scene& S, int env, const EnvDofs& D, const State& st, co
                 if (Y && opt.hess) Y->H.push_back(Trip{o + k, o + k, 2.0 * h2 * ks});
             }
     }
-    // elasticity (Eq. 1, h^2 Phi)
-    for (size_t t = 0; t < S.tet_body.size(); ++t) {
+    // elasticity (Eq. 1, h^2 Phi): per tet of the env, its density psi,
+    // x-space gradient gx and PSD-projected Hessian Hx (each tet on its own,
+    // in parallel under OpenMP), then summed in tet order
+    std::vector<int> etets;
+    for (size_t t = 0; t < S.tet_body.size(); ++t)
+        if (S.soft[S.bodies[S.tet_body[t]].second].env == env) etets.push_back((int)t);
+    const bool tet_der = Y && (opt.grad || opt.hess);
+    const size_t ntl = etets.size();
+    std::vector<double> tpsi(ntl), tgx(tet_der ? 12 * ntl : 0), tHx(tet_der && opt.hess ? 144 * ntl : 0);
+    std::vector<char> tok(ntl, 1);
+    ORC_PARALLEL_FOR_DYNAMIC
+    for (long l = 0; l < (long)ntl; ++l) {
+        const int t = etets[l];
         int sb = S.bodies[S.tet_body[t]].second;
-        if (S.soft[sb].env != env) continue;
         double F[9];
-        def_grad(S, (int)t, st.x, F);
+        def_grad(S, t, st.x, F);
         D2<9> psi;
         if (S.soft[sb].model == 1)
             psi = stvk_psi(F, S.soft[sb].mu_l, S.soft[sb].lam_l);
         else if (S.soft[sb].model == 2) {
-            if (!fcr_psi(F, S.soft[sb].mu_l, S.soft[sb].lam_l, psi)) return INF;
-        } else if (!nh_psi(F, S.soft[sb].mu_l, S.soft[sb].lam_l, psi))
-            return INF;
+            if (!fcr_psi(F, S.soft[sb].mu_l, S.soft[sb].lam_l, psi)) {
+                tok[l] = 0;
+                continue;
+            }
+        } else if (!nh_psi(F, S.soft[sb].mu_l, S.soft[sb].lam_l, psi)) {
+            tok[l] = 0;
+            continue;
+        }
+        tpsi[l] = psi.v;
+        if (!tet_der) continue;
         double w = h2 * S.tvol[t];
-        E += w * psi.v;
-        if (Y && (opt.grad || opt.hess)) {
-            double B[9][12];
-            dFdx(S, (int)t, B);
+        double B[9][12];
+        dFdx(S, t, B);
+        double* gx = &tgx[12 * l];
+        for (int j = 0; j < 12; ++j) {
+            gx[j] = 0.0;
+            for (int i = 0; i < 9; ++i) gx[j] += B[i][j] * psi.g[i];
+        }
+        if (!opt.hess) continue;
+        double HF[81];
+        for (int i = 0; i < 9; ++i)
+            for (int j = 0; j < 9; ++j) HF[9 * i + j] = psi.h[i][j];
+        psd_project(9, HF);
+        double* Hx = &tHx[144 * l];
+        for (int a = 0; a < 12; ++a)
+            for (int b = 0; b < 12; ++b) {
+                double s = 0.0;
+                for (int i = 0; i < 9; ++i)
+                    for (int j = 0; j < 9; ++j) s += B[i][a] * HF[9 * i + j] * B[j][b];
+                Hx[12 * a + b] = w * s;
+            }
+    }
+    for (size_t l = 0; l < ntl; ++l) {
+        if (!tok[l]) return INF;
+        const int t = etets[l];
+        double w = h2 * S.tvol[t];
+        E += w * tpsi[l];
+        if (tet_der) {
             const int* T = &S.tets[4 * t];
-            double gx[12] = {0};
-            for (int j = 0; j < 12; ++j)
-                for (int i = 0; i < 9; ++i) gx[j] += B[i][j] * psi.g[i];
-            double HF[81];
-            for (int i = 0; i < 9; ++i)
-                for (int j = 0; j < 9; ++j) HF[9 * i + j] = psi.h[i][j];
-            psd_project(9, HF);
-            double Hx[144];
-            for (int a = 0; a < 12; ++a)
-                for (int b = 0; b < 12; ++b) {
-                    double s = 0.0;
-                    for (int i = 0; i < 9; ++i)
-                        for (int j = 0; j < 9; ++j) s += B[i][a] * HF[9 * i + j] * B[j][b];
-                    Hx[12 * a + b] = w * s;
-                }
+            const double* gx = &tgx[12 * l];
+            const double* Hx = opt.hess ? &tHx[144 * l] : nullptr;
             for (int va = 0; va < 4; ++va) {
                 int oa = D.vert_dof[T[va]];
                 if (opt.grad)
@@ -1297,31 +1357,54 @@ double env_energy(const Scene& S, int env, const EnvDofs& D, const State& st, co
     double kap = S.kappa[env];
     int nact = 0;
     double dm = INF;
-    for (const Pair& pr : pairs) {
+    // per pair: distance, and for an active pair its barrier value, gradient
+    // and PSD-projected Hessian (each pair on its own, in parallel under
+    // OpenMP); the sums below then run in pair order
+    const bool pair_der = Y && (opt.grad || opt.hess);
+    const size_t npr = pairs.size();
+    std::vector<double> pd(npr), pb(npr), pgl(pair_der ? 12 * npr : 0), pHl(pair_der ? 144 * npr : 0);
+    ORC_PARALLEL_FOR_DYNAMIC
+    for (long k = 0; k < (long)npr; ++k) {
+        const Pair& pr = pairs[k];
         double x12[12];
         stencil(P, pr, x12);
         double d2 = stencil_d2(x12, pr.is_ee);
-        if (!(d2 > 0.0)) return INF;
+        if (!(d2 > 0.0)) {
+            pd[k] = -1.0;
+            continue;
+        }
         double d = std::sqrt(d2);
-        dm = std::min(dm, d);
+        pd[k] = d;
         if (!(d < S.P.dhat)) continue;
-        ++nact;
         double epsx = pr.is_ee ? ee_eps_x(S, pr) : 0.0;
-        if (!(Y && (opt.grad || opt.hess))) {
+        if (!pair_der) {
             double b = barrier(d, S.P.dhat);
             if (pr.is_ee) b *= ee_mollifier_value(x12, epsx);
-            E += kap * b;
+            pb[k] = b;
             continue;
         }
         D2<12> b;
         pair_barrier(x12, pr.is_ee, S.P.dhat, epsx, b);
-        E += kap * b.v;
-        double gl[12], Hl[144];
+        pb[k] = b.v;
+        double* gl = &pgl[12 * k];
+        double* Hl = &pHl[144 * k];
         for (int i = 0; i < 12; ++i) {
             gl[i] = kap * b.g[i];
             for (int j = 0; j < 12; ++j) Hl[12 * i + j] = kap * b.h[i][j];
         }
         psd_project(12, Hl);  // projected in the 12-dim pair space (Eq. 8)
+    }
+    for (size_t pi = 0; pi < npr; ++pi) {
+        const Pair& pr = pairs[pi];
+        const double d = pd[pi];
+        if (d < 0.0) return INF;
+        dm = std::min(dm, d);
+        if (!(d < S.P.dhat)) continue;
+        ++nact;
+        E += kap * pb[pi];
+        if (!pair_der) continue;
+        const double* gl = &pgl[12 * pi];
+        const double* Hl = &pHl[144 * pi];
         int off[4], nd[4];
         double J[4][3][12];
         for (int k = 0; k < 4; ++k) nd[k] = sv_jac(S, D, pr.s[k], off[k], J[k]);
@@ -1458,6 +1541,25 @@ double accd(const double* x12in, const double* p12in, bool is_ee, double s, doub
         tl = 0.9 * d / lp;
     }
     return t;
+}
+
+// min(1, ACCD bound of every swept pair) for the motion P0 -> P1 (s = 0.1,
+// t_c = 1): each pair's bound on its own (in parallel under OpenMP), then
+// the minimum in pair order
+double swept_accd_min(const std::vector<P3>& P0, const std::vector<P3>& P1, const std::vector<Pair>& swept) {
+    std::vector<double> tb(swept.size());
+    ORC_PARALLEL_FOR_DYNAMIC
+    for (long k = 0; k < (long)swept.size(); ++k) {
+        const Pair& pr = swept[k];
+        double x12[12], e12[12], p12[12];
+        stencil(P0, pr, x12);
+        stencil(P1, pr, e12);
+        for (int i = 0; i < 12; ++i) p12[i] = e12[i] - x12[i];
+        tb[k] = accd(x12, p12, pr.is_ee, 0.1, 1.0, 10000);
+    }
+    double alpha = 1.0;
+    for (double t : tb) alpha = std::min(alpha, t);
+    return alpha;
 }
 
 // ===========================================================================
@@ -1632,13 +1734,12 @@ void commit_state(Scene& S, const State& st) {
         for (int k = 0; k < 12; ++k) S.aff[a].q[k] = st.q[12 * a + k];
 }
 
-int newton_env(Scene& S, int env, double tol, StepStats& ss) {
-    EnvDofs D = env_dofs(S, env);
-    State st;
-    get_state(S, st);
-    std::vector<double> y;
-    store_dofs(S, D, st, y);
-    // preconditioner blocks for CG
+// The Newton system H p = rhs of an env: `which` 0 as the stepper solves it
+// (dense Cholesky up to 2,500 DOF, else CG with block-Jacobi blocks of one
+// soft vertex (3) or one affine body (12) to relative residual 1e-12),
+// 1 dense Cholesky, 2 that CG.
+bool newton_solve(const EnvDofs& D, const Sys& Y, const std::vector<double>& rhs, std::vector<double>& p, int which) {
+    if (which == 1 || (which == 0 && D.n <= 2500)) return dense_solve(D.n, Y.H, rhs, p);
     std::vector<int> bo, bn;
     for (int i : D.verts) {
         bo.push_back(D.vert_dof[i]);
@@ -1648,6 +1749,15 @@ int newton_env(Scene& S, int env, double tol, StepStats& ss) {
         bo.push_back(D.aff_dof[a]);
         bn.push_back(12);
     }
+    return cg_solve(D.n, Y.H, rhs, bo, bn, 1e-12, p);
+}
+
+int newton_env(Scene& S, int env, double tol, StepStats& ss) {
+    EnvDofs D = env_dofs(S, env);
+    State st;
+    get_state(S, st);
+    std::vector<double> y;
+    store_dofs(S, D, st, y);
     for (int it = 0; it < S.P.max_newton; ++it) {
         load_dofs(S, D, y, st);
         std::vector<P3> P;
@@ -1662,8 +1772,7 @@ int newton_env(Scene& S, int env, double tol, StepStats& ss) {
         ss.n_active = nact;
         std::vector<double> rhs(D.n), p;
         for (int i = 0; i < D.n; ++i) rhs[i] = -Y.g[i];
-        bool ok = (D.n <= 2500) ? dense_solve(D.n, Y.H, rhs, p) : cg_solve(D.n, Y.H, rhs, bo, bn, 1e-12, p);
-        if (!ok) return E_LIN;
+        if (!newton_solve(D, Y, rhs, p, 0)) return E_LIN;
         if (step_inf_norm(S, D, p) <= tol) {
             ss.energy = E0;
             commit_state(S, st);
@@ -1679,15 +1788,7 @@ int newton_env(Scene& S, int env, double tol, StepStats& ss) {
         all_sv_pos(S, s1.x, s1.q, P1);
         std::vector<Pair> swept;
         candidate_pairs(S, env, P, &P1, swept);
-        double alpha = 1.0;
-        for (const Pair& pr : swept) {
-            double x12[12], p12[12];
-            stencil(P, pr, x12);
-            double e12[12];
-            stencil(P1, pr, e12);
-            for (int i = 0; i < 12; ++i) p12[i] = e12[i] - x12[i];
-            alpha = std::min(alpha, accd(x12, p12, pr.is_ee, 0.1, 1.0, 10000));
-        }
+        double alpha = swept_accd_min(P, P1, swept);
         // backtracking line search on the energy over the swept candidates
         double Eprev = env_energy(S, env, D, st, swept, nullptr, EvalOpt{false, false});
         bool acc = false;
@@ -1776,14 +1877,7 @@ void warm_start(Scene& S, int env, StepStats& ss) {
     all_sv_pos(S, s1.x, s1.q, P1);
     std::vector<Pair> swept;
     candidate_pairs(S, env, P0, &P1, swept);
-    double alpha = 1.0;
-    for (const Pair& pr : swept) {
-        double x12[12], e12[12], p12[12];
-        stencil(P0, pr, x12);
-        stencil(P1, pr, e12);
-        for (int i = 0; i < 12; ++i) p12[i] = e12[i] - x12[i];
-        alpha = std::min(alpha, accd(x12, p12, pr.is_ee, 0.1, 1.0, 10000));
-    }
+    double alpha = swept_accd_min(P0, P1, swept);
     for (int i = 0; i < D.n; ++i) y1[i] = y0[i] + alpha * dl[i];
     load_dofs(S, D, y1, s1);
     double E0 = env_energy(S, env, D, st, swept, nullptr, EvalOpt{false, false});
@@ -2373,6 +2467,42 @@ double orc_env_eval(void* s, int env, const double* y, double* g, double* H, int
         for (const Trip& t : Y.H) H[(size_t)t.i * D.n + t.j] += t.v;
     }
     return E;
+}
+
+// Newton system of env at DOF vector y (as orc_env_eval assembles it) solved
+// for p = -H^-1 g with newton_solve's `which` (0 the stepper's choice, 1 dense
+// Cholesky, 2 CG); p: n doubles.  Returns 0, or -1 if the solve failed.
+int orc_newton_system_solve(void* s, int env, const double* y, int which, double* p) {
+    Scene& S = *(Scene*)s;
+    EnvDofs D = env_dofs(S, env);
+    State st;
+    get_state(S, st);
+    std::vector<double> yy(y, y + D.n);
+    load_dofs(S, D, yy, st);
+    std::vector<P3> P;
+    all_sv_pos(S, st.x, st.q, P);
+    std::vector<Pair> pairs;
+    candidate_pairs(S, env, P, nullptr, pairs);
+    Sys Y;
+    env_energy(S, env, D, st, pairs, &Y, EvalOpt{true, true});
+    std::vector<double> rhs(D.n), out;
+    for (int i = 0; i < D.n; ++i) rhs[i] = -Y.g[i];
+    if (!newton_solve(D, Y, rhs, out, which)) return -1;
+    std::copy(out.begin(), out.end(), p);
+    return 0;
+}
+
+// OpenMP threads of the parallel loops (results do not depend on it); the
+// library starts with 1.  n <= 0 only reads.  Returns the count in use (1
+// without OpenMP).
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) g_orc_threads = n;
+    return g_orc_threads;
+#else
+    (void)n;
+    return 1;
+#endif
 }
 
 // ---------------------------------------------------------------------------

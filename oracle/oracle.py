@@ -55,6 +55,8 @@ def lib():
         L.orc_prepare.argtypes = [C.c_void_p, C.c_int, C.c_int]
         L.orc_env_eval.restype = C.c_double
         L.orc_env_eval.argtypes = [C.c_void_p, C.c_int, dp, dp, dp, ip]
+        L.orc_newton_system_solve.argtypes = [C.c_void_p, C.c_int, dp, C.c_int, dp]
+        L.orc_set_threads.argtypes = [C.c_int]
         L.orc_stencil_d2.restype = C.c_double
         L.orc_stencil_d2.argtypes = [dp, C.c_int, ip, dp, dp, dp]
         L.orc_pair_barrier.restype = C.c_double
@@ -273,6 +275,22 @@ class Oracle:
         na = np.zeros(1, dtype=np.int32)
         E = lib().orc_env_eval(self.h, env, _dp(y), _dp(g), _dp(H), _ip(na))
         return E, g, H, int(na[0])
+
+    def newton_direction(self, y, env=0, which=0):
+        """p = -H^-1 g of the Newton system at DOF vector y, solved as the
+        stepper does (which 0: dense Cholesky up to 2,500 DOF, else CG to a
+        1e-12 relative residual), or by dense Cholesky (1) or that CG (2)."""
+        y = _d(y)
+        p = np.zeros(len(y))
+        if lib().orc_newton_system_solve(self.h, env, _dp(y), int(which), _dp(p)) != 0:
+            raise RuntimeError("oracle linear solve failed")
+        return p
+
+
+def set_threads(n: int) -> int:
+    """Threads of the oracle's parallel loops (results are bit-identical for
+    any count; the library starts with 1).  Returns the count in use."""
+    return lib().orc_set_threads(int(n))
 
 
 # local functions -----------------------------------------------------------
