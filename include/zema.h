@@ -43,10 +43,10 @@ typedef enum {
     ZEMA_ERR_INVERTED_INPUT = 5,
     ZEMA_ERR_NEWTON_MAXITER = 6,
     ZEMA_ERR_LINESEARCH = 7,
-    ZEMA_ERR_PCG_MAXITER = 8,    /* reserved: a solve that reaches max_pcg returns its last
-                                    iterate, which the Newton step test and the line search judge */
+    ZEMA_ERR_PCG_MAXITER = 8,    /* a linear solve reached max_pcg iterations without meeting
+                                    pcg_rel_tol */
     ZEMA_ERR_NONFINITE = 9,
-    ZEMA_ERR_FAULT_INJECTED = 10, /* reserved: the library injects no faults */
+    ZEMA_ERR_FAULT_INJECTED = 10, /* a failure armed by zema_inject_fault */
     ZEMA_ERR_STATE = 11           /* call not allowed in the scene's current state */
 } zema_status;
 
@@ -152,18 +152,31 @@ zema_status zema_set_kinematic_target(zema_scene* s, int32_t body, const double 
 /* Advances n_steps time steps (Eq. 11).  stats may be NULL.  Errors:
  * ZEMA_ERR_NEWTON_MAXITER (no convergence within max_newton iterations),
  * ZEMA_ERR_LINESEARCH (no energy decrease after 60 halvings),
+ * ZEMA_ERR_PCG_MAXITER (a linear solve reached max_pcg iterations),
  * ZEMA_ERR_NONFINITE (a non-finite value in the linear solve),
+ * ZEMA_ERR_FAULT_INJECTED (see zema_inject_fault),
  * ZEMA_ERR_INTERSECTING_INPUT (at the first step, as zema_finalize),
  * ZEMA_ERR_OOM, ZEMA_ERR_CUDA.  The state then stays at the last completed
  * step. */
 zema_status zema_step(zema_scene* s, int32_t n_steps, zema_step_stats* stats);
 
-/* State of one body into a caller-owned host buffer of cap doubles.
- * Tet body: x then v (nv x 3 each); affine body: q then qdot (12 each).
- * *written receives the number of doubles. */
+/* State of one body into a caller-owned host buffer of cap doubles: the
+ * quantities Eq. 11 advances, positions x^t and velocities v^t of a soft body
+ * (Eq. 1), q^t and qdot^t of an affine body (Eq. 2).  Tet body: x then v
+ * (nv x 3 each); affine body: q then qdot (12 each, the caller's frame, A by
+ * rows).  *written (nullable) receives the number of doubles.  Before the
+ * first step it returns the initial state given at add time.  A body id out
+ * of range or cap too small: ZEMA_ERR_INVALID_ARG, buffer untouched.
+ * Synchronises the scene's stream. */
 zema_status zema_get_state(const zema_scene* s, int32_t body, double* out, int64_t cap, int64_t* written);
 
-/* Sets the state of one body (same layout as zema_get_state). */
+/* Sets the state (x^t, v^t or q^t, qdot^t of Eq. 11) of one body, same
+ * layout as zema_get_state; n must equal the body's count exactly, else
+ * ZEMA_ERR_INVALID_ARG with the state unchanged.  Before the first step it
+ * replaces the initial state; afterwards the next step starts from it (the
+ * caller is responsible for not creating intersections: nothing re-checks
+ * them).  A fixed body's velocity is forced to zero.  Synchronises the
+ * scene's stream. */
 zema_status zema_set_state(zema_scene* s, int32_t body, const double* in, int64_t n);
 
 /* All positions/velocities at once, device-to-device: x_dev and v_dev are
@@ -181,6 +194,47 @@ zema_status zema_get_kappa(const zema_scene* s, int32_t env, double* kappa);
  * gradient-balance rule for it). */
 zema_status zema_set_kappa(zema_scene* s, int32_t env, double kappa, double kappa_min);
 
+/* Whole-scene checkpoint (the time-stepping state of Eq. 11 with everything
+ * else that carries over from one step to the next): node positions and
+ * velocities x^t, v^t; the kinematic targets q~ and multipliers lambda_A of
+ * Eq. 13 and the prismatic joints' multipliers; per env the barrier stiffness
+ * kappa and kappa_min and the d_min of its doubling rule.  The scene's
+ * definition (bodies, materials, springs, joints) is not part of it: load a
+ * checkpoint only into a scene built by the same calls in the same order,
+ * in either precision.  Stepping both scenes on then gives bit-identical
+ * results (up to the autotuner's measured choice, see zema_autotune).
+ * zema_checkpoint_size: bytes of a checkpoint of this scene (after
+ * finalize; else ZEMA_ERR_STATE).  zema_save_checkpoint copies it into the
+ * caller's host buffer of cap bytes (*written = its size; a smaller cap is
+ * ZEMA_ERR_INVALID_ARG).  zema_load_checkpoint restores it; a header that does
+ * not match the scene's node, affine-body, joint and env counts, a wrong
+ * size or non-finite state is ZEMA_ERR_INVALID_ARG and leaves the scene
+ * unchanged.  The buffer is the caller's; neither call retains it. */
+zema_status zema_checkpoint_size(const zema_scene* s, int64_t* bytes);
+zema_status zema_save_checkpoint(const zema_scene* s, void* buf, int64_t cap, int64_t* written);
+zema_status zema_load_checkpoint(zema_scene* s, const void* buf, int64_t bytes);
+
+/* Host-side fault injection for testing a caller's failure handling (the
+ * paper has no counterpart).  Arms one failure at Newton iteration
+ * newton_iter (0-based, counted over all Newton iterations of the next
+ * zema_step call); it fires once and then disarms:
+ *  ZEMA_FAULT_STATUS        a kernel reads the armed device flag and writes
+ *                           ZEMA_ERR_FAULT_INJECTED into a device status word
+ *                           that the host reads with the step-norm test;
+ *  ZEMA_FAULT_SOLVE_NONFINITE a kernel reads the flag and marks the linear
+ *                           solves of that iteration as having met a
+ *                           non-finite value: ZEMA_ERR_NONFINITE;
+ *  ZEMA_FAULT_NO_DECREASE   the line search of that iteration sees no trial
+ *                           point lower the energy: ZEMA_ERR_LINESEARCH after
+ *                           its 60 halvings.
+ * zema_step then returns that status with the state at the last completed
+ * step, as for a real failure.  ZEMA_FAULT_NONE disarms.  Nothing faults,
+ * traps or hangs the GPU.  With the learned warm start, a no-decrease fault
+ * in a step that started from the learned proposal is absorbed by its
+ * fallback to the constant-velocity start. */
+enum { ZEMA_FAULT_NONE = 0, ZEMA_FAULT_STATUS = 1, ZEMA_FAULT_SOLVE_NONFINITE = 2, ZEMA_FAULT_NO_DECREASE = 3 };
+zema_status zema_inject_fault(zema_scene* s, int32_t kind, int32_t newton_iter);
+
 /* Number of CUDA kernels the library has launched in this process (all
  * scenes and entry points); a benchmark reads it before and after a timed
  * region. */
@@ -196,7 +250,14 @@ long long zema_launch_count(void);
 int zema_profile_kernel(const char* name);
 int zema_profile_read(double* ms_total, long long* launches, double* alg_bytes);
 
+/* Message of the last failed call on s (library-owned, valid until the next
+ * call on s; "" if none; "null scene" for s == NULL).  It names the failing
+ * step of the method, e.g. the Newton cap of the convergence test (config
+ * Newton tolerance) or the line search of the minimisation of Eq. 11. */
 const char* zema_last_error(const zema_scene* s);
+/* Releases the scene and all device memory it owns (through the scene's
+ * allocator hooks when given) after its stream's work completes.  NULL is a
+ * no-op; s must not be used afterwards. */
 void zema_destroy_scene(zema_scene* s);
 
 /* ------------------------------------------------------------------------
@@ -230,12 +291,14 @@ zema_status zema_candidates_raw(int64_t nsv, const double* pos0, const double* p
 
 /* zema_candidates_raw for callers that cannot allocate device memory (the
  * paper has no counterpart: it is a deployment variant of the broad phase).
- * Callers that record work into a CUDA stream capture, draw all device
- * memory from a pool fixed in advance, or must not call an allocator inside a
- * real-time loop cannot use zema_candidates_raw, which allocates scratch.
- * This entry point allocates nothing: every scratch buffer lives in one
- * file-scope device array of 64 MiB that each GPU loading the library holds
- * until the process exits.
+ * Callers that draw all device memory from a pool fixed in advance, or must
+ * not call an allocator inside a real-time loop, cannot use
+ * zema_candidates_raw, which allocates scratch.  This entry point allocates
+ * nothing: every scratch buffer lives in one file-scope device array of
+ * 64 MiB that each GPU loading the library holds until the process exits.
+ * It is not usable inside a CUDA stream capture: partway through, it
+ * synchronises `stream` and reads counts back to the host to size the
+ * following launches.
  *  - Inputs (pos0, pos1 nullable, sv_body, b_class, b_env, edges, tris) and
  *    outputs (pt_out, ee_out: cap pairs of int32 each) are DEVICE pointers;
  *    n_out (2 counts, may exceed cap: outputs then truncated) is host memory.
@@ -244,12 +307,16 @@ zema_status zema_candidates_raw(int64_t nsv, const double* pos0, const double* p
  *    host data).
  *  - Limits: nsv + ne + nt <= 65536, else ZEMA_ERR_INVALID_ARG; a scene whose
  *    grid entries and pair lists do not fit the 64 MiB array returns
- *    ZEMA_ERR_OOM.  Neither case touches the outputs' contents beyond n_out.
+ *    ZEMA_ERR_OOM.  Neither case writes the outputs or n_out.
+ *  - The device index arrays are checked by a kernel before any other kernel
+ *    indexes with them: a body id outside [0, nb), a body class outside
+ *    [0, 3], a negative env or an edge or triangle vertex outside [0, nsv)
+ *    returns ZEMA_ERR_INVALID_ARG with the outputs untouched.
  *  - The first call on a device resolves the array's device address
- *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *    (cudaGetSymbolAddress).
  *  - All calls share the one array and leave their contents in it; calls
  *    that overlap on the GPU (other streams or threads) race.  The call
- *    synchronises `stream` before returning. */
+ *    synchronises `stream` before returning, on every path. */
 zema_status zema_candidates_raw_noalloc(int64_t nsv, const double* pos0, const double* pos1, const int32_t* sv_body,
                                         int64_t nb, const int32_t* b_class, const int32_t* b_env, int64_t ne,
                                         const int32_t* edges, int64_t nt, const int32_t* tris, double inflate,

@@ -794,7 +794,7 @@ __global__ void __launch_bounds__(256) k_pcg_persistent(PcgArgs<Real> a) {
     }
     grid.sync();
     if (blockIdx.x == 0)
-        for (int e = tid; e < NE; e += blockDim.x) a.conv[e] = s_conv[e] == 2 ? 2 : 1;
+        for (int e = tid; e < NE; e += blockDim.x) a.conv[e] = s_conv[e] == 2 ? 2 : (s_conv[e] ? 1 : 3);
 }
 
 }  // namespace zema

@@ -1,12 +1,13 @@
 // Broad phase for callers that cannot allocate device memory.
 //
-// Some callers cannot call cudaMalloc while they run the contact query: code
-// that records work into a CUDA stream capture (where allocation calls are
-// not allowed), runtimes that hand out all device memory up front from a
-// fixed pool, or real-time loops that forbid allocator calls for latency.
+// Some callers cannot call cudaMalloc while they run the contact query:
+// runtimes that hand out all device memory up front from a fixed pool, or
+// real-time loops that forbid allocator calls for latency.
 // zema_candidates_raw_noalloc serves them: it takes device buffers for its
 // inputs and outputs and keeps every scratch buffer of the broad phase in one
-// file-scope device array of fixed size, so no call allocates.
+// file-scope device array of fixed size, so no call allocates.  The call is
+// not for stream capture: it synchronises its stream and reads counts back to
+// the host partway through, to size the following launches.
 #include <map>
 #include <mutex>
 
@@ -41,6 +42,31 @@ void* bump_alloc(size_t bytes, void*, void* ctx) {
 
 void bump_free(void*, void*, void*) {}
 
+// Checks the caller's device index arrays before any kernel indexes with
+// them: body ids in [0, nb), body classes in [0, 3], envs >= 0, edge and
+// triangle vertices in [0, nsv).  A bad entry sets *bad (no access is made
+// through it).
+__global__ void k_noalloc_check(const int* sv_body, int nsv, const int* b_class, const int* b_env, int nb,
+                                const int* edges, int ne, const int* tris, int nt, int* bad) {
+    const long long n = (long long)nsv + nb + 2ll * ne + 3ll * nt;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        bool ok;
+        if (i < nsv) {
+            ok = sv_body[i] >= 0 && sv_body[i] < nb;
+        } else if (i < nsv + nb) {
+            const long long b = i - nsv;
+            ok = b_class[b] >= 0 && b_class[b] <= 3 && b_env[b] >= 0;
+        } else {
+            const long long k = i - nsv - nb;
+            const int v = k < 2ll * ne ? edges[k] : tris[k - 2ll * ne];
+            ok = v >= 0 && v < nsv;
+        }
+        if (!ok) *bad = 1;
+    }
+}
+
+// env of every surface vertex from its body (ids checked above)
 __global__ void k_noalloc_sv_env(const int* sv_body, const int* b_env, int n, int* sv_env) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) sv_env[i] = b_env[sv_body[i]];
@@ -84,6 +110,16 @@ extern "C" zema_status zema_candidates_raw_noalloc(int64_t nsv, const double* po
         A.ff = bump_free;
         A.ctx = &bump;
         A.stream = st;
+        // the caller's index arrays, checked on the device before use
+        int* bad = (int*)A.get(sizeof(int));
+        ZCHECK(cudaMemsetAsync(bad, 0, sizeof(int), st));
+        ZL(k_noalloc_check, 148, 256, 0, st)(sv_body, (int)nsv, b_class, b_env, (int)nb, edges, (int)ne, tris,
+                                             (int)nt, bad);
+        ZLAUNCH();
+        int bad_h = 0;
+        ZCHECK(cudaMemcpyAsync(&bad_h, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+        ZCHECK(cudaStreamSynchronize(st));
+        if (bad_h) return ZEMA_ERR_INVALID_ARG;
         // sv_env from the body envs, in the fixed scratch
         int* sve = (int*)A.get(((size_t)nsv + 1) * sizeof(int));
         if (nsv) ZL(k_noalloc_sv_env, div_up(nsv, 256), 256, 0, st)(sv_body, b_env, (int)nsv, sve);
@@ -101,7 +137,7 @@ extern "C" zema_status zema_candidates_raw_noalloc(int64_t nsv, const double* po
         v.tris = (const int3*)tris;
         v.infl = inflate;
         v.inv_cell = 1.0 / cell_size;
-        static uint32_t host_counts[16];  // pageable: no pinned allocation
+        uint32_t host_counts[16];  // this call's own (pageable: no pinned allocation)
         BroadPhase bp;
         bp.h_counts = host_counts;
         zema_status status = ZEMA_OK;
@@ -115,8 +151,11 @@ extern "C" zema_status zema_candidates_raw_noalloc(int64_t nsv, const double* po
             ZCHECK(cudaStreamSynchronize(st));
         } catch (const ZemaError& e) {
             status = (zema_status)e.status;
+            // kernels queued before the failure still use the array: let them
+            // finish before another call may reuse it
+            cudaStreamSynchronize(st);
         }
-        bp.h_counts = nullptr;  // static storage: not for cudaFreeHost
+        bp.h_counts = nullptr;  // stack storage: not for cudaFreeHost
         return status;
     } catch (const ZemaError& e) {
         return (zema_status)e.status;

@@ -597,7 +597,8 @@ __global__ void __launch_bounds__(kPcgcThreads, 1) k_pcg_cluster(PcgcArgs<Real> 
     if (own_a) a.x_out[3 * (size_t)ns1 + tid] = (double)xa;
     if (rank == 0 && tid == 0) {
         a.iters[e] = it;
-        a.conv[e] = bad ? 2 : 1;  // 2: non-finite right-hand side or matrix
+        // 2: non-finite right-hand side or matrix; 3: max_iter reached first
+        a.conv[e] = bad ? 2 : (done ? 1 : 3);
     }
     cl.sync();  // no CTA leaves while a partner may still read its shared memory
 }

@@ -140,6 +140,12 @@ struct zema_scene {
     Geo G{};
     // stats of the current call
     zema_step_stats S{};
+    // host-side fault injection (zema_inject_fault): kind, the Newton
+    // iteration of the call it fires at, the call's Newton iteration count,
+    // the kind armed for the current iteration, and the device flag / status
+    // word the injection kernels read and write
+    int fault_kind = 0, fault_at = 0, newton_count = 0, fault_armed = 0;
+    DBuf<int> fault_dev;
     // per-step scratch
     DBuf<double> dirw, lam_save;
     std::vector<double> dmin_last;
@@ -183,6 +189,23 @@ void up(zema_scene* s, DBuf<T>& d, const std::vector<T>& h) {
 double now_ms() {
     using namespace std::chrono;
     return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+// ---------------------------------------------------------------------------
+// Host-side fault injection (zema_inject_fault).  The host arms a device flag
+// for one Newton iteration; these kernels read it and report a failure
+// through the same status words the real failures use.  Nothing is made to
+// fault, trap or hang.
+// ---------------------------------------------------------------------------
+// the status word flag[1] of an armed flag[0]: ZEMA_ERR_FAULT_INJECTED
+__global__ void k_fault_status_word(int* flag) {
+    if (threadIdx.x == 0 && flag[0]) flag[1] = ZEMA_ERR_FAULT_INJECTED;
+}
+// an armed flag marks every env's linear solve as having met a non-finite
+// value (the solve kernels' own conv code 2)
+__global__ void k_fault_solve_status(const int* flag, int* conv, int n_envs) {
+    if (!flag[0]) return;
+    for (int e = threadIdx.x; e < n_envs; e += blockDim.x) conv[e] = 2;
 }
 
 // ---------------------------------------------------------------------------
@@ -1485,6 +1508,8 @@ int64_t pcg_t(zema_scene* s, const std::vector<int>& done_h) {
         ZCHECK(cudaStreamSynchronize(st));
         for (int e = 0; e < NE; ++e) {
             if (s->hi[NE + e] == 2) fail(ZEMA_ERR_NONFINITE, "non-finite value in the linear solve");
+            if (s->hi[NE + e] == 3)
+                fail(ZEMA_ERR_PCG_MAXITER, "linear solve reached max_pcg iterations without meeting its tolerance");
             tot += s->hi[e];
             mx = std::max<int64_t>(mx, s->hi[e]);
         }
@@ -1611,6 +1636,10 @@ int64_t pcg_t(zema_scene* s, const std::vector<int>& done_h) {
             launch_cluster(rhs, xo, s->pcgc_cs[pi], tol2_env);
         else
             launch_grid(rhs, xo, tol2_env);
+        if (s->fault_armed == ZEMA_FAULT_SOLVE_NONFINITE) {
+            ZL(k_fault_solve_status, 1, 128, 0, st)(s->fault_dev.p, s->conv.p, NE);
+            ZLAUNCH();
+        }
         collect();
     };
     run_solve(s->b.p, s->p.p);
@@ -1694,8 +1723,15 @@ void step_norm(zema_scene* s) {
     ZL(k_step_norm, red_grid(NE), kRedThreads, 0, st)(s->G, s->p.p, s->part7.p);
     ZL(k_max_total, div_up(NE, 64), 64, 0, st)(s->part7.p, NE, s->E.p);
     ZLAUNCH();
+    const bool probe = s->fault_armed == ZEMA_FAULT_STATUS;
+    if (probe) {
+        ZL(k_fault_status_word, 1, 32, 0, st)(s->fault_dev.p);
+        ZLAUNCH();
+        ZCHECK(cudaMemcpyAsync(s->hi, s->fault_dev.p + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+    }
     ZCHECK(cudaMemcpyAsync(s->hd, s->E.p, NE * sizeof(double), cudaMemcpyDeviceToHost, st));
     ZCHECK(cudaStreamSynchronize(st));
+    if (probe && s->hi[0] != 0) fail(s->hi[0], "fault injected by zema_inject_fault");
 }
 
 // Line search along direction dir from x (Newton step or warm-start
@@ -1755,6 +1791,8 @@ int line_search(zema_scene* s, const double* dir, const std::vector<int>& done_h
         ZL(k_axpy_env, div_up(s->n_nodes, TB), TB, 0, st)(G, s->x.p, dir, s->alpha.p, s->xtrial.p);
         ZLAUNCH();
         energy(s, s->xtrial.p, s->swept.p, s->swept_env.p);
+        if (!warm && s->fault_armed == ZEMA_FAULT_NO_DECREASE)
+            for (int e = 0; e < NE; ++e) s->hd[e] = INFINITY;  // every trial point rejected
         bool all = true;
         for (int e = 0; e < NE; ++e) {
             if (acc[e]) continue;
@@ -2025,6 +2063,15 @@ void do_step(zema_scene* s) {
                 double tb = now_ms();
                 s->S.ms_phase[0] += tb - ta;
                 grad_hess(s);
+                // fault injection: armed for this iteration only (one shot)
+                s->fault_armed = 0;
+                if (s->fault_kind && s->newton_count == s->fault_at) {
+                    s->fault_armed = s->fault_kind;
+                    s->fault_kind = 0;
+                    const int on[2] = {1, 0};
+                    ZCHECK(cudaMemcpyAsync(s->fault_dev.p, on, 2 * sizeof(int), cudaMemcpyHostToDevice, st));
+                }
+                ++s->newton_count;
                 ZCHECK(cudaStreamSynchronize(st));
                 double tc = now_ms();
                 s->S.ms_phase[2] += tc - tb;
@@ -2418,6 +2465,7 @@ zema_status zema_step(zema_scene* s, int32_t n_steps, zema_step_stats* stats) {
     }
     std::memset(&s->S, 0, sizeof(s->S));
     s->S.dmin = INFINITY;
+    s->newton_count = 0;
     zema_status status = ZEMA_OK;
     for (int k = 0; k < n_steps; ++k) {
         try {
@@ -2425,10 +2473,12 @@ zema_status zema_step(zema_scene* s, int32_t n_steps, zema_step_stats* stats) {
         } catch (const ZemaError& e) {
             s->err = e.msg;
             status = (zema_status)e.status;
+            s->fault_armed = 0;
             restore_step(s);
             break;
         }
     }
+    s->fault_armed = 0;
     if (stats) *stats = s->S;
     return status;
 }
@@ -2600,6 +2650,128 @@ zema_status zema_set_kappa(zema_scene* s, int32_t env, double kappa, double kapp
         ZCHECK(cudaMemcpyAsync(s->kappa_min.p + env, &kappa_min, sizeof(double), cudaMemcpyHostToDevice, s->st));
         ZCHECK(cudaStreamSynchronize(s->st));
         s->kappa_ready[env] = 1;
+        return ZEMA_OK;
+    }
+    ZEMA_CATCH(s)
+}
+
+// Whole-scene checkpoint: every quantity that carries over from one time
+// step to the next (Eq. 11 state, kinematic targets and augmented-Lagrangian
+// multipliers of Eq. 13, the per-env barrier stiffness and the d_min of the
+// stiffness rule).  Layout: 8 uint64 header words (magic, version, nodes,
+// affine bodies, joints, envs, first step done, 0), then doubles: x and v (3
+// per node), q~ and lambda_A (12 per affine body), lambda of the joints (12
+// each), kappa, kappa_min, last d_min and kappa-set flag (one per env).
+constexpr uint64_t kCkptMagic = 0x31504B43414D455Aull;  // "ZEMACKP1"
+
+size_t ckpt_doubles(const zema_scene* s) {
+    return 6 * (size_t)s->n_nodes + 24 * (size_t)s->n_aff + 12 * (size_t)s->G.n_joints + 4 * (size_t)s->n_envs;
+}
+
+zema_status zema_checkpoint_size(const zema_scene* s, int64_t* bytes) {
+    if (!s || !bytes) return ZEMA_ERR_INVALID_ARG;
+    if (!s->finalized) return ZEMA_ERR_STATE;
+    *bytes = (int64_t)(8 * sizeof(uint64_t) + ckpt_doubles(s) * sizeof(double));
+    return ZEMA_OK;
+}
+
+zema_status zema_save_checkpoint(const zema_scene* cs, void* buf, int64_t cap, int64_t* written) {
+    zema_scene* s = const_cast<zema_scene*>(cs);
+    if (!s || !buf) return ZEMA_ERR_INVALID_ARG;
+    if (!s->finalized) return ZEMA_ERR_STATE;
+    const size_t nd = ckpt_doubles(s), bytes = 8 * sizeof(uint64_t) + nd * sizeof(double);
+    if (cap < (int64_t)bytes) return ZEMA_ERR_INVALID_ARG;
+    ZEMA_TRY(s) {
+        uint64_t* h = (uint64_t*)buf;
+        const int NE = s->n_envs, NA = s->n_aff, NJ = s->G.n_joints;
+        const size_t n3 = 3 * (size_t)s->n_nodes;
+        h[0] = kCkptMagic;
+        h[1] = 1;
+        h[2] = (uint64_t)s->n_nodes;
+        h[3] = (uint64_t)NA;
+        h[4] = (uint64_t)NJ;
+        h[5] = (uint64_t)NE;
+        h[6] = s->first_step_done ? 1 : 0;
+        h[7] = 0;
+        double* d = (double*)(h + 8);
+        cudaStream_t st = s->st;
+        ZCHECK(cudaMemcpyAsync(d, s->x.p, n3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        ZCHECK(cudaMemcpyAsync(d + n3, s->v.p, n3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        d += 2 * n3;
+        if (NA) {
+            ZCHECK(cudaMemcpyAsync(d, s->qtarget.p, 12 * (size_t)NA * sizeof(double), cudaMemcpyDeviceToHost, st));
+            ZCHECK(cudaMemcpyAsync(d + 12 * (size_t)NA, s->lamA.p, 12 * (size_t)NA * sizeof(double),
+                                   cudaMemcpyDeviceToHost, st));
+        }
+        d += 24 * (size_t)NA;
+        if (NJ) ZCHECK(cudaMemcpyAsync(d, s->lamJ.p, 12 * (size_t)NJ * sizeof(double), cudaMemcpyDeviceToHost, st));
+        d += 12 * (size_t)NJ;
+        ZCHECK(cudaMemcpyAsync(d, s->kappa.p, NE * sizeof(double), cudaMemcpyDeviceToHost, st));
+        ZCHECK(cudaMemcpyAsync(d + NE, s->kappa_min.p, NE * sizeof(double), cudaMemcpyDeviceToHost, st));
+        ZCHECK(cudaStreamSynchronize(st));
+        for (int e = 0; e < NE; ++e) {
+            d[2 * NE + e] = e < (int)s->dmin_last.size() ? s->dmin_last[e] : INFINITY;
+            d[3 * NE + e] = s->kappa_ready[e] ? 1.0 : 0.0;
+        }
+        if (written) *written = (int64_t)bytes;
+        return ZEMA_OK;
+    }
+    ZEMA_CATCH(s)
+}
+
+zema_status zema_load_checkpoint(zema_scene* s, const void* buf, int64_t bytes) {
+    if (!s || !buf || bytes < (int64_t)(8 * sizeof(uint64_t))) return ZEMA_ERR_INVALID_ARG;
+    if (!s->finalized) {
+        zema_status r = zema_finalize(s);
+        if (r != ZEMA_OK) return r;
+    }
+    const uint64_t* h = (const uint64_t*)buf;
+    const int NE = s->n_envs, NA = s->n_aff, NJ = s->G.n_joints;
+    if (h[0] != kCkptMagic || h[1] != 1 || h[2] != (uint64_t)s->n_nodes || h[3] != (uint64_t)NA ||
+        h[4] != (uint64_t)NJ || h[5] != (uint64_t)NE)
+        return ZEMA_ERR_INVALID_ARG;
+    if (bytes != (int64_t)(8 * sizeof(uint64_t) + ckpt_doubles(s) * sizeof(double))) return ZEMA_ERR_INVALID_ARG;
+    const double* d = (const double*)(h + 8);
+    const size_t n3 = 3 * (size_t)s->n_nodes;
+    for (size_t i = 0; i < 2 * n3; ++i)
+        if (!std::isfinite(d[i])) return ZEMA_ERR_INVALID_ARG;
+    for (int e = 0; e < NE; ++e) {
+        const double* k = d + 2 * n3 + 24 * (size_t)NA + 12 * (size_t)NJ;
+        if (!(k[e] >= 0.0 && k[e] < INFINITY) || !(k[NE + e] >= 0.0 && k[NE + e] < INFINITY))
+            return ZEMA_ERR_INVALID_ARG;
+    }
+    ZEMA_TRY(s) {
+        cudaStream_t st = s->st;
+        ZCHECK(cudaMemcpyAsync(s->x.p, d, n3 * sizeof(double), cudaMemcpyHostToDevice, st));
+        ZCHECK(cudaMemcpyAsync(s->v.p, d + n3, n3 * sizeof(double), cudaMemcpyHostToDevice, st));
+        d += 2 * n3;
+        if (NA) {
+            ZCHECK(cudaMemcpyAsync(s->qtarget.p, d, 12 * (size_t)NA * sizeof(double), cudaMemcpyHostToDevice, st));
+            ZCHECK(cudaMemcpyAsync(s->lamA.p, d + 12 * (size_t)NA, 12 * (size_t)NA * sizeof(double),
+                                   cudaMemcpyHostToDevice, st));
+        }
+        d += 24 * (size_t)NA;
+        if (NJ) ZCHECK(cudaMemcpyAsync(s->lamJ.p, d, 12 * (size_t)NJ * sizeof(double), cudaMemcpyHostToDevice, st));
+        d += 12 * (size_t)NJ;
+        ZCHECK(cudaMemcpyAsync(s->kappa.p, d, NE * sizeof(double), cudaMemcpyHostToDevice, st));
+        ZCHECK(cudaMemcpyAsync(s->kappa_min.p, d + NE, NE * sizeof(double), cudaMemcpyHostToDevice, st));
+        ZCHECK(cudaStreamSynchronize(st));
+        s->first_step_done = h[6] != 0;
+        s->dmin_last.assign(d + 2 * NE, d + 3 * NE);
+        for (int e = 0; e < NE; ++e) s->kappa_ready[e] = d[3 * NE + e] != 0.0 ? 1 : 0;
+        return ZEMA_OK;
+    }
+    ZEMA_CATCH(s)
+}
+
+zema_status zema_inject_fault(zema_scene* s, int32_t kind, int32_t newton_iter) {
+    if (!s || kind < ZEMA_FAULT_NONE || kind > ZEMA_FAULT_NO_DECREASE || newton_iter < 0) return ZEMA_ERR_INVALID_ARG;
+    ZEMA_TRY(s) {
+        s->fault_dev.ensure(&s->A, 2);
+        ZCHECK(cudaMemsetAsync(s->fault_dev.p, 0, 2 * sizeof(int), s->st));
+        ZCHECK(cudaStreamSynchronize(s->st));
+        s->fault_kind = kind;
+        s->fault_at = newton_iter;
         return ZEMA_OK;
     }
     ZEMA_CATCH(s)

@@ -110,6 +110,10 @@ def lib():
     FP = C.POINTER(C.c_float)
     L.zema_load_warmstart.argtypes = [C.c_void_p, C.c_void_p, C.c_int64]
     L.zema_autotune.argtypes = [C.c_void_p]
+    L.zema_checkpoint_size.argtypes = [C.c_void_p, LP]
+    L.zema_save_checkpoint.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, LP]
+    L.zema_load_checkpoint.argtypes = [C.c_void_p, C.c_void_p, C.c_int64]
+    L.zema_inject_fault.argtypes = [C.c_void_p, C.c_int32, C.c_int32]
     L.zema_get_tuning.argtypes = [C.c_void_p, C.c_int32, IP, IP, FP, C.c_int32, IP]
     L.zema_record_warmstart.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]
     L.zema_record_warmstart_affine.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]
@@ -372,6 +376,29 @@ class Scene:
         _check(lib().zema_step(self.h, n, C.byref(st)), self.h)
         self.step_index += n
         return st.as_dict()
+
+    def save_checkpoint(self) -> tuple:
+        """(checkpoint bytes, script step index): the whole scene's
+        step-to-step state (zema_save_checkpoint)."""
+        n = C.c_int64()
+        _check(lib().zema_checkpoint_size(self.h, C.byref(n)), self.h)
+        buf = np.zeros(n.value, dtype=np.uint8)
+        w = C.c_int64()
+        _check(lib().zema_save_checkpoint(self.h, buf.ctypes.data_as(C.c_void_p), n.value, C.byref(w)), self.h)
+        return buf, self.step_index
+
+    def load_checkpoint(self, ckpt):
+        """Restore a (bytes, step index) pair of save_checkpoint, from this
+        scene or one built from the same bodies (either precision)."""
+        buf, step_index = ckpt
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        _check(lib().zema_load_checkpoint(self.h, buf.ctypes.data_as(C.c_void_p), buf.nbytes), self.h)
+        self.step_index = step_index
+
+    def inject_fault(self, kind: int, newton_iter: int = 0):
+        """Arm one failure of the next step call (zema_inject_fault): 1 status
+        word, 2 non-finite solve, 3 no line-search decrease; 0 disarms."""
+        _check(lib().zema_inject_fault(self.h, int(kind), int(newton_iter)), self.h)
 
     def get_state(self, body):
         cap = 1 << 24

@@ -1,12 +1,18 @@
 """The allocation-free broad phase against the allocating one.
 
 zema_candidates_raw_noalloc exists for callers that cannot allocate device
-memory while they query contacts (inside a CUDA stream capture, with a device
-memory pool fixed in advance, or in a loop that must not call an allocator).
-It keeps all scratch in one fixed device array.  Here it must return exactly
-the pairs, in exactly the order, that zema_candidates_raw returns for the
-same inputs, on two calls in a row (the second reuses the array the first
-left behind).  This file is collected last on purpose.
+memory while they query contacts (with a device memory pool fixed in
+advance, or in a loop that must not call an allocator).  It keeps all
+scratch in one fixed device array.  Here it must return exactly the pairs,
+in exactly the order, that zema_candidates_raw returns for the same inputs,
+on two calls in a row (the second reuses the array the first left behind);
+report ZEMA_ERR_OOM when a query does not fit the array and
+ZEMA_ERR_INVALID_ARG for bad device index arrays, both without touching the
+outputs, and work normally afterwards.
+
+The file name sorts last so that, in a run that stops at the first failure,
+a failure here comes after every other GPU test has run.  Nothing here
+depends on that order: each test also passes alone in a fresh process.
 """
 import numpy as np
 import pytest
@@ -78,3 +84,62 @@ def test_noalloc_rejects_oversized_input():
     with pytest.raises(Z.ZemaError) as ei:
         Z.candidates_raw_noalloc(pos, z(n), z(1), z(1), z(0, 2), z(0, 3), 0.01, 0.05, z(16, 2), z(16, 2))
     assert ei.value.status == 1
+
+
+def test_noalloc_out_of_memory_then_normal():
+    # 4,000 vertices and triangles of one soft body packed into a 1 mm cube
+    # with a 1 cm inflation: every point-triangle and edge-edge pair
+    # overlaps, about 1e8 pairs, far beyond the fixed 64 MiB array
+    import torch
+
+    from paper_2311_05945_b300 import zema as Z
+    rng = np.random.default_rng(7)
+    n = 4000
+    P = 1e-3 * rng.random((n, 3))
+    T = np.stack([rng.permutation(n)[:3] for _ in range(n)]).astype(np.int32)
+    E = np.unique(np.sort(np.concatenate([T[:, [0, 1]], T[:, [1, 2]], T[:, [2, 0]]]), axis=1), axis=0)
+    E = E[:20000].astype(np.int32)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    svb = np.zeros(n, dtype=np.int32)
+    bc, be = np.zeros(1, dtype=np.int32), np.zeros(1, dtype=np.int32)
+    cap = 1 << 10
+    pt = torch.full((cap, 2), -1, dtype=torch.int32, device="cuda")
+    ee = torch.full((cap, 2), -1, dtype=torch.int32, device="cuda")
+    with pytest.raises(Z.ZemaError) as ei:
+        Z.candidates_raw_noalloc(dev(P), dev(svb), dev(bc), dev(be), dev(E), dev(T), 0.01, 0.05, pt, ee)
+    assert ei.value.status == 2
+    assert bool((pt == -1).all()) and bool((ee == -1).all())
+    # the array is usable again at once
+    cell, infl, cap = 0.04, 0.01, 1 << 16
+    P, svb, bc, be, E, T = surface(33)
+    pt_ref, ee_ref = Z.candidates_raw(P, svb, bc, be, E, T, infl, cell_size=cell)
+    pt = torch.full((cap, 2), -1, dtype=torch.int32, device="cuda")
+    ee = torch.full((cap, 2), -1, dtype=torch.int32, device="cuda")
+    npt, nee = Z.candidates_raw_noalloc(dev(P), dev(svb), dev(bc), dev(be), dev(E), dev(T), infl, cell, pt, ee)
+    assert (npt, nee) == (len(pt_ref), len(ee_ref))
+    assert np.array_equal(pt[:npt].cpu().numpy(), pt_ref)
+    assert np.array_equal(ee[:nee].cpu().numpy(), ee_ref)
+
+
+@pytest.mark.parametrize("field", ["body", "edge", "tri", "class"])
+def test_noalloc_rejects_bad_device_indices(field):
+    import torch
+
+    from paper_2311_05945_b300 import zema as Z
+    P, svb, bc, be, E, T = surface(34)
+    svb, E, T, bc = svb.copy(), E.copy(), T.copy(), bc.copy()
+    if field == "body":
+        svb[5] = len(bc)          # one past the last body
+    elif field == "edge":
+        E[3, 1] = len(P)          # one past the last vertex
+    elif field == "tri":
+        T[2, 0] = -1
+    else:
+        bc[0] = 4
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    pt = torch.full((64, 2), -1, dtype=torch.int32, device="cuda")
+    ee = torch.full((64, 2), -1, dtype=torch.int32, device="cuda")
+    with pytest.raises(Z.ZemaError) as ei:
+        Z.candidates_raw_noalloc(dev(P), dev(svb), dev(bc), dev(be), dev(E), dev(T), 0.01, 0.04, pt, ee)
+    assert ei.value.status == 1
+    assert bool((pt == -1).all()) and bool((ee == -1).all())
