@@ -1,26 +1,36 @@
 #!/usr/bin/env python3
 """Benchmark: IPC time steps per second of the soft-rigid coupled IPC stepper.
 
-Workload: the parallel-jaw grasp scene (seeded synthetic stand-in for the
-paper's grasp objects): a jittered Kuhn-lattice soft ellipsoid (semi-axes
-4/2/3 cm, 9,600 tets, Neo-Hookean E = 5e4 Pa, nu = 0.45) on a fixed floor,
-squeezed and lifted by two kinematic affine box fingers (972 triangles each),
-mu = 0.8, dt = 0.005 s, Newton tolerance 1e-3 x bbox diagonal x dt.  A "step"
-is one full time step of the method (predictor, lagged friction, warm start,
-projected Newton with broad phase, distances, PSD Hessians, assembly, PCG,
-ACCD line search, velocity update).  Timed steps are steps [W, W + K) of the
-grasp script after W warm-up steps.
+Default workload: the batched parallel-jaw grasp, 256 environments per GPU in
+one scene (seeded synthetic stand-ins for the paper's grasp objects: soft
+ellipsoids, tori and boxes of 2k-20k tets, log-uniform, E log-uniform in
+[1e4, 1e6] Pa, mu in [0.3, 1.0], nu = 0.45), each squeezed by two kinematic
+affine box fingers (972 triangles each) on a fixed floor, dt = 0.005 s,
+Newton tolerance 1e-3 x bbox diagonal x dt.  A "step" is one full time step
+of the method over every environment (predictor, lagged friction, warm
+start, projected Newton with broad phase, distances, PSD Hessians, assembly,
+PCG, ACCD line search, velocity update); the unit is env-steps/s.
+
+Timed window: steps [S0, S0 + K) of the grasp script with S0 = max(20, W):
+the fingers start 0.5 cm off the object and close at 0.25 mm per step, so
+from step 20 on both fingers and the floor are in contact.  The first S0
+steps run untimed (the last W of them are the warm-up); the state at S0 is
+checkpointed and every form below is timed from that same state:
+
+  headline   mixed precision, all envs batched, learned warm start
+  cv         mixed precision, all envs batched, constant-velocity warm start
+  plain      plain FP64, all envs batched, constant-velocity warm start
+  sequential plain FP64 with the envs stepped one at a time (a strided
+             sample of the batch, each env positioned by itself)
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                [--workload c2|c3|c5]
+                [--workload c3|c2|c5] [--envs E]
 
---workload c3 times the batched grasp (env-steps/s); --workload c5 the dense
+--workload c2 times the single-env grasp (steps/s), --workload c5 the dense
 soft-rigid pile (8 soft bodies of ~60k tets, 20 affine spheres and tori, a
-fixed bin), one scene too large for a cluster solve.
-
-One JSON line on rank 0.  Under torchrun each rank steps its own replica of
-the workload (environments are independent: weak scaling, no collective in
-the step); the slowest rank's time is used.
+fixed bin; one scene).  One JSON line on rank 0.  Under torchrun each rank
+steps its own batch of E envs (seeds 1000 + E r + i: weak scaling, no
+collective in the step); the slowest rank's time is used.
 """
 import argparse
 import json
@@ -35,16 +45,16 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "IPC time steps/sec at fixed Newton tol, batched+warm-start vs plain, one B300"
-UNIT = "steps/s"
-WORKLOAD = "parallel-jaw grasp, 1 env: soft ellipsoid 9600 tets + 2 kinematic affine fingers (972 tris each) + fixed floor"
-ROOFLINE_KERNEL = "k_pcg_cluster"
+C2_WORKLOAD = "parallel-jaw grasp, 1 env: soft ellipsoid 9600 tets + 2 kinematic affine fingers (972 tris each) + fixed floor"
 # the grid-wide solve of the scenes too large for one cluster
 ROOFLINE_KERNEL_BY_WORKLOAD = {"c2": "k_pcg_cluster", "c3": "k_pcg_cluster", "c5": "k_pcg_persistent"}
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
-# ROOFLINE_KERNEL per workload, from an ncu capture: c2, the first solve of
-# grasp step 20 (751.9 us, near the bench's 705 us average launch); None where
-# no capture was taken or once the kernel changes.
-ROOFLINE_TRAFFIC = {"c2": 1384448 + 8448, "c3": None, "c5": None}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
+# roofline kernel, from an ncu capture of the kernel as it stands; None where
+# no capture was taken since the kernel last changed.
+ROOFLINE_TRAFFIC = {"c2": None, "c3": None, "c5": None}
+# first step of the grasp script with both fingers on the object
+CONTACT_STEP = {"c2": 20, "c3": 20, "c5": 13}
+WEIGHTS = os.path.join(ROOT, "paper_2311_05945_b300", "weights")
 
 
 def measured_peaks():
@@ -105,146 +115,196 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def build_scene(args=None, rank=0, world=1):
-    """The rank's scene: the single-env grasp, or its share of the batched
-    grasp (contiguous env range balanced by tet count; env i keeps seed
-    1000 + i whatever the sharding)."""
+def window(args):
+    """First timed step of the grasp script: the contact window's start, or
+    later when more warm-up steps are asked for."""
+    return max(CONTACT_STEP[args.workload], args.warmup)
+
+
+def build_scene(args, rank=0, world=1):
+    """The rank's scene: the single-env grasp, the pile, or the rank's batch
+    of args.envs grasp envs (seeds 1000 + args.envs * rank + i)."""
     from paper_2311_05945_b300 import scenes
-    if args is None or args.workload == "c2":
-        return scenes.scene_c2()
+    n_steps = window(args) + args.steps + 1
+    if args.workload == "c2":
+        return scenes.scene_c2(n_steps=n_steps)
     if args.workload == "c5":
-        # one scene: every rank steps its own replica
-        return scenes.scene_c5(n_steps=args.warmup + args.steps, tets_per_body=args.c5_tets)
-    from paper_2311_05945_b300.sharding import shard_envs
-    full = scenes.scene_c3(n_envs=args.envs, n_steps=args.warmup + args.steps)
-    w = [0] * args.envs
-    for b in full.tets:
+        return scenes.scene_c5(n_steps=n_steps, tets_per_body=args.c5_tets)
+    return scenes.scene_c3(n_envs=args.envs, n_steps=n_steps, seed0=1000 + args.envs * rank)
+
+
+def env_tets(sc):
+    w = [0] * sc.n_envs
+    for b in sc.tets:
         w[b.env] += len(b.tets)
-    a, b = shard_envs(w, world)[rank]
-    return scenes.scene_c3(n_envs=b - a, n_steps=args.warmup + args.steps, seed0=1000 + a)
+    return w
 
 
-def oracle_steps_per_s(n_warm, n_steps, sc=None):
-    """The CPU oracle, as it stands, on the same workload (single core)."""
-    from oracle.oracle import Oracle
-    sc = build_scene() if sc is None else sc
-    o = Oracle(sc)
-    if n_warm:
-        o.step(n_warm)
-    t0 = time.perf_counter()
-    o.step(n_steps)
-    dt = time.perf_counter() - t0
-    return n_steps / dt, dt
-
-
-def workload_name(args, sc, envs_per_rank):
+def workload_name(args, sc):
     """The config's workload string (the same for both arms)."""
     if args.workload == "c2":
-        return WORKLOAD
+        return C2_WORKLOAD
     if args.workload == "c5":
         return (f"dense soft-rigid pile: {sum(len(b.tets) for b in sc.tets)} tets in {len(sc.tets)} soft bodies "
                 f"+ {sum(1 for a in sc.affines if a.mode == 0)} affine spheres/tori "
                 f"({max(len(a.F) for a in sc.affines)} tris max) in a fixed 5-box bin, one scene")
-    return (f"batched parallel-jaw grasp, {args.envs} envs (ellipsoid/torus/box, 2k-20k tets log-uniform, "
-            f"E 1e4-1e6, mu 0.3-1.0), one launch per phase over all envs; {envs_per_rank} envs per rank")
+    return (f"batched parallel-jaw grasp, {args.envs} envs per GPU (ellipsoid/torus/box, 2k-20k tets log-uniform, "
+            f"{sum(env_tets(sc))} tets on rank 0, E 1e4-1e6, mu 0.3-1.0), all envs in one launch per kernel")
 
 
-def oracle_sample(args, n_warm, n_steps):
-    """Time the CPU oracle, as it stands, on a bounded sample of the workload:
-    returns (value in the workload's unit, seconds, description)."""
+def unit_of(args):
+    return "env-steps/s" if args.workload == "c3" else "steps/s"
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+def oracle_scene(args, sc):
+    """(scene, description) of the oracle's sample: for the batched grasp the
+    env of the batch whose tet count is closest to the batch mean, on its
+    own; the single-env grasp itself; for the pile the same generator at 300
+    tets per body (the oracle's all-pairs search cannot step the full pile
+    in bounded time)."""
     from paper_2311_05945_b300 import scenes
-    if args.workload == "c5":
-        # the oracle's brute-force pair search is quadratic in the surface
-        # size: one step of the full pile does not fit the sample bound, so
-        # the sample is the same pile generator at 300 tets per body
-        small = scenes.scene_c5(n_steps=2, tets_per_body=300, n_seg=8, bin_subdiv=1)
-        v, dt = oracle_steps_per_s(0, 1, small)
-        return v, dt, (f"step 0 of the same pile generator at 300 tets per body, 8 x 8 affine meshes, unsplit "
-                       f"bin faces, on the CPU oracle ({dt:.1f} s)")
+    n_steps = window(args) + args.steps + 1
     if args.workload == "c3":
-        v, dt = oracle_steps_per_s(0, 1, scenes.scene_c3(n_envs=1, n_steps=2))
-        return v, dt, f"env 0 of the batch (seed 1000), step 0, on the CPU oracle ({dt:.1f} s)"
-    v, dt = oracle_steps_per_s(n_warm, n_steps)
-    return v, dt, (f"grasp steps [{n_warm}, {n_warm + n_steps}) of the same script on the CPU oracle "
-                   f"({dt:.1f} s)")
+        w = env_tets(sc)
+        mean = sum(w) / len(w)
+        k = min(range(len(w)), key=lambda i: abs(w[i] - mean))
+        return (scenes.scene_c3(n_envs=1, n_steps=n_steps, seed0=1000 + k),
+                f"env {k} of the batch (seed {1000 + k}, {w[k]} tets, the batch mean is {mean:.0f})")
+    if args.workload == "c5":
+        return (scenes.scene_c5(n_steps=4, tets_per_body=300, n_seg=8, bin_subdiv=1),
+                "the same pile generator at 300 tets per body, 8 x 8 affine meshes, unsplit bin faces")
+    return scenes.scene_c2(n_steps=n_steps), "the grasp itself"
+
+
+def oracle_rate(args, sc, n_time, threads):
+    """The CPU oracle, as it stands, on the window of the GPU arm: positioned
+    untimed to the window's first step (all host threads; the OpenMP build
+    is bit-identical to the serial one), then n_time steps timed with
+    `threads` threads.  Returns (rate in the workload's unit, seconds,
+    sample description)."""
+    from oracle import oracle as O
+    osc, desc = oracle_scene(args, sc)
+    s0 = 0 if args.workload == "c5" else window(args)
+    nproc = os.cpu_count() or 1
+    O.set_threads(nproc)
+    o = O.Oracle(osc)
+    if s0:
+        o.step(s0)
+    O.set_threads(threads)
+    t0 = time.perf_counter()
+    o.step(n_time)
+    dt = time.perf_counter() - t0
+    O.set_threads(1)
+    where = "its first steps" if args.workload == "c5" else f"steps [{s0}, {s0 + n_time})"
+    return n_time / dt, dt, f"{desc}: {where} of the same script on the CPU oracle, {threads} thread(s) ({dt:.1f} s)"
 
 
 def run_reference(args, rank):
     if rank != 0:
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
-    # the GPU arm times steps [W, W + K) of the grasp script: step the oracle
-    # untimed to W (capped so that the run stays within a few minutes), then
-    # time up to 3 steps of the same window
-    n_warm = min(args.warmup, 40)
-    n_steps = max(1, min(args.steps, 3))
-    unit = "env-steps/s" if args.workload == "c3" else UNIT
-    sc = None if args.workload == "c2" else build_scene(args, 0, world)
-    name = workload_name(args, sc, sc.n_envs if sc is not None else 1)
-    v, dt, sample = oracle_sample(args, n_warm, n_steps)
+    n_time = max(1, min(args.steps, 3))
+    sc = build_scene(args, 0, world)
+    cores = os.cpu_count() or 1
+    v, dt, sample = oracle_rate(args, sc, n_time, cores)
+    unit = unit_of(args)
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": unit, "n_gpus": args.gpus,
-        "steps": n_steps if args.workload == "c2" else 1, "warmup": n_warm if args.workload == "c2" else 0,
+        "steps": n_time, "warmup": window(args) if args.workload != "c5" else 0,
         "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic (seeded generators)",
-        "config": {"workload": name, "form": "CPU oracle: serial FP64, brute-force pairs, direct/CG solve"},
-        "cpu_baseline": {"value": v, "unit": unit, "cores": 1, "kind": "oracle", "sample": sample},
+        "config": {"workload": workload_name(args, sc),
+                   "form": "CPU oracle: FP64, brute-force pairs, direct/CG solve, OpenMP over independent loops "
+                           "(bit-identical to serial)"},
+        "cpu_baseline": {"value": v, "unit": unit, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
 def state_bytes(sc):
     return sum(8 * 6 * len(b.X) for b in sc.tets) + 8 * 24 * len(sc.affines)
 
 
-def time_form(args, world, dist, precision, profile_kernel=None):
-    """W warm-up steps, then K timed steps of the grasp script in one form."""
+def load_weights(g):
+    """Load every trained warm-start network that applies to the scene."""
+    from paper_2311_05945_b300 import zema as Z
+    n = 0
+    for name in ("warmstart.bin", "warmstart_affine.bin"):
+        path = os.path.join(WEIGHTS, name)
+        if os.path.exists(path):
+            dims, theta = Z.read_warmstart_blob(open(path, "rb").read())
+            g.load_warmstart(dims, theta)
+            n += 1
+    return n
+
+
+class Form:
+    """The statistics and time of one timed form."""
+
+    def __init__(self, name, ms, stats, units, steps):
+        self.name, self.ms, self.stats = name, ms, stats
+        self.value = units * steps / (ms / 1e3)
+
+    def summary(self):
+        agg = {k: sum(s[k] for s in self.stats) for k in ("newton_iters", "pcg_iters", "ls_halvings", "al_rounds",
+                                                           "pcg_refines", "warm_accepted", "warm_learned",
+                                                           "warm_fallback")}
+        return {"value": self.value, "ms_per_step": self.ms / len(self.stats), **agg}
+
+
+def timed_steps(g, k, flush, dist=None, profile_kernel=None, profile_region=False):
+    """k steps with CUDA events on the library's stream, the L2 flushed before
+    each; returns (total ms, per-step stats, launches, profile)."""
     import torch
 
     from paper_2311_05945_b300 import zema as Z
-
-    rank = int(os.environ.get("RANK", "0"))
-    sc = build_scene(args, rank, world)
-    gpu = Z.Scene(sc, precision=precision)
+    from paper_2311_05945_b300.sharding import max_over_ranks
     st = torch.cuda.current_stream()
-    for k in range(args.warmup):
-        if k == args.warmup - 1:
-            gpu.autotune()  # the solve's CTAs per env, timed on a warm-up system
-        gpu.step(1)
-    torch.cuda.synchronize()
-    # L2 flush buffer: 512 MB, written between timed steps (L2 is 126 MB)
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float64, device="cuda")
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
     stats = []
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    if args.profile_region and profile_kernel:
+    if profile_region:
         torch.cuda.profiler.start()
     if profile_kernel:
         Z.profile_kernel(profile_kernel)
     l0 = Z.launch_count()
-    for k in range(args.steps):
+    for i in range(k):
         flush.zero_()
-        ev[k][0].record(st)
-        stats.append(gpu.step(1))
-        ev[k][1].record(st)
+        ev[i][0].record(st)
+        stats.append(g.step(1))
+        ev[i][1].record(st)
     torch.cuda.synchronize()
-    if args.profile_region and profile_kernel:
+    if profile_region:
         torch.cuda.profiler.stop()
     launches = Z.launch_count() - l0
     prof = Z.profile_read() if profile_kernel else None
     Z.profile_kernel(None)
-    total_ms = sum(a.elapsed_time(b) for a, b in ev)
-    from paper_2311_05945_b300.sharding import max_over_ranks
-    total_ms = max_over_ranks(total_ms, dist, "cuda")
-    gpu.tuned = gpu.tuning()
-    return sc, gpu, total_ms, stats, launches, prof
+    total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), dist, "cuda")
+    return total_ms, stats, launches, prof
+
+
+def sequential_sample(args, sc):
+    """Env ids of the plain sequential form: a stride over the batch."""
+    n = sc.n_envs
+    m = max(1, min(n, args.seq_envs))
+    return [int(i * n / m) for i in range(m)]
 
 
 def run_ours(args, rank, world):
     import torch
+
+    from paper_2311_05945_b300 import scenes
+    from paper_2311_05945_b300 import zema as Z
+    from paper_2311_05945_b300.sharding import max_over_ranks
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
@@ -252,43 +312,81 @@ def run_ours(args, rank, world):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    # plain FP64 stepper over the same steps (the comparison form)
-    _, _, plain_ms, plain_stats, _, _ = time_form(args, world, dist, 0)
-    # headline: mixed precision + warm start; clocks sampled while it runs
+    K, S0 = args.steps, window(args)
+    sc = build_scene(args, rank, world)
+    units = sc.n_envs if args.workload == "c3" else 1
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float64, device="cuda")  # 512 MB > L2
+    # untimed positioning to the window's first step in the mixed form (the
+    # last W steps are the warm-up; the solve's autotuner runs on the last)
+    g = Z.Scene(sc, precision=1, warm_start=1)
+    for k in range(S0):
+        if k == S0 - 1:
+            g.autotune()
+        g.step(1)
+    torch.cuda.synchronize()
+    ck = g.save_checkpoint()
+    forms = {}
+    # mixed + constant-velocity warm start (no network loaded yet)
+    ms, stats, _, _ = timed_steps(g, K, flush, dist)
+    forms["cv"] = Form("cv", ms, stats, units, K)
+    # headline: mixed + learned warm start; clocks and the roofline kernel
+    # sampled while it runs
+    g.load_checkpoint(ck)
+    n_nets = load_weights(g)
     clocks = Clocks(local)
     clocks.start()
-    sc, gpu, total_ms, stats, launches, prof = time_form(args, world, dist, 1,
-                                                         ROOFLINE_KERNEL_BY_WORKLOAD[args.workload])
+    kname = ROOFLINE_KERNEL_BY_WORKLOAD[args.workload]
+    ms, stats, launches, prof = timed_steps(g, K, flush, dist, kname, args.profile_region)
     clk = clocks.stop()
-    from paper_2311_05945_b300.sharding import max_over_ranks
-    envs_per_rank = sc.n_envs
-    units = world * envs_per_rank if args.workload == "c3" else world
-    value = units * args.steps / (total_ms / 1e3)
-    plain_value = units * args.steps / (plain_ms / 1e3)
-    # end to end through the C ABI with pinned host buffers, over the same
-    # step window [W, W + K) of a fresh scene: every timed step uploads the
-    # bodies' states from pinned host memory, steps, and reads them back
-    from paper_2311_05945_b300 import zema as Z
-    e2e_steps = args.steps if args.e2e_steps is None else max(1, min(args.steps, args.e2e_steps))
-    g2 = Z.Scene(sc, precision=1)
-    for _ in range(args.warmup):
-        g2.step(1)
+    head = Form("headline", ms, stats, units, K)
+    tuned = g.tuning()
+    # end to end through the C ABI with pinned host buffers, same window,
+    # same form: every step uploads all bodies' states, steps, reads them back
+    g.load_checkpoint(ck)
     bodies = list(range(len(sc.body_order())))
-    host = [torch.from_numpy(g2.get_state(b)).pin_memory() for b in bodies]
+    host = [torch.from_numpy(g.get_state(b)).pin_memory() for b in bodies]
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     t0 = time.perf_counter()
-    for _ in range(e2e_steps):
+    for _ in range(K):
         for b in bodies:
-            g2.set_state_ptr(b, host[b].data_ptr(), host[b].numel())
-        g2.step(1)
+            g.set_state_ptr(b, host[b].data_ptr(), host[b].numel())
+        g.step(1)
         for b in bodies:
-            g2.get_state_ptr(b, host[b].data_ptr(), host[b].numel())
+            g.get_state_ptr(b, host[b].data_ptr(), host[b].numel())
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    e2e_val = units * e2e_steps / max_over_ranks(e2e_s, dist, "cuda")
-    g2.close()
+    e2e_val = units * K / max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+    g.close()
+    # plain FP64, batched, from the same checkpoint (one untimed step for its
+    # own autotuning first)
+    gp = Z.Scene(sc, precision=0)
+    gp.load_checkpoint(ck)
+    gp.autotune()
+    gp.step(1)
+    gp.load_checkpoint(ck)
+    ms, stats, _, _ = timed_steps(gp, K, flush, dist)
+    forms["plain"] = Form("plain", ms, stats, units, K)
+    gp.close()
+    # plain FP64, envs stepped one at a time (strided sample, each env
+    # positioned by itself in FP64)
+    if args.workload == "c3" and args.seq_envs > 0:
+        ids = sequential_sample(args, sc)
+        seq_ms, seq_stats = 0.0, []
+        for i in ids:
+            one = scenes.scene_c3(n_envs=1, n_steps=S0 + K + 1, seed0=1000 + args.envs * rank + i)
+            gs = Z.Scene(one, precision=0)
+            for k in range(S0):
+                if k == S0 - 1:
+                    gs.autotune()
+                gs.step(1)
+            ms, stats, _, _ = timed_steps(gs, K, flush)
+            seq_ms += ms
+            seq_stats += stats
+            gs.close()
+        seq_ms = max_over_ranks(seq_ms, dist, "cuda")
+        seq = Form("sequential", seq_ms, seq_stats, len(ids), K)
+        forms["sequential"] = seq
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -300,40 +398,52 @@ def run_ours(args, rank, world):
     if k_launches:
         per_launch_bytes = k_bytes / k_launches
         achieved = per_launch_bytes / (k_ms / k_launches / 1e3) / 1e9
-        roof = {"kernel": ROOFLINE_KERNEL_BY_WORKLOAD[args.workload], "bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
+        roof = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
                 "frac": achieved / peak_gbs, "traffic": ROOFLINE_TRAFFIC.get(args.workload),
                 "peak_source": "measured" if peaks else "fallback",
                 "alg_bytes_per_launch": per_launch_bytes, "avg_launch_us": 1e3 * k_ms / k_launches,
-                "launches": k_launches, "share_of_step_time": k_ms / total_ms if world == 1 else None}
-    unit = "env-steps/s" if args.workload == "c3" else UNIT
+                "launches": k_launches, "share_of_step_time": k_ms / head.ms if world == 1 else None}
+    unit = unit_of(args)
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        v, dt, sample = oracle_sample(args, 0, args.cpu_steps)
-        cpu = {"value": v, "unit": unit, "cores": 1, "kind": "oracle", "sample": sample}
-    agg = {k: sum(s[k] for s in stats) for k in ("newton_iters", "pcg_iters", "ls_halvings", "al_rounds", "pcg_refines")}
-    phase = {k: sum(s["ms_phase"][k] for s in stats) for k in stats[0]["ms_phase"]}
+        cores = os.cpu_count() or 1
+        v, _, sample = oracle_rate(args, sc, args.cpu_steps, cores)
+        v1, _, sample1 = oracle_rate(args, sc, 1, 1) if args.cpu_serial else (None, None, None)
+        cpu = {"value": v, "unit": unit, "cores": cores, "kind": "oracle", "sample": sample}
+        if v1 is not None:
+            cpu["serial_1_core"] = {"value": v1, "sample": sample1}
+    phase = {k: sum(s["ms_phase"][k] for s in head.stats) for k in head.stats[0]["ms_phase"]}
+    cfg = {
+        "workload": workload_name(args, sc),
+        "timed_steps": [S0, S0 + K],
+        "form": ("mixed precision (FP32 Hessians, matrices and PCG with FP64 residual refinement; FP64 gradients, "
+                 "energies, distances, CCD and convergence) + learned warm start (trained networks: "
+                 f"{n_nets}; CCD-filtered, energy-checked, plain-Newton fallback)"
+                 + ("; all envs batched" if args.workload == "c3" else "")),
+        "headline": head.summary(),
+        "mixed_cv_warm_start": forms["cv"].summary(),
+        "plain_fp64_batched" if args.workload == "c3" else "plain_fp64": forms["plain"].summary(),
+        "speedup_vs_plain": head.value / forms["plain"].value,
+        "parallelism": (f"weak: {args.envs} envs per rank on {world} ranks" if args.workload == "c3"
+                        else f"replicas x{world}") if world > 1 else "single GPU",
+        "l2": "flushed between timed steps (512 MB write)",
+        "state": f"every form starts from the same checkpoint at step {S0}",
+        "pcg_autotune": {"ctas_per_env": tuned[0], "solve_ms_by_ctas": {str(k): round(v, 4)
+                                                                         for k, v in tuned[1].items()}},
+        "host_phase_ms": {k: round(v, 2) for k, v in phase.items()},
+    }
+    if "sequential" in forms:
+        seq = forms["sequential"]
+        cfg["plain_fp64_sequential"] = {**seq.summary(), "envs_sampled": sequential_sample(args, sc),
+                                        "how": "each sampled env alone in its own scene, positioned to the "
+                                               "window in FP64, timed over the same steps; env-steps/s over "
+                                               "the sample"}
+        cfg["speedup_vs_plain_sequential"] = head.value / seq.value
     line = {
-        "metric": METRIC, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "metric": METRIC, "value": head.value, "unit": unit, "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": head.ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "mixed f32/f64", "data": "synthetic (seeded generators)",
-        "config": {"workload": workload_name(args, sc, envs_per_rank),
-                   "timed_steps": [args.warmup, args.warmup + args.steps],
-                   "form": "mixed precision (FP32 Hessians, matrices and PCG with FP64 residual refinement; FP64 "
-                           "gradients/energies/distances/CCD/convergence) + CCD-filtered constant-velocity warm "
-                           "start" + ("; all envs batched" if args.workload == "c3" else "; 1 env so no batching"),
-                   "plain_fp64": {"value": plain_value, "ms_per_step": plain_ms / args.steps,
-                                  "newton_iters": sum(s["newton_iters"] for s in plain_stats),
-                                  "pcg_iters": sum(s["pcg_iters"] for s in plain_stats)},
-                   "speedup_vs_plain": value / plain_value,
-                   "parallelism": (f"envs sharded over {world} ranks" if args.workload == "c3" else f"replicas x{world}")
-                   if world > 1 else "single GPU",
-                   "l2": "flushed between timed steps (512 MB write)",
-                   "newton_iters": agg["newton_iters"], "pcg_iters": agg["pcg_iters"],
-                   "ls_halvings": agg["ls_halvings"], "al_rounds": agg["al_rounds"],
-                   "pcg_fp64_refinements": agg["pcg_refines"],
-                   "pcg_autotune": {"ctas_per_env": gpu.tuned[0],
-                                    "solve_ms_by_ctas": {str(k): round(v, 4) for k, v in gpu.tuned[1].items()}},
-                   "host_phase_ms": {k: round(v, 2) for k, v in phase.items()}},
+        "config": cfg,
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": unit, "h2d_bytes_per_step": state_bytes(sc),
@@ -349,17 +459,18 @@ def run_ours(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c5"],
-                    help="c2: the single-env grasp (headline); c3: the batched grasp, env-steps/s; "
+    ap.add_argument("--workload", default="c3", choices=["c2", "c3", "c5"],
+                    help="c3: the batched grasp (headline, env-steps/s); c2: the single-env grasp; "
                          "c5: the dense soft-rigid pile")
     ap.add_argument("--c5-tets", type=int, default=60000, help="tets per soft body of the pile (c5)")
-    ap.add_argument("--envs", type=int, default=256, help="envs of the batched grasp (c3)")
-    ap.add_argument("--e2e-steps", type=int, default=None,
-                    help="end-to-end steps (default: the timed steps, same window)")
+    ap.add_argument("--envs", type=int, default=256, help="envs per GPU of the batched grasp (c3)")
+    ap.add_argument("--seq-envs", type=int, default=16,
+                    help="envs of the batch sampled for the plain sequential form (c3; 0 skips it)")
     ap.add_argument("--cpu-steps", type=int, default=2)
+    ap.add_argument("--cpu-serial", action="store_true", help="also time one oracle step on 1 thread")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-region", action="store_true",
                     help="bracket the headline form's timed steps with cudaProfilerStart/Stop "
