@@ -73,3 +73,24 @@ def loss_and_grad(theta, dims, x, t, bf16=False):
             dz = _q((dz @ _q(W, bf16).T) * (zs[l - 1] > 0), bf16)
     grads.reverse()
     return loss, np.concatenate([np.concatenate([gW.ravel(), gb]) for gW, gb in grads]).astype(theta.dtype)
+
+
+def grad_abs_scale(theta, dims, x, t, bf16=False):
+    """Per gradient entry, the sum of the magnitudes of the products that make
+    it up (|h_in|^T |dz| for a weight, sum |dz| for a bias), with |dz| back
+    propagated through |W|: the scale of the entry's rounding error, since a
+    rounding change of one operand moves the entry by at most that operand's
+    relative change times this sum.  Same flat layout as the gradient."""
+    layers = unpack(theta, dims)
+    y, zs = forward(theta, dims, x, bf16)
+    n = y.size
+    dz = np.abs(_q((2.0 / n) * (y - t), bf16))
+    out = []
+    for l in range(len(layers) - 1, -1, -1):
+        W, _ = layers[l]
+        h_in = np.abs(_q(x, bf16) if l == 0 else _q(np.maximum(zs[l - 1], 0), bf16))
+        out.append((h_in.T @ dz, dz.sum(axis=0)))
+        if l > 0:
+            dz = (dz @ np.abs(_q(W, bf16)).T) * (zs[l - 1] > 0)
+    out.reverse()
+    return np.concatenate([np.concatenate([gW.ravel(), gb]) for gW, gb in out]).astype(theta.dtype)

@@ -388,6 +388,7 @@ __global__ void __launch_bounds__(EL_T) k_elastic_gh(Geo G, const double* x, T* 
     T* sm = (T*)smraw;
     int t = blockIdx.x * EL_T + threadIdx.x;
     if (t >= G.n_tets) return;
+    if (G.env_done && G.env_done[G.node_env[G.tets[t].x]]) return;
     SMat<9, T> H{sm + threadIdx.x, EL_T};
     double F[9], P[9], psi;
     int4 Tt;
@@ -445,6 +446,7 @@ __global__ void __launch_bounds__(EL_T) k_elastic_gh(Geo G, const double* x, T* 
 // soft inertia (Eq. 1) and elasticity (Eq. 1, h^2 Phi) energies per env
 __global__ void k_soft_energy(Geo G, const double* x, const double* xhat, double* part) {
     int env = blockIdx.y;
+    if (env_is_done(G, env)) return;
     int n0 = G.env_node_start[env], n1 = G.env_node_start[env + 1];
     chunk_sum(
         n0, n1,
@@ -485,6 +487,7 @@ __global__ void k_soft_grad(Geo G, const double* x, const double* xhat, const do
     if (n >= G.n_nodes) return;
     double m = G.node_mass[n];
     if (m == 0.0) return;  // affine node
+    if (env_is_done(G, G.node_env[n])) return;
     V3 d = ld3(x + 3 * (size_t)n) - ld3(xhat + 3 * (size_t)n);
     V3 s = m * d;
     if (G.spring_k && G.spring_k[n] > 0.0)
@@ -546,6 +549,7 @@ __device__ inline double affine_energy(const Geo& G, const double* x, const doub
 
 __global__ void k_affine_energy(Geo G, const double* x, const double* xhat, AffKin K, double* part) {
     int env = blockIdx.y;
+    if (env_is_done(G, env)) return;
     chunk_sum(
         G.env_aff_start[env], G.env_aff_start[env + 1],
         [&](int b) -> double { return affine_energy(G, x, xhat, K, b); }, part_slot(part, ET_AFFINE, G.n_envs, env));
@@ -564,6 +568,7 @@ __global__ void __launch_bounds__(AF_T) k_affine_gh(Geo G, const double* x, cons
     if (b >= G.n_aff) return;
     int mode = G.aff_mode[b];
     int n0 = G.aff_node0[b];
+    if (env_is_done(G, G.node_env[n0])) return;
     T* blk = stage_blk + (size_t)b * 144;
     for (int i = 0; i < 144; ++i) blk[i] = T(0);
     if (mode == 1) {
@@ -781,6 +786,7 @@ __global__ void __launch_bounds__(kWarpPairs) k_barrier_gh(Geo G, const double* 
 __global__ void k_barrier_energy(Geo G, const double* X, const PairRec* rec, const uint32_t* env_off,
                                  const double* kappa_env, double* part) {
     int env = blockIdx.y;
+    if (env_is_done(G, env)) return;
     double kap = kappa_env[env];
     chunk_sum(
         (int)env_off[env], (int)env_off[env + 1],
@@ -896,6 +902,7 @@ __device__ inline double joint_energy(const Geo& G, const double* x, int j) {
 
 __global__ void k_joint_energy(Geo G, const double* x, double* part) {
     const int env = blockIdx.y;
+    if (env_is_done(G, env)) return;
     chunk_sum(
         G.env_joint_start[env], G.env_joint_start[env + 1], [&](int j) -> double { return joint_energy(G, x, j); },
         part_slot(part, ET_JOINT, G.n_envs, env));
@@ -909,6 +916,7 @@ __global__ void k_joint_gh(Geo G, const double* x, T* stage, double* g) {
     if (blockIdx.x != 0 || threadIdx.x != 0) return;
     for (int j = 0; j < G.n_joints; ++j) {
         const JointDev J = G.joints[j];
+        if (env_is_done(G, G.node_env[J.n1])) continue;
         double c[12], Jm[12][24], w[12];
         joint_eval(J, x, c, Jm);
         for (int m = 0; m < 12; ++m) w[m] = 2.0 * J.kappa * c[m] - G.lamJ[12 * (size_t)j + m];
@@ -1020,6 +1028,7 @@ __device__ __forceinline__ V3 lag_u(const double* X, const double* Xt, const Lag
 
 __global__ void k_friction_energy(Geo G, const double* X, const double* Xt, Lag L, double* part) {
     int env = blockIdx.y;
+    if (env_is_done(G, env)) return;
     double eh = G.eps_v * G.h;
     chunk_sum(
         (int)L.env_off[env], (int)L.env_off[env + 1],
@@ -1035,6 +1044,7 @@ template <class T>
 __global__ void k_friction_gh(Geo G, const double* X, const double* Xt, Lag L, T* pH, double* pG) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= L.n_pairs) return;
+    if (env_is_done(G, G.sv_env[L.rec[i].s[0]])) return;  // k_contact_count drops the record
     double eh = G.eps_v * G.h;
     V3 u = lag_u(X, Xt, L, i);
     V3 n = ld3(L.n + 3 * (size_t)i);

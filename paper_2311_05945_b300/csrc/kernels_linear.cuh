@@ -15,6 +15,7 @@ template <class T>
 __global__ void k_static_values(Geo G, int n_blocks, const T* stage, T* S_val) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= n_blocks) return;
+    if (env_is_done(G, G.node_env[G.S_col[b]])) return;  // a block's nodes share one env
     T s[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     for (int k = G.S_src_ptr[b]; k < G.S_src_ptr[b + 1]; ++k) {
         const T* q = stage + 9 * (size_t)G.S_src[k];
@@ -28,6 +29,7 @@ template <class T>
 __global__ void k_static_diag(Geo G, const int* S_diag, T* S_val) {
     int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= G.n_nodes) return;
+    if (env_is_done(G, G.node_env[n])) return;
     T* o = S_val + 9 * (size_t)S_diag[n];
     if (G.node_fixed[n]) {
         for (int i = 0; i < 9; ++i) o[i] = (i % 4 == 0) ? T(1) : T(0);
@@ -76,6 +78,10 @@ __device__ inline void pair_nodes(const Geo& G, const PairRec& r, PairNodes& P) 
 __global__ void k_contact_count(Geo G, const PairRec* rec, int n, uint32_t* cnt_blk, uint32_t* cnt_g) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    if (env_is_done(G, G.sv_env[rec[i].s[0]])) {  // a converged env: no blocks
+        cnt_blk[i] = cnt_g[i] = 0;
+        return;
+    }
     PairNodes P;
     pair_nodes(G, rec[i], P);
     cnt_blk[i] = (uint32_t)(P.m * P.m);
@@ -94,6 +100,7 @@ __global__ void k_contact_emit(Geo G, const PairRec* rec, int n, const T* pH, co
     const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int i = (int)(gt / kEmitPairLanes), l = (int)(gt % kEmitPairLanes);
     if (i >= n) return;
+    if (env_is_done(G, G.sv_env[rec[i].s[0]])) return;
     PairNodes P;
     pair_nodes(G, rec[i], P);
     const T* H = pH + (size_t)i * 144;
@@ -255,6 +262,7 @@ __global__ void k_precond(Geo G, Bsr<T> S, Bsr<T> C, T* Minv_s) {
     if (u >= G.n_units) return;
     int kind = G.unit_kind[u], idx = G.unit_idx[u];
     if (kind != 0) return;
+    if (env_is_done(G, G.node_env[idx])) return;
     T a[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     add_row_blocks(S, idx, idx, idx + 1, a, 3, 0);
     add_row_blocks(C, idx, idx, idx + 1, a, 3, 0);
@@ -300,6 +308,7 @@ __global__ void __launch_bounds__(32 * kPrecondAffWarps) k_precond_aff(Geo G, Bs
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int idx = blockIdx.x * kPrecondAffWarps + w;
     if (idx >= G.n_aff) return;  // uniform over the warp
+    if (env_is_done(G, G.node_env[G.aff_node0[idx]])) return;  // uniform over the warp
     T* sA = reinterpret_cast<T*>(sbuf) + 144 * w;
     for (int i = lane; i < 144; i += 32) sA[i] = T(0);
     __syncwarp();

@@ -612,6 +612,10 @@ __global__ void k_residual64(Geo G, Bsr<T> S, Bsr<T> C, const double* x, const d
     const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int n = (int)(gt >> 5), l = threadIdx.x & 31;
     if (n >= G.n_nodes) return;  // the whole warp
+    if (skip[G.node_env[n]]) {  // the whole warp
+        if (l < 3) r[3 * (size_t)n + l] = 0.0;
+        return;
+    }
     double y[3] = {0.0, 0.0, 0.0};
     for (int pass = 0; pass < 2; ++pass) {
         const Bsr<T>& A = pass ? C : S;

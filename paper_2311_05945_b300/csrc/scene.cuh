@@ -86,7 +86,13 @@ struct Geo {
     const int* S_col;
     const int* S_src_ptr;           // per block: range into S_src
     const int* S_src;               // staging block index (tets first, then affine bodies)
+    // nullable, per env: nonzero = the env's Newton solve has converged; the
+    // per-iteration kernels then skip its elements, bodies, blocks, pairs and
+    // energy terms (its results are not used until its next solve)
+    const int* env_done = nullptr;
 };
+
+__device__ __forceinline__ bool env_is_done(const Geo& G, int env) { return G.env_done && G.env_done[env]; }
 
 // world position of a surface vertex from node positions x
 __device__ __forceinline__ V3 sv_pos(const Geo& G, const double* x, int s) {

@@ -149,6 +149,12 @@ struct zema_scene {
     // per-step scratch
     DBuf<double> dirw, lam_save;
     std::vector<double> dmin_last;
+    // the step-start values of what a step may change before it completes
+    // (kappa, kappa_min and their flags, d_min), put back by restore_step
+    DBuf<double> kap_save;
+    std::vector<int> kappa_ready_save;
+    std::vector<double> dmin_last_save;
+    bool first_step_done_save = false;
     // learned warm start: network, soft-vertex list (node order) with their
     // tet body, per-body node range / rest half-diagonal / centroid, features
     Mlp* ws_net = nullptr;
@@ -1970,7 +1976,7 @@ void ws_features(zema_scene* s) {
     ZLAUNCH();
 }
 
-void restore_step(zema_scene* s);
+void restore_step(zema_scene* s, bool all = true);
 
 // One time step of every environment.
 void do_step(zema_scene* s) {
@@ -1980,6 +1986,12 @@ void do_step(zema_scene* s) {
     int NE = s->n_envs;
     size_t n3 = 3 * (size_t)s->n_nodes;
     double t0 = now_ms();
+    W.kap_save.ensure(&s->A, 2 * (size_t)NE);
+    ZCHECK(cudaMemcpyAsync(W.kap_save.p, s->kappa.p, NE * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    ZCHECK(cudaMemcpyAsync(W.kap_save.p + NE, s->kappa_min.p, NE * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    W.kappa_ready_save = s->kappa_ready;
+    W.dmin_last_save = W.dmin_last;
+    W.first_step_done_save = s->first_step_done;
     W.lam_save.ensure(&s->A, 12 * (size_t)s->n_aff + 12);
     if (s->n_aff)
         ZCHECK(cudaMemcpyAsync(W.lam_save.p, s->lamA.p, 12 * (size_t)s->n_aff * sizeof(double),
@@ -2048,6 +2060,12 @@ void do_step(zema_scene* s) {
         }
         for (int e = 0; e < NE; ++e) s->S.warm_accepted += acc[e];
         int rounds = 0;
+        // while Newton runs, the per-iteration kernels skip converged envs
+        // (flagged in s->skip, kept equal to `done`); off again on every exit
+        struct DoneMask {
+            Geo& G;
+            ~DoneMask() { G.env_done = nullptr; }
+        } done_mask{G};
         for (;;) {
             bool converged = false;
             for (int it = 0; it < s->P.max_newton; ++it) {
@@ -2059,6 +2077,7 @@ void do_step(zema_scene* s) {
                 // candidate list contains every pair with d < dhat at x
                 for (int e = 0; e < NE; ++e) s->hi[e] = done[e] ? 1 : 0;
                 ZCHECK(cudaMemcpyAsync(s->skip.p, s->hi, NE * sizeof(int), cudaMemcpyHostToDevice, st));
+                G.env_done = s->skip.p;
                 active_from(s, s->X.p, s->swept.p, s->swept_env.p, s->n_swept, true, s->skip.p);
                 double tb = now_ms();
                 s->S.ms_phase[0] += tb - ta;
@@ -2101,6 +2120,7 @@ void do_step(zema_scene* s) {
                 if (hv < 0) fail(ZEMA_ERR_LINESEARCH, "line search found no decrease after 60 halvings");
                 s->S.ls_halvings += hv;
             }
+            G.env_done = nullptr;
             if (!converged) fail(ZEMA_ERR_NEWTON_MAXITER, "Newton did not converge within max_newton iterations");
             // kinematic augmented Lagrangian (Eq. 13)
             if (s->n_aff == 0) break;
@@ -2139,7 +2159,7 @@ void do_step(zema_scene* s) {
             if (e.status != ZEMA_ERR_NEWTON_MAXITER && e.status != ZEMA_ERR_LINESEARCH) throw;
             // the learned start did not converge: plain Newton from the
             // constant-velocity start decides the step
-            restore_step(s);
+            restore_step(s, false);  // the step's kappa stays
             s->S.warm_fallback += 1;
             rounds = solve(false);
         }
@@ -2182,11 +2202,22 @@ void do_step(zema_scene* s) {
     ZCHECK(cudaStreamSynchronize(st));
 }
 
-void restore_step(zema_scene* s) {
+// Back to the step's start: x = x^t and the multipliers; with all, also the
+// barrier stiffness state (kappa, its flags, d_min) the step may have set
+// before it failed.
+void restore_step(zema_scene* s, bool all) {
     zema_scene& W = *s;
     cudaStream_t st = s->st;
     size_t n3 = 3 * (size_t)s->n_nodes;
     cudaMemcpyAsync(s->x.p, s->xt.p, n3 * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    if (all && W.kap_save.p) {
+        const int NE = s->n_envs;
+        cudaMemcpyAsync(s->kappa.p, W.kap_save.p, NE * sizeof(double), cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(s->kappa_min.p, W.kap_save.p + NE, NE * sizeof(double), cudaMemcpyDeviceToDevice, st);
+        s->kappa_ready = W.kappa_ready_save;
+        W.dmin_last = W.dmin_last_save;
+        s->first_step_done = W.first_step_done_save;
+    }
     if (s->n_aff && W.lam_save.p)
         cudaMemcpyAsync(s->lamA.p, W.lam_save.p, 12 * (size_t)s->n_aff * sizeof(double), cudaMemcpyDeviceToDevice, st);
     if (s->G.n_joints && W.lamJ_save.p)

@@ -1,0 +1,146 @@
+"""Parity at the benchmark's own sizes and lengths.
+
+- The full-size single-env grasp (9,600 tets, 6.3k DOF): one GPU step from the
+  oracle's own state at a contact step (both fingers and the floor on the
+  object), FP64 and mixed precision, against one oracle step from the same
+  state: positions within 1e-5 of the bbox diagonal and the total
+  incremental potential within 1e-7 relative.
+- C1's full 100 steps, free running at 1e-2 of the Newton tolerance.
+- The learned warm start against the oracle's plain trajectory: the start
+  changes where Newton begins, not what it converges to, so the same bound
+  holds step by step.
+The oracle runs on all host cores (bit-identical to its serial build).
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from oracle.oracle import Oracle
+from paper_2311_05945_b300 import scenes as S
+
+pytestmark = pytest.mark.gpu
+
+TIGHT = 1e-2
+C2_STEP = 22  # both fingers on the object from step 20
+
+
+@pytest.fixture(scope="module")
+def c2_contact_state():
+    """The oracle's own state of the grasp at step C2_STEP."""
+    O.set_threads(os.cpu_count() or 1)
+    try:
+        sc = S.scene_c2(n_steps=C2_STEP + 2)
+        orc = Oracle(sc)
+        orc.step(C2_STEP)
+        st = [orc.get_state(b) for b in range(len(sc.body_order()))]
+        yield sc, st, orc.kappa(), orc.kappa_min(), orc.diag()
+    finally:
+        O.set_threads(1)
+
+
+def weights_blob(name):
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    return open(os.path.join(root, "paper_2311_05945_b300", "weights", name), "rb").read()
+
+
+def affine_vertices(obj, sc):
+    out = []
+    for i, a in enumerate(sc.affines):
+        q = obj.affine_q(i)
+        out.append((a.V @ q[3:].reshape(3, 3).T + q[:3]).ravel())
+    return np.concatenate(out)
+
+
+def soft_positions(obj, sc):
+    return np.concatenate([obj.tet_positions(i).ravel() for i in range(len(sc.tets))])
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_c2_full_size_one_step_from_oracle_contact_state(c2_contact_state, precision):
+    from paper_2311_05945_b300 import zema as Z
+    sc, st0, kap, kmin, diag = c2_contact_state
+    O.set_threads(os.cpu_count() or 1)
+    try:
+        # the same start on both sides: the oracle's step-22 bodies, its
+        # stiffness, multipliers at zero, the script's targets of step 22
+        orc = Oracle(sc, tol_scale=TIGHT)
+        gpu = Z.Scene(sc, precision=precision, tol_scale=TIGHT)
+        for b, x in enumerate(st0):
+            orc.set_state(b, x)
+            gpu.set_state(b, x)
+        orc.set_kappa(0, kap, kmin)
+        gpu.set_kappa(0, kap, kmin)
+        orc.step_index = gpu.step_index = C2_STEP
+        orc.step(1)
+        stats = gpu.step(1)
+        assert stats["max_active"] > 0 and stats["dmin"] > 0
+        err = max(np.abs(soft_positions(orc, sc) - soft_positions(gpu, sc)).max(),
+                  np.abs(affine_vertices(orc, sc) - affine_vertices(gpu, sc)).max())
+        assert err < 1e-5 * diag, err / diag
+        # both results under the step's potential, evaluated by the oracle
+        ev = Oracle(sc, tol_scale=TIGHT)
+        for b, x in enumerate(st0):
+            ev.set_state(b, x)
+        ev.set_kappa(0, kap, kmin)
+        ev.step_index = C2_STEP
+        ev.prepare(0)
+        ends = {}
+        for name, src in (("oracle", orc), ("gpu", gpu)):
+            for b in range(len(st0)):
+                x = src.get_state(b)
+                ev.set_state(b, x)
+            ends[name] = ev.eval(ev.dofs())[0]
+        assert abs(ends["gpu"] - ends["oracle"]) <= 1e-7 * abs(ends["oracle"]), ends
+        gpu.close()
+    finally:
+        O.set_threads(1)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_c1_full_length_trajectory(precision):
+    from paper_2311_05945_b300 import zema as Z
+    sc = S.scene_c1(n_steps=100)
+    orc = Oracle(sc, tol_scale=TIGHT)
+    gpu = Z.Scene(sc, precision=precision, tol_scale=TIGHT)
+    diag = orc.diag()
+    worst = 0.0
+    for k in range(100):
+        orc.step(1)
+        st = gpu.step(1)
+        err = max(np.abs(orc.tet_positions(0) - gpu.tet_positions(0)).max(),
+                  np.abs(affine_vertices(orc, sc) - affine_vertices(gpu, sc)).max())
+        worst = max(worst, err)
+        assert err < 1e-5 * diag, (k, err / diag)
+        assert st["dmin"] > 0
+    print(f"C1 100 steps, precision {precision}: worst {worst / diag:.2e} x diagonal")
+    gpu.close()
+
+
+def test_learned_warm_start_follows_oracle_plain_trajectory():
+    # a small grasp env of the batch (3,360 tets) through first contact with
+    # the learned start; the oracle steps the same env with the plain
+    # constant-velocity start
+    from paper_2311_05945_b300 import zema as Z
+    O.set_threads(os.cpu_count() or 1)
+    try:
+        sc = S.scene_c3(n_envs=1, n_steps=26, seed0=1001)
+        orc = Oracle(sc, tol_scale=TIGHT)
+        gpu = Z.Scene(sc, precision=1, tol_scale=TIGHT, warm_start=1)
+        dims, theta = Z.read_warmstart_blob(weights_blob("warmstart.bin"))
+        gpu.load_warmstart(dims, theta)
+        diag = orc.diag()
+        learned = 0
+        for k in range(24):
+            orc.step(1)
+            st = gpu.step(1)
+            learned += st["warm_learned"]
+            err = max(np.abs(orc.tet_positions(0) - gpu.tet_positions(0)).max(),
+                      np.abs(affine_vertices(orc, sc) - affine_vertices(gpu, sc)).max())
+            assert err < 1e-5 * diag, (k, err / diag)
+            assert st["dmin"] > 0
+        print(f"learned corrections accepted in {learned} of 24 steps")
+        gpu.close()
+    finally:
+        O.set_threads(1)

@@ -51,3 +51,24 @@ def test_bf16_rounding_matches_a_library_conversion():
     out = mlp_ref.round_bf16(a)
     assert np.array_equal(out.view(np.uint32), ref.view(np.uint32))
     assert out[-8] == 1.0 and out[-7] == np.float32(1 + 2 ** -6)  # ties go to the even significand
+
+
+def test_abs_scale_bounds_the_gradient_and_is_tight_without_cancellation():
+    # |g| <= scale always (triangle inequality); with non-negative inputs,
+    # weights and output errors nothing cancels and the two are equal
+    rng = np.random.default_rng(6)
+    dims = [4, 6, 3]
+    n_par = sum(dims[l] * dims[l + 1] + dims[l + 1] for l in range(len(dims) - 1))
+    theta = np.abs(rng.normal(size=n_par))
+    x = np.abs(rng.normal(size=(11, dims[0])))
+    t = -np.ones((11, dims[-1]))  # below every output: all output errors positive
+    _, g = mlp_ref.loss_and_grad(theta, dims, x, t)
+    s = mlp_ref.grad_abs_scale(theta, dims, x, t)
+    assert np.allclose(np.abs(g), s, rtol=1e-12, atol=0)
+    theta2 = rng.normal(size=n_par)
+    x2 = rng.normal(size=(11, dims[0]))
+    t2 = rng.normal(size=(11, dims[-1]))
+    _, g2 = mlp_ref.loss_and_grad(theta2, dims, x2, t2)
+    s2 = mlp_ref.grad_abs_scale(theta2, dims, x2, t2)
+    assert np.all(np.abs(g2) <= s2 * (1 + 1e-12))
+    assert np.any(np.abs(g2) < 0.9 * s2)  # signs mixed: some entries cancel
