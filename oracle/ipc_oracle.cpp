@@ -2492,6 +2492,35 @@ int orc_newton_system_solve(void* s, int env, const double* y, int which, double
     return 0;
 }
 
+// Contact force sensing (paper section on contact force sensing): per body
+// b, out[3 b .. 3 b + 2] = (1 / h^2) sum over the body's surface vertices v
+// of dB/dx_v, B = kappa e b(d) summed over the pairs with d < dhat at the
+// current state (all pairs by brute force).  Returns 0.
+int orc_contact_forces(void* s, double* out) {
+    Scene& S = *(Scene*)s;
+    State st;
+    get_state(S, st);
+    std::vector<P3> P;
+    all_sv_pos(S, st.x, st.q, P);
+    std::fill(out, out + 3 * S.bodies.size(), 0.0);
+    const double h2 = S.P.dt * S.P.dt;
+    for (int env = 0; env < S.n_envs; ++env) {
+        std::vector<Pair> pairs;
+        candidate_pairs(S, env, P, nullptr, pairs);
+        for (const Pair& pr : pairs) {
+            double x12[12];
+            stencil(P, pr, x12);
+            D2<12> b;
+            if (!pair_barrier(x12, pr.is_ee, S.P.dhat, pr.is_ee ? ee_eps_x(S, pr) : 0.0, b)) continue;
+            for (int k = 0; k < 4; ++k) {
+                const int body = S.sv[pr.s[k]].body;
+                for (int i = 0; i < 3; ++i) out[3 * body + i] += S.kappa[env] * b.g[3 * k + i] / h2;
+            }
+        }
+    }
+    return 0;
+}
+
 // OpenMP threads of the parallel loops (results do not depend on it); the
 // library starts with 1.  n <= 0 only reads.  Returns the count in use (1
 // without OpenMP).

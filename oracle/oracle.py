@@ -57,6 +57,7 @@ def lib():
         L.orc_env_eval.argtypes = [C.c_void_p, C.c_int, dp, dp, dp, ip]
         L.orc_newton_system_solve.argtypes = [C.c_void_p, C.c_int, dp, C.c_int, dp]
         L.orc_set_threads.argtypes = [C.c_int]
+        L.orc_contact_forces.argtypes = [C.c_void_p, dp]
         L.orc_stencil_d2.restype = C.c_double
         L.orc_stencil_d2.argtypes = [dp, C.c_int, ip, dp, dp, dp]
         L.orc_pair_barrier.restype = C.c_double
@@ -275,6 +276,14 @@ class Oracle:
         na = np.zeros(1, dtype=np.int32)
         E = lib().orc_env_eval(self.h, env, _dp(y), _dp(g), _dp(H), _ip(na))
         return E, g, H, int(na[0])
+
+    def contact_forces(self):
+        """(n_bodies, 3) resultant barrier contact force of every body at the
+        current state, in newtons (dB/dx summed over the body's surface
+        vertices, over h^2; the force on the body is the negative)."""
+        out = np.zeros(3 * len(self.body_ids))
+        lib().orc_contact_forces(self.h, _dp(out))
+        return out.reshape(-1, 3)
 
     def newton_direction(self, y, env=0, which=0):
         """p = -H^-1 g of the Newton system at DOF vector y, solved as the

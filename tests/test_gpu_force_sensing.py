@@ -79,3 +79,23 @@ def test_force_controlled_grasp_lifts_the_object():
     assert abs(forces[g.affine_body_id(floor)]).max() < 1e-9  # off the floor
     assert g.tet_positions(0)[:, 1].min() > y0 + 0.005
     g.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_sensed_forces_match_the_oracle(precision):
+    # the library's force sensing against the oracle's (its barrier gradient
+    # by dual numbers over brute-force pairs) at the same in-contact states:
+    # the tiny scene and C1, with the oracle's states and stiffness
+    from paper_2311_05945_b300.zema import Scene
+    for sc, steps in ((S.scene_tiny_contact(mu=0.5), 6), (S.scene_c1(n_steps=14), 12)):
+        orc = Oracle(sc)
+        orc.step(steps)
+        g = Scene(sc, precision=precision)
+        for b in range(len(sc.body_order())):
+            g.set_state(b, orc.get_state(b))
+        g.set_kappa(0, orc.kappa(), orc.kappa_min())
+        Fo, Fg = orc.contact_forces(), g.contact_forces()
+        scale = np.abs(Fo).max()
+        assert scale > 0
+        assert np.abs(Fg - Fo).max() <= 1e-9 * scale, (np.abs(Fg - Fo).max(), scale)
+        g.close()

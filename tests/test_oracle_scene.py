@@ -637,6 +637,14 @@ def test_single_contact_barrier_and_friction_energy(gap):
     E, _, _, na = o.eval(o.dofs(), grad=True)
     assert na == 1
     assert abs(E - kappa * b) <= 1e-12 * kappa * b, (E, kappa * b)
+    # sensed contact force: the barrier gradient with respect to the tip is
+    # kappa b'(gap) along the face normal (+y), over h^2; the fixed body gets
+    # its negative (the third law)
+    F = o.contact_forces()
+    ref_f = kappa * b1 / p.dt ** 2
+    assert abs(F[1, 1] - ref_f) <= 1e-9 * abs(ref_f), (F[1], ref_f)
+    assert np.abs(F[1, [0, 2]]).max() <= 1e-9 * abs(ref_f)
+    assert np.abs(F[0] + F[1]).max() <= 1e-9 * abs(ref_f)
     o.prepare(0, friction=True)
     E = o.eval(o.dofs())[0]
     ref = kappa * b + 0.4 * kappa * abs(b1) * p.eps_v * p.dt / 3
