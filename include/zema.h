@@ -82,6 +82,15 @@ typedef struct {
     zema_alloc_fn alloc;   /* optional device allocator */
     zema_free_fn free;
     void* alloc_ctx;
+    /* Schedule pins (0: chosen by the library).  Neither changes the method,
+     * only the order of sums: with both pinned, an env's results depend on
+     * that env alone, so a batch split into env ranges steps each env bit for
+     * bit as the whole batch does. */
+    double cell_size;      /* spatial-hash cell edge (m); <= 0: the mean surface edge length, at
+                              least dhat */
+    int32_t pcg_cluster_size; /* CTAs per env of the cluster solve (1, 2, 4, 8 or 16); 0: about one per
+                                 128 nodes or the autotuner's choice.  A size the scene or device cannot
+                                 run makes zema_step return ZEMA_ERR_INVALID_ARG */
 } zema_scene_params;
 
 /* Per-step statistics (summed over the steps of one zema_step call, over all
@@ -348,15 +357,21 @@ zema_status zema_local_accd(int64_t n, const double* x12, const double* p12, con
 /* Autotuner of the linear solve's launch schedule (the paper has no
  * counterpart).  The next solve of the scene times the cluster solve of that
  * step's system with every valid number of CTAs per environment (1, 2, 4, 8,
- * 16: best of two runs each, results discarded) and keeps the fastest for
+ * 16), in both residency variants (see zema_get_tuning; best of two runs
+ * each, results discarded) and keeps the fastest for
  * the rest of the scene's life; that solve and every later one use it.  A
  * scene that is never tuned uses about one CTA per 128 nodes (at most 16)
  * and is bit-reproducible run to run; tuning picks by measured time, so two
  * tuned scenes may differ in rounding. */
 zema_status zema_autotune(zema_scene* s);
-/* The cluster size in use (0: not chosen yet, -1: grid-wide solve) for
+/* The cluster schedule in use (0: not chosen yet, -1: grid-wide solve) for
  * precision 0 (FP64) or 1 (mixed), and the autotuner's measurements:
- * candidate sizes and solve times in ms (up to cap entries; *n = count). */
+ * candidate schedules and solve times in ms (up to cap entries; *n =
+ * count).  A schedule is the number of CTAs per env (1, 2, 4, 8, 16), plus
+ * 100 for the variant that keeps two CTAs resident per SM (half the
+ * registers per thread, matrix read through L1/L2): the autotuner tries
+ * both, since with many envs the solve is bound by how many clusters run at
+ * once. */
 zema_status zema_get_tuning(const zema_scene* s, int32_t precision, int32_t* cluster_size, int32_t* cand, float* ms,
                             int32_t cap, int32_t* n);
 

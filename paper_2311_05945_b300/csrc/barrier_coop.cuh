@@ -59,42 +59,17 @@ __device__ __forceinline__ int rr_partner(int i, int r) {
     return (2 * r - i + 18) % 9;
 }
 
-// out = T^T P(scale T H T^T) T for the 12x12 slot-space Hessian H (row-major
-// in shared memory; its storage is reused), by the 16 lanes of a half-warp.
-// Vs (100 values) and lam (10) are shared scratch of the pair.
+// PSD part P = V max(L, 0) V^T of a symmetric 9x9 matrix A by the 16 lanes
+// of a half-warp: lane i < 9 holds row i of A in a[0..8] (a[9] = 0, lanes
+// 9-15 all zeros).  Parallel cyclic Jacobi with rows in registers; P goes to
+// shared memory (81 values, row-major).  Vs (100 values) and lam (10) are
+// shared scratch.
 template <class T>
-__device__ void coop_project(T* H, T* Vs, T* lam, double scale, T* out, unsigned mask) {
+__device__ void coop_psd9(T (&a)[kCoopN], T* P, T* Vs, T* lam, unsigned mask) {
     const int lane = threadIdx.x & (kCoopLanes - 1);
-    T a[kCoopN], v[kCoopN];
+    T v[kCoopN];
 #pragma unroll
-    for (int c = 0; c < kCoopN; ++c) {
-        a[c] = T(0);
-        v[c] = (c == lane) ? T(1) : T(0);
-    }
-    if (lane < 9) {
-        // row lane = 3k + al of K: K(3k+al, 3l+b) = scale sum_ij T[k][i] T[l][j] H(3i+al, 3j+b)
-        const int k = lane / 3, al = lane - 3 * k;
-        T w[4][9];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int l = 0; l < 3; ++l)
-#pragma unroll
-                for (int b = 0; b < 3; ++b) {
-                    T s = 0;
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) s += (T)tcoef(l, j) * H[(3 * i + al) * 12 + 3 * j + b];
-                    w[i][3 * l + b] = s;
-                }
-        const T sc = (T)scale;
-#pragma unroll
-        for (int c = 0; c < 9; ++c) {
-            T s = 0;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) s += (T)tcoef(k, i) * w[i][c];
-            a[c] = sc * s;
-        }
-    }
+    for (int c = 0; c < kCoopN; ++c) v[c] = (c == lane) ? T(1) : T(0);
     for (int sweep = 0; sweep < CoopSweeps<T>::n; ++sweep) {
         // stop when the off-diagonal mass is at the rounding floor of T
         T dg = sel_row(a, lane), rowsq = 0;
@@ -134,19 +109,19 @@ __device__ void coop_project(T* H, T* Vs, T* lam, double scale, T* out, unsigned
 #pragma unroll
             for (int m = 1; m <= 4; ++m) {
                 const int i1 = (r + m) % 9, i2 = (r - m + 9) % 9;
-                const int P = i1 < i2 ? i1 : i2, Q = i1 < i2 ? i2 : i1;
-                const T cm = hshfl(mask, c, P), sm = hshfl(mask, s, P);
-                T t1 = a[P], t2 = a[Q];
-                a[P] = cm * t1 - sm * t2;
+                const int P1 = i1 < i2 ? i1 : i2, Q = i1 < i2 ? i2 : i1;
+                const T cm = hshfl(mask, c, P1), sm = hshfl(mask, s, P1);
+                T t1 = a[P1], t2 = a[Q];
+                a[P1] = cm * t1 - sm * t2;
                 a[Q] = sm * t1 + cm * t2;
-                t1 = v[P];
+                t1 = v[P1];
                 t2 = v[Q];
-                v[P] = cm * t1 - sm * t2;
+                v[P1] = cm * t1 - sm * t2;
                 v[Q] = sm * t1 + cm * t2;
             }
         }
     }
-    // P = V max(L, 0) V^T, then out = T^T P T
+    // P = V max(L, 0) V^T
     if (lane < 9) {
         T l = sel_row(a, lane);
         lam[lane] = l > T(0) ? l : T(0);
@@ -159,9 +134,46 @@ __device__ void coop_project(T* H, T* Vs, T* lam, double scale, T* out, unsigned
         T s = 0;
 #pragma unroll
         for (int k = 0; k < 9; ++k) s += Vs[10 * i + k] * lam[k] * Vs[10 * jj + k];
-        H[e] = s;  // H's storage now holds P (9x9, row-major)
+        P[e] = s;
     }
     __syncwarp(mask);
+}
+
+// out = T^T P(scale T H T^T) T for the 12x12 slot-space Hessian H (row-major
+// in shared memory; its storage is reused), by the 16 lanes of a half-warp.
+// Vs (100 values) and lam (10) are shared scratch of the pair.
+template <class T>
+__device__ void coop_project(T* H, T* Vs, T* lam, double scale, T* out, unsigned mask) {
+    const int lane = threadIdx.x & (kCoopLanes - 1);
+    T a[kCoopN];
+#pragma unroll
+    for (int c = 0; c < kCoopN; ++c) a[c] = T(0);
+    if (lane < 9) {
+        // row lane = 3k + al of K: K(3k+al, 3l+b) = scale sum_ij T[k][i] T[l][j] H(3i+al, 3j+b)
+        const int k = lane / 3, al = lane - 3 * k;
+        T w[4][9];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int l = 0; l < 3; ++l)
+#pragma unroll
+                for (int b = 0; b < 3; ++b) {
+                    T s = 0;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) s += (T)tcoef(l, j) * H[(3 * i + al) * 12 + 3 * j + b];
+                    w[i][3 * l + b] = s;
+                }
+        const T sc = (T)scale;
+#pragma unroll
+        for (int c = 0; c < 9; ++c) {
+            T s = 0;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) s += (T)tcoef(k, i) * w[i][c];
+            a[c] = sc * s;
+        }
+    }
+    __syncwarp(mask);  // every lane has read H: its storage now takes P
+    coop_psd9<T>(a, H, Vs, lam, mask);
     for (int e = lane; e < 144; e += kCoopLanes) {
         const int row = e / 12, col = e - 12 * row;
         const int i = row / 3, al = row - 3 * i, jj = col / 3, b = col - 3 * jj;

@@ -555,40 +555,68 @@ __global__ void k_affine_energy(Geo G, const double* x, const double* xhat, AffK
         [&](int b) -> double { return affine_energy(G, x, xhat, K, b); }, part_slot(part, ET_AFFINE, G.n_envs, env));
 }
 
-constexpr int AF_T = 32;
+constexpr int kAffBodies = 4;  // affine bodies per 64-thread block of k_affine_gh
 
 // gradient (FP64, directly into g, the body's nodes only) and 16 Hessian
-// blocks (in T)
+// blocks (in T), one affine body per half-warp: the 9x9 orthogonality
+// Hessian (A-space) is built by lanes 0-8, one row each, and projected to PSD
+// by the 16-lane parallel Jacobi (coop_psd9); lane 0 then assembles the
+// blocks and the gradient.
 template <class T>
-__global__ void __launch_bounds__(AF_T) k_affine_gh(Geo G, const double* x, const double* xhat, AffKin K,
-                                                    T* stage_blk, double* g) {
-    extern __shared__ unsigned char smraw[];
-    T* sm = (T*)smraw;
-    int b = blockIdx.x * AF_T + threadIdx.x;
-    if (b >= G.n_aff) return;
-    int mode = G.aff_mode[b];
-    int n0 = G.aff_node0[b];
+__global__ void __launch_bounds__(kCoopLanes * kAffBodies) k_affine_gh(Geo G, const double* x, const double* xhat,
+                                                                      AffKin K, T* stage_blk, double* g) {
+    __shared__ T sP[kAffBodies][81];
+    __shared__ T sV[kAffBodies][100];
+    __shared__ T sL[kAffBodies][10];
+    const int hw = threadIdx.x / kCoopLanes, lane = threadIdx.x & (kCoopLanes - 1);
+    const unsigned mask = 0xFFFFu << (threadIdx.x & 16);
+    const int b = blockIdx.x * kAffBodies + hw;
+    if (b >= G.n_aff) return;  // the whole half-warp
+    const int mode = G.aff_mode[b];
+    const int n0 = G.aff_node0[b];
     if (env_is_done(G, G.node_env[n0])) return;
     T* blk = stage_blk + (size_t)b * 144;
-    for (int i = 0; i < 144; ++i) blk[i] = T(0);
     if (mode == 1) {
-        for (int j = 0; j < 4; ++j) st3(g + 3 * (size_t)(n0 + j), v3(0, 0, 0));
+        for (int i = lane; i < 144; i += kCoopLanes) blk[i] = T(0);
+        if (lane < 4) st3(g + 3 * (size_t)(n0 + lane), v3(0, 0, 0));
         return;
     }
-    SMat<9, T> H{sm + threadIdx.x, AF_T}, W{sm + 81 * AF_T + threadIdx.x, AF_T};
-    V3 c[4], ch[4];
-    for (int j = 0; j < 4; ++j) {
-        c[j] = ld3(x + 3 * (size_t)(n0 + j));
-        ch[j] = ld3(xhat + 3 * (size_t)(n0 + j));
+    V3 c[4];
+    for (int j = 0; j < 4; ++j) c[j] = ld3(x + 3 * (size_t)(n0 + j));
+    // orthogonality: Phi = sum_jk (c_j . c_k - delta_jk)^2, its Hessian in
+    // A = (c_1, c_2, c_3) built by rows (lane r < 9: row r = 3 i + a)
+    const double w = G.h * G.h * G.aff_stiff[b] * G.aff_vol[b];
+    double Gm[3][3];
+    for (int j = 0; j < 3; ++j)
+        for (int k = 0; k < 3; ++k) Gm[j][k] = dot(c[1 + j], c[1 + k]) - (j == k ? 1.0 : 0.0);
+    T a[kCoopN];
+    for (int q = 0; q < kCoopN; ++q) a[q] = T(0);
+    if (lane < 9) {
+        const int i = lane / 3, al = lane - 3 * i;
+        for (int l = 0; l < 3; ++l)
+            for (int bb = 0; bb < 3; ++bb) {
+                double v = comp(c[1 + l], al) * comp(c[1 + i], bb);
+                if (al == bb) v += Gm[i][l];
+                if (i == l)
+                    v += comp(c[1], al) * comp(c[1], bb) + comp(c[2], al) * comp(c[2], bb) +
+                         comp(c[3], al) * comp(c[3], bb);
+                a[3 * l + bb] = (T)(4.0 * w * v);
+            }
     }
+    coop_psd9<T>(a, sP[hw], sV[hw], sL[hw], mask);
+    if (lane != 0) return;
+    const T* P = sP[hw];
+    for (int i = 0; i < 144; ++i) blk[i] = T(0);
+    V3 ch[4];
+    for (int j = 0; j < 4; ++j) ch[j] = ld3(xhat + 3 * (size_t)(n0 + j));
     const double* S = G.aff_S + 9 * (size_t)b;
     double m = G.aff_m[b];
     V3 gr[4];
     gr[0] = m * (c[0] - ch[0]);
     for (int j = 0; j < 3; ++j) {
-        V3 s = v3(0, 0, 0);
-        for (int k = 0; k < 3; ++k) s = s + S[3 * j + k] * (c[1 + k] - ch[1 + k]);
-        gr[1 + j] = s;
+        V3 sj = v3(0, 0, 0);
+        for (int k = 0; k < 3; ++k) sj = sj + S[3 * j + k] * (c[1 + k] - ch[1 + k]);
+        gr[1 + j] = sj;
     }
     // inertia blocks: (0,0) m I ; (j,k) S_jk I
     auto blk_add_diag = [&](int j, int k, double v) {
@@ -600,35 +628,16 @@ __global__ void __launch_bounds__(AF_T) k_affine_gh(Geo G, const double* x, cons
     blk_add_diag(0, 0, m);
     for (int j = 0; j < 3; ++j)
         for (int k = 0; k < 3; ++k) blk_add_diag(1 + j, 1 + k, S[3 * j + k]);
-    // orthogonality: Phi = sum_jk (c_j . c_k - delta_jk)^2
-    double w = G.h * G.h * G.aff_stiff[b] * G.aff_vol[b];
-    double Gm[3][3];
-    for (int j = 0; j < 3; ++j)
-        for (int k = 0; k < 3; ++k) Gm[j][k] = dot(c[1 + j], c[1 + k]) - (j == k ? 1.0 : 0.0);
     for (int i = 0; i < 3; ++i) {
-        V3 s = v3(0, 0, 0);
-        for (int k = 0; k < 3; ++k) s = s + Gm[i][k] * c[1 + k];
-        gr[1 + i] = gr[1 + i] + (4.0 * w) * s;
+        V3 si = v3(0, 0, 0);
+        for (int k = 0; k < 3; ++k) si = si + Gm[i][k] * c[1 + k];
+        gr[1 + i] = gr[1 + i] + (4.0 * w) * si;
     }
-    double CC[9];
-    for (int a = 0; a < 3; ++a)
-        for (int bb = 0; bb < 3; ++bb)
-            CC[3 * a + bb] = comp(c[1], a) * comp(c[1], bb) + comp(c[2], a) * comp(c[2], bb) + comp(c[3], a) * comp(c[3], bb);
-    for (int i = 0; i < 3; ++i)
-        for (int l = 0; l < 3; ++l)
-            for (int a = 0; a < 3; ++a)
-                for (int bb = 0; bb < 3; ++bb) {
-                    double v = comp(c[1 + l], a) * comp(c[1 + i], bb);
-                    if (a == bb) v += Gm[i][l];
-                    if (i == l) v += CC[3 * a + bb];
-                    H(3 * i + a, 3 * l + bb) = (T)(4.0 * w * v);
-                }
-    psd_project<9, T>(H, W);
     for (int i = 0; i < 3; ++i)
         for (int l = 0; l < 3; ++l) {
             T* o = blk + (4 * (1 + i) + (1 + l)) * 9;
-            for (int a = 0; a < 3; ++a)
-                for (int bb = 0; bb < 3; ++bb) o[3 * a + bb] += H(3 * i + a, 3 * l + bb);
+            for (int al = 0; al < 3; ++al)
+                for (int bb = 0; bb < 3; ++bb) o[3 * al + bb] += P[9 * (3 * i + al) + 3 * l + bb];
         }
     if (mode == 2) {
         const double* qt = K.qtarget + 12 * (size_t)b;

@@ -192,8 +192,13 @@ __device__ __forceinline__ Real group_sum(Real v) {
     return v;
 }
 
-template <class Real>
-__global__ void __launch_bounds__(kPcgcThreads, 1) k_pcg_cluster(PcgcArgs<Real> a) {
+// kMinBlocks CTAs resident per SM: 1 keeps every owned row's state in
+// registers and may stage the matrix slice in shared memory (few envs); 2
+// halves the register budget (the compiler spills the preconditioner blocks
+// to L1-cached local memory) and never stages, so that twice as many
+// clusters run at once (many envs, where the solve is latency-bound)
+template <class Real, int kMinBlocks>
+__global__ void __launch_bounds__(kPcgcThreads, kMinBlocks) k_pcg_cluster(PcgcArgs<Real> a) {
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
     const Geo& G = a.G;
@@ -230,10 +235,13 @@ __global__ void __launch_bounds__(kPcgcThreads, 1) k_pcg_cluster(PcgcArgs<Real> 
     const int n_soft = ns1 - nb, n_arow = nend - ns1;
     // soft rows per CTA, balanced by the rows' stored blocks (static and
     // contact, plus 2 per row for its fixed cost) when no CTA then owns more
-    // than max_rows rows, else an equal split; every CTA finds the same
-    // boundaries (binary searches over the same prefix sums)
+    // than twice its equal share (and no more than the layout's max_rows),
+    // else an equal split; every CTA finds the same boundaries (binary
+    // searches over the same prefix sums).  The bound depends on this env
+    // alone, so the partition does too.
     __shared__ int s_bounds[kPcgcMaxCluster + 1];
     if (threadIdx.x == 0) {
+        const int max_rows_env = min(2 * ((n_soft + cs - 1) / cs) + 1, a.max_rows);
         auto cum = [&](int row) -> long long {
             return (long long)a.S.rowptr[row] + a.C.rowptr[row] + 2ll * row;
         };
@@ -255,7 +263,7 @@ __global__ void __launch_bounds__(kPcgcThreads, 1) k_pcg_cluster(PcgcArgs<Real> 
                 b = l;
             }
             s_bounds[r] = b;
-            ok &= b - s_bounds[r - 1] <= a.max_rows - 1;
+            ok &= b - s_bounds[r - 1] <= max_rows_env - 1;
         }
         if (!ok)
             for (int r = 0; r <= cs; ++r) s_bounds[r] = nb + (int)(((long long)n_soft * r) / cs);

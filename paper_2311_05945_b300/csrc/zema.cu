@@ -519,7 +519,7 @@ void build(zema_scene* s) {
         sum_len += std::sqrt(d2);
     }
     double mean_len = s->n_edges ? sum_len / s->n_edges : s->P.dhat;
-    s->cell = std::max(mean_len, s->P.dhat);
+    s->cell = s->P.cell_size > 0.0 ? s->P.cell_size : std::max(mean_len, s->P.dhat);
     // ---- bodies
     std::vector<int> body_class_h(s->bodies.size());
     std::vector<double> body_mu_h(s->bodies.size());
@@ -1077,8 +1077,6 @@ void build(zema_scene* s) {
     // dynamic shared memory opt-in for the per-thread matrix kernels
     ZCHECK(cudaFuncSetAttribute(k_elastic_gh<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 81 * EL_T * 8));
     ZCHECK(cudaFuncSetAttribute(k_elastic_gh<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 81 * EL_T * 4));
-    ZCHECK(cudaFuncSetAttribute(k_affine_gh<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 81 * AF_T * 8));
-    ZCHECK(cudaFuncSetAttribute(k_affine_gh<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 81 * AF_T * 4));
     ZCHECK(cudaStreamSynchronize(st));
     for (size_t b = 0; b < s->tin.size(); ++b)
         if (!s->tin[b].spring_v.empty()) upload_springs(s, (int)b);
@@ -1220,7 +1218,7 @@ void grad_hess_t(zema_scene* s, bool barrier, bool friction, bool hess) {
     ZLAUNCH();
     ZCHECK(cudaMemsetAsync(s->g.p, 0, 3 * (size_t)s->n_nodes * sizeof(double), st));
     if (s->n_aff)
-        ZL(k_affine_gh<T>, div_up(s->n_aff, AF_T), AF_T, 2 * 81 * AF_T * sizeof(T), st)(
+        ZL(k_affine_gh<T>, div_up(s->n_aff, kAffBodies), kCoopLanes * kAffBodies, 0, st)(
             G, s->x.p, s->xhat.p, kin(s), stage + 144 * (size_t)s->n_tets, s->g.p);
     ZLAUNCH();
     ZL(k_soft_grad, div_up(s->n_nodes, TB), TB, 0, st)(G, s->x.p, s->xhat.p, s->stage_g.p, s->g.p);
@@ -1345,10 +1343,22 @@ void grad_hess(zema_scene* s, bool barrier = true, bool friction = true, bool he
 // vector, the owned rows' q and the affine rows' partials.
 // ---------------------------------------------------------------------------
 constexpr size_t kPcgcMaxSmem = 200 * 1024;
+// dynamic shared memory of the variant with two CTAs per SM
+constexpr size_t kPcgcMaxSmem2 = 104 * 1024;
+
+// A cluster schedule code: CTAs per env (1..16), plus 100 for the variant
+// that keeps two CTAs resident per SM.
+inline int sched_cs(int code) { return code % 100; }
+inline int sched_occ(int code) { return code >= 100 ? 2 : 1; }
+template <class T>
+inline auto pcgc_kernel(int code) {
+    return sched_occ(code) == 2 ? k_pcg_cluster<T, 2> : k_pcg_cluster<T, 1>;
+}
 
 // rows a CTA may own (the solve balances rows by their blocks within this
 // bound): twice the equal share, at most what its threads hold in registers
-int pcgc_max_rows(const zema_scene* s, int cs) {
+int pcgc_max_rows(const zema_scene* s, int code) {
+    const int cs = sched_cs(code);
     return std::min(2 * ((s->pcgc_max_soft + cs - 1) / cs) + 1, kPcgcOwn * kPcgcThreads + 1);
 }
 
@@ -1357,11 +1367,11 @@ int pcgc_max_rows(const zema_scene* s, int cs) {
 int pcgc_chunk_cap(const zema_scene*, int) { return 0; }
 
 template <class T>
-size_t pcgc_smem_base(const zema_scene* s, int cs) {
-    const size_t tasks = (size_t)pcgc_max_rows(s, cs) + 4 * (size_t)s->pcgc_max_aff, ch = pcgc_chunk_cap(s, cs);
+size_t pcgc_smem_base(const zema_scene* s, int code) {
+    const size_t tasks = (size_t)pcgc_max_rows(s, code) + 4 * (size_t)s->pcgc_max_aff, ch = pcgc_chunk_cap(s, code);
     return (tasks + ch) * sizeof(int4) + ((tasks + 4) & ~(size_t)3) * sizeof(int) +
            (3 * (kPcgcThreads / 32) + 8 + pcgc_pstride<T>() * (size_t)s->pcgc_max_env_nodes +
-            3 * (size_t)pcgc_max_rows(s, cs) + 24 * (size_t)s->pcgc_max_aff + 3 * ch) *
+            3 * (size_t)pcgc_max_rows(s, code) + 24 * (size_t)s->pcgc_max_aff + 3 * ch) *
                sizeof(T) +
            16;  // alignment of the staged slice
 }
@@ -1371,12 +1381,13 @@ size_t pcgc_smem_base(const zema_scene* s, int cs) {
 // slice (soft rows' S blocks and the CTA's share of the affine rows') with
 // room for contact blocks; 0 (the solve reads the matrix from L1/L2) if not.
 template <class T>
-int pcgc_slice_cap(const zema_scene* cs_scene, int cs) {
+int pcgc_slice_cap(const zema_scene* cs_scene, int code) {
     zema_scene* s = const_cast<zema_scene*>(cs_scene);
-    const auto key = std::make_pair((int)sizeof(T), cs);
+    const auto key = std::make_pair((int)sizeof(T), code);
     auto hit = s->pcgc_cap.find(key);
     if (hit != s->pcgc_cap.end()) return hit->second;
-    if (sizeof(T) != sizeof(float)) {  // the slice is staged in FP32 solves only
+    const int cs = sched_cs(code);
+    if (sizeof(T) != sizeof(float) || sched_occ(code) == 2) {  // staged in FP32 one-per-SM solves only
         s->pcgc_cap[key] = 0;
         return 0;
     }
@@ -1397,7 +1408,7 @@ int pcgc_slice_cap(const zema_scene* cs_scene, int cs) {
         }
     }
     const size_t per = 12 * sizeof(float);  // a block: 9 values, its column, 2 pad
-    const size_t base = pcgc_smem_base<T>(s, cs);
+    const size_t base = pcgc_smem_base<T>(s, code);
     const long long avail = base >= kPcgcMaxSmem ? 0 : (long long)((kPcgcMaxSmem - base) / per);
     const int cap = avail >= mx + mx / 4 + 128 ? (int)avail : 0;
     s->pcgc_cap[key] = cap;
@@ -1405,15 +1416,16 @@ int pcgc_slice_cap(const zema_scene* cs_scene, int cs) {
 }
 
 template <class T>
-size_t pcgc_smem(const zema_scene* s, int cs) {
-    return pcgc_smem_base<T>(s, cs) + (size_t)pcgc_slice_cap<T>(s, cs) * 12 * sizeof(float);
+size_t pcgc_smem(const zema_scene* s, int code) {
+    return pcgc_smem_base<T>(s, code) + (size_t)pcgc_slice_cap<T>(s, code) * 12 * sizeof(float);
 }
 
 template <class T>
-void pcgc_config(const zema_scene* s, int cs, cudaLaunchConfig_t& cfg, cudaLaunchAttribute* at) {
+void pcgc_config(const zema_scene* s, int code, cudaLaunchConfig_t& cfg, cudaLaunchAttribute* at) {
+    const int cs = sched_cs(code);
     cfg.gridDim = dim3((unsigned)(cs * s->n_envs));
     cfg.blockDim = dim3(kPcgcThreads);
-    cfg.dynamicSmemBytes = pcgc_smem<T>(s, cs);
+    cfg.dynamicSmemBytes = pcgc_smem<T>(s, code);
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = (unsigned)cs;
     at[0].val.clusterDim.y = 1;
@@ -1430,18 +1442,22 @@ int pcgc_choose(zema_scene* s) {
     // the env's vector must fit in shared memory, a CTA's rows in its
     // threads' registers, the affine rows in one CTA
     if (pcgc_smem_base<T>(s, 16) > kPcgcMaxSmem || 12 * s->pcgc_max_aff > kPcgcThreads) return -1;
-    ZCHECK(cudaFuncSetAttribute(k_pcg_cluster<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPcgcMaxSmem));
-    if (want > 8) {
-        if (cudaFuncSetAttribute(k_pcg_cluster<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
-            cudaGetLastError();
-            want = 8;
-        }
+    ZCHECK(cudaFuncSetAttribute(k_pcg_cluster<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPcgcMaxSmem));
+    ZCHECK(cudaFuncSetAttribute(k_pcg_cluster<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPcgcMaxSmem2));
+    // the rest of the SM's storage stays L1 for the matrix rows (one CTA per
+    // SM) or holds two CTAs' shared memory
+    bool nonportable = true;
+    if (cudaFuncSetAttribute(k_pcg_cluster<T, 1>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
+        cudaFuncSetAttribute(k_pcg_cluster<T, 2>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+        cudaGetLastError();
+        nonportable = false;
     }
+    if (want > 8 && !nonportable) want = 8;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute at[1];
     pcgc_config<T>(s, want, cfg, at);
     int maxcs = 0;
-    if (cudaOccupancyMaxPotentialClusterSize(&maxcs, k_pcg_cluster<T>, &cfg) != cudaSuccess || maxcs < 1) {
+    if (cudaOccupancyMaxPotentialClusterSize(&maxcs, k_pcg_cluster<T, 1>, &cfg) != cudaSuccess || maxcs < 1) {
         cudaGetLastError();
         return -1;
     }
@@ -1453,9 +1469,9 @@ int pcgc_choose(zema_scene* s) {
     ZCHECK(cudaGetDevice(&dev));
     ZCHECK(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
     int pct = (int)std::min<size_t>(100, (100 * (cfg.dynamicSmemBytes + 2048) + smem_sm - 1) / std::max(1, smem_sm));
-    ZCHECK(cudaFuncSetAttribute(k_pcg_cluster<T>, cudaFuncAttributePreferredSharedMemoryCarveout, pct));
+    ZCHECK(cudaFuncSetAttribute(k_pcg_cluster<T, 1>, cudaFuncAttributePreferredSharedMemoryCarveout, pct));
     int ncl = 0;
-    if (cudaOccupancyMaxActiveClusters(&ncl, k_pcg_cluster<T>, &cfg) != cudaSuccess || ncl < 1) {
+    if (cudaOccupancyMaxActiveClusters(&ncl, k_pcg_cluster<T, 1>, &cfg) != cudaSuccess || ncl < 1) {
         cudaGetLastError();
         return -1;
     }
@@ -1464,15 +1480,16 @@ int pcgc_choose(zema_scene* s) {
 
 // whether cluster size cs can run the cluster solve of this scene
 template <class T>
-bool pcgc_valid(zema_scene* s, int cs) {
+bool pcgc_valid(zema_scene* s, int code) {
+    const int cs = sched_cs(code);
     if (cs < 1 || cs > 16 || (s->pcgc_max_soft + cs - 1) / cs > kPcgcOwn * kPcgcThreads ||
-        pcgc_smem<T>(s, cs) > kPcgcMaxSmem)
+        pcgc_smem<T>(s, code) > (sched_occ(code) == 2 ? kPcgcMaxSmem2 : kPcgcMaxSmem))
         return false;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute at[1];
-    pcgc_config<T>(s, cs, cfg, at);
+    pcgc_config<T>(s, code, cfg, at);
     int ncl = 0;
-    if (cudaOccupancyMaxActiveClusters(&ncl, k_pcg_cluster<T>, &cfg) != cudaSuccess || ncl < 1) {
+    if (cudaOccupancyMaxActiveClusters(&ncl, pcgc_kernel<T>(code), &cfg) != cudaSuccess || ncl < 1) {
         cudaGetLastError();
         return false;
     }
@@ -1501,7 +1518,16 @@ int64_t pcg_t(zema_scene* s, const std::vector<int>& done_h) {
     ZCHECK(cudaMemcpyAsync(s->conv.p, s->hi, NE * sizeof(int), cudaMemcpyHostToDevice, st));
     ZCHECK(cudaMemsetAsync(s->pcg_iters.p, 0, NE * sizeof(int), st));
     const int pi = s->P.precision == 1 ? 1 : 0;
-    if (s->P.pcg_kind != 1 && s->pcgc_cs[pi] == 0) s->pcgc_cs[pi] = pcgc_choose<T>(s);
+    if (s->P.pcg_kind != 1 && s->pcgc_cs[pi] == 0) {
+        if (s->P.pcg_cluster_size > 0) {
+            // pinned by the caller
+            if (pcgc_choose<T>(s) < 0 || !pcgc_valid<T>(s, s->P.pcg_cluster_size))
+                fail(ZEMA_ERR_INVALID_ARG, "pcg_cluster_size cannot run the cluster solve of this scene");
+            s->pcgc_cs[pi] = s->P.pcg_cluster_size;
+        } else {
+            s->pcgc_cs[pi] = pcgc_choose<T>(s);
+        }
+    }
     if (s->P.pcg_kind == 2 && s->pcgc_cs[pi] < 0)
         fail(ZEMA_ERR_INVALID_ARG, "cluster PCG unavailable for this scene on this device");
     const bool use_cluster = s->P.pcg_kind != 1 && s->pcgc_cs[pi] > 0;
@@ -1545,9 +1571,18 @@ int64_t pcg_t(zema_scene* s, const std::vector<int>& done_h) {
         cudaLaunchAttribute at[1];
         pcgc_config<T>(s, cs, cfg, at);
         cfg.stream = st;
+        if (sched_occ(cs) == 2) {
+            // shared memory for two CTAs per SM, the rest L1
+            int dev = 0, smem_sm = 0;
+            ZCHECK(cudaGetDevice(&dev));
+            ZCHECK(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+            const int pct = (int)std::min<size_t>(
+                100, (100 * 2 * (cfg.dynamicSmemBytes + 8192) + smem_sm - 1) / std::max(1, smem_sm));
+            ZCHECK(cudaFuncSetAttribute(k_pcg_cluster<T, 2>, cudaFuncAttributePreferredSharedMemoryCarveout, pct));
+        }
         {
             LaunchScope ls("k_pcg_cluster");
-            ZCHECK(cudaLaunchKernelEx(&cfg, k_pcg_cluster<T>, c));
+            ZCHECK(cudaLaunchKernelEx(&cfg, pcgc_kernel<T>(cs), c));
         }
         ZLAUNCH();
     };
@@ -1610,7 +1645,8 @@ int64_t pcg_t(zema_scene* s, const std::vector<int>& done_h) {
         ZCHECK(cudaEventCreate(&e1));
         float best = INFINITY;
         int best_cs = s->pcgc_cs[pi];
-        for (int cs = 1; cs <= 16; cs *= 2) {
+        for (int code : {1, 2, 4, 8, 16, 101, 102, 104, 108, 116}) {
+            const int cs = code;
             if (!pcgc_valid<T>(s, cs)) continue;
             float ms = INFINITY;
             for (int rep = 0; rep < 2; ++rep) {
@@ -2278,7 +2314,9 @@ void zema_default_params(zema_scene_params* p) {
 zema_status zema_create_scene(const zema_scene_params* params, zema_scene** out) {
     if (!params || !out) return ZEMA_ERR_INVALID_ARG;
     if (!(params->dt > 0) || !(params->dhat > 0) || params->n_envs < 1 || !(params->eps_v > 0) ||
-        params->pcg_kind < 0 || params->pcg_kind > 2)
+        params->pcg_kind < 0 || params->pcg_kind > 2 || !(params->cell_size < INFINITY) ||
+        (params->pcg_cluster_size != 0 && params->pcg_cluster_size != 1 && params->pcg_cluster_size != 2 &&
+         params->pcg_cluster_size != 4 && params->pcg_cluster_size != 8 && params->pcg_cluster_size != 16))
         return ZEMA_ERR_INVALID_ARG;
     zema_scene* s = new (std::nothrow) zema_scene();
     if (!s) return ZEMA_ERR_OOM;
@@ -2928,7 +2966,8 @@ zema_status zema_record_warmstart_affine(zema_scene* s, float* features, float* 
 
 zema_status zema_autotune(zema_scene* s) {
     if (!s) return ZEMA_ERR_INVALID_ARG;
-    s->pcgc_tune[0] = s->pcgc_tune[1] = true;
+    // a pinned cluster size is kept
+    s->pcgc_tune[0] = s->pcgc_tune[1] = s->P.pcg_cluster_size <= 0;
     return ZEMA_OK;
 }
 

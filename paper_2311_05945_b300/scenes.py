@@ -435,11 +435,13 @@ def scene_c2(n_steps: int = 300, finger_subdiv: int = 9, precision: int = 0) -> 
 
 
 def scene_c3(n_envs: int = 256, n_steps: int = 200, min_tets=2000, max_tets=20000,
-             finger_subdiv: int = 9, precision: int = 1, seed0: int = 1000) -> Scene:
+             finger_subdiv: int = 9, precision: int = 1, seed0: int = 1000, slot0: int = 0) -> Scene:
     """Batched grasping: env i (seed seed0+i) draws its object kind (ellipsoid,
     torus, box), tet count log-uniform in [min_tets, max_tets], E log-uniform in
     [1e4, 1e6], mu uniform in [0.3, 1.0]; nu = 0.45.  Envs are placed 0.5 m
-    apart along x so they are spatially disjoint.  Training envs use seeds from
+    apart along x (env i at slot slot0 + i) so they are spatially disjoint; a
+    range of a larger batch built with seed0 and slot0 advanced together has
+    the same coordinates as in the whole batch.  Training envs use seeds from
     1000, held-out evaluation envs from 100000."""
     p = Params(dt=0.005, dhat=1e-3, kappa=0.0, eps_v=1e-3, newton_tol_rel=1e-3, precision=precision)
     s = Scene("c3_batched_grasp", p, n_envs=n_envs, n_steps=n_steps)
@@ -453,7 +455,7 @@ def scene_c3(n_envs: int = 256, n_steps: int = 200, min_tets=2000, max_tets=2000
         mu = 0.3 + 0.7 * u[3]
         sp = _spacing_for_count(kind, nt)
         allf += grasp_env(s, i, kind, sp, seed=seed0 + i, E=E, nu=0.45, mu=mu,
-                          offset=(0.5 * i, 0.0, 0.0), finger_subdiv=finger_subdiv)
+                          offset=(0.5 * (slot0 + i), 0.0, 0.0), finger_subdiv=finger_subdiv)
     s.script = grasp_script(allf, p.dt)
     s.fingers = allf
     return s

@@ -35,6 +35,7 @@ class Params(C.Structure):
         ("max_newton", C.c_int32), ("max_pcg", C.c_int32), ("max_al_rounds", C.c_int32),
         ("precision", C.c_int32), ("n_envs", C.c_int32), ("warm_start", C.c_int32), ("pcg_kind", C.c_int32),
         ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p),
+        ("cell_size", C.c_double), ("pcg_cluster_size", C.c_int32),
     ]
 
 
@@ -201,7 +202,7 @@ class Scene:
 
     def __init__(self, scene: _scenes.Scene, precision: Optional[int] = None, tol_scale: float = 1.0,
                  torch_alloc: bool = True, kappa: Optional[float] = None, pcg_kind: int = 0,
-                 warm_start: int = 0):
+                 warm_start: int = 0, cell_size: float = 0.0, pcg_cluster_size: int = 0):
         L = lib()
         p = scene.params
         P = Params()
@@ -221,6 +222,8 @@ class Scene:
         P.n_envs = scene.n_envs
         P.pcg_kind = pcg_kind
         P.warm_start = warm_start
+        P.cell_size = cell_size
+        P.pcg_cluster_size = pcg_cluster_size
         P.stream = _stream()
         if torch_alloc:
             P.alloc = _ALLOC

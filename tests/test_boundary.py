@@ -69,6 +69,7 @@ def test_default_params_match_the_header():
     assert tuple(p.gravity) == (0.0, -9.81, 0.0)
     assert (p.max_newton, p.max_pcg, p.max_al_rounds) == (100, 10000, 10)
     assert (p.precision, p.n_envs, p.warm_start, p.pcg_kind) == (0, 1, 0, 0)
+    assert (p.cell_size, p.pcg_cluster_size) == (0.0, 0)
     assert not p.stream and not p.alloc and not p.free
 
 
