@@ -88,9 +88,10 @@ typedef struct {
      * bit as the whole batch does. */
     double cell_size;      /* spatial-hash cell edge (m); <= 0: the mean surface edge length, at
                               least dhat */
-    int32_t pcg_cluster_size; /* CTAs per env of the cluster solve (1, 2, 4, 8 or 16); 0: about one per
-                                 128 nodes or the autotuner's choice.  A size the scene or device cannot
-                                 run makes zema_step return ZEMA_ERR_INVALID_ARG */
+    int32_t pcg_cluster_size; /* cluster schedule of the solve: CTAs per env (1, 2, 4, 8 or 16), plus 100
+                                 for the two-CTAs-per-SM variant (see zema_get_tuning); 0: about one CTA
+                                 per 128 nodes or the autotuner's choice.  A schedule the scene or device
+                                 cannot run makes zema_step return ZEMA_ERR_INVALID_ARG */
 } zema_scene_params;
 
 /* Per-step statistics (summed over the steps of one zema_step call, over all

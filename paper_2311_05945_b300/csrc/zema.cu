@@ -2315,8 +2315,9 @@ zema_status zema_create_scene(const zema_scene_params* params, zema_scene** out)
     if (!params || !out) return ZEMA_ERR_INVALID_ARG;
     if (!(params->dt > 0) || !(params->dhat > 0) || params->n_envs < 1 || !(params->eps_v > 0) ||
         params->pcg_kind < 0 || params->pcg_kind > 2 || !(params->cell_size < INFINITY) ||
-        (params->pcg_cluster_size != 0 && params->pcg_cluster_size != 1 && params->pcg_cluster_size != 2 &&
-         params->pcg_cluster_size != 4 && params->pcg_cluster_size != 8 && params->pcg_cluster_size != 16))
+        (params->pcg_cluster_size != 0 && (params->pcg_cluster_size % 100 == 0 || params->pcg_cluster_size > 116 ||
+                                           (16 % (params->pcg_cluster_size % 100)) != 0 ||
+                                           (params->pcg_cluster_size > 16 && params->pcg_cluster_size < 101))))
         return ZEMA_ERR_INVALID_ARG;
     zema_scene* s = new (std::nothrow) zema_scene();
     if (!s) return ZEMA_ERR_OOM;

@@ -40,7 +40,7 @@ def run(scene, steps, warm_start, blob):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--weights", required=True)
-    ap.add_argument("--envs", type=int, default=8)
+    ap.add_argument("--envs", type=int, default=64)
     ap.add_argument("--steps", type=int, default=120)
     ap.add_argument("--seed0", type=int, default=100000)
     ap.add_argument("--out", default=None)

@@ -1,7 +1,9 @@
 """Train the learned Newton warm start on trajectories the stepper generates.
 
-Data: the batched grasp scene (training seeds 1000...) and the single-env
-grasp, stepped with the default constant-velocity warm start; every step
+Data: the batched grasp scene (training seeds 1000-1255 by default: 256 envs
+x 200 steps, the 50k env-steps of the learned-warm-start configuration) and
+the single-env grasp, stepped with the default constant-velocity warm start;
+every step
 records each soft vertex's 13 features at the step's start and its
 displacement over the step beyond h v^t (both scaled by h^2 |g|).  Training: the
 library's tensor-core MLP (13 -> 128 -> 128 -> 128 -> 3), mean squared error,
@@ -48,10 +50,10 @@ def collect(scene, steps, log):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", required=True)
-    ap.add_argument("--envs", type=int, default=16, help="training envs of the batched grasp")
-    ap.add_argument("--steps", type=int, default=120, help="recorded steps per scene")
-    ap.add_argument("--c2-steps", type=int, default=150)
-    ap.add_argument("--iters", type=int, default=3000)
+    ap.add_argument("--envs", type=int, default=256, help="training envs of the batched grasp (seeds 1000...)")
+    ap.add_argument("--steps", type=int, default=200, help="recorded steps per scene")
+    ap.add_argument("--c2-steps", type=int, default=300)
+    ap.add_argument("--iters", type=int, default=20000)
     ap.add_argument("--batch", type=int, default=65536)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--seed", type=int, default=7)
@@ -69,7 +71,8 @@ def main():
     log("collecting trajectories")
     parts = [collect(S.scene_c3(n_envs=args.envs, n_steps=args.steps), args.steps, log)]
     if args.c2_steps:
-        parts.append(collect(S.scene_c2(), args.c2_steps, log))
+        parts.append(collect(S.scene_c2(n_steps=args.c2_steps), args.c2_steps, log))
+    report["env_steps"] = args.envs * args.steps + args.c2_steps
     X = torch.cat([p[0] for p in parts]).contiguous()
     Y = torch.cat([p[1] for p in parts]).contiguous()
     ok = torch.isfinite(X).all(1) & torch.isfinite(Y).all(1)

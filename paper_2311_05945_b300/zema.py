@@ -278,14 +278,17 @@ class Scene:
         _check(lib().zema_autotune(self.h), self.h)
 
     def tuning(self, precision=None):
-        """(cluster size in use, {candidate: solve ms}) of the autotuner."""
+        """(cluster schedule in use, {candidate: solve ms}) of the autotuner;
+        a schedule is the CTAs per env, plus 100 for the two-CTAs-per-SM
+        variant."""
         p = self._P.precision if precision is None else precision
         cs, n = C.c_int32(), C.c_int32()
-        cand = np.zeros(8, dtype=np.int32)
-        ms = np.zeros(8, dtype=np.float32)
-        _check(lib().zema_get_tuning(self.h, p, C.byref(cs), _ip(cand), ms.ctypes.data_as(C.POINTER(C.c_float)), 8,
+        cap = 32
+        cand = np.zeros(cap, dtype=np.int32)
+        ms = np.zeros(cap, dtype=np.float32)
+        _check(lib().zema_get_tuning(self.h, p, C.byref(cs), _ip(cand), ms.ctypes.data_as(C.POINTER(C.c_float)), cap,
                                      C.byref(n)), self.h)
-        return cs.value, {int(cand[i]): float(ms[i]) for i in range(n.value)}
+        return cs.value, {int(cand[i]): float(ms[i]) for i in range(min(n.value, cap))}
 
     def load_warmstart(self, dims, theta):
         """Load a learned warm-start network: per soft vertex (dims[0] = 13,

@@ -153,3 +153,23 @@ def test_autotuned_cluster_solve_keeps_parity():
     diag = orc.diag()
     err = np.abs(env_positions(orc, sc, 0) - env_positions(gpu, sc, 0)).max()
     assert err < 1e-5 * diag, err / diag
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("schedule", [2, 102, 104])
+def test_cluster_schedules_keep_parity(precision, schedule):
+    # both residency variants of the cluster solve (one CTA per SM with the
+    # matrix slice staged in shared memory; two per SM, matrix through L1/L2)
+    # at pinned cluster sizes: one tight step from the oracle's in-contact C1
+    # state lands on the oracle's step
+    sc = S.scene_c1()
+    orc = Oracle(sc, tol_scale=1e-2)
+    orc.step(12)
+    gpu = gpu_scene(sc, tol_scale=1e-2, precision=precision, pcg_cluster_size=schedule)
+    transplant(orc, gpu, sc)
+    orc.step(1)
+    gpu.step(1)
+    assert gpu.tuning()[0] == schedule
+    diag = orc.diag()
+    err = np.abs(env_positions(orc, sc, 0) - env_positions(gpu, sc, 0)).max()
+    assert err < 1e-5 * diag, err / diag
