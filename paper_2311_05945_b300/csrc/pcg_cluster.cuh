@@ -53,6 +53,7 @@ struct PcgcArgs {
     int max_aff;         // affine bodies per env, max over envs
     int slice_cap;       // blocks of a CTA's matrix slice that fit in shared memory (0: never staged)
     int chunk_cap;       // SpMV chunks a CTA can hold (more: one task per row instead)
+    const int* env_list; // nullable: cluster k solves env env_list[k] (a group of envs), else env k
 };
 
 constexpr int kPcgcThreads = 512;
@@ -204,7 +205,7 @@ __global__ void __launch_bounds__(kPcgcThreads, kMinBlocks) k_pcg_cluster(PcgcAr
     const Geo& G = a.G;
     const int cs = (int)cl.num_blocks();
     const int rank = (int)cl.block_rank();
-    const int e = blockIdx.x / cs;
+    const int e = a.env_list ? a.env_list[blockIdx.x / cs] : (int)(blockIdx.x / cs);
     if (e >= G.n_envs) return;       // whole cluster (grid is n_envs * cs)
     if (a.conv[e] != 0) return;      // whole cluster: env needs no solve
 

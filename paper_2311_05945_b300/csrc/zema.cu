@@ -118,6 +118,12 @@ struct zema_scene {
     bool pcgc_tune[2] = {false, false};  // autotune the cluster size at the next solve
     std::vector<std::pair<int, float>> pcgc_tuned[2];  // (cluster size, solve ms) measured by the autotuner
     int pcgc_max_env_nodes = 0, pcgc_max_soft = 0, pcgc_max_aff = 0;
+    std::vector<int> env_soft_h;  // soft nodes per env
+    // size-binned schedules, per multiplier m: the envs of each cluster size
+    // 1, 2, 4, 8, 16 (groups in that order) in one device list, and the 6
+    // group offsets
+    DBuf<int> pcgc_bin_list[3];
+    std::vector<int> pcgc_bin_off[3];
     std::vector<int> S_rowptr_h;  // host copy of the static pattern's row pointers
     std::map<std::pair<int, int>, int> pcgc_cap;  // (value size, CTAs per env) -> staged slice capacity
     DBuf<double> tolv;
@@ -604,6 +610,7 @@ void build(zema_scene* s) {
         s->pcgc_max_env_nodes = std::max(s->pcgc_max_env_nodes, env_node_start[e + 1] - env_node_start[e]);
         s->pcgc_max_soft = std::max(s->pcgc_max_soft, nsoft);
         s->pcgc_max_aff = std::max(s->pcgc_max_aff, na);
+        s->env_soft_h.push_back(nsoft);
     }
     up(s, s->tile_u0, tu0);
     up(s, s->tile_u1, tu1);
@@ -1347,9 +1354,13 @@ constexpr size_t kPcgcMaxSmem = 200 * 1024;
 constexpr size_t kPcgcMaxSmem2 = 104 * 1024;
 
 // A cluster schedule code: CTAs per env (1..16), plus 100 for the variant
-// that keeps two CTAs resident per SM.
+// that keeps two CTAs resident per SM; plus 1000 for the size-binned form,
+// where the low digits are a multiplier m (1 or 2) and every env runs with
+// m times the smallest cluster whose CTAs hold its rows (at most 16), one
+// launch per cluster size.
+inline bool sched_binned(int code) { return code >= 1000; }
 inline int sched_cs(int code) { return code % 100; }
-inline int sched_occ(int code) { return code >= 100 ? 2 : 1; }
+inline int sched_occ(int code) { return (code % 1000) >= 100 ? 2 : 1; }
 template <class T>
 inline auto pcgc_kernel(int code) {
     return sched_occ(code) == 2 ? k_pcg_cluster<T, 2> : k_pcg_cluster<T, 1>;
@@ -1358,6 +1369,7 @@ inline auto pcgc_kernel(int code) {
 // rows a CTA may own (the solve balances rows by their blocks within this
 // bound): twice the equal share, at most what its threads hold in registers
 int pcgc_max_rows(const zema_scene* s, int code) {
+    if (sched_binned(code)) return kPcgcOwn * kPcgcThreads + 1;  // every group's bound
     const int cs = sched_cs(code);
     return std::min(2 * ((s->pcgc_max_soft + cs - 1) / cs) + 1, kPcgcOwn * kPcgcThreads + 1);
 }
@@ -1387,7 +1399,7 @@ int pcgc_slice_cap(const zema_scene* cs_scene, int code) {
     auto hit = s->pcgc_cap.find(key);
     if (hit != s->pcgc_cap.end()) return hit->second;
     const int cs = sched_cs(code);
-    if (sizeof(T) != sizeof(float) || sched_occ(code) == 2) {  // staged in FP32 one-per-SM solves only
+    if (sizeof(T) != sizeof(float) || sched_occ(code) == 2 || sched_binned(code)) {  // staged: FP32, one per SM, uniform
         s->pcgc_cap[key] = 0;
         return 0;
     }
@@ -1420,10 +1432,36 @@ size_t pcgc_smem(const zema_scene* s, int code) {
     return pcgc_smem_base<T>(s, code) + (size_t)pcgc_slice_cap<T>(s, code) * 12 * sizeof(float);
 }
 
+// The env groups of a size-binned schedule with multiplier m (built once):
+// env e runs with cs_e = min(16, m * c_e) CTAs, c_e the smallest power of two
+// whose CTAs hold the env's soft rows; groups by cs in the order 1, 2, 4,
+// 8, 16.  Returns the 6 group offsets into s->pcgc_bin_list[m].
+const std::vector<int>& pcgc_bins(zema_scene* s, int m) {
+    std::vector<int>& off = s->pcgc_bin_off[m];
+    if (!off.empty()) return off;
+    std::vector<int> grp[5];
+    for (int e = 0; e < s->n_envs; ++e) {
+        int c = 1;
+        while (c < 16 && (s->env_soft_h[e] + c - 1) / c > kPcgcOwn * kPcgcThreads) c *= 2;
+        int k = 0;
+        for (int cs = std::min(16, m * c); cs > 1; cs /= 2) ++k;
+        grp[k].push_back(e);
+    }
+    std::vector<int> list;
+    off.push_back(0);
+    for (int k = 0; k < 5; ++k) {
+        list.insert(list.end(), grp[k].begin(), grp[k].end());
+        off.push_back((int)list.size());
+    }
+    up(s, s->pcgc_bin_list[m], list);
+    return off;
+}
+
 template <class T>
-void pcgc_config(const zema_scene* s, int code, cudaLaunchConfig_t& cfg, cudaLaunchAttribute* at) {
-    const int cs = sched_cs(code);
-    cfg.gridDim = dim3((unsigned)(cs * s->n_envs));
+void pcgc_config(const zema_scene* s, int code, cudaLaunchConfig_t& cfg, cudaLaunchAttribute* at, int cs_group = 0,
+                 int n_group = 0) {
+    const int cs = cs_group ? cs_group : sched_cs(code);
+    cfg.gridDim = dim3((unsigned)(cs * (cs_group ? n_group : s->n_envs)));
     cfg.blockDim = dim3(kPcgcThreads);
     cfg.dynamicSmemBytes = pcgc_smem<T>(s, code);
     at[0].id = cudaLaunchAttributeClusterDimension;
@@ -1481,6 +1519,24 @@ int pcgc_choose(zema_scene* s) {
 // whether cluster size cs can run the cluster solve of this scene
 template <class T>
 bool pcgc_valid(zema_scene* s, int code) {
+    if (sched_binned(code)) {
+        const int m = sched_cs(code);
+        if ((m != 1 && m != 2) || pcgc_smem<T>(s, code) > (sched_occ(code) == 2 ? kPcgcMaxSmem2 : kPcgcMaxSmem))
+            return false;
+        const std::vector<int>& off = pcgc_bins(s, m);
+        for (int k = 0, cs = 1; k < 5; ++k, cs *= 2) {
+            if (off[k + 1] == off[k]) continue;
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute at[1];
+            pcgc_config<T>(s, code, cfg, at, cs, off[k + 1] - off[k]);
+            int ncl = 0;
+            if (cudaOccupancyMaxActiveClusters(&ncl, pcgc_kernel<T>(code), &cfg) != cudaSuccess || ncl < 1) {
+                cudaGetLastError();
+                return false;
+            }
+        }
+        return true;
+    }
     const int cs = sched_cs(code);
     if (cs < 1 || cs > 16 || (s->pcgc_max_soft + cs - 1) / cs > kPcgcOwn * kPcgcThreads ||
         pcgc_smem<T>(s, code) > (sched_occ(code) == 2 ? kPcgcMaxSmem2 : kPcgcMaxSmem))
@@ -1567,6 +1623,7 @@ int64_t pcg_t(zema_scene* s, const std::vector<int>& done_h) {
         c.max_aff = s->pcgc_max_aff;
         c.slice_cap = pcgc_slice_cap<T>(s, cs);
         c.chunk_cap = pcgc_chunk_cap(s, cs);
+        c.env_list = nullptr;
         cudaLaunchConfig_t cfg = {};
         cudaLaunchAttribute at[1];
         pcgc_config<T>(s, cs, cfg, at);
@@ -1579,6 +1636,21 @@ int64_t pcg_t(zema_scene* s, const std::vector<int>& done_h) {
             const int pct = (int)std::min<size_t>(
                 100, (100 * 2 * (cfg.dynamicSmemBytes + 8192) + smem_sm - 1) / std::max(1, smem_sm));
             ZCHECK(cudaFuncSetAttribute(k_pcg_cluster<T, 2>, cudaFuncAttributePreferredSharedMemoryCarveout, pct));
+        }
+        if (sched_binned(cs)) {
+            // one launch per env group, each with its own cluster size
+            const std::vector<int>& off = pcgc_bins(s, sched_cs(cs));
+            for (int k = 0, cg = 1; k < 5; ++k, cg *= 2) {
+                const int ng = off[k + 1] - off[k];
+                if (!ng) continue;
+                c.env_list = s->pcgc_bin_list[sched_cs(cs)].p + off[k];
+                pcgc_config<T>(s, cs, cfg, at, cg, ng);
+                cfg.stream = st;
+                LaunchScope ls("k_pcg_cluster");
+                ZCHECK(cudaLaunchKernelEx(&cfg, pcgc_kernel<T>(cs), c));
+            }
+            ZLAUNCH();
+            return;
         }
         {
             LaunchScope ls("k_pcg_cluster");
@@ -1645,7 +1717,7 @@ int64_t pcg_t(zema_scene* s, const std::vector<int>& done_h) {
         ZCHECK(cudaEventCreate(&e1));
         float best = INFINITY;
         int best_cs = s->pcgc_cs[pi];
-        for (int code : {1, 2, 4, 8, 16, 101, 102, 104, 108, 116}) {
+        for (int code : {1, 2, 4, 8, 16, 101, 102, 104, 108, 116, 1001, 1002, 1101, 1102}) {
             const int cs = code;
             if (!pcgc_valid<T>(s, cs)) continue;
             float ms = INFINITY;
@@ -2314,11 +2386,15 @@ void zema_default_params(zema_scene_params* p) {
 zema_status zema_create_scene(const zema_scene_params* params, zema_scene** out) {
     if (!params || !out) return ZEMA_ERR_INVALID_ARG;
     if (!(params->dt > 0) || !(params->dhat > 0) || params->n_envs < 1 || !(params->eps_v > 0) ||
-        params->pcg_kind < 0 || params->pcg_kind > 2 || !(params->cell_size < INFINITY) ||
-        (params->pcg_cluster_size != 0 && (params->pcg_cluster_size % 100 == 0 || params->pcg_cluster_size > 116 ||
-                                           (16 % (params->pcg_cluster_size % 100)) != 0 ||
-                                           (params->pcg_cluster_size > 16 && params->pcg_cluster_size < 101))))
+        params->pcg_kind < 0 || params->pcg_kind > 2 || !(params->cell_size < INFINITY))
         return ZEMA_ERR_INVALID_ARG;
+    if (params->pcg_cluster_size != 0) {
+        // a schedule code: 1..16 (powers of two), + 100, or binned 1001, 1002, 1101, 1102
+        const int v = params->pcg_cluster_size, low = v % 100;
+        const bool uniform = (v < 100 || (v > 100 && v < 200)) && low > 0 && low <= 16 && (low & (low - 1)) == 0;
+        const bool binned = v == 1001 || v == 1002 || v == 1101 || v == 1102;
+        if (!uniform && !binned) return ZEMA_ERR_INVALID_ARG;
+    }
     zema_scene* s = new (std::nothrow) zema_scene();
     if (!s) return ZEMA_ERR_OOM;
     s->P = *params;

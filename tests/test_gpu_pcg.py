@@ -156,12 +156,13 @@ def test_autotuned_cluster_solve_keeps_parity():
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-@pytest.mark.parametrize("schedule", [2, 102, 104])
+@pytest.mark.parametrize("schedule", [2, 102, 104, 1001, 1102])
 def test_cluster_schedules_keep_parity(precision, schedule):
     # both residency variants of the cluster solve (one CTA per SM with the
     # matrix slice staged in shared memory; two per SM, matrix through L1/L2)
-    # at pinned cluster sizes: one tight step from the oracle's in-contact C1
-    # state lands on the oracle's step
+    # at pinned cluster sizes, and the size-binned schedules (one launch per
+    # cluster size): one tight step from the oracle's in-contact C1 state
+    # lands on the oracle's step
     sc = S.scene_c1()
     orc = Oracle(sc, tol_scale=1e-2)
     orc.step(12)
@@ -173,3 +174,21 @@ def test_cluster_schedules_keep_parity(precision, schedule):
     diag = orc.diag()
     err = np.abs(env_positions(orc, sc, 0) - env_positions(gpu, sc, 0)).max()
     assert err < 1e-5 * diag, err / diag
+
+
+@pytest.mark.parametrize("schedule", [8, 1001, 1102])
+def test_binned_schedule_on_a_batch_of_uneven_envs(schedule):
+    # envs of 2k-12k tets fall into several cluster-size groups; every env of
+    # the batch stays within the parity bound of the same batch solved with
+    # one uniform schedule (both mixed, tight tolerance)
+    sc = S.scene_c3(n_envs=6, n_steps=24, min_tets=2000, max_tets=12000)
+    ref = gpu_scene(sc, tol_scale=1e-2, precision=1, pcg_cluster_size=16)
+    g = gpu_scene(sc, tol_scale=1e-2, precision=1, pcg_cluster_size=schedule)
+    ref.step(22)
+    g.step(22)
+    assert g.tuning()[0] == schedule
+    for e in range(sc.n_envs):
+        pr, pg = env_positions(ref, sc, e), env_positions(g, sc, e)
+        ext = pr.reshape(-1, 3)
+        diag = float(np.linalg.norm(ext.max(0) - ext.min(0)))
+        assert np.abs(pr - pg).max() < 1e-5 * diag, (e, np.abs(pr - pg).max() / diag)
