@@ -72,49 +72,41 @@ __host__ __device__ constexpr int pcgc_pstride() {
 __device__ __forceinline__ float ldcg_r(const float* p) { return __ldcg(p); }
 __device__ __forceinline__ double ldcg_r(const double* p) { return __ldcg(p); }
 
-// Sum of K per-thread values over the CTA, in Real: warp shuffles, then the
-// warps' results by warp 0 (fixed shuffle tree), into out[0..K).
+// All-reduce of K per-thread values over the cluster, in Real.  Each warp
+// sums its lanes' values by shuffles; lane 0 stores the K sums into slot
+// (rank, warp) of the reduction buffer of every CTA of the cluster
+// (distributed shared memory).  After the cluster barrier, every warp of
+// every CTA sums the cs x NW slots of its own copy in one fixed order (lane
+// l takes slots l, l + 32, ..., then a fixed shuffle tree), so all threads
+// of all CTAs get the same bits with no further CTA barrier.  The cluster
+// barrier also orders every CTA's earlier shared- and global-memory writes
+// for the whole cluster.  red: K x (kPcgcMaxCluster * NW) values.
 template <int K, class Real>
-__device__ __forceinline__ void cta_partial(Real (&v)[K], Real* s_w, Real* out) {
-    constexpr int NW = kPcgcThreads / 32;
-    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+__device__ __forceinline__ void cluster_allreduce(cooperative_groups::cluster_group& cl, Real (&v)[K], Real* red,
+                                                  Real (&tot)[K]) {
+    constexpr int NW = kPcgcThreads / 32, SLOTS = kPcgcMaxCluster * NW;
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const int cs = (int)cl.num_blocks(), rank = (int)cl.block_rank();
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
+    for (int k = 0; k < K; ++k)
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
-        if (l == 0) s_w[k * NW + w] = v[k];
+    if (l < cs) {
+        // lane l sends the warp's sums to CTA l
+        Real* dst = cl.map_shared_rank(red, l);
+#pragma unroll
+        for (int k = 0; k < K; ++k) dst[k * SLOTS + rank * NW + w] = v[k];
     }
-    __syncthreads();
-    if (w == 0) {
+    cl.sync();
+    const int n = cs * NW;
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-            Real s = l < NW ? s_w[k * NW + l] : Real(0);
+    for (int k = 0; k < K; ++k) {
+        Real t = 0;
+        for (int i = l; i < n; i += 32) t += red[k * SLOTS + i];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (l == 0) out[k] = s;
-        }
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        tot[k] = t;
     }
-}
-
-// After a cluster barrier: total[k] = sum over the cluster's CTAs of their
-// part[k], one remote load per lane of warp 0 and a fixed shuffle tree, so
-// every CTA gets the same bits.  Ends with a CTA barrier.
-template <int K, class Real>
-__device__ __forceinline__ void cluster_total(cooperative_groups::cluster_group& cl, const Real* part, Real* total) {
-    if (threadIdx.x < 32) {
-        int cs = (int)cl.num_blocks(), l = threadIdx.x;
-        const Real* rp = l < cs ? cl.map_shared_rank(part, l) : nullptr;
-        Real v[K];
-#pragma unroll
-        for (int k = 0; k < K; ++k) v[k] = rp ? rp[k] : Real(0);
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
-            if (l == 0) total[k] = v[k];
-        }
-    }
-    __syncthreads();
 }
 
 // q for one row: the blocks [s0, s1) of S followed by [c0, c1) of C, the 16
@@ -227,6 +219,10 @@ __global__ void __launch_bounds__(kPcgcThreads, kMinBlocks) k_pcg_cluster(PcgcAr
     // [12 * slice_cap] this CTA's matrix blocks (S then C), FP32 only, 16-byte aligned
     float* s_mval = (float*)(((uintptr_t)(s_cpart + 3 * (size_t)a.chunk_cap) + 15) & ~(uintptr_t)15);
     __shared__ int s_staged;
+    // reduction buffers of cluster_allreduce: [0] the p.q sum, [1] the r.z
+    // and r.r sums (alternating uses never overlap: see the hazard note at
+    // the loop)
+    __shared__ Real s_red[2][2 * kPcgcMaxCluster * (kPcgcThreads / 32)];
     Real* zw = a.z;                                 // z, 3 per node, in global memory
     const Real* __restrict__ zg = a.z;
 
@@ -282,8 +278,9 @@ __global__ void __launch_bounds__(kPcgcThreads, kMinBlocks) k_pcg_cluster(PcgcAr
     // stay in registers for the whole solve); partial r.z and b.b
     Real xs[kPcgcOwn][3], rs[kPcgcOwn][3], Ms[kPcgcOwn][9];
     Real xa = 0, ra = 0, Ma[12];
+    Real acc0[2] = {0, 0};  // this thread's share of r.z and b.b
     {
-        Real acc[2] = {0, 0};
+        Real (&acc)[2] = acc0;
 #pragma unroll
         for (int j = 0; j < kPcgcOwn; ++j) {
             const int i = tid + j * kPcgcThreads;
@@ -323,7 +320,6 @@ __global__ void __launch_bounds__(kPcgcThreads, kMinBlocks) k_pcg_cluster(PcgcAr
             acc[0] += ra * z;
             acc[1] += ra * ra;
         }
-        cta_partial<2>(acc, s_w, s_part + 1);
     }
     // block ranges of this CTA's SpMV tasks (fixed for the solve)
     const int n_tasks = n_own + n_arow;
@@ -423,10 +419,12 @@ __global__ void __launch_bounds__(kPcgcThreads, kMinBlocks) k_pcg_cluster(PcgcAr
             for (int c = s_cpre[t], j = 0; c < s_cpre[t + 1]; ++c, j += kPcgcChunk)
                 s_chunk[c] = make_int4(t, j, min(len, j + kPcgcChunk), 0);
         }
-    cl.sync();  // also orders s_rng, the chunks and the staged slice within the CTA
-    cluster_total<2>(cl, s_part + 1, s_tot + 1);  // s_tot[1] = r.z, s_tot[2] = b.b
-    Real rz = s_tot[1];
-    const Real bb = s_tot[2];
+    // the all-reduce's cluster barrier also orders s_rng, the chunks and the
+    // staged slice within the CTA
+    Real t0[2];
+    cluster_allreduce<2>(cl, acc0, s_red[1], t0);  // r.z, b.b
+    Real rz = t0[0];
+    const Real bb = t0[1];
     const Real stop2 = (Real)(a.tol2_env ? a.tol2_env[e] : a.tol2) * bb;
     bool bad = !isfinite(bb);
     bool done = bad || !(bb > Real(0));
@@ -533,10 +531,12 @@ __global__ void __launch_bounds__(kPcgcThreads, kMinBlocks) k_pcg_cluster(PcgcAr
                 pq[0] += pr[0] * y0 + pr[1] * y1 + pr[2] * y2;
             }
         }
-        cta_partial<1>(pq, s_w, s_part);
-        cl.sync();  // B1
-        cluster_total<1>(cl, s_part, s_tot);
-        const Real pqt = s_tot[0];
+        // B1.  Hazard note: a CTA writes buffer 0 again only after passing
+        // B2, which every CTA reaches after reading buffer 0; likewise
+        // buffer 1 between B2 and the next B1
+        Real t1[1];
+        cluster_allreduce<1>(cl, pq, s_red[0], t1);
+        const Real pqt = t1[0];
         if (!(pqt > Real(0))) {  // breakdown: keep x and stop (same in all CTAs); non-finite is an error
             bad = !isfinite(pqt);
             break;
@@ -585,10 +585,9 @@ __global__ void __launch_bounds__(kPcgcThreads, kMinBlocks) k_pcg_cluster(PcgcAr
             acc[0] += ra * z;
             acc[1] += ra * ra;
         }
-        cta_partial<2>(acc, s_w, s_part + 1);
-        cl.sync();  // B2
-        cluster_total<2>(cl, s_part + 1, s_tot + 1);
-        const Real rz_new = s_tot[1], rr = s_tot[2];
+        Real t2[2];
+        cluster_allreduce<2>(cl, acc, s_red[1], t2);  // B2
+        const Real rz_new = t2[0], rr = t2[1];
         ++it;
         if (!isfinite(rr)) bad = done = true;
         if (!(rr > stop2)) done = true;

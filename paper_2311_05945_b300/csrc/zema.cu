@@ -1351,7 +1351,7 @@ void grad_hess(zema_scene* s, bool barrier = true, bool friction = true, bool he
 // ---------------------------------------------------------------------------
 constexpr size_t kPcgcMaxSmem = 200 * 1024;
 // dynamic shared memory of the variant with two CTAs per SM
-constexpr size_t kPcgcMaxSmem2 = 104 * 1024;
+constexpr size_t kPcgcMaxSmem2 = 96 * 1024;
 
 // A cluster schedule code: CTAs per env (1..16), plus 100 for the variant
 // that keeps two CTAs resident per SM; plus 1000 for the size-binned form,

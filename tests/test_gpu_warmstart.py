@@ -63,11 +63,13 @@ def test_recorded_features_and_targets_match_states():
 
 
 def test_learned_start_converges_and_follows_the_plain_run():
+    # at 1e-2 of the Newton tolerance both starts converge to the same
+    # minimiser step after step: positions within the parity bound
     from paper_2311_05945_b300.zema import Scene, read_warmstart_blob
     dims, theta = read_warmstart_blob(open(WEIGHTS, "rb").read())
     sc = S.scene_c3(n_envs=2, n_steps=40, min_tets=2000, max_tets=6000, seed0=100100)
-    a = Scene(sc, warm_start=0)
-    b = Scene(sc, warm_start=1)
+    a = Scene(sc, warm_start=0, tol_scale=1e-2)
+    b = Scene(sc, warm_start=1, tol_scale=1e-2)
     b.load_warmstart(dims, theta)
     na = nb = 0
     for k in range(30):
@@ -75,11 +77,41 @@ def test_learned_start_converges_and_follows_the_plain_run():
         na += sa["newton_iters"]
         nb += sb["newton_iters"]
         assert sb["dmin"] > 0
-    diag = max(np.ptp(np.asarray(bd.X), axis=0).max() for bd in sc.tets)
-    for i in range(len(sc.tets)):
-        err = np.abs(a.tet_positions(i) - b.tet_positions(i)).max()
-        assert err < 1e-2 * diag, (i, err)
+    for i, bd in enumerate(sc.tets):
+        pa = a.tet_positions(i)
+        diag = float(np.linalg.norm(pa.max(0) - pa.min(0)))
+        err = np.abs(pa - b.tet_positions(i)).max()
+        assert err < 1e-5 * diag, (i, err / diag)
     print(f"Newton iterations over 30 steps: constant-velocity {na}, learned {nb}")
+
+
+def test_measured_iteration_ratio_on_held_out_envs():
+    # the learned start at the scale it was trained and evaluated at (the
+    # committed report: 51,500 env-steps of training, 64 held-out envs x 120
+    # steps) costs Newton iterations instead of saving them; a live sample of
+    # 8 held-out envs through first contact measures the same: a ratio above
+    # 1 and bounded, since the plain start and the energy checks keep every
+    # step converging to the same tolerance
+    import json
+
+    from paper_2311_05945_b300.zema import Scene, read_warmstart_blob
+    rep = json.load(open(os.path.join(os.path.dirname(WEIGHTS), "warmstart_eval.json")))
+    assert rep["envs"] == 64 and rep["steps"] == 120 and rep["seed0"] == 100000
+    assert 1.0 <= rep["newton_ratio"] <= 1.25
+    dims, theta = read_warmstart_blob(open(WEIGHTS, "rb").read())
+    sc = S.scene_c3(n_envs=8, n_steps=40, seed0=100000)
+    its = []
+    for ws in (0, 1):
+        g = Scene(sc, warm_start=ws)
+        if ws:
+            g.load_warmstart(dims, theta)
+        st = g.step(36)
+        its.append(st["newton_iters"])
+        g.close()
+    ratio = its[1] / its[0]
+    print(f"Newton iterations, 8 held-out envs x 36 steps: constant-velocity {its[0]}, learned {its[1]} "
+          f"(ratio {ratio:.3f})")
+    assert 0.95 <= ratio <= 1.25
 
 
 def test_network_predicts_held_out_steps_better_than_constant_velocity():
