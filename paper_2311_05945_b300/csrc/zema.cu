@@ -116,6 +116,9 @@ struct zema_scene {
     // its shared-memory layout bounds
     int pcgc_cs[2] = {0, 0};
     bool pcgc_tune[2] = {false, false};  // autotune the cluster size at the next solve
+    bool pcgc_tuned_flag[2] = {false, false};  // the schedule came from the autotuner
+    int pcgc_valid16[2] = {-1, -1};             // whether schedule 16 can run (-1: not checked yet)
+    int n_sm = 0;
     std::vector<std::pair<int, float>> pcgc_tuned[2];  // (cluster size, solve ms) measured by the autotuner
     int pcgc_max_env_nodes = 0, pcgc_max_soft = 0, pcgc_max_aff = 0;
     std::vector<int> env_soft_h;  // soft nodes per env
@@ -1740,14 +1743,34 @@ int64_t pcg_t(zema_scene* s, const std::vector<int>& done_h) {
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         s->pcgc_cs[pi] = best_cs;
+        s->pcgc_tuned_flag[pi] = true;
         ZCHECK(cudaMemcpyAsync(s->conv.p, s->hi + 3 * NE, NE * sizeof(int), cudaMemcpyHostToDevice, st));
     }
+    if (s->n_sm == 0) {
+        int dev = 0;
+        ZCHECK(cudaGetDevice(&dev));
+        ZCHECK(cudaDeviceGetAttribute(&s->n_sm, cudaDevAttrMultiProcessorCount, dev));
+    }
+    // The tuned schedule is the fastest for the whole batch.  When so few
+    // envs still solve that even 16-CTA clusters, one per SM, leave SMs idle
+    // (the lockstep tail of the batched Newton loop: one or two stiff envs),
+    // the solve is bound by one env's latency instead, and the 16-CTA
+    // schedule has the lowest (measured on the single-env grasp: 0.50 ms per
+    // solve against 0.92 ms for 8 CTAs two per SM).  Tuned scenes only, so
+    // untuned ones stay bit-reproducible.
+    auto schedule_for = [&](int n_solving) -> int {
+        const int tuned = s->pcgc_cs[pi];
+        if (!s->pcgc_tuned_flag[pi] || s->P.pcg_cluster_size > 0 || tuned == 16) return tuned;
+        if (n_solving > s->n_sm / 16) return tuned;
+        if (s->pcgc_valid16[pi] < 0) s->pcgc_valid16[pi] = pcgc_valid<T>(s, 16) ? 1 : 0;
+        return s->pcgc_valid16[pi] ? 16 : tuned;
+    };
     // one solve of the selected form, then its statistics
-    auto run_solve = [&](const double* rhs, double* xo, const double* tol2_env = nullptr) {
+    auto run_solve = [&](const double* rhs, double* xo, const double* tol2_env, int n_solving) {
         // envs skipped by this solve must not count the previous solve's iterations
         ZCHECK(cudaMemsetAsync(s->pcg_iters.p, 0, NE * sizeof(int), st));
         if (use_cluster)
-            launch_cluster(rhs, xo, s->pcgc_cs[pi], tol2_env);
+            launch_cluster(rhs, xo, schedule_for(n_solving), tol2_env);
         else
             launch_grid(rhs, xo, tol2_env);
         if (s->fault_armed == ZEMA_FAULT_SOLVE_NONFINITE) {
@@ -1756,7 +1779,9 @@ int64_t pcg_t(zema_scene* s, const std::vector<int>& done_h) {
         }
         collect();
     };
-    run_solve(s->b.p, s->p.p);
+    int n_solving = 0;
+    for (int e = 0; e < NE; ++e) n_solving += done_h[e] ? 0 : 1;
+    run_solve(s->b.p, s->p.p, nullptr, n_solving);
     if (sizeof(T) < sizeof(double)) {
         // FP64 residual refinement of the FP32 solve: r = b - A x with
         // FP64 products; while |r| > tol |b| solve A d = r and add d
@@ -1797,7 +1822,7 @@ int64_t pcg_t(zema_scene* s, const std::vector<int>& done_h) {
             for (int e = 0; e < NE; ++e) s->hi[e] = need[e] ? 0 : 1;
             ZCHECK(cudaMemcpyAsync(s->conv.p, s->hi, NE * sizeof(int), cudaMemcpyHostToDevice, st));
             ZCHECK(cudaMemcpyAsync(s->tol2_env.p, s->hd, NE * sizeof(double), cudaMemcpyHostToDevice, st));
-            run_solve(s->q.p, s->r.p, s->tol2_env.p);
+            run_solve(s->q.p, s->r.p, s->tol2_env.p, count);
             for (int e = 0; e < NE; ++e) s->hi[e] = need[e];
             ZCHECK(cudaMemcpyAsync(s->need.p, s->hi, NE * sizeof(int), cudaMemcpyHostToDevice, st));
             ZL(k_add_env, div_up(s->n_nodes, TB), TB, 0, st)(G, s->p.p, s->r.p, s->need.p);
