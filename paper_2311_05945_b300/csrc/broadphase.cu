@@ -261,7 +261,14 @@ struct Table {
 // per query stride over each cell's bucket; a ballot places the group's hits
 // in entry order, so the output is the serial visiting order (cells in
 // z, y, x order, entries in table order, then the oversize list).
+//
+// WRITE false: the counting pass.  It also keeps the first kQuerySlots hits
+// of each query, in order, in the query's slots (slots[kQuerySlots q ..]);
+// k_slots_out then moves the queries whose hits all fit into the output, and
+// the WRITE pass walks again only the queries with more hits (cnt[q] >
+// kQuerySlots), so most queries are walked once.
 constexpr int kQueryLanes = 16;
+constexpr int kQuerySlots = 8;
 template <bool WRITE>
 __global__ void k_query(BPView v, int kind, int nq, const double* qbox, const double* ebox_all, const int* qcb,
                         const int* ecb_all, Table T, const int* big, int nbig, int n_entries_all, uint32_t* cnt,
@@ -273,6 +280,7 @@ __global__ void k_query(BPView v, int kind, int nq, const double* qbox, const do
         if (!WRITE && l == 0) cnt[q] = 0;
         return;
     }
+    if (WRITE && cnt[q] <= (uint32_t)kQuerySlots) return;  // already out of its slots (or a large query)
     const unsigned gshift = threadIdx.x & 16u;
     const unsigned gmask = 0xFFFFu << gshift;
     Box6 a = ld_box(qbox + 6 * (size_t)q);
@@ -283,10 +291,11 @@ __global__ void k_query(BPView v, int kind, int nq, const double* qbox, const do
         return;
     }
     uint32_t c = 0;  // hits so far, the same in all lanes of the group
-    const uint32_t o = WRITE ? off[q] : 0u;
+    const uint32_t o = WRITE ? off[q] : (uint32_t)kQuerySlots * (uint32_t)q;
     auto emit = [&](bool hit, int e) {
         const unsigned b = (__ballot_sync(gmask, hit) >> gshift) & 0xFFFFu;
-        if (WRITE && hit) out[o + c + __popc(b & ((1u << l) - 1u))] = make_int2(q, e);
+        const uint32_t at = c + __popc(b & ((1u << l) - 1u));
+        if (hit && (WRITE || at < (uint32_t)kQuerySlots)) out[o + at] = make_int2(q, e);
         c += __popc(b);
     };
     auto test = [&](int e) -> bool {
@@ -341,6 +350,19 @@ __global__ void k_query(BPView v, int kind, int nq, const double* qbox, const do
         emit(hit, e);
     }
     if (!WRITE && l == 0) cnt[q] = c;
+}
+
+// Queries whose hits all fit their slots: the hits into the output at the
+// query's offset, in order (large queries, flagged in big_flag, are left to
+// k_query_big; queries with more hits to the WRITE pass of k_query).
+__global__ void k_slots_out(int nq, const uint32_t* cnt, const uint32_t* off, const uint32_t* big_flag,
+                            const int2* slots, int2* out) {
+    const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int q = (int)(gt / kQuerySlots), j = (int)(gt % kQuerySlots);
+    if (q >= nq || big_flag[q]) return;
+    const uint32_t c = cnt[q];
+    if (c > (uint32_t)kQuerySlots || (uint32_t)j >= c) return;
+    out[off[q] + j] = slots[(size_t)kQuerySlots * q + j];
 }
 
 // Block-wide placement: each thread counts the hits of its items, an
@@ -577,12 +599,14 @@ void BroadPhase::run(Allocator* A, const BPView& v, cudaStream_t st) {
     if (nsv) ZL(k_compact_flags, div_up(nsv, TB), TB, 0, st)(pflag.p, pflagoff.p, 0u, nsv, big_p.p);
     if (ne) ZL(k_compact_flags, div_up(ne, TB), TB, 0, st)(pflag.p + nsv, pflagoff.p + nsv, nbp, ne, big_q.p);
     ZLAUNCH();
+    slot_pt.ensure(A, (size_t)kQuerySlots * nsv + 1);
+    slot_ee.ensure(A, (size_t)kQuerySlots * ne + 1);
     if (nsv)
         ZL(k_query<false>, div_up((size_t)nsv * kQueryLanes, TB), TB, 0, st)(v, 0, nsv, pbox.p, tbox.p, pcb.p, tcb.p, TT, big_t.p, (int)nbt, nt,
-                                                       qcnt_pt.p, nullptr, nullptr);
+                                                       qcnt_pt.p, nullptr, slot_pt.p);
     if (ne)
         ZL(k_query<false>, div_up((size_t)ne * kQueryLanes, TB), TB, 0, st)(v, 1, ne, ebox.p, ebox.p, ecb.p, ecb.p, TE, big_e.p, (int)nbe, ne,
-                                                      qcnt_ee.p, nullptr, nullptr);
+                                                      qcnt_ee.p, nullptr, slot_ee.p);
     if (nbp)
         ZL(k_query_big<false>, nbp, 256, 0, st)(v, 0, big_p.p, pbox.p, tbox.p, nt, qcnt_pt.p, nullptr, nullptr, pcb.p,
                                                 tcb.p, TT, big_t.p, (int)nbt);
@@ -600,12 +624,18 @@ void BroadPhase::run(Allocator* A, const BPView& v, cudaStream_t st) {
     n_ee = h_counts[5];
     pt.ensure(A, n_pt + 1);
     ee.ensure(A, n_ee + 1);
-    if (nsv && n_pt)
-        ZL(k_query<true>, div_up((size_t)nsv * kQueryLanes, TB), TB, 0, st)(v, 0, nsv, pbox.p, tbox.p, pcb.p, tcb.p, TT, big_t.p, (int)nbt, nt, nullptr,
-                                                      qoff_pt.p, pt.p);
-    if (ne && n_ee)
-        ZL(k_query<true>, div_up((size_t)ne * kQueryLanes, TB), TB, 0, st)(v, 1, ne, ebox.p, ebox.p, ecb.p, ecb.p, TE, big_e.p, (int)nbe, ne, nullptr,
-                                                     qoff_ee.p, ee.p);
+    if (nsv && n_pt) {
+        ZL(k_slots_out, div_up((size_t)nsv * kQuerySlots, TB), TB, 0, st)(nsv, qcnt_pt.p, qoff_pt.p, pflag.p, slot_pt.p,
+                                                                         pt.p);
+        ZL(k_query<true>, div_up((size_t)nsv * kQueryLanes, TB), TB, 0, st)(v, 0, nsv, pbox.p, tbox.p, pcb.p, tcb.p, TT, big_t.p, (int)nbt, nt,
+                                                      qcnt_pt.p, qoff_pt.p, pt.p);
+    }
+    if (ne && n_ee) {
+        ZL(k_slots_out, div_up((size_t)ne * kQuerySlots, TB), TB, 0, st)(ne, qcnt_ee.p, qoff_ee.p, pflag.p + nsv,
+                                                                        slot_ee.p, ee.p);
+        ZL(k_query<true>, div_up((size_t)ne * kQueryLanes, TB), TB, 0, st)(v, 1, ne, ebox.p, ebox.p, ecb.p, ecb.p, TE, big_e.p, (int)nbe, ne,
+                                                     qcnt_ee.p, qoff_ee.p, ee.p);
+    }
     if (nbp && n_pt)
         ZL(k_query_big<true>, nbp, 256, 0, st)(v, 0, big_p.p, pbox.p, tbox.p, nt, nullptr, qoff_pt.p, pt.p, pcb.p, tcb.p,
                                                TT, big_t.p, (int)nbt);

@@ -42,6 +42,7 @@ struct BroadPhase {
     DBuf<uint32_t> qcnt_pt, qoff_pt, qcnt_ee, qoff_ee;
     DBuf<uint32_t> tmp;
     DBuf<int2> pt, ee;  // outputs: (sv, tri), (edge, edge)
+    DBuf<int2> slot_pt, slot_ee;  // the counting pass's first hits per query
     DBuf<uint32_t> hcount;  // pinned-size mirror of counts on device
     uint32_t n_pt = 0, n_ee = 0;
     uint32_t* h_counts = nullptr;  // pinned host [4]
