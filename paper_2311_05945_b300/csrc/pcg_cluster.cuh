@@ -63,6 +63,7 @@ constexpr int kPcgcStageBatch = 16;  // values of z per thread whose loads are i
 constexpr int kPcgcOwn = 2;         // soft rows per thread: a CTA owns at most 2 * kPcgcThreads rows
 constexpr int kPcgcRefine = 3;      // FP64 residual refinements of an FP32 solve
 constexpr int kPcgcChunk = 8;       // blocks per SpMV chunk
+constexpr int kPcgcRowIlp = 4;      // blocks per lane whose loads are issued together (matrix in L1/L2)
 // values per node of the staged p vector
 template <class Real>
 __host__ __device__ constexpr int pcgc_pstride() {
@@ -165,17 +166,25 @@ template <class Real>
 __device__ __forceinline__ void row_part(const Bsr<Real>& S, const Bsr<Real>& C, int4 g, int jb, int je,
                                          const Real* s_p, int nb, int n_env, int gl, Real& y0, Real& y1, Real& y2) {
     const int ls = g.y - g.x, n = je;
-    // two blocks per iteration (independent accumulators), summed in a fixed order
-    Real u0 = 0, u1 = 0, u2 = 0;
-    int j = jb + gl;
-    for (; j + kPcgcGroup < n; j += 2 * kPcgcGroup) {
-        block_fma(S, C, g, ls, j, s_p, nb, n_env, y0, y1, y2);
-        block_fma(S, C, g, ls, j + kPcgcGroup, s_p, nb, n_env, u0, u1, u2);
+    // kPcgcRowIlp blocks per lane per pass (predicated, independent
+    // accumulators) so that their loads from L1/L2 are in flight together;
+    // the accumulators are summed in a fixed order
+    Real a[kPcgcRowIlp][3];
+#pragma unroll
+    for (int t = 0; t < kPcgcRowIlp; ++t) a[t][0] = a[t][1] = a[t][2] = Real(0);
+    for (int j0 = jb + gl; j0 < n; j0 += kPcgcRowIlp * kPcgcGroup) {
+#pragma unroll
+        for (int t = 0; t < kPcgcRowIlp; ++t) {
+            const int j = j0 + t * kPcgcGroup;
+            if (j < n) block_fma(S, C, g, ls, j, s_p, nb, n_env, a[t][0], a[t][1], a[t][2]);
+        }
     }
-    if (j < n) block_fma(S, C, g, ls, j, s_p, nb, n_env, y0, y1, y2);
-    y0 += u0;
-    y1 += u1;
-    y2 += u2;
+#pragma unroll
+    for (int t = 0; t < kPcgcRowIlp; ++t) {
+        y0 += a[t][0];
+        y1 += a[t][1];
+        y2 += a[t][2];
+    }
 }
 
 template <class Real>

@@ -1877,8 +1877,16 @@ void step_norm(zema_scene* s) {
 // proposal): ACCD bound over the swept candidates, then halving until
 // E(x + alpha dir) <= E(x) per env.  On success x is advanced.  Returns the
 // number of halvings, or -1 when an env fails.
+//
+// e_at_x (nullable, per env): in, the potential at x where known (NaN where
+// not); out, the potential at the new x.  The potential at x does not depend
+// on which swept list its barrier is summed over, as long as the list holds
+// every pair with d < dhat at x, and every list built from a motion that
+// starts at x does; so an env's value from the line search that reached x
+// stands in for a new evaluation (only the order of the sum differs).
 int line_search(zema_scene* s, const double* dir, const std::vector<int>& done_h, bool warm,
-                std::vector<int>* accepted, int warm_halvings = 0, bool strict = false) {
+                std::vector<int>* accepted, int warm_halvings = 0, bool strict = false,
+                std::vector<double>* e_at_x = nullptr) {
     // warm-start proposals get warm_halvings halvings (default: a single energy
     // check), Newton steps up to 60; strict: a step must lower the energy
     // (the learned correction), otherwise it may also keep it equal
@@ -1915,8 +1923,17 @@ int line_search(zema_scene* s, const double* dir, const std::vector<int>& done_h
     ZCHECK(cudaStreamSynchronize(st));
     s->S.ms_phase[4] += now_ms() - t0;
     t0 = now_ms();
-    energy(s, s->x.p, s->swept.p, s->swept_env.p);
-    std::vector<double> E0(s->hd, s->hd + NE);
+    bool need_e0 = e_at_x == nullptr;
+    if (e_at_x)
+        for (int e = 0; e < NE; ++e) need_e0 |= !done_h[e] && std::isnan((*e_at_x)[e]);
+    std::vector<double> E0(NE, 0.0);
+    if (need_e0) {
+        energy(s, s->x.p, s->swept.p, s->swept_env.p);
+        E0.assign(s->hd, s->hd + NE);
+    } else {
+        E0 = *e_at_x;
+    }
+    std::vector<double> Eacc(E0);  // the potential at the accepted point, per env
     std::vector<int> acc(NE, 0);
     for (int e = 0; e < NE; ++e)
         if (done_h[e]) {
@@ -1937,6 +1954,7 @@ int line_search(zema_scene* s, const double* dir, const std::vector<int>& done_h
             if (acc[e]) continue;
             if (strict ? s->hd[e] < E0[e] : s->hd[e] <= E0[e]) {
                 acc[e] = 1;
+                Eacc[e] = s->hd[e];
             } else if (k < max_halvings) {
                 alpha[e] *= 0.5;
                 ++halvings;
@@ -1954,8 +1972,12 @@ int line_search(zema_scene* s, const double* dir, const std::vector<int>& done_h
     }
     // envs that never accepted (warm start only): alpha = 0
     for (int e = 0; e < NE; ++e)
-        if (!acc[e]) alpha[e] = 0.0;
+        if (!acc[e]) {
+            alpha[e] = 0.0;
+            Eacc[e] = E0[e];
+        }
     if (accepted) *accepted = acc;
+    if (e_at_x) *e_at_x = Eacc;
     ZCHECK(cudaMemcpyAsync(s->alpha.p, alpha.data(), NE * sizeof(double), cudaMemcpyHostToDevice, st));
     ZL(k_axpy_env, div_up(s->n_nodes, TB), TB, 0, st)(G, s->x.p, dir, s->alpha.p, s->xtrial.p);
     ZLAUNCH();
@@ -2177,7 +2199,8 @@ void do_step(zema_scene* s) {
         ZL(k_scale_dir, div_up(s->n_nodes, TB), TB, 0, st)(G, s->v.p, s->P.dt, W.dirw.p);
         ZLAUNCH();
         std::vector<int> done(NE, 0), acc;
-        line_search(s, W.dirw.p, done, true, &acc);
+        std::vector<double> e_at_x(NE, NAN);  // the potential at the current x, per env
+        line_search(s, W.dirw.p, done, true, &acc, 0, false, &e_at_x);
         if (use_learned) {
             ZCHECK(cudaMemsetAsync(W.dirw.p, 0, n3 * sizeof(double), st));
             if (learned_soft)
@@ -2188,7 +2211,7 @@ void do_step(zema_scene* s) {
                                                                        s->ws_aout.p, ws_scale(s), W.dirw.p);
             ZLAUNCH();
             std::vector<int> acc2;
-            line_search(s, W.dirw.p, done, true, &acc2, kWsHalvings, true);
+            line_search(s, W.dirw.p, done, true, &acc2, kWsHalvings, true, &e_at_x);
             for (int e = 0; e < NE; ++e) s->S.warm_learned += acc2[e];
         }
         for (int e = 0; e < NE; ++e) s->S.warm_accepted += acc[e];
@@ -2249,7 +2272,7 @@ void do_step(zema_scene* s) {
                 ZCHECK(cudaMemcpyAsync(s->need.p, s->hi, NE * sizeof(int), cudaMemcpyHostToDevice, st));
                 ZL(k_mask_env, div_up(s->n_nodes, TB), TB, 0, st)(G, s->p.p, s->need.p);
                 ZLAUNCH();
-                int hv = line_search(s, s->p.p, done, false, nullptr);
+                int hv = line_search(s, s->p.p, done, false, nullptr, 0, false, &e_at_x);
                 if (hv < 0) fail(ZEMA_ERR_LINESEARCH, "line search found no decrease after 60 halvings");
                 s->S.ls_halvings += hv;
             }
@@ -2269,6 +2292,7 @@ void do_step(zema_scene* s) {
             for (int e = 0; e < NE; ++e) any |= s->hi[e] != 0;
             if (!any || rounds >= s->P.max_al_rounds) break;
             ++rounds;
+            std::fill(e_at_x.begin(), e_at_x.end(), NAN);  // the multipliers change the potential
             ZL(k_al_update, div_up(s->n_aff, 64), 64, 0, st)(G, s->x.p, s->qtarget.p, s->lamA.p, s->need.p);
             if (G.n_joints)
                 ZL(k_joint_update, div_up(G.n_joints, 64), 64, 0, st)(G, s->x.p, s->lamJ.p, s->need.p);
