@@ -145,20 +145,27 @@ __device__ __forceinline__ void block_fma4(const float4* blk, const float* sp, i
 // blocks [jb, je) of a row of the staged slice (local S range, then local C range)
 __device__ __forceinline__ void row_part4(const float4* slice, int4 g, int jb, int je, const float* sp, int nb,
                                           int n_env, int gl, float& y0, float& y1, float& y2) {
+    // the accumulation order of row_part (kPcgcRowIlp accumulators summed in
+    // order), so that a staged and an unstaged slice give the same bits
     const int ls = g.y - g.x;
-    float u0 = 0, u1 = 0, u2 = 0;
-    int j = jb + gl;
-    for (; j + kPcgcGroup < je; j += 2 * kPcgcGroup) {
-        const int k0 = j < ls ? g.x + j : g.z + (j - ls);
-        const int j1 = j + kPcgcGroup;
-        const int k1 = j1 < ls ? g.x + j1 : g.z + (j1 - ls);
-        block_fma4(slice + 3 * (size_t)k0, sp, nb, n_env, y0, y1, y2);
-        block_fma4(slice + 3 * (size_t)k1, sp, nb, n_env, u0, u1, u2);
+    float a[kPcgcRowIlp][3];
+#pragma unroll
+    for (int t = 0; t < kPcgcRowIlp; ++t) a[t][0] = a[t][1] = a[t][2] = 0.0f;
+    for (int j0 = jb + gl; j0 < je; j0 += kPcgcRowIlp * kPcgcGroup) {
+#pragma unroll
+        for (int t = 0; t < kPcgcRowIlp; ++t) {
+            const int j = j0 + t * kPcgcGroup;
+            if (j < je)
+                block_fma4(slice + 3 * (size_t)(j < ls ? g.x + j : g.z + (j - ls)), sp, nb, n_env, a[t][0], a[t][1],
+                           a[t][2]);
+        }
     }
-    if (j < je) block_fma4(slice + 3 * (size_t)(j < ls ? g.x + j : g.z + (j - ls)), sp, nb, n_env, y0, y1, y2);
-    y0 += u0;
-    y1 += u1;
-    y2 += u2;
+#pragma unroll
+    for (int t = 0; t < kPcgcRowIlp; ++t) {
+        y0 += a[t][0];
+        y1 += a[t][1];
+        y2 += a[t][2];
+    }
 }
 
 // blocks [jb, je) of the row's combined index space (S range, then C range)
