@@ -160,12 +160,8 @@ __global__ void k_seg_starts(const uint32_t* head, const uint32_t* hoff, uint32_
 // combines them, so the long segments (blocks between an affine body's nodes
 // collect one contribution per pair touching the body) do not serialise.
 template <int W, class T>
-__global__ void k_seg_sum(const uint32_t* seg, uint32_t nu, const uint32_t* perm, const T* stage, T* out,
-                          const uint64_t* key, uint64_t* ukey) {
-    const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t u = (uint32_t)(gt >> 5);
-    const int l = threadIdx.x & 31;
-    if (u >= nu) return;  // the whole warp
+__device__ __forceinline__ void seg_sum_one(const uint32_t* seg, uint32_t u, int l, const uint32_t* perm,
+                                            const T* stage, T* out, const uint64_t* key, uint64_t* ukey) {
     T s[W];
 #pragma unroll
     for (int q = 0; q < W; ++q) s[q] = 0;
@@ -189,10 +185,23 @@ __global__ void k_seg_sum(const uint32_t* seg, uint32_t nu, const uint32_t* perm
     if (l == 0) ukey[u] = key[b];
 }
 
+// The count of unique keys is read on the device (*nu_dev), so no host round
+// trip sizes the launch: warps stride over the keys.
+template <int W, class T>
+__global__ void k_seg_sum(const uint32_t* seg, const uint32_t* nu_dev, const uint32_t* perm, const T* stage, T* out,
+                          const uint64_t* key, uint64_t* ukey) {
+    const uint32_t nu = *nu_dev;
+    const int l = threadIdx.x & 31;
+    const uint32_t n_warps = (uint32_t)((gridDim.x * (long long)blockDim.x) >> 5);
+    for (uint32_t u = (uint32_t)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5); u < nu; u += n_warps)
+        seg_sum_one<W, T>(seg, u, l, perm, stage, out, key, ukey);
+}
+
 // contact BSR: row pointers and columns from the unique (row, col) keys
-__global__ void k_contact_rows(const uint64_t* ukey, uint32_t nu, int n_nodes, int* rowptr, int* col) {
+__global__ void k_contact_rows(const uint64_t* ukey, const uint32_t* nu_dev, int n_nodes, int* rowptr, int* col) {
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r > n_nodes) return;
+    const uint32_t nu = *nu_dev;
     // first unique key with row >= r
     uint64_t target = (uint64_t)r * (uint64_t)n_nodes;
     uint32_t lo = 0, hi = nu;
@@ -208,9 +217,9 @@ __global__ void k_contact_rows(const uint64_t* ukey, uint32_t nu, int n_nodes, i
         for (uint32_t k = lo; k < nu && ukey[k] < target + (uint64_t)n_nodes; ++k) col[k] = (int)(ukey[k] % n_nodes);
 }
 
-__global__ void k_add_contact_grad(const uint64_t* ukey, const double* gsum, uint32_t nu, double* g) {
+__global__ void k_add_contact_grad(const uint64_t* ukey, const double* gsum, const uint32_t* nu_dev, double* g) {
     uint32_t u = blockIdx.x * blockDim.x + threadIdx.x;
-    if (u >= nu) return;
+    if (u >= *nu_dev) return;
     size_t n = (size_t)ukey[u];
     for (int r = 0; r < 3; ++r) g[3 * n + r] += gsum[3 * (size_t)u + r];
 }

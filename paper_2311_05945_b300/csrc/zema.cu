@@ -142,10 +142,13 @@ struct zema_scene {
     DBuf<double> bstage, gstage, C_val, gsum;
     DBuf<int> C_rowptr, C_col;
     uint32_t n_cblocks = 0;
+    bool n_cblocks_pending = false;  // the count waits in h32[8] for the next read-back
+    DBuf<uint32_t> cnt_u;            // unique contact blocks and gradient nodes, on the device
     // pinned host scratch
     uint32_t* h32 = nullptr;
     double* hd = nullptr;
     int* hi = nullptr;
+    double* h_alpha = nullptr;  // the line search's ACCD bounds, read back with its first trial
     Geo G{};
     // stats of the current call
     zema_step_stats S{};
@@ -189,6 +192,7 @@ struct zema_scene {
         if (h32) cudaFreeHost(h32);
         if (hd) cudaFreeHost(hd);
         if (hi) cudaFreeHost(hi);
+        if (h_alpha) cudaFreeHost(h_alpha);
     }
 };
 
@@ -954,6 +958,7 @@ void build(zema_scene* s) {
     if (!s->h32) ZCHECK(cudaMallocHost(&s->h32, 64 * sizeof(uint32_t)));
     if (!s->hd) ZCHECK(cudaMallocHost(&s->hd, (8 * (size_t)NE + 64) * sizeof(double)));
     if (!s->hi) ZCHECK(cudaMallocHost(&s->hi, (4 * (size_t)NE + 64) * sizeof(int)));
+    if (!s->h_alpha) ZCHECK(cudaMallocHost(&s->h_alpha, ((size_t)NE + 8) * sizeof(double)));
     // learned warm start: soft vertices in node order, their body, per-body
     // node range and rest half-diagonal
     {
@@ -1271,6 +1276,7 @@ void grad_hess_t(zema_scene* s, bool barrier, bool friction, bool hess) {
     if (nr == 0) {
         ZCHECK(cudaMemsetAsync(s->C_rowptr.p, 0, (s->n_nodes + 1) * sizeof(int), st));
         s->n_cblocks = 0;
+        s->n_cblocks_pending = false;
         s->C_col.ensure(A, 1);
         s->C_val.ensure(A, 9);
         return;
@@ -1313,30 +1319,34 @@ void grad_hess_t(zema_scene* s, bool barrier, bool friction, bool hess) {
     s->hoff.ensure(A, mx + 1);
     s->seg.ensure(A, mx + 1);
     s->ukey.ensure(A, mx);
+    // the unique counts stay on the device: the unique-block and unique-node
+    // launches read them there (sized by their upper bounds nb and ng), and
+    // the host picks the block count up at the solve's next read-back
+    s->cnt_u.ensure(A, 4);
     ZL(k_heads, div_up(nb, TB), TB, 0, st)(s->bkey.p, nb, s->head.p);
     exclusive_scan(s->head.p, s->hoff.p, nb, s->tmp32.p, st);
     ZL(k_seg_starts, div_up(nb + 1, TB), TB, 0, st)(s->head.p, s->hoff.p, nb, s->seg.p);
-    ZCHECK(cudaMemcpyAsync(s->h32 + 2, s->hoff.p + nb, 4, cudaMemcpyDeviceToHost, st));
-    ZCHECK(cudaStreamSynchronize(st));
-    uint32_t nu = s->h32[2];
-    s->C_val.ensure(A, 9 * (size_t)nu + 9);
-    s->C_col.ensure(A, nu + 1);
-    ZL((k_seg_sum<9, T>), div_up(32 * (long long)nu, 128), 128, 0, st)(s->seg.p, nu, s->bval.p, (const T*)s->bstage.p, (T*)s->C_val.p,
-                                                        s->bkey.p, s->ukey.p);
-    ZL(k_contact_rows, div_up(s->n_nodes + 1, TB), TB, 0, st)(s->ukey.p, nu, s->n_nodes, s->C_rowptr.p, s->C_col.p);
+    ZCHECK(cudaMemcpyAsync(s->cnt_u.p, s->hoff.p + nb, 4, cudaMemcpyDeviceToDevice, st));
+    ZCHECK(cudaMemcpyAsync(s->h32 + 8, s->hoff.p + nb, 4, cudaMemcpyDeviceToHost, st));
+    s->C_val.ensure(A, 9 * (size_t)nb + 9);
+    s->C_col.ensure(A, nb + 1);
+    const int seg_grid = std::max(1, std::min(div_up(32 * (long long)nb, 128), 148 * 32));
+    ZL((k_seg_sum<9, T>), seg_grid, 128, 0, st)(s->seg.p, s->cnt_u.p, s->bval.p, (const T*)s->bstage.p,
+                                               (T*)s->C_val.p, s->bkey.p, s->ukey.p);
+    ZL(k_contact_rows, div_up(s->n_nodes + 1, TB), TB, 0, st)(s->ukey.p, s->cnt_u.p, s->n_nodes, s->C_rowptr.p,
+                                                             s->C_col.p);
     ZLAUNCH();
-    s->n_cblocks = nu;
+    s->n_cblocks_pending = true;
     // unique gradient nodes
     ZL(k_heads, div_up(ng, TB), TB, 0, st)(s->gkey.p, ng, s->head.p);
     exclusive_scan(s->head.p, s->hoff.p, ng, s->tmp32.p, st);
     ZL(k_seg_starts, div_up(ng + 1, TB), TB, 0, st)(s->head.p, s->hoff.p, ng, s->seg.p);
-    ZCHECK(cudaMemcpyAsync(s->h32 + 3, s->hoff.p + ng, 4, cudaMemcpyDeviceToHost, st));
-    ZCHECK(cudaStreamSynchronize(st));
-    uint32_t nug = s->h32[3];
-    s->gsum.ensure(A, 3 * (size_t)nug + 3);
-    ZL((k_seg_sum<3, double>), div_up(32 * (long long)nug, 128), 128, 0, st)(s->seg.p, nug, s->gval.p, s->gstage.p, s->gsum.p,
-                                                              s->gkey.p, s->ukey.p);
-    ZL(k_add_contact_grad, div_up(nug, 128), 128, 0, st)(s->ukey.p, s->gsum.p, nug, s->g.p);
+    ZCHECK(cudaMemcpyAsync(s->cnt_u.p + 1, s->hoff.p + ng, 4, cudaMemcpyDeviceToDevice, st));
+    s->gsum.ensure(A, 3 * (size_t)ng + 3);
+    const int gseg_grid = std::max(1, std::min(div_up(32 * (long long)ng, 128), 148 * 32));
+    ZL((k_seg_sum<3, double>), gseg_grid, 128, 0, st)(s->seg.p, s->cnt_u.p + 1, s->gval.p, s->gstage.p, s->gsum.p,
+                                                      s->gkey.p, s->ukey.p);
+    ZL(k_add_contact_grad, div_up(ng, 128), 128, 0, st)(s->ukey.p, s->gsum.p, s->cnt_u.p + 1, s->g.p);
     ZLAUNCH();
 }
 
@@ -1836,6 +1846,10 @@ int64_t pcg_t(zema_scene* s, const std::vector<int>& done_h) {
     // written, p and q read, z written, the preconditioner read (9 values per
     // soft node, 144 per affine body); direction: z read, p read and written.
     // 36 vector values per node in the solve's type.
+    if (s->n_cblocks_pending) {  // read back with the solve's statistics
+        s->n_cblocks = s->h32[8];
+        s->n_cblocks_pending = false;
+    }
     {
         double nn = s->n_nodes;
         double bs = 9.0 * sizeof(T) + 4.0;  // one stored block and its column index
@@ -1918,9 +1932,11 @@ int line_search(zema_scene* s, const double* dir, const std::vector<int>& done_h
     ZCHECK(cudaMemsetAsync(s->capflag.p, 0, sizeof(int), st));
     if (ns) ZL(k_accd, div_up(ns, 128), 128, 0, st)(G, s->X.p, s->q.p, s->swept.p, (int)ns, s->alpha.p, s->capflag.p);
     ZLAUNCH();
+    // the first trial takes the ACCD bounds where they are, on the device; the
+    // host reads them back with that trial's energies (no round trip here)
     std::vector<double> alpha(NE);
-    ZCHECK(cudaMemcpyAsync(alpha.data(), s->alpha.p, NE * sizeof(double), cudaMemcpyDeviceToHost, st));
-    ZCHECK(cudaStreamSynchronize(st));
+    ZCHECK(cudaMemcpyAsync(s->h_alpha, s->alpha.p, NE * sizeof(double), cudaMemcpyDeviceToHost, st));
+    bool alpha_known = false;
     s->S.ms_phase[4] += now_ms() - t0;
     t0 = now_ms();
     bool need_e0 = e_at_x == nullptr;
@@ -1936,17 +1952,21 @@ int line_search(zema_scene* s, const double* dir, const std::vector<int>& done_h
     std::vector<double> Eacc(E0);  // the potential at the accepted point, per env
     std::vector<int> acc(NE, 0);
     for (int e = 0; e < NE; ++e)
-        if (done_h[e]) {
-            acc[e] = 1;
-            alpha[e] = 0.0;
-        }
+        if (done_h[e]) acc[e] = 1;  // converged: no step (its direction is zero)
     int halvings = 0;
     bool fail_ls = false;
     for (int k = 0; k <= max_halvings; ++k) {
-        ZCHECK(cudaMemcpyAsync(s->alpha.p, alpha.data(), NE * sizeof(double), cudaMemcpyHostToDevice, st));
+        if (alpha_known)
+            ZCHECK(cudaMemcpyAsync(s->alpha.p, alpha.data(), NE * sizeof(double), cudaMemcpyHostToDevice, st));
         ZL(k_axpy_env, div_up(s->n_nodes, TB), TB, 0, st)(G, s->x.p, dir, s->alpha.p, s->xtrial.p);
         ZLAUNCH();
         energy(s, s->xtrial.p, s->swept.p, s->swept_env.p);
+        if (!alpha_known) {
+            alpha.assign(s->h_alpha, s->h_alpha + NE);
+            for (int e = 0; e < NE; ++e)
+                if (done_h[e]) alpha[e] = 0.0;
+            alpha_known = true;
+        }
         if (!warm && s->fault_armed == ZEMA_FAULT_NO_DECREASE)
             for (int e = 0; e < NE; ++e) s->hd[e] = INFINITY;  // every trial point rejected
         bool all = true;
@@ -2237,7 +2257,7 @@ void do_step(zema_scene* s) {
                 active_from(s, s->X.p, s->swept.p, s->swept_env.p, s->n_swept, true, s->skip.p);
                 double tb = now_ms();
                 s->S.ms_phase[0] += tb - ta;
-                grad_hess(s);
+                grad_hess(s);  // no read-back: the solve's is the next
                 // fault injection: armed for this iteration only (one shot)
                 s->fault_armed = 0;
                 if (s->fault_kind && s->newton_count == s->fault_at) {
@@ -2247,7 +2267,6 @@ void do_step(zema_scene* s) {
                     ZCHECK(cudaMemcpyAsync(s->fault_dev.p, on, 2 * sizeof(int), cudaMemcpyHostToDevice, st));
                 }
                 ++s->newton_count;
-                ZCHECK(cudaStreamSynchronize(st));
                 double tc = now_ms();
                 s->S.ms_phase[2] += tc - tb;
                 s->S.pcg_iters += pcg(s, done);
