@@ -149,6 +149,13 @@ struct zema_scene {
     double* hd = nullptr;
     int* hi = nullptr;
     double* h_alpha = nullptr;  // the line search's ACCD bounds, read back with its first trial
+    // a solve's iteration counts and status (pinned, 2 per env), read back
+    // with the next round trip; its kernel name and value size for the
+    // roofline's byte count
+    int* h_pcg = nullptr;
+    bool pcg_pending = false;
+    int pcg_pending_tsize = 0;
+    const char* pcg_pending_kname = nullptr;
     Geo G{};
     // stats of the current call
     zema_step_stats S{};
@@ -193,6 +200,7 @@ struct zema_scene {
         if (hd) cudaFreeHost(hd);
         if (hi) cudaFreeHost(hi);
         if (h_alpha) cudaFreeHost(h_alpha);
+        if (h_pcg) cudaFreeHost(h_pcg);
     }
 };
 
@@ -959,6 +967,7 @@ void build(zema_scene* s) {
     if (!s->hd) ZCHECK(cudaMallocHost(&s->hd, (8 * (size_t)NE + 64) * sizeof(double)));
     if (!s->hi) ZCHECK(cudaMallocHost(&s->hi, (4 * (size_t)NE + 64) * sizeof(int)));
     if (!s->h_alpha) ZCHECK(cudaMallocHost(&s->h_alpha, ((size_t)NE + 8) * sizeof(double)));
+    if (!s->h_pcg) ZCHECK(cudaMallocHost(&s->h_pcg, (2 * (size_t)NE + 8) * sizeof(int)));
     // learned warm start: soft vertices in node order, their body, per-body
     // node range and rest half-diagonal
     {
@@ -1565,12 +1574,45 @@ bool pcgc_valid(zema_scene* s, int code) {
     return true;
 }
 
+// After a stream synchronisation: the statistics of the solve whose read-back
+// was waiting (status, iterations into the step's count, and the solve's
+// algorithmic bytes for the live roofline, per iteration the bytes of a
+// streaming PCG iteration whose three fused passes keep nothing on chip:
+// SpMV, every stored block (9 values + 4 B column) and the row pointers
+// (8 B per row), p read, q written; update, x and r read and written, p and
+// q read, z written, the preconditioner read (9 values per soft node, 144
+// per affine body); direction, z read, p read and written; 36 vector values
+// per node in the solve's type).
+void pcg_finish(zema_scene* s) {
+    if (!s->pcg_pending) return;
+    s->pcg_pending = false;
+    const int NE = s->n_envs;
+    int64_t tot = 0;
+    for (int e = 0; e < NE; ++e) {
+        if (s->h_pcg[NE + e] == 2) fail(ZEMA_ERR_NONFINITE, "non-finite value in the linear solve");
+        if (s->h_pcg[NE + e] == 3)
+            fail(ZEMA_ERR_PCG_MAXITER, "linear solve reached max_pcg iterations without meeting its tolerance");
+        tot += s->h_pcg[e];
+    }
+    s->S.pcg_iters += tot;
+    if (s->n_cblocks_pending) {  // read back with the solve's statistics
+        s->n_cblocks = s->h32[8];
+        s->n_cblocks_pending = false;
+    }
+    const double ts = s->pcg_pending_tsize;
+    const double nn = s->n_nodes;
+    const double bs = 9.0 * ts + 4.0;  // one stored block and its column index
+    const double pre = 9.0 * ts * (nn - 4.0 * s->n_aff) + 144.0 * ts * s->n_aff;
+    const double per_it = bs * ((double)s->n_sblocks + (double)s->n_cblocks) + nn * (8.0 + 36.0 * ts) + pre;
+    alg_bytes_add(s->pcg_pending_kname, per_it * (double)tot / std::max(1, NE));
+}
+
 // ---------------------------------------------------------------------------
 // PCG: solve (S + C) p = -g for every env not flagged in done_h (one
 // persistent cooperative launch per solve)
 // ---------------------------------------------------------------------------
 template <class T>
-int64_t pcg_t(zema_scene* s, const std::vector<int>& done_h) {
+void pcg_t(zema_scene* s, const std::vector<int>& done_h) {
     cudaStream_t st = s->st;
     Geo& G = s->G;
     int NE = s->n_envs;
@@ -1601,19 +1643,18 @@ int64_t pcg_t(zema_scene* s, const std::vector<int>& done_h) {
         fail(ZEMA_ERR_INVALID_ARG, "cluster PCG unavailable for this scene on this device");
     const bool use_cluster = s->P.pcg_kind != 1 && s->pcgc_cs[pi] > 0;
     const char* kname = use_cluster ? "k_pcg_cluster" : "k_pcg_persistent";
-    int64_t tot = 0, mx = 0;
-    // iterations of the last launch (and its non-finite flags) into tot / mx
+    // the iterations and status of the last launch go to pinned memory, to
+    // be read after the next synchronisation (pcg_finish)
     auto collect = [&]() {
-        ZCHECK(cudaMemcpyAsync(s->hi, s->pcg_iters.p, NE * sizeof(int), cudaMemcpyDeviceToHost, st));
-        ZCHECK(cudaMemcpyAsync(s->hi + NE, s->conv.p, NE * sizeof(int), cudaMemcpyDeviceToHost, st));
-        ZCHECK(cudaStreamSynchronize(st));
-        for (int e = 0; e < NE; ++e) {
-            if (s->hi[NE + e] == 2) fail(ZEMA_ERR_NONFINITE, "non-finite value in the linear solve");
-            if (s->hi[NE + e] == 3)
-                fail(ZEMA_ERR_PCG_MAXITER, "linear solve reached max_pcg iterations without meeting its tolerance");
-            tot += s->hi[e];
-            mx = std::max<int64_t>(mx, s->hi[e]);
+        if (s->pcg_pending) {  // never two waiting at once
+            ZCHECK(cudaStreamSynchronize(st));
+            pcg_finish(s);
         }
+        ZCHECK(cudaMemcpyAsync(s->h_pcg, s->pcg_iters.p, NE * sizeof(int), cudaMemcpyDeviceToHost, st));
+        ZCHECK(cudaMemcpyAsync(s->h_pcg + NE, s->conv.p, NE * sizeof(int), cudaMemcpyDeviceToHost, st));
+        s->pcg_pending = true;
+        s->pcg_pending_tsize = (int)sizeof(T);
+        s->pcg_pending_kname = kname;
     };
     // one cluster solve with cs CTAs per env (launch only)
     auto launch_cluster = [&](const double* rhs, double* xo, int cs, const double* tol2_env = nullptr) {
@@ -1810,6 +1851,7 @@ int64_t pcg_t(zema_scene* s, const std::vector<int>& done_h) {
             ZCHECK(cudaMemcpyAsync(prr.data(), s->part5.p, nc * sizeof(double), cudaMemcpyDeviceToHost, st));
             ZCHECK(cudaMemcpyAsync(pbb.data(), s->part7.p, nc * sizeof(double), cudaMemcpyDeviceToHost, st));
             ZCHECK(cudaStreamSynchronize(st));
+            pcg_finish(s);  // the solve before this residual
             int count = 0;
             const double tol2 = s->P.pcg_rel_tol * s->P.pcg_rel_tol;
             for (int e = 0; e < NE; ++e) {
@@ -1839,34 +1881,20 @@ int64_t pcg_t(zema_scene* s, const std::vector<int>& done_h) {
             ZLAUNCH();
         }
     }
-    // Algorithmic bytes of the solve for the live roofline, per iteration:
-    // the bytes of a streaming PCG iteration whose three fused passes keep
-    // nothing on chip.  SpMV: every stored block (9 values + 4 B column) and
-    // the row pointers (8 B per row), p read, q written; update: x, r read and
-    // written, p and q read, z written, the preconditioner read (9 values per
-    // soft node, 144 per affine body); direction: z read, p read and written.
-    // 36 vector values per node in the solve's type.
-    if (s->n_cblocks_pending) {  // read back with the solve's statistics
-        s->n_cblocks = s->h32[8];
-        s->n_cblocks_pending = false;
-    }
-    {
-        double nn = s->n_nodes;
-        double bs = 9.0 * sizeof(T) + 4.0;  // one stored block and its column index
-        double pre = 9.0 * sizeof(T) * (nn - 4.0 * s->n_aff) + 144.0 * sizeof(T) * s->n_aff;
-        double per_it = bs * ((double)s->n_sblocks + (double)s->n_cblocks) + nn * (8.0 + 36.0 * sizeof(T)) + pre;
-        alg_bytes_add(kname, per_it * (double)tot / std::max(1, NE));
-    }
     // done envs: zero direction
     for (int e = 0; e < NE; ++e) s->hi[e] = done_h[e];
     ZCHECK(cudaMemcpyAsync(s->need.p, s->hi, NE * sizeof(int), cudaMemcpyHostToDevice, st));
     ZL(k_mask_env, div_up(s->n_nodes, TB), TB, 0, st)(G, s->p.p, s->need.p);
     ZLAUNCH();
-    return tot;
 }
 
-int64_t pcg(zema_scene* s, const std::vector<int>& done_h) {
-    return s->P.precision == 1 ? pcg_t<float>(s, done_h) : pcg_t<double>(s, done_h);
+// The solve of the Newton system; its statistics and status are read back
+// with the step-norm test (pcg_finish after step_norm).
+void pcg(zema_scene* s, const std::vector<int>& done_h) {
+    if (s->P.precision == 1)
+        pcg_t<float>(s, done_h);
+    else
+        pcg_t<double>(s, done_h);
 }
 
 // per-env max step component -> s->hd
@@ -2269,8 +2297,9 @@ void do_step(zema_scene* s) {
                 ++s->newton_count;
                 double tc = now_ms();
                 s->S.ms_phase[2] += tc - tb;
-                s->S.pcg_iters += pcg(s, done);
+                pcg(s, done);
                 step_norm(s);
+                pcg_finish(s);  // the solve's status and statistics, read back with the step norm
                 s->S.ms_phase[3] += now_ms() - tc;
                 bool all = true;
                 for (int e = 0; e < NE; ++e) {
