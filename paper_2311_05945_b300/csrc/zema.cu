@@ -57,6 +57,8 @@ inline dim3 red_grid(int n_envs) { return dim3(kChunks, n_envs); }
 
 }  // namespace
 
+constexpr int kUpSlots = 128;  // pinned upload slots per scene (see zema_scene::h_up_i)
+
 struct zema_scene {
     zema_scene_params P;
     Allocator A;
@@ -149,11 +151,23 @@ struct zema_scene {
     double* hd = nullptr;
     int* hi = nullptr;
     double* h_alpha = nullptr;  // the line search's ACCD bounds, read back with its first trial
+    // per-env host-to-device uploads go through a ring of pinned slots, so
+    // that the host never rewrites a pinned buffer whose asynchronous copy
+    // may not have run yet (a stream synchronises many times per ring turn)
+    int* h_up_i = nullptr;
+    double* h_up_d = nullptr;
+    unsigned h_up_pos = 0;
     // a solve's iteration counts and status (pinned, 2 per env), read back
     // with the next round trip; its kernel name and value size for the
     // roofline's byte count
     int* h_pcg = nullptr;
     bool pcg_pending = false;
+    // the cluster solve's launch order: envs by their last solve's cost
+    // (iterations x nodes), largest first, so that the longest solves start
+    // first and the launch does not end on one late long solve
+    std::vector<double> env_cost;
+    std::vector<int> env_order_h;
+    DBuf<int> env_order;
     int pcg_pending_tsize = 0;
     const char* pcg_pending_kname = nullptr;
     Geo G{};
@@ -200,6 +214,8 @@ struct zema_scene {
         if (hd) cudaFreeHost(hd);
         if (hi) cudaFreeHost(hi);
         if (h_alpha) cudaFreeHost(h_alpha);
+        if (h_up_i) cudaFreeHost(h_up_i);
+        if (h_up_d) cudaFreeHost(h_up_d);
         if (h_pcg) cudaFreeHost(h_pcg);
     }
 };
@@ -207,6 +223,21 @@ struct zema_scene {
 namespace {
 
 void fail(int status, const std::string& m) { throw ZemaError{status, m}; }
+
+// n_envs values into device memory through the next pinned ring slot (see
+// zema_scene::h_up_i)
+void upload_env_ints(zema_scene* s, int* dst, const int* src) {
+    const int NE = s->n_envs;
+    int* slot = s->h_up_i + (size_t)(s->h_up_pos++ % kUpSlots) * NE;
+    std::memcpy(slot, src, NE * sizeof(int));
+    ZCHECK(cudaMemcpyAsync(dst, slot, NE * sizeof(int), cudaMemcpyHostToDevice, s->st));
+}
+void upload_env_doubles(zema_scene* s, double* dst, const double* src) {
+    const int NE = s->n_envs;
+    double* slot = s->h_up_d + (size_t)(s->h_up_pos++ % kUpSlots) * NE;
+    std::memcpy(slot, src, NE * sizeof(double));
+    ZCHECK(cudaMemcpyAsync(dst, slot, NE * sizeof(double), cudaMemcpyHostToDevice, s->st));
+}
 
 template <class T>
 void up(zema_scene* s, DBuf<T>& d, const std::vector<T>& h) {
@@ -967,6 +998,8 @@ void build(zema_scene* s) {
     if (!s->hd) ZCHECK(cudaMallocHost(&s->hd, (8 * (size_t)NE + 64) * sizeof(double)));
     if (!s->hi) ZCHECK(cudaMallocHost(&s->hi, (4 * (size_t)NE + 64) * sizeof(int)));
     if (!s->h_alpha) ZCHECK(cudaMallocHost(&s->h_alpha, ((size_t)NE + 8) * sizeof(double)));
+    if (!s->h_up_i) ZCHECK(cudaMallocHost(&s->h_up_i, (size_t)kUpSlots * NE * sizeof(int)));
+    if (!s->h_up_d) ZCHECK(cudaMallocHost(&s->h_up_d, (size_t)kUpSlots * NE * sizeof(double)));
     if (!s->h_pcg) ZCHECK(cudaMallocHost(&s->h_pcg, (2 * (size_t)NE + 8) * sizeof(int)));
     // learned warm start: soft vertices in node order, their body, per-body
     // node range and rest half-diagonal
@@ -1595,6 +1628,10 @@ void pcg_finish(zema_scene* s) {
         tot += s->h_pcg[e];
     }
     s->S.pcg_iters += tot;
+    if ((int)s->env_cost.size() == NE)
+        for (int e = 0; e < NE; ++e)
+            if (s->h_pcg[e] > 0)
+                s->env_cost[e] = (double)s->h_pcg[e] * (s->env_node_start_h[e + 1] - s->env_node_start_h[e]);
     if (s->n_cblocks_pending) {  // read back with the solve's statistics
         s->n_cblocks = s->h32[8];
         s->n_cblocks_pending = false;
@@ -1626,7 +1663,7 @@ void pcg_t(zema_scene* s, const std::vector<int>& done_h) {
     ZL(k_negate, div_up(3 * (size_t)s->n_nodes, TB), TB, 0, st)(s->g.p, s->b.p, 3 * (size_t)s->n_nodes);
     ZLAUNCH();
     for (int e = 0; e < NE; ++e) s->hi[e] = s->hi[3 * NE + e] = done_h[e];
-    ZCHECK(cudaMemcpyAsync(s->conv.p, s->hi, NE * sizeof(int), cudaMemcpyHostToDevice, st));
+    upload_env_ints(s, s->conv.p, s->hi);
     ZCHECK(cudaMemsetAsync(s->pcg_iters.p, 0, NE * sizeof(int), st));
     const int pi = s->P.precision == 1 ? 1 : 0;
     if (s->P.pcg_kind != 1 && s->pcgc_cs[pi] == 0) {
@@ -1678,6 +1715,24 @@ void pcg_t(zema_scene* s, const std::vector<int>& done_h) {
         c.slice_cap = pcgc_slice_cap<T>(s, cs);
         c.chunk_cap = pcgc_chunk_cap(s, cs);
         c.env_list = nullptr;
+        if (NE > 1 && !sched_binned(cs)) {
+            // longest solves first (the order changes no env's arithmetic)
+            if ((int)s->env_cost.size() != NE) {
+                s->env_cost.resize(NE);
+                for (int e = 0; e < NE; ++e) s->env_cost[e] = s->env_node_start_h[e + 1] - s->env_node_start_h[e];
+            }
+            std::vector<int> order(NE);
+            for (int e = 0; e < NE; ++e) order[e] = e;
+            std::stable_sort(order.begin(), order.end(),
+                             [&](int a, int b) { return s->env_cost[a] > s->env_cost[b]; });
+            if (order != s->env_order_h) {
+                s->env_order_h = order;
+                s->env_order.ensure(&s->A, NE);
+                ZCHECK(cudaMemcpyAsync(s->env_order.p, s->env_order_h.data(), NE * sizeof(int),
+                                       cudaMemcpyHostToDevice, st));
+            }
+            c.env_list = s->env_order.p;
+        }
         cudaLaunchConfig_t cfg = {};
         cudaLaunchAttribute at[1];
         pcgc_config<T>(s, cs, cfg, at);
@@ -1776,7 +1831,7 @@ void pcg_t(zema_scene* s, const std::vector<int>& done_h) {
             if (!pcgc_valid<T>(s, cs)) continue;
             float ms = INFINITY;
             for (int rep = 0; rep < 2; ++rep) {
-                ZCHECK(cudaMemcpyAsync(s->conv.p, s->hi + 3 * NE, NE * sizeof(int), cudaMemcpyHostToDevice, st));
+                upload_env_ints(s, s->conv.p, s->hi + 3 * NE);
                 ZCHECK(cudaEventRecord(e0, st));
                 launch_cluster(s->b.p, s->r.p, cs);
                 ZCHECK(cudaEventRecord(e1, st));
@@ -1795,7 +1850,7 @@ void pcg_t(zema_scene* s, const std::vector<int>& done_h) {
         cudaEventDestroy(e1);
         s->pcgc_cs[pi] = best_cs;
         s->pcgc_tuned_flag[pi] = true;
-        ZCHECK(cudaMemcpyAsync(s->conv.p, s->hi + 3 * NE, NE * sizeof(int), cudaMemcpyHostToDevice, st));
+        upload_env_ints(s, s->conv.p, s->hi + 3 * NE);
     }
     if (s->n_sm == 0) {
         int dev = 0;
@@ -1842,7 +1897,7 @@ void pcg_t(zema_scene* s, const std::vector<int>& done_h) {
         std::vector<double> prr(nc), pbb(nc);
         for (int ref = 0; ref < kPcgcRefine; ++ref) {
             for (int e = 0; e < NE; ++e) s->hi[e] = need[e] ? 0 : 1;
-            ZCHECK(cudaMemcpyAsync(s->conv.p, s->hi, NE * sizeof(int), cudaMemcpyHostToDevice, st));
+            upload_env_ints(s, s->conv.p, s->hi);
             ZL(k_residual64<T>, div_up(32 * (long long)s->n_nodes, 128), 128, 0, st)(G, S, C, s->p.p, s->b.p,
                                                                                     s->conv.p, s->q.p);
             ZL(k_env_dot2, red_grid(NE), kRedThreads, 0, st)(G, s->b.p, s->q.p, s->part4.p, s->part5.p);
@@ -1872,18 +1927,18 @@ void pcg_t(zema_scene* s, const std::vector<int>& done_h) {
             if (!count) break;
             s->S.pcg_refines += count;
             for (int e = 0; e < NE; ++e) s->hi[e] = need[e] ? 0 : 1;
-            ZCHECK(cudaMemcpyAsync(s->conv.p, s->hi, NE * sizeof(int), cudaMemcpyHostToDevice, st));
-            ZCHECK(cudaMemcpyAsync(s->tol2_env.p, s->hd, NE * sizeof(double), cudaMemcpyHostToDevice, st));
+            upload_env_ints(s, s->conv.p, s->hi);
+            upload_env_doubles(s, s->tol2_env.p, s->hd);
             run_solve(s->q.p, s->r.p, s->tol2_env.p, count);
             for (int e = 0; e < NE; ++e) s->hi[e] = need[e];
-            ZCHECK(cudaMemcpyAsync(s->need.p, s->hi, NE * sizeof(int), cudaMemcpyHostToDevice, st));
+            upload_env_ints(s, s->need.p, s->hi);
             ZL(k_add_env, div_up(s->n_nodes, TB), TB, 0, st)(G, s->p.p, s->r.p, s->need.p);
             ZLAUNCH();
         }
     }
     // done envs: zero direction
     for (int e = 0; e < NE; ++e) s->hi[e] = done_h[e];
-    ZCHECK(cudaMemcpyAsync(s->need.p, s->hi, NE * sizeof(int), cudaMemcpyHostToDevice, st));
+    upload_env_ints(s, s->need.p, s->hi);
     ZL(k_mask_env, div_up(s->n_nodes, TB), TB, 0, st)(G, s->p.p, s->need.p);
     ZLAUNCH();
 }
@@ -1953,7 +2008,7 @@ int line_search(zema_scene* s, const double* dir, const std::vector<int>& done_h
     for (int e = 0; e < NE; ++e) any_done |= done_h[e] != 0;
     if (any_done) {
         for (int e = 0; e < NE; ++e) s->hi[e] = done_h[e] ? 1 : 0;
-        ZCHECK(cudaMemcpyAsync(s->skip.p, s->hi, NE * sizeof(int), cudaMemcpyHostToDevice, st));
+        upload_env_ints(s, s->skip.p, s->hi);
     }
     uint32_t ns = candidates(s, s->X.p, s->q.p, s->swept, s->swept_env, any_done ? s->skip.p : nullptr);
     s->n_swept = ns;
@@ -2280,7 +2335,7 @@ void do_step(zema_scene* s) {
                 // warm start or the previous Newton step), so that swept
                 // candidate list contains every pair with d < dhat at x
                 for (int e = 0; e < NE; ++e) s->hi[e] = done[e] ? 1 : 0;
-                ZCHECK(cudaMemcpyAsync(s->skip.p, s->hi, NE * sizeof(int), cudaMemcpyHostToDevice, st));
+                upload_env_ints(s, s->skip.p, s->hi);
                 G.env_done = s->skip.p;
                 active_from(s, s->X.p, s->swept.p, s->swept_env.p, s->n_swept, true, s->skip.p);
                 double tb = now_ms();
@@ -2317,7 +2372,7 @@ void do_step(zema_scene* s) {
                 }
                 // zero the direction of envs that just converged
                 for (int e = 0; e < NE; ++e) s->hi[e] = done[e];
-                ZCHECK(cudaMemcpyAsync(s->need.p, s->hi, NE * sizeof(int), cudaMemcpyHostToDevice, st));
+                upload_env_ints(s, s->need.p, s->hi);
                 ZL(k_mask_env, div_up(s->n_nodes, TB), TB, 0, st)(G, s->p.p, s->need.p);
                 ZLAUNCH();
                 int hv = line_search(s, s->p.p, done, false, nullptr, 0, false, &e_at_x);
@@ -2349,7 +2404,7 @@ void do_step(zema_scene* s) {
             // the resuming envs may have been left out of the last swept list:
             // candidates at x (static boxes) for them
             for (int e = 0; e < NE; ++e) s->hi[e] = done[e];
-            ZCHECK(cudaMemcpyAsync(s->skip.p, s->hi, NE * sizeof(int), cudaMemcpyHostToDevice, st));
+            upload_env_ints(s, s->skip.p, s->hi);
             ZL(k_sv_pos, div_up(s->n_sv, TB), TB, 0, st)(G, s->x.p, s->X.p);
             ZLAUNCH();
             s->n_swept = candidates(s, s->X.p, nullptr, s->swept, s->swept_env, s->skip.p);
