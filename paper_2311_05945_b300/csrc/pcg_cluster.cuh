@@ -54,6 +54,8 @@ struct PcgcArgs {
     int slice_cap;       // blocks of a CTA's matrix slice that fit in shared memory (0: never staged)
     int chunk_cap;       // SpMV chunks a CTA can hold (more: one task per row instead)
     const int* env_list; // nullable: cluster k solves env env_list[k] (a group of envs), else env k
+    const float4* pk;    // nullable (FP32 only): S then C packed by k_pack_blocks, read by unstaged CTAs
+    int pk_c0;           // index of C's first block in pk
 };
 
 constexpr int kPcgcThreads = 512;
@@ -74,38 +76,48 @@ __device__ __forceinline__ float ldcg_r(const float* p) { return __ldcg(p); }
 __device__ __forceinline__ double ldcg_r(const double* p) { return __ldcg(p); }
 
 // All-reduce of K per-thread values over the cluster, in Real.  Each warp
-// sums its lanes' values by shuffles; lane 0 stores the K sums into slot
-// (rank, warp) of the reduction buffer of every CTA of the cluster
-// (distributed shared memory).  After the cluster barrier, every warp of
-// every CTA sums the cs x NW slots of its own copy in one fixed order (lane
-// l takes slots l, l + 32, ..., then a fixed shuffle tree), so all threads
-// of all CTAs get the same bits with no further CTA barrier.  The cluster
+// sums its lanes' values by shuffles into a slot of warp partials w; after a
+// CTA barrier warp 0 sums the NW slots (a fixed shuffle tree), and lane l
+// stores the CTA's K totals into slot rank of the reduction buffer of CTA l
+// (distributed shared memory).  After the cluster barrier every thread sums
+// the cs slots of its own copy in rank order, so all threads of all CTAs get
+// the same bits.  One remote store per CTA pair and cs values to sum: the
+// cluster barrier, not the traffic around it, sets the cost.  The cluster
 // barrier also orders every CTA's earlier shared- and global-memory writes
-// for the whole cluster.  red: K x (kPcgcMaxCluster * NW) values.
+// for the whole cluster.  red: K x kPcgcMaxCluster values; w: K x NW.
 template <int K, class Real>
 __device__ __forceinline__ void cluster_allreduce(cooperative_groups::cluster_group& cl, Real (&v)[K], Real* red,
-                                                  Real (&tot)[K]) {
-    constexpr int NW = kPcgcThreads / 32, SLOTS = kPcgcMaxCluster * NW;
+                                                  Real* w_part, Real (&tot)[K]) {
+    constexpr int NW = kPcgcThreads / 32;
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     const int cs = (int)cl.num_blocks(), rank = (int)cl.block_rank();
 #pragma unroll
     for (int k = 0; k < K; ++k)
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
-    if (l < cs) {
-        // lane l sends the warp's sums to CTA l
-        Real* dst = cl.map_shared_rank(red, l);
+    if (l == 0)
 #pragma unroll
-        for (int k = 0; k < K; ++k) dst[k * SLOTS + rank * NW + w] = v[k];
+        for (int k = 0; k < K; ++k) w_part[k * NW + w] = v[k];
+    __syncthreads();
+    if (w == 0) {
+        Real y[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            y[k] = l < NW ? w_part[k * NW + l] : Real(0);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) y[k] += __shfl_xor_sync(0xffffffffu, y[k], o);
+        }
+        if (l < cs) {
+            Real* dst = cl.map_shared_rank(red, l);
+#pragma unroll
+            for (int k = 0; k < K; ++k) dst[k * kPcgcMaxCluster + rank] = y[k];
+        }
     }
     cl.sync();
-    const int n = cs * NW;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         Real t = 0;
-        for (int i = l; i < n; i += 32) t += red[k * SLOTS + i];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        for (int r = 0; r < cs; ++r) t += red[k * kPcgcMaxCluster + r];
         tot[k] = t;
     }
 }
@@ -129,11 +141,22 @@ __device__ __forceinline__ void block_fma(const Bsr<Real>& S, const Bsr<Real>& C
     y2 += v[6] * p0 + v[7] * p1 + v[8] * p2;
 }
 
-// a block of the staged FP32 slice: 12 floats (the 9 values, the column as
-// int bits, 2 pad) read as three 16-byte vectors
+// a packed FP32 block: 12 floats (the 9 values, the column as int bits, 2
+// pad) read as three 16-byte vectors, from the staged slice in shared memory
+// or (kGlobal) from the packed matrix through the read-only data cache
+template <bool kGlobal>
 __device__ __forceinline__ void block_fma4(const float4* blk, const float* sp, int nb, int n_env, float& y0,
                                            float& y1, float& y2) {
-    const float4 a = blk[0], b = blk[1], c4 = blk[2];
+    float4 a, b, c4;
+    if constexpr (kGlobal) {
+        a = __ldg(blk);
+        b = __ldg(blk + 1);
+        c4 = __ldg(blk + 2);
+    } else {
+        a = blk[0];
+        b = blk[1];
+        c4 = blk[2];
+    }
     const unsigned c = (unsigned)(__float_as_int(c4.y) - nb);
     if (c >= (unsigned)n_env) return;  // cannot happen: blocks stay inside one env
     const float p0 = sp[3 * c], p1 = sp[3 * c + 1], p2 = sp[3 * c + 2];
@@ -142,7 +165,8 @@ __device__ __forceinline__ void block_fma4(const float4* blk, const float* sp, i
     y2 += b.z * p0 + b.w * p1 + c4.x * p2;
 }
 
-// blocks [jb, je) of a row of the staged slice (local S range, then local C range)
+// blocks [jb, je) of a row of packed blocks (S range, then C range)
+template <bool kGlobal>
 __device__ __forceinline__ void row_part4(const float4* slice, int4 g, int jb, int je, const float* sp, int nb,
                                           int n_env, int gl, float& y0, float& y1, float& y2) {
     // the accumulation order of row_part (kPcgcRowIlp accumulators summed in
@@ -156,7 +180,7 @@ __device__ __forceinline__ void row_part4(const float4* slice, int4 g, int jb, i
         for (int t = 0; t < kPcgcRowIlp; ++t) {
             const int j = j0 + t * kPcgcGroup;
             if (j < je)
-                block_fma4(slice + 3 * (size_t)(j < ls ? g.x + j : g.z + (j - ls)), sp, nb, n_env, a[t][0], a[t][1],
+                block_fma4<kGlobal>(slice + 3 * (size_t)(j < ls ? g.x + j : g.z + (j - ls)), sp, nb, n_env, a[t][0], a[t][1],
                            a[t][2]);
         }
     }
@@ -223,7 +247,7 @@ __global__ void __launch_bounds__(kPcgcThreads, kMinBlocks) k_pcg_cluster(PcgcAr
     int4* s_rng = smi;                         // [max_tasks] block ranges of the SpMV tasks in S and C
     int4* s_chunk = s_rng + max_tasks;         // [chunk_cap] (task, first, end) of each SpMV chunk
     int* s_cpre = (int*)(s_chunk + a.chunk_cap);  // [max_tasks + 1] first chunk of each task
-    Real* s_w = (Real*)(s_cpre + ((max_tasks + 4) & ~3));  // [3][NW] warp partials
+    Real* s_w = (Real*)(s_cpre + ((max_tasks + 4) & ~3));  // [3][NW] warp partials of the all-reduce
     Real* s_part = s_w + 3 * NW;       // [4] this CTA's partials (read by the cluster)
     Real* s_tot = s_part + 4;          // [4] cluster totals
     constexpr int PS = pcgc_pstride<Real>();
@@ -238,7 +262,7 @@ __global__ void __launch_bounds__(kPcgcThreads, kMinBlocks) k_pcg_cluster(PcgcAr
     // reduction buffers of cluster_allreduce: [0] the p.q sum, [1] the r.z
     // and r.r sums (alternating uses never overlap: see the hazard note at
     // the loop)
-    __shared__ Real s_red[2][2 * kPcgcMaxCluster * (kPcgcThreads / 32)];
+    __shared__ Real s_red[2][2 * kPcgcMaxCluster];
     Real* zw = a.z;                                 // z, 3 per node, in global memory
     const Real* __restrict__ zg = a.z;
 
@@ -438,7 +462,7 @@ __global__ void __launch_bounds__(kPcgcThreads, kMinBlocks) k_pcg_cluster(PcgcAr
     // the all-reduce's cluster barrier also orders s_rng, the chunks and the
     // staged slice within the CTA
     Real t0[2];
-    cluster_allreduce<2>(cl, acc0, s_red[1], t0);  // r.z, b.b
+    cluster_allreduce<2>(cl, acc0, s_red[1], s_w, t0);  // r.z, b.b
     Real rz = t0[0];
     const Real bb = t0[1];
     const Real stop2 = (Real)(a.tol2_env ? a.tol2_env[e] : a.tol2) * bb;
@@ -484,7 +508,10 @@ __global__ void __launch_bounds__(kPcgcThreads, kMinBlocks) k_pcg_cluster(PcgcAr
                     const int4 g = s_rng[ch.x];
                     if constexpr (sizeof(Real) == sizeof(float)) {
                         if (staged)
-                            row_part4(slice4, g, ch.y, ch.z, sp4, nb, n_env, gl, y0, y1, y2);
+                            row_part4<false>(slice4, g, ch.y, ch.z, sp4, nb, n_env, gl, y0, y1, y2);
+                        else if (a.pk)
+                            row_part4<true>(a.pk, make_int4(g.x, g.y, g.z + a.pk_c0, g.w + a.pk_c0), ch.y, ch.z, sp4,
+                                            nb, n_env, gl, y0, y1, y2);
                         else
                             row_part(a.S, a.C, g, ch.y, ch.z, s_p, nb, n_env, gl, y0, y1, y2);
                     } else {
@@ -528,7 +555,10 @@ __global__ void __launch_bounds__(kPcgcThreads, kMinBlocks) k_pcg_cluster(PcgcAr
                 const int len = (g.y - g.x) + (g.w - g.z);
                 if constexpr (sizeof(Real) == sizeof(float)) {
                     if (staged)
-                        row_part4(slice4, g, 0, len, sp4, nb, n_env, gl, y0, y1, y2);
+                        row_part4<false>(slice4, g, 0, len, sp4, nb, n_env, gl, y0, y1, y2);
+                    else if (a.pk)
+                        row_part4<true>(a.pk, make_int4(g.x, g.y, g.z + a.pk_c0, g.w + a.pk_c0), 0, len, sp4, nb,
+                                        n_env, gl, y0, y1, y2);
                     else
                         row_part(a.S, a.C, g, 0, len, s_p, nb, n_env, gl, y0, y1, y2);
                 } else {
@@ -551,7 +581,7 @@ __global__ void __launch_bounds__(kPcgcThreads, kMinBlocks) k_pcg_cluster(PcgcAr
         // B2, which every CTA reaches after reading buffer 0; likewise
         // buffer 1 between B2 and the next B1
         Real t1[1];
-        cluster_allreduce<1>(cl, pq, s_red[0], t1);
+        cluster_allreduce<1>(cl, pq, s_red[0], s_w, t1);
         const Real pqt = t1[0];
         if (!(pqt > Real(0))) {  // breakdown: keep x and stop (same in all CTAs); non-finite is an error
             bad = !isfinite(pqt);
@@ -602,7 +632,7 @@ __global__ void __launch_bounds__(kPcgcThreads, kMinBlocks) k_pcg_cluster(PcgcAr
             acc[1] += ra * ra;
         }
         Real t2[2];
-        cluster_allreduce<2>(cl, acc, s_red[1], t2);  // B2
+        cluster_allreduce<2>(cl, acc, s_red[1], s_w, t2);  // B2
         const Real rz_new = t2[0], rr = t2[1];
         ++it;
         if (!isfinite(rr)) bad = done = true;
@@ -625,6 +655,27 @@ __global__ void __launch_bounds__(kPcgcThreads, kMinBlocks) k_pcg_cluster(PcgcAr
         a.conv[e] = bad ? 2 : (done ? 1 : 3);
     }
     cl.sync();  // no CTA leaves while a partner may still read its shared memory
+}
+
+// The FP32 matrix packed for the cluster solve: block k of S, then block k
+// of C at nS + k, as 12 floats (the 9 values, the column as int bits, 2 zero
+// pads), so that an unstaged CTA reads a block with three 16-byte loads
+// instead of ten scalar ones.  The C block count is read on the device; the
+// blocks of converged envs are not written (their clusters return at once).
+__global__ void k_pack_blocks(Geo G, Bsr<float> S, Bsr<float> C, int nS, const int* nC, float4* pk) {
+    const long long n = (long long)nS + *nC;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        const bool in_s = k < nS;
+        const long long j = in_s ? k : k - nS;
+        const int col = in_s ? S.col[j] : C.col[j];
+        if (env_is_done(G, G.node_env[col])) continue;
+        const float* v = (in_s ? S.val : C.val) + 9 * j;
+        float4* o = pk + 3 * k;
+        o[0] = make_float4(v[0], v[1], v[2], v[3]);
+        o[1] = make_float4(v[4], v[5], v[6], v[7]);
+        o[2] = make_float4(v[8], __int_as_float(col), 0.0f, 0.0f);
+    }
 }
 
 // FP64 residual of an FP32 solve: r = b - A x per node (A the stored FP32

@@ -143,6 +143,7 @@ struct zema_scene {
     DBuf<uint64_t> bkey, bkey2, gkey, gkey2, ukey;
     DBuf<double> bstage, gstage, C_val, gsum;
     DBuf<int> C_rowptr, C_col;
+    DBuf<float4> pk;  // the FP32 matrix packed for the cluster solve (k_pack_blocks)
     uint32_t n_cblocks = 0;
     bool n_cblocks_pending = false;  // the count waits in h32[8] for the next read-back
     DBuf<uint32_t> cnt_u;            // unique contact blocks and gradient nodes, on the device
@@ -1680,6 +1681,17 @@ void pcg_t(zema_scene* s, const std::vector<int>& done_h) {
         fail(ZEMA_ERR_INVALID_ARG, "cluster PCG unavailable for this scene on this device");
     const bool use_cluster = s->P.pcg_kind != 1 && s->pcgc_cs[pi] > 0;
     const char* kname = use_cluster ? "k_pcg_cluster" : "k_pcg_persistent";
+    // FP32 cluster solves read the matrix packed (fixed for all solves of
+    // this system, refinements included)
+    const float4* pk = nullptr;
+    if (sizeof(T) == sizeof(float) && use_cluster) {
+        s->pk.ensure(&s->A, 3 * ((size_t)s->n_sblocks + s->C_col.cap) + 3);
+        ZL(k_pack_blocks, 148 * 8, 256, 0, st)(G, Bsr<float>{S.rowptr, S.col, (const float*)S.val},
+                                              Bsr<float>{C.rowptr, C.col, (const float*)C.val}, (int)s->n_sblocks,
+                                              s->C_rowptr.p + s->n_nodes, s->pk.p);
+        ZLAUNCH();
+        pk = s->pk.p;
+    }
     // the iterations and status of the last launch go to pinned memory, to
     // be read after the next synchronisation (pcg_finish)
     auto collect = [&]() {
@@ -1715,6 +1727,8 @@ void pcg_t(zema_scene* s, const std::vector<int>& done_h) {
         c.slice_cap = pcgc_slice_cap<T>(s, cs);
         c.chunk_cap = pcgc_chunk_cap(s, cs);
         c.env_list = nullptr;
+        c.pk = pk;
+        c.pk_c0 = (int)s->n_sblocks;
         if (NE > 1 && !sched_binned(cs)) {
             // longest solves first (the order changes no env's arithmetic)
             if ((int)s->env_cost.size() != NE) {
