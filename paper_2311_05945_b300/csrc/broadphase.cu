@@ -267,7 +267,8 @@ struct Table {
 // k_slots_out then moves the queries whose hits all fit into the output, and
 // the WRITE pass walks again only the queries with more hits (cnt[q] >
 // kQuerySlots), so most queries are walked once.
-constexpr int kQueryLanes = 16;
+constexpr int kQueryLanes = 8;  // a power of two below 32 (most buckets hold a few entries)
+static_assert(kQueryLanes < 32 && (kQueryLanes & (kQueryLanes - 1)) == 0, "query group: power of two below 32");
 constexpr int kQuerySlots = 8;
 template <bool WRITE>
 __global__ void k_query(BPView v, int kind, int nq, const double* qbox, const double* ebox_all, const int* qcb,
@@ -281,8 +282,9 @@ __global__ void k_query(BPView v, int kind, int nq, const double* qbox, const do
         return;
     }
     if (WRITE && cnt[q] <= (uint32_t)kQuerySlots) return;  // already out of its slots (or a large query)
-    const unsigned gshift = threadIdx.x & 16u;
-    const unsigned gmask = 0xFFFFu << gshift;
+    constexpr unsigned kGroupBits = (1u << kQueryLanes) - 1u;
+    const unsigned gshift = threadIdx.x & (32u - kQueryLanes);
+    const unsigned gmask = kGroupBits << gshift;
     Box6 a = ld_box(qbox + 6 * (size_t)q);
     double nc = box_cells(a, v.inv_cell);
     if (!(nc <= kMaxQueryCells)) {
@@ -293,7 +295,7 @@ __global__ void k_query(BPView v, int kind, int nq, const double* qbox, const do
     uint32_t c = 0;  // hits so far, the same in all lanes of the group
     const uint32_t o = WRITE ? off[q] : (uint32_t)kQuerySlots * (uint32_t)q;
     auto emit = [&](bool hit, int e) {
-        const unsigned b = (__ballot_sync(gmask, hit) >> gshift) & 0xFFFFu;
+        const unsigned b = (__ballot_sync(gmask, hit) >> gshift) & kGroupBits;
         const uint32_t at = c + __popc(b & ((1u << l) - 1u));
         if (hit && (WRITE || at < (uint32_t)kQuerySlots)) out[o + at] = make_int2(q, e);
         c += __popc(b);
