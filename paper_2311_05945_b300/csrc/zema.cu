@@ -1730,15 +1730,25 @@ void pcg_t(zema_scene* s, const std::vector<int>& done_h) {
         c.pk = pk;
         c.pk_c0 = (int)s->n_sblocks;
         if (NE > 1 && !sched_binned(cs)) {
-            // longest solves first (the order changes no env's arithmetic)
+            // launch order by the envs' last solve cost (iterations x nodes;
+            // the order changes no env's arithmetic)
             if ((int)s->env_cost.size() != NE) {
                 s->env_cost.resize(NE);
                 for (int e = 0; e < NE; ++e) s->env_cost[e] = s->env_node_start_h[e + 1] - s->env_node_start_h[e];
             }
-            std::vector<int> order(NE);
-            for (int e = 0; e < NE; ++e) order[e] = e;
-            std::stable_sort(order.begin(), order.end(),
+            std::vector<int> by_cost(NE), order;
+            for (int e = 0; e < NE; ++e) by_cost[e] = e;
+            std::stable_sort(by_cost.begin(), by_cost.end(),
                              [&](int a, int b) { return s->env_cost[a] > s->env_cost[b]; });
+            // the costliest first, each followed by the cheapest left, so
+            // that the clusters resident at once keep a mixed working set
+            // (all-large first waves overflow L2 and re-read their matrices
+            // from DRAM every iteration)
+            order.reserve(NE);
+            for (int i = 0, j = NE - 1; i <= j; ++i, --j) {
+                order.push_back(by_cost[i]);
+                if (i != j) order.push_back(by_cost[j]);
+            }
             if (order != s->env_order_h) {
                 s->env_order_h = order;
                 s->env_order.ensure(&s->A, NE);
