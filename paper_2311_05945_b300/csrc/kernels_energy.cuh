@@ -673,65 +673,75 @@ __device__ __forceinline__ double pair_eps_x(const Geo& G, const PairRec& r) {
     return 1e-3 * dot(a, a) * dot(b, b);
 }
 
-// Barrier gradient (FP64) and PSD-projected Hessian (T) of up to 32 pairs
-// per warp (one warp per block):
-//   phase 1  one pair per lane: distance type, barrier value and FP64
-//            gradient, and the 12x12 slot-space Hessian into shared memory
-//            (all lanes busy, so the FP64 instructions are issued once per 32
-//            pairs instead of once per 2);
-//   phase 2  each half-warp projects its 16 pairs in turn with the 16-lane
-//            Jacobi of barrier_coop.cuh, reusing one scratch area.
-// load(i, x, is_ee, eps_x, kappa) supplies pair i's stencil.  A Hessian
-// outside T's range (degenerate stencil) is left out; the pair still
-// contributes its exact FP64 gradient.
-constexpr int kWarpPairs = 32;
-constexpr int kHPad = 145;  // per-pair stride in shared memory: odd, so the 32 lanes' slots fall in distinct banks
+// Barrier gradient (FP64) and PSD-projected Hessian (T) of many pairs, in
+// two launches so that each runs within its own register budget:
+//   raw      one pair per thread: distance type, barrier value and FP64
+//            gradient, and the unprojected 12x12 slot-space Hessian written
+//            in place of the pair's output block; flag 1 marks a block to
+//            project (0: inactive pair);
+//   project  one pair per half-warp at 64 registers per thread (four times
+//            the resident warps of the raw pass): the block into shared
+//            memory, then the 16-lane Jacobi projection of barrier_coop.cuh
+//            back into the output block.
+// The arithmetic and its order are those of the one-pair-per-half-warp form
+// below, so both give the same bits.  load(i, x, is_ee, eps_x, kappa)
+// supplies pair i's stencil.  A Hessian outside T's range (degenerate
+// stencil) is left out; the pair still contributes its exact FP64 gradient.
+constexpr int kRawThreads = 32;  // one warp per block: 32 Hessian blocks in shared memory
+constexpr int kRawPad = 145;     // per-pair stride in shared memory: odd, so the 32 lanes' slots fall in distinct banks
+constexpr int kProjPairs = 8;    // pairs per 128-thread block of the projection
 
 template <class T, class Load>
-__device__ __forceinline__ void barrier_gh_warp(int n, const Load& load, double dhat, T* pH, double* pG,
-                                                double* pE) {
-    __shared__ T sH[kWarpPairs][kHPad];
-    __shared__ T sVs[2][100];
-    __shared__ T sLam[2][16];
-    __shared__ int sAct[kWarpPairs];
-    __shared__ double sKap[kWarpPairs];
-    const int lane = threadIdx.x & 31;
-    const int base = blockIdx.x * kWarpPairs;
+__device__ __forceinline__ void barrier_gh_raw(int n, const Load& load, double dhat, T* pH, double* pG, double* pE,
+                                               int* flag) {
+    __shared__ T sH[kRawThreads][kRawPad];
+    const int lane = threadIdx.x;
+    const int base = blockIdx.x * kRawThreads;
     const int i = base + lane;
-    int act = 0;
-    double kap = 0.0;
     if (i < n) {
         V3 x[4];
         int is_ee;
-        double eps_x;
+        double eps_x, kap, E = 0.0, g12[12];
         load(i, x, is_ee, eps_x, kap);
-        double E = 0.0, g12[12];
-        act = pair_barrier<T>(x, is_ee != 0, dhat, kap, eps_x, E, g12, SMat<12, T>{sH[lane], 1}, true);
+        const int act =
+            pair_barrier<T>(x, is_ee != 0, dhat, kap, eps_x, E, g12, SMat<12, T>{sH[lane], 1}, true);
         for (int a = 0; a < 12; ++a) pG[(size_t)i * 12 + a] = act ? g12[a] : 0.0;
         if (pE) pE[i] = act ? E : 0.0;
-        if (act) {
-            bool finite = true;
-            for (int a = 0; a < 144; ++a) finite &= isfinite(sH[lane][a]);
-            if (!finite) act = 2;
-        }
+        flag[i] = act ? 1 : 0;
     }
-    sAct[lane] = act;
-    sKap[lane] = kap;
     __syncwarp();
-    const int half = lane >> 4, hl = lane & 15;
-    const unsigned mask = 0xFFFFu << (lane & 16);
-    for (int k = 0; k < 16; ++k) {
-        const int p = 16 * half + k;
-        const int ip = base + p;
-        if (ip >= n) break;  // uniform over the half-warp
-        T* out = pH + (size_t)ip * 144;
-        if (sAct[p] != 1) {
-            for (int e = hl; e < 144; e += kCoopLanes) out[e] = T(0);
-            continue;
-        }
-        coop_project<T>(sH[p], sVs[half], sLam[half], sKap[p], out, mask);
-        __syncwarp(mask);  // the scratch is reused by the next pair
+    // the warp's blocks are contiguous in pH: one coalesced sweep
+    const int m = min(kRawThreads, n - base);
+    for (int k = lane; k < 144 * m; k += kRawThreads) {
+        const int p = k / 144;
+        pH[(size_t)base * 144 + k] = sH[p][k - 144 * p];
     }
+}
+
+template <class T>
+__device__ __forceinline__ void barrier_project_half(int n, double kap, const int* flag, T* pH) {
+    __shared__ T sm[kProjPairs][kCoopSmem];
+    const int grp = threadIdx.x / kCoopLanes, lane = threadIdx.x & (kCoopLanes - 1);
+    const int i = blockIdx.x * kProjPairs + grp;
+    if (i >= n) return;  // the whole half-warp
+    const unsigned mask = 0xFFFFu << (threadIdx.x & 16);
+    T* out = pH + (size_t)i * 144;
+    T* H = sm[grp];
+    const bool act = flag[i] == 1;
+    bool finite = true;
+    if (act)
+        for (int e = lane; e < 144; e += kCoopLanes) {
+            const T v = out[e];
+            H[e] = v;
+            finite &= isfinite(v);
+        }
+    finite = __all_sync(mask, finite);
+    if (!act || !finite) {
+        for (int e = lane; e < 144; e += kCoopLanes) out[e] = T(0);
+        return;
+    }
+    __syncwarp(mask);
+    coop_project<T>(H, H + 144, H + 244, kap, out, mask);
 }
 
 // Few pairs (an IPC step often has only hundreds): one pair per half-warp,
@@ -776,11 +786,12 @@ __global__ void __launch_bounds__(kCoopLanes * kCoopPairs) k_barrier_gh_half(Geo
     coop_project<T>(H, H + 144, H + 244, kap, out, mask);
 }
 
-// Many pairs: the warp layout above (32 pairs per warp).
-constexpr int kWarpLayoutMinPairs = 16384;
+// Many pairs: the two-launch form above.
+constexpr int kSplitMinPairs = 16384;
 template <class T>
-__global__ void __launch_bounds__(kWarpPairs) k_barrier_gh(Geo G, const double* X, const PairRec* rec, int n,
-                                                          const double* kappa_env, T* pH, double* pG) {
+__global__ void __launch_bounds__(kRawThreads) k_barrier_gh_raw(Geo G, const double* X, const PairRec* rec, int n,
+                                                               const double* kappa_env, T* pH, double* pG,
+                                                               int* flag) {
     auto load = [&](int i, V3* x, int& is_ee, double& eps_x, double& kap) {
         const PairRec r = rec[i];
         for (int k = 0; k < 4; ++k) x[k] = ld3(X + 3 * (size_t)r.s[k]);
@@ -788,7 +799,16 @@ __global__ void __launch_bounds__(kWarpPairs) k_barrier_gh(Geo G, const double* 
         eps_x = pair_eps_x(G, r);
         kap = kappa_env[G.sv_env[r.s[0]]];
     };
-    barrier_gh_warp<T>(n, load, G.dhat, pH, pG, nullptr);
+    barrier_gh_raw<T>(n, load, G.dhat, pH, pG, nullptr, flag);
+}
+
+template <class T>
+__global__ void __launch_bounds__(kCoopLanes * kProjPairs, 8) k_barrier_project(Geo G, const PairRec* rec, int n,
+                                                                                 const double* kappa_env,
+                                                                                 const int* flag, T* pH) {
+    const int i = blockIdx.x * kProjPairs + (int)(threadIdx.x / kCoopLanes);
+    const double kap = i < n ? kappa_env[G.sv_env[rec[i].s[0]]] : 0.0;
+    barrier_project_half<T>(n, kap, flag, pH);
 }
 
 // barrier energy over a pair list per env (ranges from env_off)

@@ -137,6 +137,7 @@ struct zema_scene {
     DBuf<PairRec> cand, act, swept, lag, recs;
     DBuf<uint32_t> flag, flagoff, pt_env, ee_env, m_env, act_env, swept_env, lag_env, tmp32;
     DBuf<double> lag_w, lag_n, lag_c, pH, pG;
+    DBuf<int> pflag;  // per active pair: its Hessian block awaits projection
     uint32_t n_act = 0, n_swept = 0, n_lag = 0;
     // contact assembly
     DBuf<uint32_t> cnt_blk, off_blk, cnt_g, off_g, bval, bval2, gval, gval2, head, hoff, seg;
@@ -1299,10 +1300,13 @@ void grad_hess_t(zema_scene* s, bool barrier, bool friction, bool hess) {
     if (na) {
         // few pairs: a half-warp per pair keeps many warps busy; many pairs:
         // 32 per warp issues the FP64 part once per 32 pairs
-        if (na >= (uint32_t)kWarpLayoutMinPairs)
-            ZL(k_barrier_gh<T>, div_up(na, kWarpPairs), kWarpPairs, 0, st)(G, s->X.p, s->act.p, (int)na, s->kappa.p,
-                                                                          pH, s->pG.p);
-        else
+        if (na >= (uint32_t)kSplitMinPairs) {
+            s->pflag.ensure(A, na + 1);
+            ZL(k_barrier_gh_raw<T>, div_up(na, kRawThreads), kRawThreads, 0, st)(G, s->X.p, s->act.p, (int)na,
+                                                                               s->kappa.p, pH, s->pG.p, s->pflag.p);
+            ZL(k_barrier_project<T>, div_up(na, kProjPairs), kCoopLanes * kProjPairs, 0, st)(
+                G, s->act.p, (int)na, s->kappa.p, s->pflag.p, pH);
+        } else
             ZL(k_barrier_gh_half<T>, div_up(na, kCoopPairs), kCoopLanes * kCoopPairs, 0, st)(
                 G, s->X.p, s->act.p, (int)na, s->kappa.p, pH, s->pG.p);
     }
@@ -3324,17 +3328,21 @@ __global__ void k_sv_env_of(const int* sv_body, const int* b_env, int n, int* sv
     if (i < n) sv_env[i] = b_env[sv_body[i]];
 }
 
-// the scene's barrier kernel on caller stencils (kappa = 1)
-__global__ void __launch_bounds__(kWarpPairs) k_local_barrier(const double* x12, const int* is_ee,
-                                                             const double* eps_x, int n, double dhat,
-                                                             double* e_out, double* g_out, double* H_out) {
+// the scene's barrier kernels (the two-launch form) on caller stencils (kappa = 1)
+__global__ void __launch_bounds__(kRawThreads) k_local_barrier(const double* x12, const int* is_ee,
+                                                              const double* eps_x, int n, double dhat, double* e_out,
+                                                              double* g_out, double* H_out, int* flag) {
     auto load = [&](int i, V3* x, int& ee, double& eps, double& kap) {
         for (int k = 0; k < 4; ++k) x[k] = ld3(x12 + 12 * (size_t)i + 3 * k);
         ee = is_ee[i];
         eps = eps_x[i];
         kap = 1.0;
     };
-    barrier_gh_warp<double>(n, load, dhat, H_out, g_out, e_out);
+    barrier_gh_raw<double>(n, load, dhat, H_out, g_out, e_out, flag);
+}
+
+__global__ void __launch_bounds__(kCoopLanes * kProjPairs) k_local_project(int n, const int* flag, double* H_out) {
+    barrier_project_half<double>(n, 1.0, flag, H_out);
 }
 
 __global__ void k_local_distance(const double* x12, const int* is_ee, int n, double* d2, double* w) {
@@ -3510,7 +3518,9 @@ zema_status zema_local_barrier(int64_t n, const double* x12, const int32_t* is_e
         double* E = T.put<double>(nullptr, (size_t)n);
         double* g = T.put<double>(nullptr, 12 * (size_t)n);
         double* H = T.put<double>(nullptr, 144 * (size_t)n);
-        ZL(k_local_barrier, div_up(n, kWarpPairs), kWarpPairs, 0, st)(dx, de, dp, (int)n, dhat, E, g, H);
+        int* flag = T.put<int>(nullptr, (size_t)n);
+        ZL(k_local_barrier, div_up(n, kRawThreads), kRawThreads, 0, st)(dx, de, dp, (int)n, dhat, E, g, H, flag);
+        ZL(k_local_project, div_up(n, kProjPairs), kCoopLanes * kProjPairs, 0, st)((int)n, flag, H);
         ZLAUNCH();
         get(e_out, E, n, st);
         get(g_out, g, 12 * n, st);
