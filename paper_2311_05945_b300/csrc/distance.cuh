@@ -680,8 +680,34 @@ __device__ inline bool pair_barrier(const V3* x, bool is_ee, double dhat, double
 }
 
 // energy only: kappa * e * b(d), 0 when inactive
+// Squared gap between the bounding boxes of a stencil's two primitives (the
+// point x0 and the triangle x1 x2 x3, or the edges x0 x1 and x2 x3): a lower
+// bound of the squared distance, from differences, min and max only (a few
+// FP64 operations against the hundreds of the distance classification).
+__device__ __forceinline__ double stencil_box_gap2(const V3* x, bool is_ee) {
+    auto axis = [&](double a0, double a1, double b0, double b1, double b2) {
+        const double amin = is_ee ? fmin(a0, a1) : a0, amax = is_ee ? fmax(a0, a1) : a0;
+        const double bmin = is_ee ? fmin(b1, b2) : fmin(b0, fmin(b1, b2));
+        const double bmax = is_ee ? fmax(b1, b2) : fmax(b0, fmax(b1, b2));
+        const double g = fmax(fmax(bmin - amax, amin - bmax), 0.0);
+        return g * g;
+    };
+    // edges: (x0, x1) against (x2, x3); point-triangle: x0 against (x1, x2, x3)
+    return axis(x[0].x, x[1].x, x[1].x, x[2].x, x[3].x) + axis(x[0].y, x[1].y, x[1].y, x[2].y, x[3].y) +
+           axis(x[0].z, x[1].z, x[1].z, x[2].z, x[3].z);
+}
+
+// whether a stencil is certainly farther apart than dhat: its box gap
+// exceeds dhat with a 1 % margin, far above the rounding of either
+// computation, so the exact distance is at least dhat and the barrier, its
+// derivatives and the active flag are all exactly zero
+__device__ __forceinline__ bool stencil_beyond(const V3* x, bool is_ee, double dhat) {
+    return stencil_box_gap2(x, is_ee) > 1.0201 * dhat * dhat;
+}
+
 __device__ inline double pair_barrier_energy(const V3* x, bool is_ee, double dhat, double kappa, double eps_x,
                                              double* dist_out) {
+    if (!dist_out && stencil_beyond(x, is_ee, dhat)) return 0.0;
     double d2 = stencil_d2(x, is_ee);
     double d = sqrt(d2);
     if (dist_out) *dist_out = d;

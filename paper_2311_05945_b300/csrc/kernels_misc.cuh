@@ -108,6 +108,16 @@ __device__ inline double accd(const V3* x0, const V3* p0, bool is_ee, double s, 
     double tl = (1.0 - s) * d / lp;
     for (int it = 0; it < max_iter; ++it) {
         for (int k = 0; k < 4; ++k) x[k] = x[k] + tl * p[k];
+        if (it == 0) {
+            // t is 0 here, so the distance only sets the next advance: a
+            // first advance past t_c (a pair far apart for its motion) ends
+            // without it
+            t += tl;
+            if (t > tc) return tc;
+            d = sqrt(stencil_d2(x, is_ee));
+            tl = 0.9 * d / lp;
+            continue;
+        }
         d = sqrt(stencil_d2(x, is_ee));
         if (t > 0.0 && d < gap) return t;
         t += tl;
@@ -145,6 +155,10 @@ __global__ void k_active_flags(Geo G, const double* X, const PairRec* rec, int n
     PairRec r = rec[i];
     V3 x[4];
     load_stencil(X, r, x);
+    if (stencil_beyond(x, r.is_ee != 0, G.dhat)) {
+        flag[i] = 0u;
+        return;
+    }
     double d = sqrt(stencil_d2(x, r.is_ee != 0));
     bool a = d < G.dhat;
     flag[i] = a ? 1u : 0u;
