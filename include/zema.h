@@ -159,6 +159,16 @@ zema_status zema_finalize(zema_scene* s);
  * step (Eq. 13). */
 zema_status zema_set_kinematic_target(zema_scene* s, int32_t body, const double q_target[12]);
 
+/* The same for n kinematic bodies in one call (Eq. 13; the batched form of
+ * the scripted grasps of the paper's parallel grasp generation): bodies (n
+ * ids of affine bodies, each at most once) and q_targets (n x 12, caller's
+ * frame, row k for bodies[k]), both host memory, read before the call
+ * returns.  One host-to-device copy and one scatter on the scene's stream,
+ * ordered before the next step; the call does not wait for them.
+ * ZEMA_ERR_INVALID_ARG (nothing set) for a negative n, a NULL array with
+ * n > 0, an id that is not an affine body, or a repeated id. */
+zema_status zema_set_kinematic_targets(zema_scene* s, int64_t n, const int32_t* bodies, const double* q_targets);
+
 /* Advances n_steps time steps (Eq. 11).  stats may be NULL.  Errors:
  * ZEMA_ERR_NEWTON_MAXITER (no convergence within max_newton iterations),
  * ZEMA_ERR_LINESEARCH (no energy decrease after 60 halvings),

@@ -36,7 +36,9 @@ struct ZemaError {
 long long& launch_counter();
 struct LaunchScope {
     bool timed;
-    explicit LaunchScope(const char* name);
+    // count = false: a region around launches counted on their own (timed
+    // as one when it is the selected kernel)
+    explicit LaunchScope(const char* name, bool count = true);
     ~LaunchScope();
 };
 void set_current_stream(cudaStream_t st);

@@ -38,8 +38,8 @@ void alg_bytes_add(const char* name, double bytes) {
     if (P.on && P.name == name) P.bytes += bytes;
 }
 
-LaunchScope::LaunchScope(const char* name) : timed(false) {
-    ++launch_counter();
+LaunchScope::LaunchScope(const char* name, bool count) : timed(false) {
+    if (count) ++launch_counter();
     Prof& P = prof();
     if (!P.on) return;
     // match the kernel name, ignoring template arguments

@@ -208,8 +208,27 @@ struct zema_scene {
     DBuf<float> ws_feat, ws_out;
     float* rec_feat = nullptr;  // caller's device buffers while recording
     float* rec_targ = nullptr;
+    // zema_set_kinematic_targets: pinned staging of (device affine index,
+    // 12 target values) records, their device copy, and the event after the
+    // copy out of the staging (waited on before the staging is rewritten)
+    mutable std::vector<int> aff_dev_of_input;  // device index of each affine body (order of addition)
+    // size-binned solves: one stream per cluster size, the fork event and
+    // the join events
+    cudaStream_t bin_st[5] = {};
+    cudaEvent_t bin_fork = nullptr, bin_join[5] = {};
+    double* h_kin = nullptr;
+    size_t h_kin_cap = 0;
+    DBuf<double> kin_up;
+    cudaEvent_t kin_ev = nullptr;
 
     ~zema_scene() {
+        if (h_kin) cudaFreeHost(h_kin);
+        for (int k = 0; k < 5; ++k) {
+            if (bin_st[k]) cudaStreamDestroy(bin_st[k]);
+            if (bin_join[k]) cudaEventDestroy(bin_join[k]);
+        }
+        if (bin_fork) cudaEventDestroy(bin_fork);
+        if (kin_ev) cudaEventDestroy(kin_ev);
         delete ws_net;
         delete ws_anet;
         if (h32) cudaFreeHost(h32);
@@ -1775,16 +1794,30 @@ void pcg_t(zema_scene* s, const std::vector<int>& done_h) {
             ZCHECK(cudaFuncSetAttribute(k_pcg_cluster<T, 2>, cudaFuncAttributePreferredSharedMemoryCarveout, pct));
         }
         if (sched_binned(cs)) {
-            // one launch per env group, each with its own cluster size
+            // one launch per env group, each with its own cluster size, on
+            // streams of their own so that the groups run at once (forked
+            // from and joined back into the scene's stream; timed as one)
             const std::vector<int>& off = pcgc_bins(s, sched_cs(cs));
+            if (!s->bin_fork) {
+                ZCHECK(cudaEventCreateWithFlags(&s->bin_fork, cudaEventDisableTiming));
+                for (int k = 0; k < 5; ++k) {
+                    ZCHECK(cudaStreamCreateWithFlags(&s->bin_st[k], cudaStreamNonBlocking));
+                    ZCHECK(cudaEventCreateWithFlags(&s->bin_join[k], cudaEventDisableTiming));
+                }
+            }
+            LaunchScope region("k_pcg_cluster", false);
+            ZCHECK(cudaEventRecord(s->bin_fork, st));
             for (int k = 0, cg = 1; k < 5; ++k, cg *= 2) {
                 const int ng = off[k + 1] - off[k];
                 if (!ng) continue;
                 c.env_list = s->pcgc_bin_list[sched_cs(cs)].p + off[k];
                 pcgc_config<T>(s, cs, cfg, at, cg, ng);
-                cfg.stream = st;
-                LaunchScope ls("k_pcg_cluster");
+                cfg.stream = s->bin_st[k];
+                ZCHECK(cudaStreamWaitEvent(s->bin_st[k], s->bin_fork, 0));
+                ++launch_counter();
                 ZCHECK(cudaLaunchKernelEx(&cfg, pcgc_kernel<T>(cs), c));
+                ZCHECK(cudaEventRecord(s->bin_join[k], s->bin_st[k]));
+                ZCHECK(cudaStreamWaitEvent(st, s->bin_join[k], 0));
             }
             ZLAUNCH();
             return;
@@ -2515,15 +2548,18 @@ void restore_step(zema_scene* s, bool all) {
 }
 
 int affine_dev_index(const zema_scene* s, int input_idx) {
-    // device affine order = env-major order of input bodies
-    int k = 0;
-    for (int e = 0; e < s->n_envs; ++e)
-        for (size_t i = 0; i < s->ain.size(); ++i)
-            if (s->ain[i].env == e) {
-                if ((int)i == input_idx) return k;
-                ++k;
-            }
-    return -1;
+    // device affine order = env-major order of input bodies (a stable
+    // ordering by env, built once per body count)
+    std::vector<int>& m = s->aff_dev_of_input;
+    if (m.size() != s->ain.size()) {
+        std::vector<int> order(s->ain.size());
+        for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int a, int b) { return s->ain[a].env < s->ain[b].env; });
+        m.assign(order.size(), -1);
+        for (size_t k = 0; k < order.size(); ++k) m[order[k]] = (int)k;
+    }
+    return input_idx >= 0 && input_idx < (int)m.size() ? m[input_idx] : -1;
 }
 
 #define ZEMA_TRY(s)                                  \
@@ -2777,6 +2813,58 @@ zema_status zema_set_kinematic_target(zema_scene* s, int32_t body, const double 
         ZCHECK(cudaMemcpyAsync(s->qtarget.p + 12 * (size_t)a, q_target, 12 * sizeof(double), cudaMemcpyHostToDevice,
                                s->st));
         ZCHECK(cudaStreamSynchronize(s->st));
+        return ZEMA_OK;
+    }
+    ZEMA_CATCH(s)
+}
+
+namespace {
+// records of 13 doubles: the device affine index, then the 12 target values
+__global__ void k_scatter_targets(const double* rec, int n, double* qtarget) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 12 * n) return;
+    const int r = i / 12, c = i - 12 * r;
+    const int a = (int)rec[13 * (size_t)r];
+    qtarget[12 * (size_t)a + c] = rec[13 * (size_t)r + 1 + c];
+}
+}  // namespace
+
+zema_status zema_set_kinematic_targets(zema_scene* s, int64_t n, const int32_t* bodies, const double* q_targets) {
+    if (s) set_current_stream(s->st);
+    if (!s || n < 0 || (n > 0 && (!bodies || !q_targets))) return ZEMA_ERR_INVALID_ARG;
+    std::vector<char> seen(s->bodies.size(), 0);
+    for (int64_t k = 0; k < n; ++k) {
+        const int32_t b = bodies[k];
+        if (b < 0 || b >= (int)s->bodies.size() || s->bodies[b].first != 1 || seen[b]) return ZEMA_ERR_INVALID_ARG;
+        seen[b] = 1;
+    }
+    if (n == 0) return ZEMA_OK;
+    ZEMA_TRY(s) {
+        if (!s->finalized) {
+            zema_status r = zema_finalize(s);
+            if (r != ZEMA_OK) return r;
+        }
+        const size_t need = 13 * (size_t)n;
+        if (!s->kin_ev) ZCHECK(cudaEventCreateWithFlags(&s->kin_ev, cudaEventDisableTiming));
+        // the last call's copy out of the staging has run before it is rewritten
+        ZCHECK(cudaEventSynchronize(s->kin_ev));
+        if (need > s->h_kin_cap) {
+            if (s->h_kin) ZCHECK(cudaFreeHost(s->h_kin));
+            s->h_kin = nullptr;
+            s->h_kin_cap = 0;
+            ZCHECK(cudaMallocHost(&s->h_kin, need * sizeof(double)));
+            s->h_kin_cap = need;
+        }
+        for (int64_t k = 0; k < n; ++k) {
+            double* r = s->h_kin + 13 * (size_t)k;
+            r[0] = (double)affine_dev_index(s, s->bodies[bodies[k]].second);
+            std::memcpy(r + 1, q_targets + 12 * (size_t)k, 12 * sizeof(double));
+        }
+        s->kin_up.ensure(&s->A, need);
+        ZCHECK(cudaMemcpyAsync(s->kin_up.p, s->h_kin, need * sizeof(double), cudaMemcpyHostToDevice, s->st));
+        ZCHECK(cudaEventRecord(s->kin_ev, s->st));
+        ZL(k_scatter_targets, div_up(12 * n, 256), 256, 0, s->st)(s->kin_up.p, (int)n, s->qtarget.p);
+        ZLAUNCH();
         return ZEMA_OK;
     }
     ZEMA_CATCH(s)

@@ -417,6 +417,19 @@ def grasp_script(fingers_all, dt, close_steps=40, hold_steps=60, lift_steps=200,
             out[idx] = pose(q0, sign, step + 1)
         return out
 
+    # the same targets for all fingers at once: (affine indices, (n, 12))
+    idx_all = np.array([f[0] for f in fingers_all], dtype=np.int64)
+    sign_all = np.array([f[1] for f in fingers_all], dtype=np.float64)
+    q0_all = np.array([f[2] for f in fingers_all], dtype=np.float64).reshape(len(fingers_all), 12)
+
+    def arrays(step):
+        n = step + 1
+        Q = q0_all.copy()
+        Q[:, 2] -= sign_all * close_speed * dt * min(n, close_steps)
+        Q[:, 1] += lift_height * min(max(n - close_steps - hold_steps, 0), lift_steps) / lift_steps
+        return idx_all, Q
+
+    script.arrays = arrays
     return script
 
 

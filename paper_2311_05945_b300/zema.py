@@ -83,6 +83,7 @@ def lib():
                                        C.c_double, C.c_double, C.c_int32, IP]
     L.zema_finalize.argtypes = [C.c_void_p]
     L.zema_set_kinematic_target.argtypes = [C.c_void_p, C.c_int32, DP]
+    L.zema_set_kinematic_targets.argtypes = [C.c_void_p, C.c_int64, IP, DP]
     L.zema_step.argtypes = [C.c_void_p, C.c_int32, C.POINTER(StepStats)]
     L.zema_get_state.argtypes = [C.c_void_p, C.c_int32, DP, C.c_int64, LP]
     L.zema_set_state.argtypes = [C.c_void_p, C.c_int32, DP, C.c_int64]
@@ -343,12 +344,25 @@ class Scene:
         qq = _d(q)
         _check(lib().zema_set_kinematic_target(self.h, self.affine_body_id(affine_index), _dp(qq)), self.h)
 
+    def set_kinematic_targets(self, affine_indices, Q):
+        """Targets Q (n, 12) of the kinematic affine bodies affine_indices
+        (n,) for the next step, in one call."""
+        ids = _i(np.array([self.affine_body_id(int(i)) for i in affine_indices], dtype=np.int32))
+        QQ = _d(np.asarray(Q, dtype=np.float64).reshape(len(ids), 12))
+        _check(lib().zema_set_kinematic_targets(self.h, len(ids), _ip(ids), _dp(QQ)), self.h)
+
     def apply_script(self):
         if self.scene.script is None:
             return
-        for idx, q in self.scene.script(self.step_index).items():
-            qq = _d(q)
-            _check(lib().zema_set_kinematic_target(self.h, self.affine_body_id(idx), _dp(qq)), self.h)
+        arrays = getattr(self.scene.script, "arrays", None)
+        if arrays is not None:
+            idx, Q = arrays(self.step_index)
+        else:
+            targets = self.scene.script(self.step_index)
+            idx = list(targets.keys())
+            Q = np.array([targets[i] for i in idx], dtype=np.float64).reshape(len(idx), 12)
+        if len(idx):
+            self.set_kinematic_targets(idx, Q)
 
     def step(self, n: int = 1, script: bool = True) -> dict:
         """Advance n steps (the scene's kinematic script is applied before

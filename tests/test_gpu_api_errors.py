@@ -87,3 +87,37 @@ def test_joint_argument_checks_before_finalize():
     jid = C.c_int32(-1)
     assert L.zema_add_prismatic_joint(h, ids[0], ids[1], dp, 0.0, C.byref(jid)) == 0 and jid.value == 0
     L.zema_destroy_scene(h)
+
+
+def test_batched_kinematic_targets():
+    """zema_set_kinematic_targets sets every listed body's target in one call:
+    a 3-env grasp batch stepped through it follows the per-body calls bit for
+    bit; repeated ids, non-affine ids and NULL arrays are rejected."""
+    from paper_2311_05945_b300 import zema as Z
+    sc = S.scene_c3(n_envs=3, n_steps=8, min_tets=800, max_tets=1200)
+    a = Z.Scene(sc)
+    b = Z.Scene(sc)
+    L = Z.lib()
+    script = sc.script
+    for step in range(6):
+        a.step(1)  # batched call (the script's arrays)
+        for idx, q in script(b.step_index).items():
+            b.set_kinematic_target(idx, q)
+        b.step(1, script=False)
+    for i in range(len(sc.tets)):
+        assert np.array_equal(a.tet_positions(i), b.tet_positions(i))
+    for i in range(len(sc.affines)):
+        assert np.array_equal(a.affine_q(i), b.affine_q(i))
+    h = a.h
+    q = np.zeros((2, 12))
+    dp = q.ctypes.data_as(C.POINTER(C.c_double))
+    fid = a.affine_body_id(script.arrays(0)[0][0])
+    rep = np.array([fid, fid], dtype=np.int32)
+    assert L.zema_set_kinematic_targets(h, 2, rep.ctypes.data_as(C.POINTER(C.c_int32)), dp) == INVALID_ARG
+    soft = np.array([a.tet_body_id(0), fid], dtype=np.int32)
+    assert L.zema_set_kinematic_targets(h, 2, soft.ctypes.data_as(C.POINTER(C.c_int32)), dp) == INVALID_ARG
+    assert L.zema_set_kinematic_targets(h, 2, None, dp) == INVALID_ARG
+    assert L.zema_set_kinematic_targets(h, -1, None, None) == INVALID_ARG
+    assert L.zema_set_kinematic_targets(h, 0, None, None) == 0
+    a.close()
+    b.close()

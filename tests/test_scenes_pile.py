@@ -81,3 +81,17 @@ def test_pile_full_size_counts():
         sp = S._spacing_for_count(kind, 60000, 2.5, hi=0.1)
         m, _ = S._solid(kind, 2.5, sp)
         assert 0.95 * 60000 < 6 * int(m.sum()) < 1.05 * 60000
+
+
+def test_grasp_script_arrays_match_per_finger_targets():
+    """The grasp script's all-fingers form gives the per-finger targets bit
+    for bit at every phase (closing, holding, lifting)."""
+    import numpy as np
+
+    from paper_2311_05945_b300 import scenes as S
+    sc = S.scene_c3(n_envs=3, n_steps=8, min_tets=300, max_tets=400)
+    for step in (0, 5, 39, 40, 99, 100, 150, 299, 400):
+        d = sc.script(step)
+        idx, Q = sc.script.arrays(step)
+        assert list(idx) == list(d.keys())
+        assert np.array_equal(Q, np.array([d[i] for i in idx]))
