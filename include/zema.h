@@ -382,8 +382,9 @@ zema_status zema_autotune(zema_scene* s);
  * 100 for the variant that keeps two CTAs resident per SM (half the
  * registers per thread, matrix read through L1/L2).  Codes from 1000 are
  * size-binned: every env runs with m times the smallest cluster whose CTAs
- * hold its rows (at most 16; m = code % 100, 1 or 2; plus 100 again for two
- * CTAs per SM), one launch per cluster size.  The autotuner tries them all,
+ * hold its rows (at most 16; m = code % 100, 1, 2 or 4; plus 100 again for
+ * two CTAs per SM), one launch per cluster size, each on a stream of its own
+ * so that the sizes run at once.  The autotuner tries them all,
  * since with many envs of uneven sizes the solve is bound by how many
  * clusters run at once. */
 zema_status zema_get_tuning(const zema_scene* s, int32_t precision, int32_t* cluster_size, int32_t* cand, float* ms,

@@ -56,6 +56,13 @@ struct PcgcArgs {
     const int* env_list; // nullable: cluster k solves env env_list[k] (a group of envs), else env k
     const float4* pk;    // nullable (FP32 only): S then C packed by k_pack_blocks, read by unstaged CTAs
     int pk_c0;           // index of C's first block in pk
+    // FP64 residual refinement inside the launch (FP32 solves): up to
+    // `refine` rounds of r = b - A x in FP64 and, while |r|^2 > tol2 |b|^2,
+    // a correction solve of A d = r added to x; 0 = none.  r64: 3 doubles
+    // per node of scratch; refines (nullable): per env, the rounds taken
+    int refine;
+    double* r64;
+    int* refines;
 };
 
 constexpr int kPcgcThreads = 512;
@@ -64,6 +71,7 @@ constexpr int kPcgcMaxCluster = 16;
 constexpr int kPcgcStageBatch = 16;  // values of z per thread whose loads are issued together
 constexpr int kPcgcOwn = 2;         // soft rows per thread: a CTA owns at most 2 * kPcgcThreads rows
 constexpr int kPcgcRefine = 3;      // FP64 residual refinements of an FP32 solve
+constexpr int kPcgcRefAff = 16;     // affine bodies per env up to which the refinement runs in the launch
 constexpr int kPcgcChunk = 8;       // blocks per SpMV chunk
 constexpr int kPcgcRowIlp = 4;      // blocks per lane whose loads are issued together (matrix in L1/L2)
 // values per node of the staged p vector
@@ -225,6 +233,46 @@ __device__ __forceinline__ Real group_sum(Real v) {
     return v;
 }
 
+// FP64 products of the blocks [jb, je) of a task's combined range (S, then
+// C) with the FP64 vector xg (global, written earlier in this launch: read
+// through L2), the matrix from the staged slice, the packed FP32 matrix or
+// the BSR arrays, as the SpMV reads it
+template <class Real>
+__device__ __forceinline__ void row_part64(const PcgcArgs<Real>& a, bool staged, const float* smv, int4 g, int jb,
+                                           int je, const double* xg, int gl, double& y0, double& y1, double& y2) {
+    const int ls = g.y - g.x;
+    for (int j = jb + gl; j < je; j += kPcgcGroup) {
+        const bool in_s = j < ls;
+        double v[9];
+        int col;
+        if (staged) {
+            const int k = in_s ? g.x + j : g.z + (j - ls);
+            const float* r = smv + 12 * (size_t)k;
+#pragma unroll
+            for (int c = 0; c < 9; ++c) v[c] = r[c];
+            col = __float_as_int(r[9]);
+        } else if (a.pk) {
+            const int k = in_s ? g.x + j : a.pk_c0 + g.z + (j - ls);
+            const float4 q0 = __ldg(a.pk + 3 * (size_t)k), q1 = __ldg(a.pk + 3 * (size_t)k + 1),
+                         q2 = __ldg(a.pk + 3 * (size_t)k + 2);
+            v[0] = q0.x, v[1] = q0.y, v[2] = q0.z, v[3] = q0.w, v[4] = q1.x, v[5] = q1.y, v[6] = q1.z, v[7] = q1.w;
+            v[8] = q2.x;
+            col = __float_as_int(q2.y);
+        } else {
+            const int k = in_s ? g.x + j : g.z + (j - ls);
+            const Real* r = (in_s ? a.S.val : a.C.val) + 9 * (size_t)k;
+#pragma unroll
+            for (int c = 0; c < 9; ++c) v[c] = (double)r[c];
+            col = (in_s ? a.S.col : a.C.col)[k];
+        }
+        const double x0 = __ldcg(xg + 3 * (size_t)col), x1 = __ldcg(xg + 3 * (size_t)col + 1),
+                     x2 = __ldcg(xg + 3 * (size_t)col + 2);
+        y0 += v[0] * x0 + v[1] * x1 + v[2] * x2;
+        y1 += v[3] * x0 + v[4] * x1 + v[5] * x2;
+        y2 += v[6] * x0 + v[7] * x1 + v[8] * x2;
+    }
+}
+
 // kMinBlocks CTAs resident per SM: 1 keeps every owned row's state in
 // registers and may stage the matrix slice in shared memory (few envs); 2
 // halves the register budget (the compiler spills the preconditioner blocks
@@ -314,24 +362,37 @@ __global__ void __launch_bounds__(kPcgcThreads, kMinBlocks) k_pcg_cluster(PcgcAr
     // in the last rank, component tid of the affine rows (tid < 12 n_aff)
     const bool own_a = aff_owner && tid < 12 * n_aff;
 
-    // ---- init: x = 0, r = b, z = M^-1 r (x, r and the 3x3 blocks of M^-1
-    // stay in registers for the whole solve); partial r.z and b.b
+    // the 3x3 blocks of M^-1 of the owned rows, and the affine owner's rows
+    // of its bodies' 12x12 blocks, stay in registers for the whole launch
     Real xs[kPcgcOwn][3], rs[kPcgcOwn][3], Ms[kPcgcOwn][9];
     Real xa = 0, ra = 0, Ma[12];
-    Real acc0[2] = {0, 0};  // this thread's share of r.z and b.b
-    {
-        Real (&acc)[2] = acc0;
+#pragma unroll
+    for (int j = 0; j < kPcgcOwn; ++j) {
+        const int i = tid + j * kPcgcThreads;
+        if (i >= n_own) continue;
+        const Real* M = a.Minv_s + 9 * (size_t)(lo + i);
+#pragma unroll
+        for (int c = 0; c < 9; ++c) Ms[j][c] = M[c];
+    }
+    if (own_a) {
+        const int bi = tid / 12, i = tid - 12 * bi;
+        const Real* M = a.Minv_a + 144 * (size_t)(ab0 + bi) + 12 * i;
+#pragma unroll
+        for (int c = 0; c < 12; ++c) Ma[c] = M[c];
+    }
+    // ---- init of a solve from the right-hand side rhs (b, or the FP64
+    // residual of a refinement round): x = 0, r = rhs, z = M^-1 r (x and r
+    // stay in registers); the thread's share of r.z and r.r into acc
+    auto init = [&](const double* rhs, Real (&acc)[2]) {
+        acc[0] = acc[1] = 0;
 #pragma unroll
         for (int j = 0; j < kPcgcOwn; ++j) {
             const int i = tid + j * kPcgcThreads;
             if (i >= n_own) continue;
             const size_t o = 3 * (size_t)(lo + i);
-            const Real* M = a.Minv_s + 9 * (size_t)(lo + i);
-#pragma unroll
-            for (int c = 0; c < 9; ++c) Ms[j][c] = M[c];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                rs[j][c] = (Real)a.b[o + c];
+                rs[j][c] = (Real)rhs[o + c];
                 xs[j][c] = 0;
             }
 #pragma unroll
@@ -342,12 +403,9 @@ __global__ void __launch_bounds__(kPcgcThreads, kMinBlocks) k_pcg_cluster(PcgcAr
                 acc[1] += rs[j][c] * rs[j][c];
             }
         }
+        xa = 0;
         if (own_a) {
-            const int bi = tid / 12, i = tid - 12 * bi;
-            const Real* M = a.Minv_a + 144 * (size_t)(ab0 + bi) + 12 * i;
-#pragma unroll
-            for (int c = 0; c < 12; ++c) Ma[c] = M[c];
-            ra = (Real)a.b[3 * (size_t)ns1 + tid];
+            ra = (Real)rhs[3 * (size_t)ns1 + tid];
             s_ra[tid] = ra;
         }
         __syncthreads();
@@ -360,7 +418,9 @@ __global__ void __launch_bounds__(kPcgcThreads, kMinBlocks) k_pcg_cluster(PcgcAr
             acc[0] += ra * z;
             acc[1] += ra * ra;
         }
-    }
+    };
+    Real acc0[2];
+    init(a.b, acc0);
     // block ranges of this CTA's SpMV tasks (fixed for the solve)
     const int n_tasks = n_own + n_arow;
     for (int task = tid; task < n_tasks; task += kPcgcThreads) {
@@ -459,20 +519,27 @@ __global__ void __launch_bounds__(kPcgcThreads, kMinBlocks) k_pcg_cluster(PcgcAr
             for (int c = s_cpre[t], j = 0; c < s_cpre[t + 1]; ++c, j += kPcgcChunk)
                 s_chunk[c] = make_int4(t, j, min(len, j + kPcgcChunk), 0);
         }
+    constexpr int kGroupsPerWarp = 32 / kPcgcGroup;
+    const int warp = tid >> 5, sub = (tid & 31) / kPcgcGroup, gl = tid & (kPcgcGroup - 1);
+    const int n_groups = kPcgcThreads / kPcgcGroup;
+    // FP64 reductions and affine partial products of the refinement rounds
+    __shared__ double s_red64[2 * kPcgcMaxCluster];
+    __shared__ double s_w64[2 * NW];
+    __shared__ double s_qa64[12 * kPcgcRefAff];
+    Real tol_pass = (Real)(a.tol2_env ? a.tol2_env[e] : a.tol2);
+    int it_total = 0, n_ref = 0, status = 3;
+    for (int pass = 0;; ++pass) {
     // the all-reduce's cluster barrier also orders s_rng, the chunks and the
-    // staged slice within the CTA
+    // staged slice within the CTA (and, in later passes, z of the new init)
     Real t0[2];
-    cluster_allreduce<2>(cl, acc0, s_red[1], s_w, t0);  // r.z, b.b
+    cluster_allreduce<2>(cl, acc0, s_red[1], s_w, t0);  // r.z, r.r
     Real rz = t0[0];
     const Real bb = t0[1];
-    const Real stop2 = (Real)(a.tol2_env ? a.tol2_env[e] : a.tol2) * bb;
+    const Real stop2 = tol_pass * bb;
     bool bad = !isfinite(bb);
     bool done = bad || !(bb > Real(0));
     Real beta = 0;
     int it = 0;
-    constexpr int kGroupsPerWarp = 32 / kPcgcGroup;
-    const int warp = tid >> 5, sub = (tid & 31) / kPcgcGroup, gl = tid & (kPcgcGroup - 1);
-    const int n_groups = kPcgcThreads / kPcgcGroup;
     while (!done && it < a.max_iter) {
         // ---- p_k = z_k + beta p_{k-1} over the env, in place (every CTA
         // holds the same p); z comes from L2, written there by its owner
@@ -640,19 +707,87 @@ __global__ void __launch_bounds__(kPcgcThreads, kMinBlocks) k_pcg_cluster(PcgcAr
         beta = rz != Real(0) ? rz_new / rz : Real(0);
         rz = rz_new;
     }
-    // solution out (double) for the owned units
+    it_total += it;
+    // solution out (double) for the owned units: x of the first pass, plus
+    // the correction d of each refinement round
 #pragma unroll
     for (int j = 0; j < kPcgcOwn; ++j) {
         const int i = tid + j * kPcgcThreads;
         if (i >= n_own) continue;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) a.x_out[3 * (size_t)(lo + i) + c] = (double)xs[j][c];
+        for (int c = 0; c < 3; ++c) {
+            double* xo = a.x_out + 3 * (size_t)(lo + i) + c;
+            *xo = pass ? *xo + (double)xs[j][c] : (double)xs[j][c];
+        }
     }
-    if (own_a) a.x_out[3 * (size_t)ns1 + tid] = (double)xa;
+    if (own_a) {
+        double* xo = a.x_out + 3 * (size_t)ns1 + tid;
+        *xo = pass ? *xo + (double)xa : (double)xa;
+    }
+    // 2: non-finite right-hand side or matrix; 3: max_iter reached first
+    status = bad ? 2 : (done ? 1 : 3);
+    if (status != 1 || pass >= a.refine) break;
+    // ---- FP64 residual r = b - A x (FP64 products over the stored matrix),
+    // |r|^2 and |b|^2; a correction solve of A d = r while |r|^2 > tol2 |b|^2
+    cl.sync();  // x of every CTA written
+    double acc64[2] = {0.0, 0.0};
+    for (int tb = kGroupsPerWarp * warp; tb < n_tasks; tb += n_groups) {
+        const int task = tb + sub;
+        const bool valid = task < n_tasks;
+        double y0 = 0.0, y1 = 0.0, y2 = 0.0;
+        if (valid) {
+            const int4 g = s_rng[task];
+            row_part64(a, staged, s_mval, g, 0, (g.y - g.x) + (g.w - g.z), a.x_out, gl, y0, y1, y2);
+        }
+        y0 = group_sum(y0);
+        y1 = group_sum(y1);
+        y2 = group_sum(y2);
+        if (valid && gl == 0) {
+            if (task < n_own) {
+                const size_t o = 3 * (size_t)(lo + task);
+                const double b0 = a.b[o], b1 = a.b[o + 1], b2 = a.b[o + 2];
+                const double r0 = b0 - y0, r1 = b1 - y1, r2 = b2 - y2;
+                a.r64[o] = r0;
+                a.r64[o + 1] = r1;
+                a.r64[o + 2] = r2;
+                acc64[0] += r0 * r0 + r1 * r1 + r2 * r2;
+                acc64[1] += b0 * b0 + b1 * b1 + b2 * b2;
+            } else {
+                double* q = s_qa64 + 3 * (task - n_own);
+                q[0] = y0;
+                q[1] = y1;
+                q[2] = y2;
+            }
+        }
+    }
+    cl.sync();  // the CTAs' partial products of the affine rows
+    if (own_a) {
+        double y = 0.0;
+        for (int rk = 0; rk < cs; ++rk) y += cl.map_shared_rank(s_qa64, rk)[tid];
+        const size_t o = 3 * (size_t)ns1 + tid;
+        const double bv = a.b[o], r = bv - y;
+        a.r64[o] = r;
+        acc64[0] += r * r;
+        acc64[1] += bv * bv;
+    }
+    double t64[2];
+    cluster_allreduce<2>(cl, acc64, s_red64, s_w64, t64);
+    if (!isfinite(t64[0])) {
+        status = 2;
+        break;
+    }
+    const double tol2 = a.tol2_env ? a.tol2_env[e] : a.tol2;
+    if (!(t64[0] > tol2 * t64[1])) break;
+    // the correction only has to bring |r - A d| under tol |b|: its solve
+    // stops at half of that, relative to |r|
+    ++n_ref;
+    tol_pass = (Real)fmin(0.25, 0.25 * tol2 * t64[1] / t64[0]);
+    init(a.r64, acc0);
+    }
     if (rank == 0 && tid == 0) {
-        a.iters[e] = it;
-        // 2: non-finite right-hand side or matrix; 3: max_iter reached first
-        a.conv[e] = bad ? 2 : (done ? 1 : 3);
+        a.iters[e] = it_total;
+        a.conv[e] = status;
+        if (a.refines) a.refines[e] = n_ref;
     }
     cl.sync();  // no CTA leaves while a partner may still read its shared memory
 }

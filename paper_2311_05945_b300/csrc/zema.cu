@@ -110,7 +110,7 @@ struct zema_scene {
     // per env
     DBuf<double> tol2_env;
     DBuf<double> kappa, kappa_min, alpha, E, dmin, part, part2, part3, part4, part5, part6, part7;
-    DBuf<int> conv, pcg_iters, need, capflag, skip;
+    DBuf<int> conv, pcg_iters, need, capflag, skip, pcg_refines;
     DBuf<int> tile_u0, tile_u1, tile_n0, tile_n1, tile_env, env_tile_start;
     DBuf<double> pt_a, pt_b, pt_c, pt_d, pt_e;
     int n_tiles = 0, pcg_grid = 0, pcg_grid_f = 0;
@@ -127,8 +127,8 @@ struct zema_scene {
     // size-binned schedules, per multiplier m: the envs of each cluster size
     // 1, 2, 4, 8, 16 (groups in that order) in one device list, and the 6
     // group offsets
-    DBuf<int> pcgc_bin_list[3];
-    std::vector<int> pcgc_bin_off[3];
+    DBuf<int> pcgc_bin_list[5];
+    std::vector<int> pcgc_bin_off[5];
     std::vector<int> S_rowptr_h;  // host copy of the static pattern's row pointers
     std::map<std::pair<int, int>, int> pcgc_cap;  // (value size, CTAs per env) -> staged slice capacity
     DBuf<double> tolv;
@@ -171,6 +171,7 @@ struct zema_scene {
     std::vector<int> env_order_h;
     DBuf<int> env_order;
     int pcg_pending_tsize = 0;
+    bool pcg_pending_refines = false;  // the waiting read-back holds in-launch refinement counts
     const char* pcg_pending_kname = nullptr;
     Geo G{};
     // stats of the current call
@@ -1011,7 +1012,7 @@ void build(zema_scene* s) {
     for (DBuf<double>* b : {&s->kappa, &s->kappa_min, &s->alpha, &s->E, &s->dmin, &s->tol2_env}) b->ensure(A, NE + 1);
     for (DBuf<double>* b : {&s->part, &s->part2, &s->part3, &s->part4, &s->part5, &s->part6, &s->part7})
         b->ensure(A, (size_t)ET_COUNT * NE * kChunks + 8);
-    for (DBuf<int>* b : {&s->conv, &s->pcg_iters, &s->need, &s->skip}) b->ensure(A, NE + 1);
+    for (DBuf<int>* b : {&s->conv, &s->pcg_iters, &s->need, &s->skip, &s->pcg_refines}) b->ensure(A, NE + 1);
     s->capflag.ensure(A, 1);
     for (DBuf<uint32_t>* b : {&s->pt_env, &s->ee_env, &s->m_env, &s->act_env, &s->swept_env, &s->lag_env})
         b->ensure(A, NE + 2);
@@ -1021,7 +1022,7 @@ void build(zema_scene* s) {
     if (!s->h_alpha) ZCHECK(cudaMallocHost(&s->h_alpha, ((size_t)NE + 8) * sizeof(double)));
     if (!s->h_up_i) ZCHECK(cudaMallocHost(&s->h_up_i, (size_t)kUpSlots * NE * sizeof(int)));
     if (!s->h_up_d) ZCHECK(cudaMallocHost(&s->h_up_d, (size_t)kUpSlots * NE * sizeof(double)));
-    if (!s->h_pcg) ZCHECK(cudaMallocHost(&s->h_pcg, (2 * (size_t)NE + 8) * sizeof(int)));
+    if (!s->h_pcg) ZCHECK(cudaMallocHost(&s->h_pcg, (3 * (size_t)NE + 8) * sizeof(int)));
     // learned warm start: soft vertices in node order, their body, per-body
     // node range and rest half-diagonal
     {
@@ -1600,7 +1601,7 @@ template <class T>
 bool pcgc_valid(zema_scene* s, int code) {
     if (sched_binned(code)) {
         const int m = sched_cs(code);
-        if ((m != 1 && m != 2) || pcgc_smem<T>(s, code) > (sched_occ(code) == 2 ? kPcgcMaxSmem2 : kPcgcMaxSmem))
+        if ((m != 1 && m != 2 && m != 4) || pcgc_smem<T>(s, code) > (sched_occ(code) == 2 ? kPcgcMaxSmem2 : kPcgcMaxSmem))
             return false;
         const std::vector<int>& off = pcgc_bins(s, m);
         for (int k = 0, cs = 1; k < 5; ++k, cs *= 2) {
@@ -1650,6 +1651,7 @@ void pcg_finish(zema_scene* s) {
         if (s->h_pcg[NE + e] == 3)
             fail(ZEMA_ERR_PCG_MAXITER, "linear solve reached max_pcg iterations without meeting its tolerance");
         tot += s->h_pcg[e];
+        if (s->pcg_pending_refines) s->S.pcg_refines += s->h_pcg[2 * NE + e];
     }
     s->S.pcg_iters += tot;
     if ((int)s->env_cost.size() == NE)
@@ -1715,6 +1717,11 @@ void pcg_t(zema_scene* s, const std::vector<int>& done_h) {
         ZLAUNCH();
         pk = s->pk.p;
     }
+    // FP32 cluster solves refine against FP64 residuals inside the launch
+    // (envs with up to kPcgcRefAff affine bodies), each env on its own as
+    // soon as its solve converges; the grid-wide solve refines from the host
+    const bool refine_in_launch = sizeof(T) < sizeof(double) && use_cluster && s->pcgc_max_aff <= kPcgcRefAff;
+    if (refine_in_launch) s->q.ensure(&s->A, std::max<size_t>(3 * (size_t)s->n_nodes + 3, 3 * (size_t)s->n_sv + 3));
     // the iterations and status of the last launch go to pinned memory, to
     // be read after the next synchronisation (pcg_finish)
     auto collect = [&]() {
@@ -1724,6 +1731,9 @@ void pcg_t(zema_scene* s, const std::vector<int>& done_h) {
         }
         ZCHECK(cudaMemcpyAsync(s->h_pcg, s->pcg_iters.p, NE * sizeof(int), cudaMemcpyDeviceToHost, st));
         ZCHECK(cudaMemcpyAsync(s->h_pcg + NE, s->conv.p, NE * sizeof(int), cudaMemcpyDeviceToHost, st));
+        if (refine_in_launch)
+            ZCHECK(cudaMemcpyAsync(s->h_pcg + 2 * NE, s->pcg_refines.p, NE * sizeof(int), cudaMemcpyDeviceToHost, st));
+        s->pcg_pending_refines = refine_in_launch;
         s->pcg_pending = true;
         s->pcg_pending_tsize = (int)sizeof(T);
         s->pcg_pending_kname = kname;
@@ -1752,6 +1762,9 @@ void pcg_t(zema_scene* s, const std::vector<int>& done_h) {
         c.env_list = nullptr;
         c.pk = pk;
         c.pk_c0 = (int)s->n_sblocks;
+        c.refine = refine_in_launch && tol2_env == nullptr ? kPcgcRefine : 0;
+        c.r64 = s->q.p;
+        c.refines = s->pcg_refines.p;
         if (NE > 1 && !sched_binned(cs)) {
             // launch order by the envs' last solve cost (iterations x nodes;
             // the order changes no env's arithmetic)
@@ -1887,7 +1900,7 @@ void pcg_t(zema_scene* s, const std::vector<int>& done_h) {
         ZCHECK(cudaEventCreate(&e1));
         float best = INFINITY;
         int best_cs = s->pcgc_cs[pi];
-        for (int code : {1, 2, 4, 8, 16, 101, 102, 104, 108, 116, 1001, 1002, 1101, 1102}) {
+        for (int code : {1, 2, 4, 8, 16, 101, 102, 104, 108, 116, 1001, 1002, 1004, 1101, 1102, 1104}) {
             const int cs = code;
             if (!pcgc_valid<T>(s, cs)) continue;
             float ms = INFINITY;
@@ -1934,8 +1947,10 @@ void pcg_t(zema_scene* s, const std::vector<int>& done_h) {
     };
     // one solve of the selected form, then its statistics
     auto run_solve = [&](const double* rhs, double* xo, const double* tol2_env, int n_solving) {
-        // envs skipped by this solve must not count the previous solve's iterations
+        // envs skipped by this solve must not count the previous solve's
+        // iterations and refinement rounds
         ZCHECK(cudaMemsetAsync(s->pcg_iters.p, 0, NE * sizeof(int), st));
+        if (refine_in_launch) ZCHECK(cudaMemsetAsync(s->pcg_refines.p, 0, NE * sizeof(int), st));
         if (use_cluster)
             launch_cluster(rhs, xo, schedule_for(n_solving), tol2_env);
         else
@@ -1949,7 +1964,7 @@ void pcg_t(zema_scene* s, const std::vector<int>& done_h) {
     int n_solving = 0;
     for (int e = 0; e < NE; ++e) n_solving += done_h[e] ? 0 : 1;
     run_solve(s->b.p, s->p.p, nullptr, n_solving);
-    if (sizeof(T) < sizeof(double)) {
+    if (sizeof(T) < sizeof(double) && !refine_in_launch) {
         // FP64 residual refinement of the FP32 solve: r = b - A x with
         // FP64 products; while |r| > tol |b| solve A d = r and add d
         std::vector<int> need(NE);
@@ -2605,10 +2620,10 @@ zema_status zema_create_scene(const zema_scene_params* params, zema_scene** out)
         params->pcg_kind < 0 || params->pcg_kind > 2 || !(params->cell_size < INFINITY))
         return ZEMA_ERR_INVALID_ARG;
     if (params->pcg_cluster_size != 0) {
-        // a schedule code: 1..16 (powers of two), + 100, or binned 1001, 1002, 1101, 1102
+        // a schedule code: 1..16 (powers of two), + 100, or binned 1001, 1002, 1004, 1101, 1102, 1104
         const int v = params->pcg_cluster_size, low = v % 100;
         const bool uniform = (v < 100 || (v > 100 && v < 200)) && low > 0 && low <= 16 && (low & (low - 1)) == 0;
-        const bool binned = v == 1001 || v == 1002 || v == 1101 || v == 1102;
+        const bool binned = v == 1001 || v == 1002 || v == 1004 || v == 1101 || v == 1102 || v == 1104;
         if (!uniform && !binned) return ZEMA_ERR_INVALID_ARG;
     }
     zema_scene* s = new (std::nothrow) zema_scene();

@@ -51,6 +51,25 @@ def test_solver_forms_one_step_parity_c1(precision, pcg_kind):
     assert err < 1e-5 * diag, err / diag
 
 
+@pytest.mark.parametrize("pcg_kind", [1, 2])
+def test_fp64_refinement_of_fp32_solves(pcg_kind):
+    # at a linear tolerance FP32 iterations cannot meet, every mixed solve
+    # is refined against FP64 residuals (inside the cluster launch, or from
+    # the host for the grid-wide form) and the step follows the oracle
+    sc = S.scene_c1()
+    sc.params.pcg_rel_tol = 1e-9
+    orc = Oracle(sc, tol_scale=1e-2)
+    orc.step(12)
+    gpu = gpu_scene(sc, tol_scale=1e-2, precision=1, pcg_kind=pcg_kind)
+    transplant(orc, gpu, sc)
+    orc.step(1)
+    st = gpu.step(1)
+    assert st["pcg_refines"] > 0
+    diag = orc.diag()
+    err = np.abs(env_positions(orc, sc, 0) - env_positions(gpu, sc, 0)).max()
+    assert err < 1e-5 * diag, err / diag
+
+
 def test_solver_forms_free_fall_exact():
     # no contact: the minimiser is the analytic free fall; both forms solve the
     # linear system to round-off at a tight tolerance
@@ -94,11 +113,15 @@ def test_batched_envs_one_step_parity_in_contact():
     gpu = gpu_scene(sc, tol_scale=1e-2, precision=1)
     transplant(orc, gpu, sc)
     orc.step(1)
-    gpu.step(1)
+    st = gpu.step(1)
     for e in range(sc.n_envs):
         d = orc.diag(e)
         err = np.abs(env_positions(orc, sc, e) - env_positions(gpu, sc, e)).max()
         assert err < 1e-5 * d, (e, err / d)
+    # at most 3 refinement rounds per env and solve (an env solves once per
+    # Newton iteration, the converged one included, in every AL round)
+    solves = st["newton_iters"] + sc.n_envs * (1 + st["al_rounds"])
+    assert 0 <= st["pcg_refines"] <= 3 * solves, (st["pcg_refines"], solves)
 
 
 def test_batched_deterministic_and_kinds_agree():
