@@ -92,6 +92,12 @@ typedef struct {
                                  for the two-CTAs-per-SM variant (see zema_get_tuning); 0: about one CTA
                                  per 128 nodes or the autotuner's choice.  A schedule the scene or device
                                  cannot run makes zema_step return ZEMA_ERR_INVALID_ARG */
+    int32_t al_extrapolate; /* 1 (default): each step starts the kinematic multipliers lambda_A of
+                               Eq. 13 at 2 lambda^t - lambda^(t-1), the linear extrapolation of the
+                               last two steps' converged values (the paper does not say how the
+                               augmented-Lagrangian iteration starts; the rounds still run until
+                               max |q - q~| <= tol, so the constraint met is the same); 0: each
+                               step starts at lambda^t */
 } zema_scene_params;
 
 /* Per-step statistics (summed over the steps of one zema_step call, over all

@@ -618,6 +618,7 @@ D2<9> ortho(const double* A9) {
 struct Params {
     double dt, dhat, kappa, eps_v, tol_rel, g[3], pcg_rel_tol;
     int max_newton, max_al_rounds;
+    int al_extrapolate;  // start each step's kinematic multipliers at 2 lambda^t - lambda^(t-1)
 };
 
 struct Affine {
@@ -626,6 +627,7 @@ struct Affine {
     std::vector<int> F;
     double rho, stiffness, mu;
     double q[12], qd[12], qt[12], qhat[12], qtarget[12], lamA[12];
+    double lamA_prev[12];  // the multipliers at the end of the step before the last one
     double M[144];
     double m, vol;
     int sv0;  // first surface vertex
@@ -1891,6 +1893,18 @@ void warm_start(Scene& S, int env, StepStats& ss) {
 int step_env(Scene& S, int env, StepStats& ss) {
     const double h = S.P.dt;
     EnvDofs D = env_dofs(S, env);
+    // the augmented-Lagrangian iteration of Eq. 13 starts from the linear
+    // extrapolation of the last two steps' converged multipliers (a reading:
+    // the paper does not say where it starts)
+    if (S.P.al_extrapolate)
+        for (Affine& A : S.aff) {
+            if (A.env != env || A.mode != 2) continue;
+            for (int k = 0; k < 12; ++k) {
+                const double l = A.lamA[k];
+                A.lamA[k] = 2.0 * l - A.lamA_prev[k];
+                A.lamA_prev[k] = l;
+            }
+        }
     predict(S, env);
     if (!S.kappa_init[env]) {
         init_kappa(S, env);
@@ -1940,6 +1954,16 @@ int step_env(Scene& S, int env, StepStats& ss) {
     }
     ss.al_rounds = rounds;
     if (status != OK) return status;
+    // with the extrapolation, the step ends with one more multiplier update
+    // from the accepted state (no new solve), so that the values the next
+    // step extrapolates from carry no part of the deviation the tolerance let
+    // through
+    if (S.P.al_extrapolate)
+        for (Affine& A : S.aff) {
+            if (A.env != env || A.mode != 2) continue;
+            const double kA = 1e3 * A.m, sm = std::sqrt(A.m);
+            for (int k = 0; k < 12; ++k) A.lamA[k] -= kA * (A.q[k] - A.qtarget[k]) / sm;
+        }
     // velocities (Eq. 11)
     for (int i : D.verts)
         for (int k = 0; k < 3; ++k) S.v[3 * i + k] = (S.x[3 * i + k] - S.xt[3 * i + k]) / h;
@@ -1966,7 +1990,7 @@ int step_env(Scene& S, int env, StepStats& ss) {
 extern "C" {
 
 // dparams: dt, dhat, kappa, eps_v, tol_rel, gx, gy, gz, pcg_rel_tol
-// iparams: max_newton, max_al_rounds, n_envs
+// iparams: max_newton, max_al_rounds, n_envs, al_extrapolate
 void* orc_create(const double* dp, const int* ip) {
     Scene* S = new Scene();
     S->P.dt = dp[0];
@@ -1981,6 +2005,7 @@ void* orc_create(const double* dp, const int* ip) {
     S->P.max_newton = ip[0];
     S->P.max_al_rounds = ip[1];
     S->n_envs = ip[2];
+    S->P.al_extrapolate = ip[3];
     return S;
 }
 
@@ -2033,6 +2058,7 @@ int orc_add_affine_body(void* s, int env, const double* V, long nv, const int* F
         A.qd[k] = qd0 ? qd0[k] : 0.0;
         A.qtarget[k] = q0[k];
         A.lamA[k] = 0.0;
+        A.lamA_prev[k] = 0.0;
     }
     // mass matrix M_b = integral rho J^T J over the body (Eq. 2) via the
     // divergence theorem: tetrahedra (0, a, b, c) over the closed surface

@@ -109,7 +109,8 @@ class Oracle:
         self.scene = scene
         dpar = np.array([p.dt, p.dhat, p.kappa, p.eps_v, p.newton_tol_rel * tol_scale,
                          p.gravity[0], p.gravity[1], p.gravity[2], p.pcg_rel_tol], dtype=np.float64)
-        ipar = np.array([p.max_newton, p.max_al_rounds, scene.n_envs], dtype=np.int32)
+        ipar = np.array([p.max_newton, p.max_al_rounds, scene.n_envs, getattr(p, "al_extrapolate", 1)],
+                        dtype=np.int32)
         self.h = L.orc_create(_dp(dpar), _ip(ipar))
         self.body_ids = []
         for kind, i in scene.body_order():

@@ -320,11 +320,13 @@ __global__ void k_al_check(Geo G, const double* x, AffKin K, const double* tol_e
     if (m > tol_env[env]) atomicMax(&need_env[env], 1);
 }
 
+// lambda_A -= kappa_A (q - q~) / sqrt(m) for the kinematic bodies of the envs
+// flagged in need_env (all envs when need_env is NULL)
 __global__ void k_al_update(Geo G, const double* x, const double* qtarget, double* lamA, const int* need_env) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= G.n_aff || G.aff_mode[b] != 2) return;
     int env = G.node_env[G.aff_node0[b]];
-    if (!need_env[env]) return;
+    if (need_env && !need_env[env]) return;
     double q[12];
     aff_row_q(G, x, b, q);
     double m = G.aff_m[b];

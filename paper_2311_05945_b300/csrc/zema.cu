@@ -184,6 +184,10 @@ struct zema_scene {
     DBuf<int> fault_dev;
     // per-step scratch
     DBuf<double> dirw, lam_save;
+    // kinematic multipliers at the end of the step before the last one (the
+    // extrapolation's second point), and the step-start copies of lambda_A
+    // and of it, put back by a full restore_step
+    DBuf<double> lamA_prev, lam_hist;
     std::vector<double> dmin_last;
     // the step-start values of what a step may change before it completes
     // (kappa, kappa_min and their flags, d_min), put back by restore_step
@@ -964,6 +968,7 @@ void build(zema_scene* s) {
         for (int k = 0; k < 12; ++k) qt_h[12 * a + k] = s->ain[aff_perm[a]].q0[k];
     up(s, s->qtarget, qt_h);
     up(s, s->lamA, lam_h);
+    up(s, s->lamA_prev, lam_h);
     // ---- per-env bbox diagonal (and centre) of the initial state
     s->diag_h.assign(NE, 0.0);
     std::vector<double> envc_h(3 * (size_t)NE, 0.0);
@@ -2313,6 +2318,16 @@ void ws_features(zema_scene* s) {
 void restore_step(zema_scene* s, bool all = true);
 
 // One time step of every environment.
+// lambda_A <- 2 lambda_A - lambda_prev, lambda_prev <- the old lambda_A, for
+// the kinematic bodies (the others keep lambda_A = 0)
+__global__ void k_al_extrapolate(Geo G, double* lamA, double* lam_prev) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 12 * G.n_aff || G.aff_mode[i / 12] != 2) return;
+    const double l = lamA[i];
+    lamA[i] = 2.0 * l - lam_prev[i];
+    lam_prev[i] = l;
+}
+
 void do_step(zema_scene* s) {
     zema_scene& W = *s;
     cudaStream_t st = s->st;
@@ -2327,6 +2342,17 @@ void do_step(zema_scene* s) {
     W.dmin_last_save = W.dmin_last;
     W.first_step_done_save = s->first_step_done;
     W.lam_save.ensure(&s->A, 12 * (size_t)s->n_aff + 12);
+    if (s->n_aff && s->P.al_extrapolate) {
+        // the multipliers start at the extrapolation of the last two steps';
+        // the values before it are kept for a full restore
+        const size_t na12 = 12 * (size_t)s->n_aff;
+        W.lam_hist.ensure(&s->A, 2 * na12 + 12);
+        ZCHECK(cudaMemcpyAsync(W.lam_hist.p, s->lamA.p, na12 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        ZCHECK(cudaMemcpyAsync(W.lam_hist.p + na12, s->lamA_prev.p, na12 * sizeof(double), cudaMemcpyDeviceToDevice,
+                               st));
+        ZL(k_al_extrapolate, div_up(na12, 128), 128, 0, st)(G, s->lamA.p, s->lamA_prev.p);
+        ZLAUNCH();
+    }
     if (s->n_aff)
         ZCHECK(cudaMemcpyAsync(W.lam_save.p, s->lamA.p, 12 * (size_t)s->n_aff * sizeof(double),
                                cudaMemcpyDeviceToDevice, st));
@@ -2503,6 +2529,13 @@ void do_step(zema_scene* s) {
         rounds = solve(false);
     }
     s->S.al_rounds += rounds;
+    // with the extrapolation, one more multiplier update from the accepted
+    // state (no new solve), so that the values the next step extrapolates
+    // from carry no part of the deviation the tolerance let through
+    if (s->n_aff && s->P.al_extrapolate) {
+        ZL(k_al_update, div_up(s->n_aff, 64), 64, 0, st)(G, s->x.p, s->qtarget.p, s->lamA.p, nullptr);
+        ZLAUNCH();
+    }
     // d_min at the accepted state (last active-pair pass) and energy of env 0
     std::vector<double> dm(NE);
     ZCHECK(cudaMemcpyAsync(dm.data(), s->dmin.p, NE * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -2554,7 +2587,12 @@ void restore_step(zema_scene* s, bool all) {
         W.dmin_last = W.dmin_last_save;
         s->first_step_done = W.first_step_done_save;
     }
-    if (s->n_aff && W.lam_save.p)
+    if (all && s->n_aff && s->P.al_extrapolate && W.lam_hist.p) {
+        // the multipliers before the step's extrapolation
+        const size_t na12 = 12 * (size_t)s->n_aff;
+        cudaMemcpyAsync(s->lamA.p, W.lam_hist.p, na12 * sizeof(double), cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(s->lamA_prev.p, W.lam_hist.p + na12, na12 * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    } else if (s->n_aff && W.lam_save.p)
         cudaMemcpyAsync(s->lamA.p, W.lam_save.p, 12 * (size_t)s->n_aff * sizeof(double), cudaMemcpyDeviceToDevice, st);
     if (s->G.n_joints && W.lamJ_save.p)
         cudaMemcpyAsync(s->lamJ.p, W.lamJ_save.p, 12 * (size_t)s->G.n_joints * sizeof(double),
@@ -2612,6 +2650,7 @@ void zema_default_params(zema_scene_params* p) {
     p->max_pcg = 10000;
     p->max_al_rounds = 10;
     p->n_envs = 1;
+    p->al_extrapolate = 1;
 }
 
 zema_status zema_create_scene(const zema_scene_params* params, zema_scene** out) {
@@ -3092,9 +3131,10 @@ zema_status zema_set_kappa(zema_scene* s, int32_t env, double kappa, double kapp
 // per node), q~ and lambda_A (12 per affine body), lambda of the joints (12
 // each), kappa, kappa_min, last d_min and kappa-set flag (one per env).
 constexpr uint64_t kCkptMagic = 0x31504B43414D455Aull;  // "ZEMACKP1"
+constexpr uint64_t kCkptVersion = 2;  // 2: with the kinematic multipliers of the step before
 
 size_t ckpt_doubles(const zema_scene* s) {
-    return 6 * (size_t)s->n_nodes + 24 * (size_t)s->n_aff + 12 * (size_t)s->G.n_joints + 4 * (size_t)s->n_envs;
+    return 6 * (size_t)s->n_nodes + 36 * (size_t)s->n_aff + 12 * (size_t)s->G.n_joints + 4 * (size_t)s->n_envs;
 }
 
 zema_status zema_checkpoint_size(const zema_scene* s, int64_t* bytes) {
@@ -3115,7 +3155,7 @@ zema_status zema_save_checkpoint(const zema_scene* cs, void* buf, int64_t cap, i
         const int NE = s->n_envs, NA = s->n_aff, NJ = s->G.n_joints;
         const size_t n3 = 3 * (size_t)s->n_nodes;
         h[0] = kCkptMagic;
-        h[1] = 1;
+        h[1] = kCkptVersion;
         h[2] = (uint64_t)s->n_nodes;
         h[3] = (uint64_t)NA;
         h[4] = (uint64_t)NJ;
@@ -3131,8 +3171,10 @@ zema_status zema_save_checkpoint(const zema_scene* cs, void* buf, int64_t cap, i
             ZCHECK(cudaMemcpyAsync(d, s->qtarget.p, 12 * (size_t)NA * sizeof(double), cudaMemcpyDeviceToHost, st));
             ZCHECK(cudaMemcpyAsync(d + 12 * (size_t)NA, s->lamA.p, 12 * (size_t)NA * sizeof(double),
                                    cudaMemcpyDeviceToHost, st));
+            ZCHECK(cudaMemcpyAsync(d + 24 * (size_t)NA, s->lamA_prev.p, 12 * (size_t)NA * sizeof(double),
+                                   cudaMemcpyDeviceToHost, st));
         }
-        d += 24 * (size_t)NA;
+        d += 36 * (size_t)NA;
         if (NJ) ZCHECK(cudaMemcpyAsync(d, s->lamJ.p, 12 * (size_t)NJ * sizeof(double), cudaMemcpyDeviceToHost, st));
         d += 12 * (size_t)NJ;
         ZCHECK(cudaMemcpyAsync(d, s->kappa.p, NE * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -3156,7 +3198,7 @@ zema_status zema_load_checkpoint(zema_scene* s, const void* buf, int64_t bytes) 
     }
     const uint64_t* h = (const uint64_t*)buf;
     const int NE = s->n_envs, NA = s->n_aff, NJ = s->G.n_joints;
-    if (h[0] != kCkptMagic || h[1] != 1 || h[2] != (uint64_t)s->n_nodes || h[3] != (uint64_t)NA ||
+    if (h[0] != kCkptMagic || h[1] != kCkptVersion || h[2] != (uint64_t)s->n_nodes || h[3] != (uint64_t)NA ||
         h[4] != (uint64_t)NJ || h[5] != (uint64_t)NE)
         return ZEMA_ERR_INVALID_ARG;
     if (bytes != (int64_t)(8 * sizeof(uint64_t) + ckpt_doubles(s) * sizeof(double))) return ZEMA_ERR_INVALID_ARG;
@@ -3165,7 +3207,7 @@ zema_status zema_load_checkpoint(zema_scene* s, const void* buf, int64_t bytes) 
     for (size_t i = 0; i < 2 * n3; ++i)
         if (!std::isfinite(d[i])) return ZEMA_ERR_INVALID_ARG;
     for (int e = 0; e < NE; ++e) {
-        const double* k = d + 2 * n3 + 24 * (size_t)NA + 12 * (size_t)NJ;
+        const double* k = d + 2 * n3 + 36 * (size_t)NA + 12 * (size_t)NJ;
         if (!(k[e] >= 0.0 && k[e] < INFINITY) || !(k[NE + e] >= 0.0 && k[NE + e] < INFINITY))
             return ZEMA_ERR_INVALID_ARG;
     }
@@ -3178,8 +3220,10 @@ zema_status zema_load_checkpoint(zema_scene* s, const void* buf, int64_t bytes) 
             ZCHECK(cudaMemcpyAsync(s->qtarget.p, d, 12 * (size_t)NA * sizeof(double), cudaMemcpyHostToDevice, st));
             ZCHECK(cudaMemcpyAsync(s->lamA.p, d + 12 * (size_t)NA, 12 * (size_t)NA * sizeof(double),
                                    cudaMemcpyHostToDevice, st));
+            ZCHECK(cudaMemcpyAsync(s->lamA_prev.p, d + 24 * (size_t)NA, 12 * (size_t)NA * sizeof(double),
+                                   cudaMemcpyHostToDevice, st));
         }
-        d += 24 * (size_t)NA;
+        d += 36 * (size_t)NA;
         if (NJ) ZCHECK(cudaMemcpyAsync(s->lamJ.p, d, 12 * (size_t)NJ * sizeof(double), cudaMemcpyHostToDevice, st));
         d += 12 * (size_t)NJ;
         ZCHECK(cudaMemcpyAsync(s->kappa.p, d, NE * sizeof(double), cudaMemcpyHostToDevice, st));

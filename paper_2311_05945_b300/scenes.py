@@ -203,6 +203,7 @@ class Params:
     pcg_rel_tol: float = 1e-4
     precision: int = 0          # 0: FP64, 1: mixed FP32/FP64
     max_al_rounds: int = 10
+    al_extrapolate: int = 1     # kinematic multipliers start at 2 lambda^t - lambda^(t-1)
 
 
 @dataclass

@@ -35,7 +35,7 @@ class Params(C.Structure):
         ("max_newton", C.c_int32), ("max_pcg", C.c_int32), ("max_al_rounds", C.c_int32),
         ("precision", C.c_int32), ("n_envs", C.c_int32), ("warm_start", C.c_int32), ("pcg_kind", C.c_int32),
         ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p),
-        ("cell_size", C.c_double), ("pcg_cluster_size", C.c_int32),
+        ("cell_size", C.c_double), ("pcg_cluster_size", C.c_int32), ("al_extrapolate", C.c_int32),
     ]
 
 
@@ -219,6 +219,7 @@ class Scene:
         P.max_newton = p.max_newton
         P.max_pcg = p.max_pcg
         P.max_al_rounds = p.max_al_rounds
+        P.al_extrapolate = p.al_extrapolate
         P.precision = p.precision if precision is None else precision
         P.n_envs = scene.n_envs
         P.pcg_kind = pcg_kind

@@ -139,3 +139,46 @@ def test_checkpoint_across_precisions_and_mismatch():
         a.load_checkpoint(bad)
     for g in (a, m, other):
         g.close()
+
+
+def small_grasp():
+    # two grasp envs at test size; the fingers close on the objects by step 20
+    return S.scene_c3(n_envs=2, n_steps=40, min_tets=300, max_tets=600, finger_subdiv=3)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_checkpoint_resume_with_kinematic_multipliers(precision):
+    # the fingers' multipliers and the previous step's (the extrapolation's
+    # second point) are part of the checkpoint: resuming in contact is bit
+    # for bit
+    from paper_2311_05945_b300 import zema as Z
+    sc = small_grasp()
+    a = Z.Scene(sc, precision=precision)
+    a.step(24)
+    ck = a.save_checkpoint()
+    a.step(4)
+    b = Z.Scene(sc, precision=precision)
+    b.load_checkpoint(ck)
+    b.step(4)
+    assert_same(snapshot(a, sc), snapshot(b, sc))
+    a.close()
+    b.close()
+
+
+def test_fault_on_a_grasp_step_restores_the_multipliers():
+    # a failed contact step puts the multipliers and their history back: the
+    # trajectory then equals one that never saw the fault
+    from paper_2311_05945_b300 import zema as Z
+    sc = small_grasp()
+    g, ref = Z.Scene(sc, precision=1), Z.Scene(sc, precision=1)
+    g.step(24)
+    ref.step(24)
+    before = snapshot(g, sc)
+    g.inject_fault(FAULT_STATUS, 0)
+    assert failing_step(g) == FAULT_INJECTED
+    assert_same(snapshot(g, sc), before)
+    g.step(3)
+    ref.step(3)
+    assert_same(snapshot(g, sc), snapshot(ref, sc))
+    g.close()
+    ref.close()

@@ -434,6 +434,31 @@ def test_kinematic_body_tracks_its_target():
     assert np.abs(o0.affine_q(0) - target(0)).max() > tol
 
 
+def test_kinematic_multiplier_extrapolation():
+    # Each step's augmented-Lagrangian iteration starts from 2 lambda^t -
+    # lambda^(t-1), and a step ends with one more multiplier update from its
+    # accepted state.  The body stays on its target at every step either way;
+    # once the start-up transient has passed, the extrapolated multipliers
+    # need no further round, where the unextrapolated ones (lagging by one
+    # step's change) would.  Without the end-of-step update the tolerance's
+    # slack compounds through the extrapolation until the rounds fail to
+    # converge (measured on this scene: a deviation of 8 x tol at step 8).
+    target = S.kinematic_track_target
+    rounds = {}
+    for ex in (0, 1):
+        s = S.scene_kinematic_track(10, n_steps=14)
+        s.params.al_extrapolate = ex
+        o = Oracle(s)
+        tol = s.params.newton_tol_rel * o.diag() * s.params.dt
+        r = []
+        for n in range(14):
+            st = o.step(1)
+            r.append(int(st[0, 0, 2]))
+            assert np.abs(o.affine_q(0) - target(n)).max() <= tol, (ex, n)
+        rounds[ex] = r
+    assert sum(rounds[1][4:]) == 0, rounds
+
+
 def test_kappa_min_is_a_thousand_mean_lumped_masses():
     # the adaptive barrier stiffness floor: 1e3 x the mean lumped soft-vertex mass
     s = S.scene_c1()
