@@ -93,6 +93,11 @@ __device__ __forceinline__ bool prim_skipped(const BPView& v, int kind, int i) {
     return v.env_skip && v.env_skip[prim_env(v, kind, i)];
 }
 
+// global id of local primitive 0 of a kind (0 points, 1 edges, 2 triangles)
+__device__ __forceinline__ int base_of(const BPView& v, int kind) {
+    return kind == 0 ? v.sv_base : (kind == 1 ? v.edge_base : v.tri_base);
+}
+
 // kind: 0 points, 1 edges, 2 tris.  For edges and tris also the grid entry
 // count (0 when oversize) and the oversize flag.  Primitives of skipped envs
 // get an empty box and no entries.
@@ -101,22 +106,23 @@ __global__ void k_boxes(BPView v, int kind, int n, double* box, int* cb, uint32_
     if (i >= n) return;
     int ids[3];
     int m;
+    const int gi = i + base_of(v, kind);
     if (kind == 0) {
-        ids[0] = i;
+        ids[0] = gi;
         m = 1;
     } else if (kind == 1) {
-        int2 e = v.edges[i];
+        int2 e = v.edges[gi];
         ids[0] = e.x;
         ids[1] = e.y;
         m = 2;
     } else {
-        int3 t = v.tris[i];
+        int3 t = v.tris[gi];
         ids[0] = t.x;
         ids[1] = t.y;
         ids[2] = t.z;
         m = 3;
     }
-    if (prim_skipped(v, kind, i)) {
+    if (prim_skipped(v, kind, gi)) {
         for (int k = 0; k < 3; ++k) {
             box[6 * (size_t)i + k] = INFINITY;
             box[6 * (size_t)i + 3 + k] = -INFINITY;
@@ -221,8 +227,9 @@ __device__ __forceinline__ int query_env(const BPView& v, int kind, int q) {
     return v.sv_env[kind == 0 ? q : v.edges[q].x];
 }
 
-// entry range [lo, hi) of a query's env (kind 0 queries meet triangles, kind
-// 1 edges); the whole table when the primitives are not ordered by env
+// local entry range [lo, hi) of the env of (global) query q (kind 0 queries
+// meet triangles, kind 1 edges); the whole table when the primitives are not
+// ordered by env
 __device__ __forceinline__ void env_entries(const BPView& v, int kind, int q, int n_all, int& lo, int& hi) {
     const int* st = kind == 0 ? v.env_tri_start : v.env_edge_start;
     if (!st) {
@@ -230,9 +237,9 @@ __device__ __forceinline__ void env_entries(const BPView& v, int kind, int q, in
         hi = n_all;
         return;
     }
-    const int e = query_env(v, kind, q);
-    lo = st[e];
-    hi = st[e + 1];
+    const int e = query_env(v, kind, q), eb = kind == 0 ? v.tri_base : v.edge_base;
+    lo = st[e] - eb;
+    hi = st[e + 1] - eb;
 }
 
 // first index k of the ascending list a[0..n) with a[k] >= x
@@ -277,7 +284,9 @@ __global__ void k_query(BPView v, int kind, int nq, const double* qbox, const do
     const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int q = (int)(gt / kQueryLanes), l = (int)(gt % kQueryLanes);
     if (q >= nq) return;  // the whole group
-    if (prim_skipped(v, kind, q)) {
+    // global ids of the query and of local entry 0
+    const int qg = q + base_of(v, kind), eb = kind == 0 ? v.tri_base : v.edge_base;
+    if (prim_skipped(v, kind, qg)) {
         if (!WRITE && l == 0) cnt[q] = 0;
         return;
     }
@@ -297,12 +306,12 @@ __global__ void k_query(BPView v, int kind, int nq, const double* qbox, const do
     auto emit = [&](bool hit, int e) {
         const unsigned b = (__ballot_sync(gmask, hit) >> gshift) & kGroupBits;
         const uint32_t at = c + __popc(b & ((1u << l) - 1u));
-        if (hit && (WRITE || at < (uint32_t)kQuerySlots)) out[o + at] = make_int2(q, e);
+        if (hit && (WRITE || at < (uint32_t)kQuerySlots)) out[o + at] = make_int2(qg, e + eb);
         c += __popc(b);
     };
     auto test = [&](int e) -> bool {
-        if (kind == 0) return pt_ok(v, q, e);
-        return q < e && ee_ok(v, q, e);
+        if (kind == 0) return pt_ok(v, qg, e + eb);
+        return q < e && ee_ok(v, qg, e + eb);
     };
     int qc[6];
     for (int k = 0; k < 6; ++k) qc[k] = qcb[6 * (size_t)q + k];
@@ -334,7 +343,7 @@ __global__ void k_query(BPView v, int kind, int nq, const double* qbox, const do
     int b_lo = 0, b_hi = nbig;
     if (v.env_tri_start) {
         int lo, hi;
-        env_entries(v, kind, q, n_entries_all, lo, hi);
+        env_entries(v, kind, qg, n_entries_all, lo, hi);
         b_lo = lower_bound_i(big, nbig, lo);
         b_hi = lower_bound_i(big, nbig, hi);
     }
@@ -407,17 +416,19 @@ __global__ void k_query_big(BPView v, int kind, const int* qlist, const double* 
                             const int* ecb_all, Table T, const int* big, int nbig) {
     __shared__ uint32_t sc[257];
     const int q = qlist[blockIdx.x];
+    // global ids of the query and of local entry 0
+    const int qg = q + base_of(v, kind), eb = kind == 0 ? v.tri_base : v.edge_base;
     const Box6 a = ld_box(qbox + 6 * (size_t)q);
     const uint32_t base = WRITE ? off[q] : 0u;
     auto test = [&](int e) -> bool {
         if (kind == 1 && e <= q) return false;
         Box6 b = ld_box(ebox_all + 6 * (size_t)e);
         if (!overlap(a, b)) return false;
-        return kind == 0 ? pt_ok(v, q, e) : ee_ok(v, q, e);
+        return kind == 0 ? pt_ok(v, qg, e + eb) : ee_ok(v, qg, e + eb);
     };
     const double ncell = box_cells(a, v.inv_cell);
     int lo, hi;
-    env_entries(v, kind, q, n_entries_all, lo, hi);  // other envs' entries never pair
+    env_entries(v, kind, qg, n_entries_all, lo, hi);  // other envs' entries never pair
     // walk the cells only where that is clearly less work than the scan
     if (ncell <= kWalkCells && 4.0 * ncell <= (double)(hi - lo)) {
         int qc[6];
@@ -450,7 +461,7 @@ __global__ void k_query_big(BPView v, int kind, const int* qlist, const double* 
                 return c;
             },
             [&](uint32_t o) {
-                for (int li = c0; li < c1; ++li) cell_hits(li, [&](int e) { out[o++] = make_int2(q, e); });
+                for (int li = c0; li < c1; ++li) cell_hits(li, [&](int e) { out[o++] = make_int2(qg, e + eb); });
             });
         // oversize entries (not in the grid), ascending ids, the query's env
         int b_lo = 0, b_hi = nbig;
@@ -469,7 +480,7 @@ __global__ void k_query_big(BPView v, int kind, const int* qlist, const double* 
             },
             [&](uint32_t o) {
                 for (int k = k0; k < k1; ++k)
-                    if (test(big[k])) out[o++] = make_int2(q, big[k]);
+                    if (test(big[k])) out[o++] = make_int2(qg, big[k] + eb);
             });
         if (!WRITE && threadIdx.x == 0) cnt[q] = n_grid + n_big;
         return;
@@ -485,7 +496,7 @@ __global__ void k_query_big(BPView v, int kind, const int* qlist, const double* 
         },
         [&](uint32_t o) {
             for (int e = e0; e < e1; ++e)
-                if (test(e)) out[o++] = make_int2(q, e);
+                if (test(e)) out[o++] = make_int2(qg, e + eb);
         });
     if (!WRITE && threadIdx.x == 0) cnt[q] = n;
 }
@@ -494,7 +505,7 @@ __global__ void k_query_big(BPView v, int kind, const int* qlist, const double* 
 __global__ void k_query_flag(BPView v, int kind, const double* box, int n, uint32_t* flag) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    if (prim_skipped(v, kind, i)) {
+    if (prim_skipped(v, kind, i + base_of(v, kind))) {
         flag[i] = 0u;
         return;
     }

@@ -24,6 +24,10 @@ struct BPView {
     // the oversize-entry lists are then searched within the query's env only
     const int* env_tri_start = nullptr;
     const int* env_edge_start = nullptr;
+    // a contiguous range of the primitives: local point, edge and triangle i
+    // are the global ones sv_base + i, edge_base + i, tri_base + i (every
+    // other array above is indexed globally); output pairs hold global ids
+    int sv_base = 0, edge_base = 0, tri_base = 0;
 };
 
 struct BroadPhase {

@@ -180,11 +180,15 @@ __global__ void k_env_gather(const uint32_t* scan, const uint32_t* start, int n_
 
 // env offsets of the PT (by surface vertex) and EE (by edge) candidate lists
 // and of their per-env merge
-__global__ void k_pair_env_offsets(Geo G, const uint32_t* qoff_pt, const uint32_t* qoff_ee, uint32_t* pt_env,
-                                   uint32_t* ee_env, uint32_t* m_env) {
+// per env, the first PT pair, EE pair and merged pair of its queries; the
+// broad phase covered the local point queries [sv_base, sv_base + nsv) and
+// edge queries [edge_base, edge_base + ne) (qoff_* over those, n + 1 each)
+__global__ void k_pair_env_offsets(Geo G, const uint32_t* qoff_pt, const uint32_t* qoff_ee, int sv_base, int nsv,
+                                   int edge_base, int ne, uint32_t* pt_env, uint32_t* ee_env, uint32_t* m_env) {
     int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e > G.n_envs) return;
-    uint32_t a = qoff_pt[G.env_sv_start[e]], b = qoff_ee[G.env_edge_start[e]];
+    const int ip = min(max(G.env_sv_start[e] - sv_base, 0), nsv), ie = min(max(G.env_edge_start[e] - edge_base, 0), ne);
+    uint32_t a = qoff_pt[ip], b = qoff_ee[ie];
     pt_env[e] = a;
     ee_env[e] = b;
     m_env[e] = a + b;

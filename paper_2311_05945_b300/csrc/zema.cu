@@ -76,7 +76,7 @@ struct zema_scene {
     std::vector<double> aff_com_h;     // 3 per affine body
     std::vector<int> aff_mode_h;
     std::vector<double> diag_h, tol_h; // per env
-    std::vector<int> env_aff_start_h, env_node_start_h, env_sv_start_h, env_edge_start_h;
+    std::vector<int> env_aff_start_h, env_node_start_h, env_sv_start_h, env_edge_start_h, env_tri_start_h;
     std::vector<double> node_mass_h, aff_m_in;  // host copies for the kappa rule
     int n_nodes = 0, n_soft = 0, n_aff = 0, n_tets = 0, n_sv = 0, n_edges = 0, n_tris = 0, n_units = 0;
     int n_sblocks = 0;
@@ -110,7 +110,7 @@ struct zema_scene {
     // per env
     DBuf<double> tol2_env;
     DBuf<double> kappa, kappa_min, alpha, E, dmin, part, part2, part3, part4, part5, part6, part7;
-    DBuf<int> conv, pcg_iters, need, capflag, skip, pcg_refines;
+    DBuf<int> conv, pcg_iters, need, capflag, skip, pcg_refines, ls_skip;
     DBuf<int> tile_u0, tile_u1, tile_n0, tile_n1, tile_env, env_tile_start;
     DBuf<double> pt_a, pt_b, pt_c, pt_d, pt_e;
     int n_tiles = 0, pcg_grid = 0, pcg_grid_f = 0;
@@ -585,6 +585,7 @@ void build(zema_scene* s) {
     s->n_tris = (int)tris_h.size();
     s->env_sv_start_h = env_sv_start;
     s->env_edge_start_h = env_edge_start;
+    s->env_tri_start_h = env_tri_start;
     std::vector<double> edge_rest2_h(s->n_edges);
     double sum_len = 0.0;
     for (int i = 0; i < s->n_edges; ++i) {
@@ -1017,7 +1018,8 @@ void build(zema_scene* s) {
     for (DBuf<double>* b : {&s->kappa, &s->kappa_min, &s->alpha, &s->E, &s->dmin, &s->tol2_env}) b->ensure(A, NE + 1);
     for (DBuf<double>* b : {&s->part, &s->part2, &s->part3, &s->part4, &s->part5, &s->part6, &s->part7})
         b->ensure(A, (size_t)ET_COUNT * NE * kChunks + 8);
-    for (DBuf<int>* b : {&s->conv, &s->pcg_iters, &s->need, &s->skip, &s->pcg_refines}) b->ensure(A, NE + 1);
+    for (DBuf<int>* b : {&s->conv, &s->pcg_iters, &s->need, &s->skip, &s->pcg_refines, &s->ls_skip})
+        b->ensure(A, NE + 1);
     s->capflag.ensure(A, 1);
     for (DBuf<uint32_t>* b : {&s->pt_env, &s->ee_env, &s->m_env, &s->act_env, &s->swept_env, &s->lag_env})
         b->ensure(A, NE + 2);
@@ -1178,14 +1180,26 @@ __global__ void k_reset_dmin(double* dmin, int n, const int* keep) {
 }
 
 // Candidate pairs (static boxes of X0, or swept X0 -> X1) into `out` with
-// per-env offsets; envs flagged in env_skip contribute no pairs.
+// per-env offsets; envs flagged in env_skip contribute no pairs, and only the
+// primitives of envs [e_lo, e_hi] are searched at all (every env flagged
+// outside that range; e_hi < e_lo: none), so that a batch whose last few
+// envs still iterate searches only their range.
 uint32_t candidates(zema_scene* s, const double* X0, const double* X1, DBuf<PairRec>& out, DBuf<uint32_t>& env_off,
-                    const int* env_skip = nullptr) {
+                    const int* env_skip = nullptr, int e_lo = 0, int e_hi = -2) {
     cudaStream_t st = s->st;
+    if (e_hi == -2) e_hi = s->n_envs - 1;
     BPView v;
-    v.nsv = s->n_sv;
-    v.ne = s->n_edges;
-    v.nt = s->n_tris;
+    // an empty range searches nothing (all offsets 0)
+    const bool empty = e_hi < e_lo;
+    const int sv0 = empty ? 0 : s->env_sv_start_h[e_lo], sv1 = empty ? 0 : s->env_sv_start_h[e_hi + 1];
+    const int ed0 = empty ? 0 : s->env_edge_start_h[e_lo], ed1 = empty ? 0 : s->env_edge_start_h[e_hi + 1];
+    const int tr0 = empty ? 0 : s->env_tri_start_h[e_lo], tr1 = empty ? 0 : s->env_tri_start_h[e_hi + 1];
+    v.nsv = sv1 - sv0;
+    v.ne = ed1 - ed0;
+    v.nt = tr1 - tr0;
+    v.sv_base = sv0;
+    v.edge_base = ed0;
+    v.tri_base = tr0;
     v.X0 = X0;
     v.X1 = X1;
     v.sv_body = s->sv_body.p;
@@ -1202,8 +1216,8 @@ uint32_t candidates(zema_scene* s, const double* X0, const double* X1, DBuf<Pair
     uint32_t n = s->bp.n_pt + s->bp.n_ee;
     out.ensure(&s->A, n + 1);
     int NE = s->n_envs;
-    ZL(k_pair_env_offsets, div_up(NE + 1, 64), 64, 0, st)(s->G, s->bp.qoff_pt.p, s->bp.qoff_ee.p, s->pt_env.p,
-                                                          s->ee_env.p, env_off.p);
+    ZL(k_pair_env_offsets, div_up(NE + 1, 64), 64, 0, st)(s->G, s->bp.qoff_pt.p, s->bp.qoff_ee.p, v.sv_base, v.nsv,
+                                                          v.edge_base, v.ne, s->pt_env.p, s->ee_env.p, env_off.p);
     ZLAUNCH();
     if (n)
         ZL(k_merge_pairs, div_up(n, TB), TB, 0, st)(s->G, s->bp.pt.p, s->bp.ee.p, s->pt_env.p, s->ee_env.p, env_off.p,
@@ -1211,6 +1225,15 @@ uint32_t candidates(zema_scene* s, const double* X0, const double* X1, DBuf<Pair
     ZLAUNCH();
     s->S.max_candidates = std::max<int64_t>(s->S.max_candidates, n);
     return n;
+}
+
+// The first and last env not flagged in done (e_hi < e_lo when all are)
+void active_range(const std::vector<int>& done, int& e_lo, int& e_hi) {
+    const int NE = (int)done.size();
+    e_lo = 0;
+    while (e_lo < NE && done[e_lo]) ++e_lo;
+    e_hi = NE - 1;
+    while (e_hi >= e_lo && done[e_hi]) --e_hi;
 }
 
 // Active pairs (d < dhat) at X among the n pairs of `list` (env offsets
@@ -2091,7 +2114,9 @@ int line_search(zema_scene* s, const double* dir, const std::vector<int>& done_h
         for (int e = 0; e < NE; ++e) s->hi[e] = done_h[e] ? 1 : 0;
         upload_env_ints(s, s->skip.p, s->hi);
     }
-    uint32_t ns = candidates(s, s->X.p, s->q.p, s->swept, s->swept_env, any_done ? s->skip.p : nullptr);
+    int e_lo = 0, e_hi = NE - 1;
+    active_range(done_h, e_lo, e_hi);
+    uint32_t ns = candidates(s, s->X.p, s->q.p, s->swept, s->swept_env, any_done ? s->skip.p : nullptr, e_lo, e_hi);
     s->n_swept = ns;
     ZCHECK(cudaMemsetAsync(s->capflag.p, 0, sizeof(int), st));
     if (ns) ZL(k_accd, div_up(ns, 128), 128, 0, st)(G, s->X.p, s->q.p, s->swept.p, (int)ns, s->alpha.p, s->capflag.p);
@@ -2119,11 +2144,25 @@ int line_search(zema_scene* s, const double* dir, const std::vector<int>& done_h
         if (done_h[e]) acc[e] = 1;  // converged: no step (its direction is zero)
     int halvings = 0;
     bool fail_ls = false;
+    // after the first trial only the envs still halving evaluate the
+    // potential: the others (converged, or accepted already) are masked for
+    // the energy kernels, whose per-env sums do not depend on one another
+    const int* const done_mask = G.env_done;
+    struct RestoreMask {
+        Geo& G;
+        const int* m;
+        ~RestoreMask() { G.env_done = m; }
+    } restore_mask{G, done_mask};
     for (int k = 0; k <= max_halvings; ++k) {
         if (alpha_known)
             ZCHECK(cudaMemcpyAsync(s->alpha.p, alpha.data(), NE * sizeof(double), cudaMemcpyHostToDevice, st));
         ZL(k_axpy_env, div_up(s->n_nodes, TB), TB, 0, st)(G, s->x.p, dir, s->alpha.p, s->xtrial.p);
         ZLAUNCH();
+        if (k > 0) {
+            for (int e = 0; e < NE; ++e) s->hi[e] = acc[e] ? 1 : 0;
+            upload_env_ints(s, s->ls_skip.p, s->hi);
+            G.env_done = s->ls_skip.p;
+        }
         energy(s, s->xtrial.p, s->swept.p, s->swept_env.p);
         if (!alpha_known) {
             alpha.assign(s->h_alpha, s->h_alpha + NE);
@@ -2509,7 +2548,9 @@ void do_step(zema_scene* s) {
             upload_env_ints(s, s->skip.p, s->hi);
             ZL(k_sv_pos, div_up(s->n_sv, TB), TB, 0, st)(G, s->x.p, s->X.p);
             ZLAUNCH();
-            s->n_swept = candidates(s, s->X.p, nullptr, s->swept, s->swept_env, s->skip.p);
+            int e_lo = 0, e_hi = NE - 1;
+            active_range(done, e_lo, e_hi);
+            s->n_swept = candidates(s, s->X.p, nullptr, s->swept, s->swept_env, s->skip.p, e_lo, e_hi);
         }
         return rounds;
     };
