@@ -2074,29 +2074,14 @@ void step_norm(zema_scene* s) {
     if (probe && s->hi[0] != 0) fail(s->hi[0], "fault injected by zema_inject_fault");
 }
 
-// Line search along direction dir from x (Newton step or warm-start
-// proposal): ACCD bound over the swept candidates, then halving until
-// E(x + alpha dir) <= E(x) per env.  On success x is advanced.  Returns the
-// number of halvings, or -1 when an env fails.
-//
-// e_at_x (nullable, per env): in, the potential at x where known (NaN where
-// not); out, the potential at the new x.  The potential at x does not depend
-// on which swept list its barrier is summed over, as long as the list holds
-// every pair with d < dhat at x, and every list built from a motion that
-// starts at x does; so an env's value from the line search that reached x
-// stands in for a new evaluation (only the order of the sum differs).
-int line_search(zema_scene* s, const double* dir, const std::vector<int>& done_h, bool warm,
-                std::vector<int>* accepted, int warm_halvings = 0, bool strict = false,
-                std::vector<double>* e_at_x = nullptr) {
-    // warm-start proposals get warm_halvings halvings (default: a single energy
-    // check), Newton steps up to 60; strict: a step must lower the energy
-    // (the learned correction), otherwise it may also keep it equal
-    const int max_halvings = warm ? warm_halvings : 60;
+// Swept candidates of the motion from x along dir (alpha = 1): X = X(x), q =
+// X(x + dir) (kept in q, which energy() does not overwrite), the pairs into
+// s->swept / s->swept_env and their count into s->n_swept; converged envs
+// (done_h) take no step and stay out; s->alpha is left at 1 for every env.
+void swept_candidates(zema_scene* s, const double* dir, const std::vector<int>& done_h) {
     cudaStream_t st = s->st;
     Geo& G = s->G;
     int NE = s->n_envs;
-    double t0 = now_ms();
-    // swept candidates X(x) -> X(x + dir)
     ZL(k_sv_pos, div_up(s->n_sv, TB), TB, 0, st)(G, s->x.p, s->X.p);
     std::vector<double> one(NE, 1.0);
     ZCHECK(cudaMemcpyAsync(s->alpha.p, one.data(), NE * sizeof(double), cudaMemcpyHostToDevice, st));
@@ -2116,8 +2101,42 @@ int line_search(zema_scene* s, const double* dir, const std::vector<int>& done_h
     }
     int e_lo = 0, e_hi = NE - 1;
     active_range(done_h, e_lo, e_hi);
-    uint32_t ns = candidates(s, s->X.p, s->q.p, s->swept, s->swept_env, any_done ? s->skip.p : nullptr, e_lo, e_hi);
-    s->n_swept = ns;
+    s->n_swept = candidates(s, s->X.p, s->q.p, s->swept, s->swept_env, any_done ? s->skip.p : nullptr, e_lo, e_hi);
+}
+
+// Line search along direction dir from x (Newton step or warm-start
+// proposal): ACCD bound over the swept candidates, then halving until
+// E(x + alpha dir) <= E(x) per env.  On success x is advanced.  Returns the
+// number of halvings, or -1 when an env fails.
+//
+// e_at_x (nullable, per env): in, the potential at x where known (NaN where
+// not); out, the potential at the new x.  The potential at x does not depend
+// on which swept list its barrier is summed over, as long as the list holds
+// every pair with d < dhat at x, and every list built from a motion that
+// starts at x does; so an env's value from the line search that reached x
+// stands in for a new evaluation (only the order of the sum differs).
+int line_search(zema_scene* s, const double* dir, const std::vector<int>& done_h, bool warm,
+                std::vector<int>* accepted, int warm_halvings = 0, bool strict = false,
+                std::vector<double>* e_at_x = nullptr, bool swept_ready = false) {
+    // warm-start proposals get warm_halvings halvings (default: a single energy
+    // check), Newton steps up to 60; strict: a step must lower the energy
+    // (the learned correction), otherwise it may also keep it equal
+    const int max_halvings = warm ? warm_halvings : 60;
+    cudaStream_t st = s->st;
+    Geo& G = s->G;
+    int NE = s->n_envs;
+    double t0 = now_ms();
+    // swept candidates X(x) -> X(x + dir) (unless the step's start built them
+    // for this direction already); alpha = 1 on the device
+    uint32_t ns;
+    if (swept_ready) {
+        std::vector<double> one(NE, 1.0);
+        ZCHECK(cudaMemcpyAsync(s->alpha.p, one.data(), NE * sizeof(double), cudaMemcpyHostToDevice, st));
+        ns = s->n_swept;
+    } else {
+        swept_candidates(s, dir, done_h);
+        ns = s->n_swept;
+    }
     ZCHECK(cudaMemsetAsync(s->capflag.p, 0, sizeof(int), st));
     if (ns) ZL(k_accd, div_up(ns, 128), 128, 0, st)(G, s->X.p, s->q.p, s->swept.p, (int)ns, s->alpha.p, s->capflag.p);
     ZLAUNCH();
@@ -2210,11 +2229,14 @@ int line_search(zema_scene* s, const double* dir, const std::vector<int>& done_h
 }
 
 // lag friction at the current x (= x^t): records, weights, normals, mu lambda
-void lag_friction(zema_scene* s) {
+// (list: a candidate list that holds every pair with d < dhat at x, such as
+// the swept candidates of a motion starting at x; NULL: a broad phase at x)
+void lag_friction(zema_scene* s, const PairRec* list = nullptr, const uint32_t* list_env = nullptr,
+                  uint32_t n_list = 0) {
     cudaStream_t st = s->st;
     ZL(k_sv_pos, div_up(s->n_sv, TB), TB, 0, st)(s->G, s->x.p, s->Xt.p);
     ZLAUNCH();
-    uint32_t na = active_pairs(s, s->Xt.p, false);
+    uint32_t na = list ? active_from(s, s->Xt.p, list, list_env, n_list, false) : active_pairs(s, s->Xt.p, false);
     s->lag.ensure(&s->A, na + 1);
     s->lag_w.ensure(&s->A, 4 * (size_t)na + 4);
     s->lag_n.ensure(&s->A, 3 * (size_t)na + 3);
@@ -2405,8 +2427,16 @@ void do_step(zema_scene* s) {
     ZLAUNCH();
     bool first = !s->first_step_done;
     init_kappa(s);
+    // the constant-velocity warm start's swept candidates (x^t -> x^t + h v)
+    // hold every pair with d < dhat at x^t: one broad phase serves both the
+    // friction lagging and the warm start's line search
+    W.dirw.ensure(&s->A, n3 + 3);
+    ZL(k_scale_dir, div_up(s->n_nodes, TB), TB, 0, st)(G, s->v.p, s->P.dt, W.dirw.p);
+    ZLAUNCH();
+    swept_candidates(s, W.dirw.p, std::vector<int>(NE, 0));
+    bool swept_fresh = true;
     // lagged friction at x^t (Eq. 9-10); d_min at x^t for the kappa rule
-    lag_friction(s);
+    lag_friction(s, s->swept.p, s->swept_env.p, s->n_swept);
     if (first) {
         // d_min over active pairs at x^t
         ZL(k_sv_pos, div_up(s->n_sv, TB), TB, 0, st)(G, s->x.p, s->X.p);
@@ -2444,7 +2474,8 @@ void do_step(zema_scene* s) {
         ZLAUNCH();
         std::vector<int> done(NE, 0), acc;
         std::vector<double> e_at_x(NE, NAN);  // the potential at the current x, per env
-        line_search(s, W.dirw.p, done, true, &acc, 0, false, &e_at_x);
+        line_search(s, W.dirw.p, done, true, &acc, 0, false, &e_at_x, swept_fresh);
+        swept_fresh = false;  // later line searches overwrite the list
         if (use_learned) {
             ZCHECK(cudaMemsetAsync(W.dirw.p, 0, n3 * sizeof(double), st));
             if (learned_soft)
