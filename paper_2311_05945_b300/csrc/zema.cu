@@ -2151,7 +2151,16 @@ int line_search(zema_scene* s, const double* dir, const std::vector<int>& done_h
     if (e_at_x)
         for (int e = 0; e < NE; ++e) need_e0 |= !done_h[e] && std::isnan((*e_at_x)[e]);
     std::vector<double> E0(NE, 0.0);
-    if (need_e0) {
+    if (need_e0 && e_at_x) {
+        // only the envs whose potential at x is not known evaluate it
+        const int* const keep_mask = G.env_done;
+        for (int e = 0; e < NE; ++e) s->hi[e] = done_h[e] || !std::isnan((*e_at_x)[e]) ? 1 : 0;
+        upload_env_ints(s, s->ls_skip.p, s->hi);
+        G.env_done = s->ls_skip.p;
+        energy(s, s->x.p, s->swept.p, s->swept_env.p);
+        G.env_done = keep_mask;
+        for (int e = 0; e < NE; ++e) E0[e] = std::isnan((*e_at_x)[e]) ? s->hd[e] : (*e_at_x)[e];
+    } else if (need_e0) {
         energy(s, s->x.p, s->swept.p, s->swept_env.p);
         E0.assign(s->hd, s->hd + NE);
     } else {
@@ -2497,92 +2506,107 @@ void do_step(zema_scene* s) {
             Geo& G;
             ~DoneMask() { G.env_done = nullptr; }
         } done_mask{G};
+        // Newton with the kinematic augmented-Lagrangian rounds of Eq. 13 per
+        // env: when an env's step falls under the tolerance, its constraint
+        // is checked at that x (read back with the step norm); an env that
+        // needs a round gets its multipliers updated and goes on iterating at
+        // once, with a zero step in that iteration's line search (so its pairs
+        // at x enter the next swept list), instead of waiting for the whole
+        // batch to converge and restarting then.  An env's arithmetic is the
+        // same either way.  Each round restarts the env's Newton count.
+        std::vector<int> env_rounds(NE, 0), env_it(NE, 0), resume(NE, 0);
+        int* need_h = s->hi + 2 * NE;  // pinned: the AL check, read back with the step norm
+        const bool al = s->n_aff > 0;
+        bool converged = false;
         for (;;) {
-            bool converged = false;
-            for (int it = 0; it < s->P.max_newton; ++it) {
-                double ta = now_ms();
-                ZL(k_sv_pos, div_up(s->n_sv, TB), TB, 0, st)(G, s->x.p, s->X.p);
-                ZLAUNCH();
-                // x was reached by a line search along the last swept motion (the
-                // warm start or the previous Newton step), so that swept
-                // candidate list contains every pair with d < dhat at x
-                for (int e = 0; e < NE; ++e) s->hi[e] = done[e] ? 1 : 0;
-                upload_env_ints(s, s->skip.p, s->hi);
-                G.env_done = s->skip.p;
-                active_from(s, s->X.p, s->swept.p, s->swept_env.p, s->n_swept, true, s->skip.p);
-                double tb = now_ms();
-                s->S.ms_phase[0] += tb - ta;
-                grad_hess(s);  // no read-back: the solve's is the next
-                // fault injection: armed for this iteration only (one shot)
-                s->fault_armed = 0;
-                if (s->fault_kind && s->newton_count == s->fault_at) {
-                    s->fault_armed = s->fault_kind;
-                    s->fault_kind = 0;
-                    const int on[2] = {1, 0};
-                    ZCHECK(cudaMemcpyAsync(s->fault_dev.p, on, 2 * sizeof(int), cudaMemcpyHostToDevice, st));
+            bool over = false;
+            for (int e = 0; e < NE; ++e)
+                if (!done[e]) {
+                    over |= env_it[e] >= s->P.max_newton;
+                    ++env_it[e];
                 }
-                ++s->newton_count;
-                double tc = now_ms();
-                s->S.ms_phase[2] += tc - tb;
-                pcg(s, done);
-                step_norm(s);
-                pcg_finish(s);  // the solve's status and statistics, read back with the step norm
-                s->S.ms_phase[3] += now_ms() - tc;
-                bool all = true;
-                for (int e = 0; e < NE; ++e) {
-                    if (done[e]) continue;
-                    if (s->hd[e] <= s->tol_h[e]) {
-                        done[e] = 1;
-                    } else {
-                        all = false;
-                        s->S.newton_iters += 1;
-                    }
-                }
-                if (all) {
-                    converged = true;
-                    break;
-                }
-                // zero the direction of envs that just converged
-                for (int e = 0; e < NE; ++e) s->hi[e] = done[e];
-                upload_env_ints(s, s->need.p, s->hi);
-                ZL(k_mask_env, div_up(s->n_nodes, TB), TB, 0, st)(G, s->p.p, s->need.p);
-                ZLAUNCH();
-                int hv = line_search(s, s->p.p, done, false, nullptr, 0, false, &e_at_x);
-                if (hv < 0) fail(ZEMA_ERR_LINESEARCH, "line search found no decrease after 60 halvings");
-                s->S.ls_halvings += hv;
-            }
-            G.env_done = nullptr;
-            if (!converged) fail(ZEMA_ERR_NEWTON_MAXITER, "Newton did not converge within max_newton iterations");
-            // kinematic augmented Lagrangian (Eq. 13)
-            if (s->n_aff == 0) break;
-            ZCHECK(cudaMemsetAsync(s->need.p, 0, NE * sizeof(int), st));
-            ZL(k_al_check, div_up(s->n_aff, 64), 64, 0, st)(G, s->x.p, kin(s), s->tolv.p, s->need.p);
-            if (G.n_joints)
-                ZL(k_joint_check, div_up(G.n_joints, 64), 64, 0, st)(G, s->x.p, s->tolv.p, s->P.newton_tol_rel,
-                                                                    s->need.p);
-            ZLAUNCH();
-            ZCHECK(cudaMemcpyAsync(s->hi, s->need.p, NE * sizeof(int), cudaMemcpyDeviceToHost, st));
-            ZCHECK(cudaStreamSynchronize(st));
-            bool any = false;
-            for (int e = 0; e < NE; ++e) any |= s->hi[e] != 0;
-            if (!any || rounds >= s->P.max_al_rounds) break;
-            ++rounds;
-            std::fill(e_at_x.begin(), e_at_x.end(), NAN);  // the multipliers change the potential
-            ZL(k_al_update, div_up(s->n_aff, 64), 64, 0, st)(G, s->x.p, s->qtarget.p, s->lamA.p, s->need.p);
-            if (G.n_joints)
-                ZL(k_joint_update, div_up(G.n_joints, 64), 64, 0, st)(G, s->x.p, s->lamJ.p, s->need.p);
-            ZLAUNCH();
-            for (int e = 0; e < NE; ++e) done[e] = s->hi[e] ? 0 : 1;
-            // the resuming envs may have been left out of the last swept list:
-            // candidates at x (static boxes) for them
-            for (int e = 0; e < NE; ++e) s->hi[e] = done[e];
-            upload_env_ints(s, s->skip.p, s->hi);
+            if (over) break;
+            double ta = now_ms();
             ZL(k_sv_pos, div_up(s->n_sv, TB), TB, 0, st)(G, s->x.p, s->X.p);
             ZLAUNCH();
-            int e_lo = 0, e_hi = NE - 1;
-            active_range(done, e_lo, e_hi);
-            s->n_swept = candidates(s, s->X.p, nullptr, s->swept, s->swept_env, s->skip.p, e_lo, e_hi);
+            // x was reached by a line search along the last swept motion (the
+            // warm start or the previous Newton step, a zero one for an env
+            // resuming after an AL round), so that swept candidate list
+            // contains every pair with d < dhat at x
+            for (int e = 0; e < NE; ++e) s->hi[e] = done[e] ? 1 : 0;
+            upload_env_ints(s, s->skip.p, s->hi);
+            G.env_done = s->skip.p;
+            active_from(s, s->X.p, s->swept.p, s->swept_env.p, s->n_swept, true, s->skip.p);
+            double tb = now_ms();
+            s->S.ms_phase[0] += tb - ta;
+            grad_hess(s);  // no read-back: the solve's is the next
+            // fault injection: armed for this iteration only (one shot)
+            s->fault_armed = 0;
+            if (s->fault_kind && s->newton_count == s->fault_at) {
+                s->fault_armed = s->fault_kind;
+                s->fault_kind = 0;
+                const int on[2] = {1, 0};
+                ZCHECK(cudaMemcpyAsync(s->fault_dev.p, on, 2 * sizeof(int), cudaMemcpyHostToDevice, st));
+            }
+            ++s->newton_count;
+            double tc = now_ms();
+            s->S.ms_phase[2] += tc - tb;
+            pcg(s, done);
+            if (al) {
+                ZCHECK(cudaMemsetAsync(s->need.p, 0, NE * sizeof(int), st));
+                ZL(k_al_check, div_up(s->n_aff, 64), 64, 0, st)(G, s->x.p, kin(s), s->tolv.p, s->need.p);
+                if (G.n_joints)
+                    ZL(k_joint_check, div_up(G.n_joints, 64), 64, 0, st)(G, s->x.p, s->tolv.p,
+                                                                        s->P.newton_tol_rel, s->need.p);
+                ZLAUNCH();
+                ZCHECK(cudaMemcpyAsync(need_h, s->need.p, NE * sizeof(int), cudaMemcpyDeviceToHost, st));
+            }
+            step_norm(s);
+            pcg_finish(s);  // the solve's status and statistics, read back with the step norm
+            s->S.ms_phase[3] += now_ms() - tc;
+            bool all = true, any_resume = false;
+            for (int e = 0; e < NE; ++e) {
+                resume[e] = 0;
+                if (done[e]) continue;
+                if (s->hd[e] <= s->tol_h[e]) {
+                    if (al && need_h[e] && env_rounds[e] < s->P.max_al_rounds) {
+                        resume[e] = 1;
+                        ++env_rounds[e];
+                        env_it[e] = 0;
+                        e_at_x[e] = NAN;  // the multipliers change the potential
+                        any_resume = true;
+                        all = false;
+                    } else {
+                        done[e] = 1;
+                    }
+                } else {
+                    all = false;
+                    s->S.newton_iters += 1;
+                }
+            }
+            if (any_resume) {
+                upload_env_ints(s, s->need.p, resume.data());
+                ZL(k_al_update, div_up(s->n_aff, 64), 64, 0, st)(G, s->x.p, s->qtarget.p, s->lamA.p, s->need.p);
+                if (G.n_joints)
+                    ZL(k_joint_update, div_up(G.n_joints, 64), 64, 0, st)(G, s->x.p, s->lamJ.p, s->need.p);
+                ZLAUNCH();
+            }
+            if (all) {
+                converged = true;
+                break;
+            }
+            // zero the direction of envs that just converged or resume
+            for (int e = 0; e < NE; ++e) s->hi[e] = done[e] || resume[e] ? 1 : 0;
+            upload_env_ints(s, s->need.p, s->hi);
+            ZL(k_mask_env, div_up(s->n_nodes, TB), TB, 0, st)(G, s->p.p, s->need.p);
+            ZLAUNCH();
+            int hv = line_search(s, s->p.p, done, false, nullptr, 0, false, &e_at_x);
+            if (hv < 0) fail(ZEMA_ERR_LINESEARCH, "line search found no decrease after 60 halvings");
+            s->S.ls_halvings += hv;
         }
+        G.env_done = nullptr;
+        if (!converged) fail(ZEMA_ERR_NEWTON_MAXITER, "Newton did not converge within max_newton iterations");
+        for (int e = 0; e < NE; ++e) rounds = std::max(rounds, env_rounds[e]);
         return rounds;
     };
     int rounds = 0;
