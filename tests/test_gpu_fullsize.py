@@ -98,6 +98,70 @@ def test_c2_full_size_one_step_from_oracle_contact_state(c2_contact_state, preci
         O.set_threads(1)
 
 
+def checkpoint_kappas(ck):
+    """(kappa, kappa_min) per env from a checkpoint (version 2 layout)."""
+    buf = ck[0]
+    h = buf[:64].view(np.uint64)
+    n, na, nj, ne = (int(h[i]) for i in (2, 3, 4, 5))
+    d = buf[64:].view(np.float64)
+    o = 6 * n + 36 * na + 12 * nj
+    return d[o:o + ne].copy(), d[o + ne:o + 2 * ne].copy()
+
+
+def test_bench_batch_sampled_envs_against_oracle():
+    # The benchmark's own batch in its launch configuration: 256 grasp envs
+    # (2.05 M tets) in one scene, mixed precision, the autotuned solve
+    # schedule, the trained warm-start networks loaded; the Newton tolerance
+    # at 1e-2 of the default so that each side lands within a small fraction
+    # of the bound from the minimiser.  Two sampled envs' states in the
+    # contact window go to the oracle (each env alone, at its batch
+    # coordinates); one step of each side must agree within 1e-5 of the env's
+    # bbox diagonal.
+    from paper_2311_05945_b300 import zema as Z
+    s0, sample = 21, (82, 200)
+    sc = S.scene_c3(n_envs=256, n_steps=s0 + 3)
+    g = Z.Scene(sc, precision=1, warm_start=1, tol_scale=TIGHT)
+    for name in ("warmstart.bin", "warmstart_affine.bin"):
+        dims, theta = Z.read_warmstart_blob(weights_blob(name))
+        g.load_warmstart(dims, theta)
+    for k in range(s0):
+        if k == s0 - 1:
+            g.autotune()
+        g.step(1)
+    kap, kmin = checkpoint_kappas(g.save_checkpoint())
+    n_aff_env = [sum(1 for a in sc.affines if a.env == e) for e in range(sc.n_envs)]
+    O.set_threads(os.cpu_count() or 1)
+    try:
+        orcs = {}
+        for e in sample:
+            one = S.scene_c3(n_envs=1, n_steps=s0 + 3, seed0=1000 + e, slot0=e)
+            orc = Oracle(one, tol_scale=TIGHT)
+            # bodies of env e in the batch, in the single-env scene's order
+            aff_e = [i for i, a in enumerate(sc.affines) if a.env == e]
+            assert len(aff_e) == n_aff_env[e] == len(one.affines)
+            orc.set_state(orc.tet_body_id(0), g.get_state(g.tet_body_id(e)))
+            for j, i in enumerate(aff_e):
+                orc.set_state(orc.affine_body_id(j), g.get_state(g.affine_body_id(i)))
+            orc.set_kappa(0, kap[e], kmin[e])
+            orc.step_index = g.step_index
+            orcs[e] = (one, orc, aff_e)
+        g.step(1)
+        for e, (one, orc, aff_e) in orcs.items():
+            orc.step(1)
+            d = orc.diag()
+            err = np.abs(orc.tet_positions(0) - g.tet_positions(e)).max()
+            for j, i in enumerate(aff_e):
+                a = one.affines[j]
+                qo, qg = orc.affine_q(j), g.affine_q(i)
+                vo = a.V @ qo[3:].reshape(3, 3).T + qo[:3]
+                vg = a.V @ qg[3:].reshape(3, 3).T + qg[:3]
+                err = max(err, np.abs(vo - vg).max())
+            assert err < 1e-5 * d, (e, err / d)
+    finally:
+        O.set_threads(1)
+    g.close()
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_c1_full_length_trajectory(precision):
     from paper_2311_05945_b300 import zema as Z
