@@ -213,14 +213,14 @@ struct zema_scene {
     DBuf<float> ws_feat, ws_out;
     float* rec_feat = nullptr;  // caller's device buffers while recording
     float* rec_targ = nullptr;
-    // zema_set_kinematic_targets: pinned staging of (device affine index,
-    // 12 target values) records, their device copy, and the event after the
-    // copy out of the staging (waited on before the staging is rewritten)
     mutable std::vector<int> aff_dev_of_input;  // device index of each affine body (order of addition)
     // size-binned solves: one stream per cluster size, the fork event and
     // the join events
     cudaStream_t bin_st[5] = {};
     cudaEvent_t bin_fork = nullptr, bin_join[5] = {};
+    // zema_set_kinematic_targets: pinned staging of (device affine index,
+    // 12 target values) records, their device copy, and the event after the
+    // copy out of the staging (waited on before the staging is rewritten)
     double* h_kin = nullptr;
     size_t h_kin_cap = 0;
     DBuf<double> kin_up;
@@ -1180,10 +1180,10 @@ __global__ void k_reset_dmin(double* dmin, int n, const int* keep) {
 }
 
 // Candidate pairs (static boxes of X0, or swept X0 -> X1) into `out` with
-// per-env offsets; envs flagged in env_skip contribute no pairs, and only the
-// primitives of envs [e_lo, e_hi] are searched at all (every env flagged
-// outside that range; e_hi < e_lo: none), so that a batch whose last few
-// envs still iterate searches only their range.
+// per-env offsets.  Only the primitives of envs e_lo..e_hi are searched (the
+// envs outside that range contribute no pairs; e_hi < e_lo searches nothing),
+// so that a batch whose last few envs still iterate searches only their
+// range; inside it, envs flagged in env_skip contribute no pairs.
 uint32_t candidates(zema_scene* s, const double* X0, const double* X1, DBuf<PairRec>& out, DBuf<uint32_t>& env_off,
                     const int* env_skip = nullptr, int e_lo = 0, int e_hi = -2) {
     cudaStream_t st = s->st;
