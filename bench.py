@@ -51,9 +51,9 @@ ROOFLINE_KERNEL_BY_WORKLOAD = {"c2": "k_pcg_cluster", "c3": "k_pcg_cluster", "c5
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
 # roofline kernel, from an ncu capture of the kernel as it stands; None where
 # no capture was taken since the kernel last changed.  c3: the mean over the
-# 11 solves of grasp step 20 at 256 envs (a size-binned solve, one launch per
+# 7 solves of grasp step 20 at 256 envs (a size-binned solve, one launch per
 # cluster size, counts as one launch here as in the live timing).
-ROOFLINE_TRAFFIC = {"c2": None, "c3": 217e6, "c5": None}
+ROOFLINE_TRAFFIC = {"c2": None, "c3": 330e6, "c5": None}
 # first step of the grasp script with both fingers on the object
 CONTACT_STEP = {"c2": 20, "c3": 20, "c5": 13}
 WEIGHTS = os.path.join(ROOT, "paper_2311_05945_b300", "weights")
