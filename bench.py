@@ -342,21 +342,19 @@ def run_ours(args, rank, world):
     clk = clocks.stop()
     head = Form("headline", ms, stats, units, K)
     tuned = g.tuning()
-    # end to end through the C ABI with pinned host buffers, same window,
-    # same form: every step uploads all bodies' states, steps, reads them back
+    # end to end through the C ABI with a pinned host buffer, same window,
+    # same form: every step uploads every body's state (one copy), steps,
+    # and reads them all back (one copy)
     g.load_checkpoint(ck)
-    bodies = list(range(len(sc.body_order())))
-    host = [torch.from_numpy(g.get_state(b)).pin_memory() for b in bodies]
+    host = torch.from_numpy(g.get_scene_state()).pin_memory()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     t0 = time.perf_counter()
     for _ in range(K):
-        for b in bodies:
-            g.set_state_ptr(b, host[b].data_ptr(), host[b].numel())
+        g.set_scene_state_ptr(host.data_ptr(), host.numel())
         g.step(1)
-        for b in bodies:
-            g.get_state_ptr(b, host[b].data_ptr(), host[b].numel())
+        g.get_scene_state_ptr(host.data_ptr(), host.numel())
     torch.cuda.synchronize()
     e2e_val = units * K / max_over_ranks(time.perf_counter() - t0, dist, "cuda")
     g.close()

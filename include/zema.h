@@ -205,6 +205,18 @@ zema_status zema_get_state(const zema_scene* s, int32_t body, double* out, int64
  * scene's stream. */
 zema_status zema_set_state(zema_scene* s, int32_t body, const double* in, int64_t n);
 
+/* The state of every body at once (Eq. 11's x^t, v^t, q^t, qdot^t): the
+ * layouts of zema_get_state, bodies back to back in order of addition, n
+ * doubles in all (zema_scene_state_size).  One copy each way through a
+ * device buffer the scene owns; pinned host memory makes it a direct DMA.
+ * Get: cap < n is ZEMA_ERR_INVALID_ARG (buffer untouched); set: n must equal
+ * the size exactly, else ZEMA_ERR_INVALID_ARG with the state unchanged; a
+ * fixed body's velocity is forced to zero, as with zema_set_state.  Both
+ * synchronise the scene's stream; ZEMA_ERR_STATE before zema_finalize. */
+zema_status zema_scene_state_size(const zema_scene* s, int64_t* n);
+zema_status zema_get_scene_state(const zema_scene* s, double* out, int64_t cap, int64_t* written);
+zema_status zema_set_scene_state(zema_scene* s, const double* in, int64_t n);
+
 /* All positions/velocities at once, device-to-device: x_dev and v_dev are
  * device arrays of 3 * (total soft vertices) doubles in order of body
  * addition (either may be NULL). */

@@ -221,6 +221,14 @@ struct zema_scene {
     // zema_set_kinematic_targets: pinned staging of (device affine index,
     // 12 target values) records, their device copy, and the event after the
     // copy out of the staging (waited on before the staging is rewritten)
+    // zema_get/set_scene_state: per body (order of addition) its first node,
+    // vertex count (tet bodies; -1 for affine bodies), offset in the flat
+    // state, fixed flag and (affine) centre of mass; and the device copy of
+    // the flat state
+    DBuf<int> sst_node0, sst_nv, sst_fixed;
+    DBuf<int64_t> sst_off;
+    DBuf<double> sst_com, sst_buf;
+    int64_t sst_n = -1;
     double* h_kin = nullptr;
     size_t h_kin_cap = 0;
     DBuf<double> kin_up;
@@ -3147,6 +3155,149 @@ zema_status zema_set_state(zema_scene* s, int32_t body, const double* in, int64_
         size_t n0 = s->aff_node0_h[bk.second];
         ZCHECK(cudaMemcpyAsync(s->x.p + 3 * n0, xc, 12 * sizeof(double), cudaMemcpyHostToDevice, s->st));
         ZCHECK(cudaMemcpyAsync(s->v.p + 3 * n0, vc, 12 * sizeof(double), cudaMemcpyHostToDevice, s->st));
+        ZCHECK(cudaStreamSynchronize(s->st));
+        return ZEMA_OK;
+    }
+    ZEMA_CATCH(s)
+}
+
+}  // extern "C"
+
+namespace {
+// The flat state of every body in order of addition (the layout of
+// zema_get_state, bodies back to back) to (set) or from (get) the node
+// arrays.  One block per body: a tet body's vertices (x then v) by the
+// block's threads; an affine body's 24 values by thread 0 (caller's frame
+// q = (p, A by rows) against the internal p' = p + A com and columns of A).
+template <bool kSet>
+__global__ void k_scene_state(int n_bodies, const int* node0, const int* nv, const int64_t* off, const int* fixed,
+                              const double* com, double* x, double* v, double* flat) {
+    const int b = blockIdx.x;
+    if (b >= n_bodies) return;
+    const int n0 = node0[b], m = nv[b];
+    double* f = flat + off[b];
+    if (m >= 0) {
+        for (int i = threadIdx.x; i < 3 * m; i += blockDim.x) {
+            if (kSet) {
+                x[3 * (size_t)n0 + i] = f[i];
+                v[3 * (size_t)n0 + i] = f[3 * (size_t)m + i];
+            } else {
+                f[i] = x[3 * (size_t)n0 + i];
+                f[3 * (size_t)m + i] = v[3 * (size_t)n0 + i];
+            }
+        }
+        return;
+    }
+    if (threadIdx.x != 0) return;
+    const double* c = com + 3 * (size_t)b;
+    double* xc = x + 3 * (size_t)n0;
+    double* vc = v + 3 * (size_t)n0;
+    for (int i = 0; i < 3; ++i) {
+        double Ac = 0.0, Adc = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            if (kSet) {
+                xc[3 * (1 + k) + i] = f[3 + 3 * i + k];
+                vc[3 * (1 + k) + i] = fixed[b] ? 0.0 : f[12 + 3 + 3 * i + k];
+                Ac += f[3 + 3 * i + k] * c[k];
+                Adc += f[12 + 3 + 3 * i + k] * c[k];
+            } else {
+                f[3 + 3 * i + k] = xc[3 * (1 + k) + i];
+                f[12 + 3 + 3 * i + k] = vc[3 * (1 + k) + i];
+                Ac += xc[3 * (1 + k) + i] * c[k];
+                Adc += vc[3 * (1 + k) + i] * c[k];
+            }
+        }
+        if (kSet) {
+            xc[i] = f[i] + Ac;
+            vc[i] = fixed[b] ? 0.0 : f[12 + i] + Adc;
+        } else {
+            f[i] = xc[i] - Ac;
+            f[12 + i] = vc[i] - Adc;
+        }
+    }
+}
+
+// the per-body tables of the flat scene state (built once)
+int64_t scene_state_tables(zema_scene* s) {
+    if (s->sst_n >= 0) return s->sst_n;
+    const int nb = (int)s->bodies.size();
+    std::vector<int> node0(nb), nv(nb), fixed(nb, 0);
+    std::vector<int64_t> off(nb);
+    std::vector<double> com(3 * (size_t)nb, 0.0);
+    int64_t o = 0;
+    for (int b = 0; b < nb; ++b) {
+        const auto bk = s->bodies[b];
+        off[b] = o;
+        if (bk.first == 0) {
+            node0[b] = s->tet_body_node0[bk.second];
+            nv[b] = (int)(s->tin[bk.second].X.size() / 3);
+            o += 6 * (int64_t)nv[b];
+        } else {
+            node0[b] = s->aff_node0_h[bk.second];
+            nv[b] = -1;
+            fixed[b] = s->ain[bk.second].mode == 1 ? 1 : 0;
+            for (int k = 0; k < 3; ++k) com[3 * (size_t)b + k] = s->aff_com_h[3 * (size_t)bk.second + k];
+            o += 24;
+        }
+    }
+    up(s, s->sst_node0, node0);
+    up(s, s->sst_nv, nv);
+    up(s, s->sst_fixed, fixed);
+    up(s, s->sst_off, off);
+    up(s, s->sst_com, com);
+    s->sst_buf.ensure(&s->A, (size_t)o + 1);
+    s->sst_n = o;
+    return o;
+}
+}  // namespace
+
+extern "C" {
+
+zema_status zema_scene_state_size(const zema_scene* cs, int64_t* n) {
+    zema_scene* s = const_cast<zema_scene*>(cs);
+    if (!s || !n) return ZEMA_ERR_INVALID_ARG;
+    if (!s->finalized) return ZEMA_ERR_STATE;
+    ZEMA_TRY(s) {
+        *n = scene_state_tables(s);
+        return ZEMA_OK;
+    }
+    ZEMA_CATCH(s)
+}
+
+zema_status zema_get_scene_state(const zema_scene* cs, double* out, int64_t cap, int64_t* written) {
+    zema_scene* s = const_cast<zema_scene*>(cs);
+    if (s) set_current_stream(s->st);
+    if (!s || !out) return ZEMA_ERR_INVALID_ARG;
+    if (!s->finalized) return ZEMA_ERR_STATE;
+    ZEMA_TRY(s) {
+        const int64_t n = scene_state_tables(s);
+        if (cap < n) return ZEMA_ERR_INVALID_ARG;
+        const int nb = (int)s->bodies.size();
+        if (nb)
+            ZL(k_scene_state<false>, nb, 128, 0, s->st)(nb, s->sst_node0.p, s->sst_nv.p, s->sst_off.p,
+                                                        s->sst_fixed.p, s->sst_com.p, s->x.p, s->v.p, s->sst_buf.p);
+        ZLAUNCH();
+        ZCHECK(cudaMemcpyAsync(out, s->sst_buf.p, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+        ZCHECK(cudaStreamSynchronize(s->st));
+        if (written) *written = n;
+        return ZEMA_OK;
+    }
+    ZEMA_CATCH(s)
+}
+
+zema_status zema_set_scene_state(zema_scene* s, const double* in, int64_t n) {
+    if (s) set_current_stream(s->st);
+    if (!s || !in) return ZEMA_ERR_INVALID_ARG;
+    if (!s->finalized) return ZEMA_ERR_STATE;
+    ZEMA_TRY(s) {
+        if (n != scene_state_tables(s)) return ZEMA_ERR_INVALID_ARG;
+        const int nb = (int)s->bodies.size();
+        ZCHECK(cudaMemcpyAsync(s->sst_buf.p, in, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, s->st));
+        if (nb)
+            ZL(k_scene_state<true>, nb, 128, 0, s->st)(nb, s->sst_node0.p, s->sst_nv.p, s->sst_off.p, s->sst_fixed.p,
+                                                       s->sst_com.p, s->x.p, s->v.p, s->sst_buf.p);
+        ZLAUNCH();
+        // the caller may reuse `in` on return
         ZCHECK(cudaStreamSynchronize(s->st));
         return ZEMA_OK;
     }

@@ -84,6 +84,9 @@ def lib():
     L.zema_finalize.argtypes = [C.c_void_p]
     L.zema_set_kinematic_target.argtypes = [C.c_void_p, C.c_int32, DP]
     L.zema_set_kinematic_targets.argtypes = [C.c_void_p, C.c_int64, IP, DP]
+    L.zema_scene_state_size.argtypes = [C.c_void_p, LP]
+    L.zema_get_scene_state.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, LP]
+    L.zema_set_scene_state.argtypes = [C.c_void_p, C.c_void_p, C.c_int64]
     L.zema_step.argtypes = [C.c_void_p, C.c_int32, C.POINTER(StepStats)]
     L.zema_get_state.argtypes = [C.c_void_p, C.c_int32, DP, C.c_int64, LP]
     L.zema_set_state.argtypes = [C.c_void_p, C.c_int32, DP, C.c_int64]
@@ -420,6 +423,28 @@ class Scene:
         """Arm one failure of the next step call (zema_inject_fault): 1 status
         word, 2 non-finite solve, 3 no line-search decrease; 0 disarms."""
         _check(lib().zema_inject_fault(self.h, int(kind), int(newton_iter)), self.h)
+
+    def scene_state_size(self) -> int:
+        n = C.c_int64()
+        _check(lib().zema_scene_state_size(self.h, C.byref(n)), self.h)
+        return n.value
+
+    def get_scene_state(self) -> np.ndarray:
+        """Every body's state, bodies back to back in order of addition."""
+        out = np.zeros(self.scene_state_size())
+        _check(lib().zema_get_scene_state(self.h, out.ctypes.data_as(C.c_void_p), len(out), None), self.h)
+        return out
+
+    def set_scene_state(self, arr):
+        a = _d(arr)
+        _check(lib().zema_set_scene_state(self.h, a.ctypes.data_as(C.c_void_p), len(a)), self.h)
+
+    def get_scene_state_ptr(self, ptr, cap):
+        """Into caller memory at ptr (host, e.g. pinned)."""
+        _check(lib().zema_get_scene_state(self.h, C.c_void_p(ptr), cap, None), self.h)
+
+    def set_scene_state_ptr(self, ptr, n):
+        _check(lib().zema_set_scene_state(self.h, C.c_void_p(ptr), n), self.h)
 
     def get_state(self, body):
         cap = 1 << 24

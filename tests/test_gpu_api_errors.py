@@ -121,3 +121,37 @@ def test_batched_kinematic_targets():
     assert L.zema_set_kinematic_targets(h, 0, None, None) == 0
     a.close()
     b.close()
+
+
+def test_whole_scene_state():
+    """zema_get/set_scene_state: every body's state in one flat array (the
+    per-body layouts back to back in order of addition); a step after setting
+    it equals a step after setting each body, bit for bit; size mismatches
+    are rejected with nothing changed."""
+    from paper_2311_05945_b300 import zema as Z
+    sc = S.scene_c3(n_envs=2, n_steps=12, min_tets=300, max_tets=600, finger_subdiv=3)
+    a, b = Z.Scene(sc, precision=1), Z.Scene(sc, precision=1)
+    a.step(6)
+    flat = a.get_scene_state()
+    per = [a.get_state(i) for i in range(len(sc.body_order()))]
+    assert np.array_equal(flat, np.concatenate(per))
+    # the same state into two fresh scenes, once through the flat call and
+    # once per body (the multipliers stay at their fresh values in both)
+    b.set_scene_state(flat)
+    assert np.array_equal(b.get_scene_state(), flat)
+    c = Z.Scene(sc, precision=1)
+    for i, x in enumerate(per):
+        c.set_state(i, x)
+    for g in (b, c):
+        g.step_index = a.step_index
+    b.step(2)
+    c.step(2)
+    assert np.array_equal(b.get_scene_state(), c.get_scene_state())
+    L, h = Z.lib(), b.h
+    keep = b.get_scene_state()
+    short = np.zeros(len(flat) - 1)
+    assert L.zema_set_scene_state(h, short.ctypes.data_as(C.c_void_p), len(short)) == INVALID_ARG
+    assert L.zema_get_scene_state(h, short.ctypes.data_as(C.c_void_p), len(short), None) == INVALID_ARG
+    assert np.array_equal(b.get_scene_state(), keep)
+    for g in (a, b, c):
+        g.close()
