@@ -68,7 +68,8 @@ typedef struct {
     double pcg_rel_tol;    /* PCG stop: |r| <= pcg_rel_tol * |b| */
     int32_t max_newton;    /* Newton iteration cap per solve */
     int32_t max_pcg;       /* PCG iteration cap per solve */
-    int32_t max_al_rounds; /* kinematic augmented-Lagrangian rounds per step */
+    int32_t max_al_rounds; /* kinematic augmented-Lagrangian rounds per env and step (each round
+                              restarts the env's max_newton count) */
     int32_t precision;     /* 0: FP64 throughout; 1: mixed (FP32 Hessians, stored matrices,
                               preconditioner and PCG with FP64 residual refinement; FP64
                               gradients, energies, distances, ACCD and convergence test) */
@@ -107,7 +108,7 @@ typedef struct {
     int64_t newton_iters;   /* applied Newton steps */
     int64_t pcg_iters;      /* PCG iterations over all solves */
     int64_t ls_halvings;    /* line-search halvings */
-    int64_t al_rounds;      /* kinematic AL outer rounds */
+    int64_t al_rounds;      /* kinematic AL rounds: per step the largest count of any env */
     int64_t warm_accepted;  /* accepted warm-start proposals (per env step) */
     int64_t max_candidates; /* largest candidate-pair count seen in one broad phase */
     int64_t max_active;     /* largest active (d < dhat) pair count */
@@ -115,7 +116,8 @@ typedef struct {
     double kappa;           /* barrier stiffness of env 0 after the last step */
     double energy;          /* incremental potential of env 0 at the last converged iterate */
     double ms_phase[6];     /* host-timed phases: DCD, energy, Hessian, linear, CCD, other (ms) */
-    int64_t pcg_refines;    /* FP64 residual-refinement restarts of FP32 solves (mixed precision) */
+    int64_t pcg_refines;    /* FP64 residual-refinement correction solves of FP32 solves (mixed
+                               precision), summed over envs */
     int64_t warm_learned;   /* accepted learned warm-start corrections (per env step) */
     int64_t warm_fallback;  /* steps redone from the constant-velocity start after Newton failed from the learned one */
 } zema_step_stats;
