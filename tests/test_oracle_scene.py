@@ -459,6 +459,36 @@ def test_kinematic_multiplier_extrapolation():
     assert sum(rounds[1][4:]) == 0, rounds
 
 
+def test_kinematic_multiplier_extrapolation_is_exact_for_a_linearly_growing_force():
+    # A kinematic box driven along x with constant jerk j needs a force that
+    # grows linearly in time.  The unextrapolated multipliers start every step
+    # one step's change behind and leave the body a constant lag (under the
+    # tolerance here, so no round runs); the extrapolated ones, 2 lambda^t -
+    # lambda^(t-1) after the end-of-step update, are exact for a linear
+    # history, so the body lands on its target.  A wrong extrapolation weight
+    # or a missing end-of-step update leaves a lag of the unextrapolated size.
+    def target(n, dt, j=1000.0):
+        t = (n + 1) * dt
+        q = np.zeros(12)
+        q[:3] = (j * t ** 3 / 6.0, 0.5, 0.0)
+        q[3] = q[7] = q[11] = 1.0
+        return q
+
+    last = {}
+    for ex in (0, 1):
+        s = S.scene_kinematic_track(10, n_steps=14)
+        s.params.al_extrapolate = ex
+        dt = s.params.dt
+        s.script = lambda n, dt=dt: {0: target(n, dt)}
+        o = Oracle(s)
+        tol = s.params.newton_tol_rel * o.diag() * dt
+        for n in range(14):
+            o.step(1)
+        last[ex] = np.abs(o.affine_q(0) - target(13, dt)).max() / tol
+    assert last[0] > 0.5, last
+    assert last[1] < 0.01, last
+
+
 def test_kappa_min_is_a_thousand_mean_lumped_masses():
     # the adaptive barrier stiffness floor: 1e3 x the mean lumped soft-vertex mass
     s = S.scene_c1()
