@@ -80,7 +80,9 @@ class AutoGrasp:
                 self.q[idx][2] -= self.sign[idx] * phi(f[idx], self.f_star, self.k) * self.close_speed * self.dt
             elif self.lift_done[e] < self.lift_steps:
                 self.q[idx][1] += self.lift_height / self.lift_steps
-            self.gpu.set_kinematic_target(idx, self.q[idx])
+        if self.q:
+            idx = list(self.q)
+            self.gpu.set_kinematic_targets(idx, np.array([self.q[i] for i in idx], dtype=np.float64))
         for e in self.lift_done:
             if self.lift_done[e] is not None and self.lift_done[e] < self.lift_steps:
                 self.lift_done[e] += 1
