@@ -5,8 +5,11 @@ f* = 0.5 N).  Then the controller's host logic (closing by phi, the stop and
 stall rules, the per-env lift, one batch of targets per step) on a stand-in
 scene with prescribed forces."""
 import math
+import types
 
-from paper_2311_05945_b300.grasp import phi
+import numpy as np
+
+from paper_2311_05945_b300.grasp import AutoGrasp, phi
 
 
 def test_phi_end_points_and_cutoff():
@@ -36,12 +39,6 @@ def test_phi_small_force_decay():
 # ---------------------------------------------------------------------------
 # The controller's host logic on a stand-in scene: forces are prescribed per
 # step, and the targets the controller hands over are recorded.
-
-import types
-
-import numpy as np
-
-from paper_2311_05945_b300.grasp import AutoGrasp
 
 
 class _RecordingScene:
