@@ -90,9 +90,11 @@ typedef struct {
     double cell_size;      /* spatial-hash cell edge (m); <= 0: the mean surface edge length, at
                               least dhat */
     int32_t pcg_cluster_size; /* cluster schedule of the solve: CTAs per env (1, 2, 4, 8 or 16), plus 100
-                                 for the two-CTAs-per-SM variant (see zema_get_tuning); 0: about one CTA
-                                 per 128 nodes or the autotuner's choice.  A schedule the scene or device
-                                 cannot run makes zema_step return ZEMA_ERR_INVALID_ARG */
+                                 for the two-CTAs-per-SM variant, or a size-binned code 1001, 1002, 1004,
+                                 1101, 1102, 1104 (see zema_get_tuning); 0: about one CTA per 128 nodes
+                                 or the autotuner's choice.  Any other value makes zema_create_scene
+                                 return ZEMA_ERR_INVALID_ARG; a schedule the scene or device cannot run
+                                 makes zema_step return it */
     int32_t al_extrapolate; /* 1 (default): each step starts the kinematic multipliers lambda_A of
                                Eq. 13 at 2 lambda^t - lambda^(t-1), the linear extrapolation of the
                                last two steps' converged values (the paper does not say how the

@@ -73,6 +73,37 @@ def test_default_params_match_the_header():
     assert not p.stream and not p.alloc and not p.free
 
 
+
+def test_create_scene_checks_its_parameters_on_the_host():
+    # zema_create_scene validates the parameters before any device work:
+    # the schedule pin accepts the documented codes only
+    from paper_2311_05945_b300.zema import Params
+    L = ctypes.CDLL(zbuild.build())
+    L.zema_default_params.argtypes = [ctypes.POINTER(Params)]
+    L.zema_create_scene.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_void_p)]
+    L.zema_destroy_scene.argtypes = [ctypes.c_void_p]
+
+    def create(**kw):
+        p = Params()
+        L.zema_default_params(ctypes.byref(p))
+        for k, v in kw.items():
+            setattr(p, k, v)
+        h = ctypes.c_void_p()
+        r = L.zema_create_scene(ctypes.byref(p), ctypes.byref(h))
+        if r == 0:
+            L.zema_destroy_scene(h)
+        return r
+
+    ok = [1, 2, 4, 8, 16, 101, 102, 104, 108, 116, 1001, 1002, 1004, 1101, 1102, 1104]
+    for code in ok:
+        assert create(pcg_cluster_size=code) == 0, code
+    for code in (-1, 3, 6, 32, 100, 103, 132, 200, 1000, 1003, 1008, 1100, 1202, 2002):
+        assert create(pcg_cluster_size=code) == 1, code
+    assert create(pcg_kind=3) == 1 and create(pcg_kind=-1) == 1
+    assert create(n_envs=0) == 1 and create(dt=0.0) == 1 and create(dhat=-1e-3) == 1
+    assert create(eps_v=0.0) == 1 and create(cell_size=float("inf")) == 1
+    assert create(n_envs=256, pcg_kind=2, cell_size=0.004) == 0
+
 def _affine_adder():
     from paper_2311_05945_b300.zema import Params
     L = ctypes.CDLL(zbuild.build())
