@@ -51,3 +51,39 @@ def test_window_starts_at_contact_and_sample_strides():
     assert ids == list(range(0, 256, 16))
     args.seq_envs = 400
     assert bench.sequential_sample(args, argparse.Namespace(n_envs=256)) == list(range(256))
+
+
+def test_clock_record_parsing(tmp_path):
+    # the clocks line summarises nvidia-smi's samples: median SM clock under
+    # load, the maximum, and every throttle reason seen active at least once
+    rows = [
+        "0, 2032, 2032, 700.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 1980, 2032, 1090.5, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2010, 2032, 1050.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, [N/A], 2032, [N/A], [N/A], [N/A], [N/A], [N/A], [N/A]",
+        "0, 2032",
+    ]
+    path = tmp_path / "clocks.csv"
+    path.write_text("\n".join(rows) + "\n")
+
+    class Done:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    c = bench.Clocks(0)
+    c.proc, c.path = Done(), str(path)
+    out = c.stop()
+    assert out == {"sm_mhz": 2010.0, "sm_max_mhz": 2032.0, "reasons": ["sw_power_cap"], "samples": 3}
+    assert not path.exists()
+    # a throttle that a run must be rejected for is reported by name
+    path.write_text("0, 1500, 2032, 900.0, 0x48, Not Active, Active, Not Active, Not Active\n")
+    c.proc, c.path = Done(), str(path)
+    assert c.stop()["reasons"] == ["hw_thermal_slowdown"]
+    # no sampler, or no usable sample: no clocks line
+    assert bench.Clocks(0).stop() is None
+    path.write_text("")
+    c.proc, c.path = Done(), str(path)
+    assert c.stop() is None
