@@ -1,10 +1,12 @@
-"""The batched grasp generator (C3) against its recipe, on the CPU: per env a
+"""The grasp generators on the CPU.  The batched grasp (C3) against its recipe, on the CPU: per env a
 seeded object kind, a tet count log-uniform in [2k, 20k], E log-uniform in
 [1e4, 1e6] Pa, mu uniform in [0.3, 1], nu = 0.45, two kinematic fingers of
 972 triangles and a fixed floor, envs 0.5 m apart and spatially disjoint.
 A range of envs built on its own (seed and slot advanced together) is the
 same, array for array and target for target, as that range of the whole
-batch: this is what lets ranks step disjoint env ranges of one batch."""
+batch: this is what lets ranks step disjoint env ranges of one batch.  The
+single-env grasp (C2) against its recipe and its finger script, which
+brings both fingers to the object at the 20th step."""
 import math
 
 import numpy as np
@@ -87,3 +89,45 @@ def test_c3_env_range_equals_that_range_of_the_whole_batch():
                 assert (jf in tf) == (jp in tp)
                 if jf in tf:
                     assert np.array_equal(tf[jf], tp[jp]), (step, i)
+
+
+def test_c2_grasp_recipe_and_script():
+    # one env: a 4 / 2 / 3 cm ellipsoid lattice of 9,600 tets (E = 5e4, nu =
+    # 0.45) 0.5 dhat above a fixed floor, two kinematic 6 x 3 x 1 cm fingers
+    # of 972 triangles 0.5 cm off its z extremes; mu = 0.8, h = 5 ms
+    sc = S.scene_c2(n_steps=300)
+    p = sc.params
+    assert (p.dt, p.dhat) == (0.005, 1e-3)
+    (b,) = sc.tets
+    assert len(b.tets) == 9600 and (b.E, b.nu, b.mu) == (5e4, 0.45, 0.8)
+    ext = b.X.max(0) - b.X.min(0)
+    assert np.all(np.abs(ext - (0.08, 0.04, 0.06)) <= 2 * 0.004), ext
+    floor = [a for a in sc.affines if a.mode == 1]
+    fingers = [a for a in sc.affines if a.mode == 2]
+    assert len(floor) == 1 and len(fingers) == 2
+    top = floor[0].q0[1] + floor[0].V[:, 1].max()
+    assert abs(b.X[:, 1].min() - top - 0.5 * p.dhat) < 1e-15
+    zmax, zmin = b.X[:, 2].max(), b.X[:, 2].min()
+    for a in fingers:
+        assert len(a.F) == 972 and a.mu == 0.8
+        fe = a.V.max(0) - a.V.min(0)
+        assert np.allclose(fe, (0.06, 0.03, 0.01))
+        inner = a.q0[2] + (a.V[:, 2].min() if a.q0[2] > 0 else a.V[:, 2].max())
+        assert abs(abs(inner - (zmax if a.q0[2] > 0 else zmin)) - 0.005) < 1e-12
+    # script: close at 5 cm/s for 40 steps, hold 60, lift 5 cm over 200;
+    # arrays(n) are the targets of the state after step n
+    idx, Q0 = sc.script.arrays(-1)
+    fing = {i: sign for i, sign, _ in sc.fingers}
+    for n, closed, lifted in ((0, 0.00025, 0.0), (19, 0.005, 0.0), (39, 0.01, 0.0), (99, 0.01, 0.0),
+                              (199, 0.01, 0.025), (299, 0.01, 0.05)):
+        _, Q = sc.script.arrays(n)
+        for j, i in enumerate(idx):
+            assert abs(-(Q[j, 2] - Q0[j, 2]) * fing[int(i)] - closed) < 1e-15, (n, closed)
+            assert abs(Q[j, 1] - Q0[j, 1] - lifted) < 1e-15
+    # both fingers reach the object's extremes at the 20th step: the start of
+    # the contact window the benchmark times
+    _, Q = sc.script.arrays(19)
+    for j, i in enumerate(idx):
+        a = sc.affines[int(i)]
+        inner = Q[j, 2] + (a.V[:, 2].min() if fing[int(i)] > 0 else a.V[:, 2].max())
+        assert abs(inner - (zmax if fing[int(i)] > 0 else zmin)) < 1e-12
