@@ -1,5 +1,6 @@
-"""The grasp generators on the CPU.  The batched grasp (C3) against its recipe, on the CPU: per env a
-seeded object kind, a tet count log-uniform in [2k, 20k], E log-uniform in
+"""The grasp generators on the CPU.
+
+The batched grasp (C3) against its recipe: per env a seeded object kind, a tet count log-uniform in [2k, 20k], E log-uniform in
 [1e4, 1e6] Pa, mu uniform in [0.3, 1], nu = 0.45, two kinematic fingers of
 972 triangles and a fixed floor, envs 0.5 m apart and spatially disjoint.
 A range of envs built on its own (seed and slot advanced together) is the
