@@ -1,12 +1,14 @@
 """The grasp generators on the CPU.
 
-The batched grasp (C3) against its recipe: per env a seeded object kind, a tet count log-uniform in [2k, 20k], E log-uniform in
-[1e4, 1e6] Pa, mu uniform in [0.3, 1], nu = 0.45, two kinematic fingers of
-972 triangles and a fixed floor, envs 0.5 m apart and spatially disjoint.
-A range of envs built on its own (seed and slot advanced together) is the
-same, array for array and target for target, as that range of the whole
-batch: this is what lets ranks step disjoint env ranges of one batch.  The
-single-env grasp (C2) against its recipe and its finger script, which
+The batched grasp (C3) against its recipe: per env a seeded object kind, a
+tet count log-uniform in [2k, 20k], E log-uniform in [1e4, 1e6] Pa, mu
+uniform in [0.3, 1], nu = 0.45, two kinematic fingers of 972 triangles and a
+fixed floor, envs 0.5 m apart and spatially disjoint.  A range of envs built
+on its own (seed and slot advanced together) is the same, array for array
+and target for target, as that range of the whole batch: this is what lets
+ranks step disjoint env ranges of one batch.
+
+The single-env grasp (C2) against its recipe and its finger script, which
 brings both fingers to the object at the 20th step."""
 import math
 
