@@ -1094,14 +1094,14 @@ struct State {
     std::vector<double> q;  // all affine states (12 per body)
 };
 
-void load_dofs(const Scene& S, const EnvDofs& D, const std::vector<double>& y, State& st) {
+void load_dofs(const Scene&, const EnvDofs& D, const std::vector<double>& y, State& st) {
     for (int i : D.verts)
         for (int k = 0; k < 3; ++k) st.x[3 * i + k] = y[D.vert_dof[i] + k];
     for (int a : D.affs)
         for (int k = 0; k < 12; ++k) st.q[12 * a + k] = y[D.aff_dof[a] + k];
 }
 
-void store_dofs(const Scene& S, const EnvDofs& D, const State& st, std::vector<double>& y) {
+void store_dofs(const Scene&, const EnvDofs& D, const State& st, std::vector<double>& y) {
     y.assign(D.n, 0.0);
     for (int i : D.verts)
         for (int k = 0; k < 3; ++k) y[D.vert_dof[i] + k] = st.x[3 * i + k];
