@@ -2,7 +2,10 @@
 the host-only part of the boundary (no GPU needed): default parameters,
 parameter checks, scene creation, a body added and one rejected with its
 status and message, and teardown.  This checks that the header is valid C
-(no C++ or torch types) and that the entry points link from C."""
+(no C++ or torch types) and that the entry points link from C.  The
+binding's ctypes structures are checked against the C layout (size and
+every field's offset)."""
+import ctypes
 import os
 import subprocess
 
@@ -66,3 +69,33 @@ def test_c99_client_links_and_drives_the_host_calls(tmp_path):
     out = subprocess.run([str(exe)], check=True, capture_output=True, text=True, timeout=60).stdout.split("\n")
     assert out[:8] == ["defaults 0.01 0.001 100 10000", "n_envs0 1", "schedule3 1", "create 0 1", "add 0 0",
                        "inverted 5 1", "env2 1", "done"], out
+
+
+def _c_layout(tmp_path, struct, fields):
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "zema.h"', "int main(void) {",
+             f'    printf("sizeof %zu\\n", sizeof({struct}));']
+    for f in fields:
+        lines.append(f'    printf("{f} %zu\\n", offsetof({struct}, {f}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / f"{struct}.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / struct
+    try:
+        subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                        str(exe)], check=True, capture_output=True, text=True)
+    except FileNotFoundError:
+        pytest.skip("no C compiler")
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True, timeout=60).stdout.split()
+    return {k: int(v) for k, v in zip(out[0::2], out[1::2])}
+
+
+def test_binding_structures_match_the_c_layout(tmp_path):
+    # the ctypes structures of the binding have the C structures' size and
+    # every field at the C offset, field by field
+    from paper_2311_05945_b300.zema import Params, StepStats
+    for struct, cls in (("zema_scene_params", Params), ("zema_step_stats", StepStats)):
+        names = [f for f, _ in cls._fields_]
+        c = _c_layout(tmp_path, struct, names)
+        assert c["sizeof"] == ctypes.sizeof(cls), struct
+        for f in names:
+            assert c[f] == getattr(cls, f).offset, (struct, f)
