@@ -204,3 +204,54 @@ def test_tet_body_arguments_checked_at_add_time():
     assert add([[0, 1, 2, 3]], nu=0.5) == 1  # incompressible limit
     assert add([[0, 1, 2, 3]], env=1) == 1   # one env only
     L.zema_destroy_scene(h)
+
+
+def _header_prototypes():
+    src = open(os.path.join(ROOT, "include", "zema.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"#[^\n]*", "", src)
+    protos = {}
+    for m in re.finditer(r"([A-Za-z_][A-Za-z_0-9 \*]*?)\b(zema_[a-z_0-9]+)\s*\(([^)]*)\)\s*;", src):
+        ret, name, args = m.group(1).strip(), m.group(2), m.group(3).strip()
+        params = [] if args in ("", "void") else [a.strip() for a in args.split(",")]
+        protos[name] = (ret, params)
+    return protos
+
+
+def _kind_of_c(param):
+    # pointer (or array) parameters, else the scalar type
+    if "*" in param or "[" in param:
+        return "ptr"
+    t = re.sub(r"\bconst\b", "", param).split()
+    return " ".join(t[:-1])
+
+
+def test_binding_argtypes_match_the_header():
+    # every entry point the binding declares takes the header's parameters:
+    # the same count, a pointer where the header has one, the same scalar
+    # type elsewhere, and the header's non-status return types
+    import ctypes as C
+
+    from paper_2311_05945_b300 import zema as Z
+    scalar = {"int32_t": C.c_int32, "int64_t": C.c_int64, "uint64_t": C.c_uint64, "double": C.c_double,
+              "float": C.c_float}
+    protos = _header_prototypes()
+    assert sorted(protos) == declared_symbols()
+    L = Z.lib()
+    checked = 0
+    for name, (ret, params) in protos.items():
+        f = getattr(L, name)
+        assert f.argtypes is not None, name
+        assert len(f.argtypes) == len(params), name
+        for a, p in zip(f.argtypes, params):
+            k = _kind_of_c(p)
+            if k == "ptr":
+                assert a in (C.c_void_p, C.c_char_p) or hasattr(a, "_type_") and issubclass(a, C._Pointer), (name, p)
+            else:
+                assert a is scalar[k], (name, p, a)
+        if ret == "const char*":
+            assert f.restype is C.c_char_p, name
+        elif ret == "long long":
+            assert f.restype is C.c_longlong, name
+        checked += 1
+    assert checked == len(protos)
