@@ -519,8 +519,11 @@ zema_status zema_record_warmstart_affine(zema_scene* s, float* features, float* 
  * reductions in a fixed order).
  * ------------------------------------------------------------------------ */
 typedef struct zema_mlp zema_mlp;
-/* dims: n_layers + 1 widths (1..4096), n_layers 1..16; weights He-uniform from
- * a SplitMix64 stream seeded with `seed`, biases zero. */
+/* dims: n_layers + 1 widths (1..4096), n_layers 1..16 (else
+ * ZEMA_ERR_INVALID_ARG); weights He-uniform from a SplitMix64 stream seeded
+ * with `seed`, biases zero.  ZEMA_ERR_OOM when device memory runs out,
+ * ZEMA_ERR_CUDA on any other CUDA failure (no device included); *out is
+ * written only on success. */
 zema_status zema_mlp_create(const int32_t* dims, int32_t n_layers, uint64_t seed, void* stream, zema_mlp** out);
 void zema_mlp_destroy(zema_mlp* m);
 zema_status zema_mlp_n_params(const zema_mlp* m, int64_t* n);

@@ -1,6 +1,7 @@
 // Tensor-core MLP: BF16 operands, FP32 accumulation, deterministic training.
 #include <cmath>
 #include <cstring>
+#include <new>
 #include <string>
 
 #include "mlp.cuh"
@@ -403,16 +404,19 @@ extern "C" zema_status zema_mlp_create(const int32_t* dims, int32_t n_layers, ui
     if (!dims || !out || n_layers < 1 || n_layers > 16) return ZEMA_ERR_INVALID_ARG;
     for (int l = 0; l <= n_layers; ++l)
         if (dims[l] < 1 || dims[l] > 4096) return ZEMA_ERR_INVALID_ARG;
+    zema_mlp* m = new (std::nothrow) zema_mlp();
+    if (!m) return ZEMA_ERR_OOM;
     try {
-        zema_mlp* m = new zema_mlp();
         m->net = new zema::Mlp(std::vector<int>(dims, dims + n_layers + 1), seed, (cudaStream_t)stream);
-        *out = m;
-        return ZEMA_OK;
     } catch (const ZemaError& e) {
+        delete m;
         return mlp_status(e);
     } catch (...) {
+        delete m;
         return ZEMA_ERR_OOM;
     }
+    *out = m;
+    return ZEMA_OK;
 }
 
 extern "C" void zema_mlp_destroy(zema_mlp* m) {

@@ -22,7 +22,11 @@ struct Allocator {
             if (!p) throw ZemaError{2, "device allocation failed"};
         } else {
             cudaError_t e = cudaMalloc(&p, bytes);
-            if (e != cudaSuccess) throw ZemaError{2, std::string("cudaMalloc: ") + cudaGetErrorString(e)};
+            // out of memory is ZEMA_ERR_OOM; any other failure (no device, a
+            // lost context) is ZEMA_ERR_CUDA
+            if (e != cudaSuccess)
+                throw ZemaError{e == cudaErrorMemoryAllocation ? 2 : 3,
+                                std::string("cudaMalloc: ") + cudaGetErrorString(e)};
         }
         bytes_live += bytes;
         return p;

@@ -255,3 +255,28 @@ def test_binding_argtypes_match_the_header():
             assert f.restype is C.c_longlong, name
         checked += 1
     assert checked == len(protos)
+
+
+def test_mlp_create_checks_its_arguments_on_the_host():
+    # widths 1..4096 and 1..16 layers are checked before any device work; on
+    # a machine without a GPU a valid network fails with a status and no
+    # handle instead of a CPU fallback
+    import torch
+
+    from paper_2311_05945_b300 import zema as Z
+    L = Z.lib()
+
+    def create(dims, n_layers=None):
+        d = (ctypes.c_int32 * len(dims))(*dims)
+        h = ctypes.c_void_p()
+        r = L.zema_mlp_create(d, len(dims) - 1 if n_layers is None else n_layers, 7, None, ctypes.byref(h))
+        return r, h.value
+
+    assert create([13, 128, 3], n_layers=0) == (1, None)
+    assert create([13] * 18, n_layers=17) == (1, None)
+    assert create([13, 0, 3]) == (1, None)
+    assert create([13, 4097, 3]) == (1, None)
+    assert create([-1, 128, 3]) == (1, None)
+    if not torch.cuda.is_available():
+        r, h = create([13, 128, 128, 128, 3])
+        assert (r, h) == (3, None)  # ZEMA_ERR_CUDA: no device
