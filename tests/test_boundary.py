@@ -280,3 +280,30 @@ def test_mlp_create_checks_its_arguments_on_the_host():
     if not torch.cuda.is_available():
         r, h = create([13, 128, 128, 128, 3])
         assert (r, h) == (3, None)  # ZEMA_ERR_CUDA: no device
+
+
+def test_local_entry_points_check_arguments_and_take_empty_input_on_the_host():
+    # the per-stencil entry points check their arguments before any device
+    # work, and an empty batch (n = 0) returns ZEMA_OK without one
+    import numpy as np
+
+    from paper_2311_05945_b300 import zema as Z
+    L = Z.lib()
+    DP, IP = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)
+    d = np.zeros(16 * 144)
+    i = np.zeros(16, dtype=np.int32)
+    dp, ip = d.ctypes.data_as(DP), i.ctypes.data_as(IP)
+    calls = {
+        "barrier": lambda n, dhat=1e-3: L.zema_local_barrier(n, dp, ip, dp, dhat, dp, dp, dp, None),
+        "distance": lambda n: L.zema_local_distance(n, dp, ip, dp, dp, None),
+        "neo_hookean": lambda n: L.zema_local_neo_hookean(n, dp, 1.0, 1.0, dp, dp, dp, None),
+        "elastic": lambda n, model=0: L.zema_local_elastic(n, dp, 1.0, 1.0, model, dp, dp, dp, None),
+        "accd": lambda n: L.zema_local_accd(n, dp, dp, ip, dp, None),
+    }
+    for name, f in calls.items():
+        assert f(0) == 0, name
+        assert f(-1) == 1, name
+    assert calls["barrier"](0, dhat=0.0) == 1
+    assert calls["elastic"](0, model=3) == 1 and calls["elastic"](0, model=-1) == 1
+    assert L.zema_local_distance(0, None, ip, dp, dp, None) == 1
+    assert L.zema_local_accd(0, dp, None, ip, dp, None) == 1
