@@ -307,3 +307,46 @@ def test_local_entry_points_check_arguments_and_take_empty_input_on_the_host():
     assert calls["elastic"](0, model=3) == 1 and calls["elastic"](0, model=-1) == 1
     assert L.zema_local_distance(0, None, ip, dp, dp, None) == 1
     assert L.zema_local_accd(0, dp, None, ip, dp, None) == 1
+
+
+def test_affine_body_arguments_checked_at_add_time():
+    # host-side checks of zema_add_affine_body besides the mesh: env range,
+    # density, stiffness, friction, mode (0 dynamic, 1 fixed, 2 kinematic),
+    # the initial state; the message is kept for zema_last_error
+    import numpy as np
+
+    from paper_2311_05945_b300 import scenes as S
+    from paper_2311_05945_b300.zema import Params
+    L = ctypes.CDLL(zbuild.build())
+    DP, IP = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)
+    L.zema_default_params.argtypes = [ctypes.POINTER(Params)]
+    L.zema_create_scene.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_void_p)]
+    L.zema_add_affine_body.argtypes = [ctypes.c_void_p, ctypes.c_int32, DP, ctypes.c_int64, IP, ctypes.c_int64, DP,
+                                       DP, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int32, IP]
+    L.zema_last_error.restype = ctypes.c_char_p
+    L.zema_last_error.argtypes = [ctypes.c_void_p]
+    L.zema_destroy_scene.argtypes = [ctypes.c_void_p]
+    p = Params()
+    L.zema_default_params(ctypes.byref(p))
+    p.n_envs = 2
+    h = ctypes.c_void_p()
+    assert L.zema_create_scene(ctypes.byref(p), ctypes.byref(h)) == 0
+    V, F = S.box_surface((0.1, 0.1, 0.1), 1)
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    F = np.ascontiguousarray(F, dtype=np.int32)
+    q = np.zeros(12)
+    q[[3, 7, 11]] = 1.0
+    bid = ctypes.c_int32(-1)
+
+    def add(env=0, rho=1000.0, stiffness=1e8, mu=0.5, mode=0, q0=q):
+        return L.zema_add_affine_body(h, env, V.ctypes.data_as(DP), len(V), F.ctypes.data_as(IP), len(F),
+                                      None if q0 is None else q0.ctypes.data_as(DP), None, rho, stiffness, mu,
+                                      mode, ctypes.byref(bid))
+
+    assert add(mode=0) == 0 and bid.value == 0
+    assert add(env=1, mode=1) == 0 and add(env=1, mode=2) == 0 and bid.value == 2
+    for bad in (dict(env=2), dict(env=-1), dict(rho=0.0), dict(stiffness=0.0), dict(mu=-0.1), dict(mode=3),
+                dict(mode=-1), dict(q0=None), dict(rho=float("nan"))):
+        assert add(**bad) == 1, bad
+        assert L.zema_last_error(h) == b"invalid affine body arguments"
+    L.zema_destroy_scene(h)
