@@ -350,3 +350,82 @@ def test_affine_body_arguments_checked_at_add_time():
         assert add(**bad) == 1, bad
         assert L.zema_last_error(h) == b"invalid affine body arguments"
     L.zema_destroy_scene(h)
+
+
+def test_material_spring_and_joint_calls_checked_before_the_first_step():
+    # zema_set_material, zema_set_springs and zema_add_prismatic_joint check
+    # their arguments on the host; before the first step they touch no device
+    import numpy as np
+
+    from paper_2311_05945_b300 import scenes as S
+    from paper_2311_05945_b300.zema import Params
+    L = ctypes.CDLL(zbuild.build())
+    DP, IP = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)
+    L.zema_default_params.argtypes = [ctypes.POINTER(Params)]
+    L.zema_create_scene.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_void_p)]
+    L.zema_add_tet_body.argtypes = [ctypes.c_void_p, ctypes.c_int32, DP, ctypes.c_int64, IP, ctypes.c_int64, DP, DP,
+                                    ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, IP]
+    L.zema_add_affine_body.argtypes = [ctypes.c_void_p, ctypes.c_int32, DP, ctypes.c_int64, IP, ctypes.c_int64, DP,
+                                       DP, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int32, IP]
+    L.zema_set_material.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32]
+    L.zema_set_springs.argtypes = [ctypes.c_void_p, ctypes.c_int32, IP, ctypes.c_int64, DP, ctypes.c_double]
+    L.zema_add_prismatic_joint.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, DP, ctypes.c_double, IP]
+    L.zema_last_error.restype = ctypes.c_char_p
+    L.zema_last_error.argtypes = [ctypes.c_void_p]
+    L.zema_destroy_scene.argtypes = [ctypes.c_void_p]
+    p = Params()
+    L.zema_default_params(ctypes.byref(p))
+    p.n_envs = 2
+    h = ctypes.c_void_p()
+    assert L.zema_create_scene(ctypes.byref(p), ctypes.byref(h)) == 0
+    X = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], dtype=np.float64)
+    T = np.array([[0, 1, 2, 3]], dtype=np.int32)
+    bid = ctypes.c_int32()
+    assert L.zema_add_tet_body(h, 0, X.ctypes.data_as(DP), 4, T.ctypes.data_as(IP), 1, None, None, 1e5, 0.4,
+                               1000.0, 0.5, ctypes.byref(bid)) == 0                 # body 0: soft, env 0
+    V, F = S.box_surface((0.1, 0.1, 0.1), 1)
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    F = np.ascontiguousarray(F, dtype=np.int32)
+    q = np.zeros(12)
+    q[[3, 7, 11]] = 1.0
+    for env, mode in ((0, 0), (0, 1), (1, 0), (0, 1)):                          # bodies 1..4
+        assert L.zema_add_affine_body(h, env, V.ctypes.data_as(DP), len(V), F.ctypes.data_as(IP), len(F),
+                                      q.ctypes.data_as(DP), None, 1000.0, 1e8, 0.5, mode, ctypes.byref(bid)) == 0
+    assert bid.value == 4
+    # materials: soft bodies only, models 0..2
+    assert [L.zema_set_material(h, 0, m) for m in (1, 2, 0)] == [0, 0, 0]
+    assert L.zema_set_material(h, 0, 3) == 1 and L.zema_set_material(h, 1, 0) == 1
+    assert L.zema_set_material(h, 9, 0) == 1
+    # springs: vertex ids of the body, finite targets, finite k >= 0
+    v = np.array([0, 3], dtype=np.int32)
+    x = np.zeros((2, 3))
+
+    def springs(body=0, verts=v, targets=x, k=10.0):
+        return L.zema_set_springs(h, body, verts.ctypes.data_as(IP), len(verts), targets.ctypes.data_as(DP), k)
+
+    assert springs() == 0
+    assert L.zema_set_springs(h, 0, None, 0, None, 0.0) == 0
+    assert springs(verts=np.array([0, 4], dtype=np.int32)) == 1
+    assert springs(k=-1.0) == 1 and springs(k=float("inf")) == 1
+    assert springs(targets=np.array([[0.0, 0.0, 0.0], [np.nan, 0.0, 0.0]])) == 1
+    assert springs(body=1) == 1
+    # prismatic joints: two distinct affine bodies of one env, one of them
+    # dynamic, a nonzero finite axis
+    jid = ctypes.c_int32(-1)
+    ax = np.array([0.0, 2.0, 0.0])
+
+    def joint(b1, b2, axis=ax, kappa=0.0):
+        return L.zema_add_prismatic_joint(h, b1, b2, axis.ctypes.data_as(DP), kappa, ctypes.byref(jid))
+
+    assert joint(1, 2) == 0 and jid.value == 0
+    assert joint(1, 1) == 1 and joint(0, 1) == 1 and joint(1, 9) == 1
+    assert joint(1, 2, kappa=float("inf")) == 1
+    assert L.zema_last_error(h) == b"a prismatic joint needs two distinct affine bodies and an axis"
+    assert joint(1, 3) == 1
+    assert L.zema_last_error(h) == b"jointed bodies must share an env and at least one must be dynamic"
+    assert joint(2, 4) == 1
+    assert L.zema_last_error(h) == b"jointed bodies must share an env and at least one must be dynamic"
+    assert joint(1, 2, axis=np.zeros(3)) == 1 and joint(1, 2, axis=np.array([np.nan, 1.0, 0.0])) == 1
+    assert L.zema_last_error(h) == b"joint axis must be a nonzero finite vector"
+    assert joint(4, 1) == 0 and jid.value == 1
+    L.zema_destroy_scene(h)
