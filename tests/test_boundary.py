@@ -316,17 +316,10 @@ def test_affine_body_arguments_checked_at_add_time():
     import numpy as np
 
     from paper_2311_05945_b300 import scenes as S
-    from paper_2311_05945_b300.zema import Params
-    L = ctypes.CDLL(zbuild.build())
+    from paper_2311_05945_b300 import zema as Z
+    L = Z.lib()  # the binding's declared signatures
     DP, IP = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)
-    L.zema_default_params.argtypes = [ctypes.POINTER(Params)]
-    L.zema_create_scene.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_void_p)]
-    L.zema_add_affine_body.argtypes = [ctypes.c_void_p, ctypes.c_int32, DP, ctypes.c_int64, IP, ctypes.c_int64, DP,
-                                       DP, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int32, IP]
-    L.zema_last_error.restype = ctypes.c_char_p
-    L.zema_last_error.argtypes = [ctypes.c_void_p]
-    L.zema_destroy_scene.argtypes = [ctypes.c_void_p]
-    p = Params()
+    p = Z.Params()
     L.zema_default_params(ctypes.byref(p))
     p.n_envs = 2
     h = ctypes.c_void_p()
@@ -358,22 +351,10 @@ def test_material_spring_and_joint_calls_checked_before_the_first_step():
     import numpy as np
 
     from paper_2311_05945_b300 import scenes as S
-    from paper_2311_05945_b300.zema import Params
-    L = ctypes.CDLL(zbuild.build())
+    from paper_2311_05945_b300 import zema as Z
+    L = Z.lib()  # the binding's declared signatures
     DP, IP = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)
-    L.zema_default_params.argtypes = [ctypes.POINTER(Params)]
-    L.zema_create_scene.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_void_p)]
-    L.zema_add_tet_body.argtypes = [ctypes.c_void_p, ctypes.c_int32, DP, ctypes.c_int64, IP, ctypes.c_int64, DP, DP,
-                                    ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, IP]
-    L.zema_add_affine_body.argtypes = [ctypes.c_void_p, ctypes.c_int32, DP, ctypes.c_int64, IP, ctypes.c_int64, DP,
-                                       DP, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int32, IP]
-    L.zema_set_material.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32]
-    L.zema_set_springs.argtypes = [ctypes.c_void_p, ctypes.c_int32, IP, ctypes.c_int64, DP, ctypes.c_double]
-    L.zema_add_prismatic_joint.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, DP, ctypes.c_double, IP]
-    L.zema_last_error.restype = ctypes.c_char_p
-    L.zema_last_error.argtypes = [ctypes.c_void_p]
-    L.zema_destroy_scene.argtypes = [ctypes.c_void_p]
-    p = Params()
+    p = Z.Params()
     L.zema_default_params(ctypes.byref(p))
     p.n_envs = 2
     h = ctypes.c_void_p()
