@@ -410,3 +410,60 @@ def test_material_spring_and_joint_calls_checked_before_the_first_step():
     assert L.zema_last_error(h) == b"joint axis must be a nonzero finite vector"
     assert joint(4, 1) == 0 and jid.value == 1
     L.zema_destroy_scene(h)
+
+
+def test_state_calls_before_the_first_step_are_host_only():
+    # before the first step zema_get_state / zema_set_state read and write
+    # the bodies' initial states on the host (tet body: x then v, nv x 3
+    # each; affine body: q then qdot, 12 each, in the caller's frame); the
+    # whole-scene state and checkpoint calls need a built scene and return
+    # ZEMA_ERR_STATE
+    import numpy as np
+
+    from paper_2311_05945_b300 import scenes as S
+    from paper_2311_05945_b300 import zema as Z
+    L = Z.lib()
+    DP, IP = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)
+    p = Z.Params()
+    L.zema_default_params(ctypes.byref(p))
+    h = ctypes.c_void_p()
+    assert L.zema_create_scene(ctypes.byref(p), ctypes.byref(h)) == 0
+    X = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], dtype=np.float64)
+    T = np.array([[0, 1, 2, 3]], dtype=np.int32)
+    bid = ctypes.c_int32()
+    assert L.zema_add_tet_body(h, 0, X.ctypes.data_as(DP), 4, T.ctypes.data_as(IP), 1, None, None, 1e5, 0.4,
+                               1000.0, 0.5, ctypes.byref(bid)) == 0
+    V, F = S.box_surface((0.1, 0.1, 0.1), 1)
+    V = np.ascontiguousarray(V + 3.0, dtype=np.float64)
+    F = np.ascontiguousarray(F, dtype=np.int32)
+    q = np.array([0.5, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0, 1.0])
+    assert L.zema_add_affine_body(h, 0, V.ctypes.data_as(DP), len(V), F.ctypes.data_as(IP), len(F),
+                                  q.ctypes.data_as(DP), None, 1000.0, 1e8, 0.5, 0, ctypes.byref(bid)) == 0
+    out = np.full(32, -1.0)
+    n = ctypes.c_int64(-1)
+
+    def get(body, cap):
+        out[:] = -1.0
+        return L.zema_get_state(h, body, out.ctypes.data_as(DP), cap, ctypes.byref(n))
+
+    assert get(0, 24) == 0 and n.value == 24
+    assert np.array_equal(out[:12], X.ravel()) and np.all(out[12:24] == 0.0) and np.all(out[24:] == -1.0)
+    assert get(1, 24) == 0 and n.value == 24
+    assert np.array_equal(out[:12], q) and np.all(out[12:24] == 0.0)
+    assert get(0, 23) == 1 and get(1, 23) == 1 and get(2, 32) == 1 and get(-1, 32) == 1
+    assert np.all(out == -1.0)
+    st = np.arange(24, dtype=np.float64) * 0.01
+    for body in (0, 1):
+        assert L.zema_set_state(h, body, st.ctypes.data_as(DP), 24) == 0
+        assert get(body, 24) == 0 and np.array_equal(out[:24], st)
+        assert L.zema_set_state(h, body, st.ctypes.data_as(DP), 23) == 1
+    assert L.zema_set_state(h, 0, None, 24) == 1
+    STATE = 11
+    m = ctypes.c_int64()
+    assert L.zema_scene_state_size(h, ctypes.byref(m)) == STATE
+    assert L.zema_get_scene_state(h, out.ctypes.data_as(ctypes.c_void_p), 32, ctypes.byref(m)) == STATE
+    assert L.zema_set_scene_state(h, out.ctypes.data_as(ctypes.c_void_p), 32) == STATE
+    assert L.zema_checkpoint_size(h, ctypes.byref(m)) == STATE
+    assert L.zema_save_checkpoint(h, out.ctypes.data_as(ctypes.c_void_p), 256, ctypes.byref(m)) == STATE
+    assert L.zema_copy_soft_state_device(h, None, None) == STATE
+    L.zema_destroy_scene(h)
