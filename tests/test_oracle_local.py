@@ -317,6 +317,27 @@ def test_accd_head_on_closed_form():
     assert O.accd(x, p, 0)[0] == 1.0
 
 
+def test_accd_crossed_edges_closed_form():
+    # edge b crosses over edge a at height d0 (perpendicular, closest points
+    # interior) and closes at relative speed P, either edge b alone or both
+    # edges half each: the distance falls as d0 - P t and the displacement
+    # bound, after the mean displacement is taken out, is P, so the step
+    # bound is 0.9 d0 / P for s = 0.1
+    for d0, P in ((1e-2, 0.05), (3e-4, 1.0), (0.2, 0.21)):
+        x = np.array([-1.0, 0.1, 0.0, 1.0, 0.1, 0.0, 0.2, -1.0, d0, 0.2, 1.0, d0])
+        for share_a in (0.0, 0.5):
+            p = np.zeros(12)
+            p[[2, 5]] = share_a * P
+            p[[8, 11]] = -(1.0 - share_a) * P
+            t, _ = O.accd(x, p, 1)
+            assert abs(t - 0.9 * d0 / P) < 1e-12 * max(1, d0 / P), (d0, P, share_a, t)
+    # sliding along each other at a fixed height never shortens the distance
+    x = np.array([-1.0, 0.1, 0.0, 1.0, 0.1, 0.0, 0.2, -1.0, 1e-3, 0.2, 1.0, 1e-3])
+    p = np.zeros(12)
+    p[[6, 9]] = 0.3
+    assert O.accd(x, p, 1)[0] == 1.0
+
+
 def true_toi(x, p, is_ee, n=4000):
     ts = np.linspace(0, 1, n + 1)
     d = np.array([O.stencil_d2(x + t * p, is_ee)[0] for t in ts])
