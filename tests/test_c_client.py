@@ -7,6 +7,7 @@ binding's ctypes structures are checked against the C layout (size and
 every field's offset)."""
 import ctypes
 import os
+import re
 import subprocess
 
 import pytest
@@ -103,7 +104,6 @@ def test_binding_structures_match_the_c_layout(tmp_path):
 
 def test_readme_c_example_compiles_and_links(tmp_path):
     # the C example of the README stays valid against the header and links
-    import re
     lib = zbuild.build()
     text = open(os.path.join(ROOT, "README.md")).read()
     m = re.search(r"```c\n(.*?)```", text, re.S)
