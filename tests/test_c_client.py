@@ -7,7 +7,6 @@ binding's ctypes structures are checked against the C layout (size and
 every field's offset)."""
 import ctypes
 import os
-import re
 import subprocess
 
 import pytest
@@ -100,20 +99,3 @@ def test_binding_structures_match_the_c_layout(tmp_path):
         assert c["sizeof"] == ctypes.sizeof(cls), struct
         for f in names:
             assert c[f] == getattr(cls, f).offset, (struct, f)
-
-
-def test_readme_c_example_compiles_and_links(tmp_path):
-    # the C example of the README stays valid against the header and links
-    lib = zbuild.build()
-    text = open(os.path.join(ROOT, "README.md")).read()
-    m = re.search(r"```c\n(.*?)```", text, re.S)
-    assert m, "no C example"
-    src = tmp_path / "example.c"
-    src.write_text(m.group(1))
-    libdir = os.path.dirname(lib)
-    try:
-        subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I",
-                        os.path.join(ROOT, "include"), str(src), "-o", str(tmp_path / "example"), "-L", libdir,
-                        "-lzema", f"-Wl,-rpath,{libdir}"], check=True, capture_output=True, text=True)
-    except FileNotFoundError:
-        pytest.skip("no C compiler")
